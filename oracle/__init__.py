@@ -1,0 +1,250 @@
+"""FP64 CPU oracle of the Si(001) dimer-angle Langevin dynamics (arXiv 2409.06412).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The library under ``paper_2409_06412_gb300`` never does, and this
+package imports nothing from it: the two share no code.
+
+The arithmetic lives in ``xy_oracle.c`` (plain C, doubles, one loop per
+equation of the paper); this module compiles it with gcc and marshals numpy
+arrays through ctypes.  Multi-lattice runs are spread over host threads with
+one lattice per call (ctypes releases the GIL), which changes no arithmetic.
+
+Parameter vector order: (J_par, J_perp, h, p, q, eta, dt, staggered).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xy_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libxy_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+PARAM_NAMES = ("J_par", "J_perp", "h", "p", "q", "eta", "dt", "staggered")
+PAPER_PARAMS = dict(J_par=10.0, J_perp=0.1, h=1.0, p=2.5, q=2.0, eta=1.0, dt=0.01, staggered=0.0)
+T_C = 0.1969 * 10.0  # Fig. 4 caption: (beta_c J_par)^-1 = 0.1969 at J_par = 10
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libxy_oracle.so`` (gcc, -O2, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+def _declare(L):
+    P = ctypes.POINTER
+    d, i32, i64, u64, u32 = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32
+    vp = ctypes.c_void_p
+    L.xyo_philox_batch.argtypes = [i64, vp, vp, vp]
+    L.xyo_gauss_batch.argtypes = [u64, i32, i32, i64, i64, i32, vp]
+    L.xyo_wrap_batch.argtypes = [i64, vp, vp]
+    L.xyo_uniform.argtypes = [u32]
+    L.xyo_uniform.restype = d
+    L.xyo_temperature.argtypes = [i64, i32, vp, vp]
+    L.xyo_temperature.restype = d
+    L.xyo_init_theta.argtypes = [i32, i32, i32, i32, u64, i32, vp]
+    L.xyo_force.argtypes = [i32, i32, vp, vp, vp]
+    L.xyo_observe.argtypes = [i32, i32, vp, vp, vp, P(d), P(d)]
+    L.xyo_run_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i64, i64, vp, vp, i32, vp]
+    L.xyo_run_lattice.restype = i64
+    L.xyo_harmonic_msd.argtypes = [i64, i64, d, d, d, d, u64, vp]
+    L.xyo_ccl.argtypes = [i32, i32, vp, vp]
+    L.xyo_ccl.restype = i64
+    L.xyo_adjoint_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i64, i64, vp, vp,
+                                      d, d, P(d), vp, vp, vp]
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def param_vector(params: dict) -> np.ndarray:
+    full = dict(PAPER_PARAMS)
+    full.update(params or {})
+    return np.array([float(full[k]) for k in PARAM_NAMES], dtype=np.float64)
+
+
+def _knots(knots):
+    ks = np.ascontiguousarray(np.asarray(knots[0], dtype=np.int64))
+    Ts = np.ascontiguousarray(np.asarray(knots[1], dtype=np.float64))
+    assert ks.shape == Ts.shape and ks.ndim == 1 and ks.size >= 1
+    return ks, Ts
+
+
+# ---------------------------------------------------------------- primitives
+
+def philox(ctrs: np.ndarray, key) -> np.ndarray:
+    ctrs = np.ascontiguousarray(ctrs, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.empty_like(ctrs)
+    lib().xyo_philox_batch(ctrs.shape[0], _ptr(ctrs), _ptr(k), _ptr(out))
+    return out
+
+
+def uniform(words: np.ndarray) -> np.ndarray:
+    words = np.asarray(words, dtype=np.uint32)
+    return np.array([lib().xyo_uniform(int(w)) for w in words.ravel()]).reshape(words.shape)
+
+
+def gauss(seed: int, cfg: int, rep: int, n_sites: int, k: int, tag: int = 0) -> np.ndarray:
+    out = np.empty(n_sites, dtype=np.float64)
+    lib().xyo_gauss_batch(seed, cfg, rep, n_sites, k, tag, _ptr(out))
+    return out
+
+
+def wrap(x) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    out = np.empty_like(x)
+    lib().xyo_wrap_batch(x.size, _ptr(x), _ptr(out))
+    return out
+
+
+def temperature(k: int, knots) -> float:
+    ks, Ts = _knots(knots)
+    return lib().xyo_temperature(k, ks.size, _ptr(ks), _ptr(Ts))
+
+
+def init_theta(Lx, Ly, cfg, rep, seed, mode) -> np.ndarray:
+    th = np.zeros(Lx * Ly, dtype=np.float64)
+    lib().xyo_init_theta(Lx, Ly, cfg, rep, seed, mode, _ptr(th))
+    return th
+
+
+def force(Lx, Ly, params, theta) -> np.ndarray:
+    prm = param_vector(params)
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    F = np.empty_like(th)
+    lib().xyo_force(Lx, Ly, _ptr(prm), _ptr(th), _ptr(F))
+    return F
+
+
+def observe(Lx, Ly, params, theta, omega):
+    prm = param_vector(params)
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    om = np.ascontiguousarray(omega, dtype=np.float64).ravel()
+    M, E = ctypes.c_double(), ctypes.c_double()
+    lib().xyo_observe(Lx, Ly, _ptr(prm), _ptr(th), _ptr(om), ctypes.byref(M), ctypes.byref(E))
+    return M.value, E.value
+
+
+def run_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta, omega, record_every=0):
+    """Advance one lattice in place; returns the (n_rec, 2) array of (M_k, E_k)."""
+    prm = param_vector(params)
+    ks, Ts = _knots(knots)
+    assert theta.dtype == np.float64 and omega.dtype == np.float64
+    assert theta.flags.c_contiguous and omega.flags.c_contiguous
+    nrec_max = (n // record_every + 1) if record_every > 0 else 0
+    rec = np.zeros((max(nrec_max, 1), 2), dtype=np.float64)
+    nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), ks.size, _ptr(ks), _ptr(Ts),
+                                 k0, n, _ptr(theta), _ptr(omega), record_every, _ptr(rec))
+    return rec[:nrec].copy()
+
+
+def harmonic_msd(n_paths, n_steps, dt, eta, T, w2, seed=1) -> np.ndarray:
+    out = np.empty(n_steps + 1, dtype=np.float64)
+    lib().xyo_harmonic_msd(n_paths, n_steps, dt, eta, T, w2, seed, _ptr(out))
+    return out
+
+
+def ccl(Lx, Ly, theta32) -> tuple[np.ndarray, np.ndarray]:
+    """Labels (int32, min site index per component) and the sparse size
+    histogram as an (n_sizes, 2) int64 array of (size, count), ascending."""
+    th = np.ascontiguousarray(theta32, dtype=np.float32).ravel()
+    lab = np.empty(Lx * Ly, dtype=np.int32)
+    lib().xyo_ccl(Lx, Ly, _ptr(th), _ptr(lab))
+    _, sizes = np.unique(lab, return_counts=True)
+    vals, counts = np.unique(sizes, return_counts=True)
+    hist = np.stack([vals.astype(np.int64), counts.astype(np.int64)], axis=1) if vals.size else np.zeros((0, 2), np.int64)
+    return lab, hist
+
+
+def adjoint_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, wE, wM):
+    """Objective sum_{k=k0+1}^{k0+n}(w_E E_k + w_M |M_k|) of one lattice, its
+    gradient w.r.t. (J_par, J_perp, h, eta), and the final state."""
+    prm = param_vector(params)
+    ks, Ts = _knots(knots)
+    th0 = np.ascontiguousarray(theta0, dtype=np.float64).ravel()
+    om0 = np.ascontiguousarray(omega0, dtype=np.float64).ravel()
+    grad = np.zeros(4, dtype=np.float64)
+    obj = ctypes.c_double()
+    th1 = np.empty_like(th0)
+    om1 = np.empty_like(om0)
+    lib().xyo_adjoint_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), ks.size, _ptr(ks), _ptr(Ts), k0, n,
+                              _ptr(th0), _ptr(om0), wE, wM, ctypes.byref(obj), _ptr(grad),
+                              _ptr(th1), _ptr(om1))
+    return obj.value, grad, th1, om1
+
+
+# ---------------------------------------------------------------- batches
+
+def _workers():
+    return max(1, os.cpu_count() or 1)
+
+
+def run_batch(configs, thetas, omegas, step_now, n, record_every=0, t0=0, threads=None):
+    """Advance a batch of lattices described like the library's configurations.
+
+    configs: list of dicts with keys Lx, Ly, n_rep, seed, params, knots, n_total.
+    thetas/omegas: per config, float64 arrays (n_rep, Ly*Lx) updated in place
+    (omega is the full-step angular velocity).  step_now: per config step
+    counters (list, updated).  Returns (rec, moments) with rec[c] of shape
+    (n_rep, n_rec_c, 2) and moments (n_cfg, 6) = sums over replicas and records
+    at steps >= t0 of (1, M^2, M^4, E, E^2, |M|).
+    """
+    jobs = []
+    n_eff = []
+    for c, cf in enumerate(configs):
+        k0 = int(step_now[c])
+        ne = max(0, min(int(n), int(cf["n_total"]) - k0))
+        n_eff.append(ne)
+        for r in range(cf["n_rep"]):
+            jobs.append((c, r, k0, ne))
+
+    def work(job):
+        c, r, k0, ne = job
+        cf = configs[c]
+        return run_lattice(cf["Lx"], cf["Ly"], c, r, cf["seed"], cf["params"], cf["knots"], k0, ne,
+                           thetas[c][r], omegas[c][r], record_every)
+
+    with ThreadPoolExecutor(max_workers=threads or _workers()) as ex:
+        results = list(ex.map(work, jobs))
+
+    recs, moments = [], np.zeros((len(configs), 6), dtype=np.float64)
+    it = iter(results)
+    for c, cf in enumerate(configs):
+        k0 = int(step_now[c])
+        per = [next(it) for _ in range(cf["n_rep"])]
+        nr = per[0].shape[0] if per else 0
+        recs.append(np.stack(per) if per else np.zeros((0, 0, 2)))
+        if record_every > 0 and nr > 0:
+            first = -(-k0 // record_every) * record_every
+            ks = first + record_every * np.arange(nr)
+            for r in range(cf["n_rep"]):
+                for j in range(nr):
+                    if ks[j] >= t0:
+                        M, E = per[r][j]
+                        moments[c] += (1.0, M * M, M ** 4, E, E * E, abs(M))
+        step_now[c] = k0 + n_eff[c]
+    return recs, moments

@@ -1,0 +1,552 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+No test here retypes an oracle formula: each compares it with a closed form,
+a quadrature of the canonical distribution (App. A.2, Eq. Canonical-Dist), a
+library routine, brute force on tiny inputs, or an invariant; each is chosen so
+that a plausible slip (a dropped factor, a wrong sign or index, reused noise)
+fails it.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.sparse import coo_matrix
+from scipy.sparse.csgraph import connected_components
+
+import oracle
+from tests import inputs
+
+PI = math.pi
+
+
+# ----------------------------------------------------------------- noise
+
+
+def test_uniform_endpoints_and_exactness():
+    # (m + 1/2) 2^-23 with m the top 23 bits: the extremes are 2^-24 and 1 - 2^-24
+    u = oracle.uniform(np.array([0, 0xFFFFFFFF, 0x00000200, 0x80000000], dtype=np.uint32))
+    assert u[0] == 2.0 ** -24
+    assert u[1] == 1.0 - 2.0 ** -24
+    assert u[2] == 1.5 * 2.0 ** -23
+    assert u[3] == 0.5 + 2.0 ** -24
+    assert np.all(np.float32(u) == u)  # exact in binary32
+
+
+def test_philox_statistics_and_avalanche():
+    n = 1 << 18
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32)
+    ctr[:, 1] = 0x00010002
+    out = oracle.philox(ctr, (1, 0))
+    w = out.ravel()
+    # every output bit is fair (4n words, sigma = sqrt(4n)/2)
+    bits = ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.float64)
+    ones = bits.sum(axis=0)
+    sigma = math.sqrt(w.size) / 2
+    assert np.all(np.abs(ones - w.size / 2) < 5 * sigma)
+    # byte histogram chi-square (255 dof)
+    hist = np.bincount((w & 0xFF).astype(np.int64), minlength=256)
+    e = w.size / 256
+    chi2 = ((hist - e) ** 2 / e).sum()
+    assert 180 < chi2 < 340
+    # avalanche: flipping one counter bit flips ~half of the 128 output bits
+    for word in range(4):
+        for bit in (0, 7, 31):
+            c2 = ctr[:4096].copy()
+            c2[:, word] ^= np.uint32(1 << bit)
+            o2 = oracle.philox(c2, (1, 0))
+            flips = np.unpackbits((out[:4096] ^ o2).view(np.uint8)).reshape(4096, -1).sum(axis=1)
+            assert abs(flips.mean() - 64) < 1.0
+    # the key matters
+    o3 = oracle.philox(ctr[:4096], (2, 0))
+    assert np.mean(o3 == out[:4096]) < 1e-3
+
+
+def test_gaussian_moments_and_box_muller_radius():
+    g = np.concatenate([oracle.gauss(7, 3, 5, 1 << 16, k) for k in range(8)])
+    n = g.size
+    assert abs(g.mean()) < 4 / math.sqrt(n)
+    assert abs(g.var() - 1) < 4 * math.sqrt(2 / n)
+    kurt = (g ** 4).mean() / g.var() ** 2
+    assert abs(kurt - 3) < 4 * math.sqrt(24 / n)
+    # the two samples of one Box-Muller pair share the radius -2 ln u of the
+    # first word of the pair: check against the raw Philox words
+    k, seed, cfg, rep = 11, 7, 3, 5
+    gq = oracle.gauss(seed, cfg, rep, 64, k)
+    ctr = np.zeros((16, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(16)
+    ctr[:, 1] = (cfg << 16) | rep
+    ctr[:, 2] = k
+    w = oracle.philox(ctr, (seed, 0))
+    u = ((w >> 9).astype(np.float64) + 0.5) * 2.0 ** -23
+    r2 = gq.reshape(16, 4)
+    assert np.allclose(r2[:, 0] ** 2 + r2[:, 1] ** 2, -2 * np.log(u[:, 0]), rtol=1e-12)
+    assert np.allclose(r2[:, 2] ** 2 + r2[:, 3] ** 2, -2 * np.log(u[:, 2]), rtol=1e-12)
+    assert np.allclose(np.arctan2(r2[:, 1], r2[:, 0]) % (2 * PI), (2 * PI * u[:, 1]) % (2 * PI), atol=1e-9)
+
+
+def test_noise_streams_are_distinct():
+    a = oracle.gauss(1, 0, 0, 256, 5)
+    for other in (oracle.gauss(1, 0, 1, 256, 5), oracle.gauss(1, 1, 0, 256, 5),
+                  oracle.gauss(1, 0, 0, 256, 6), oracle.gauss(2, 0, 0, 256, 5),
+                  oracle.gauss(1, 0, 0, 256, 5, tag=1), oracle.gauss(1, 0, 0, 256, 5 + (1 << 32))):
+        assert abs(np.corrcoef(a, other)[0, 1]) < 0.3
+        assert not np.any(a == other)
+
+
+# ----------------------------------------------------------------- state space
+
+
+def test_wrap_interval_and_periodicity():
+    x = np.linspace(-20, 20, 100001)
+    w = oracle.wrap(x)
+    assert np.all(w >= -PI / 2) and np.all(w < PI / 2)
+    assert np.allclose(np.sin(2 * w), np.sin(2 * x), atol=1e-12)  # same state mod pi
+    inside = (x >= -PI / 2) & (x < PI / 2)
+    assert np.array_equal(w[inside], x[inside])
+    assert oracle.wrap([PI / 2])[0] == -PI / 2
+    assert oracle.wrap([-PI / 2])[0] == -PI / 2
+
+
+def test_temperature_schedule_linear_quench():
+    Tc = 1.969
+    knots = ([1000, 1000 + 1500], [1.5 * Tc, 0.0])  # eps(t) = -t / tau_Q with tau_Q = 1000 steps
+    for k, expect in [(0, 1.5 * Tc), (1000, 1.5 * Tc), (1500, Tc), (2500, 0.0), (9999, 0.0)]:
+        assert oracle.temperature(k, knots) == pytest.approx(expect, abs=1e-12)
+    for k in range(1000, 2500, 37):
+        eps = (oracle.temperature(k, knots) - Tc) / Tc
+        assert eps == pytest.approx(0.5 - (k - 1000) / 1000, abs=1e-12)
+
+
+def test_init_modes():
+    th = oracle.init_theta(16, 8, 0, 0, 1, 1)
+    assert np.all(th == 2 * PI / 5)
+    M, E = oracle.observe(16, 8, {}, th, np.zeros_like(th))
+    # ordered state: every bond cos 0 = 1, cos(p * 2pi/5) = cos(pi) = -1
+    assert E == pytest.approx(-10.0 - 0.1 - 1.0, abs=1e-12)
+    assert M == pytest.approx(math.sin(4 * PI / 5), abs=1e-12)
+    th = oracle.init_theta(64, 64, 2, 3, 9, 0)
+    assert np.all(th >= -PI / 2) and np.all(th < PI / 2)
+    # uniform on [0, 2 pi) folded twice onto the interval is uniform on it
+    assert abs(th.mean()) < 4 * (PI / math.sqrt(12)) / 64
+    assert abs(th.var() - PI ** 2 / 12) < 0.05
+
+
+# ----------------------------------------------------------------- model
+
+
+def _hamiltonian(Lx, Ly, prm, th, om):
+    """Eq. (XY-Hamilton-Kinetic) with Eq. (XY-Hamilton-Field), periodic,
+    written over whole arrays with np.roll."""
+    t = th.reshape(Ly, Lx)
+    w = om.reshape(Ly, Lx)
+    q, p = prm["q"], prm["p"]
+    return (0.5 * (w ** 2).sum()
+            - prm["J_par"] * np.cos(q * (t - np.roll(t, -1, axis=1))).sum()
+            - prm["J_perp"] * np.cos(q * (t - np.roll(t, -1, axis=0))).sum()
+            + prm["h"] * np.cos(p * t).sum())
+
+
+@pytest.mark.parametrize("Lx,Ly", [(8, 6), (4, 4), (2, 3), (5, 1)])
+def test_force_is_minus_gradient_of_hamiltonian(Lx, Ly):
+    prm = dict(inputs.PAPER, J_par=3.0, J_perp=-0.7, h=1.3)
+    rng = np.random.default_rng(5)
+    th = rng.uniform(-1.2, 1.2, Lx * Ly)
+    om = rng.standard_normal(Lx * Ly)
+    F = oracle.force(Lx, Ly, prm, th)
+    eps = 1e-6
+    for i in range(Lx * Ly):
+        tp, tm = th.copy(), th.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        dH = (_hamiltonian(Lx, Ly, prm, tp, om) - _hamiltonian(Lx, Ly, prm, tm, om)) / (2 * eps)
+        assert F[i] == pytest.approx(-dH, abs=2e-7)
+    M, E = oracle.observe(Lx, Ly, prm, th, om)
+    assert E * Lx * Ly == pytest.approx(_hamiltonian(Lx, Ly, prm, th, om), rel=1e-12)
+    assert M == pytest.approx(np.sin(2 * th).mean(), rel=1e-12)
+
+
+def test_ground_state_energy_reading_A():
+    """T = 0 relaxation from the ordered state plus noise reaches E/N = -J_par - J_perp - h."""
+    Lx = Ly = 8
+    rng = np.random.default_rng(1)
+    th = oracle.init_theta(Lx, Ly, 0, 0, 1, 1) + 0.05 * rng.standard_normal(Lx * Ly)
+    om = np.zeros(Lx * Ly)
+    oracle.run_lattice(Lx, Ly, 0, 0, 1, {}, ([0], [0.0]), 0, 6000, th, om)
+    M, E = oracle.observe(Lx, Ly, {}, th, om)
+    assert E == pytest.approx(-11.1, abs=1e-9)
+    assert np.allclose(th, 2 * PI / 5, atol=1e-6)
+
+
+def test_ground_state_energy_reading_B_checkerboard():
+    """J -> -J: the ground state is a checkerboard of +-phi*; its energy is the
+    minimum over phi of (|J_par| + |J_perp|) cos(4 phi) + h cos(p phi)."""
+    Lx = Ly = 8
+    Jx, Jy, h, p = 10.0, 0.1, 1.0, 2.5
+    phi = np.linspace(0, PI / 2, 2000001)
+    f = (Jx + Jy) * np.cos(4 * phi) + h * np.cos(p * phi)
+    e_min = f.min()
+    phi_star = phi[f.argmin()]
+    assert phi_star == pytest.approx(0.7995, abs=2e-3)
+    assert e_min == pytest.approx(-10.4989, abs=2e-3)
+    yy, xx = np.mgrid[0:Ly, 0:Lx]
+    sign = np.where((xx + yy) % 2 == 0, 1.0, -1.0).ravel()
+    rng = np.random.default_rng(2)
+    th = sign * 0.7 + 0.05 * rng.standard_normal(Lx * Ly)
+    om = np.zeros(Lx * Ly)
+    prm = dict(J_par=-Jx, J_perp=-Jy)
+    oracle.run_lattice(Lx, Ly, 0, 0, 1, prm, ([0], [0.0]), 0, 8000, th, om)
+    M, E = oracle.observe(Lx, Ly, prm, th, om)
+    assert E == pytest.approx(e_min, abs=1e-8)
+    assert np.allclose(np.abs(th), phi_star, atol=1e-5)
+    # staggered order parameter is the sign-corrected one
+    Ms, _ = oracle.observe(Lx, Ly, dict(prm, staggered=1.0), th, om)
+    assert abs(Ms) == pytest.approx(abs(math.sin(2 * phi_star)), abs=1e-5)
+    assert abs(M) < 1e-9
+
+
+def test_monotone_energy_descent_at_zero_temperature():
+    """dE/dt = -eta sum omega^2 <= 0 without noise; BBK keeps it up to O(dt^2)."""
+    Lx = Ly = 8
+    excess = []
+    for dt in (0.01, 0.005):
+        th = inputs.angles(1, Lx, Ly, 3)[0].astype(np.float64)
+        om = np.zeros(Lx * Ly)
+        n = int(round(5.0 / dt))
+        rec = oracle.run_lattice(Lx, Ly, 0, 0, 1, dict(dt=dt), ([0], [0.0]), 0, n, th, om, 1)
+        E = rec[:, 1]
+        dE = np.diff(E)
+        assert E[-1] < E[0] - 1.0
+        excess.append(max(dE.max(), 0.0))
+        assert dE.max() < 1e-3 * abs(E).max()
+    # any positive excursion is a discretisation effect: it shrinks at least ~4x when dt halves
+    if excess[0] > 1e-12:
+        assert excess[1] < excess[0] / 3.0
+
+
+# ----------------------------------------------------------------- canonical distribution
+
+
+def _sample_angles(Lx, Ly, n_rep, prm, T, n_burn, n_steps, every, seed=1):
+    samples = []
+    om_samples = []
+    for r in range(n_rep):
+        th = oracle.init_theta(Lx, Ly, 0, r, seed, 0)
+        om = np.zeros(Lx * Ly)
+        oracle.run_lattice(Lx, Ly, 0, r, seed, prm, ([0], [T]), 0, n_burn, th, om)
+        k = n_burn
+        while k < n_burn + n_steps:
+            oracle.run_lattice(Lx, Ly, 0, r, seed, prm, ([0], [T]), k, every, th, om)
+            k += every
+            samples.append(th.copy())
+            om_samples.append(om.copy())
+    return np.array(samples), np.array(om_samples)
+
+
+@pytest.mark.parametrize("T", [0.5, 2.0, 10.0])
+def test_single_angle_boltzmann(T):
+    """J = 0: each angle follows p(theta) ~ exp(-h cos(p theta) / T) on [-pi/2, pi/2)."""
+    prm = dict(J_par=0.0, J_perp=0.0, h=1.0)
+    th, om = _sample_angles(32, 32, 1, prm, T, 500, 8000, 40)
+    x = th.ravel()
+    edges = np.linspace(-PI / 2, PI / 2, 41)
+    hist, _ = np.histogram(x, bins=edges)
+    Z = integrate.quad(lambda t: math.exp(-math.cos(2.5 * t) / T), -PI / 2, PI / 2)[0]
+    prob = np.array([integrate.quad(lambda t: math.exp(-math.cos(2.5 * t) / T), a, b)[0] / Z
+                     for a, b in zip(edges[:-1], edges[1:])])
+    expect = prob * x.size
+    # samples are correlated in time: allow an effective-sample inflation of 4
+    z = (hist - expect) / np.sqrt(4 * expect)
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    # equipartition <omega^2> = T (pins one Gaussian per time point shared by both kicks)
+    w2 = (om ** 2).mean()
+    assert w2 == pytest.approx(T, rel=0.03)
+
+
+def test_equipartition_halves_with_fresh_draws_reading():
+    """If each half-kick drew a fresh Gaussian the injected variance would halve:
+    <omega^2> = T/2.  The oracle's shared-sample reading must give T."""
+    prm = dict(J_par=0.0, J_perp=0.0, h=0.0)
+    _, om = _sample_angles(32, 32, 1, prm, 3.0, 500, 4000, 20)
+    assert (om ** 2).mean() == pytest.approx(3.0, rel=0.03)
+
+
+def test_two_by_two_lattice_boltzmann():
+    """2 x 2 periodic lattice (each bond counted twice by the forward-bond sum):
+    averages against 4-D quadrature of exp(-H_XY / T)."""
+    prm = dict(J_par=1.0, J_perp=0.4, h=1.0)
+    T = 1.5
+    th, _ = _sample_angles(2, 2, 64, prm, T, 400, 6000, 20)
+    t = th.reshape(-1, 4)
+    n = 36
+    g = -PI / 2 + (np.arange(n) + 0.5) * PI / n
+    a, b, c, d = np.meshgrid(g, g, g, g, indexing="ij")
+    # sites: 0=(0,0) 1=(1,0) 2=(0,1) 3=(1,1); x-bonds 0-1, 2-3; y-bonds 0-2, 1-3; each twice
+    H = (-2 * prm["J_par"] * (np.cos(2 * (a - b)) + np.cos(2 * (c - d)))
+         - 2 * prm["J_perp"] * (np.cos(2 * (a - c)) + np.cos(2 * (b - d)))
+         + prm["h"] * (np.cos(2.5 * a) + np.cos(2.5 * b) + np.cos(2.5 * c) + np.cos(2.5 * d)))
+    w = np.exp(-(H - H.min()) / T)
+    w /= w.sum()
+    checks = {
+        "cos2(t0-t1)": (np.cos(2 * (a - b)), np.cos(2 * (t[:, 0] - t[:, 1]))),
+        "cos2(t0-t2)": (np.cos(2 * (a - c)), np.cos(2 * (t[:, 0] - t[:, 2]))),
+        "cos(p t0)": (np.cos(2.5 * a), np.cos(2.5 * t[:, 0])),
+        "sin^2 2t0": (np.sin(2 * a) ** 2, np.sin(2 * t[:, 0]) ** 2),
+        "sin2t0 sin2t3": (np.sin(2 * a) * np.sin(2 * d), np.sin(2 * t[:, 0]) * np.sin(2 * t[:, 3])),
+    }
+    for name, (f_grid, f_samp) in checks.items():
+        exact = (w * f_grid).sum()
+        err = f_samp.std() / math.sqrt(f_samp.size / 4.0)
+        assert abs(f_samp.mean() - exact) < 5 * err + 2e-3, (name, f_samp.mean(), exact, err)
+
+
+def test_j0_observable_closed_forms():
+    """J = 0 sites are independent: <M^2> = s2/N, <M^4> = (3(N-1)s2^2 + m4)/N^3 and
+    <E> = T/2 + h<cos p theta>, with s2 = <sin^2 2t>, m4 = <sin^4 2t> by quadrature."""
+    T = 2.0
+    L = 4
+    N = L * L
+    cfg = inputs.config(L, L, 96, seed=3, J_par=0.0, J_perp=0.0, h=1.0, knots=([0], [T]))
+    th = np.stack([oracle.init_theta(L, L, 0, r, 3, 0) for r in range(96)])
+    om = np.zeros_like(th)
+    step = [0]
+    rec, mom = oracle.run_batch([cfg], [th], [om], step, 12000, record_every=20, t0=1000)
+    assert step[0] == 12000
+    p = lambda t: math.exp(-math.cos(2.5 * t) / T)
+    Z = integrate.quad(p, -PI / 2, PI / 2)[0]
+    s2 = integrate.quad(lambda t: p(t) * math.sin(2 * t) ** 2, -PI / 2, PI / 2)[0] / Z
+    m4 = integrate.quad(lambda t: p(t) * math.sin(2 * t) ** 4, -PI / 2, PI / 2)[0] / Z
+    cp = integrate.quad(lambda t: p(t) * math.cos(2.5 * t), -PI / 2, PI / 2)[0] / Z
+    cnt = mom[0, 0]
+    M2 = mom[0, 1] / cnt
+    M4 = mom[0, 2] / cnt
+    Emean = mom[0, 3] / cnt
+    r = rec[0][:, 50:, :]
+    Ms = r[:, :, 0].ravel()
+    Es = r[:, :, 1].ravel()
+    n_eff = Ms.size / 3.0
+    assert M2 == pytest.approx(s2 / N, abs=5 * (Ms ** 2).std() / math.sqrt(n_eff))
+    assert M4 == pytest.approx((3 * (N - 1) * s2 ** 2 + m4) / N ** 3, abs=5 * (Ms ** 4).std() / math.sqrt(n_eff))
+    assert Emean == pytest.approx(T / 2 + cp, abs=5 * Es.std() / math.sqrt(n_eff))
+    assert abs(mom[0, 5] / cnt - np.abs(Ms).mean()) < 1e-3
+
+
+# ----------------------------------------------------------------- paper benchmarks
+
+
+def _msd_closed_form(t, eta, T, w2, m=1.0):
+    """Eq. (MSD-HO), evaluated in complex arithmetic (lambda_+- complex when eta < 2 omega)."""
+    root = np.sqrt(complex(eta * eta - 4 * w2))
+    lp, lm = 0.5 * (eta + root), 0.5 * (eta - root)
+    pre = eta * T / (m * (lp - lm) ** 2)
+    val = pre * ((lp + lm) / (lp * lm) + 4 / (lp + lm) * (np.exp(-(lp + lm) * t) - 1)
+                 - np.exp(-2 * lp * t) / lp - np.exp(-2 * lm * t) / lm)
+    return val.real
+
+
+@pytest.mark.parametrize("dt", [0.05, 0.01])
+@pytest.mark.parametrize("eta", [1.0, 5.0, 20.0])
+def test_benchmark_harmonic_msd(dt, eta):
+    """App. A.2 benchmark 1: omega^2 = 20, T = 20, m = 1, 1e5 paths."""
+    n_paths = 100000
+    t_end = 3.0
+    n = int(round(t_end / dt))
+    msd = oracle.harmonic_msd(n_paths, n, dt, eta, 20.0, 20.0)
+    t = dt * np.arange(n + 1)
+    exact = _msd_closed_form(t, eta, 20.0, 20.0)
+    assert abs(exact[-1] - 1.0) < 0.02 or eta < 2  # T / omega^2 = 1 in the long-time limit
+    # statistical error of a mean of x^2 over Gaussian paths, at the equilibrium scale
+    # T / omega^2 = 1, plus an O(dt) allowance for the discretisation ("small
+    # deviations" at dt = 0.05, Fig. 8): at early times the one-step scheme has an
+    # O(1) relative error on a tiny value, so the bound is absolute
+    sigma_eq = math.sqrt(2.0) * 1.0 / math.sqrt(n_paths)
+    dev = np.abs(msd - exact)
+    assert dev.max() < 5 * sigma_eq + 0.3 * dt, dev.max()
+    assert np.mean(np.abs(msd[n // 2:] - exact[n // 2:]) / exact[n // 2:]) < 0.02
+
+
+def test_benchmark_pair_cross_section():
+    """App. A.2 benchmark 2 (Fig. 9): two sites, one bond J = 40, h = 100, p = 2.5,
+    eta = 1, T = 100; theta_1 histogram (100 bins) in the slice theta_2 in
+    [0.975, 1.125] against the canonical density.  A 2 x 1 periodic lattice
+    counts the bond twice, so it runs with J_par = J / 2."""
+    J, h, T = 40.0, 100.0, 100.0
+    prm = dict(J_par=J / 2, J_perp=0.0, h=h, p=2.5)
+    n_pairs = 1024
+    Lx = 2 * n_pairs  # independent pairs side by side would couple; run them as replicas instead
+    del Lx
+    samples = []
+    every = 100
+    for r in range(n_pairs):
+        th = oracle.init_theta(2, 1, 0, r, 11, 0)
+        om = np.zeros(2)
+        oracle.run_lattice(2, 1, 0, r, 11, prm, ([0], [T]), 0, 500, th, om)
+        k = 500
+        for _ in range(60):
+            oracle.run_lattice(2, 1, 0, r, 11, prm, ([0], [T]), k, every, th, om)
+            k += every
+            samples.append(th.copy())
+    s = np.array(samples)
+    sel = (s[:, 1] >= 0.975) & (s[:, 1] <= 1.125)
+    t1 = s[sel, 0]
+    assert t1.size > 2000
+    edges = np.linspace(-PI / 2, PI / 2, 101)
+    hist, _ = np.histogram(t1, bins=edges)
+
+    def dens(a, b):
+        return integrate.dblquad(
+            lambda t2, t1_: math.exp(-(-J * math.cos(2 * (t1_ - t2)) + h * math.cos(2.5 * t1_)
+                                       + h * math.cos(2.5 * t2)) / T),
+            a, b, 0.975, 1.125)[0]
+
+    prob = np.array([dens(a, b) for a, b in zip(edges[:-1], edges[1:])])
+    prob /= prob.sum()
+    expect = prob * t1.size
+    m = expect > 5
+    chi2 = (((hist - expect) ** 2)[m] / expect[m]).sum() / m.sum()
+    assert chi2 < 2.0, chi2
+    # mean of theta_1 in the slice within 4 sigma
+    mu = (prob * 0.5 * (edges[1:] + edges[:-1])).sum()
+    assert abs(t1.mean() - mu) < 4 * t1.std() / math.sqrt(t1.size / 2)
+
+
+# ----------------------------------------------------------------- resume and domains
+
+
+def test_resume_is_bit_identical():
+    L = 8
+    cfg = dict(Lx=L, Ly=L, cfg=1, seed=5)
+    th0 = inputs.angles(1, L, L, 4)[0].astype(np.float64)
+    a_th, a_om = th0.copy(), np.zeros(L * L)
+    rec_a = oracle.run_lattice(L, L, 1, 0, 5, {}, ([0, 300], [3.0, 1.0]), 0, 300, a_th, a_om, 7)
+    b_th, b_om = th0.copy(), np.zeros(L * L)
+    rec_b1 = oracle.run_lattice(L, L, 1, 0, 5, {}, ([0, 300], [3.0, 1.0]), 0, 113, b_th, b_om, 7)
+    rec_b2 = oracle.run_lattice(L, L, 1, 0, 5, {}, ([0, 300], [3.0, 1.0]), 113, 187, b_th, b_om, 7)
+    assert np.array_equal(a_th, b_th) and np.array_equal(a_om, b_om)
+    assert np.array_equal(rec_a, np.concatenate([rec_b1, rec_b2]))
+    del cfg
+
+
+def _periodic_components(spins):
+    Ly, Lx = spins.shape
+    idx = np.arange(Lx * Ly).reshape(Ly, Lx)
+    rows, cols = [], []
+    for dy, dx in ((0, 1), (1, 0)):
+        nb = np.roll(np.roll(idx, -dy, axis=0), -dx, axis=1)
+        same = spins == np.roll(np.roll(spins, -dy, axis=0), -dx, axis=1)
+        rows.append(idx[same])
+        cols.append(nb[same])
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    g = coo_matrix((np.ones(r.size), (r, c)), shape=(Lx * Ly, Lx * Ly))
+    _, comp = connected_components(g, directed=False)
+    # canonical label: smallest site index of each component
+    mins = np.full(comp.max() + 1, Lx * Ly)
+    np.minimum.at(mins, comp, np.arange(Lx * Ly))
+    return mins[comp]
+
+
+@pytest.mark.parametrize("case", ["random", "stripes_x", "stripes_y", "checker", "uniform", "spiral", "sparse"])
+def test_ccl_against_graph_library(case):
+    L = 24
+    if case == "random":
+        s = inputs.random_spins(L, L + 8, 4)
+    elif case == "stripes_x":
+        s = inputs.stripes(L, L, 3, 0)
+    elif case == "stripes_y":
+        s = inputs.stripes(L, L, 5, 1)
+    elif case == "checker":
+        s = inputs.checkerboard(L, L)
+    elif case == "uniform":
+        s = np.ones((L, L), dtype=np.int8)
+    elif case == "spiral":
+        s = inputs.spiral(L)
+    else:
+        s = inputs.random_spins(L, L, 9, p_up=0.1)
+    Ly, Lx = s.shape
+    th = inputs.spins_to_theta(s)
+    lab, hist = oracle.ccl(Lx, Ly, th)
+    ref = _periodic_components(s)
+    assert np.array_equal(lab, ref.astype(np.int32))
+    sizes = np.bincount(ref)[np.unique(ref)]
+    vals, cnts = np.unique(sizes, return_counts=True)
+    assert np.array_equal(hist, np.stack([vals, cnts], axis=1))
+    assert hist[:, 0] @ hist[:, 1] == Lx * Ly
+    if case == "checker":
+        assert hist.tolist() == [[1, Lx * Ly]]
+    if case == "uniform":
+        assert hist.tolist() == [[Lx * Ly, 1]]
+    if case == "stripes_x":
+        # stripes of width 3 on a 24-periodic ring: 8 vertical bands, each one component
+        assert hist.tolist() == [[3 * L, 8]]
+
+
+def test_ccl_zero_angle_counts_as_up():
+    th = np.array([0.0, -0.0, -1e-7, 1e-7], dtype=np.float32)
+    lab, _ = oracle.ccl(4, 1, th)
+    # theta >= 0 (both signed zeros) is up: sites 0,1,3 are up and 3-0 wrap
+    assert lab.tolist() == [0, 0, 2, 0]
+
+
+# ----------------------------------------------------------------- adjoint
+
+
+def _fd_grad(Lx, Ly, prm, knots, n, th0, om0, wE, wM, rel=1e-5):
+    names = ("J_par", "J_perp", "h", "eta")
+    g = []
+    for nm in names:
+        base = prm[nm]
+        eps = rel * max(1.0, abs(base))
+        vals = []
+        for s in (+1, -1):
+            p2 = dict(prm)
+            p2[nm] = base + s * eps
+            obj, _, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, p2, knots, 0, n, th0, om0, wE, wM)
+            vals.append(obj)
+        g.append((vals[0] - vals[1]) / (2 * eps))
+    return np.array(g)
+
+
+@pytest.mark.parametrize("wE,wM", [(1.0, 0.0), (0.0, 1.0), (0.7, 0.3)])
+def test_adjoint_matches_finite_differences_smooth_field(wE, wM):
+    """p = 2: cos(p theta) is pi-periodic, the dynamics is smooth, so the
+    pathwise gradient equals central differences up to O(eps^2)."""
+    Lx, Ly = 6, 4
+    prm = dict(inputs.PAPER, J_par=2.0, J_perp=0.5, h=1.0, p=2.0, eta=0.8)
+    th0 = inputs.angles(1, Lx, Ly, 8)[0].astype(np.float64)
+    om0 = 0.3 * inputs.velocities(1, Lx, Ly, 8)[0].astype(np.float64)
+    knots = ([0, 150], [1.0, 0.5])
+    obj, grad, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, 150, th0, om0, wE, wM)
+    fd = _fd_grad(Lx, Ly, prm, knots, 150, th0, om0, wE, wM)
+    assert np.allclose(grad, fd, rtol=1e-6, atol=1e-7 * max(1.0, np.abs(fd).max())), (grad, fd)
+
+
+def test_adjoint_matches_finite_differences_paper_field_low_T():
+    """p = 2.5 away from the kink at +-pi/2: same agreement."""
+    Lx, Ly = 8, 4
+    prm = dict(inputs.PAPER, h=3.0)
+    th0 = oracle.init_theta(Lx, Ly, 0, 0, 1, 1) + 0.05 * inputs.velocities(1, Lx, Ly, 2)[0]
+    om0 = np.zeros(Lx * Ly)
+    knots = ([0], [0.05])
+    obj, grad, th1, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, 200, th0, om0, 1.0, 0.5)
+    assert np.abs(th1).max() < PI / 2 - 0.1
+    fd = _fd_grad(Lx, Ly, prm, knots, 200, th0, om0, 1.0, 0.5)
+    assert np.allclose(grad, fd, rtol=1e-6, atol=1e-8 * max(1.0, np.abs(fd).max())), (grad, fd)
+
+
+def test_adjoint_forward_equals_stepper():
+    """The adjoint's forward trajectory and objective are the stepper's."""
+    Lx, Ly = 8, 8
+    th0 = inputs.angles(1, Lx, Ly, 1)[0].astype(np.float64)
+    om0 = np.zeros(Lx * Ly)
+    knots = ([0], [inputs.T_C])
+    obj, grad, th1, om1 = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th0, om0, 0.6, 0.4)
+    th, om = th0.copy(), om0.copy()
+    oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th, om)
+    assert np.array_equal(th, th1) and np.array_equal(om, om1)
+    # objective = sum over k = 1..n of the stepper's records
+    th, om = th0.copy(), om0.copy()
+    rec = oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 41, th, om, 1)
+    expect = (0.6 * rec[1:, 1] + 0.4 * np.abs(rec[1:, 0])).sum()
+    assert obj == pytest.approx(expect, rel=1e-13)
