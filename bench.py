@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the BBK Langevin stepper on the static-criticality workload.
+
+Workload (one bench "step" = 10 BBK time steps of the whole batch, with one
+observable record per lattice and FP64 moment accumulation):
+  L in {128, 256, 512, 1024} periodic lattices, 32 temperatures uniform in
+  [0.9, 1.1] T_c, 16 replicas each (2048 lattices, 7.13e8 sites), ordered
+  start, J_par = 10, J_perp = 0.1, h = 1, p = 2.5, q = 2, eta = 1, dt = 0.01.
+Metric: site-updates per second (whole job), with the HBM roofline of the
+dominant kernel, the plain per-configuration launch path, the adjoint/forward
+cost on the differentiation workload (L = 256 x 64 replicas, 2000 steps,
+checkpoint every 100), domain labelling throughput and the FP64 CPU oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own copy of the batch (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TC = 1.969
+LS = (128, 256, 512, 1024)
+N_TEMPS, N_REP = 32, 16
+INNER = 10            # BBK steps per bench step
+N_TOTAL = 10 ** 5     # run length of every configuration
+T0 = N_TOTAL // 5     # moments discard the first fifth
+METRIC = "site-updates/s/GPU and % HBM roofline, batched vs plain; adjoint/forward cost"
+WORKLOAD = "static criticality: L in {128,256,512,1024}, 32 T in [0.9,1.1] T_c, 16 replicas, ordered start"
+BYTES_PER_SU = 16.0   # theta and omega (FP32) read and written once per site-update
+
+
+def temps():
+    return [TC * (0.9 + 0.2 * i / (N_TEMPS - 1)) for i in range(N_TEMPS)]
+
+
+def static_configs(seed):
+    from paper_2409_06412_gb300 import XY_INIT_ORDERED, Config
+    return [Config(Lx=L, Ly=L, n_replicas=N_REP, seed=seed, init_mode=XY_INIT_ORDERED, knots=((0,), (T,)),
+                   n_total=N_TOTAL) for L in LS for T in temps()]
+
+
+def sites_total():
+    return N_TEMPS * N_REP * sum(L * L for L in LS)
+
+
+# ------------------------------------------------------------------ clocks
+
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={CLOCK_Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel):
+    """Per-site DRAM bytes of `kernel` from the committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2409_06412_gb300", "csrc", "xy_step.cu"), "rb").read()
+    src += open(os.path.join(ROOT, "paper_2409_06412_gb300", "csrc", "xy_device.cuh"), "rb").read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("source") == digest:
+            return float(f["dram_bytes_per_site"])
+    return None
+
+
+def cuda_time(fn, stream):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    one lattice per L (temperature T_c, replica 0), 10-step chunks until the
+    budget is spent; lattices run concurrently on the host cores."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    specs = []
+    for i, L in enumerate(LS):
+        th = oracle.init_theta(L, L, 16 * i, 0, 1, 1)
+        specs.append((L, 16 * i, th, np.zeros_like(th)))
+    prm = {}
+    su, t0, k = 0, time.perf_counter(), 0
+
+    def run(sp):
+        L, c, th, om = sp
+        oracle.run_lattice(L, L, c, 0, 1, prm, ([0], [TC]), k, INNER, th, om)
+        return L * L * INNER
+
+    with ThreadPoolExecutor(max_workers=min(cores, len(specs))) as ex:
+        while time.perf_counter() - t0 < budget_s:
+            su += sum(ex.map(run, specs))
+            k += INNER
+    dt = time.perf_counter() - t0
+    return {"value": su / dt, "unit": "site-updates/s", "cores": min(cores, len(specs)), "kind": "oracle",
+            "sample": f"one lattice per L in {list(LS)} at T_c, {k} steps each ({su:.3g} site-updates, {dt:.1f} s)"}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2409_06412_gb300 import XY_PATH_BATCHED, XY_PATH_PLAIN, Config, Lattice, build
+    from paper_2409_06412_gb300 import _lib as LL
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    lat = Lattice(static_configs(seed=1 + rank), stream=stream)
+    S = sites_total()
+    R = INNER // INNER + 1
+
+    def bench_step():
+        lat.step(INNER, record_every=INNER, t0=T0)
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    l0 = lat.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        bench_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = lat.kernel_launches() - l0
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    su_step = S * INNER
+    value = world * args.steps * su_step / elapsed
+    mom, steps = lat.observe()
+
+    extra = {}
+    if rank == 0:
+        # dominant kernel, timed live with events on its stream
+        lat.set_kernel_timing(True)
+        for _ in range(3):
+            bench_step()
+        ms, nl = lat.kernel_timing()
+        lat.set_kernel_timing(False)
+        strip_sites = N_TEMPS * N_REP * sum(L * L for L in LS if L >= 256)
+        res_sites = N_TEMPS * N_REP * sum(L * L for L in LS if L < 256)
+        hbm, peak_kind = peaks()
+        strip_s = ms[1] / 1e3 / max(nl[1], 1)
+        achieved = BYTES_PER_SU * strip_sites / strip_s / 1e9
+        traffic = ncu_traffic("strip_step_kernel")
+        extra["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(achieved / hbm, 4), "peak_kind": f"{peak_kind} copy bandwidth",
+                             "kernel": "strip_step_kernel",
+                             "traffic": (round(traffic * strip_sites) if traffic else None),
+                             "algorithmic_bytes_per_launch": int(BYTES_PER_SU * strip_sites),
+                             "launch_ms": round(strip_s * 1e3, 4)}
+        extra["kernel_ms_per_step"] = {"resident": round(ms[0] / max(nl[0], 1) / INNER, 4),
+                                       "strip": round(strip_s * 1e3, 4)}
+        extra["resident_su_per_s"] = (res_sites * INNER) / (ms[0] / 1e3 / max(nl[0], 1)) if nl[0] else None
+
+        # plain per-configuration launch path on the same batch
+        lat.set_path(XY_PATH_PLAIN)
+        bench_step()
+        n_plain = 2
+        tp = cuda_time(lambda: [bench_step() for _ in range(n_plain)], stream)
+        lat.set_path(XY_PATH_BATCHED)
+        plain = n_plain * su_step / tp
+        extra["plain"] = {"value": plain, "unit": "site-updates/s", "batched_over_plain": value / world / plain}
+
+        # end to end through the public API with host buffers: each step loads
+        # the state from pinned host memory (xy_load) and returns the records
+        # to host memory
+        blob = lat.save()
+        pinned = torch.empty(len(blob), dtype=torch.uint8).pin_memory()
+        pinned.numpy()[:] = np.frombuffer(blob, dtype=np.uint8)
+        rec_host = torch.empty((lat.n_lattices, R, 2), dtype=torch.float64).pin_memory()
+        lib = LL.load()
+        import ctypes
+
+        def e2e_step():
+            LL.check(lib.xy_load(lat._h, ctypes.c_void_p(pinned.data_ptr()), len(blob)), "xy_load")
+            lat.step(INNER, record_every=INNER, t0=T0, rec=rec_host)
+
+        e2e_step()
+        n_e2e = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        extra["e2e"] = {"value": n_e2e * su_step / te, "unit": "site-updates/s",
+                        "h2d_bytes_per_step": len(blob), "d2h_bytes_per_step": int(rec_host.numel() * 8)}
+
+        # domain labelling throughput on the 512 L = 1024 lattices (first 64)
+        b0 = 3 * N_TEMPS * N_REP
+        lat.label_domains(b0, 8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.label_domains(b0, 64)
+        torch.cuda.synchronize()
+        tl = time.perf_counter() - t0
+        extra["ccl"] = {"value": 64 * 1024 * 1024 / tl, "unit": "labelled sites/s", "lattices": 64, "L": 1024}
+
+        # plain method, 64 x 64 single lattice, 1e4 steps: resident kernel vs plain launches
+        c1 = Lattice([Config(Lx=64, Ly=64, n_replicas=1, seed=1, init_mode=0, knots=((0,), (TC,)),
+                             n_total=10 ** 9)], stream=stream)
+        c1.step(100)
+        t_b = cuda_time(lambda: c1.step(10 ** 4), stream)
+        c1.set_path(XY_PATH_PLAIN)
+        c1.step(100)
+        t_p = cuda_time(lambda: c1.step(10 ** 4), stream)
+        extra["plain_method_64x64"] = {"batched_su_per_s": 4096 * 1e4 / t_b, "plain_su_per_s": 4096 * 1e4 / t_p,
+                                       "ratio": t_p / t_b}
+        c1.close()
+
+        # adjoint / forward on the differentiation workload
+        del pinned
+        lat.close()
+        torch.cuda.empty_cache()
+        c5 = Lattice([Config(Lx=256, Ly=256, n_replicas=64, seed=1, init_mode=1, knots=((0,), (TC,)),
+                             n_total=10 ** 9)], stream=stream)
+        c5.step(10)
+        snap = c5.save()
+        t_f = cuda_time(lambda: c5.step(2000), stream)
+        c5.load(snap)
+        t0 = time.perf_counter()
+        obj, grads = c5.adjoint(2000, checkpoint_every=100, w_E=1.0, w_M=1.0)
+        t_a = time.perf_counter() - t0
+        extra["adjoint"] = {"forward_s": t_f, "adjoint_s": t_a, "adjoint_over_forward": t_a / t_f,
+                            "objective": obj, "grads": grads[0].tolist(),
+                            "workload": "L=256 x 64 replicas, 2000 steps at T_c, checkpoint every 100"}
+        c5.close()
+        if world == 1:
+            extra["cpu_baseline"] = cpu_baseline()
+
+    if rank == 0:
+        U = (mom[:, 2] / mom[:, 0]) / (mom[:, 1] / mom[:, 0]) ** 2
+        line = {
+            "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattices": len(static_configs(1)) * N_REP, "sites": S,
+                       "bbk_steps_per_step": INNER, "record_every": INNER, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (5.7 GB state per GPU), no flush"},
+            "gpu_launches": int(launches), "clocks": clk,
+            "binder_U_range": [float(U.min()), float(U.max())],
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The FP64 oracle as it stands on the host cores, on the same metric:
+    each step is 10 BBK steps of a bounded sample of the workload (one lattice
+    per L at T_c)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    lats = []
+    for i, L in enumerate(LS):
+        th = oracle.init_theta(L, L, 16 * i, 0, 1, 1)
+        lats.append([L, 16 * i, th, np.zeros_like(th), 0])
+
+    def run(sp):
+        L, c, th, om, k = sp
+        oracle.run_lattice(L, L, c, 0, 1, {}, ([0], [TC]), k, INNER, th, om)
+        sp[4] += INNER
+        return L * L * INNER
+
+    su_step = sum(L * L for L in LS) * INNER
+    with ThreadPoolExecutor(max_workers=min(cores, len(lats))) as ex:
+        for _ in range(args.warmup):
+            list(ex.map(run, lats))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            list(ex.map(run, lats))
+        dt = time.perf_counter() - t0
+    value = args.steps * su_step / dt
+    sample = f"one lattice per L in {list(LS)} at T_c, {INNER} BBK steps per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": min(cores, len(lats)), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * xy_lattice.h -- C ABI of the GB300 (sm_103a) Langevin stepper for the
+ * symmetry-broken XY model of Si(001) dimer angles (arXiv 2409.06412).
+ *
+ * The model (paper, Sec. III):
+ *   H = sum_ij omega_ij^2 / 2                                    Eq. (XY-Hamilton-Kinetic)
+ *     - J_par  sum cos q(theta_ij - theta_i+1,j)
+ *     - J_perp sum cos q(theta_ij - theta_i,j+1)
+ *     + h sum cos(p theta_ij)                                    Eq. (XY-Hamilton-Field)
+ * with theta in [-pi/2, pi/2) (Sec. III.C), q = 2, p = 2.5, and the Langevin
+ * equations of Sec. III.D integrated by the BBK scheme of App. A.1, the angle
+ * mapped back into [-pi/2, pi/2) after every step.
+ *
+ * Conventions for every call below.
+ *  - A lattice object holds n_cfg configurations; configuration c has
+ *    n_replicas independent periodic Lx x Ly lattices.  All lattices of all
+ *    configurations are stored back to back, configuration after
+ *    configuration, replica after replica, row-major inside a lattice
+ *    (site s = y * Lx + x; x runs along the dimer rows, the J_par direction).
+ *    "Lattice b" below is the flattened (configuration, replica) index.
+ *  - theta and omega are caller-owned DEVICE buffers of float (FP32), one value
+ *    per site; the library borrows them for the lifetime of the object and
+ *    keeps the live state in them between calls.  omega holds the leapfrog
+ *    half-step angular velocity omega_{k-1/2} of the state at integer step k;
+ *    xy_omega_full() returns the full-step omega_k of the paper's scheme.
+ *  - Every call returns XY_OK (0) or a negative XY_E* code; xy_last_error()
+ *    then gives a message (thread-local, valid until the next call on that
+ *    thread).  No call throws or aborts.
+ *  - Calls are asynchronous on the stream given at creation unless stated
+ *    otherwise.  Output pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; a host pointer makes the call synchronous.
+ *  - Thread safety: one lattice object must not be used from two threads at
+ *    once.  Distinct objects are independent.
+ */
+#ifndef XY_LATTICE_H
+#define XY_LATTICE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XY_OK 0
+#define XY_EINVAL (-1)   /* bad argument, shape or state; nothing was launched */
+#define XY_ENOMEM (-2)   /* a device or host allocation failed */
+#define XY_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define XY_ETIMEOUT (-4) /* a bounded device-side loop ran out of iterations */
+#define XY_ENAN (-5)     /* a non-finite observable was produced */
+
+#define XY_INIT_UNIFORM 0 /* theta = wrap(2 pi u), u uniform from the noise generator (stream tag 1), omega = 0 */
+#define XY_INIT_ORDERED 1 /* theta = +2 pi / 5 everywhere (a field minimum at p = 2.5), omega = 0 */
+#define XY_INIT_USER 2    /* theta and the FULL-STEP omega_0 are taken from the caller's buffers */
+
+#define XY_PATH_BATCHED 0 /* tuned kernels, all configurations per launch, CUDA-graph chunks */
+#define XY_PATH_PLAIN 1   /* one plain launch per step per configuration (reference path) */
+
+#define XY_MAX_KNOTS 16
+
+typedef struct xy_lattice xy_lattice;
+
+/* One configuration: Lx % 4 == 0, Lx >= 4, Ly >= 1, 1 <= n_replicas <= 65535,
+ * at most 65536 configurations per object.  seed keys the Philox4x32-10
+ * noise; configuration index c and replica r enter its counter, so
+ * configurations that share a seed still draw independent noise. */
+typedef struct {
+    int32_t Lx;
+    int32_t Ly;
+    int32_t n_replicas;
+    int32_t init_mode;
+    uint64_t seed;
+} xy_config_desc;
+
+/* Model and integrator parameters of one configuration (Sec. III, App. A.1;
+ * the paper's production values are J_par = 10, J_perp = 0.1, h = 1, p = 2.5,
+ * q = 2, eta = 1, with dt = 0.01).  staggered_M != 0 measures the order
+ * parameter with the sign (-1)^(x+y) (antiferromagnetic reading of Sec. III.B). */
+typedef struct {
+    double J_par;
+    double J_perp;
+    double h;
+    double p;
+    double q;
+    double eta;
+    double dt;
+    int32_t staggered_M;
+    int32_t reserved;
+} xy_params;
+
+/* Create a lattice object on `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  theta/omega: device buffers of sum_c n_replicas*Lx*Ly
+ * floats, 16-byte aligned.  Initialises theta/omega per init_mode on the
+ * stream.  Allocates the second state buffer of the double-buffered stepper
+ * (8 bytes per site) and small tables.  *out receives the object. */
+int xy_lattice_create(const xy_config_desc* cfg, int n_cfg, float* theta, float* omega,
+                      void* cuda_stream, xy_lattice** out);
+
+/* Set the parameters of configuration cfg (must precede the first step).
+ * Requires dt > 0, eta >= 0. */
+int xy_set_params(xy_lattice* lat, int cfg, const xy_params* params);
+
+/* Temperature schedule of configuration cfg: T(k) piecewise linear through
+ * the knots (step_knots[i], T_knots[i]) (strictly increasing steps, T >= 0),
+ * constant outside them; a linear ramp is the quench eps(t) = -t / tau_Q of
+ * Sec. II.B, Eq. (Linear-Quench).  n_steps_total bounds the run of this
+ * configuration: stepping stops there (uneven run lengths in one batch). */
+int xy_set_schedule(xy_lattice* lat, int cfg, const int64_t* step_knots, const double* T_knots,
+                    int n_knots, int64_t n_steps_total);
+
+/* Advance every configuration by min(n, n_steps_total - step) BBK steps.
+ * record_every > 0: at every step k of this call with k % record_every == 0
+ * the lattice averages M_k = (1/N) sum sin(q theta_i) (Sec. IV.A, Eq.
+ * lattice-average) and E_k = H_k / N of the state at step k are evaluated;
+ * those with k >= t0_discard enter the FP64 running moments (xy_observe).
+ * rec (nullable; host or device): double[B][R][2] with B the total number of
+ * lattices and R = n / record_every + 1; entry r of lattice b holds (M, E) of
+ * the r-th recorded step of its configuration in this call (unfilled entries
+ * are left untouched). */
+int xy_step_n(xy_lattice* lat, int64_t n, int record_every, double* rec, int64_t t0_discard);
+
+/* Running FP64 moments per configuration (synchronous):
+ * moments[c][0..5] = sums over replicas and recorded steps >= t0 of
+ * (1, M^2, M^4, E, E^2, |M|); the paper's Binder ratio (Eq. Def-Binder-Cum) is
+ * U = (m[2]/m[0]) / (m[1]/m[0])^2.  step_now[c] (nullable) = current step.
+ * Returns XY_ENAN if any moment is not finite. */
+int xy_observe(xy_lattice* lat, double* moments, int64_t* step_now);
+
+/* Clear the running moments of every configuration. */
+int xy_reset_moments(xy_lattice* lat);
+
+/* Full-step angular velocity omega_k of lattices [b_first, b_first+b_count)
+ * into out (device, b_count*Lx*Ly floats, same layout as the state). */
+int xy_omega_full(xy_lattice* lat, int b_first, int b_count, float* out);
+
+/* Frozen-domain labelling (connected components of the Ising projection
+ * spin = (theta >= 0), 4-neighbour adjacency, periodic) of lattices
+ * [b_first, b_first+b_count), which must all have the same Lx, Ly.
+ * labels (nullable; host or device): int32[b_count][Ly*Lx], label = smallest
+ * site index of the component.  hist (nullable; host or device):
+ * int64[b_count][hist_cap][2] of (size, count) pairs in ascending size,
+ * zero-padded; n_sizes (nullable; host or device): int64[b_count] number of
+ * distinct sizes.  Returns XY_EINVAL (after writing labels) if a lattice has
+ * more than hist_cap distinct sizes. */
+int xy_label_domains(xy_lattice* lat, int b_first, int b_count, int32_t* labels, int64_t* hist,
+                     int64_t hist_cap, int64_t* n_sizes);
+
+/* Pathwise adjoint (synchronous).  Runs n BBK steps from the current state
+ * (which advances by n) with the noise held fixed and returns
+ *   objective = (1 / (B n)) sum_b sum_{k=k0+1}^{k0+n} [w_E E_k + w_M |M_k|]
+ * (B = number of lattices, k0 = current step; every configuration must be at
+ * the same step with n steps left) and grads[c][0..3] = d objective /
+ * d(J_par, J_perp, h, eta) of configuration c.  The full-step state at k0 is
+ * held fixed; the wrap has derivative 1; the kink of the field potential at
+ * +-pi/2 contributes nothing (derivative almost everywhere).  The state is
+ * checkpointed every checkpoint_every steps and each segment recomputed
+ * before its reverse sweep.  objective, grads: host. */
+int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w_E, double w_M,
+                      double* objective, double* grads);
+
+/* Select the stepping path (XY_PATH_BATCHED default, or XY_PATH_PLAIN). */
+int xy_set_path(xy_lattice* lat, int path);
+
+/* Snapshot of the complete state (synchronous): theta, omega, step counters,
+ * moments, parameters and schedules.  host_buf NULL: *size receives the size
+ * needed.  Resuming from a snapshot continues bit-identically. */
+int xy_save(xy_lattice* lat, void* host_buf, size_t* size);
+int xy_load(xy_lattice* lat, const void* host_buf, size_t size);
+
+/* Wait for all work of the object. */
+int xy_synchronize(xy_lattice* lat);
+
+/* Number of this library's kernels launched on the object since creation
+ * (graph replays count their kernel nodes). */
+int64_t xy_kernel_launches(xy_lattice* lat);
+
+#define XY_KCLASS_RESIDENT 0 /* resident stepper launches */
+#define XY_KCLASS_STRIP 1    /* strip stepper launches */
+#define XY_KCLASS_PLAIN 2    /* plain stepper launches */
+#define XY_KCLASS_COUNT 3
+
+/* Kernel timing.  on != 0: the batched path launches its kernels directly
+ * (no graph replay) and brackets every stepper launch with CUDA events on the
+ * object's stream; nothing is skipped.  on == 0 (default): graphs, no events.
+ * Switching clears the accumulated times. */
+int xy_set_kernel_timing(xy_lattice* lat, int on);
+
+/* Synchronous: accumulated device time in milliseconds (ms[XY_KCLASS_COUNT])
+ * and launch counts (launches[XY_KCLASS_COUNT]) of the timed stepper launches
+ * since timing was switched on. */
+int xy_kernel_timing(xy_lattice* lat, double* ms, int64_t* launches);
+
+void xy_lattice_destroy(xy_lattice* lat);
+const char* xy_last_error(void);
+
+/* Diagnostics: the device noise generator.  For lattice site s of
+ * (cfg, replica) at step k and stream tag: words (nullable, device
+ * uint32[n_quads][4]) = raw Philox4x32-10 output of quads 0..n_quads-1;
+ * gauss (nullable, device float[4*n_quads]) = the unit Gaussians n(t) of the
+ * sites.  Asynchronous on cuda_stream. */
+int xy_debug_noise(uint64_t seed, int cfg, int replica, int64_t k, int tag, int64_t n_quads,
+                   uint32_t* words, float* gauss, void* cuda_stream);
+
+/* Diagnostics: raw Philox4x32-10 of n arbitrary counters (device
+ * uint32[n][4]) with key (k0, k1) into out (device uint32[n][4]). */
+int xy_debug_philox(const uint32_t* counters, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
+                    void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XY_LATTICE_H */

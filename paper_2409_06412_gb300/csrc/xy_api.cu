@@ -1,0 +1,1162 @@
+// xy_api.cu -- the C ABI declared in include/xy_lattice.h: lattice objects,
+// parameter and schedule tables, the stepping paths (plain per-configuration
+// launches, or batched task tables replayed as CUDA graphs), observables,
+// domain labelling, the pathwise adjoint and snapshots.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "xy_internal.h"
+
+using namespace xy;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(XY_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+struct CfgHost {
+    xy_config_desc desc{};
+    xy_params prm{};
+    bool has_prm = false;
+    bool has_sched = false;
+    int n_knots = 0;
+    int64_t knot_step[XY_MAX_KNOTS] = {};
+    double knot_T[XY_MAX_KNOTS] = {};
+    int64_t n_total = 0;
+    int64_t step = 0;
+    bool primed = false;
+    int kind = 2;   // 0 resident, 1 strip, 2 plain (inside the batched path)
+    int H = 0;      // strip rows per row group
+};
+
+struct ResGroup {
+    int Lx, Ly, threads;
+    std::vector<ResidentTask> tasks;
+    ResidentTask* d_tasks = nullptr;
+};
+
+struct StripGroup {
+    int H;
+    std::vector<StripTask> tasks;
+    StripTask* d_tasks = nullptr;
+};
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int choose_strip_H(int Lx, int Ly)
+{
+    const bool full = Lx >= 128 ? (Lx % 128 == 0) : (Lx >= 4 && 32 % (Lx / 4) == 0);
+    if (!full) return 0;
+    const int groups = Lx >= 128 ? 1 : 32 / (Lx / 4);
+    for (int H : {64, 32, 16, 8, 4, 2, 1})
+        if (Ly % (H * groups) == 0) return H;
+    return 0;
+}
+
+}  // namespace
+
+struct xy_lattice {
+    int n_cfg = 0;
+    int64_t B = 0;
+    int64_t total_sites = 0;
+    std::vector<CfgHost> cfg;
+    std::vector<DevCfg> h_dev;
+    DevCfg* d_cfg = nullptr;
+    float *thA = nullptr, *omA = nullptr, *thB = nullptr, *omB = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    CallArgs* d_call = nullptr;
+    static constexpr int kRing = 64;
+    CallArgs* h_call = nullptr;  // pinned staging ring of kRing slots
+    cudaEvent_t call_ev[kRing] = {};
+    int call_next = 0;
+    Partials pa{};
+    double* d_moments = nullptr;
+    double2* rec_buf = nullptr;
+    size_t rec_cap = 0;
+    int* d_err = nullptr;
+    int path = XY_PATH_BATCHED;
+    std::vector<ResGroup> res_groups;
+    std::vector<StripGroup> strip_groups;
+    std::vector<int> plain_cfgs;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    // kernel timing (direct launches bracketed by events)
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    std::vector<int> ev_class;
+    size_t ev_used = 0;
+    int64_t graph_kernels = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+Buffers state_buffers(const xy_lattice* L) { return Buffers{L->thA, L->omA, L->thB, L->omB}; }
+
+int upload_cfg(xy_lattice* L)
+{
+    CK(cudaMemcpyAsync(L->d_cfg, L->h_dev.data(), sizeof(DevCfg) * L->n_cfg, cudaMemcpyHostToDevice, L->stream));
+    return XY_OK;
+}
+
+int upload_call(xy_lattice* L, const CallArgs& ca)
+{
+    // a slot is reused only after the copy that read it has executed
+    const int slot = L->call_next;
+    L->call_next = (L->call_next + 1) % xy_lattice::kRing;
+    CK(cudaEventSynchronize(L->call_ev[slot]));
+    L->h_call[slot] = ca;
+    CK(cudaMemcpyAsync(L->d_call, &L->h_call[slot], sizeof(CallArgs), cudaMemcpyHostToDevice, L->stream));
+    CK(cudaEventRecord(L->call_ev[slot], L->stream));
+    return XY_OK;
+}
+
+void fill_params(DevCfg& d, const xy_params& p)
+{
+    d.Jx = (float)p.J_par;
+    d.Jy = (float)p.J_perp;
+    d.h = (float)p.h;
+    d.p = (float)p.p;
+    d.q = (float)p.q;
+    d.dt = (float)p.dt;
+    d.hdt = (float)(0.5 * p.dt);
+    d.oma = (float)(1.0 - 0.5 * p.eta * p.dt);
+    d.inv1pa = (float)(1.0 / (1.0 + 0.5 * p.eta * p.dt));
+    d.nqJx = (float)(-p.q * p.J_par);
+    d.nqJy = (float)(-p.q * p.J_perp);
+    d.hp = (float)(p.h * p.p);
+    d.eta_d = p.eta;
+    d.dt_d = p.dt;
+    d.stag = p.staggered_M ? 1 : 0;
+}
+
+int check_ready(xy_lattice* L)
+{
+    for (int c = 0; c < L->n_cfg; ++c) {
+        if (!L->cfg[c].has_prm) return fail(XY_EINVAL, "configuration %d has no parameters (xy_set_params)", c);
+        if (!L->cfg[c].has_sched) return fail(XY_EINVAL, "configuration %d has no schedule (xy_set_schedule)", c);
+    }
+    return XY_OK;
+}
+
+// Point every configuration's call window at its current step (no stepping).
+void set_window_idle(xy_lattice* L)
+{
+    for (int c = 0; c < L->n_cfg; ++c) {
+        L->h_dev[c].k_start = L->cfg[c].step;
+        L->h_dev[c].n_call = 0;
+        L->h_dev[c].rec_first = L->cfg[c].step;
+    }
+}
+
+int prime_all(xy_lattice* L)
+{
+    bool any = false;
+    for (int c = 0; c < L->n_cfg; ++c) any |= !L->cfg[c].primed;
+    if (!any) return XY_OK;
+    set_window_idle(L);
+    int rc = upload_cfg(L);
+    if (rc) return rc;
+    for (int c = 0; c < L->n_cfg; ++c) {
+        if (L->cfg[c].primed) continue;
+        CK(launch_prime(L->d_cfg, L->h_dev[c], L->thA, L->omA, L->stream));
+        ++L->launches;
+        L->cfg[c].primed = true;
+    }
+    return XY_OK;
+}
+
+int ensure_rec(xy_lattice* L, size_t n)
+{
+    if (n <= L->rec_cap) return XY_OK;
+    if (L->rec_buf) cudaFree(L->rec_buf);
+    L->rec_buf = nullptr;
+    L->rec_cap = 0;
+    if (cudaMalloc(&L->rec_buf, n * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XY_ENOMEM, "cannot allocate %zu records", n);
+    }
+    L->rec_cap = n;
+    return XY_OK;
+}
+
+// Event pair of the next timed launch (pool grows on demand).
+int timed_begin(xy_lattice* L, cudaStream_t st, int cls, cudaEvent_t* end)
+{
+    *end = nullptr;
+    if (!L->timing || st != L->stream) return XY_OK;
+    if (L->ev_used == L->ev_pool.size()) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        L->ev_pool.push_back({a, b});
+        L->ev_class.push_back(0);
+    }
+    L->ev_class[L->ev_used] = cls;
+    CK(cudaEventRecord(L->ev_pool[L->ev_used].first, st));
+    *end = L->ev_pool[L->ev_used].second;
+    ++L->ev_used;
+    return XY_OK;
+}
+
+int timed_end(cudaEvent_t end, cudaStream_t st)
+{
+    if (end) CK(cudaEventRecord(end, st));
+    return XY_OK;
+}
+
+// Launch the batched kernels for local steps [jl0, jl0 + cnt) of the current window.
+int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, bool advance)
+{
+    const Buffers buf = state_buffers(L);
+    cudaEvent_t end;
+    int rc;
+    for (auto& g : L->res_groups) {
+        if ((rc = timed_begin(L, st, XY_KCLASS_RESIDENT, &end))) return rc;
+        CK(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, jl0, cnt, buf,
+                                L->d_call, st));
+        if ((rc = timed_end(end, st))) return rc;
+        ++L->launches;
+    }
+    for (int i = 0; i < cnt; ++i) {
+        for (auto& g : L->strip_groups) {
+            if ((rc = timed_begin(L, st, XY_KCLASS_STRIP, &end))) return rc;
+            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, jl0 + i, buf, L->d_call, L->pa,
+                                 st));
+            if ((rc = timed_end(end, st))) return rc;
+            ++L->launches;
+        }
+        for (int c : L->plain_cfgs) {
+            if ((rc = timed_begin(L, st, XY_KCLASS_PLAIN, &end))) return rc;
+            CK(launch_plain_step(L->d_cfg, L->h_dev[c], jl0 + i, buf, L->d_call, L->pa, 1, st));
+            if ((rc = timed_end(end, st))) return rc;
+            ++L->launches;
+        }
+    }
+    if (advance) {
+        CK(launch_advance(L->d_call, cnt, st));
+        ++L->launches;
+    }
+    return XY_OK;
+}
+
+int build_graph(xy_lattice* L, int chunk)
+{
+    if (L->graph) {
+        cudaGraphExecDestroy(L->graph);
+        L->graph = nullptr;
+    }
+    const int64_t before = L->launches;
+    CK(cudaStreamBeginCapture(L->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_batched_steps(L, L->cap_stream, 0, chunk, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(L->cap_stream, &g);
+    L->graph_kernels = L->launches - before;
+    L->launches = before;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(XY_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&L->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    L->graph_chunk = chunk;
+    return XY_OK;
+}
+
+// Advance every configuration by its n_call of the current window (already
+// uploaded), recording into rec_dev with stride rec_stride.
+int run_window(xy_lattice* L, int64_t n_max)
+{
+    if (n_max <= 0) return XY_OK;
+    if (L->path == XY_PATH_PLAIN) {
+        for (int64_t j = 0; j < n_max; ++j)
+            for (int c = 0; c < L->n_cfg; ++c) {
+                if (j >= L->h_dev[c].n_call) continue;
+                cudaEvent_t end;
+                int rc = timed_begin(L, L->stream, XY_KCLASS_PLAIN, &end);
+                if (rc) return rc;
+                CK(launch_plain_step(L->d_cfg, L->h_dev[c], j, state_buffers(L), L->d_call, L->pa, 1, L->stream));
+                if ((rc = timed_end(end, L->stream))) return rc;
+                ++L->launches;
+            }
+        return XY_OK;
+    }
+    const int chunk = 32;
+    const int64_t n_full = L->timing ? 0 : n_max / chunk;
+    const int rem = (int)(L->timing ? n_max : n_max % chunk);
+    if (n_full > 0) {
+        if (!L->graph || L->graph_chunk != chunk) {
+            int rc = build_graph(L, chunk);
+            if (rc) return rc;
+        }
+        for (int64_t i = 0; i < n_full; ++i) {
+            CK(cudaGraphLaunch(L->graph, L->stream));
+            L->launches += L->graph_kernels;
+        }
+    }
+    for (int64_t done = 0; done < rem;) {
+        // direct launches: at most one chunk per resident launch
+        const int cnt = (int)std::min<int64_t>(chunk, rem - done);
+        const bool more = done + cnt < rem;
+        int rc = launch_batched_steps(L, L->stream, 0, cnt, more);
+        if (rc) return rc;
+        done += cnt;
+    }
+    return XY_OK;
+}
+
+// After a window: configurations that took an odd number of steps hold their
+// state in buffer B; copy it back so that the caller's buffers are current.
+int fixup_parity(xy_lattice* L)
+{
+    for (int c = 0; c < L->n_cfg; ++c) {
+        if ((L->h_dev[c].n_call & 1) == 0) continue;
+        const DevCfg& d = L->h_dev[c];
+        const size_t bytes = sizeof(float) * (size_t)d.N * d.n_rep;
+        CK(cudaMemcpyAsync(L->thA + d.offset, L->thB + d.offset, bytes, cudaMemcpyDeviceToDevice, L->stream));
+        CK(cudaMemcpyAsync(L->omA + d.offset, L->omB + d.offset, bytes, cudaMemcpyDeviceToDevice, L->stream));
+    }
+    return XY_OK;
+}
+
+// Core of xy_step_n: n steps, records with stride rec_stride into rec_dev
+// (nullable when record_every == 0), optional moments.
+int advance_core(xy_lattice* L, int64_t n, int record_every, double2* rec_dev, int64_t rec_stride,
+                 bool do_moments, int64_t t0)
+{
+    int64_t n_max = 0;
+    for (int c = 0; c < L->n_cfg; ++c) {
+        CfgHost& h = L->cfg[c];
+        DevCfg& d = L->h_dev[c];
+        const int64_t left = h.n_total - h.step;
+        d.k_start = h.step;
+        d.n_call = std::max<int64_t>(0, std::min<int64_t>(n, left));
+        d.rec_first = record_every > 0 ? ((h.step + record_every - 1) / record_every) * record_every : h.step;
+        n_max = std::max(n_max, d.n_call);
+    }
+    int rc = upload_cfg(L);
+    if (rc) return rc;
+    CallArgs ca{};
+    ca.j_base = 0;
+    ca.rec_stride = rec_stride;
+    ca.rec_dev = rec_dev;
+    ca.k_shift = 0;
+    ca.record_every = record_every;
+    ca.fixed_parity = 0;
+    if ((rc = upload_call(L, ca))) return rc;
+    if ((rc = run_window(L, n_max))) return rc;
+    if ((rc = fixup_parity(L))) return rc;
+    if (do_moments && record_every > 0) {
+        CK(launch_moments(L->d_cfg, L->n_cfg, L->d_call, t0, L->d_moments, L->stream));
+        ++L->launches;
+    }
+    for (int c = 0; c < L->n_cfg; ++c) L->cfg[c].step += L->h_dev[c].n_call;
+    return XY_OK;
+}
+
+int classify(xy_lattice* L)
+{
+    // default kernel per configuration; see the design notes for the rules
+    std::vector<std::pair<int, int>> res_shapes;
+    int max_units = 1;
+    for (int c = 0; c < L->n_cfg; ++c) {
+        CfgHost& h = L->cfg[c];
+        const int Lx = h.desc.Lx, Ly = h.desc.Ly;
+        const int64_t nq = (int64_t)Lx * Ly / 4;
+        max_units = std::max<int>(max_units, (int)((nq + 255) / 256));
+        const int rt = resident_threads(Lx, Ly);
+        const int H = choose_strip_H(Lx, Ly);
+        if (rt > 0 && resident_smem_bytes(Lx, Ly, rt) <= 200 * 1024) {
+            h.kind = 0;
+        } else if (H > 0) {
+            h.kind = 1;
+            h.H = H;
+            max_units = std::max(max_units, strip_units_per_lattice(Lx, Ly, H));
+        } else {
+            h.kind = 2;
+        }
+    }
+    L->pa.max_units = max_units;
+    // task tables
+    for (int c = 0; c < L->n_cfg; ++c) {
+        CfgHost& h = L->cfg[c];
+        const int Lx = h.desc.Lx, Ly = h.desc.Ly;
+        if (h.kind == 0) {
+            const int rt = resident_threads(Lx, Ly);
+            ResGroup* g = nullptr;
+            for (auto& gg : L->res_groups)
+                if (gg.Lx == Lx && gg.Ly == Ly && gg.threads == rt) g = &gg;
+            if (!g) {
+                L->res_groups.push_back(ResGroup{Lx, Ly, rt, {}, nullptr});
+                g = &L->res_groups.back();
+            }
+            for (int r = 0; r < h.desc.n_replicas; ++r) g->tasks.push_back(ResidentTask{c, r});
+        } else if (h.kind == 1) {
+            StripGroup* g = nullptr;
+            for (auto& gg : L->strip_groups)
+                if (gg.H == h.H) g = &gg;
+            if (!g) {
+                L->strip_groups.push_back(StripGroup{h.H, {}, nullptr});
+                g = &L->strip_groups.back();
+            }
+            const int nu = strip_units_per_lattice(Lx, Ly, h.H);
+            const int groups = Lx >= 128 ? 1 : 32 / (Lx / 4);
+            const int rows_per_warp = h.H * groups;
+            const int strips = Lx >= 128 ? Lx / 128 : 1;
+            for (int r = 0; r < h.desc.n_replicas; ++r) {
+                int unit = 0;
+                for (int y0 = 0; y0 < Ly; y0 += rows_per_warp)
+                    for (int s = 0; s < strips; ++s)
+                        g->tasks.push_back(StripTask{c, r, unit++, nu, s * 128, y0});
+            }
+        } else {
+            L->plain_cfgs.push_back(c);
+        }
+    }
+    for (auto& g : L->res_groups) {
+        CK(cudaMalloc(&g.d_tasks, sizeof(ResidentTask) * g.tasks.size()));
+        CK(cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(ResidentTask) * g.tasks.size(), cudaMemcpyHostToDevice));
+        CK(prepare_resident(g.Lx, g.Ly, g.threads));
+    }
+    for (auto& g : L->strip_groups) {
+        CK(cudaMalloc(&g.d_tasks, sizeof(StripTask) * g.tasks.size()));
+        CK(cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(StripTask) * g.tasks.size(), cudaMemcpyHostToDevice));
+    }
+    return XY_OK;
+}
+
+void free_lattice(xy_lattice* L)
+{
+    if (!L) return;
+    if (L->graph) cudaGraphExecDestroy(L->graph);
+    for (auto& pr : L->ev_pool) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto& g : L->res_groups) cudaFree(g.d_tasks);
+    for (auto& g : L->strip_groups) cudaFree(g.d_tasks);
+    cudaFree(L->thB);
+    cudaFree(L->omB);
+    cudaFree(L->d_cfg);
+    cudaFree(L->d_call);
+    if (L->h_call) cudaFreeHost(L->h_call);
+    for (int i = 0; i < xy_lattice::kRing; ++i)
+        if (L->call_ev[i]) cudaEventDestroy(L->call_ev[i]);
+    cudaFree(L->pa.part);
+    cudaFree(L->pa.count);
+    cudaFree(L->d_moments);
+    cudaFree(L->rec_buf);
+    cudaFree(L->d_err);
+    if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
+    delete L;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* xy_last_error(void) { return g_err.c_str(); }
+
+int xy_lattice_create(const xy_config_desc* cfg, int n_cfg, float* theta, float* omega, void* cuda_stream,
+                      xy_lattice** out)
+{
+    if (!out) return fail(XY_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg || n_cfg <= 0 || n_cfg > 65536) return fail(XY_EINVAL, "need 1..65536 configurations");
+    if (!theta || !omega) return fail(XY_EINVAL, "theta/omega must be device buffers");
+    if (((uintptr_t)theta & 15) || ((uintptr_t)omega & 15)) return fail(XY_EINVAL, "theta/omega must be 16-byte aligned");
+    if (!is_device_ptr(theta) || !is_device_ptr(omega)) return fail(XY_EINVAL, "theta/omega are not device memory");
+    int64_t total = 0, B = 0;
+    for (int c = 0; c < n_cfg; ++c) {
+        const xy_config_desc& d = cfg[c];
+        if (d.Lx < 4 || d.Lx % 4 != 0) return fail(XY_EINVAL, "configuration %d: Lx must be a positive multiple of 4", c);
+        if (d.Ly < 1) return fail(XY_EINVAL, "configuration %d: Ly must be >= 1", c);
+        if (d.n_replicas < 1 || d.n_replicas > 65535) return fail(XY_EINVAL, "configuration %d: 1..65535 replicas", c);
+        if (d.init_mode < 0 || d.init_mode > 2) return fail(XY_EINVAL, "configuration %d: bad init_mode", c);
+        if ((int64_t)d.Lx * d.Ly > (int64_t)1 << 30) return fail(XY_EINVAL, "configuration %d: lattice too large", c);
+        total += (int64_t)d.Lx * d.Ly * d.n_replicas;
+        B += d.n_replicas;
+    }
+    if (B > ((int64_t)1 << 31) - 1) return fail(XY_EINVAL, "too many lattices");
+    xy_lattice* L = new xy_lattice();
+    L->n_cfg = n_cfg;
+    L->B = B;
+    L->total_sites = total;
+    L->thA = theta;
+    L->omA = omega;
+    L->stream = (cudaStream_t)cuda_stream;
+    L->cfg.resize(n_cfg);
+    L->h_dev.resize(n_cfg);
+    int64_t off = 0, b = 0;
+    for (int c = 0; c < n_cfg; ++c) {
+        CfgHost& h = L->cfg[c];
+        h.desc = cfg[c];
+        DevCfg& d = L->h_dev[c];
+        std::memset(&d, 0, sizeof d);
+        d.Lx = h.desc.Lx;
+        d.Ly = h.desc.Ly;
+        d.n_rep = h.desc.n_replicas;
+        d.cfg_index = c;
+        d.offset = off;
+        d.N = (int64_t)h.desc.Lx * h.desc.Ly;
+        d.key0 = (uint32_t)(h.desc.seed & 0xFFFFFFFFu);
+        d.key1 = (uint32_t)(h.desc.seed >> 32);
+        d.b_first = (int32_t)b;
+        off += d.N * d.n_rep;
+        b += d.n_rep;
+        // the full-step omega_0 (0, or the caller's) becomes v_0 at the first step
+        h.primed = false;
+    }
+    auto bail = [&](int code) {
+        free_lattice(L);
+        return code;
+    };
+    if (cudaMalloc(&L->thB, sizeof(float) * total) != cudaSuccess ||
+        cudaMalloc(&L->omB, sizeof(float) * total) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(XY_ENOMEM, "cannot allocate the second state buffer (%lld sites)", (long long)total));
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&L->d_cfg, sizeof(DevCfg) * n_cfg)) != cudaSuccess ||
+        (e = cudaMalloc(&L->d_call, sizeof(CallArgs))) != cudaSuccess ||
+        (e = cudaMallocHost(&L->h_call, sizeof(CallArgs) * xy_lattice::kRing)) != cudaSuccess ||
+        (e = cudaMalloc(&L->d_moments, sizeof(double) * 6 * n_cfg)) != cudaSuccess ||
+        (e = cudaMalloc(&L->d_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&L->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(XY_ENOMEM, "allocation failed: %s", cudaGetErrorString(e)));
+    }
+    for (int i = 0; i < xy_lattice::kRing; ++i)
+        if ((e = cudaEventCreateWithFlags(&L->call_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(fail(XY_ECUDA, "event: %s", cudaGetErrorString(e)));
+    int rc = classify(L);
+    if (rc) return bail(rc);
+    if ((e = cudaMalloc(&L->pa.part, sizeof(double2) * B * L->pa.max_units)) != cudaSuccess ||
+        (e = cudaMalloc(&L->pa.count, sizeof(unsigned) * B)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(XY_ENOMEM, "allocation failed: %s", cudaGetErrorString(e)));
+    }
+    if ((e = cudaMemsetAsync(L->pa.count, 0, sizeof(unsigned) * B, L->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(L->d_moments, 0, sizeof(double) * 6 * n_cfg, L->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(L->d_err, 0, sizeof(int), L->stream)) != cudaSuccess)
+        return bail(fail(XY_ECUDA, "memset: %s", cudaGetErrorString(e)));
+    if ((rc = upload_cfg(L))) return bail(rc);
+    for (int c = 0; c < n_cfg; ++c) {
+        if ((e = launch_init(L->d_cfg, L->h_dev[c], cfg[c].init_mode, theta, omega, L->stream)) != cudaSuccess)
+            return bail(fail(XY_ECUDA, "init: %s", cudaGetErrorString(e)));
+        if (cfg[c].init_mode != XY_INIT_USER) ++L->launches;
+    }
+    *out = L;
+    return XY_OK;
+}
+
+int xy_set_params(xy_lattice* L, int c, const xy_params* p)
+{
+    if (!L || !p) return fail(XY_EINVAL, "NULL argument");
+    if (c < 0 || c >= L->n_cfg) return fail(XY_EINVAL, "configuration %d out of range", c);
+    if (!(p->dt > 0.0) || !(p->eta >= 0.0) || !std::isfinite(p->J_par) || !std::isfinite(p->J_perp) ||
+        !std::isfinite(p->h) || !std::isfinite(p->p) || !std::isfinite(p->q) || !std::isfinite(p->eta) ||
+        !std::isfinite(p->dt))
+        return fail(XY_EINVAL, "parameters must be finite with dt > 0 and eta >= 0");
+    L->cfg[c].prm = *p;
+    L->cfg[c].has_prm = true;
+    fill_params(L->h_dev[c], *p);
+    return XY_OK;
+}
+
+int xy_set_schedule(xy_lattice* L, int c, const int64_t* ks, const double* Ts, int n_knots, int64_t n_total)
+{
+    if (!L || !ks || !Ts) return fail(XY_EINVAL, "NULL argument");
+    if (c < 0 || c >= L->n_cfg) return fail(XY_EINVAL, "configuration %d out of range", c);
+    if (n_knots < 1 || n_knots > XY_MAX_KNOTS) return fail(XY_EINVAL, "1..%d knots", XY_MAX_KNOTS);
+    if (n_total < 0) return fail(XY_EINVAL, "n_steps_total must be >= 0");
+    for (int i = 0; i < n_knots; ++i) {
+        if (!(Ts[i] >= 0.0) || !std::isfinite(Ts[i])) return fail(XY_EINVAL, "temperatures must be finite and >= 0");
+        if (i > 0 && ks[i] <= ks[i - 1]) return fail(XY_EINVAL, "knot steps must increase strictly");
+    }
+    CfgHost& h = L->cfg[c];
+    DevCfg& d = L->h_dev[c];
+    h.n_knots = n_knots;
+    d.n_knots = n_knots;
+    for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+        h.knot_step[i] = d.knot_step[i] = i < n_knots ? ks[i] : 0;
+        h.knot_T[i] = d.knot_T[i] = i < n_knots ? Ts[i] : 0.0;
+    }
+    h.n_total = n_total;
+    d.n_total = n_total;
+    h.has_sched = true;
+    return XY_OK;
+}
+
+int xy_set_path(xy_lattice* L, int path)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (path != XY_PATH_BATCHED && path != XY_PATH_PLAIN) return fail(XY_EINVAL, "unknown path %d", path);
+    L->path = path;
+    return XY_OK;
+}
+
+int xy_step_n(xy_lattice* L, int64_t n, int record_every, double* rec, int64_t t0)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (n < 0 || record_every < 0) return fail(XY_EINVAL, "n and record_every must be >= 0");
+    int rc = check_ready(L);
+    if (rc) return rc;
+    if ((rc = prime_all(L))) return rc;
+    if (n == 0) return XY_OK;
+    if (record_every == 0) return advance_core(L, n, 0, nullptr, 0, false, t0);
+    const int64_t R = n / record_every + 1;
+    const bool dev_rec = rec && is_device_ptr(rec) && (((uintptr_t)rec & 15) == 0);
+    double2* rd = nullptr;
+    if (dev_rec) {
+        rd = reinterpret_cast<double2*>(rec);
+    } else {
+        if ((rc = ensure_rec(L, (size_t)(L->B * R)))) return rc;
+        rd = L->rec_buf;
+    }
+    if ((rc = advance_core(L, n, record_every, rd, R, true, t0))) return rc;
+    if (rec && !dev_rec) {
+        CK(cudaMemcpyAsync(rec, rd, sizeof(double2) * L->B * R, cudaMemcpyDeviceToHost, L->stream));
+        CK(cudaStreamSynchronize(L->stream));
+    }
+    return XY_OK;
+}
+
+int xy_observe(xy_lattice* L, double* moments, int64_t* step_now)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    CK(cudaStreamSynchronize(L->stream));
+    int err = 0;
+    CK(cudaMemcpy(&err, L->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (step_now)
+        for (int c = 0; c < L->n_cfg; ++c) step_now[c] = L->cfg[c].step;
+    if (moments) {
+        CK(cudaMemcpy(moments, L->d_moments, sizeof(double) * 6 * L->n_cfg, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < 6 * L->n_cfg; ++i)
+            if (!std::isfinite(moments[i])) return fail(XY_ENAN, "moment %d of configuration %d is not finite", i % 6, i / 6);
+    }
+    if (err) return fail(err, "a device-side check failed (code %d)", err);
+    return XY_OK;
+}
+
+int xy_reset_moments(xy_lattice* L)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    CK(cudaMemsetAsync(L->d_moments, 0, sizeof(double) * 6 * L->n_cfg, L->stream));
+    return XY_OK;
+}
+
+int xy_omega_full(xy_lattice* L, int b_first, int b_count, float* out)
+{
+    if (!L || !out) return fail(XY_EINVAL, "NULL argument");
+    if (b_first < 0 || b_count < 0 || b_first + (int64_t)b_count > L->B) return fail(XY_EINVAL, "lattice range out of bounds");
+    if (!is_device_ptr(out) || ((uintptr_t)out & 15)) return fail(XY_EINVAL, "out must be 16-byte aligned device memory");
+    int rc = check_ready(L);
+    if (rc) return rc;
+    if ((rc = prime_all(L))) return rc;
+    set_window_idle(L);
+    if ((rc = upload_cfg(L))) return rc;
+    int64_t out_off = 0;
+    for (int c = 0; c < L->n_cfg; ++c) {
+        const DevCfg& d = L->h_dev[c];
+        const int lo = std::max(b_first, d.b_first), hi = std::min(b_first + b_count, d.b_first + d.n_rep);
+        if (lo >= hi) continue;
+        CK(launch_omega_full(L->d_cfg, d, lo - d.b_first, hi - lo, L->thA, L->omA, out + out_off, L->stream));
+        ++L->launches;
+        out_off += (int64_t)(hi - lo) * d.N;
+    }
+    return XY_OK;
+}
+
+int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, int64_t* hist, int64_t hist_cap,
+                     int64_t* n_sizes)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (b_first < 0 || b_count <= 0 || b_first + (int64_t)b_count > L->B) return fail(XY_EINVAL, "lattice range out of bounds");
+    if (hist && hist_cap <= 0) return fail(XY_EINVAL, "hist_cap must be > 0");
+    int Lx = -1, Ly = -1;
+    int64_t site0 = -1;
+    for (int c = 0; c < L->n_cfg; ++c) {
+        const DevCfg& d = L->h_dev[c];
+        const int lo = std::max(b_first, d.b_first), hi = std::min(b_first + b_count, d.b_first + d.n_rep);
+        if (lo >= hi) continue;
+        if (Lx < 0) {
+            Lx = d.Lx;
+            Ly = d.Ly;
+            site0 = d.offset + (int64_t)(lo - d.b_first) * d.N;
+        } else if (Lx != d.Lx || Ly != d.Ly) {
+            return fail(XY_EINVAL, "lattices of one labelling call must share Lx and Ly");
+        }
+    }
+    const int64_t N = (int64_t)Lx * Ly;
+    const bool dev_lab = labels && is_device_ptr(labels);
+    const bool dev_hist = hist && is_device_ptr(hist);
+    const bool dev_ns = n_sizes && is_device_ptr(n_sizes);
+    // lattices per chunk: 12 bytes per site of scratch, capped at 512 MB
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(b_count, ((int64_t)512 << 20) / (12 * N + 8)));
+    int32_t *lab = nullptr, *sz = nullptr, *cnt = nullptr;
+    int64_t *hs = nullptr, *ns = nullptr;
+    auto cleanup = [&]() {
+        if (!dev_lab) cudaFree(lab);
+        cudaFree(sz);
+        cudaFree(cnt);
+        if (!dev_hist) cudaFree(hs);
+        cudaFree(ns);
+    };
+    cudaError_t e = cudaSuccess;
+    if (!dev_lab) e = cudaMalloc(&lab, sizeof(int32_t) * N * per);
+    if (e == cudaSuccess) e = cudaMalloc(&sz, sizeof(int32_t) * N * per);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(int32_t) * (N + 1) * per);
+    if (e == cudaSuccess && hist && !dev_hist) e = cudaMalloc(&hs, sizeof(int64_t) * 2 * hist_cap * per);
+    if (e == cudaSuccess) e = cudaMalloc(&ns, sizeof(int64_t) * per);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(XY_ENOMEM, "labelling scratch: %s", cudaGetErrorString(e));
+    }
+    int rc = XY_OK;
+    CK(cudaMemsetAsync(L->d_err, 0, sizeof(int), L->stream));
+    for (int64_t b0 = 0; b0 < b_count && rc == XY_OK; b0 += per) {
+        const int nl = (int)std::min<int64_t>(per, b_count - b0);
+        int32_t* lab_out = dev_lab ? labels + b0 * N : lab;
+        int64_t* h_out = hist ? (dev_hist ? hist + b0 * hist_cap * 2 : hs) : nullptr;
+        if (h_out) e = cudaMemsetAsync(h_out, 0, sizeof(int64_t) * 2 * hist_cap * nl, L->stream);
+        if (e == cudaSuccess)
+            e = launch_ccl(L->thA + site0 + b0 * N, Lx, Ly, nl, lab_out, sz, cnt, h_out, hist ? hist_cap : 0, ns,
+                           L->d_err, L->stream);
+        if (e != cudaSuccess) {
+            rc = fail(XY_ECUDA, "labelling: %s", cudaGetErrorString(e));
+            break;
+        }
+        L->launches += 5;
+        if (labels && !dev_lab)
+            e = cudaMemcpyAsync(labels + b0 * N, lab, sizeof(int32_t) * N * nl, cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess && hist && !dev_hist)
+            e = cudaMemcpyAsync(hist + b0 * hist_cap * 2, hs, sizeof(int64_t) * 2 * hist_cap * nl,
+                                cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess && n_sizes)
+            e = cudaMemcpyAsync(n_sizes + b0, ns, sizeof(int64_t) * nl,
+                                dev_ns ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+        if (e != cudaSuccess) rc = fail(XY_ECUDA, "labelling: %s", cudaGetErrorString(e));
+    }
+    int err = 0;
+    if (rc == XY_OK) {
+        if (cudaMemcpy(&err, L->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) err = XY_ECUDA;
+        cudaMemset(L->d_err, 0, sizeof(int));
+    }
+    cleanup();
+    if (rc) return rc;
+    if (err == XY_EINVAL) return fail(XY_EINVAL, "a lattice has more distinct domain sizes than hist_cap");
+    if (err) return fail(err, "labelling: a bounded union loop ran out of iterations");
+    return XY_OK;
+}
+
+int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, double* objective, double* grads)
+{
+    if (!L || !objective || !grads) return fail(XY_EINVAL, "NULL argument");
+    if (n <= 0 || K <= 0) return fail(XY_EINVAL, "n and checkpoint_every must be > 0");
+    int rc = check_ready(L);
+    if (rc) return rc;
+    const int64_t k0 = L->cfg[0].step;
+    for (int c = 0; c < L->n_cfg; ++c) {
+        if (L->cfg[c].step != k0) return fail(XY_EINVAL, "all configurations must be at the same step");
+        if (L->cfg[c].n_total - k0 < n) return fail(XY_EINVAL, "configuration %d has fewer than n steps left", c);
+    }
+    if ((rc = prime_all(L))) return rc;
+    const int64_t T = L->total_sites;
+    const int64_t nseg = (n + K - 1) / K;
+    const int64_t R = n + 1;
+    int n_blocks = 0;
+    std::vector<int> block_base(L->n_cfg);
+    for (int c = 0; c < L->n_cfg; ++c) {
+        block_base[c] = n_blocks;
+        n_blocks += adjoint_blocks(L->h_dev[c]);
+    }
+    float *ck = nullptr, *seg = nullptr, *tb = nullptr, *vb = nullptr, *Fb = nullptr;
+    double2* arec = nullptr;
+    double* gacc = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(ck);
+        cudaFree(seg);
+        cudaFree(tb);
+        cudaFree(vb);
+        cudaFree(Fb);
+        cudaFree(arec);
+        cudaFree(gacc);
+    };
+    cudaError_t e = cudaMalloc(&ck, sizeof(float) * 2 * T * nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * 2 * T * (K + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&tb, sizeof(float) * T);
+    if (e == cudaSuccess) e = cudaMalloc(&vb, sizeof(float) * T);
+    if (e == cudaSuccess) e = cudaMalloc(&Fb, sizeof(float) * T);
+    if (e == cudaSuccess) e = cudaMalloc(&arec, sizeof(double2) * L->B * R);
+    if (e == cudaSuccess) e = cudaMalloc(&gacc, sizeof(double) * 6 * n_blocks);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(XY_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
+    }
+#define CKA(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cleanup();                                                                             \
+            return fail(XY_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));                        \
+        }                                                                                          \
+    } while (0)
+#define RCA(expr)                                                                                  \
+    do {                                                                                           \
+        int r_ = (expr);                                                                           \
+        if (r_) {                                                                                  \
+            cleanup();                                                                             \
+            return r_;                                                                             \
+        }                                                                                          \
+    } while (0)
+    const size_t state_bytes = sizeof(float) * T;
+    // ---- forward with checkpoints; observables at every step
+    for (int64_t s = 0; s < nseg; ++s) {
+        CKA(cudaMemcpyAsync(ck + 2 * T * s, L->thA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
+        CKA(cudaMemcpyAsync(ck + 2 * T * s + T, L->omA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
+        const int64_t ns = std::min<int64_t>(K, n - s * K);
+        RCA(advance_core(L, ns, 1, arec + s * K, R, false, 0));
+    }
+    // observation at k0 + n (first half of the next step, state untouched)
+    for (int c = 0; c < L->n_cfg; ++c) {
+        L->h_dev[c].k_start = k0 + n;
+        L->h_dev[c].n_call = 1;
+        L->h_dev[c].rec_first = k0 + n;
+    }
+    RCA(upload_cfg(L));
+    {
+        CallArgs ca{};
+        ca.rec_stride = R;
+        ca.rec_dev = arec + n;
+        ca.record_every = 1;
+        RCA(upload_call(L, ca));
+    }
+    for (int c = 0; c < L->n_cfg; ++c) {
+        CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, state_buffers(L), L->d_call, L->pa, 0, L->stream));
+        ++L->launches;
+    }
+    std::vector<double2> hrec((size_t)L->B * R);
+    CKA(cudaMemcpyAsync(hrec.data(), arec, sizeof(double2) * L->B * R, cudaMemcpyDeviceToHost, L->stream));
+    CKA(cudaStreamSynchronize(L->stream));
+    double obj = 0.0;
+    for (int64_t b = 0; b < L->B; ++b)
+        for (int64_t k = 1; k <= n; ++k) {
+            const double2 me = hrec[b * R + k];
+            obj += wE * me.y + wM * std::fabs(me.x);
+        }
+    const double inv_norm = 1.0 / ((double)L->B * (double)n);
+    *objective = obj * inv_norm;
+    // ---- reverse sweep, segment by segment
+    for (int c = 0; c < L->n_cfg; ++c) {
+        L->h_dev[c].k_start = k0;
+        L->h_dev[c].n_call = n + 1;
+        L->h_dev[c].rec_first = k0;
+    }
+    RCA(upload_cfg(L));
+    CKA(cudaMemsetAsync(tb, 0, state_bytes, L->stream));
+    CKA(cudaMemsetAsync(vb, 0, state_bytes, L->stream));
+    CKA(cudaMemsetAsync(gacc, 0, sizeof(double) * 6 * n_blocks, L->stream));
+    const int saved_path = L->path;
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int64_t ks = k0 + s * K;
+        const int64_t Ks = std::min<int64_t>(K, n - s * K);
+        const int64_t n_states = (s == nseg - 1) ? Ks + 1 : Ks;  // the last segment also needs k0 + n
+        CKA(cudaMemcpyAsync(seg, ck + 2 * T * s, 2 * state_bytes, cudaMemcpyDeviceToDevice, L->stream));
+        {
+            CallArgs ca{};
+            ca.k_shift = ks - k0;
+            ca.fixed_parity = 1;
+            RCA(upload_call(L, ca));
+        }
+        for (int64_t i = 0; i + 1 < n_states; ++i) {
+            if (i > 0) {
+                CKA(launch_add_kshift(L->d_call, 1, L->stream));
+                ++L->launches;
+            }
+            Buffers buf{seg + 2 * T * i, seg + 2 * T * i + T, seg + 2 * T * (i + 1), seg + 2 * T * (i + 1) + T};
+            if (L->path == XY_PATH_PLAIN) {
+                for (int c = 0; c < L->n_cfg; ++c) {
+                    CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, buf, L->d_call, L->pa, 1, L->stream));
+                    ++L->launches;
+                }
+            } else {
+                for (auto& g : L->res_groups) {
+                    CKA(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, 0, 1,
+                                             buf, L->d_call, L->stream));
+                    ++L->launches;
+                }
+                for (auto& g : L->strip_groups) {
+                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, 0, buf, L->d_call, L->pa,
+                                          L->stream));
+                    ++L->launches;
+                }
+                for (int c : L->plain_cfgs) {
+                    CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, buf, L->d_call, L->pa, 1, L->stream));
+                    ++L->launches;
+                }
+            }
+        }
+        for (int64_t i = n_states - 1; i >= 0; --i) {
+            AdjArgs a{};
+            a.theta = seg + 2 * T * i;
+            a.omega = seg + 2 * T * i + T;
+            a.tb = tb;
+            a.vb = vb;
+            a.Fb = Fb;
+            a.rec = arec;
+            a.rec_stride = R;
+            a.k = ks + i;
+            a.k0 = k0;
+            a.k_end = k0 + n;
+            a.wE = wE;
+            a.wM = wM;
+            a.inv_norm = inv_norm;
+            a.gacc = gacc;
+            for (int c = 0; c < L->n_cfg; ++c) {
+                CKA(launch_adjoint_phase_a(L->d_cfg, L->h_dev[c], block_base[c], a, L->stream));
+                ++L->launches;
+            }
+            for (int c = 0; c < L->n_cfg; ++c) {
+                CKA(launch_adjoint_phase_b(L->d_cfg, L->h_dev[c], a, L->stream));
+                ++L->launches;
+            }
+        }
+    }
+    L->path = saved_path;
+    std::vector<double> hg((size_t)6 * n_blocks);
+    CKA(cudaMemcpyAsync(hg.data(), gacc, sizeof(double) * 6 * n_blocks, cudaMemcpyDeviceToHost, L->stream));
+    CKA(cudaStreamSynchronize(L->stream));
+    for (int c = 0; c < L->n_cfg; ++c) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        const int nb = adjoint_blocks(L->h_dev[c]);
+        for (int bk = 0; bk < nb; ++bk)
+            for (int q = 0; q < 6; ++q) acc[q] += hg[(size_t)(block_base[c] + bk) * 6 + q];
+        const xy_params& p = L->cfg[c].prm;
+        const double bb = 1.0 / (1.0 + 0.5 * p.eta * p.dt);
+        grads[4 * c + 0] = acc[0] * inv_norm;
+        grads[4 * c + 1] = acc[1] * inv_norm;
+        grads[4 * c + 2] = acc[2] * inv_norm;
+        grads[4 * c + 3] = (0.5 * p.dt * (acc[3] - bb * bb * acc[4]) + acc[5]) * inv_norm;
+    }
+    // restore the idle window
+    set_window_idle(L);
+    RCA(upload_cfg(L));
+    cleanup();
+#undef CKA
+#undef RCA
+    return XY_OK;
+}
+
+// ---- snapshots
+namespace {
+struct SnapHeader {
+    char magic[8];
+    int64_t version, n_cfg, total, B;
+};
+struct SnapCfg {
+    xy_config_desc desc;
+    xy_params prm;
+    int64_t has_prm, has_sched, n_knots, n_total, step, primed;
+    int64_t knot_step[XY_MAX_KNOTS];
+    double knot_T[XY_MAX_KNOTS];
+};
+}  // namespace
+
+int xy_save(xy_lattice* L, void* buf, size_t* size)
+{
+    if (!L || !size) return fail(XY_EINVAL, "NULL argument");
+    const size_t need = sizeof(SnapHeader) + sizeof(SnapCfg) * L->n_cfg + sizeof(double) * 6 * L->n_cfg +
+                        sizeof(float) * 2 * L->total_sites;
+    if (!buf) {
+        *size = need;
+        return XY_OK;
+    }
+    if (*size < need) return fail(XY_EINVAL, "buffer too small: %zu < %zu", *size, need);
+    int rc = check_ready(L);
+    if (rc) return rc;
+    if ((rc = prime_all(L))) return rc;
+    char* p = (char*)buf;
+    SnapHeader hd{};
+    std::memcpy(hd.magic, "XYLATT1", 8);
+    hd.version = 1;
+    hd.n_cfg = L->n_cfg;
+    hd.total = L->total_sites;
+    hd.B = L->B;
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    for (int c = 0; c < L->n_cfg; ++c) {
+        const CfgHost& h = L->cfg[c];
+        SnapCfg s{};
+        s.desc = h.desc;
+        s.prm = h.prm;
+        s.has_prm = h.has_prm;
+        s.has_sched = h.has_sched;
+        s.n_knots = h.n_knots;
+        s.n_total = h.n_total;
+        s.step = h.step;
+        s.primed = h.primed;
+        for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+            s.knot_step[i] = h.knot_step[i];
+            s.knot_T[i] = h.knot_T[i];
+        }
+        std::memcpy(p, &s, sizeof s);
+        p += sizeof s;
+    }
+    CK(cudaMemcpyAsync(p, L->d_moments, sizeof(double) * 6 * L->n_cfg, cudaMemcpyDeviceToHost, L->stream));
+    p += sizeof(double) * 6 * L->n_cfg;
+    CK(cudaMemcpyAsync(p, L->thA, sizeof(float) * L->total_sites, cudaMemcpyDeviceToHost, L->stream));
+    p += sizeof(float) * L->total_sites;
+    CK(cudaMemcpyAsync(p, L->omA, sizeof(float) * L->total_sites, cudaMemcpyDeviceToHost, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+    *size = need;
+    return XY_OK;
+}
+
+int xy_load(xy_lattice* L, const void* buf, size_t size)
+{
+    if (!L || !buf) return fail(XY_EINVAL, "NULL argument");
+    const size_t need = sizeof(SnapHeader) + sizeof(SnapCfg) * L->n_cfg + sizeof(double) * 6 * L->n_cfg +
+                        sizeof(float) * 2 * L->total_sites;
+    if (size < need) return fail(XY_EINVAL, "snapshot too small");
+    const char* p = (const char*)buf;
+    SnapHeader hd;
+    std::memcpy(&hd, p, sizeof hd);
+    p += sizeof hd;
+    if (std::memcmp(hd.magic, "XYLATT1", 8) != 0 || hd.version != 1) return fail(XY_EINVAL, "not a snapshot");
+    if (hd.n_cfg != L->n_cfg || hd.total != L->total_sites || hd.B != L->B)
+        return fail(XY_EINVAL, "snapshot shape does not match this lattice object");
+    std::vector<SnapCfg> sc(L->n_cfg);
+    for (int c = 0; c < L->n_cfg; ++c) {
+        std::memcpy(&sc[c], p, sizeof(SnapCfg));
+        p += sizeof(SnapCfg);
+        const xy_config_desc& a = sc[c].desc;
+        const xy_config_desc& b = L->cfg[c].desc;
+        if (a.Lx != b.Lx || a.Ly != b.Ly || a.n_replicas != b.n_replicas || a.seed != b.seed)
+            return fail(XY_EINVAL, "snapshot configuration %d does not match", c);
+    }
+    CK(cudaStreamSynchronize(L->stream));
+    for (int c = 0; c < L->n_cfg; ++c) {
+        CfgHost& h = L->cfg[c];
+        const SnapCfg& s = sc[c];
+        h.prm = s.prm;
+        h.has_prm = s.has_prm != 0;
+        h.has_sched = s.has_sched != 0;
+        h.n_knots = (int)s.n_knots;
+        h.n_total = s.n_total;
+        h.step = s.step;
+        h.primed = s.primed != 0;
+        DevCfg& d = L->h_dev[c];
+        if (h.has_prm) fill_params(d, h.prm);
+        d.n_knots = h.n_knots;
+        d.n_total = h.n_total;
+        for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+            h.knot_step[i] = d.knot_step[i] = s.knot_step[i];
+            h.knot_T[i] = d.knot_T[i] = s.knot_T[i];
+        }
+    }
+    CK(cudaMemcpyAsync(L->d_moments, p, sizeof(double) * 6 * L->n_cfg, cudaMemcpyHostToDevice, L->stream));
+    p += sizeof(double) * 6 * L->n_cfg;
+    CK(cudaMemcpyAsync(L->thA, p, sizeof(float) * L->total_sites, cudaMemcpyHostToDevice, L->stream));
+    p += sizeof(float) * L->total_sites;
+    CK(cudaMemcpyAsync(L->omA, p, sizeof(float) * L->total_sites, cudaMemcpyHostToDevice, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+    set_window_idle(L);
+    return upload_cfg(L);
+}
+
+int xy_synchronize(xy_lattice* L)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    CK(cudaStreamSynchronize(L->stream));
+    return XY_OK;
+}
+
+int64_t xy_kernel_launches(xy_lattice* L) { return L ? L->launches : -1; }
+
+int xy_set_kernel_timing(xy_lattice* L, int on)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    CK(cudaStreamSynchronize(L->stream));
+    L->timing = on != 0;
+    L->ev_used = 0;
+    return XY_OK;
+}
+
+int xy_kernel_timing(xy_lattice* L, double* ms, int64_t* launches)
+{
+    if (!L || !ms || !launches) return fail(XY_EINVAL, "NULL argument");
+    CK(cudaStreamSynchronize(L->stream));
+    for (int c = 0; c < XY_KCLASS_COUNT; ++c) {
+        ms[c] = 0.0;
+        launches[c] = 0;
+    }
+    for (size_t i = 0; i < L->ev_used; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, L->ev_pool[i].first, L->ev_pool[i].second));
+        ms[L->ev_class[i]] += t;
+        launches[L->ev_class[i]] += 1;
+    }
+    return XY_OK;
+}
+
+void xy_lattice_destroy(xy_lattice* L)
+{
+    if (!L) return;
+    cudaStreamSynchronize(L->stream);
+    free_lattice(L);
+}
+
+int xy_debug_noise(uint64_t seed, int cfg, int replica, int64_t k, int tag, int64_t n_quads, uint32_t* words,
+                   float* gauss, void* stream)
+{
+    if (n_quads < 0 || cfg < 0 || cfg > 65535 || replica < 0 || replica > 65535 || tag < 0 || tag > 255)
+        return fail(XY_EINVAL, "bad noise coordinates");
+    CK(launch_debug_noise(seed, cfg, replica, k, tag, n_quads, words, gauss, (cudaStream_t)stream));
+    return XY_OK;
+}
+
+int xy_debug_philox(const uint32_t* counters, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!counters || !out))) return fail(XY_EINVAL, "bad arguments");
+    CK(launch_debug_philox(counters, k0, k1, n, out, (cudaStream_t)stream));
+    return XY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+// xy_device.cuh -- device-side building blocks shared by every stepping kernel.
+//
+// All arithmetic is written with explicit fmaf / __fmul_rn so that, with the
+// library compiled under -fmad=false, every kernel that calls these functions
+// produces bit-identical results for the same site and step (the plain, the
+// strip and the resident steppers, the prime and full-step-velocity kernels,
+// and the adjoint's recompute pass).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "xy_internal.h"
+
+namespace xy {
+
+// -------------------------------------------------------------------------
+// Counter-based noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+// Counter = (quad, (config << 16) | replica, step lo32, (tag << 24) | step hi24),
+// key = 64-bit seed.  One call gives the four Gaussians of four consecutive
+// sites (a float4 of the state).
+// -------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 noise_counter(uint32_t quad, uint32_t cfg_rep, int64_t k, uint32_t tag)
+{
+    const uint64_t ku = (uint64_t)k;
+    return make_uint4(quad, cfg_rep, (uint32_t)(ku & 0xFFFFFFFFu),
+                      (tag << 24) | (uint32_t)((ku >> 32) & 0xFFFFFFu));
+}
+
+// Uniform (m + 1/2) 2^-23 in (0,1) from the top 23 bits of a word, exactly:
+// the float 1 + m 2^-23 minus (1 - 2^-24) is exact by Sterbenz' lemma.
+__device__ __forceinline__ float uniform01(uint32_t x)
+{
+    return __fadd_rn(__uint_as_float(0x3F800000u | (x >> 9)), -0.99999994f);
+}
+
+// Box-Muller (Box & Muller 1958) of two uniform pairs, scaled by the noise
+// amplitude c: returns c*g0..c*g3 with g0 = r cos(2 pi u1), g1 = r sin(2 pi u1),
+// g2 = r' cos(2 pi u3), g3 = r' sin(2 pi u3), r = sqrt(-2 ln u0),
+// r' = sqrt(-2 ln u2).  The angle is shifted by -pi into the accurate range of
+// the hardware sine, and the sign flip is folded into the radius.
+__device__ __forceinline__ float4 gauss4_scaled(uint4 w, float c)
+{
+    const float kTwoPi = 6.28318530717958648f;
+    const float kPi = 3.14159265358979324f;
+    const float kM2Ln2 = -1.38629436111989061f;  // -2 ln 2
+    float4 out;
+    {
+        const float u0 = uniform01(w.x), u1 = uniform01(w.y);
+        const float t = __fmul_rn(kM2Ln2, __log2f(u0));   // -2 ln u0 > 0
+        const float r = __fmul_rn(__fmul_rn(t, rsqrtf(t)), -c);
+        float s, co;
+        __sincosf(fmaf(kTwoPi, u1, -kPi), &s, &co);
+        out.x = __fmul_rn(r, co);
+        out.y = __fmul_rn(r, s);
+    }
+    {
+        const float u2 = uniform01(w.z), u3 = uniform01(w.w);
+        const float t = __fmul_rn(kM2Ln2, __log2f(u2));
+        const float r = __fmul_rn(__fmul_rn(t, rsqrtf(t)), -c);
+        float s, co;
+        __sincosf(fmaf(kTwoPi, u3, -kPi), &s, &co);
+        out.z = __fmul_rn(r, co);
+        out.w = __fmul_rn(r, s);
+    }
+    return out;
+}
+
+// -------------------------------------------------------------------------
+// State space: map an angle back into [-pi/2, pi/2) (Sec. III.D).
+// -------------------------------------------------------------------------
+__device__ __forceinline__ float wrap_angle(float t)
+{
+    const float kPi = 3.14159265358979324f;
+    const float kInvPi = 0.318309886183790672f;
+    const float kHalfPi = 1.57079632679489662f;
+    const float n = floorf(fmaf(t, kInvPi, 0.5f));
+    float r = fmaf(-kPi, n, t);
+    r = (r >= kHalfPi) ? __fadd_rn(r, -kPi) : r;
+    r = (r < -kHalfPi) ? __fadd_rn(r, kPi) : r;
+    return r;
+}
+
+// -------------------------------------------------------------------------
+// Per-step constants of one configuration.
+// -------------------------------------------------------------------------
+struct StepConst {
+    float c;        // half-kick noise amplitude (1/2) sqrt(2 eta T_k) sqrt(dt)
+    float hdt;      // dt / 2
+    float dt;
+    float oma;      // 1 - eta dt / 2
+    float inv1pa;   // 1 / (1 + eta dt / 2)
+    float nqJx;     // -q J_par
+    float nqJy;     // -q J_perp
+    float hp;       // h p
+    float q, p;
+};
+
+// Temperature at step k: piecewise linear through the knots, constant outside
+// (FP64, evaluated once per thread block or warp, never per site).
+__device__ __forceinline__ double temperature_at(const DevCfg& cf, int64_t k)
+{
+    if (cf.n_knots <= 0) return 0.0;
+    if (k <= cf.knot_step[0]) return cf.knot_T[0];
+    for (int i = 0; i + 1 < cf.n_knots; ++i) {
+        if (k <= cf.knot_step[i + 1]) {
+            const double f = (double)(k - cf.knot_step[i]) / (double)(cf.knot_step[i + 1] - cf.knot_step[i]);
+            return cf.knot_T[i] + (cf.knot_T[i + 1] - cf.knot_T[i]) * f;
+        }
+    }
+    return cf.knot_T[cf.n_knots - 1];
+}
+
+__device__ __forceinline__ float noise_amp(const DevCfg& cf, int64_t k)
+{
+    const double T = temperature_at(cf, k);
+    return (float)(0.5 * sqrt(2.0 * cf.eta_d * (T > 0.0 ? T : 0.0)) * sqrt(cf.dt_d));
+}
+
+__device__ __forceinline__ StepConst step_const(const DevCfg& cf, float c)
+{
+    StepConst s;
+    s.c = c;
+    s.hdt = cf.hdt;
+    s.dt = cf.dt;
+    s.oma = cf.oma;
+    s.inv1pa = cf.inv1pa;
+    s.nqJx = cf.nqJx;
+    s.nqJy = cf.nqJy;
+    s.hp = cf.hp;
+    s.q = cf.q;
+    s.p = cf.p;
+    return s;
+}
+
+// -------------------------------------------------------------------------
+// One site of the merged BBK step (App. A.1) in leapfrog form.
+// Stored state: theta_k and v_k = omega_{k-1/2}.  With g = (dt/2) F_k + c_k n_k:
+//   omega_k     = (v_k + g) / (1 + eta dt / 2)          (end of Eq. BBK-2 of step k-1)
+//   v_{k+1}     = (1 - eta dt / 2) omega_k + g           (Eq. BBK-1 of step k)
+//   theta_{k+1} = wrap(theta_k + dt v_{k+1})             (drift + modulo)
+// -------------------------------------------------------------------------
+
+// Force on one site from its own (s, c) = (sin q t, cos q t), the sums of the
+// neighbours' (s, c) along x and y, and sin(p t):
+//   F = -q J_par (s (cL + cR) - c (sL + sR)) - q J_perp (s (cU + cD) - c (sU + sD)) + h p sin(p t)
+__device__ __forceinline__ float site_force(const StepConst& K, float s, float c, float sx, float cx,
+                                            float sy, float cy, float sinp)
+{
+    const float ax = fmaf(s, cx, -__fmul_rn(c, sx));
+    const float ay = fmaf(s, cy, -__fmul_rn(c, sy));
+    return fmaf(K.nqJx, ax, fmaf(K.nqJy, ay, __fmul_rn(K.hp, sinp)));
+}
+
+struct SiteOut {
+    float theta, v, omega;
+};
+
+__device__ __forceinline__ SiteOut site_update(const StepConst& K, float theta, float v, float F, float cn)
+{
+    SiteOut o;
+    const float g = fmaf(K.hdt, F, cn);
+    o.omega = __fmul_rn(__fadd_rn(v, g), K.inv1pa);
+    o.v = fmaf(K.oma, o.omega, g);
+    o.theta = wrap_angle(fmaf(K.dt, o.v, theta));
+    return o;
+}
+
+// Energy of one site with its forward bonds (x+1, y+1), per Eq. (XY-Hamilton-Kinetic):
+//   omega^2 / 2 - J_par cos q(t - t_{x+1}) - J_perp cos q(t - t_{y+1}) + h cos(p t)
+// with cos q(a - b) = c_a c_b + s_a s_b.
+__device__ __forceinline__ float site_energy(const DevCfg& cf, float omega, float s, float c, float sR,
+                                             float cR, float sD, float cD, float cosp)
+{
+    const float bx = fmaf(c, cR, __fmul_rn(s, sR));
+    const float by = fmaf(c, cD, __fmul_rn(s, sD));
+    float e = __fmul_rn(0.5f, __fmul_rn(omega, omega));
+    e = fmaf(-cf.Jx, bx, e);
+    e = fmaf(-cf.Jy, by, e);
+    e = fmaf(cf.h, cosp, e);
+    return e;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 ld4_stream(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4_stream(float* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
+
+__device__ __forceinline__ float f4get(const float4& v, int i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+}  // namespace xy

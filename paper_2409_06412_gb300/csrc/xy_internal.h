@@ -1,0 +1,126 @@
+// xy_internal.h -- data shared between the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/xy_lattice.h"
+
+namespace xy {
+
+// Per-configuration record in device memory (read by every kernel).
+struct DevCfg {
+    int32_t Lx, Ly, n_rep, cfg_index;
+    int64_t offset;     // first site of replica 0 in the state buffers
+    int64_t N;          // Lx * Ly
+    uint32_t key0, key1;
+    int32_t b_first;    // flattened lattice index of replica 0
+    int32_t stag;
+    // FP32 constants of the step
+    float Jx, Jy, h, p, q, dt, hdt, oma, inv1pa, nqJx, nqJy, hp;
+    double eta_d, dt_d;
+    int32_t n_knots, pad0;
+    int64_t knot_step[XY_MAX_KNOTS];
+    double knot_T[XY_MAX_KNOTS];
+    int64_t n_total;
+    // per call
+    int64_t k_start;    // step at the start of the current call
+    int64_t n_call;     // steps this configuration takes in the current call
+    int64_t rec_first;  // first step of this call with k % record_every == 0
+};
+
+// Per-call settings read by the stepping kernels.
+// Lives in device memory so that captured CUDA graphs stay valid across calls.
+struct CallArgs {
+    int64_t j_base;     // steps already done in this call (advanced by a graph node)
+    int64_t rec_stride; // R: records per lattice in rec_dev
+    double2* rec_dev;   // [B][R] (M, E)
+    int64_t k_shift;    // added to the step index (segment recompute of the adjoint)
+    int record_every;   // 0: no observables
+    int fixed_parity;   // 1: always read buffers A and write buffers B
+    int err;            // device error flag
+    int pad;
+};
+
+// One warp of the strip stepper: a 128-wide (or full-width when Lx <= 128)
+// column strip of one lattice over rows [y0, y0 + H).
+struct StripTask {
+    int32_t cfg;
+    int32_t rep;
+    int32_t unit;       // index of this warp's unit inside its lattice (observable partials)
+    int32_t n_units;    // units of the lattice
+    int32_t x0;         // first column of the strip (Lx > 128) or 0
+    int32_t y0;
+};
+
+// One thread block of the resident stepper: one whole lattice.
+struct ResidentTask {
+    int32_t cfg;
+    int32_t rep;
+};
+
+struct Buffers {
+    float* thA;
+    float* omA;
+    float* thB;
+    float* omB;
+};
+
+// Observable partial sums of one lattice assembled by "last unit" reduction.
+struct Partials {
+    double2* part;       // [B][max_units]
+    unsigned* count;     // [B]
+    int32_t max_units;
+};
+
+// ---- launchers (xy_step.cu)
+cudaError_t launch_init(const DevCfg* d_cfg, const DevCfg& h_cfg, int init_mode, float* theta, float* omega,
+                        cudaStream_t st);
+cudaError_t launch_prime(const DevCfg* d_cfg, const DevCfg& h_cfg, float* theta, float* omega, cudaStream_t st);
+cudaError_t launch_omega_full(const DevCfg* d_cfg, const DevCfg& h_cfg, int rep_first, int rep_count,
+                              const float* theta, const float* omega, float* out, cudaStream_t st);
+cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h_cfg, int64_t j_local, Buffers buf,
+                              const CallArgs* ca, Partials pa, int write_state, cudaStream_t st);
+cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int64_t j_local,
+                              Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st);
+cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
+                                 int threads, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
+                                 cudaStream_t st);
+cudaError_t prepare_resident(int Lx, int Ly, int threads);
+cudaError_t launch_advance(CallArgs* ca, int64_t by, cudaStream_t st);
+cudaError_t launch_add_kshift(CallArgs* ca, int64_t by, cudaStream_t st);
+cudaError_t launch_moments(const DevCfg* d_cfg, int n_cfg, const CallArgs* ca, int64_t t0, double* moments,
+                           cudaStream_t st);
+int resident_threads(int Lx, int Ly);
+size_t resident_smem_bytes(int Lx, int Ly, int threads);
+int strip_units_per_lattice(int Lx, int Ly, int H);
+cudaError_t launch_debug_noise(uint64_t seed, int cfg, int rep, int64_t k, int tag, int64_t n_quads,
+                               uint32_t* words, float* gauss, cudaStream_t st);
+cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
+                                cudaStream_t st);
+
+// ---- domains (xy_ccl.cu)
+cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* labels, int32_t* size_scratch,
+                       int32_t* count_scratch, int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err,
+                       cudaStream_t st);
+
+// ---- adjoint (xy_adjoint.cu)
+struct AdjArgs {
+    const float* theta;   // theta_k of all lattices (segment buffer slice)
+    const float* omega;   // v_k = omega_{k-1/2}
+    float* tb;            // adjoint of theta (in: theta_{k+1}, out: theta_k)
+    float* vb;            // adjoint of v     (in: v_{k+1},     out: v_k)
+    float* Fb;            // adjoint of F_k (scratch)
+    const double2* rec;   // forward observables [B][R] (M_k, E_k) with R = n + 1
+    int64_t rec_stride;
+    int64_t k;            // step being reversed
+    int64_t k0;           // first step of the adjoint window
+    int64_t k_end;        // k0 + n
+    double wE, wM, inv_norm;  // objective weights and 1/(B n)
+    double* gacc;         // [n_blocks][6] per-block FP64 accumulators (J_par, J_perp, h, a-bar, b-bar, c-bar-eta)
+};
+cudaError_t launch_adjoint_phase_a(const DevCfg* d_cfg, const DevCfg& h_cfg, int block_base, AdjArgs a,
+                                   cudaStream_t st);
+cudaError_t launch_adjoint_phase_b(const DevCfg* d_cfg, const DevCfg& h_cfg, AdjArgs a, cudaStream_t st);
+int adjoint_blocks(const DevCfg& h_cfg);
+
+}  // namespace xy

@@ -1,0 +1,802 @@
+// xy_step.cu -- stepping kernels of the BBK Langevin integrator on the
+// periodic Si(001) dimer-angle lattice (arXiv 2409.06412, Sec. III and App. A.1),
+// with the per-step order-parameter and energy reductions (Sec. IV.A,
+// Eq. lattice-average; App. B, Eq. ensemble-average-calculation).
+//
+// Three steppers share the per-site arithmetic of xy_device.cuh and give
+// bit-identical states:
+//   plain    one thread per quad (4 sites), neighbours from global memory/L2,
+//            one launch per step per configuration (the reference path);
+//   strip    one warp per 128-site column strip (or per full row when
+//            Lx <= 128) sweeping down H rows with a sliding window of
+//            (sin q t, cos q t) rows in registers; x neighbours by warp
+//            shuffles, one force and one Philox call per quad per step;
+//            all lattices of all configurations in one launch;
+//   resident one thread block per whole lattice held in shared memory,
+//            stepping many steps per launch (lattices up to ~24k sites).
+#include <cstdio>
+
+#include "xy_device.cuh"
+
+namespace xy {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void sc_of(float q, float th, float& s, float& c)
+{
+    __sincosf(__fmul_rn(q, th), &s, &c);
+}
+
+__device__ __forceinline__ float sinp_of(float p, float th) { return __sinf(__fmul_rn(p, th)); }
+__device__ __forceinline__ float cosp_of(float p, float th) { return __cosf(__fmul_rn(p, th)); }
+
+__device__ __forceinline__ int wrapi(int v, int n)
+{
+    const int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// Neighbourhood of one quad (4 consecutive sites of a row) read from global memory.
+struct QuadField {
+    float th[4];
+    float s[4], c[4];
+    float sx[4], cx[4];  // sums over the two x neighbours
+    float sy[4], cy[4];  // sums over the two y neighbours
+    float sR[4], cR[4];  // forward x neighbour
+    float sD[4], cD[4];  // forward y neighbour
+};
+
+__device__ __forceinline__ void quad_field(const float* lat, int Lx, int Ly, int x, int y, float q, QuadField& f)
+{
+    const float4 t = ld4(lat + (int64_t)y * Lx + x);
+    const float4 tu = ld4(lat + (int64_t)wrapi(y - 1, Ly) * Lx + x);
+    const float4 td = ld4(lat + (int64_t)wrapi(y + 1, Ly) * Lx + x);
+    const float tl = lat[(int64_t)y * Lx + wrapi(x - 1, Lx)];
+    const float tr = lat[(int64_t)y * Lx + wrapi(x + 4, Lx)];
+    float su[4], cu[4], sl, cl, sr, cr;
+    f.th[0] = t.x; f.th[1] = t.y; f.th[2] = t.z; f.th[3] = t.w;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        sc_of(q, f.th[i], f.s[i], f.c[i]);
+        sc_of(q, f4get(tu, i), su[i], cu[i]);
+        sc_of(q, f4get(td, i), f.sD[i], f.cD[i]);
+    }
+    sc_of(q, tl, sl, cl);
+    sc_of(q, tr, sr, cr);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float sLi = i == 0 ? sl : f.s[i - 1];
+        const float cLi = i == 0 ? cl : f.c[i - 1];
+        f.sR[i] = i == 3 ? sr : f.s[i + 1];
+        f.cR[i] = i == 3 ? cr : f.c[i + 1];
+        f.sx[i] = __fadd_rn(sLi, f.sR[i]);
+        f.cx[i] = __fadd_rn(cLi, f.cR[i]);
+        f.sy[i] = __fadd_rn(su[i], f.sD[i]);
+        f.cy[i] = __fadd_rn(cu[i], f.cD[i]);
+    }
+}
+
+// FP64 warp sum in a fixed butterfly order (deterministic).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Commit one unit's (M, E) partial of lattice b; the unit that arrives last
+// sums all partials of the lattice in a fixed order and writes the record.
+// Must be called by a whole warp (lane 0 holds the partial).
+__device__ void commit_partial(Partials pa, int64_t b, int unit, int n_units, double pm, double pe,
+                               double2* rec_slot, double invN)
+{
+    const int lane = threadIdx.x & 31;
+    int last = 0;
+    if (lane == 0) {
+        pa.part[b * pa.max_units + unit] = make_double2(pm, pe);
+        __threadfence();
+        const unsigned old = atomicAdd(&pa.count[b], 1u);
+        last = (old == (unsigned)(n_units - 1));
+    }
+    last = __shfl_sync(kFull, last, 0);
+    if (!last) return;
+    __threadfence();
+    double sm = 0.0, se = 0.0;
+    for (int u = lane; u < n_units; u += 32) {
+        const double2 p = __ldcg(&pa.part[b * pa.max_units + u]);
+        sm += p.x;
+        se += p.y;
+    }
+    sm = warp_sum(sm);
+    se = warp_sum(se);
+    if (lane == 0) {
+        *rec_slot = make_double2(sm * invN, se * invN);
+        pa.count[b] = 0u;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// Initial state
+// ===========================================================================
+__global__ void init_kernel(const DevCfg* cfgs, int c, int mode, float* theta, float* omega)
+{
+    const DevCfg& cf = cfgs[c];
+    const int64_t nq_lat = cf.N / 4;
+    const int64_t nq = nq_lat * cf.n_rep;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        const int rep = (int)(i / nq_lat);
+        const int64_t quad = i - (int64_t)rep * nq_lat;
+        const int64_t base = cf.offset + (int64_t)rep * cf.N + 4 * quad;
+        float4 t;
+        if (mode == XY_INIT_UNIFORM) {
+            const uint4 w = philox4x32_10(
+                noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep, 0, 1u), cf.key0,
+                cf.key1);
+            const float kTwoPi = 6.28318530717958648f;
+            t.x = wrap_angle(__fmul_rn(kTwoPi, uniform01(w.x)));
+            t.y = wrap_angle(__fmul_rn(kTwoPi, uniform01(w.y)));
+            t.z = wrap_angle(__fmul_rn(kTwoPi, uniform01(w.z)));
+            t.w = wrap_angle(__fmul_rn(kTwoPi, uniform01(w.w)));
+        } else {
+            const float o = 1.25663706143591730f;  // 2 pi / 5
+            t = make_float4(o, o, o, o);
+        }
+        st4(theta + base, t);
+        st4(omega + base, make_float4(0.f, 0.f, 0.f, 0.f));
+    }
+}
+
+cudaError_t launch_init(const DevCfg* d_cfg, const DevCfg& h, int init_mode, float* theta, float* omega,
+                        cudaStream_t st)
+{
+    if (init_mode == XY_INIT_USER) return cudaSuccess;
+    const int64_t nq = h.N / 4 * h.n_rep;
+    const int threads = 256;
+    const int blocks = (int)((nq + threads - 1) / threads < 65536 ? (nq + threads - 1) / threads : 65536);
+    init_kernel<<<blocks, threads, 0, st>>>(d_cfg, h.cfg_index, init_mode, theta, omega);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Per-quad kernels with global-memory neighbours: prime, full-step omega,
+// plain stepper.
+// ===========================================================================
+
+// Convert a full-step omega_0 (in omega) into the stored leapfrog velocity
+// v_0 = (1 + eta dt / 2) omega_0 - g_0 so that the first step reproduces
+// Eq. (BBK-1) exactly: omega_0 = (v_0 + g_0) / (1 + eta dt / 2).
+__global__ void prime_kernel(const DevCfg* cfgs, int c, float* theta, float* omega)
+{
+    const DevCfg& cf = cfgs[c];
+    __shared__ float s_c;
+    if (threadIdx.x == 0) s_c = noise_amp(cf, cf.k_start);
+    __syncthreads();
+    const StepConst K = step_const(cf, s_c);
+    const int64_t nq_lat = cf.N / 4;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nq_lat * cf.n_rep) return;
+    const int rep = (int)(i / nq_lat);
+    const int64_t quad = i - (int64_t)rep * nq_lat;
+    const int y = (int)(4 * quad / cf.Lx), x = (int)(4 * quad - (int64_t)y * cf.Lx);
+    const float* lat = theta + cf.offset + (int64_t)rep * cf.N;
+    float* om = omega + cf.offset + (int64_t)rep * cf.N + 4 * quad;
+    QuadField f;
+    quad_field(lat, cf.Lx, cf.Ly, x, y, K.q, f);
+    const uint4 w = philox4x32_10(noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep,
+                                                cf.k_start, 0u), cf.key0, cf.key1);
+    const float4 cn = gauss4_scaled(w, K.c);
+    const float4 w0 = ld4(om);
+    float out[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float F = site_force(K, f.s[s], f.c[s], f.sx[s], f.cx[s], f.sy[s], f.cy[s], sinp_of(K.p, f.th[s]));
+        const float g = fmaf(K.hdt, F, f4get(cn, s));
+        out[s] = __fadd_rn(__fdiv_rn(f4get(w0, s), K.inv1pa), -g);
+    }
+    st4(om, make_float4(out[0], out[1], out[2], out[3]));
+}
+
+cudaError_t launch_prime(const DevCfg* d_cfg, const DevCfg& h, float* theta, float* omega, cudaStream_t st)
+{
+    const int64_t nq = h.N / 4 * h.n_rep;
+    prime_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(d_cfg, h.cfg_index, theta, omega);
+    return cudaGetLastError();
+}
+
+// omega_k = (v_k + g_k) / (1 + eta dt / 2) of replicas [rep_first, rep_first + rep_count).
+__global__ void omega_full_kernel(const DevCfg* cfgs, int c, int rep_first, int rep_count, const float* theta,
+                                  const float* omega, float* out)
+{
+    const DevCfg& cf = cfgs[c];
+    __shared__ float s_c;
+    if (threadIdx.x == 0) s_c = noise_amp(cf, cf.k_start);
+    __syncthreads();
+    const StepConst K = step_const(cf, s_c);
+    const int64_t nq_lat = cf.N / 4;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nq_lat * rep_count) return;
+    const int rr = (int)(i / nq_lat);
+    const int rep = rep_first + rr;
+    const int64_t quad = i - (int64_t)rr * nq_lat;
+    const int y = (int)(4 * quad / cf.Lx), x = (int)(4 * quad - (int64_t)y * cf.Lx);
+    const float* lat = theta + cf.offset + (int64_t)rep * cf.N;
+    QuadField f;
+    quad_field(lat, cf.Lx, cf.Ly, x, y, K.q, f);
+    const uint4 w = philox4x32_10(noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep,
+                                                cf.k_start, 0u), cf.key0, cf.key1);
+    const float4 cn = gauss4_scaled(w, K.c);
+    const float4 v = ld4(omega + cf.offset + (int64_t)rep * cf.N + 4 * quad);
+    float o[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float F = site_force(K, f.s[s], f.c[s], f.sx[s], f.cx[s], f.sy[s], f.cy[s], sinp_of(K.p, f.th[s]));
+        const SiteOut so = site_update(K, f.th[s], f4get(v, s), F, f4get(cn, s));
+        o[s] = so.omega;
+    }
+    st4(out + (int64_t)rr * cf.N + 4 * quad, make_float4(o[0], o[1], o[2], o[3]));
+}
+
+cudaError_t launch_omega_full(const DevCfg* d_cfg, const DevCfg& h, int rep_first, int rep_count,
+                              const float* theta, const float* omega, float* out, cudaStream_t st)
+{
+    const int64_t nq = h.N / 4 * rep_count;
+    omega_full_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(d_cfg, h.cfg_index, rep_first, rep_count,
+                                                                     theta, omega, out);
+    return cudaGetLastError();
+}
+
+// One step of one configuration, one thread per quad.  Blocks never straddle
+// two lattices: block index = rep * blocks_per_lattice + unit.
+__global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int c, int64_t j_local, Buffers buf,
+                                                         const CallArgs* cap, Partials pa, int write_state)
+{
+    const DevCfg& cf = cfgs[c];
+    const CallArgs ca = *cap;
+    const int64_t j = ca.j_base + j_local;
+    if (j >= cf.n_call) return;
+    __shared__ float s_c;
+    __shared__ double s_red[2][8];
+    const int64_t k = cf.k_start + j + ca.k_shift;
+    if (threadIdx.x == 0) s_c = noise_amp(cf, k);
+    __syncthreads();
+    const StepConst K = step_const(cf, s_c);
+    const int64_t nq_lat = cf.N / 4;
+    const int bpl = (int)((nq_lat + blockDim.x - 1) / blockDim.x);
+    const int rep = blockIdx.x / bpl;
+    const int unit = blockIdx.x - rep * bpl;
+    const int64_t quad = (int64_t)unit * blockDim.x + threadIdx.x;
+    const bool odd = !ca.fixed_parity && (j & 1) != 0;
+    const int64_t lat_off = cf.offset + (int64_t)rep * cf.N;
+    const float* thS = (odd ? buf.thB : buf.thA) + lat_off;
+    const float* omS = (odd ? buf.omB : buf.omA) + lat_off;
+    float* thD = (odd ? buf.thA : buf.thB) + lat_off;
+    float* omD = (odd ? buf.omA : buf.omB) + lat_off;
+    const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
+    float pm = 0.f, pe = 0.f;
+    if (quad < nq_lat) {
+        const int y = (int)(4 * quad / cf.Lx), x = (int)(4 * quad - (int64_t)y * cf.Lx);
+        QuadField f;
+        quad_field(thS, cf.Lx, cf.Ly, x, y, K.q, f);
+        const uint4 w = philox4x32_10(
+            noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep, k, 0u), cf.key0, cf.key1);
+        const float4 cn = gauss4_scaled(w, K.c);
+        const float4 v = ld4(omS + 4 * quad);
+        float to[4], vo[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float F =
+                site_force(K, f.s[s], f.c[s], f.sx[s], f.cx[s], f.sy[s], f.cy[s], sinp_of(K.p, f.th[s]));
+            const SiteOut so = site_update(K, f.th[s], f4get(v, s), F, f4get(cn, s));
+            to[s] = so.theta;
+            vo[s] = so.v;
+            if (rec) {
+                const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
+                pm = fmaf(sigma, f.s[s], pm);
+                pe = __fadd_rn(pe, site_energy(cf, so.omega, f.s[s], f.c[s], f.sR[s], f.cR[s], f.sD[s], f.cD[s],
+                                               cosp_of(K.p, f.th[s])));
+            }
+        }
+        if (write_state) {
+            st4(thD + 4 * quad, make_float4(to[0], to[1], to[2], to[3]));
+            st4(omD + 4 * quad, make_float4(vo[0], vo[1], vo[2], vo[3]));
+        }
+    }
+    if (!rec) return;
+    // block partial: per-warp FP64 butterfly, then warp 0 sums the warps in order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double wm = warp_sum((double)pm), we = warp_sum((double)pe);
+    if (lane == 0) {
+        s_red[0][warp] = wm;
+        s_red[1][warp] = we;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double bm = 0.0, be = 0.0;
+        if (lane == 0)
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+                bm += s_red[0][w2];
+                be += s_red[1][w2];
+            }
+        const int64_t b = cf.b_first + rep;
+        const int64_t r = (k - cf.rec_first) / ca.record_every;
+        commit_partial(pa, b, unit, bpl, bm, be, ca.rec_dev + b * ca.rec_stride + r, 1.0 / (double)cf.N);
+    }
+}
+
+cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h, int64_t j_local, Buffers buf,
+                              const CallArgs* ca, Partials pa, int write_state, cudaStream_t st)
+{
+    const int64_t nq_lat = h.N / 4;
+    const int bpl = (int)((nq_lat + 255) / 256);
+    plain_step_kernel<<<(unsigned)(bpl * h.n_rep), 256, 0, st>>>(d_cfg, h.cfg_index, j_local, buf, ca, pa,
+                                                                  write_state);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Strip stepper: one warp sweeps H rows of a column strip.
+// ===========================================================================
+namespace {
+
+struct RowSC {
+    float s[4], c[4];
+    float se, ce;  // edge neighbour outside the strip (lane 0: left, lane 31: right)
+};
+
+__device__ __forceinline__ void row_sc(const float4& t, float te, float q, RowSC& r)
+{
+    sc_of(q, t.x, r.s[0], r.c[0]);
+    sc_of(q, t.y, r.s[1], r.c[1]);
+    sc_of(q, t.z, r.s[2], r.c[2]);
+    sc_of(q, t.w, r.s[3], r.c[3]);
+    sc_of(q, te, r.se, r.ce);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) strip_step_kernel(const DevCfg* cfgs, const StripTask* tasks, int n_tasks,
+                                                         int H, int64_t j_local, Buffers buf, const CallArgs* cap,
+                                                         Partials pa)
+{
+    const CallArgs ca = *cap;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= n_tasks) return;
+    const StripTask task = tasks[t];
+    const DevCfg& cf = cfgs[task.cfg];
+    const int64_t j = ca.j_base + j_local;
+    if (j >= cf.n_call) return;
+    const int64_t k = cf.k_start + j + ca.k_shift;
+    float c = 0.f;
+    if (lane == 0) c = noise_amp(cf, k);
+    c = __shfl_sync(kFull, c, 0);
+    const StepConst K = step_const(cf, c);
+    const int Lx = cf.Lx, Ly = cf.Ly;
+    const bool odd = !ca.fixed_parity && (j & 1) != 0;
+    const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
+    const float* __restrict__ thS = (odd ? buf.thB : buf.thA) + lat_off;
+    const float* __restrict__ omS = (odd ? buf.omB : buf.omA) + lat_off;
+    float* __restrict__ thD = (odd ? buf.thA : buf.thB) + lat_off;
+    float* __restrict__ omD = (odd ? buf.omA : buf.omB) + lat_off;
+
+    const int G = Lx >= 128 ? 32 : (Lx >> 2);     // lanes per row
+    const int grp = lane / G, lg = lane - grp * G;
+    const bool multi = Lx > 128;
+    const int x = task.x0 + 4 * lg;
+    const int ybeg = task.y0 + grp * H;
+    // edge column: lane 0 of a strip needs x0 - 1, lane 31 needs x0 + 128
+    const int xe = multi ? (lg == 0 ? wrapi(task.x0 - 1, Lx) : wrapi(task.x0 + 128, Lx)) : x;
+    const int srcL = grp * G + (lg + G - 1) % G;
+    const int srcR = grp * G + (lg + 1) % G;
+    const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
+    const uint32_t cfgrep = ((uint32_t)cf.cfg_index << 16) | (uint32_t)task.rep;
+
+    RowSC prev, cur, nxt;
+    {
+        const int yp = wrapi(ybeg - 1, Ly);
+        row_sc(ld4(thS + (int64_t)yp * Lx + x), thS[(int64_t)yp * Lx + xe], K.q, prev);
+    }
+    float4 th_cur = ld4(thS + (int64_t)ybeg * Lx + x);
+    row_sc(th_cur, thS[(int64_t)ybeg * Lx + xe], K.q, cur);
+    int yn = wrapi(ybeg + 1, Ly);
+    float4 th_nxt = ld4(thS + (int64_t)yn * Lx + x);
+    float te_nxt = thS[(int64_t)yn * Lx + xe];
+    float pm = 0.f, pe = 0.f;
+
+    for (int r = 0; r < H; ++r) {
+        const int y = ybeg + r;
+        // prefetch: theta two rows ahead, omega of this row
+        const int ynn = wrapi(y + 2, Ly);
+        const float4 th_nn = ld4(thS + (int64_t)ynn * Lx + x);
+        const float te_nn = thS[(int64_t)ynn * Lx + xe];
+        const float4 v = ld4_stream(omS + (int64_t)y * Lx + x);
+        row_sc(th_nxt, te_nxt, K.q, nxt);
+
+        // x neighbours of the quad's outer sites
+        float sL = __shfl_sync(kFull, cur.s[3], srcL);
+        float cL = __shfl_sync(kFull, cur.c[3], srcL);
+        float sR = __shfl_sync(kFull, cur.s[0], srcR);
+        float cR = __shfl_sync(kFull, cur.c[0], srcR);
+        if (multi) {
+            if (lg == 0) { sL = cur.se; cL = cur.ce; }
+            if (lg == 31) { sR = cur.se; cR = cur.ce; }
+        }
+        const uint32_t quad = (uint32_t)(((int64_t)y * Lx + x) >> 2);
+        const float4 cn = gauss4_scaled(philox4x32_10(noise_counter(quad, cfgrep, k, 0u), cf.key0, cf.key1), K.c);
+        float to[4], vo[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float sl = s == 0 ? sL : cur.s[s - 1];
+            const float cl = s == 0 ? cL : cur.c[s - 1];
+            const float sr = s == 3 ? sR : cur.s[s + 1];
+            const float cr = s == 3 ? cR : cur.c[s + 1];
+            const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
+            const float sy = __fadd_rn(prev.s[s], nxt.s[s]), cy = __fadd_rn(prev.c[s], nxt.c[s]);
+            const float th = f4get(th_cur, s);
+            const float F = site_force(K, cur.s[s], cur.c[s], sx, cx, sy, cy, sinp_of(K.p, th));
+            const SiteOut so = site_update(K, th, f4get(v, s), F, f4get(cn, s));
+            to[s] = so.theta;
+            vo[s] = so.v;
+            if (rec) {
+                const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
+                pm = fmaf(sigma, cur.s[s], pm);
+                pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
+                                               cosp_of(K.p, th)));
+            }
+        }
+        st4_stream(thD + (int64_t)y * Lx + x, make_float4(to[0], to[1], to[2], to[3]));
+        st4_stream(omD + (int64_t)y * Lx + x, make_float4(vo[0], vo[1], vo[2], vo[3]));
+        prev = cur;
+        cur = nxt;
+        th_cur = th_nxt;
+        th_nxt = th_nn;
+        te_nxt = te_nn;
+    }
+    if (rec) {
+        const double wm = warp_sum((double)pm), we = warp_sum((double)pe);
+        const int64_t b = cf.b_first + task.rep;
+        const int64_t r = (k - cf.rec_first) / ca.record_every;
+        commit_partial(pa, b, task.unit, task.n_units, wm, we, ca.rec_dev + b * ca.rec_stride + r, 1.0 / (double)cf.N);
+    }
+}
+
+// Units (warps) per lattice for the strip stepper with H rows per row group.
+int strip_units_per_lattice(int Lx, int Ly, int H)
+{
+    if (Lx >= 128) return (Lx / 128) * (Ly / H);
+    const int groups = 32 / (Lx / 4);
+    return Ly / (H * groups);
+}
+
+cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int64_t j_local,
+                              Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st)
+{
+    if (n_tasks == 0) return cudaSuccess;
+    const int warps = 8;
+    strip_step_kernel<<<(unsigned)((n_tasks + warps - 1) / warps), warps * 32, 0, st>>>(d_cfg, tasks, n_tasks, H,
+                                                                                       j_local, buf, ca, pa);
+    return cudaGetLastError();
+}
+
+
+// ===========================================================================
+// Resident stepper: one thread block holds one whole lattice in shared memory
+// and runs many steps per launch.  Thread t owns the quad column x = 4 (t % G)
+// of band t / G, a band being R consecutive rows; G = Lx / 4 <= 32 lanes span
+// a row, so x neighbours come from warp shuffles of width G.  Each step:
+//   phase 1: every band publishes (sin q t, cos q t) of its first and last
+//            row to shared memory;
+//   phase 2: every band sweeps its rows with a sliding window, taking the
+//            rows above / below the band from phase 1, and updates theta and
+//            v in place (no thread reads another thread's theta).
+// ===========================================================================
+namespace {
+struct SC4 {
+    float s[4], c[4];
+};
+
+__device__ __forceinline__ void sc4_from_theta(const float4& t, float q, SC4& r)
+{
+    sc_of(q, t.x, r.s[0], r.c[0]);
+    sc_of(q, t.y, r.s[1], r.c[1]);
+    sc_of(q, t.z, r.s[2], r.c[2]);
+    sc_of(q, t.w, r.s[3], r.c[3]);
+}
+
+__device__ __forceinline__ void sc4_load(const float2* p, SC4& r)
+{
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 b = *reinterpret_cast<const float4*>(p + 2);
+    r.s[0] = a.x; r.c[0] = a.y; r.s[1] = a.z; r.c[1] = a.w;
+    r.s[2] = b.x; r.c[2] = b.y; r.s[3] = b.z; r.c[3] = b.w;
+}
+
+__device__ __forceinline__ void sc4_store(float2* p, const SC4& r)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(r.s[0], r.c[0], r.s[1], r.c[1]);
+    *reinterpret_cast<float4*>(p + 2) = make_float4(r.s[2], r.c[2], r.s[3], r.c[3]);
+}
+}  // namespace
+
+int resident_threads(int Lx, int Ly)
+{
+    if (Lx % 4 != 0 || Lx > 128) return 0;
+    const int G = Lx / 4;
+    if (32 % G != 0) return 0;
+    for (int nt = 1024; nt >= 32; nt >>= 1) {
+        if (nt % G != 0) continue;
+        const int NB = nt / G;
+        if (NB <= Ly && Ly % NB == 0) return nt;
+    }
+    return 0;
+}
+
+size_t resident_smem_bytes(int Lx, int Ly, int threads)
+{
+    const int G = Lx / 4;
+    const int NB = threads / G;
+    return (size_t)Lx * Ly * 8 + (size_t)2 * NB * Lx * 8 + 64 * sizeof(double) + 16;
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cfgs, const ResidentTask* tasks,
+                                                                int64_t j_local, int n_steps, Buffers buf,
+                                                                const CallArgs* cap)
+{
+    extern __shared__ float4 smem4[];
+    const CallArgs ca = *cap;
+    const ResidentTask task = tasks[blockIdx.x];
+    const DevCfg& cf = cfgs[task.cfg];
+    const int64_t j0 = ca.j_base + j_local;
+    const int64_t j1 = (j0 + n_steps < cf.n_call) ? j0 + n_steps : cf.n_call;
+    if (j0 >= j1) return;
+    const int Lx = cf.Lx, Ly = cf.Ly;
+    const int N = Lx * Ly;
+    const int G = Lx >> 2;
+    const int NT = blockDim.x;
+    const int NB = NT / G, R = Ly / NB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int band = tid / G, lg = tid - band * G;
+    const int x = 4 * lg;
+    const int gb = (lane / G) * G;
+    const int srcL = gb + (lg + G - 1) % G, srcR = gb + (lg + 1) % G;
+
+    float* s_th = reinterpret_cast<float*>(smem4);
+    float* s_om = s_th + N;
+    float2* s_top = reinterpret_cast<float2*>(s_om + N);
+    float2* s_bot = s_top + NB * Lx;
+    double* s_red = reinterpret_cast<double*>(s_bot + NB * Lx);
+    float* s_c = reinterpret_cast<float*>(s_red + 64);
+
+    const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
+    {
+        const bool odd = !ca.fixed_parity && (j0 & 1) != 0;
+        const float* thS = (odd ? buf.thB : buf.thA) + lat_off;
+        const float* omS = (odd ? buf.omB : buf.omA) + lat_off;
+        for (int i = tid; i < N / 4; i += NT) {
+            st4(s_th + 4 * i, ld4(thS + 4 * i));
+            st4(s_om + 4 * i, ld4(omS + 4 * i));
+        }
+    }
+    const uint32_t cfgrep = ((uint32_t)cf.cfg_index << 16) | (uint32_t)task.rep;
+    const int ytop = band * R, ybot = band * R + R - 1;
+    const int band_up = (band + NB - 1) % NB, band_dn = (band + 1) % NB;
+
+    for (int64_t j = j0; j < j1; ++j) {
+        const int64_t k = cf.k_start + j + ca.k_shift;
+        if (tid == 0) *s_c = noise_amp(cf, k);
+        __syncthreads();
+        const StepConst K = step_const(cf, *s_c);
+        const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
+        // phase 1
+        {
+            SC4 a;
+            sc4_from_theta(ld4(s_th + ytop * Lx + x), K.q, a);
+            sc4_store(s_top + band * Lx + x, a);
+            sc4_from_theta(ld4(s_th + ybot * Lx + x), K.q, a);
+            sc4_store(s_bot + band * Lx + x, a);
+        }
+        __syncthreads();
+        // phase 2
+        SC4 prev, cur, nxt;
+        sc4_load(s_bot + band_up * Lx + x, prev);
+        sc4_load(s_top + band * Lx + x, cur);
+        float pm = 0.f, pe = 0.f;
+        for (int r = 0; r < R; ++r) {
+            const int y = ytop + r;
+            if (r == R - 1) sc4_load(s_top + band_dn * Lx + x, nxt);
+            else if (r + 1 == R - 1) sc4_load(s_bot + band * Lx + x, nxt);
+            else sc4_from_theta(ld4(s_th + (y + 1) * Lx + x), K.q, nxt);
+            const float4 th4 = ld4(s_th + y * Lx + x);
+            const float4 v4 = ld4(s_om + y * Lx + x);
+            const float sL = __shfl_sync(kFull, cur.s[3], srcL), cL = __shfl_sync(kFull, cur.c[3], srcL);
+            const float sR = __shfl_sync(kFull, cur.s[0], srcR), cR = __shfl_sync(kFull, cur.c[0], srcR);
+            const uint32_t quad = (uint32_t)((y * Lx + x) >> 2);
+            const float4 cn =
+                gauss4_scaled(philox4x32_10(noise_counter(quad, cfgrep, k, 0u), cf.key0, cf.key1), K.c);
+            float to[4], vo[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const float sl = s == 0 ? sL : cur.s[s - 1];
+                const float cl = s == 0 ? cL : cur.c[s - 1];
+                const float sr = s == 3 ? sR : cur.s[s + 1];
+                const float cr = s == 3 ? cR : cur.c[s + 1];
+                const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
+                const float sy = __fadd_rn(prev.s[s], nxt.s[s]), cy = __fadd_rn(prev.c[s], nxt.c[s]);
+                const float th = f4get(th4, s);
+                const float F = site_force(K, cur.s[s], cur.c[s], sx, cx, sy, cy, sinp_of(K.p, th));
+                const SiteOut so = site_update(K, th, f4get(v4, s), F, f4get(cn, s));
+                to[s] = so.theta;
+                vo[s] = so.v;
+                if (rec) {
+                    const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
+                    pm = fmaf(sigma, cur.s[s], pm);
+                    pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
+                                                   cosp_of(K.p, th)));
+                }
+            }
+            st4(s_th + y * Lx + x, make_float4(to[0], to[1], to[2], to[3]));
+            st4(s_om + y * Lx + x, make_float4(vo[0], vo[1], vo[2], vo[3]));
+            prev = cur;
+            cur = nxt;
+        }
+        if (rec) {
+            const double wm = warp_sum((double)pm), we = warp_sum((double)pe);
+            if (lane == 0) {
+                s_red[warp] = wm;
+                s_red[32 + warp] = we;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double bm = 0.0, be = 0.0;
+                for (int w2 = 0; w2 < NT / 32; ++w2) {
+                    bm += s_red[w2];
+                    be += s_red[32 + w2];
+                }
+                const int64_t b = cf.b_first + task.rep;
+                const int64_t r = (k - cf.rec_first) / ca.record_every;
+                ca.rec_dev[b * ca.rec_stride + r] = make_double2(bm / (double)N, be / (double)N);
+            }
+        }
+    }
+    __syncthreads();
+    {
+        const bool odd = ca.fixed_parity ? true : (j1 & 1) != 0;
+        float* thD = (odd ? buf.thB : buf.thA) + lat_off;
+        float* omD = (odd ? buf.omB : buf.omA) + lat_off;
+        for (int i = tid; i < N / 4; i += NT) {
+            st4(thD + 4 * i, ld4(s_th + 4 * i));
+            st4(omD + 4 * i, ld4(s_om + 4 * i));
+        }
+    }
+}
+
+cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
+                                 int threads, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
+                                 cudaStream_t st)
+{
+    if (n_tasks == 0) return cudaSuccess;
+    const size_t smem = resident_smem_bytes(Lx, Ly, threads);
+    if (threads > 512)
+        resident_step_kernel<1024><<<n_tasks, threads, smem, st>>>(d_cfg, tasks, j_local, n_steps, buf, ca);
+    else
+        resident_step_kernel<512><<<n_tasks, threads, smem, st>>>(d_cfg, tasks, j_local, n_steps, buf, ca);
+    return cudaGetLastError();
+}
+
+// Opt in to the dynamic shared memory of one resident shape (outside any capture).
+cudaError_t prepare_resident(int Lx, int Ly, int threads)
+{
+    const int smem = (int)resident_smem_bytes(Lx, Ly, threads);
+    if (threads > 512)
+        return cudaFuncSetAttribute(resident_step_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(resident_step_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// ===========================================================================
+// Small kernels: chunk counter, moments, diagnostics.
+// ===========================================================================
+__global__ void advance_kernel(CallArgs* ca, int64_t by) { ca->j_base += by; }
+
+cudaError_t launch_advance(CallArgs* ca, int64_t by, cudaStream_t st)
+{
+    advance_kernel<<<1, 1, 0, st>>>(ca, by);
+    return cudaGetLastError();
+}
+
+__global__ void add_kshift_kernel(CallArgs* ca, int64_t by) { ca->k_shift += by; }
+
+cudaError_t launch_add_kshift(CallArgs* ca, int64_t by, cudaStream_t st)
+{
+    add_kshift_kernel<<<1, 1, 0, st>>>(ca, by);
+    return cudaGetLastError();
+}
+
+// Running FP64 moments of one configuration (App. B, Eq.
+// ensemble-average-calculation): sums over replicas and recorded steps
+// k >= t0 of (1, M^2, M^4, E, E^2, |M|), added to moments[c][0..5].  Fixed
+// per-thread strides and a fixed tree make the sums deterministic.
+__global__ void __launch_bounds__(256) moments_kernel(const DevCfg* cfgs, const CallArgs* cap, int64_t t0,
+                                                      double* moments)
+{
+    const DevCfg& cf = cfgs[blockIdx.x];
+    const CallArgs ca = *cap;
+    __shared__ double s_acc[6][256];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int re = ca.record_every;
+    int64_t n_rec = 0;
+    if (re > 0 && cf.n_call > 0 && cf.rec_first < cf.k_start + cf.n_call)
+        n_rec = (cf.k_start + cf.n_call - 1 - cf.rec_first) / re + 1;
+    const int64_t total = n_rec * cf.n_rep;
+    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+        const int64_t rep = i / n_rec, r = i - rep * n_rec;
+        const int64_t k = cf.rec_first + r * re;
+        if (k < t0) continue;
+        const double2 me = ca.rec_dev[(cf.b_first + rep) * ca.rec_stride + r];
+        const double m2 = me.x * me.x;
+        acc[0] += 1.0;
+        acc[1] += m2;
+        acc[2] += m2 * m2;
+        acc[3] += me.y;
+        acc[4] += me.y * me.y;
+        acc[5] += fabs(me.x);
+    }
+    for (int q = 0; q < 6; ++q) s_acc[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 6; ++q) s_acc[q][threadIdx.x] += s_acc[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; ++q) moments[6 * blockIdx.x + q] += s_acc[q][0];
+}
+
+cudaError_t launch_moments(const DevCfg* d_cfg, int n_cfg, const CallArgs* ca, int64_t t0, double* moments,
+                           cudaStream_t st)
+{
+    moments_kernel<<<n_cfg, 256, 0, st>>>(d_cfg, ca, t0, moments);
+    return cudaGetLastError();
+}
+
+__global__ void debug_noise_kernel(uint64_t seed, int cfg, int rep, int64_t k, int tag, int64_t n_quads,
+                                   uint32_t* words, float* gauss)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_quads) return;
+    const uint4 w = philox4x32_10(noise_counter((uint32_t)q, ((uint32_t)cfg << 16) | (uint32_t)rep, k, (uint32_t)tag),
+                                  (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+    if (words) *reinterpret_cast<uint4*>(words + 4 * q) = w;
+    if (gauss) st4(gauss + 4 * q, gauss4_scaled(w, 1.0f));
+}
+
+cudaError_t launch_debug_noise(uint64_t seed, int cfg, int rep, int64_t k, int tag, int64_t n_quads,
+                               uint32_t* words, float* gauss, cudaStream_t st)
+{
+    if (n_quads <= 0) return cudaSuccess;
+    debug_noise_kernel<<<(unsigned)((n_quads + 255) / 256), 256, 0, st>>>(seed, cfg, rep, k, tag, n_quads, words,
+                                                                          gauss);
+    return cudaGetLastError();
+}
+
+__global__ void debug_philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = *reinterpret_cast<const uint4*>(ctr + 4 * i);
+    *reinterpret_cast<uint4*>(out + 4 * i) = philox4x32_10(c, k0, k1);
+}
+
+cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
+                                cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    debug_philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctr, k0, k1, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace xy

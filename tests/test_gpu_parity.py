@@ -1,0 +1,426 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs and identical counter-based noise.
+
+Tolerances (stated by the method's specification): max circular |dtheta| <=
+1e-4 rad after 100 steps; observables, moments and the full-step velocity are
+checked at FP32 accuracy; domain labels bit-exact; adjoint gradients within
+1e-3 relative of the oracle's FP64 adjoint.
+"""
+import ctypes
+import math
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_06412_gb300 import XY_PATH_BATCHED, XY_PATH_PLAIN, XYError, build, debug_noise, debug_philox
+from paper_2409_06412_gb300.lattice import Config, Lattice
+from tests import inputs
+from tests.gpu_helpers import circ_diff, make_pair, split_state, theta_parity
+
+pytestmark = pytest.mark.gpu
+PI = math.pi
+TC = inputs.T_C
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    oracle.build()
+
+
+# ------------------------------------------------------------------ noise
+
+
+def _counters(n, seed=0):
+    rng = np.random.default_rng(seed)
+    c = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    c[:16] = 0
+    c[16:32] = 0xFFFFFFFF
+    c[:32, 0] = np.arange(32)
+    return c
+
+
+def test_philox_bits_match_oracle():
+    total = 0
+    for chunk in range(6):
+        c = _counters(1 << 24, seed=chunk)
+        key = (0x9E3779B9 + chunk, 0xDEADBEEF ^ chunk)
+        g = debug_philox(torch.from_numpy(c.view(np.int32)).cuda(), *key).cpu().numpy().view(np.uint32)
+        o = oracle.philox(c, key)
+        assert np.array_equal(g, o), f"chunk {chunk}: {np.argwhere(g != o)[:4]}"
+        total += c.shape[0]
+    assert total >= 10 ** 8
+
+
+def test_philox_bits_match_curand():
+    """Independent implementation: cuRAND's Philox4x32-10 block function."""
+    src = os.path.join(os.path.dirname(__file__), "cuda", "curand_philox_ref.cu")
+    d = tempfile.mkdtemp()
+    so = os.path.join(d, "curand_ref.so")
+    subprocess.check_call([build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared",
+                           "-Xcompiler", "-fPIC", "-o", so, src])
+    ref = ctypes.CDLL(so)
+    ref.curand_philox_ref.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                      ctypes.c_void_p]
+    c = _counters(1 << 22, seed=99)
+    key = (12345, 678910)
+    ct = torch.from_numpy(c.view(np.int32)).cuda()
+    out = torch.empty_like(ct)
+    torch.cuda.synchronize()
+    assert ref.curand_philox_ref(ct.data_ptr(), key[0], key[1], c.shape[0], out.data_ptr()) == 0
+    mine = debug_philox(ct, *key)
+    torch.cuda.synchronize()
+    assert torch.equal(mine, out)
+    # and the oracle's
+    assert np.array_equal(oracle.philox(c[:65536], key), out[:65536].cpu().numpy().view(np.uint32))
+
+
+def test_gaussians_match_oracle():
+    n_quads = 1 << 18
+    words, g = debug_noise(7, 3, 5, 123456789012, 0, n_quads)
+    o = oracle.gauss(7, 3, 5, 4 * n_quads, 123456789012)
+    g = g.cpu().numpy().astype(np.float64)
+    d = np.abs(g - o)
+    # FP32 Box-Muller with the hardware log2 (absolute error 2^-22 near 1):
+    # the radius error is ~3e-7 / r, so tiny radii carry larger absolute error
+    w = words.cpu().numpy().view(np.uint32)
+    u0 = ((w[:, [0, 0, 2, 2]] >> 9).astype(np.float64) + 0.5) * 2.0 ** -23
+    r = np.sqrt(-2 * np.log(u0)).ravel()
+    tol = 4e-6 * (1 + np.abs(o)) + 4e-7 / r
+    assert np.all(d <= tol), (d / tol).max()
+    assert np.quantile(d, 0.9999) < 2e-5
+
+
+# ------------------------------------------------------------------ init
+
+
+def test_init_modes_match_oracle():
+    cfgs = [Config(Lx=64, Ly=32, n_replicas=3, seed=11, init_mode=0),
+            Config(Lx=128, Ly=8, n_replicas=2, seed=12, init_mode=1)]
+    lat = Lattice(cfgs)
+    torch.cuda.synchronize()
+    th = split_state(lat, lat.theta)
+    for r in range(3):
+        o = oracle.init_theta(64, 32, 0, r, 11, 0)
+        assert circ_diff(th[0][r], o).max() < 1e-6
+    assert np.all(th[1] == np.float32(2 * PI / 5))
+    assert torch.all(lat.omega == 0)
+
+
+# ------------------------------------------------------------------ stepping parity
+
+MIXED = [
+    # (Lx, Ly, n_rep): kernel chosen by the batched path
+    (64, 64, 1),     # resident, 1024 threads, one row per band
+    (128, 128, 2),   # resident, 1024 threads, 4 rows per band
+    (256, 64, 2),    # strip, 2 strips per row, edge columns from global memory
+    (32, 2048, 1),   # strip, 4 row groups per warp (sub-warp shuffles)
+    (128, 256, 1),   # strip, full-row warps
+    (12, 10, 2),     # plain (ragged width)
+    (4, 1, 3),       # plain (degenerate: self-neighbours in y, x wraps onto the quad)
+    (132, 6, 1),     # plain (width not a multiple of 128)
+]
+
+
+def _mixed_specs(T=TC, n_total=10 ** 9, **prm):
+    return [inputs.config(Lx, Ly, n, seed=1 + i, n_total=n_total, knots=([0], [T]), **prm)
+            for i, (Lx, Ly, n) in enumerate(MIXED)]
+
+
+def _mixed_thetas(specs, seed=5):
+    return [inputs.angles(s["n_rep"], s["Lx"], s["Ly"], seed + i) for i, s in enumerate(specs)]
+
+
+@pytest.mark.parametrize("path", [XY_PATH_BATCHED, XY_PATH_PLAIN])
+def test_mixed_batch_parity_100_steps(path):
+    specs = _mixed_specs()
+    thetas = _mixed_thetas(specs)
+    lat, o_th, o_om = make_pair(specs, thetas, path=path)
+    rec = lat.step(100, record_every=10, t0=20)
+    mom, steps = lat.observe()
+    assert list(steps) == [100] * len(specs)
+    step_now = [0] * len(specs)
+    o_rec, o_mom = oracle.run_batch(specs, o_th, o_om, step_now, 100, record_every=10, t0=20)
+    worst, bad = theta_parity(split_state(lat, lat.theta), o_th)
+    assert worst <= 1e-4, (worst, bad[:10])
+    # full-step angular velocity
+    om = split_state(lat, lat.omega_full())
+    for c in range(len(specs)):
+        assert np.abs(om[c] - o_om[c]).max() < 2e-3, (c, np.abs(om[c] - o_om[c]).max())
+    # records (M_k, E_k) at k = 0, 10, ..., 90
+    g = rec.cpu().numpy()
+    b = 0
+    for c, s in enumerate(specs):
+        for r in range(s["n_rep"]):
+            mine = g[b, :10]
+            ref = o_rec[c][r]
+            assert ref.shape == (10, 2)
+            assert np.abs(mine[:, 0] - ref[:, 0]).max() < 2e-5
+            assert np.all(np.abs(mine[:, 1] - ref[:, 1]) < 2e-5 * (1 + np.abs(ref[:, 1])))
+            assert np.isnan(g[b, 10]).all()  # R = n // record_every + 1; the last slot stays untouched
+            b += 1
+    assert np.allclose(mom[:, 0], o_mom[:, 0])
+    assert np.allclose(mom, o_mom, rtol=2e-5, atol=1e-7)
+
+
+def test_plain_and_batched_are_bit_identical():
+    specs = _mixed_specs()
+    thetas = _mixed_thetas(specs, seed=9)
+    a, _, _ = make_pair(specs, thetas, path=XY_PATH_BATCHED)
+    b, _, _ = make_pair(specs, thetas, path=XY_PATH_PLAIN)
+    for lat in (a, b):
+        lat.step(37)
+        lat.step(40)  # odd, then even: parity fix-up both ways, and a graph chunk
+    torch.cuda.synchronize()
+    assert torch.equal(a.theta, b.theta)
+    assert torch.equal(a.omega, b.omega)
+
+
+def test_resume_and_snapshot_are_bit_identical():
+    specs = _mixed_specs(T=3.0)
+    thetas = _mixed_thetas(specs, seed=13)
+    a, _, _ = make_pair(specs, thetas)
+    b, _, _ = make_pair(specs, thetas)
+    a.step(90, record_every=9)
+    b.step(13, record_every=9)
+    snap = b.save()
+    b.step(77, record_every=9)
+    torch.cuda.synchronize()
+    assert torch.equal(a.theta, b.theta) and torch.equal(a.omega, b.omega)
+    # reload the snapshot and redo the second part
+    b.load(snap)
+    b.step(77, record_every=9)
+    torch.cuda.synchronize()
+    assert torch.equal(a.theta, b.theta) and torch.equal(a.omega, b.omega)
+    ma, sa = a.observe()
+    mb, sb = b.observe()
+    assert np.array_equal(sa, sb)
+
+
+def test_uneven_run_lengths_in_one_batch():
+    totals = [30, 77, 100, 5, 0, 64, 99, 1]
+    specs = _mixed_specs()
+    for s, n in zip(specs, totals):
+        s["n_total"] = n
+    thetas = _mixed_thetas(specs, seed=21)
+    lat, o_th, o_om = make_pair(specs, thetas)
+    lat.step(60)
+    lat.step(60)
+    _, steps = lat.observe()
+    assert list(steps) == totals
+    step_now = [0] * len(specs)
+    oracle.run_batch(specs, o_th, o_om, step_now, 120)
+    assert step_now == totals
+    worst, bad = theta_parity(split_state(lat, lat.theta), o_th)
+    assert worst <= 1e-4, (worst, bad[:10])
+
+
+def test_quench_schedule_parity():
+    """Linear ramp eps(t) = -t / tau_Q from 1.5 T_c after an equilibration segment."""
+    tau_q = 40
+    knots = ([20, 20 + int(1.5 * tau_q)], [1.5 * TC, 0.0])
+    specs = [inputs.config(Lx, Ly, n, seed=3 + i, knots=knots, n_total=20 + int(1.5 * tau_q),
+                           eta=[0.1, 1.0, 10.0][i % 3], h=[0.5, 1.0, 2.0][i % 3])
+             for i, (Lx, Ly, n) in enumerate([(64, 64, 2), (256, 64, 1), (12, 10, 1)])]
+    thetas = _mixed_thetas(specs, seed=31)
+    lat, o_th, o_om = make_pair(specs, thetas)
+    rec = lat.step(200, record_every=5)
+    step_now = [0] * 3
+    o_rec, _ = oracle.run_batch(specs, o_th, o_om, step_now, 200, record_every=5)
+    worst, bad = theta_parity(split_state(lat, lat.theta), o_th)
+    assert worst <= 1e-4, (worst, bad[:10])
+    g = rec.cpu().numpy()
+    assert np.abs(g[0, :16, 1] - o_rec[0][0][:, 1]).max() < 1e-4
+
+
+def test_staggered_order_parameter():
+    specs = [inputs.config(64, 64, 2, seed=4, J_par=-10.0, J_perp=-0.1, staggered=1.0)]
+    thetas = _mixed_thetas(specs, seed=41)
+    lat, o_th, o_om = make_pair(specs, thetas)
+    rec = lat.step(50, record_every=5)
+    step_now = [0]
+    o_rec, _ = oracle.run_batch(specs, o_th, o_om, step_now, 50, record_every=5)
+    assert np.abs(rec.cpu().numpy()[:, :10, 0] - np.stack(o_rec[0])[:, :, 0]).max() < 2e-5
+
+
+# ------------------------------------------------------------------ edge cases
+
+
+def test_edge_cases_and_errors():
+    lat = Lattice([Config(Lx=8, Ly=8, n_replicas=1)])
+    th0 = lat.theta.clone()
+    lat.step(0)
+    torch.cuda.synchronize()
+    assert torch.equal(lat.theta, th0)
+    rec = lat.step(3, record_every=10)  # one record at k = 0
+    assert rec.shape == (1, 1, 2) and torch.isfinite(rec).all()
+    with pytest.raises(XYError):
+        lat.set_params(0, dt=-1.0)
+    with pytest.raises(XYError):
+        lat.set_schedule(0, [5, 5], [1.0, 1.0], 10)
+    with pytest.raises(XYError):
+        lat.set_schedule(0, [0], [-1.0], 10)
+    with pytest.raises(XYError):
+        lat.step(-1)
+    with pytest.raises(XYError):
+        Lattice([Config(Lx=6, Ly=4)])
+    with pytest.raises(XYError):
+        lat.label_domains(0, 2)
+    assert lat.kernel_launches() > 0
+
+
+# ------------------------------------------------------------------ domains
+
+
+@pytest.mark.parametrize("case", ["random", "stripes_x", "stripes_y", "checker", "uniform", "spiral", "sparse",
+                                  "tiny"])
+def test_domain_labels_bit_exact(case):
+    L = 96
+    s = {
+        "random": lambda: inputs.random_spins(L, L, 4),
+        "stripes_x": lambda: inputs.stripes(L, L, 3, 0),
+        "stripes_y": lambda: inputs.stripes(L, L, 5, 1),
+        "checker": lambda: inputs.checkerboard(L, L),
+        "uniform": lambda: np.ones((L, L), np.int8),
+        "spiral": lambda: inputs.spiral(L),
+        "sparse": lambda: inputs.random_spins(L, L, 9, p_up=0.08),
+        "tiny": lambda: inputs.random_spins(4, 1, 3),
+    }[case]()
+    Ly, Lx = s.shape
+    th = inputs.spins_to_theta(s).reshape(1, -1)
+    spec = inputs.config(Lx, Ly, 1)
+    lat, _, _ = make_pair([spec], [th])
+    labels, hist, n_sizes = lat.label_domains(hist_cap=Lx * Ly)
+    lab_o, hist_o = oracle.ccl(Lx, Ly, th[0])
+    assert np.array_equal(labels[0].cpu().numpy(), lab_o)
+    k = int(n_sizes[0])
+    assert k == hist_o.shape[0]
+    assert np.array_equal(hist[0, :k].cpu().numpy(), hist_o)
+    assert torch.all(hist[0, k:] == 0)
+
+
+def test_domain_labels_after_quench_and_host_outputs():
+    knots = ([50, 350], [1.5 * TC, 0.0])
+    specs = [inputs.config(256, 128, 3, seed=8, knots=knots, n_total=350)]
+    thetas = _mixed_thetas(specs, seed=51)
+    lat, _, _ = make_pair(specs, thetas)
+    lat.step(350)
+    labels, hist, n_sizes = lat.label_domains(hist_cap=4096)
+    th = split_state(lat, lat.theta)[0].astype(np.float32)
+    for r in range(3):
+        lab_o, hist_o = oracle.ccl(256, 128, th[r])
+        assert np.array_equal(labels[r].cpu().numpy(), lab_o)
+        k = int(n_sizes[r])
+        assert np.array_equal(hist[r, :k].cpu().numpy(), hist_o)
+    # host output buffers through the raw ABI
+    from paper_2409_06412_gb300 import _lib
+    lab_h = np.zeros((3, 256 * 128), np.int32)
+    hist_h = np.zeros((3, 8, 2), np.int64)
+    ns_h = np.zeros(3, np.int64)
+    rc = _lib.load().xy_label_domains(lat._h, 0, 3, lab_h.ctypes.data_as(ctypes.c_void_p),
+                                      hist_h.ctypes.data_as(ctypes.c_void_p), 8,
+                                      ns_h.ctypes.data_as(ctypes.c_void_p))
+    assert np.array_equal(lab_h, labels.cpu().numpy())
+    assert np.array_equal(ns_h, n_sizes.cpu().numpy())
+    if ns_h.max() > 8:
+        assert rc == _lib.XY_EINVAL  # more distinct sizes than hist_cap
+    assert np.array_equal(hist_h[:, :8], hist[:, :8].cpu().numpy())
+
+
+# ------------------------------------------------------------------ adjoint
+
+
+def _oracle_adjoint(specs, o_th, o_om, n, wE, wM):
+    B = sum(s["n_rep"] for s in specs)
+    obj, grads = 0.0, []
+    for c, s in enumerate(specs):
+        g = np.zeros(4)
+        for r in range(s["n_rep"]):
+            ob, gr, _, _ = oracle.adjoint_lattice(s["Lx"], s["Ly"], c, r, s["seed"], s["params"], s["knots"], 0, n,
+                                                  o_th[c][r], o_om[c][r], wE, wM)
+            obj += ob
+            g += gr
+        grads.append(g / (B * n))
+    return obj / (B * n), np.array(grads)
+
+
+@pytest.mark.parametrize("field", ["smooth_p2", "paper_p2.5_lowT"])
+def test_adjoint_matches_oracle(field):
+    if field == "smooth_p2":
+        prm = dict(J_par=2.0, J_perp=0.5, h=1.0, p=2.0, eta=0.8)
+        knots = ([0, 100], [1.0, 0.5])
+    else:
+        prm = dict(h=3.0)
+        knots = ([0], [0.05])
+    specs = [inputs.config(16, 8, 2, seed=3, knots=knots, **prm),
+             inputs.config(128, 4, 1, seed=4, knots=knots, **prm)]
+    if field == "smooth_p2":
+        thetas = _mixed_thetas(specs, seed=61)
+    else:
+        thetas = [np.full((s["n_rep"], s["Lx"] * s["Ly"]), np.float32(2 * PI / 5)) +
+                  0.05 * inputs.velocities(s["n_rep"], s["Lx"], s["Ly"], 62 + i) for i, s in enumerate(specs)]
+        thetas = [t.astype(np.float32) for t in thetas]
+    lat, o_th, o_om = make_pair(specs, thetas)
+    n, K = 100, 30
+    obj, grads = lat.adjoint(n, checkpoint_every=K, w_E=0.7, w_M=0.3)
+    o_obj, o_grads = _oracle_adjoint(specs, o_th, o_om, n, 0.7, 0.3)
+    assert obj == pytest.approx(o_obj, rel=1e-5)
+    scale = np.abs(o_grads).max(axis=1, keepdims=True)
+    assert np.all(np.abs(grads - o_grads) <= 1e-3 * scale), (grads, o_grads)
+    _, steps = lat.observe()
+    assert list(steps) == [n, n]
+
+
+def test_adjoint_autograd_function():
+    from paper_2409_06412_gb300.autograd import bbk_objective
+    specs = [inputs.config(16, 8, 2, seed=3, knots=([0], [1.0]), p=2.0, J_par=2.0, J_perp=0.5)]
+    thetas = _mixed_thetas(specs, seed=71)
+    lat, o_th, o_om = make_pair(specs, thetas)
+    J = torch.tensor([2.0], dtype=torch.float64, requires_grad=True)
+    Jp = torch.tensor([0.5], dtype=torch.float64, requires_grad=True)
+    h = torch.tensor([1.0], dtype=torch.float64, requires_grad=True)
+    eta = torch.tensor([1.0], dtype=torch.float64, requires_grad=True)
+    obj = bbk_objective(lat, J, Jp, h, eta, n=40, checkpoint_every=10, w_E=1.0, w_M=0.0)
+    obj.backward()
+    o_obj, o_grads = _oracle_adjoint(specs, o_th, o_om, 40, 1.0, 0.0)
+    assert float(obj) == pytest.approx(o_obj, rel=1e-5)
+    got = np.array([J.grad.item(), Jp.grad.item(), h.grad.item(), eta.grad.item()])
+    assert np.all(np.abs(got - o_grads[0]) <= 1e-3 * np.abs(o_grads[0]).max())
+
+
+# ------------------------------------------------------------------ full size, sampled
+
+
+def test_static_criticality_full_size_sampled():
+    """The static-criticality batch at full size (L = 128..1024, 32
+    temperatures x 16 replicas each, ordered start) in the benchmark's launch
+    configuration; one sampled lattice per L is replayed by the oracle."""
+    Ls = [128, 256, 512, 1024]
+    temps = np.linspace(0.9, 1.1, 32) * TC
+    cfgs, specs = [], []
+    for L in Ls:
+        for T in temps:
+            cfgs.append(Config(Lx=L, Ly=L, n_replicas=16, seed=1, init_mode=1, knots=((0,), (float(T),)),
+                               n_total=10 ** 5))
+            specs.append(dict(Lx=L, Ly=L, n_rep=16, seed=1, params=dict(inputs.PAPER), knots=([0], [float(T)]),
+                              n_total=10 ** 5))
+    lat = Lattice(cfgs)
+    n = 12
+    rec = lat.step(n, record_every=4)
+    torch.cuda.synchronize()
+    picks = [(0, 3), (40, 7), (77, 15), (127, 0)]  # (config, replica) with L = 128, 256, 512, 1024
+    for c, r in picks:
+        s = specs[c]
+        th = oracle.init_theta(s["Lx"], s["Ly"], c, r, 1, 1)
+        om = np.zeros_like(th)
+        o_rec = oracle.run_lattice(s["Lx"], s["Ly"], c, r, 1, s["params"], s["knots"], 0, n, th, om, 4)
+        b = sum(cc.n_replicas for cc in cfgs[:c]) + r
+        g = lat.lattice_view(lat.theta, b).cpu().numpy().ravel()
+        assert circ_diff(g, th).max() < 1e-5
+        assert np.abs(rec[b, :3, 0].cpu().numpy() - o_rec[:, 0]).max() < 2e-5
+    assert torch.isfinite(rec[:, :3]).all()
