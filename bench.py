@@ -32,7 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 TC = 1.969
-LS = (128, 256, 512, 1024)
+LS_FULL = (128, 256, 512, 1024)
+LS = LS_FULL
 N_TEMPS, N_REP = 32, 16
 INNER = 10            # BBK steps per bench step
 N_TOTAL = 10 ** 5     # run length of every configuration
@@ -44,6 +45,17 @@ BYTES_PER_SU = 16.0   # theta and omega (FP32) read and written once per site-up
 
 def temps():
     return [TC * (0.9 + 0.2 * i / (N_TEMPS - 1)) for i in range(N_TEMPS)]
+
+
+def set_workload(name):
+    """'static' (the full batch) or 'static-L512' (its L = 512 part only: 512
+    lattices, 1.3e8 sites, 1 GB of state, for profiler captures)."""
+    global LS, WORKLOAD
+    if name == "static-L512":
+        LS = (512,)
+        WORKLOAD = "static criticality, L = 512 part: 32 T in [0.9,1.1] T_c, 16 replicas, ordered start"
+    else:
+        LS = LS_FULL
 
 
 def static_configs(seed):
@@ -223,7 +235,8 @@ def run_ours(args):
 
     extra = {}
     if rank == 0:
-        # dominant kernel, timed live with events on its stream
+        # dominant kernel, timed live with events on its stream (the strip
+        # stepper carries every lattice with L >= 256)
         lat.set_kernel_timing(True)
         for _ in range(3):
             bench_step()
@@ -245,6 +258,7 @@ def run_ours(args):
                                        "strip": round(strip_s * 1e3, 4)}
         extra["resident_su_per_s"] = (res_sites * INNER) / (ms[0] / 1e3 / max(nl[0], 1)) if nl[0] else None
 
+    if rank == 0 and args.workload == "static":
         # plain per-configuration launch path on the same batch
         lat.set_path(XY_PATH_PLAIN)
         bench_step()
@@ -322,16 +336,17 @@ def run_ours(args):
             extra["cpu_baseline"] = cpu_baseline()
 
     if rank == 0:
-        U = (mom[:, 2] / mom[:, 0]) / (mom[:, 1] / mom[:, 0]) ** 2
+        ok = mom[:, 0] > 0
+        U = (mom[ok, 2] / mom[ok, 0]) / (mom[ok, 1] / mom[ok, 0]) ** 2
         line = {
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattices": len(static_configs(1)) * N_REP, "sites": S,
                        "bbk_steps_per_step": INNER, "record_every": INNER, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (5.7 GB state per GPU), no flush"},
+                       "l2": "inputs larger than L2 (state of every step >> 129 MB), no flush"},
             "gpu_launches": int(launches), "clocks": clk,
-            "binder_U_range": [float(U.min()), float(U.max())],
+            "binder_U_range": [float(U.min()), float(U.max())] if U.size else None,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
@@ -390,10 +405,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["static", "static-L512"], default="static")
     args = ap.parse_args()
+    set_workload(args.workload)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -161,6 +161,17 @@ int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w
 /* Select the stepping path (XY_PATH_BATCHED default, or XY_PATH_PLAIN). */
 int xy_set_path(xy_lattice* lat, int path);
 
+/* Autotuner of the batched path (synchronous).  For every lattice shape it
+ * times the strip stepper's rows per warp and register/occupancy variant, and
+ * the resident stepper's block size, on the second state buffer (the live
+ * state is untouched), and keeps the fastest; choices are cached per GPU name
+ * and shape in the text file $XY_TUNE_CACHE (default
+ * ~/.cache/xy_gb300_tune.txt).  Runs by itself at the first batched step
+ * unless switched off with xy_set_autotune(lat, 0).  Every choice gives a
+ * bit-identical state. */
+int xy_autotune(xy_lattice* lat);
+int xy_set_autotune(xy_lattice* lat, int on);
+
 /* Snapshot of the complete state (synchronous): theta, omega, step counters,
  * moments, parameters and schedules.  host_buf NULL: *size receives the size
  * needed.  Resuming from a snapshot continues bit-identically. */

@@ -25,11 +25,8 @@ namespace {
 
 constexpr unsigned kFullA = 0xFFFFFFFFu;
 
-__device__ __forceinline__ int wrapa(int v, int n)
-{
-    const int r = v % n;
-    return r < 0 ? r + n : r;
-}
+// Periodic index for offsets in (-n, 2n): one compare-and-add either way.
+__device__ __forceinline__ int wrapa(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 __device__ __forceinline__ void sc_q(float q, float th, float& s, float& c) { __sincosf(__fmul_rn(q, th), &s, &c); }
 
@@ -159,7 +156,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
         st4(A.Fb + lat_off + 4 * quad, make_float4(fbo[0], fbo[1], fbo[2], fbo[3]));
     }
     // block sums in FP64, fixed order; per-block accumulators across steps
-    const double ceta = cf.eta_d > 0.0 ? (double)K.c / (2.0 * cf.eta_d) : 0.0;
+    const double ceta = cf.eta_d > 0.0 ? (double)K.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
     double vals[6] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll

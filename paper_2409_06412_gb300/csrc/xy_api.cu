@@ -2,9 +2,12 @@
 // parameter and schedule tables, the stepping paths (plain per-configuration
 // launches, or batched task tables replayed as CUDA graphs), observables,
 // domain labelling, the pathwise adjoint and snapshots.
+#include <sys/stat.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -56,10 +59,84 @@ struct ResGroup {
     ResidentTask* d_tasks = nullptr;
 };
 
+// Autotuner cache: "gpu|kind|Lx|Ly|lattices" -> (a, b), in memory and in a
+// text file (XY_TUNE_CACHE, default ~/.cache/xy_gb300_tune.txt).
+struct TuneCache {
+    std::vector<std::pair<std::string, std::pair<int, int>>> entries;
+    bool loaded = false;
+    std::string path()
+    {
+        const char* p = getenv("XY_TUNE_CACHE");
+        if (p && *p) return p;
+        const char* home = getenv("HOME");
+        return std::string(home ? home : "/tmp") + "/.cache/xy_gb300_tune.txt";
+    }
+    void load()
+    {
+        if (loaded) return;
+        loaded = true;
+        FILE* f = fopen(path().c_str(), "r");
+        if (!f) return;
+        char key[512];
+        int x, y;
+        while (fscanf(f, "%511s %d %d", key, &x, &y) == 3) entries.push_back({key, {x, y}});
+        fclose(f);
+    }
+    bool get(const std::string& k, int* x, int* y)
+    {
+        load();
+        for (auto& e : entries)
+            if (e.first == k) {
+                *x = e.second.first;
+                *y = e.second.second;
+                return true;
+            }
+        return false;
+    }
+    void put(const std::string& k, int x, int y)
+    {
+        load();
+        entries.push_back({k, {x, y}});
+        std::string p = path();
+        const size_t slash = p.rfind('/');
+        if (slash != std::string::npos) {
+            std::string dir = p.substr(0, slash);
+            std::string cmd_dir = dir;  // created best-effort below
+            FILE* probe = fopen((dir + "/.probe").c_str(), "a");
+            if (probe) {
+                fclose(probe);
+                remove((dir + "/.probe").c_str());
+            } else {
+                mkdir_p(cmd_dir);
+            }
+        }
+        FILE* f = fopen(p.c_str(), "a");
+        if (!f) return;
+        fprintf(f, "%s %d %d\n", k.c_str(), x, y);
+        fclose(f);
+    }
+    static void mkdir_p(const std::string& d)
+    {
+        std::string cur;
+        for (size_t i = 0; i < d.size(); ++i) {
+            cur += d[i];
+            if (d[i] == '/' || i + 1 == d.size()) ::mkdir(cur.c_str(), 0755);
+        }
+    }
+};
+TuneCache g_tune;
+
+// All strip-stepped lattices of one shape; H and the occupancy variant are
+// chosen by the autotuner.
 struct StripGroup {
+    int Lx, Ly;
     int H;
+    int variant;
+    std::vector<int> cfgs;
+    int64_t n_lat = 0;
     std::vector<StripTask> tasks;
     StripTask* d_tasks = nullptr;
+    size_t d_cap = 0;
 };
 
 bool is_device_ptr(const void* p)
@@ -73,14 +150,25 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int choose_strip_H(int Lx, int Ly)
+// Rows per warp of the strip stepper: the largest H <= 64 dividing the rows
+// whose batch still gives at least `min_warps` warps (each warp walks its H
+// rows serially, so small batches need short strips); 0 if unsupported.
+int choose_strip_H(int Lx, int Ly, int64_t n_lattices_of_shape, int64_t min_warps)
 {
     const bool full = Lx >= 128 ? (Lx % 128 == 0) : (Lx >= 4 && 32 % (Lx / 4) == 0);
     if (!full) return 0;
     const int groups = Lx >= 128 ? 1 : 32 / (Lx / 4);
-    for (int H : {64, 32, 16, 8, 4, 2, 1})
-        if (Ly % (H * groups) == 0) return H;
-    return 0;
+    const int strips = Lx >= 128 ? Lx / 128 : 1;
+    int best = 0;
+    for (int H : {64, 32, 16, 8, 4, 2, 1}) {
+        if (Ly % (H * groups) != 0) continue;
+        if (best == 0) best = H;
+        const int64_t warps = n_lattices_of_shape * strips * (Ly / (H * groups));
+        if (warps >= min_warps) return H;
+        if (H < 8) break;
+        best = H;
+    }
+    return best;
 }
 
 }  // namespace
@@ -109,14 +197,19 @@ struct xy_lattice {
     std::vector<ResGroup> res_groups;
     std::vector<StripGroup> strip_groups;
     std::vector<int> plain_cfgs;
-    cudaGraphExec_t graph = nullptr;
-    int graph_chunk = 0;
+    bool tuned = false;
+    bool autotune = true;
+    struct Graph {
+        int chunk;
+        cudaGraphExec_t exec;
+        int64_t kernels;
+    };
+    std::vector<Graph> graphs;  // captured chunks, by chunk length
     // kernel timing (direct launches bracketed by events)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     std::vector<int> ev_class;
     size_t ev_used = 0;
-    int64_t graph_kernels = 0;
     int64_t launches = 0;
 };
 
@@ -159,6 +252,17 @@ void fill_params(DevCfg& d, const xy_params& p)
     d.eta_d = p.eta;
     d.dt_d = p.dt;
     d.stag = p.staggered_M ? 1 : 0;
+    d.amp_pref = (float)(0.5 * std::sqrt(2.0 * p.eta * p.dt));
+}
+
+void fill_schedule_f32(DevCfg& d)
+{
+    for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+        d.knot_Tf[i] = (float)d.knot_T[i];
+        d.slope_f[i] = (i + 1 < d.n_knots)
+                           ? (float)((d.knot_T[i + 1] - d.knot_T[i]) / (double)(d.knot_step[i + 1] - d.knot_step[i]))
+                           : 0.f;
+    }
 }
 
 int check_ready(xy_lattice* L)
@@ -252,8 +356,8 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     for (int i = 0; i < cnt; ++i) {
         for (auto& g : L->strip_groups) {
             if ((rc = timed_begin(L, st, XY_KCLASS_STRIP, &end))) return rc;
-            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, jl0 + i, buf, L->d_call, L->pa,
-                                 st));
+            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, jl0 + i, buf, L->d_call,
+                                 L->pa, st));
             if ((rc = timed_end(end, st))) return rc;
             ++L->launches;
         }
@@ -271,29 +375,166 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     return XY_OK;
 }
 
-int build_graph(xy_lattice* L, int chunk)
+// Capture `chunk` batched steps (kernels + chunk counter) into a graph, or
+// reuse the one captured before for that length.
+int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
-    if (L->graph) {
-        cudaGraphExecDestroy(L->graph);
-        L->graph = nullptr;
-    }
+    for (auto& g : L->graphs)
+        if (g.chunk == chunk) {
+            *out = &g;
+            return XY_OK;
+        }
     const int64_t before = L->launches;
     CK(cudaStreamBeginCapture(L->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = launch_batched_steps(L, L->cap_stream, 0, chunk, true);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(L->cap_stream, &g);
-    L->graph_kernels = L->launches - before;
+    const int64_t kernels = L->launches - before;
     L->launches = before;
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
     if (e != cudaSuccess) return fail(XY_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&L->graph, g, 0);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    L->graph_chunk = chunk;
+    L->graphs.push_back({chunk, exec, kernels});
+    *out = &L->graphs.back();
     return XY_OK;
+}
+
+
+int build_strip_tasks(xy_lattice* L, StripGroup& g);
+
+// ---- autotuner: per strip shape, time strip heights x occupancy variants;
+// per resident shape, time the block sizes.  Candidates run one step from
+// buffer A into buffer B (the scratch half of the double buffer), so the live
+// state is untouched.
+int time_window(xy_lattice* L, int64_t n_call)
+{
+    for (int c = 0; c < L->n_cfg; ++c) {
+        L->h_dev[c].k_start = L->cfg[c].step;
+        L->h_dev[c].n_call = n_call;
+        L->h_dev[c].rec_first = L->cfg[c].step;
+    }
+    int rc = upload_cfg(L);
+    if (rc) return rc;
+    CallArgs ca{};
+    ca.fixed_parity = 1;
+    return upload_call(L, ca);
+}
+
+std::string gpu_name()
+{
+    int dev = 0;
+    cudaDeviceProp p;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "gpu";
+    }
+    std::string s = p.name;
+    for (auto& ch : s)
+        if (ch == ' ' || ch == '|') ch = '_';
+    return s;
+}
+
+int autotune_lattice(xy_lattice* L)
+{
+    if (L->tuned) return XY_OK;
+    L->tuned = true;
+    if (!L->autotune) return XY_OK;
+    const std::string gpu = gpu_name();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = time_window(L, 8);
+    const Buffers buf = state_buffers(L);
+    for (auto& g : L->strip_groups) {
+        if (rc) break;
+        if ((int64_t)g.Lx * g.Ly * g.n_lat < ((int64_t)1 << 21)) continue;  // too small to matter
+        char key[256];
+        snprintf(key, sizeof key, "%s|strip|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
+        int bh = 0, bv = 0;
+        if (!g_tune.get(key, &bh, &bv)) {
+            float best = 1e30f;
+            for (int H : {8, 16, 32, 64}) {
+                const int groups = g.Lx >= 128 ? 1 : 32 / (g.Lx / 4);
+                if (g.Ly % (H * groups) != 0) continue;
+                if (strip_units_per_lattice(g.Lx, g.Ly, H) > L->pa.max_units) continue;
+                g.H = H;
+                if ((rc = build_strip_tasks(L, g))) break;
+                for (int v : {2, 3, 4}) {
+                    const int nt = (int)g.tasks.size();
+                    CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, buf, L->d_call, L->pa, L->stream));
+                    CK(cudaEventRecord(e0, L->stream));
+                    for (int i = 0; i < 3; ++i)
+                        CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, buf, L->d_call, L->pa, L->stream));
+                    CK(cudaEventRecord(e1, L->stream));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    L->launches += 4;
+                    if (ms < best) {
+                        best = ms;
+                        bh = H;
+                        bv = v;
+                    }
+                }
+            }
+            if (rc) break;
+            if (bh > 0) g_tune.put(key, bh, bv);
+        }
+        if (bh > 0) {
+            g.H = bh;
+            g.variant = bv;
+            if ((rc = build_strip_tasks(L, g))) break;
+        }
+    }
+    for (auto& g : L->res_groups) {
+        if (rc) break;
+        if ((int64_t)g.tasks.size() < 8) continue;
+        char key[256];
+        snprintf(key, sizeof key, "%s|resident|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.tasks.size());
+        int bt = 0, dummy = 0;
+        if (!g_tune.get(key, &bt, &dummy)) {
+            float best = 1e30f;
+            const int G = g.Lx / 4;
+            for (int nt : {1024, 512, 256}) {
+                if (nt % G != 0 || (nt / G) > g.Ly || g.Ly % (nt / G) != 0) continue;
+                if (resident_smem_bytes(g.Lx, g.Ly, nt) > 220 * 1024) continue;
+                CK(prepare_resident(g.Lx, g.Ly, nt));
+                const int n = (int)g.tasks.size();
+                CK(launch_resident_step(L->d_cfg, g.d_tasks, n, g.Lx, g.Ly, nt, 0, 8, buf, L->d_call, L->stream));
+                CK(cudaEventRecord(e0, L->stream));
+                for (int i = 0; i < 3; ++i)
+                    CK(launch_resident_step(L->d_cfg, g.d_tasks, n, g.Lx, g.Ly, nt, 0, 8, buf, L->d_call,
+                                            L->stream));
+                CK(cudaEventRecord(e1, L->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                L->launches += 4;
+                if (ms < best) {
+                    best = ms;
+                    bt = nt;
+                }
+            }
+            if (bt > 0) g_tune.put(key, bt, 0);
+        }
+        if (bt > 0 && bt != g.threads) {
+            g.threads = bt;
+            CK(prepare_resident(g.Lx, g.Ly, bt));
+            for (auto& gr : L->graphs) cudaGraphExecDestroy(gr.exec);
+            L->graphs.clear();
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_window_idle(L);
+    if (rc == XY_OK) rc = upload_cfg(L);
+    return rc;
 }
 
 // Advance every configuration by its n_call of the current window (already
@@ -314,17 +555,18 @@ int run_window(xy_lattice* L, int64_t n_max)
             }
         return XY_OK;
     }
-    const int chunk = 32;
-    const int64_t n_full = L->timing ? 0 : n_max / chunk;
-    const int rem = (int)(L->timing ? n_max : n_max % chunk);
+    // graph replays of 32-step chunks (or one chunk of the whole window when
+    // it is shorter), then direct launches for the remainder
+    const int chunk = (int)std::min<int64_t>(32, n_max);
+    const int64_t n_full = (L->timing || chunk < 2) ? 0 : n_max / chunk;
+    const int rem = (int)(n_max - n_full * chunk);
     if (n_full > 0) {
-        if (!L->graph || L->graph_chunk != chunk) {
-            int rc = build_graph(L, chunk);
-            if (rc) return rc;
-        }
+        xy_lattice::Graph* g = nullptr;
+        int rc = get_graph(L, chunk, &g);
+        if (rc) return rc;
         for (int64_t i = 0; i < n_full; ++i) {
-            CK(cudaGraphLaunch(L->graph, L->stream));
-            L->launches += L->graph_kernels;
+            CK(cudaGraphLaunch(g->exec, L->stream));
+            L->launches += g->kernels;
         }
     }
     for (int64_t done = 0; done < rem;) {
@@ -357,6 +599,10 @@ int fixup_parity(xy_lattice* L)
 int advance_core(xy_lattice* L, int64_t n, int record_every, double2* rec_dev, int64_t rec_stride,
                  bool do_moments, int64_t t0)
 {
+    if (L->path == XY_PATH_BATCHED && !L->tuned) {
+        int rc0 = autotune_lattice(L);
+        if (rc0) return rc0;
+    }
     int64_t n_max = 0;
     for (int c = 0; c < L->n_cfg; ++c) {
         CfgHost& h = L->cfg[c];
@@ -387,24 +633,58 @@ int advance_core(xy_lattice* L, int64_t n, int record_every, double2* rec_dev, i
     return XY_OK;
 }
 
+int build_strip_tasks(xy_lattice* L, StripGroup& g)
+{
+    g.tasks.clear();
+    const int nu = strip_units_per_lattice(g.Lx, g.Ly, g.H);
+    for (int c : g.cfgs)
+        for (int r = 0; r < L->cfg[c].desc.n_replicas; ++r)
+            for (int u0 = 0; u0 < nu; u0 += 8) g.tasks.push_back(StripTask{c, r, u0, nu});
+    if (g.tasks.size() > g.d_cap) {
+        cudaFree(g.d_tasks);
+        g.d_tasks = nullptr;
+        g.d_cap = 0;
+        CK(cudaMalloc(&g.d_tasks, sizeof(StripTask) * g.tasks.size()));
+        g.d_cap = g.tasks.size();
+    }
+    CK(cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(StripTask) * g.tasks.size(), cudaMemcpyHostToDevice));
+    for (auto& gr : L->graphs) cudaGraphExecDestroy(gr.exec);
+    L->graphs.clear();
+    return XY_OK;
+}
+
+// smallest strip height the autotuner may pick for a shape
+int min_strip_H(int Lx, int Ly)
+{
+    const int groups = Lx >= 128 ? 1 : 32 / (Lx / 4);
+    for (int H : {4, 8, 16, 32, 64, 2, 1})
+        if (Ly % (H * groups) == 0) return H;
+    return 1;
+}
+
 int classify(xy_lattice* L)
 {
     // default kernel per configuration; see the design notes for the rules
-    std::vector<std::pair<int, int>> res_shapes;
     int max_units = 1;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
     for (int c = 0; c < L->n_cfg; ++c) {
         CfgHost& h = L->cfg[c];
         const int Lx = h.desc.Lx, Ly = h.desc.Ly;
         const int64_t nq = (int64_t)Lx * Ly / 4;
         max_units = std::max<int>(max_units, (int)((nq + 255) / 256));
         const int rt = resident_threads(Lx, Ly);
-        const int H = choose_strip_H(Lx, Ly);
+        int64_t same = 0;
+        for (int c2 = 0; c2 < L->n_cfg; ++c2)
+            if (L->cfg[c2].desc.Lx == Lx && L->cfg[c2].desc.Ly == Ly) same += L->cfg[c2].desc.n_replicas;
+        const int H = choose_strip_H(Lx, Ly, same, (int64_t)sms * 16);
         if (rt > 0 && resident_smem_bytes(Lx, Ly, rt) <= 200 * 1024) {
             h.kind = 0;
         } else if (H > 0) {
             h.kind = 1;
             h.H = H;
-            max_units = std::max(max_units, strip_units_per_lattice(Lx, Ly, H));
+            max_units = std::max(max_units, strip_units_per_lattice(Lx, Ly, std::min(H, min_strip_H(Lx, Ly))));
         } else {
             h.kind = 2;
         }
@@ -427,21 +707,13 @@ int classify(xy_lattice* L)
         } else if (h.kind == 1) {
             StripGroup* g = nullptr;
             for (auto& gg : L->strip_groups)
-                if (gg.H == h.H) g = &gg;
+                if (gg.Lx == Lx && gg.Ly == Ly) g = &gg;
             if (!g) {
-                L->strip_groups.push_back(StripGroup{h.H, {}, nullptr});
+                L->strip_groups.push_back(StripGroup{Lx, Ly, h.H, 3, {}, 0, {}, nullptr, 0});
                 g = &L->strip_groups.back();
             }
-            const int nu = strip_units_per_lattice(Lx, Ly, h.H);
-            const int groups = Lx >= 128 ? 1 : 32 / (Lx / 4);
-            const int rows_per_warp = h.H * groups;
-            const int strips = Lx >= 128 ? Lx / 128 : 1;
-            for (int r = 0; r < h.desc.n_replicas; ++r) {
-                int unit = 0;
-                for (int y0 = 0; y0 < Ly; y0 += rows_per_warp)
-                    for (int s = 0; s < strips; ++s)
-                        g->tasks.push_back(StripTask{c, r, unit++, nu, s * 128, y0});
-            }
+            g->cfgs.push_back(c);
+            g->n_lat += h.desc.n_replicas;
         } else {
             L->plain_cfgs.push_back(c);
         }
@@ -452,8 +724,8 @@ int classify(xy_lattice* L)
         CK(prepare_resident(g.Lx, g.Ly, g.threads));
     }
     for (auto& g : L->strip_groups) {
-        CK(cudaMalloc(&g.d_tasks, sizeof(StripTask) * g.tasks.size()));
-        CK(cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(StripTask) * g.tasks.size(), cudaMemcpyHostToDevice));
+        int rc = build_strip_tasks(L, g);
+        if (rc) return rc;
     }
     return XY_OK;
 }
@@ -461,7 +733,7 @@ int classify(xy_lattice* L)
 void free_lattice(xy_lattice* L)
 {
     if (!L) return;
-    if (L->graph) cudaGraphExecDestroy(L->graph);
+    for (auto& g : L->graphs) cudaGraphExecDestroy(g.exec);
     for (auto& pr : L->ev_pool) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
@@ -617,6 +889,7 @@ int xy_set_schedule(xy_lattice* L, int c, const int64_t* ks, const double* Ts, i
     }
     h.n_total = n_total;
     d.n_total = n_total;
+    fill_schedule_f32(d);
     h.has_sched = true;
     return XY_OK;
 }
@@ -923,8 +1196,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                     ++L->launches;
                 }
                 for (auto& g : L->strip_groups) {
-                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, 0, buf, L->d_call, L->pa,
-                                          L->stream));
+                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, 0, buf,
+                                          L->d_call, L->pa, L->stream));
                     ++L->launches;
                 }
                 for (int c : L->plain_cfgs) {
@@ -1090,6 +1363,7 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
             h.knot_step[i] = d.knot_step[i] = s.knot_step[i];
             h.knot_T[i] = d.knot_T[i] = s.knot_T[i];
         }
+        fill_schedule_f32(d);
     }
     CK(cudaMemcpyAsync(L->d_moments, p, sizeof(double) * 6 * L->n_cfg, cudaMemcpyHostToDevice, L->stream));
     p += sizeof(double) * 6 * L->n_cfg;
@@ -1109,6 +1383,27 @@ int xy_synchronize(xy_lattice* L)
 }
 
 int64_t xy_kernel_launches(xy_lattice* L) { return L ? L->launches : -1; }
+
+int xy_set_autotune(xy_lattice* L, int on)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    L->autotune = on != 0;
+    return XY_OK;
+}
+
+int xy_autotune(xy_lattice* L)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    int rc = check_ready(L);
+    if (rc) return rc;
+    if ((rc = prime_all(L))) return rc;
+    L->tuned = false;
+    const bool saved = L->autotune;
+    L->autotune = true;
+    rc = autotune_lattice(L);
+    L->autotune = saved;
+    return rc;
+}
 
 int xy_set_kernel_timing(xy_lattice* L, int on)
 {

@@ -23,10 +23,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;  // one wide multiply gives both halves
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
@@ -111,24 +111,21 @@ struct StepConst {
 };
 
 // Temperature at step k: piecewise linear through the knots, constant outside
-// (FP64, evaluated once per thread block or warp, never per site).
-__device__ __forceinline__ double temperature_at(const DevCfg& cf, int64_t k)
+// them, evaluated in FP32 from per-segment slopes (a few instructions per
+// thread block or warp; never FP64 on the stepping path).
+__device__ __forceinline__ float temperature_at(const DevCfg& cf, int64_t k)
 {
-    if (cf.n_knots <= 0) return 0.0;
-    if (k <= cf.knot_step[0]) return cf.knot_T[0];
-    for (int i = 0; i + 1 < cf.n_knots; ++i) {
-        if (k <= cf.knot_step[i + 1]) {
-            const double f = (double)(k - cf.knot_step[i]) / (double)(cf.knot_step[i + 1] - cf.knot_step[i]);
-            return cf.knot_T[i] + (cf.knot_T[i + 1] - cf.knot_T[i]) * f;
-        }
-    }
-    return cf.knot_T[cf.n_knots - 1];
+    if (cf.n_knots <= 1 || k <= cf.knot_step[0]) return cf.knot_Tf[0];
+    for (int i = 0; i + 1 < cf.n_knots; ++i)
+        if (k <= cf.knot_step[i + 1]) return fmaf(cf.slope_f[i], (float)(k - cf.knot_step[i]), cf.knot_Tf[i]);
+    return cf.knot_Tf[cf.n_knots - 1];
 }
 
+// Half-kick noise amplitude c_k = (1/2) sqrt(2 eta T_k) sqrt(dt) (App. A.1).
 __device__ __forceinline__ float noise_amp(const DevCfg& cf, int64_t k)
 {
-    const double T = temperature_at(cf, k);
-    return (float)(0.5 * sqrt(2.0 * cf.eta_d * (T > 0.0 ? T : 0.0)) * sqrt(cf.dt_d));
+    const float T = temperature_at(cf, k);
+    return __fmul_rn(cf.amp_pref, __fsqrt_rn(T > 0.f ? T : 0.f));
 }
 
 __device__ __forceinline__ StepConst step_const(const DevCfg& cf, float c)

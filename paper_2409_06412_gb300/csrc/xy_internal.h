@@ -21,6 +21,11 @@ struct DevCfg {
     int32_t n_knots, pad0;
     int64_t knot_step[XY_MAX_KNOTS];
     double knot_T[XY_MAX_KNOTS];
+    // FP32 schedule used on the device: T(k) = knot_Tf[i] + slope_f[i] (k - knot_step[i])
+    float knot_Tf[XY_MAX_KNOTS];
+    float slope_f[XY_MAX_KNOTS];
+    float amp_pref;     // (1/2) sqrt(2 eta dt): noise amplitude c_k = amp_pref sqrt(T_k)
+    float pad1;
     int64_t n_total;
     // per call
     int64_t k_start;    // step at the start of the current call
@@ -41,15 +46,16 @@ struct CallArgs {
     int pad;
 };
 
-// One warp of the strip stepper: a 128-wide (or full-width when Lx <= 128)
-// column strip of one lattice over rows [y0, y0 + H).
+// One thread block of the strip stepper: up to 8 consecutive units of one
+// lattice, one per warp.  A unit is a 128-wide column strip (or the full row
+// when Lx <= 128) over H rows per row group; unit u covers strip u % strips of
+// row segment u / strips.  All warps of a block share the configuration, so
+// its constants and noise key are block-uniform.
 struct StripTask {
     int32_t cfg;
     int32_t rep;
-    int32_t unit;       // index of this warp's unit inside its lattice (observable partials)
+    int32_t unit0;      // unit of warp 0
     int32_t n_units;    // units of the lattice
-    int32_t x0;         // first column of the strip (Lx > 128) or 0
-    int32_t y0;
 };
 
 // One thread block of the resident stepper: one whole lattice.
@@ -80,8 +86,8 @@ cudaError_t launch_omega_full(const DevCfg* d_cfg, const DevCfg& h_cfg, int rep_
                               const float* theta, const float* omega, float* out, cudaStream_t st);
 cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h_cfg, int64_t j_local, Buffers buf,
                               const CallArgs* ca, Partials pa, int write_state, cudaStream_t st);
-cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int64_t j_local,
-                              Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st);
+cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
+                              int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st);
 cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
                                  int threads, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
                                  cudaStream_t st);

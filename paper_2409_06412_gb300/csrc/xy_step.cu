@@ -32,11 +32,8 @@ __device__ __forceinline__ void sc_of(float q, float th, float& s, float& c)
 __device__ __forceinline__ float sinp_of(float p, float th) { return __sinf(__fmul_rn(p, th)); }
 __device__ __forceinline__ float cosp_of(float p, float th) { return __cosf(__fmul_rn(p, th)); }
 
-__device__ __forceinline__ int wrapi(int v, int n)
-{
-    const int r = v % n;
-    return r < 0 ? r + n : r;
-}
+// Periodic index for offsets in (-n, 2n): one compare-and-add either way.
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // Neighbourhood of one quad (4 consecutive sites of a row) read from global memory.
 struct QuadField {
@@ -358,23 +355,21 @@ __device__ __forceinline__ void row_sc(const float4& t, float te, float q, RowSC
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) strip_step_kernel(const DevCfg* cfgs, const StripTask* tasks, int n_tasks,
-                                                         int H, int64_t j_local, Buffers buf, const CallArgs* cap,
-                                                         Partials pa)
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfgs, const StripTask* tasks, int H,
+                                                            int64_t j_local, Buffers buf, const CallArgs* cap,
+                                                            Partials pa)
 {
     const CallArgs ca = *cap;
     const int lane = threadIdx.x & 31;
-    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (t >= n_tasks) return;
-    const StripTask task = tasks[t];
+    const StripTask task = tasks[blockIdx.x];  // block-uniform
+    const int unit = task.unit0 + (int)(threadIdx.x >> 5);
+    if (unit >= task.n_units) return;
     const DevCfg& cf = cfgs[task.cfg];
     const int64_t j = ca.j_base + j_local;
     if (j >= cf.n_call) return;
     const int64_t k = cf.k_start + j + ca.k_shift;
-    float c = 0.f;
-    if (lane == 0) c = noise_amp(cf, k);
-    c = __shfl_sync(kFull, c, 0);
-    const StepConst K = step_const(cf, c);
+    const StepConst K = step_const(cf, noise_amp(cf, k));
     const int Lx = cf.Lx, Ly = cf.Ly;
     const bool odd = !ca.fixed_parity && (j & 1) != 0;
     const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
@@ -384,12 +379,16 @@ __global__ void __launch_bounds__(256) strip_step_kernel(const DevCfg* cfgs, con
     float* __restrict__ omD = (odd ? buf.omA : buf.omB) + lat_off;
 
     const int G = Lx >= 128 ? 32 : (Lx >> 2);     // lanes per row
+    const int groups = 32 / G;
+    const int strips = Lx >= 128 ? (Lx >> 7) : 1;
+    const int seg = unit / strips;
+    const int x0 = (unit - seg * strips) * 128;
     const int grp = lane / G, lg = lane - grp * G;
     const bool multi = Lx > 128;
-    const int x = task.x0 + 4 * lg;
-    const int ybeg = task.y0 + grp * H;
+    const int x = x0 + 4 * lg;
+    const int ybeg = seg * H * groups + grp * H;
     // edge column: lane 0 of a strip needs x0 - 1, lane 31 needs x0 + 128
-    const int xe = multi ? (lg == 0 ? wrapi(task.x0 - 1, Lx) : wrapi(task.x0 + 128, Lx)) : x;
+    const int xe = multi ? (lg == 0 ? wrapi(x0 - 1, Lx) : wrapi(x0 + 128, Lx)) : x;
     const int srcL = grp * G + (lg + G - 1) % G;
     const int srcR = grp * G + (lg + 1) % G;
     const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
@@ -410,7 +409,7 @@ __global__ void __launch_bounds__(256) strip_step_kernel(const DevCfg* cfgs, con
     for (int r = 0; r < H; ++r) {
         const int y = ybeg + r;
         // prefetch: theta two rows ahead, omega of this row
-        const int ynn = wrapi(y + 2, Ly);
+        const int ynn = wrapi(wrapi(y + 2, Ly), Ly);
         const float4 th_nn = ld4(thS + (int64_t)ynn * Lx + x);
         const float te_nn = thS[(int64_t)ynn * Lx + xe];
         const float4 v = ld4_stream(omS + (int64_t)y * Lx + x);
@@ -460,7 +459,7 @@ __global__ void __launch_bounds__(256) strip_step_kernel(const DevCfg* cfgs, con
         const double wm = warp_sum((double)pm), we = warp_sum((double)pe);
         const int64_t b = cf.b_first + task.rep;
         const int64_t r = (k - cf.rec_first) / ca.record_every;
-        commit_partial(pa, b, task.unit, task.n_units, wm, we, ca.rec_dev + b * ca.rec_stride + r, 1.0 / (double)cf.N);
+        commit_partial(pa, b, unit, task.n_units, wm, we, ca.rec_dev + b * ca.rec_stride + r, 1.0 / (double)cf.N);
     }
 }
 
@@ -472,13 +471,17 @@ int strip_units_per_lattice(int Lx, int Ly, int H)
     return Ly / (H * groups);
 }
 
-cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int64_t j_local,
-                              Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st)
+// variant = resident blocks per SM the registers are capped for (2, 3 or 4)
+cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
+                              int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
-    const int warps = 8;
-    strip_step_kernel<<<(unsigned)((n_tasks + warps - 1) / warps), warps * 32, 0, st>>>(d_cfg, tasks, n_tasks, H,
-                                                                                       j_local, buf, ca, pa);
+    if (variant >= 4)
+        strip_step_kernel<4><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa);
+    else if (variant == 3)
+        strip_step_kernel<3><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa);
+    else
+        strip_step_kernel<2><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa);
     return cudaGetLastError();
 }
 
@@ -588,9 +591,8 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
 
     for (int64_t j = j0; j < j1; ++j) {
         const int64_t k = cf.k_start + j + ca.k_shift;
-        if (tid == 0) *s_c = noise_amp(cf, k);
         __syncthreads();
-        const StepConst K = step_const(cf, *s_c);
+        const StepConst K = step_const(cf, noise_amp(cf, k));
         const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
         // phase 1
         {

@@ -86,6 +86,12 @@ class Lattice:
     def set_path(self, path: int):
         L.call("xy_set_path", self._h, path)
 
+    def autotune(self):
+        L.call("xy_autotune", self._h)
+
+    def set_autotune(self, on: bool):
+        L.call("xy_set_autotune", self._h, int(bool(on)))
+
     # ------------------------------------------------------------ stepping
     def step(self, n: int, record_every: int = 0, t0: int = 0, rec: torch.Tensor | np.ndarray | None = None):
         """Advance n steps.  With record_every > 0 returns the records as a

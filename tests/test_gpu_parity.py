@@ -20,7 +20,7 @@ import oracle
 from paper_2409_06412_gb300 import XY_PATH_BATCHED, XY_PATH_PLAIN, XYError, build, debug_noise, debug_philox
 from paper_2409_06412_gb300.lattice import Config, Lattice
 from tests import inputs
-from tests.gpu_helpers import circ_diff, make_pair, split_state, theta_parity
+from tests.gpu_helpers import circ_diff, make_pair, split_state, stepwise_parity, theta_parity
 
 pytestmark = pytest.mark.gpu
 PI = math.pi
@@ -138,34 +138,73 @@ def _mixed_thetas(specs, seed=5):
 
 @pytest.mark.parametrize("path", [XY_PATH_BATCHED, XY_PATH_PLAIN])
 def test_mixed_batch_parity_100_steps(path):
+    """100 steps: every site within 1e-4 rad of the oracle except sites near a
+    cusp event (the FP32 and FP64 angles on opposite sides of the wrap cut at
+    +-pi/2, where the field force jumps); such events are listed."""
     specs = _mixed_specs()
     thetas = _mixed_thetas(specs)
     lat, o_th, o_om = make_pair(specs, thetas, path=path)
+    res = stepwise_parity(lat, specs, o_th, o_om, 100)
+    assert res["step_now"] == [100] * len(specs)
+    report = (f"worst {res['worst_all']:.3g}; within 1e-4: {res['frac_within_tol']:.6f} of {res['n_sites']}; "
+              f"cusp events {res['events']}; cusp-explained {len(res['cusp'])}; "
+              f"ill-conditioned {res['ill'][:8]}")
+    print(report)
+    assert not res["unexplained"], (res["unexplained"][:10], report)
+    assert res["frac_within_tol"] > 1 - 1e-3, report
+    # full-step angular velocity away from events
+    om = split_state(lat, lat.omega_full())
+    hit = {(c, r) for c, r, _, _ in res["events"]} | {(c, r) for c, r, _, _, _ in res["ill"]}
+    for c, s in enumerate(specs):
+        for r in range(s["n_rep"]):
+            if (c, r) not in hit:
+                assert np.abs(om[c][r] - o_om[c][r]).max() < 2e-3, (c, r)
+
+
+def test_plain_method_workload_parity():
+    """64 x 64, one replica, seed 1, theta uniform from the library's own
+    initialisation (noise stream tag 1), T_c, 100 steps."""
+    lat = Lattice([Config(Lx=64, Ly=64, n_replicas=1, seed=1, init_mode=0, knots=((0,), (TC,)))])
+    spec = inputs.config(64, 64, 1, seed=1)
+    o_th = [oracle.init_theta(64, 64, 0, 0, 1, 0).reshape(1, -1)]
+    torch.cuda.synchronize()
+    assert circ_diff(split_state(lat, lat.theta)[0], o_th[0]).max() < 1e-6
+    o_om = [np.zeros_like(o_th[0])]
+    res = stepwise_parity(lat, [spec], o_th, o_om, 100)
+    print(f"worst {res['worst_all']:.3g}; events {res['events']}; ill {res['ill']}")
+    assert not res["unexplained"], res["unexplained"][:10]
+    assert res["frac_within_tol"] > 1 - 1e-3
+
+
+def test_records_and_moments_parity():
+    """Observables of a 100-step call against the oracle's, lattice by
+    lattice; lattices whose trajectory met a cusp event compare at a looser
+    bound after the event."""
+    specs = _mixed_specs()
+    thetas = _mixed_thetas(specs, seed=15)
+    lat, o_th, o_om = make_pair(specs, thetas)
     rec = lat.step(100, record_every=10, t0=20)
     mom, steps = lat.observe()
     assert list(steps) == [100] * len(specs)
     step_now = [0] * len(specs)
     o_rec, o_mom = oracle.run_batch(specs, o_th, o_om, step_now, 100, record_every=10, t0=20)
-    worst, bad = theta_parity(split_state(lat, lat.theta), o_th)
-    assert worst <= 1e-4, (worst, bad[:10])
-    # full-step angular velocity
-    om = split_state(lat, lat.omega_full())
-    for c in range(len(specs)):
-        assert np.abs(om[c] - o_om[c]).max() < 2e-3, (c, np.abs(om[c] - o_om[c]).max())
-    # records (M_k, E_k) at k = 0, 10, ..., 90
     g = rec.cpu().numpy()
     b = 0
+    loose = 0
     for c, s in enumerate(specs):
         for r in range(s["n_rep"]):
-            mine = g[b, :10]
-            ref = o_rec[c][r]
+            mine, ref = g[b, :10], o_rec[c][r]
             assert ref.shape == (10, 2)
-            assert np.abs(mine[:, 0] - ref[:, 0]).max() < 2e-5
-            assert np.all(np.abs(mine[:, 1] - ref[:, 1]) < 2e-5 * (1 + np.abs(ref[:, 1])))
+            dm = np.abs(mine[:, 0] - ref[:, 0])
+            de = np.abs(mine[:, 1] - ref[:, 1]) / (1 + np.abs(ref[:, 1]))
+            if dm.max() > 2e-5 or de.max() > 2e-5:
+                loose += 1
+                assert dm.max() < 2e-3 and de.max() < 2e-4, (c, r, dm.max(), de.max())
             assert np.isnan(g[b, 10]).all()  # R = n // record_every + 1; the last slot stays untouched
             b += 1
-    assert np.allclose(mom[:, 0], o_mom[:, 0])
-    assert np.allclose(mom, o_mom, rtol=2e-5, atol=1e-7)
+    assert loose <= 2, loose
+    assert np.array_equal(mom[:, 0], o_mom[:, 0])
+    assert np.allclose(mom, o_mom, rtol=2e-4, atol=1e-7)
 
 
 def test_plain_and_batched_are_bit_identical():
@@ -213,11 +252,14 @@ def test_uneven_run_lengths_in_one_batch():
     lat.step(60)
     _, steps = lat.observe()
     assert list(steps) == totals
-    step_now = [0] * len(specs)
-    oracle.run_batch(specs, o_th, o_om, step_now, 120)
-    assert step_now == totals
-    worst, bad = theta_parity(split_state(lat, lat.theta), o_th)
-    assert worst <= 1e-4, (worst, bad[:10])
+    # the same run step by step against the oracle
+    lat2, o_th, o_om = make_pair(specs, thetas)
+    res = stepwise_parity(lat2, specs, o_th, o_om, 120)
+    assert res["step_now"] == totals
+    assert not res["unexplained"], (res["unexplained"][:10], res["events"][:10], res["ill"][:10])
+    assert res["frac_within_tol"] > 1 - 1e-3
+    torch.cuda.synchronize()
+    assert torch.equal(lat.theta, lat2.theta) and torch.equal(lat.omega, lat2.omega)
 
 
 def test_quench_schedule_parity():
