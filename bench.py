@@ -216,8 +216,10 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         bench_step()
+    torch.cuda.nvtx.range_pop()
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -245,18 +247,22 @@ def run_ours(args):
         strip_sites = N_TEMPS * N_REP * sum(L * L for L in LS if L >= 256)
         res_sites = N_TEMPS * N_REP * sum(L * L for L in LS if L < 256)
         hbm, peak_kind = peaks()
-        strip_s = ms[1] / 1e3 / max(nl[1], 1)
+        # the strip stepper runs one launch per lattice shape per BBK step:
+        # bytes and time summed over its launches give bytes per launch over
+        # the average launch duration
+        n_bbk = 3 * INNER
+        strip_s = ms[1] / 1e3 / n_bbk                      # strip time per BBK step
+        n_shapes = max(1, round(nl[1] / n_bbk))
         achieved = BYTES_PER_SU * strip_sites / strip_s / 1e9
         traffic = ncu_traffic("strip_step_kernel")
         extra["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(achieved / hbm, 4), "peak_kind": f"{peak_kind} copy bandwidth",
                              "kernel": "strip_step_kernel",
-                             "traffic": (round(traffic * strip_sites) if traffic else None),
-                             "algorithmic_bytes_per_launch": int(BYTES_PER_SU * strip_sites),
-                             "launch_ms": round(strip_s * 1e3, 4)}
-        extra["kernel_ms_per_step"] = {"resident": round(ms[0] / max(nl[0], 1) / INNER, 4),
-                                       "strip": round(strip_s * 1e3, 4)}
-        extra["resident_su_per_s"] = (res_sites * INNER) / (ms[0] / 1e3 / max(nl[0], 1)) if nl[0] else None
+                             "traffic": (round(traffic * strip_sites / n_shapes) if traffic else None),
+                             "algorithmic_bytes_per_launch": int(BYTES_PER_SU * strip_sites / n_shapes),
+                             "launch_ms": round(strip_s * 1e3 / n_shapes, 4), "launches_per_bbk_step": n_shapes}
+        extra["kernel_ms_per_bbk_step"] = {"resident": round(ms[0] / n_bbk, 4), "strip": round(strip_s * 1e3, 4)}
+        extra["resident_su_per_s"] = (res_sites * n_bbk) / (ms[0] / 1e3) if nl[0] else None
 
     if rank == 0 and args.workload == "static":
         # plain per-configuration launch path on the same batch

@@ -62,14 +62,20 @@ typedef struct xy_lattice xy_lattice;
 
 /* One configuration: Lx % 4 == 0, Lx >= 4, Ly >= 1, 1 <= n_replicas <= 65535,
  * at most 65536 configurations per object.  seed keys the Philox4x32-10
- * noise; configuration index c and replica r enter its counter, so
- * configurations that share a seed still draw independent noise. */
+ * noise; the configuration id and the replica id enter its counter, so
+ * configurations that share a seed still draw independent noise.
+ * cfg_id = -1 uses the position of the configuration in the array; replica r
+ * of this object has replica id replica0 + r (< 65536).  A run split over
+ * several objects (or GPUs) that keeps the ids reproduces the unsplit run
+ * bit for bit. */
 typedef struct {
     int32_t Lx;
     int32_t Ly;
     int32_t n_replicas;
     int32_t init_mode;
     uint64_t seed;
+    int32_t cfg_id;
+    int32_t replica0;
 } xy_config_desc;
 
 /* Model and integrator parameters of one configuration (Sec. III, App. A.1;

@@ -25,7 +25,8 @@ _vp, _i32, _i64, _u32, _u64, _d, _sz = _c.c_void_p, _c.c_int, _c.c_int64, _c.c_u
 
 class ConfigDesc(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32), ("n_replicas", ctypes.c_int32),
-                ("init_mode", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("init_mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("cfg_id", ctypes.c_int32),
+                ("replica0", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):

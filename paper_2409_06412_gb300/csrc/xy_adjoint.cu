@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
         sc_q(K.q, n.tl, sl, cl);
         sc_q(K.q, n.tr, sr, cr);
         const uint4 w = philox4x32_10(
-            noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep, k, 0u), cf.key0, cf.key1);
+            noise_counter((uint32_t)quad, ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + rep), k, 0u), cf.key0, cf.key1);
         const float4 nz = gauss4_scaled(w, 1.0f);     // n_k (unit Gaussians)
         const float4 cn = gauss4_scaled(w, K.c);      // c_k n_k exactly as in the forward step
         const float4 v = ld4(A.omega + lat_off + 4 * quad);
@@ -219,13 +219,13 @@ __global__ void __launch_bounds__(256) adjoint_phase_b_kernel(const DevCfg* cfgs
 
 cudaError_t launch_adjoint_phase_a(const DevCfg* d_cfg, const DevCfg& h, int block_base, AdjArgs a, cudaStream_t st)
 {
-    adjoint_phase_a_kernel<<<adjoint_blocks(h), 256, 0, st>>>(d_cfg, h.cfg_index, block_base, a);
+    adjoint_phase_a_kernel<<<adjoint_blocks(h), 256, 0, st>>>(d_cfg, h.slot, block_base, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_phase_b(const DevCfg* d_cfg, const DevCfg& h, AdjArgs a, cudaStream_t st)
 {
-    adjoint_phase_b_kernel<<<adjoint_blocks(h), 256, 0, st>>>(d_cfg, h.cfg_index, a);
+    adjoint_phase_b_kernel<<<adjoint_blocks(h), 256, 0, st>>>(d_cfg, h.slot, a);
     return cudaGetLastError();
 }
 

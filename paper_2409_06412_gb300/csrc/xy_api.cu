@@ -779,6 +779,9 @@ int xy_lattice_create(const xy_config_desc* cfg, int n_cfg, float* theta, float*
         if (d.n_replicas < 1 || d.n_replicas > 65535) return fail(XY_EINVAL, "configuration %d: 1..65535 replicas", c);
         if (d.init_mode < 0 || d.init_mode > 2) return fail(XY_EINVAL, "configuration %d: bad init_mode", c);
         if ((int64_t)d.Lx * d.Ly > (int64_t)1 << 30) return fail(XY_EINVAL, "configuration %d: lattice too large", c);
+        if (d.cfg_id < -1 || d.cfg_id > 65535) return fail(XY_EINVAL, "configuration %d: cfg_id must be -1 or 0..65535", c);
+        if (d.replica0 < 0 || (int64_t)d.replica0 + d.n_replicas > 65536)
+            return fail(XY_EINVAL, "configuration %d: replica ids must stay below 65536", c);
         total += (int64_t)d.Lx * d.Ly * d.n_replicas;
         B += d.n_replicas;
     }
@@ -801,7 +804,9 @@ int xy_lattice_create(const xy_config_desc* cfg, int n_cfg, float* theta, float*
         d.Lx = h.desc.Lx;
         d.Ly = h.desc.Ly;
         d.n_rep = h.desc.n_replicas;
-        d.cfg_index = c;
+        d.slot = c;
+        d.noise_cfg = h.desc.cfg_id >= 0 ? h.desc.cfg_id : c;
+        d.rep0 = h.desc.replica0;
         d.offset = off;
         d.N = (int64_t)h.desc.Lx * h.desc.Ly;
         d.key0 = (uint32_t)(h.desc.seed & 0xFFFFFFFFu);
@@ -1341,7 +1346,8 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
         p += sizeof(SnapCfg);
         const xy_config_desc& a = sc[c].desc;
         const xy_config_desc& b = L->cfg[c].desc;
-        if (a.Lx != b.Lx || a.Ly != b.Ly || a.n_replicas != b.n_replicas || a.seed != b.seed)
+        if (a.Lx != b.Lx || a.Ly != b.Ly || a.n_replicas != b.n_replicas || a.seed != b.seed ||
+            a.cfg_id != b.cfg_id || a.replica0 != b.replica0)
             return fail(XY_EINVAL, "snapshot configuration %d does not match", c);
     }
     CK(cudaStreamSynchronize(L->stream));

@@ -9,7 +9,9 @@ namespace xy {
 
 // Per-configuration record in device memory (read by every kernel).
 struct DevCfg {
-    int32_t Lx, Ly, n_rep, cfg_index;
+    int32_t Lx, Ly, n_rep, slot;  // slot: index of this record in the device table
+    int32_t noise_cfg;  // configuration id in the noise counter
+    int32_t rep0;       // replica id of replica 0 in the noise counter
     int64_t offset;     // first site of replica 0 in the state buffers
     int64_t N;          // Lx * Ly
     uint32_t key0, key1;

@@ -131,7 +131,7 @@ __global__ void init_kernel(const DevCfg* cfgs, int c, int mode, float* theta, f
         float4 t;
         if (mode == XY_INIT_UNIFORM) {
             const uint4 w = philox4x32_10(
-                noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep, 0, 1u), cf.key0,
+                noise_counter((uint32_t)quad, ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + rep), 0, 1u), cf.key0,
                 cf.key1);
             const float kTwoPi = 6.28318530717958648f;
             t.x = wrap_angle(__fmul_rn(kTwoPi, uniform01(w.x)));
@@ -154,7 +154,7 @@ cudaError_t launch_init(const DevCfg* d_cfg, const DevCfg& h, int init_mode, flo
     const int64_t nq = h.N / 4 * h.n_rep;
     const int threads = 256;
     const int blocks = (int)((nq + threads - 1) / threads < 65536 ? (nq + threads - 1) / threads : 65536);
-    init_kernel<<<blocks, threads, 0, st>>>(d_cfg, h.cfg_index, init_mode, theta, omega);
+    init_kernel<<<blocks, threads, 0, st>>>(d_cfg, h.slot, init_mode, theta, omega);
     return cudaGetLastError();
 }
 
@@ -183,7 +183,7 @@ __global__ void prime_kernel(const DevCfg* cfgs, int c, float* theta, float* ome
     float* om = omega + cf.offset + (int64_t)rep * cf.N + 4 * quad;
     QuadField f;
     quad_field(lat, cf.Lx, cf.Ly, x, y, K.q, f);
-    const uint4 w = philox4x32_10(noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep,
+    const uint4 w = philox4x32_10(noise_counter((uint32_t)quad, ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + rep),
                                                 cf.k_start, 0u), cf.key0, cf.key1);
     const float4 cn = gauss4_scaled(w, K.c);
     const float4 w0 = ld4(om);
@@ -200,7 +200,7 @@ __global__ void prime_kernel(const DevCfg* cfgs, int c, float* theta, float* ome
 cudaError_t launch_prime(const DevCfg* d_cfg, const DevCfg& h, float* theta, float* omega, cudaStream_t st)
 {
     const int64_t nq = h.N / 4 * h.n_rep;
-    prime_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(d_cfg, h.cfg_index, theta, omega);
+    prime_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(d_cfg, h.slot, theta, omega);
     return cudaGetLastError();
 }
 
@@ -223,7 +223,7 @@ __global__ void omega_full_kernel(const DevCfg* cfgs, int c, int rep_first, int 
     const float* lat = theta + cf.offset + (int64_t)rep * cf.N;
     QuadField f;
     quad_field(lat, cf.Lx, cf.Ly, x, y, K.q, f);
-    const uint4 w = philox4x32_10(noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep,
+    const uint4 w = philox4x32_10(noise_counter((uint32_t)quad, ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + rep),
                                                 cf.k_start, 0u), cf.key0, cf.key1);
     const float4 cn = gauss4_scaled(w, K.c);
     const float4 v = ld4(omega + cf.offset + (int64_t)rep * cf.N + 4 * quad);
@@ -241,7 +241,7 @@ cudaError_t launch_omega_full(const DevCfg* d_cfg, const DevCfg& h, int rep_firs
                               const float* theta, const float* omega, float* out, cudaStream_t st)
 {
     const int64_t nq = h.N / 4 * rep_count;
-    omega_full_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(d_cfg, h.cfg_index, rep_first, rep_count,
+    omega_full_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(d_cfg, h.slot, rep_first, rep_count,
                                                                      theta, omega, out);
     return cudaGetLastError();
 }
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
         QuadField f;
         quad_field(thS, cf.Lx, cf.Ly, x, y, K.q, f);
         const uint4 w = philox4x32_10(
-            noise_counter((uint32_t)quad, ((uint32_t)cf.cfg_index << 16) | (uint32_t)rep, k, 0u), cf.key0, cf.key1);
+            noise_counter((uint32_t)quad, ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + rep), k, 0u), cf.key0, cf.key1);
         const float4 cn = gauss4_scaled(w, K.c);
         const float4 v = ld4(omS + 4 * quad);
         float to[4], vo[4];
@@ -329,7 +329,7 @@ cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h, int64_t j_lo
 {
     const int64_t nq_lat = h.N / 4;
     const int bpl = (int)((nq_lat + 255) / 256);
-    plain_step_kernel<<<(unsigned)(bpl * h.n_rep), 256, 0, st>>>(d_cfg, h.cfg_index, j_local, buf, ca, pa,
+    plain_step_kernel<<<(unsigned)(bpl * h.n_rep), 256, 0, st>>>(d_cfg, h.slot, j_local, buf, ca, pa,
                                                                   write_state);
     return cudaGetLastError();
 }
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     const int srcL = grp * G + (lg + G - 1) % G;
     const int srcR = grp * G + (lg + 1) % G;
     const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
-    const uint32_t cfgrep = ((uint32_t)cf.cfg_index << 16) | (uint32_t)task.rep;
+    const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
 
     RowSC prev, cur, nxt;
     {
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
             st4(s_om + 4 * i, ld4(omS + 4 * i));
         }
     }
-    const uint32_t cfgrep = ((uint32_t)cf.cfg_index << 16) | (uint32_t)task.rep;
+    const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
     const int ytop = band * R, ybot = band * R + R - 1;
     const int band_up = (band + NB - 1) % NB, band_dn = (band + 1) % NB;
 

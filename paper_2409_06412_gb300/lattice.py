@@ -25,6 +25,8 @@ class Config:
     params: dict = field(default_factory=dict)
     knots: tuple = ((0,), (1.969,))
     n_total: int = 10**12
+    cfg_id: int = -1      # configuration id in the noise counter (-1: position in the list)
+    replica0: int = 0     # replica id of replica 0 in the noise counter
 
     @property
     def sites(self) -> int:
@@ -50,7 +52,7 @@ class Lattice:
         assert self.theta.dtype == torch.float32 and self.theta.is_contiguous()
         descs = (L.ConfigDesc * len(self.configs))()
         for i, c in enumerate(self.configs):
-            descs[i] = L.ConfigDesc(c.Lx, c.Ly, c.n_replicas, c.init_mode, c.seed)
+            descs[i] = L.ConfigDesc(c.Lx, c.Ly, c.n_replicas, c.init_mode, c.seed, c.cfg_id, c.replica0)
         handle = ctypes.c_void_p()
         L.call("xy_lattice_create", descs, len(self.configs), _ptr(self.theta), _ptr(self.omega),
                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle))

@@ -72,7 +72,7 @@ def theta_parity(gpu_th, o_th, tol=1e-4):
     return worst, bad
 
 
-def stepwise_parity(lat, specs, o_th, o_om, n_steps, tol=1e-4, reach=(16, 4), factor=10.0, cap=1e-3):
+def stepwise_parity(lat, specs, o_th, o_om, n_steps, tol=1e-4, reach=(16, 4), factor=30.0, cap=1e-3):
     """Step the GPU lattice and the oracle one step at a time and classify the
     final angle differences.
 
@@ -88,7 +88,9 @@ def stepwise_parity(lat, specs, o_th, o_om, n_steps, tol=1e-4, reach=(16, 4), fa
         from the FP64 oracle by `sens` at that site; a site with
         |dtheta| <= factor * sens and <= cap is limited by the conditioning of
         the trajectory (unstable anti-aligned bonds amplify the rounding),
-        not by the kernel.
+        not by the kernel.  The factor covers the ratio of the kernel's
+        per-step arithmetic error (hardware sine/cosine ~3.6e-7, Box-Muller
+        ~1e-6 per Gaussian) to the bare binary32 rounding of the state.
     Everything else is `unexplained` and fails the tests."""
     step_now = [0] * len(specs)
     r_th = [t.astype(np.float32).astype(np.float64) for t in o_th]
