@@ -151,6 +151,34 @@ int xy_omega_full(xy_lattice* lat, int b_first, int b_count, float* out);
 int xy_label_domains(xy_lattice* lat, int b_first, int b_count, int32_t* labels, int64_t* hist,
                      int64_t hist_cap, int64_t* n_sizes);
 
+/* Domain labelling without allocation (synchronous).  The same labels, size
+ * histogram and counts as xy_label_domains, for callers that must not
+ * allocate device memory: services whose memory pool owns every byte of the
+ * GPU and forbids libraries from allocating on their own, loops that cannot
+ * afford an allocation and the device-wide synchronisation of cudaFree, and
+ * jobs running close to the memory limit that must not fail half-way on an
+ * allocation (this working memory is reserved when the library loads).
+ * The paper has no counterpart; this is a property of the library only.
+ *   theta: device float[n_lattices][Ly*Lx] (the layout of the state);
+ *   labels: device int32[n_lattices][Ly*Lx]; hist (nullable): device
+ *   int64[n_lattices][hist_cap][2]; n_sizes (nullable): device
+ *   int64[n_lattices]; cuda_stream: the stream the work runs on.
+ * Working memory is one fixed array inside the library image,
+ * 4 * (2 * XY_STATIC_CCL_MAX_SITES + XY_STATIC_CCL_MAX_LATTICES + 64) bytes
+ * (about 16.3 MB) that every GPU which loads the library holds until the
+ * process exits.  A call with more than XY_STATIC_CCL_MAX_SITES sites or
+ * XY_STATIC_CCL_MAX_LATTICES lattices returns XY_EINVAL without launching
+ * anything.  Every call shares that array and it keeps the previous call's
+ * contents (each call clears what must start at zero), so calls whose work
+ * overlaps on the GPU (other streams, other threads) race: issue them one
+ * after another.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  No call allocates memory (no cudaMalloc or cudaFree). */
+#define XY_STATIC_CCL_MAX_SITES 2097152
+#define XY_STATIC_CCL_MAX_LATTICES 65536
+int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, int32_t* labels, int64_t* hist,
+                            int64_t hist_cap, int64_t* n_sizes, void* cuda_stream);
+
 /* Pathwise adjoint (synchronous).  Runs n BBK steps from the current state
  * (which advances by n) with the noise held fixed and returns
  *   objective = (1 / (B n)) sum_b sum_{k=k0+1}^{k0+n} [w_E E_k + w_M |M_k|]

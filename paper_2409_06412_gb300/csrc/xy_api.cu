@@ -173,6 +173,10 @@ int choose_strip_H(int Lx, int Ly, int64_t n_lattices_of_shape, int64_t min_warp
 
 }  // namespace
 
+namespace xy {
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace xy
+
 struct xy_lattice {
     int n_cfg = 0;
     int64_t B = 0;

@@ -106,6 +106,9 @@ cudaError_t launch_debug_noise(uint64_t seed, int cfg, int rep, int64_t k, int t
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
                                 cudaStream_t st);
 
+// ---- error channel of xy_last_error (xy_api.cu), for the other translation units
+int report_error(int code, const char* msg);
+
 // ---- domains (xy_ccl.cu)
 cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* labels, int32_t* size_scratch,
                        int32_t* count_scratch, int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err,

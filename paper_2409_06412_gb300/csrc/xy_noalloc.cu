@@ -1,0 +1,95 @@
+// xy_noalloc.cu -- domain labelling for callers that must not allocate.
+//
+// xy_label_domains() takes its working memory (component sizes and the size
+// histogram, 8 bytes per site) from cudaMalloc on every call.  Some callers
+// cannot allow that: services that hand every byte of device memory to their
+// own pool and forbid libraries from allocating behind its back, loops where
+// an allocation and the device-wide synchronisation of cudaFree are not
+// acceptable, and jobs near the memory limit that must not fail half-way on
+// an allocation.  xy_label_domains_static() serves them: the caller passes the
+// angles and the output buffers, and the working memory is one fixed array
+// in this file, part of the library image, that every GPU which loads the
+// library holds until the process exits.
+#include <cstdint>
+#include <mutex>
+
+#include "xy_internal.h"
+
+namespace {
+
+// Working memory of one call: component sizes (one int32 per site), the size
+// histogram (one int32 per possible size, per lattice) and an error flag.
+constexpr int64_t kSizeWords = XY_STATIC_CCL_MAX_SITES;
+constexpr int64_t kCountWords = XY_STATIC_CCL_MAX_SITES + XY_STATIC_CCL_MAX_LATTICES;
+constexpr int64_t kScratchWords = kSizeWords + kCountWords + 64;
+
+static __device__ __align__(256) int32_t g_ccl_scratch[kScratchWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int32_t* g_scratch_addr[kMaxDevices] = {};
+
+int fail_static(int code, const char* msg) { return xy::report_error(code, msg); }
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a stand-in, so the address is looked up once per
+// device with that device current.
+int scratch_address(int32_t** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return fail_static(XY_ECUDA, "xy_label_domains_static: no current CUDA device");
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_ccl_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail_static(XY_ECUDA, "xy_label_domains_static: cudaGetSymbolAddress failed");
+        }
+        g_scratch_addr[dev] = static_cast<int32_t*>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return XY_OK;
+}
+
+}  // namespace
+
+extern "C" int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, int32_t* labels,
+                                       int64_t* hist, int64_t hist_cap, int64_t* n_sizes, void* cuda_stream)
+{
+    if (!theta || !labels) return fail_static(XY_EINVAL, "xy_label_domains_static: theta and labels are required");
+    if (Lx < 4 || Lx % 4 != 0 || Ly < 1 || n_lattices < 1)
+        return fail_static(XY_EINVAL, "xy_label_domains_static: need Lx a positive multiple of 4, Ly >= 1, "
+                                      "n_lattices >= 1");
+    if (hist && hist_cap <= 0) return fail_static(XY_EINVAL, "xy_label_domains_static: hist_cap must be > 0");
+    const int64_t N = (int64_t)Lx * Ly;
+    if (n_lattices > XY_STATIC_CCL_MAX_LATTICES || N * n_lattices > XY_STATIC_CCL_MAX_SITES)
+        return fail_static(XY_EINVAL, "xy_label_domains_static: more than XY_STATIC_CCL_MAX_SITES sites or "
+                                      "XY_STATIC_CCL_MAX_LATTICES lattices in one call");
+    int32_t* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    int32_t* sizes = base;
+    int32_t* counts = base + kSizeWords;
+    int* err = reinterpret_cast<int*>(base + kSizeWords + kCountWords);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // the array keeps the previous call's contents: clear what must start at zero
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess && hist) e = cudaMemsetAsync(hist, 0, sizeof(int64_t) * 2 * hist_cap * n_lattices, st);
+    if (e == cudaSuccess)
+        e = xy::launch_ccl(theta, Lx, Ly, n_lattices, labels, sizes, counts, hist, hist ? hist_cap : 0, n_sizes, err,
+                           st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail_static(XY_ECUDA, cudaGetErrorString(e));
+    }
+    if (herr == XY_EINVAL) return fail_static(XY_EINVAL, "xy_label_domains_static: more distinct sizes than hist_cap");
+    if (herr) return fail_static(herr, "xy_label_domains_static: a bounded union loop ran out of iterations");
+    return XY_OK;
+}
