@@ -130,6 +130,7 @@ TuneCache g_tune;
 // chosen by the autotuner.
 struct StripGroup {
     int Lx, Ly;
+    uint64_t seed;  // one noise key per group: the round keys become kernel parameters
     int H;
     int variant;
     std::vector<int> cfgs;
@@ -360,8 +361,8 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     for (int i = 0; i < cnt; ++i) {
         for (auto& g : L->strip_groups) {
             if ((rc = timed_begin(L, st, XY_KCLASS_STRIP, &end))) return rc;
-            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, jl0 + i, buf, L->d_call,
-                                 L->pa, st));
+            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, g.seed, jl0 + i, buf,
+                                 L->d_call, L->pa, st));
             if ((rc = timed_end(end, st))) return rc;
             ++L->launches;
         }
@@ -471,10 +472,12 @@ int autotune_lattice(xy_lattice* L)
                 if ((rc = build_strip_tasks(L, g))) break;
                 for (int v : {2, 3, 4}) {
                     const int nt = (int)g.tasks.size();
-                    CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, buf, L->d_call, L->pa, L->stream));
+                    CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, g.seed, 0, buf, L->d_call, L->pa,
+                                         L->stream));
                     CK(cudaEventRecord(e0, L->stream));
                     for (int i = 0; i < 3; ++i)
-                        CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, buf, L->d_call, L->pa, L->stream));
+                        CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, g.seed, 0, buf, L->d_call, L->pa,
+                                             L->stream));
                     CK(cudaEventRecord(e1, L->stream));
                     CK(cudaEventSynchronize(e1));
                     float ms = 0.f;
@@ -711,9 +714,9 @@ int classify(xy_lattice* L)
         } else if (h.kind == 1) {
             StripGroup* g = nullptr;
             for (auto& gg : L->strip_groups)
-                if (gg.Lx == Lx && gg.Ly == Ly) g = &gg;
+                if (gg.Lx == Lx && gg.Ly == Ly && gg.seed == h.desc.seed) g = &gg;
             if (!g) {
-                L->strip_groups.push_back(StripGroup{Lx, Ly, h.H, 3, {}, 0, {}, nullptr, 0});
+                L->strip_groups.push_back(StripGroup{Lx, Ly, h.desc.seed, h.H, 3, {}, 0, {}, nullptr, 0});
                 g = &L->strip_groups.back();
             }
             g->cfgs.push_back(c);
@@ -1205,8 +1208,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                     ++L->launches;
                 }
                 for (auto& g : L->strip_groups) {
-                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, 0, buf,
-                                          L->d_call, L->pa, L->stream));
+                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, g.seed, 0,
+                                          buf, L->d_call, L->pa, L->stream));
                     ++L->launches;
                 }
                 for (int c : L->plain_cfgs) {

@@ -34,6 +34,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same function with the ten round keys precomputed (kernel parameters,
+// so every XOR takes its key from the constant bank).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const PhiloxKeys& K)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+        c = make_uint4(hi1 ^ c.y ^ K.k0[r], lo1, hi0 ^ c.w ^ K.k1[r], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 noise_counter(uint32_t quad, uint32_t cfg_rep, int64_t k, uint32_t tag)
 {
     const uint64_t ku = (uint64_t)k;

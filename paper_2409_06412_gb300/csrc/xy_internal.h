@@ -66,6 +66,26 @@ struct ResidentTask {
     int32_t rep;
 };
 
+// Round keys of Philox4x32-10 for one seed: round r uses
+// (k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85).
+struct PhiloxKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+inline PhiloxKeys philox_round_keys(uint64_t seed)
+{
+    PhiloxKeys k;
+    uint32_t a = (uint32_t)(seed & 0xFFFFFFFFu), b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k.k0[r] = a;
+        k.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return k;
+}
+
 struct Buffers {
     float* thA;
     float* omA;
@@ -89,7 +109,8 @@ cudaError_t launch_omega_full(const DevCfg* d_cfg, const DevCfg& h_cfg, int rep_
 cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h_cfg, int64_t j_local, Buffers buf,
                               const CallArgs* ca, Partials pa, int write_state, cudaStream_t st);
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
-                              int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st);
+                              uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
+                              cudaStream_t st);
 cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
                                  int threads, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
                                  cudaStream_t st);

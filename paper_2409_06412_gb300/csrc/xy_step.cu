@@ -339,26 +339,124 @@ cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h, int64_t j_lo
 // ===========================================================================
 namespace {
 
-struct RowSC {
+// One row of a strip as seen by one lane: the raw angles of its quad and of
+// its edge column, and their (sin q t, cos q t).
+struct RowBuf {
+    float4 th;
+    float te;
     float s[4], c[4];
-    float se, ce;  // edge neighbour outside the strip (lane 0: left, lane 31: right)
 };
 
-__device__ __forceinline__ void row_sc(const float4& t, float te, float q, RowSC& r)
+__device__ __forceinline__ void rowbuf_sc(float q, RowBuf& r)
 {
-    sc_of(q, t.x, r.s[0], r.c[0]);
-    sc_of(q, t.y, r.s[1], r.c[1]);
-    sc_of(q, t.z, r.s[2], r.c[2]);
-    sc_of(q, t.w, r.s[3], r.c[3]);
-    sc_of(q, te, r.se, r.ce);
+    sc_of(q, r.th.x, r.s[0], r.c[0]);
+    sc_of(q, r.th.y, r.s[1], r.c[1]);
+    sc_of(q, r.th.z, r.s[2], r.c[2]);
+    sc_of(q, r.th.w, r.s[3], r.c[3]);
+}
+
+// Everything one lane needs to update its quad in every row of its unit.
+struct StripCtx {
+    const float* __restrict__ thS;
+    const float* __restrict__ omS;
+    float* __restrict__ thD;
+    float* __restrict__ omD;
+    int Lx, Ly, x, xe, srcL, srcR, lg;
+    bool multi, rec;
+    uint32_t cfgrep;
+    int64_t k;
+    StepConst K;
+    float pm, pe;
+};
+
+// All rows of the unit, one row per iteration with a sliding window of three
+// rows of (sin q t, cos q t); the raw angles run two rows ahead.  Row
+// pointers advance by Lx per row and wrap at the lattice end.
+template <bool REC>
+__device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const PhiloxKeys& keys, int ybeg, int H)
+{
+    const int64_t Lx = X.Lx;
+    const int64_t Nsites = Lx * X.Ly;
+    int yp = ybeg - 1;
+    if (yp < 0) yp += X.Ly;
+    int yn = ybeg + 1;
+    if (yn >= X.Ly) yn -= X.Ly;
+    int ynn = yn + 1;
+    if (ynn >= X.Ly) ynn -= X.Ly;
+    RowBuf P, C, N;
+    P.th = ld4(X.thS + yp * Lx + X.x);
+    C.th = ld4(X.thS + (int64_t)ybeg * Lx + X.x);
+    C.te = X.thS[(int64_t)ybeg * Lx + X.xe];
+    N.th = ld4(X.thS + yn * Lx + X.x);
+    N.te = X.thS[yn * Lx + X.xe];
+    rowbuf_sc(X.K.q, P);
+    rowbuf_sc(X.K.q, C);
+    const float* p_nn = X.thS + ynn * Lx;           // row y + 2
+    const float* p_v = X.omS + (int64_t)ybeg * Lx;   // row y
+    float* p_to = X.thD + (int64_t)ybeg * Lx;
+    float* p_vo = X.omD + (int64_t)ybeg * Lx;
+    uint32_t quad = (uint32_t)(((int64_t)ybeg * Lx + X.x) >> 2);
+    const uint32_t dquad = (uint32_t)(Lx >> 2);
+    for (int r = 0; r < H; ++r) {
+        const int y = ybeg + r;
+        const float4 th_nn = ld4(p_nn + X.x);
+        const float te_nn = p_nn[X.xe];
+        const float4 v = ld4_stream(p_v + X.x);
+        rowbuf_sc(X.K.q, N);
+        float sL = __shfl_sync(kFull, C.s[3], X.srcL);
+        float cL = __shfl_sync(kFull, C.c[3], X.srcL);
+        float sR = __shfl_sync(kFull, C.s[0], X.srcR);
+        float cR = __shfl_sync(kFull, C.c[0], X.srcR);
+        if (X.multi) {
+            // the strip's edge column (lane 0: x0 - 1, lane 31: x0 + 128)
+            float se, ce;
+            sc_of(X.K.q, C.te, se, ce);
+            if (X.lg == 0) { sL = se; cL = ce; }
+            if (X.lg == 31) { sR = se; cR = ce; }
+        }
+        const float4 cn = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, X.cfgrep, X.k, 0u), keys), X.K.c);
+        float to[4], vo[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float sl = s == 0 ? sL : C.s[s - 1];
+            const float cl = s == 0 ? cL : C.c[s - 1];
+            const float sr = s == 3 ? sR : C.s[s + 1];
+            const float cr = s == 3 ? cR : C.c[s + 1];
+            const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
+            const float sy = __fadd_rn(P.s[s], N.s[s]), cy = __fadd_rn(P.c[s], N.c[s]);
+            const float th = f4get(C.th, s);
+            const float F = site_force(X.K, C.s[s], C.c[s], sx, cx, sy, cy, sinp_of(X.K.p, th));
+            const SiteOut so = site_update(X.K, th, f4get(v, s), F, f4get(cn, s));
+            to[s] = so.theta;
+            vo[s] = so.v;
+            if (REC) {
+                const float sigma = (cf.stag && ((X.x + s + y) & 1)) ? -1.f : 1.f;
+                X.pm = fmaf(sigma, C.s[s], X.pm);
+                X.pe = __fadd_rn(X.pe, site_energy(cf, so.omega, C.s[s], C.c[s], sr, cr, N.s[s], N.c[s],
+                                                   cosp_of(X.K.p, th)));
+            }
+        }
+        st4_stream(p_to + X.x, make_float4(to[0], to[1], to[2], to[3]));
+        st4_stream(p_vo + X.x, make_float4(vo[0], vo[1], vo[2], vo[3]));
+        P = C;
+        C = N;
+        N.th = th_nn;
+        N.te = te_nn;
+        p_v += Lx;
+        p_to += Lx;
+        p_vo += Lx;
+        quad += dquad;
+        p_nn += Lx;
+        if (p_nn >= X.thS + Nsites) p_nn -= Nsites;
+    }
 }
 
 }  // namespace
 
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfgs, const StripTask* tasks, int H,
-                                                            int64_t j_local, Buffers buf, const CallArgs* cap,
-                                                            Partials pa)
+                                                               int64_t j_local, Buffers buf, const CallArgs* cap,
+                                                               Partials pa, PhiloxKeys keys)
 {
     const CallArgs ca = *cap;
     const int lane = threadIdx.x & 31;
@@ -368,98 +466,44 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     const DevCfg& cf = cfgs[task.cfg];
     const int64_t j = ca.j_base + j_local;
     if (j >= cf.n_call) return;
-    const int64_t k = cf.k_start + j + ca.k_shift;
-    const StepConst K = step_const(cf, noise_amp(cf, k));
-    const int Lx = cf.Lx, Ly = cf.Ly;
+    StripCtx X;
+    X.k = cf.k_start + j + ca.k_shift;
+    X.K = step_const(cf, noise_amp(cf, X.k));
+    X.Lx = cf.Lx;
+    X.Ly = cf.Ly;
     const bool odd = !ca.fixed_parity && (j & 1) != 0;
     const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
-    const float* __restrict__ thS = (odd ? buf.thB : buf.thA) + lat_off;
-    const float* __restrict__ omS = (odd ? buf.omB : buf.omA) + lat_off;
-    float* __restrict__ thD = (odd ? buf.thA : buf.thB) + lat_off;
-    float* __restrict__ omD = (odd ? buf.omA : buf.omB) + lat_off;
+    X.thS = (odd ? buf.thB : buf.thA) + lat_off;
+    X.omS = (odd ? buf.omB : buf.omA) + lat_off;
+    X.thD = (odd ? buf.thA : buf.thB) + lat_off;
+    X.omD = (odd ? buf.omA : buf.omB) + lat_off;
 
-    const int G = Lx >= 128 ? 32 : (Lx >> 2);     // lanes per row
+    const int G = X.Lx >= 128 ? 32 : (X.Lx >> 2);  // lanes per row
     const int groups = 32 / G;
-    const int strips = Lx >= 128 ? (Lx >> 7) : 1;
+    const int strips = X.Lx >= 128 ? (X.Lx >> 7) : 1;
     const int seg = unit / strips;
     const int x0 = (unit - seg * strips) * 128;
-    const int grp = lane / G, lg = lane - grp * G;
-    const bool multi = Lx > 128;
-    const int x = x0 + 4 * lg;
+    const int grp = lane / G;
+    X.lg = lane - grp * G;
+    X.multi = X.Lx > 128;
+    X.x = x0 + 4 * X.lg;
     const int ybeg = seg * H * groups + grp * H;
     // edge column: lane 0 of a strip needs x0 - 1, lane 31 needs x0 + 128
-    const int xe = multi ? (lg == 0 ? wrapi(x0 - 1, Lx) : wrapi(x0 + 128, Lx)) : x;
-    const int srcL = grp * G + (lg + G - 1) % G;
-    const int srcR = grp * G + (lg + 1) % G;
-    const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
-    const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
-
-    RowSC prev, cur, nxt;
-    {
-        const int yp = wrapi(ybeg - 1, Ly);
-        row_sc(ld4(thS + (int64_t)yp * Lx + x), thS[(int64_t)yp * Lx + xe], K.q, prev);
-    }
-    float4 th_cur = ld4(thS + (int64_t)ybeg * Lx + x);
-    row_sc(th_cur, thS[(int64_t)ybeg * Lx + xe], K.q, cur);
-    int yn = wrapi(ybeg + 1, Ly);
-    float4 th_nxt = ld4(thS + (int64_t)yn * Lx + x);
-    float te_nxt = thS[(int64_t)yn * Lx + xe];
-    float pm = 0.f, pe = 0.f;
-
-    for (int r = 0; r < H; ++r) {
-        const int y = ybeg + r;
-        // prefetch: theta two rows ahead, omega of this row
-        const int ynn = wrapi(wrapi(y + 2, Ly), Ly);
-        const float4 th_nn = ld4(thS + (int64_t)ynn * Lx + x);
-        const float te_nn = thS[(int64_t)ynn * Lx + xe];
-        const float4 v = ld4_stream(omS + (int64_t)y * Lx + x);
-        row_sc(th_nxt, te_nxt, K.q, nxt);
-
-        // x neighbours of the quad's outer sites
-        float sL = __shfl_sync(kFull, cur.s[3], srcL);
-        float cL = __shfl_sync(kFull, cur.c[3], srcL);
-        float sR = __shfl_sync(kFull, cur.s[0], srcR);
-        float cR = __shfl_sync(kFull, cur.c[0], srcR);
-        if (multi) {
-            if (lg == 0) { sL = cur.se; cL = cur.ce; }
-            if (lg == 31) { sR = cur.se; cR = cur.ce; }
-        }
-        const uint32_t quad = (uint32_t)(((int64_t)y * Lx + x) >> 2);
-        const float4 cn = gauss4_scaled(philox4x32_10(noise_counter(quad, cfgrep, k, 0u), cf.key0, cf.key1), K.c);
-        float to[4], vo[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const float sl = s == 0 ? sL : cur.s[s - 1];
-            const float cl = s == 0 ? cL : cur.c[s - 1];
-            const float sr = s == 3 ? sR : cur.s[s + 1];
-            const float cr = s == 3 ? cR : cur.c[s + 1];
-            const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
-            const float sy = __fadd_rn(prev.s[s], nxt.s[s]), cy = __fadd_rn(prev.c[s], nxt.c[s]);
-            const float th = f4get(th_cur, s);
-            const float F = site_force(K, cur.s[s], cur.c[s], sx, cx, sy, cy, sinp_of(K.p, th));
-            const SiteOut so = site_update(K, th, f4get(v, s), F, f4get(cn, s));
-            to[s] = so.theta;
-            vo[s] = so.v;
-            if (rec) {
-                const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
-                pm = fmaf(sigma, cur.s[s], pm);
-                pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
-                                               cosp_of(K.p, th)));
-            }
-        }
-        st4_stream(thD + (int64_t)y * Lx + x, make_float4(to[0], to[1], to[2], to[3]));
-        st4_stream(omD + (int64_t)y * Lx + x, make_float4(vo[0], vo[1], vo[2], vo[3]));
-        prev = cur;
-        cur = nxt;
-        th_cur = th_nxt;
-        th_nxt = th_nn;
-        te_nxt = te_nn;
-    }
-    if (rec) {
-        const double wm = warp_sum((double)pm), we = warp_sum((double)pe);
+    X.xe = X.multi ? (X.lg == 0 ? wrapi(x0 - 1, X.Lx) : wrapi(x0 + 128, X.Lx)) : X.x;
+    X.srcL = grp * G + (X.lg + G - 1) % G;
+    X.srcR = grp * G + (X.lg + 1) % G;
+    X.rec = ca.record_every > 0 && (X.k % ca.record_every) == 0;
+    X.cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
+    X.pm = 0.f;
+    X.pe = 0.f;
+    if (X.rec) {
+        strip_rows<true>(X, cf, keys, ybeg, H);
+        const double wm = warp_sum((double)X.pm), we = warp_sum((double)X.pe);
         const int64_t b = cf.b_first + task.rep;
-        const int64_t r = (k - cf.rec_first) / ca.record_every;
+        const int64_t r = (X.k - cf.rec_first) / ca.record_every;
         commit_partial(pa, b, unit, task.n_units, wm, we, ca.rec_dev + b * ca.rec_stride + r, 1.0 / (double)cf.N);
+    } else {
+        strip_rows<false>(X, cf, keys, ybeg, H);
     }
 }
 
@@ -471,17 +515,20 @@ int strip_units_per_lattice(int Lx, int Ly, int H)
     return Ly / (H * groups);
 }
 
-// variant = resident blocks per SM the registers are capped for (2, 3 or 4)
+// variant = resident blocks per SM the registers are capped for (2, 3 or 4).
+// Every task of one launch uses the noise key `seed`.
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
-                              int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa, cudaStream_t st)
+                              uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
+                              cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
+    const PhiloxKeys keys = philox_round_keys(seed);
     if (variant >= 4)
-        strip_step_kernel<4><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa);
+        strip_step_kernel<4><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
     else if (variant == 3)
-        strip_step_kernel<3><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa);
+        strip_step_kernel<3><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
     else
-        strip_step_kernel<2><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa);
+        strip_step_kernel<2><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
     return cudaGetLastError();
 }
 
