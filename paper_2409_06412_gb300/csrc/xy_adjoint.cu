@@ -229,4 +229,238 @@ cudaError_t launch_adjoint_phase_b(const DevCfg* d_cfg, const DevCfg& h, AdjArgs
     return cudaGetLastError();
 }
 
+
+// ===========================================================================
+// Fused reverse step on the strip decomposition of the forward stepper.
+//
+// One launch performs phase B of step kB = kA + 1 (the Hessian stencil on
+// F-bar_{kB}, reading theta_{kB}) and phase A of step kA (site-local,
+// reading theta_{kA}, v_{kA}) on the same rows: tb and vb are touched only at
+// their own site, so they are updated in place; F-bar of step kA goes to a
+// second buffer because phase B of the next launch reads it with its
+// neighbours.  Each warp walks its unit's rows with sliding windows of
+// (sin q t, cos q t) of both time levels and of F-bar; x neighbours come by
+// shuffles and the strip's edge columns from global memory, as in the
+// forward stepper.  Either phase can be switched off (segment ends).
+// ===========================================================================
+namespace {
+
+struct RevRow {
+    float4 th;
+    float te;
+    float s[4], c[4];
+};
+
+__device__ __forceinline__ void rev_sc(float q, RevRow& r)
+{
+    sc_q(q, r.th.x, r.s[0], r.c[0]);
+    sc_q(q, r.th.y, r.s[1], r.c[1]);
+    sc_q(q, r.th.z, r.s[2], r.c[2]);
+    sc_q(q, r.th.w, r.s[3], r.c[3]);
+}
+
+__device__ __forceinline__ void rev_load(const float* lat, int64_t row, int x, int xe, RevRow& r)
+{
+    r.th = ld4(lat + row + x);
+    r.te = lat[row + xe];
+}
+
+}  // namespace
+
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* cfgs, const StripTask* tasks, int H,
+                                                                  RevArgs R, PhiloxKeys keys)
+{
+    __shared__ double s_red[6][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const StripTask task = tasks[blockIdx.x];
+    const int unit = task.unit0 + warp;
+    const bool active = unit < task.n_units;
+    const DevCfg& cf = cfgs[task.cfg];
+    const int Lx = cf.Lx, Ly = cf.Ly;
+    const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
+    const float q = cf.q, q2 = __fmul_rn(cf.q, cf.q), hp2 = __fmul_rn(cf.hp, cf.p);
+    const StepConst KA = step_const(cf, noise_amp(cf, R.kA));
+    const float invN = 1.0f / (float)cf.N;
+    const float wE = R.wE, wM = R.wM;
+    const bool observe = R.kA > R.k0, first = R.kA == R.k0;
+    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f;
+    if (active) {
+        const int G = Lx >= 128 ? 32 : (Lx >> 2);
+        const int groups = 32 / G;
+        const int strips = Lx >= 128 ? (Lx >> 7) : 1;
+        const int seg = unit / strips;
+        const int x0 = (unit - seg * strips) * 128;
+        const int grp = lane / G, lg = lane - grp * G;
+        const bool multi = Lx > 128;
+        const int x = x0 + 4 * lg;
+        const int ybeg = seg * H * groups + grp * H;
+        const int xe = multi ? (lg == 0 ? wrapa(x0 - 1, Lx) : wrapa(x0 + 128, Lx)) : x;
+        const int srcL = grp * G + (lg + G - 1) % G;
+        const int srcR = grp * G + (lg + 1) % G;
+        const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
+        const float* thB = R.thB + lat_off;
+        const float* FbI = R.FbIn + lat_off;
+        const float* thA = R.thA + lat_off;
+        const float* vA = R.vA + lat_off;
+        float* tb = R.tb + lat_off;
+        float* vb = R.vb + lat_off;
+        float* FbO = R.FbOut + lat_off;
+        float sgnM = 0.f;
+        if (R.doA && observe && R.wM != 0.f) {
+            const double M = R.rec[(int64_t)(cf.b_first + task.rep) * R.rec_stride + (R.kA - R.k0)].x;
+            sgnM = M > 0.0 ? 1.f : (M < 0.0 ? -1.f : 0.f);
+        }
+        RevRow PB, CB, NB, PA, CA, NA;
+        float4 FP, FC, FN;
+        const int yp = wrapa(ybeg - 1, Ly);
+        if (R.doB) {
+            rev_load(thB, (int64_t)yp * Lx, x, xe, PB);
+            rev_load(thB, (int64_t)ybeg * Lx, x, xe, CB);
+            rev_sc(q, PB);
+            rev_sc(q, CB);
+            FP = ld4(FbI + (int64_t)yp * Lx + x);
+            FC = ld4(FbI + (int64_t)ybeg * Lx + x);
+        }
+        if (R.doA) {
+            rev_load(thA, (int64_t)yp * Lx, x, xe, PA);
+            rev_load(thA, (int64_t)ybeg * Lx, x, xe, CA);
+            rev_sc(KA.q, PA);
+            rev_sc(KA.q, CA);
+        }
+        for (int r = 0; r < H; ++r) {
+            const int y = ybeg + r;
+            const int yn = wrapa(y + 1, Ly);
+            const int64_t row = (int64_t)y * Lx, rown = (int64_t)yn * Lx;
+            float4 tb4 = ld4(tb + row + x);
+            // ---------------- phase B of step kB at row y
+            if (R.doB) {
+                rev_load(thB, rown, x, xe, NB);
+                FN = ld4(FbI + rown + x);
+                const float fe = FbI[row + xe];
+                rev_sc(q, NB);
+                float sL = __shfl_sync(kFullA, CB.s[3], srcL), cL = __shfl_sync(kFullA, CB.c[3], srcL);
+                float sR = __shfl_sync(kFullA, CB.s[0], srcR), cR = __shfl_sync(kFullA, CB.c[0], srcR);
+                float fL = __shfl_sync(kFullA, FC.w, srcL), fR = __shfl_sync(kFullA, FC.x, srcR);
+                if (multi) {
+                    float se, ce;
+                    sc_q(q, CB.te, se, ce);
+                    if (lg == 0) { sL = se; cL = ce; fL = fe; }
+                    if (lg == 31) { sR = se; cR = ce; fR = fe; }
+                }
+                float out[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float sl = i == 0 ? sL : CB.s[i - 1], cl = i == 0 ? cL : CB.c[i - 1];
+                    const float sr = i == 3 ? sR : CB.s[i + 1], cr = i == 3 ? cR : CB.c[i + 1];
+                    const float fl = i == 0 ? fL : f4get(FC, i - 1), fr = i == 3 ? fR : f4get(FC, i + 1);
+                    const float fj = f4get(FC, i);
+                    const float kl = fmaf(CB.c[i], cl, CB.s[i] * sl), kr = fmaf(CB.c[i], cr, CB.s[i] * sr);
+                    const float ku = fmaf(CB.c[i], PB.c[i], CB.s[i] * PB.s[i]);
+                    const float kd = fmaf(CB.c[i], NB.c[i], CB.s[i] * NB.s[i]);
+                    const float hx = fmaf(kl, fl - fj, kr * (fr - fj));
+                    const float hy = fmaf(ku, f4get(FP, i) - fj, kd * (f4get(FN, i) - fj));
+                    float acc = q2 * fmaf(cf.Jx, hx, cf.Jy * hy);
+                    acc = fmaf(hp2, __cosf(__fmul_rn(cf.p, f4get(CB.th, i))) * fj, acc);
+                    out[i] = __fadd_rn(f4get(tb4, i), acc);
+                }
+                tb4 = make_float4(out[0], out[1], out[2], out[3]);
+                PB = CB;
+                CB = NB;
+                FP = FC;
+                FC = FN;
+            }
+            // ---------------- phase A of step kA at row y
+            if (R.doA) {
+                rev_load(thA, rown, x, xe, NA);
+                const float4 v = ld4(vA + row + x);
+                const float4 vb4 = ld4(vb + row + x);
+                rev_sc(KA.q, NA);
+                float sL = __shfl_sync(kFullA, CA.s[3], srcL), cL = __shfl_sync(kFullA, CA.c[3], srcL);
+                float sR = __shfl_sync(kFullA, CA.s[0], srcR), cR = __shfl_sync(kFullA, CA.c[0], srcR);
+                if (multi) {
+                    float se, ce;
+                    sc_q(KA.q, CA.te, se, ce);
+                    if (lg == 0) { sL = se; cL = ce; }
+                    if (lg == 31) { sR = se; cR = ce; }
+                }
+                const uint32_t quad = (uint32_t)((row + x) >> 2);
+                const float4 nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.kA, 0u), keys), 1.0f);
+                float tbo[4], vbo[4], fbo[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float sl = i == 0 ? sL : CA.s[i - 1], cl = i == 0 ? cL : CA.c[i - 1];
+                    const float sr = i == 3 ? sR : CA.s[i + 1], cr = i == 3 ? cR : CA.c[i + 1];
+                    const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
+                    const float sy = __fadd_rn(PA.s[i], NA.s[i]), cy = __fadd_rn(PA.c[i], NA.c[i]);
+                    const float th = f4get(CA.th, i);
+                    const float sinp = __sinf(__fmul_rn(KA.p, th));
+                    const float F = site_force(KA, CA.s[i], CA.c[i], sx, cx, sy, cy, sinp);
+                    const float cn = __fmul_rn(KA.c, f4get(nz, i));
+                    const float g = fmaf(KA.hdt, F, cn);
+                    const float om = __fmul_rn(__fadd_rn(f4get(v, i), g), KA.inv1pa);
+                    const float vbt = fmaf(KA.dt, f4get(tb4, i), f4get(vb4, i));
+                    float omb = __fmul_rn(KA.oma, vbt);
+                    float gb = vbt;
+                    abar = fmaf(-om, vbt, abar);
+                    float tbi = f4get(tb4, i);
+                    if (observe) {
+                        omb = fmaf(wE * invN, om, omb);
+                        tbi = fmaf(-wE * invN, F, tbi);
+                        const float sigma = (cf.stag && ((x + i + y) & 1)) ? -1.f : 1.f;
+                        tbi = fmaf(wM * invN * sgnM * sigma * KA.q, CA.c[i], tbi);
+                        aJx = fmaf(-wE * invN, fmaf(CA.c[i], cr, CA.s[i] * sr), aJx);
+                        aJy = fmaf(-wE * invN, fmaf(CA.c[i], NA.c[i], CA.s[i] * NA.s[i]), aJy);
+                        ah = fmaf(wE * invN, __cosf(__fmul_rn(KA.p, th)), ah);
+                    }
+                    float vbk = 0.f;
+                    if (!first) {
+                        vbk = __fmul_rn(KA.inv1pa, omb);
+                        gb = fmaf(KA.inv1pa, omb, gb);
+                        bbar = fmaf(__fadd_rn(f4get(v, i), g), omb, bbar);
+                    }
+                    const float fb = __fmul_rn(KA.hdt, gb);
+                    cbar = fmaf(gb, f4get(nz, i), cbar);
+                    aJx = fmaf(fb, -KA.q * fmaf(CA.s[i], cx, -CA.c[i] * sx), aJx);
+                    aJy = fmaf(fb, -KA.q * fmaf(CA.s[i], cy, -CA.c[i] * sy), aJy);
+                    ah = fmaf(fb, KA.p * sinp, ah);
+                    tbo[i] = tbi;
+                    vbo[i] = vbk;
+                    fbo[i] = fb;
+                }
+                st4(tb + row + x, make_float4(tbo[0], tbo[1], tbo[2], tbo[3]));
+                st4(vb + row + x, make_float4(vbo[0], vbo[1], vbo[2], vbo[3]));
+                st4(FbO + row + x, make_float4(fbo[0], fbo[1], fbo[2], fbo[3]));
+                PA = CA;
+                CA = NA;
+            } else {
+                st4(tb + row + x, tb4);
+            }
+        }
+    }
+    // per-block FP64 accumulators in a fixed order (only phase A contributes)
+    if (!R.doA) return;
+    const double ceta = cf.eta_d > 0.0 ? (double)KA.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
+    double vals[6] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double w = warp_sum_a(vals[k]);
+        if (lane == 0) s_red[k][warp] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double acc = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) acc += s_red[threadIdx.x][w2];
+        R.gacc[(int64_t)(R.block_base + blockIdx.x) * 6 + threadIdx.x] += acc;
+    }
+}
+
+cudaError_t launch_adjoint_strip(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, uint64_t seed,
+                                 RevArgs R, cudaStream_t st)
+{
+    if (n_tasks == 0) return cudaSuccess;
+    adjoint_strip_kernel<2><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, philox_round_keys(seed));
+    return cudaGetLastError();
+}
+
 }  // namespace xy

@@ -1084,17 +1084,59 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     if ((rc = prime_all(L))) return rc;
     const int64_t T = L->total_sites;
     const int64_t nseg = (n + K - 1) / K;
-    const int64_t R = n + 1;
+    const int64_t R_ = n + 1;
+    // reverse kernels: strip decomposition where the shape allows it (fused
+    // reverse step), per-quad phase kernels otherwise
+    struct AdjGroup {
+        int Lx, Ly, H;
+        uint64_t seed;
+        std::vector<StripTask> tasks;
+        StripTask* d_tasks = nullptr;
+        int block_base = 0;
+    };
+    std::vector<AdjGroup> adj_groups;
+    std::vector<int> adj_plain;
     int n_blocks = 0;
-    std::vector<int> block_base(L->n_cfg);
-    for (int c = 0; c < L->n_cfg; ++c) {
-        block_base[c] = n_blocks;
-        n_blocks += adjoint_blocks(L->h_dev[c]);
+    std::vector<int> block_base(L->n_cfg, 0);
+    {
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        for (int c = 0; c < L->n_cfg; ++c) {
+            const xy_config_desc& d = L->cfg[c].desc;
+            int64_t same = 0;
+            for (int c2 = 0; c2 < L->n_cfg; ++c2)
+                if (L->cfg[c2].desc.Lx == d.Lx && L->cfg[c2].desc.Ly == d.Ly) same += L->cfg[c2].desc.n_replicas;
+            const int H = choose_strip_H(d.Lx, d.Ly, same, (int64_t)sms * 8);
+            if (H <= 0) {
+                adj_plain.push_back(c);
+                continue;
+            }
+            AdjGroup* g = nullptr;
+            for (auto& gg : adj_groups)
+                if (gg.Lx == d.Lx && gg.Ly == d.Ly && gg.H == H && gg.seed == d.seed) g = &gg;
+            if (!g) {
+                adj_groups.push_back(AdjGroup{d.Lx, d.Ly, H, d.seed, {}, nullptr, 0});
+                g = &adj_groups.back();
+            }
+            const int nu = strip_units_per_lattice(d.Lx, d.Ly, H);
+            for (int r = 0; r < d.n_replicas; ++r)
+                for (int u0 = 0; u0 < nu; u0 += 8) g->tasks.push_back(StripTask{c, r, u0, nu});
+        }
+        for (auto& g : adj_groups) {
+            g.block_base = n_blocks;
+            n_blocks += (int)g.tasks.size();
+        }
+        for (int c : adj_plain) {
+            block_base[c] = n_blocks;
+            n_blocks += adjoint_blocks(L->h_dev[c]);
+        }
     }
     float *ck = nullptr, *seg = nullptr, *tb = nullptr, *vb = nullptr, *Fb = nullptr;
     double2* arec = nullptr;
     double* gacc = nullptr;
     auto cleanup = [&]() {
+        for (auto& g : adj_groups) cudaFree(g.d_tasks);
         cudaFree(ck);
         cudaFree(seg);
         cudaFree(tb);
@@ -1107,8 +1149,14 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * 2 * T * (K + 1));
     if (e == cudaSuccess) e = cudaMalloc(&tb, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&vb, sizeof(float) * T);
-    if (e == cudaSuccess) e = cudaMalloc(&Fb, sizeof(float) * T);
-    if (e == cudaSuccess) e = cudaMalloc(&arec, sizeof(double2) * L->B * R);
+    if (e == cudaSuccess) e = cudaMalloc(&Fb, sizeof(float) * 2 * T);
+    if (e == cudaSuccess) e = cudaMalloc(&arec, sizeof(double2) * L->B * R_);
+    for (auto& g : adj_groups) {
+        if (e != cudaSuccess) break;
+        e = cudaMalloc(&g.d_tasks, sizeof(StripTask) * g.tasks.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(StripTask) * g.tasks.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&gacc, sizeof(double) * 6 * n_blocks);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1137,7 +1185,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         CKA(cudaMemcpyAsync(ck + 2 * T * s, L->thA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
         CKA(cudaMemcpyAsync(ck + 2 * T * s + T, L->omA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
         const int64_t ns = std::min<int64_t>(K, n - s * K);
-        RCA(advance_core(L, ns, 1, arec + s * K, R, false, 0));
+        RCA(advance_core(L, ns, 1, arec + s * K, R_, false, 0));
     }
     // observation at k0 + n (first half of the next step, state untouched)
     for (int c = 0; c < L->n_cfg; ++c) {
@@ -1148,7 +1196,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     RCA(upload_cfg(L));
     {
         CallArgs ca{};
-        ca.rec_stride = R;
+        ca.rec_stride = R_;
         ca.rec_dev = arec + n;
         ca.record_every = 1;
         RCA(upload_call(L, ca));
@@ -1157,13 +1205,13 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, state_buffers(L), L->d_call, L->pa, 0, L->stream));
         ++L->launches;
     }
-    std::vector<double2> hrec((size_t)L->B * R);
-    CKA(cudaMemcpyAsync(hrec.data(), arec, sizeof(double2) * L->B * R, cudaMemcpyDeviceToHost, L->stream));
+    std::vector<double2> hrec((size_t)L->B * R_);
+    CKA(cudaMemcpyAsync(hrec.data(), arec, sizeof(double2) * L->B * R_, cudaMemcpyDeviceToHost, L->stream));
     CKA(cudaStreamSynchronize(L->stream));
     double obj = 0.0;
     for (int64_t b = 0; b < L->B; ++b)
         for (int64_t k = 1; k <= n; ++k) {
-            const double2 me = hrec[b * R + k];
+            const double2 me = hrec[b * R_ + k];
             obj += wE * me.y + wM * std::fabs(me.x);
         }
     const double inv_norm = 1.0 / ((double)L->B * (double)n);
@@ -1177,8 +1225,66 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     RCA(upload_cfg(L));
     CKA(cudaMemsetAsync(tb, 0, state_bytes, L->stream));
     CKA(cudaMemsetAsync(vb, 0, state_bytes, L->stream));
+    CKA(cudaMemsetAsync(Fb, 0, 2 * state_bytes, L->stream));
     CKA(cudaMemsetAsync(gacc, 0, sizeof(double) * 6 * n_blocks, L->stream));
-    const int saved_path = L->path;
+    int fcur = 0;  // F-bar ping-pong: Fb + fcur * T holds F-bar of the last phase A
+    // one reverse launch: phase B of step kA + 1 (states at slot iB) and phase A
+    // of step kA (slot iA); either may be off
+    auto rev_launch = [&](bool doA, bool doB, int64_t kA, int64_t iA, int64_t iB) -> int {
+        RevArgs R{};
+        R.thB = seg + 2 * T * iB;
+        R.FbIn = Fb + (int64_t)fcur * T;
+        R.thA = seg + 2 * T * iA;
+        R.vA = seg + 2 * T * iA + T;
+        R.tb = tb;
+        R.vb = vb;
+        R.FbOut = Fb + (int64_t)(1 - fcur) * T;
+        R.rec = arec;
+        R.rec_stride = R_;
+        R.kA = kA;
+        R.k0 = k0;
+        R.wE = (float)wE;
+        R.wM = (float)wM;
+        R.doA = doA;
+        R.doB = doB;
+        R.gacc = gacc;
+        for (auto& g : adj_groups) {
+            R.block_base = g.block_base;
+            CK(launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, L->stream));
+            ++L->launches;
+        }
+        for (int c : adj_plain) {
+            if (doB) {
+                AdjArgs a{};
+                a.theta = R.thB;
+                a.tb = tb;
+                a.Fb = Fb + (int64_t)fcur * T;
+                CK(launch_adjoint_phase_b(L->d_cfg, L->h_dev[c], a, L->stream));
+                ++L->launches;
+            }
+            if (doA) {
+                AdjArgs a{};
+                a.theta = R.thA;
+                a.omega = R.vA;
+                a.tb = tb;
+                a.vb = vb;
+                a.Fb = Fb + (int64_t)(1 - fcur) * T;
+                a.rec = arec;
+                a.rec_stride = R_;
+                a.k = kA;
+                a.k0 = k0;
+                a.k_end = k0 + n;
+                a.wE = wE;
+                a.wM = wM;
+                a.inv_norm = inv_norm;
+                a.gacc = gacc;
+                CK(launch_adjoint_phase_a(L->d_cfg, L->h_dev[c], block_base[c], a, L->stream));
+                ++L->launches;
+            }
+        }
+        if (doA) fcur = 1 - fcur;
+        return XY_OK;
+    };
     for (int64_t s = nseg - 1; s >= 0; --s) {
         const int64_t ks = k0 + s * K;
         const int64_t Ks = std::min<int64_t>(K, n - s * K);
@@ -1218,47 +1324,32 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 }
             }
         }
-        for (int64_t i = n_states - 1; i >= 0; --i) {
-            AdjArgs a{};
-            a.theta = seg + 2 * T * i;
-            a.omega = seg + 2 * T * i + T;
-            a.tb = tb;
-            a.vb = vb;
-            a.Fb = Fb;
-            a.rec = arec;
-            a.rec_stride = R;
-            a.k = ks + i;
-            a.k0 = k0;
-            a.k_end = k0 + n;
-            a.wE = wE;
-            a.wM = wM;
-            a.inv_norm = inv_norm;
-            a.gacc = gacc;
-            for (int c = 0; c < L->n_cfg; ++c) {
-                CKA(launch_adjoint_phase_a(L->d_cfg, L->h_dev[c], block_base[c], a, L->stream));
-                ++L->launches;
-            }
-            for (int c = 0; c < L->n_cfg; ++c) {
-                CKA(launch_adjoint_phase_b(L->d_cfg, L->h_dev[c], a, L->stream));
-                ++L->launches;
-            }
-        }
+        // reverse: A(top); B(i) A(i-1) for i = top..1; B(0)
+        const int64_t top = n_states - 1;
+        RCA(rev_launch(true, false, ks + top, top, top));
+        for (int64_t i = top; i >= 1; --i) RCA(rev_launch(true, true, ks + i - 1, i - 1, i));
+        RCA(rev_launch(false, true, ks - 1, 0, 0));
     }
-    L->path = saved_path;
     std::vector<double> hg((size_t)6 * n_blocks);
     CKA(cudaMemcpyAsync(hg.data(), gacc, sizeof(double) * 6 * n_blocks, cudaMemcpyDeviceToHost, L->stream));
     CKA(cudaStreamSynchronize(L->stream));
-    for (int c = 0; c < L->n_cfg; ++c) {
-        double acc[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<double> acc((size_t)6 * L->n_cfg, 0.0);
+    for (auto& g : adj_groups)
+        for (size_t t = 0; t < g.tasks.size(); ++t)
+            for (int q = 0; q < 6; ++q) acc[6 * g.tasks[t].cfg + q] += hg[(size_t)(g.block_base + t) * 6 + q];
+    for (int c : adj_plain) {
         const int nb = adjoint_blocks(L->h_dev[c]);
         for (int bk = 0; bk < nb; ++bk)
-            for (int q = 0; q < 6; ++q) acc[q] += hg[(size_t)(block_base[c] + bk) * 6 + q];
+            for (int q = 0; q < 6; ++q) acc[6 * c + q] += hg[(size_t)(block_base[c] + bk) * 6 + q];
+    }
+    for (int c = 0; c < L->n_cfg; ++c) {
         const xy_params& p = L->cfg[c].prm;
         const double bb = 1.0 / (1.0 + 0.5 * p.eta * p.dt);
-        grads[4 * c + 0] = acc[0] * inv_norm;
-        grads[4 * c + 1] = acc[1] * inv_norm;
-        grads[4 * c + 2] = acc[2] * inv_norm;
-        grads[4 * c + 3] = (0.5 * p.dt * (acc[3] - bb * bb * acc[4]) + acc[5]) * inv_norm;
+        const double* ac = &acc[6 * c];
+        grads[4 * c + 0] = ac[0] * inv_norm;
+        grads[4 * c + 1] = ac[1] * inv_norm;
+        grads[4 * c + 2] = ac[2] * inv_norm;
+        grads[4 * c + 3] = (0.5 * p.dt * (ac[3] - bb * bb * ac[4]) + ac[5]) * inv_norm;
     }
     // restore the idle window
     set_window_idle(L);

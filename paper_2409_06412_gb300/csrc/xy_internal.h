@@ -155,4 +155,24 @@ cudaError_t launch_adjoint_phase_a(const DevCfg* d_cfg, const DevCfg& h_cfg, int
 cudaError_t launch_adjoint_phase_b(const DevCfg* d_cfg, const DevCfg& h_cfg, AdjArgs a, cudaStream_t st);
 int adjoint_blocks(const DevCfg& h_cfg);
 
+// Fused reverse step on strip tasks: phase B of step kA + 1 and phase A of step kA.
+struct RevArgs {
+    const float* thB;    // theta_{kA+1}
+    const float* FbIn;   // F-bar_{kA+1}
+    const float* thA;    // theta_{kA}
+    const float* vA;     // v_{kA}
+    float* tb;           // adjoint of theta (in place)
+    float* vb;           // adjoint of v (in place)
+    float* FbOut;        // F-bar_{kA}
+    const double2* rec;  // forward observables [B][R]
+    int64_t rec_stride;
+    int64_t kA, k0;
+    float wE, wM;
+    int doA, doB;
+    double* gacc;        // [blocks][6]
+    int block_base;
+};
+cudaError_t launch_adjoint_strip(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, uint64_t seed,
+                                 RevArgs R, cudaStream_t st);
+
 }  // namespace xy

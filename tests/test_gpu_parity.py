@@ -399,8 +399,11 @@ def test_adjoint_matches_oracle(field):
     else:
         prm = dict(h=3.0)
         knots = ([0], [0.05])
+    # fused strip reverse kernel (16 x 8 with sub-warp rows, 128 x 4) and the
+    # per-quad fallback (12 x 10, a width the strip decomposition does not take)
     specs = [inputs.config(16, 8, 2, seed=3, knots=knots, **prm),
-             inputs.config(128, 4, 1, seed=4, knots=knots, **prm)]
+             inputs.config(128, 4, 1, seed=4, knots=knots, **prm),
+             inputs.config(12, 10, 1, seed=4, knots=knots, **prm)]
     if field == "smooth_p2":
         thetas = _mixed_thetas(specs, seed=61)
     else:
@@ -415,7 +418,7 @@ def test_adjoint_matches_oracle(field):
     scale = np.abs(o_grads).max(axis=1, keepdims=True)
     assert np.all(np.abs(grads - o_grads) <= 1e-3 * scale), (grads, o_grads)
     _, steps = lat.observe()
-    assert list(steps) == [n, n]
+    assert list(steps) == [n, n, n]
 
 
 def test_adjoint_autograd_function():
