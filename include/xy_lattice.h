@@ -219,14 +219,18 @@ int xy_synchronize(xy_lattice* lat);
  * (graph replays count their kernel nodes). */
 int64_t xy_kernel_launches(xy_lattice* lat);
 
-#define XY_KCLASS_RESIDENT 0 /* resident stepper launches */
-#define XY_KCLASS_STRIP 1    /* strip stepper launches */
-#define XY_KCLASS_PLAIN 2    /* plain stepper launches */
-#define XY_KCLASS_COUNT 3
+#define XY_KCLASS_RESIDENT 0  /* resident stepper launches */
+#define XY_KCLASS_STRIP 1     /* strip stepper launches */
+#define XY_KCLASS_PLAIN 2     /* plain stepper launches */
+#define XY_KCLASS_ADJ_FWD 3   /* adjoint: forward pass with checkpoints and records (one span per call) */
+#define XY_KCLASS_ADJ_RECOMP 4 /* adjoint: recompute of the checkpoint segments (one span per call) */
+#define XY_KCLASS_ADJ_REV 5   /* adjoint: reverse sweep kernels (one span per call) */
+#define XY_KCLASS_COUNT 6
 
 /* Kernel timing.  on != 0: the batched path launches its kernels directly
  * (no graph replay) and brackets every stepper launch with CUDA events on the
- * object's stream; nothing is skipped.  on == 0 (default): graphs, no events.
+ * object's stream, and the adjoint brackets its three phases (the spans
+ * include the kernels of every class inside them); nothing is skipped.  on == 0 (default): graphs, no events.
  * Switching clears the accumulated times. */
 int xy_set_kernel_timing(xy_lattice* lat, int on);
 

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
 {
     const DevCfg& cf = cfgs[c];
     __shared__ float s_c;
-    __shared__ double s_red[6][8];
+    __shared__ double s_red[kGacc][8];
     const int64_t k = A.k;
     if (threadIdx.x == 0) s_c = noise_amp(cf, k);
     __syncthreads();
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
     const bool observe = k > A.k0;
     const bool first = k == A.k0;
     const float invN = 1.0f / (float)cf.N;
-    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f;
+    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f, eacc = 0.f;
     if (quad < nq_lat) {
         const int y = (int)(4 * quad / cf.Lx), x = (int)(4 * quad - (int64_t)y * cf.Lx);
         Nbr4 n;
@@ -131,9 +131,17 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
                 const float sigma = (cf.stag && ((x + i + y) & 1)) ? -1.f : 1.f;
                 tbi = fmaf(wM * invN * sgnM * sigma * K.q, co[i], tbi);
                 // explicit parameter dependence of E (forward bonds)
-                aJx = fmaf(-wE * invN, fmaf(co[i], cR, s[i] * sR), aJx);
-                aJy = fmaf(-wE * invN, fmaf(co[i], cd[i], s[i] * sd[i]), aJy);
-                ah = fmaf(wE * invN, __cosf(__fmul_rn(K.p, n.t[i])), ah);
+                const float bx = fmaf(co[i], cR, s[i] * sR);
+                const float by = fmaf(co[i], cd[i], s[i] * sd[i]);
+                const float cp = __cosf(__fmul_rn(K.p, n.t[i]));
+                aJx = fmaf(-wE * invN, bx, aJx);
+                aJy = fmaf(-wE * invN, by, aJy);
+                ah = fmaf(wE * invN, cp, ah);
+                float e = __fmul_rn(0.5f, __fmul_rn(om, om));
+                e = fmaf(-cf.Jx, bx, e);
+                e = fmaf(-cf.Jy, by, e);
+                e = fmaf(cf.h, cp, e);
+                eacc = fmaf(wE * invN, e, eacc);
             }
             float vbk = 0.f;
             if (!first) {
@@ -157,18 +165,18 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
     }
     // block sums in FP64, fixed order; per-block accumulators across steps
     const double ceta = cf.eta_d > 0.0 ? (double)K.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
-    double vals[6] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta};
+    double vals[kGacc] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta, eacc};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < kGacc; ++q) {
         const double w = warp_sum_a(vals[q]);
         if (lane == 0) s_red[q][warp] = w;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (threadIdx.x < kGacc) {
         double acc = 0.0;
         for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) acc += s_red[threadIdx.x][w2];
-        A.gacc[(int64_t)(block_base + blockIdx.x) * 6 + threadIdx.x] += acc;
+        A.gacc[(int64_t)(block_base + blockIdx.x) * kGacc + threadIdx.x] += acc;
     }
 }
 
@@ -267,11 +275,11 @@ __device__ __forceinline__ void rev_load(const float* lat, int64_t row, int x, i
 
 }  // namespace
 
-template <int MINB>
+template <int MINB, bool DOA, bool DOB>
 __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* cfgs, const StripTask* tasks, int H,
                                                                   RevArgs R, PhiloxKeys keys)
 {
-    __shared__ double s_red[6][8];
+    __shared__ double s_red[kGacc][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const StripTask task = tasks[blockIdx.x];
     const int unit = task.unit0 + warp;
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
     const float invN = 1.0f / (float)cf.N;
     const float wE = R.wE, wM = R.wM;
     const bool observe = R.kA > R.k0, first = R.kA == R.k0;
-    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f;
+    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f, eacc = 0.f;
     if (active) {
         const int G = Lx >= 128 ? 32 : (Lx >> 2);
         const int groups = 32 / G;
@@ -307,14 +315,14 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
         float* vb = R.vb + lat_off;
         float* FbO = R.FbOut + lat_off;
         float sgnM = 0.f;
-        if (R.doA && observe && R.wM != 0.f) {
+        if (DOA && observe && R.wM != 0.f) {
             const double M = R.rec[(int64_t)(cf.b_first + task.rep) * R.rec_stride + (R.kA - R.k0)].x;
             sgnM = M > 0.0 ? 1.f : (M < 0.0 ? -1.f : 0.f);
         }
         RevRow PB, CB, NB, PA, CA, NA;
         float4 FP, FC, FN;
         const int yp = wrapa(ybeg - 1, Ly);
-        if (R.doB) {
+        if (DOB) {
             rev_load(thB, (int64_t)yp * Lx, x, xe, PB);
             rev_load(thB, (int64_t)ybeg * Lx, x, xe, CB);
             rev_sc(q, PB);
@@ -322,7 +330,7 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
             FP = ld4(FbI + (int64_t)yp * Lx + x);
             FC = ld4(FbI + (int64_t)ybeg * Lx + x);
         }
-        if (R.doA) {
+        if (DOA) {
             rev_load(thA, (int64_t)yp * Lx, x, xe, PA);
             rev_load(thA, (int64_t)ybeg * Lx, x, xe, CA);
             rev_sc(KA.q, PA);
@@ -334,7 +342,7 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
             const int64_t row = (int64_t)y * Lx, rown = (int64_t)yn * Lx;
             float4 tb4 = ld4(tb + row + x);
             // ---------------- phase B of step kB at row y
-            if (R.doB) {
+            if (DOB) {
                 rev_load(thB, rown, x, xe, NB);
                 FN = ld4(FbI + rown + x);
                 const float fe = FbI[row + xe];
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
                 FC = FN;
             }
             // ---------------- phase A of step kA at row y
-            if (R.doA) {
+            if (DOA) {
                 rev_load(thA, rown, x, xe, NA);
                 const float4 v = ld4(vA + row + x);
                 const float4 vb4 = ld4(vb + row + x);
@@ -409,9 +417,18 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
                         tbi = fmaf(-wE * invN, F, tbi);
                         const float sigma = (cf.stag && ((x + i + y) & 1)) ? -1.f : 1.f;
                         tbi = fmaf(wM * invN * sgnM * sigma * KA.q, CA.c[i], tbi);
-                        aJx = fmaf(-wE * invN, fmaf(CA.c[i], cr, CA.s[i] * sr), aJx);
-                        aJy = fmaf(-wE * invN, fmaf(CA.c[i], NA.c[i], CA.s[i] * NA.s[i]), aJy);
-                        ah = fmaf(wE * invN, __cosf(__fmul_rn(KA.p, th)), ah);
+                        const float bx = fmaf(CA.c[i], cr, CA.s[i] * sr);
+                        const float by = fmaf(CA.c[i], NA.c[i], CA.s[i] * NA.s[i]);
+                        const float cp = __cosf(__fmul_rn(KA.p, th));
+                        aJx = fmaf(-wE * invN, bx, aJx);
+                        aJy = fmaf(-wE * invN, by, aJy);
+                        ah = fmaf(wE * invN, cp, ah);
+                        // the objective's energy term: w_E E_kA summed over sites (E linear in the sum)
+                        float e = __fmul_rn(0.5f, __fmul_rn(om, om));
+                        e = fmaf(-cf.Jx, bx, e);
+                        e = fmaf(-cf.Jy, by, e);
+                        e = fmaf(cf.h, cp, e);
+                        eacc = fmaf(wE * invN, e, eacc);
                     }
                     float vbk = 0.f;
                     if (!first) {
@@ -439,27 +456,35 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
         }
     }
     // per-block FP64 accumulators in a fixed order (only phase A contributes)
-    if (!R.doA) return;
+    if (!DOA) return;
     const double ceta = cf.eta_d > 0.0 ? (double)KA.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
-    double vals[6] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta};
+    double vals[kGacc] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta, eacc};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < kGacc; ++k) {
         const double w = warp_sum_a(vals[k]);
         if (lane == 0) s_red[k][warp] = w;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (threadIdx.x < kGacc) {
         double acc = 0.0;
         for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) acc += s_red[threadIdx.x][w2];
-        R.gacc[(int64_t)(R.block_base + blockIdx.x) * 6 + threadIdx.x] += acc;
+        R.gacc[(int64_t)(R.block_base + blockIdx.x) * kGacc + threadIdx.x] += acc;
     }
 }
 
+// R.doA / R.doB select the phases; split = true runs phase B and phase A as
+// two launches (fewer registers each) instead of one fused launch.
 cudaError_t launch_adjoint_strip(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, uint64_t seed,
-                                 RevArgs R, cudaStream_t st)
+                                 RevArgs R, bool split, cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
-    adjoint_strip_kernel<2><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, philox_round_keys(seed));
+    const PhiloxKeys keys = philox_round_keys(seed);
+    if (R.doA && R.doB && !split) {
+        adjoint_strip_kernel<2, true, true><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, keys);
+        return cudaGetLastError();
+    }
+    if (R.doB) adjoint_strip_kernel<4, false, true><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, keys);
+    if (R.doA) adjoint_strip_kernel<2, true, false><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, keys);
     return cudaGetLastError();
 }
 

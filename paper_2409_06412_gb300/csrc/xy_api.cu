@@ -345,6 +345,15 @@ int timed_end(cudaEvent_t end, cudaStream_t st)
     return XY_OK;
 }
 
+// A timed span of the adjoint that contains other timed launches: its own
+// event pair, recorded outside the per-launch pairs.
+struct Span {
+    xy_lattice* L;
+    cudaEvent_t end = nullptr;
+    int open(int cls) { return timed_begin(L, L->stream, cls, &end); }
+    int close() { return timed_end(end, L->stream); }
+};
+
 // Launch the batched kernels for local steps [jl0, jl0 + cnt) of the current window.
 int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, bool advance)
 {
@@ -604,7 +613,7 @@ int fixup_parity(xy_lattice* L)
 // Core of xy_step_n: n steps, records with stride rec_stride into rec_dev
 // (nullable when record_every == 0), optional moments.
 int advance_core(xy_lattice* L, int64_t n, int record_every, double2* rec_dev, int64_t rec_stride,
-                 bool do_moments, int64_t t0)
+                 bool do_moments, int64_t t0, bool m_only = false)
 {
     if (L->path == XY_PATH_BATCHED && !L->tuned) {
         int rc0 = autotune_lattice(L);
@@ -629,6 +638,7 @@ int advance_core(xy_lattice* L, int64_t n, int record_every, double2* rec_dev, i
     ca.k_shift = 0;
     ca.record_every = record_every;
     ca.fixed_parity = 0;
+    ca.m_only = m_only ? 1 : 0;
     if ((rc = upload_call(L, ca))) return rc;
     if ((rc = run_window(L, n_max))) return rc;
     if ((rc = fixup_parity(L))) return rc;
@@ -1093,6 +1103,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         std::vector<StripTask> tasks;
         StripTask* d_tasks = nullptr;
         int block_base = 0;
+        int64_t n_lat = 0;
+        bool split = false;  // phase B and phase A as two launches
     };
     std::vector<AdjGroup> adj_groups;
     std::vector<int> adj_plain;
@@ -1122,6 +1134,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
             const int nu = strip_units_per_lattice(d.Lx, d.Ly, H);
             for (int r = 0; r < d.n_replicas; ++r)
                 for (int u0 = 0; u0 < nu; u0 += 8) g->tasks.push_back(StripTask{c, r, u0, nu});
+            g->n_lat += d.n_replicas;
         }
         for (auto& g : adj_groups) {
             g.block_base = n_blocks;
@@ -1157,7 +1170,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         if (e == cudaSuccess)
             e = cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(StripTask) * g.tasks.size(), cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&gacc, sizeof(double) * 6 * n_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&gacc, sizeof(double) * kGacc * n_blocks);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cleanup();
@@ -1180,12 +1193,14 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         }                                                                                          \
     } while (0)
     const size_t state_bytes = sizeof(float) * T;
+    Span sp{L};
+    RCA(sp.open(XY_KCLASS_ADJ_FWD));
     // ---- forward with checkpoints; observables at every step
     for (int64_t s = 0; s < nseg; ++s) {
         CKA(cudaMemcpyAsync(ck + 2 * T * s, L->thA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
         CKA(cudaMemcpyAsync(ck + 2 * T * s + T, L->omA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
         const int64_t ns = std::min<int64_t>(K, n - s * K);
-        RCA(advance_core(L, ns, 1, arec + s * K, R_, false, 0));
+        RCA(advance_core(L, ns, 0, nullptr, 0, false, 0));
     }
     // observation at k0 + n (first half of the next step, state untouched)
     for (int c = 0; c < L->n_cfg; ++c) {
@@ -1199,23 +1214,15 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         ca.rec_stride = R_;
         ca.rec_dev = arec + n;
         ca.record_every = 1;
+        ca.m_only = 1;
         RCA(upload_call(L, ca));
     }
     for (int c = 0; c < L->n_cfg; ++c) {
         CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, state_buffers(L), L->d_call, L->pa, 0, L->stream));
         ++L->launches;
     }
-    std::vector<double2> hrec((size_t)L->B * R_);
-    CKA(cudaMemcpyAsync(hrec.data(), arec, sizeof(double2) * L->B * R_, cudaMemcpyDeviceToHost, L->stream));
-    CKA(cudaStreamSynchronize(L->stream));
-    double obj = 0.0;
-    for (int64_t b = 0; b < L->B; ++b)
-        for (int64_t k = 1; k <= n; ++k) {
-            const double2 me = hrec[b * R_ + k];
-            obj += wE * me.y + wM * std::fabs(me.x);
-        }
+    RCA(sp.close());
     const double inv_norm = 1.0 / ((double)L->B * (double)n);
-    *objective = obj * inv_norm;
     // ---- reverse sweep, segment by segment
     for (int c = 0; c < L->n_cfg; ++c) {
         L->h_dev[c].k_start = k0;
@@ -1226,7 +1233,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     CKA(cudaMemsetAsync(tb, 0, state_bytes, L->stream));
     CKA(cudaMemsetAsync(vb, 0, state_bytes, L->stream));
     CKA(cudaMemsetAsync(Fb, 0, 2 * state_bytes, L->stream));
-    CKA(cudaMemsetAsync(gacc, 0, sizeof(double) * 6 * n_blocks, L->stream));
+    CKA(cudaMemsetAsync(gacc, 0, sizeof(double) * kGacc * n_blocks, L->stream));
     int fcur = 0;  // F-bar ping-pong: Fb + fcur * T holds F-bar of the last phase A
     // one reverse launch: phase B of step kA + 1 (states at slot iB) and phase A
     // of step kA (slot iA); either may be off
@@ -1250,8 +1257,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         R.gacc = gacc;
         for (auto& g : adj_groups) {
             R.block_base = g.block_base;
-            CK(launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, L->stream));
-            ++L->launches;
+            CK(launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, g.split, L->stream));
+            L->launches += (g.split && doA && doB) ? 2 : 1;
         }
         for (int c : adj_plain) {
             if (doB) {
@@ -1285,67 +1292,160 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         if (doA) fcur = 1 - fcur;
         return XY_OK;
     };
+    // fused or split reverse launches per strip group: timed once on scratch
+    // outputs with the first segment's states (the kernels' cost does not
+    // depend on the data), cached per GPU and shape
+    auto tune_reverse = [&]() -> int {
+        const std::string gpu = gpu_name();
+        float *s_tb = nullptr, *s_vb = nullptr, *s_fb = nullptr;
+        double* s_g = nullptr;
+        bool need = false;
+        for (auto& g : adj_groups) {
+            char key[256];
+            snprintf(key, sizeof key, "%s|adjrev|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
+            int sp = 0, dummy = 0;
+            if (g_tune.get(key, &sp, &dummy)) g.split = sp != 0;
+            else need = true;
+        }
+        if (!need || T < 2) return XY_OK;
+        cudaError_t e2 = cudaMalloc(&s_tb, sizeof(float) * 3 * T);
+        if (e2 == cudaSuccess) e2 = cudaMalloc(&s_g, sizeof(double) * kGacc * n_blocks);
+        if (e2 != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(s_tb);
+            return XY_OK;  // no scratch: keep the fused launch
+        }
+        s_vb = s_tb + T;
+        s_fb = s_tb + 2 * T;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (auto& g : adj_groups) {
+            char key[256];
+            snprintf(key, sizeof key, "%s|adjrev|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
+            int sp = 0, dummy = 0;
+            if (g_tune.get(key, &sp, &dummy)) continue;
+            RevArgs R{};
+            R.thB = seg + 2 * T;
+            R.FbIn = s_fb;
+            R.thA = seg;
+            R.vA = seg + T;
+            R.tb = s_tb;
+            R.vb = s_vb;
+            R.FbOut = s_fb;
+            R.rec = arec;
+            R.rec_stride = R_;
+            R.kA = k0;
+            R.k0 = k0;
+            R.wE = (float)wE;
+            R.wM = (float)wM;
+            R.doA = 1;
+            R.doB = 1;
+            R.gacc = s_g;
+            R.block_base = g.block_base;
+            float best[2] = {0.f, 0.f};
+            for (int v = 0; v < 2; ++v) {
+                launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, v == 1, L->stream);
+                cudaEventRecord(e0, L->stream);
+                for (int i = 0; i < 3; ++i)
+                    launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, v == 1, L->stream);
+                cudaEventRecord(e1, L->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&best[v], e0, e1);
+                L->launches += v == 1 ? 8 : 4;
+            }
+            g.split = best[1] < best[0];
+            g_tune.put(key, g.split ? 1 : 0, 0);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(s_tb);
+        cudaFree(s_g);
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return fail(XY_ECUDA, "reverse tuning: %s", cudaGetErrorString(le));
+        return XY_OK;
+    };
     for (int64_t s = nseg - 1; s >= 0; --s) {
         const int64_t ks = k0 + s * K;
         const int64_t Ks = std::min<int64_t>(K, n - s * K);
         const int64_t n_states = (s == nseg - 1) ? Ks + 1 : Ks;  // the last segment also needs k0 + n
+        Span spr{L};
+        RCA(spr.open(XY_KCLASS_ADJ_RECOMP));
         CKA(cudaMemcpyAsync(seg, ck + 2 * T * s, 2 * state_bytes, cudaMemcpyDeviceToDevice, L->stream));
         {
+            // step ks + i runs as local step i (k = k0 + i + (ks - k0)) from slot i
+            // into slot i + 1, and records M_{ks+i} for the signs of |M|
             CallArgs ca{};
             ca.k_shift = ks - k0;
             ca.fixed_parity = 1;
+            ca.record_every = 1;
+            ca.rec_dev = arec;
+            ca.rec_stride = R_;
+            ca.m_only = 1;
             RCA(upload_call(L, ca));
         }
-        for (int64_t i = 0; i + 1 < n_states; ++i) {
-            if (i > 0) {
-                CKA(launch_add_kshift(L->d_call, 1, L->stream));
-                ++L->launches;
-            }
+        // Ks steps: every state of the segment is stepped from once, so M of each is
+        // recorded; slot Ks (the next checkpoint, or k0 + n) is written too
+        for (int64_t i = 0; i < Ks; ++i) {
             Buffers buf{seg + 2 * T * i, seg + 2 * T * i + T, seg + 2 * T * (i + 1), seg + 2 * T * (i + 1) + T};
             if (L->path == XY_PATH_PLAIN) {
                 for (int c = 0; c < L->n_cfg; ++c) {
-                    CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, buf, L->d_call, L->pa, 1, L->stream));
+                    CKA(launch_plain_step(L->d_cfg, L->h_dev[c], i, buf, L->d_call, L->pa, 1, L->stream));
                     ++L->launches;
                 }
             } else {
                 for (auto& g : L->res_groups) {
-                    CKA(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, 0, 1,
+                    CKA(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, i, 1,
                                              buf, L->d_call, L->stream));
                     ++L->launches;
                 }
                 for (auto& g : L->strip_groups) {
-                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, g.seed, 0,
+                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, g.seed, i,
                                           buf, L->d_call, L->pa, L->stream));
                     ++L->launches;
                 }
                 for (int c : L->plain_cfgs) {
-                    CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, buf, L->d_call, L->pa, 1, L->stream));
+                    CKA(launch_plain_step(L->d_cfg, L->h_dev[c], i, buf, L->d_call, L->pa, 1, L->stream));
                     ++L->launches;
                 }
             }
         }
+        RCA(spr.close());
+        if (s == nseg - 1) RCA(tune_reverse());
         // reverse: A(top); B(i) A(i-1) for i = top..1; B(0)
+        Span sv{L};
+        RCA(sv.open(XY_KCLASS_ADJ_REV));
         const int64_t top = n_states - 1;
         RCA(rev_launch(true, false, ks + top, top, top));
         for (int64_t i = top; i >= 1; --i) RCA(rev_launch(true, true, ks + i - 1, i - 1, i));
         RCA(rev_launch(false, true, ks - 1, 0, 0));
+        RCA(sv.close());
     }
-    std::vector<double> hg((size_t)6 * n_blocks);
-    CKA(cudaMemcpyAsync(hg.data(), gacc, sizeof(double) * 6 * n_blocks, cudaMemcpyDeviceToHost, L->stream));
+    std::vector<double2> hrec((size_t)L->B * R_);
+    CKA(cudaMemcpyAsync(hrec.data(), arec, sizeof(double2) * L->B * R_, cudaMemcpyDeviceToHost, L->stream));
+    std::vector<double> hg((size_t)kGacc * n_blocks);
+    CKA(cudaMemcpyAsync(hg.data(), gacc, sizeof(double) * kGacc * n_blocks, cudaMemcpyDeviceToHost, L->stream));
     CKA(cudaStreamSynchronize(L->stream));
-    std::vector<double> acc((size_t)6 * L->n_cfg, 0.0);
+    std::vector<double> acc((size_t)kGacc * L->n_cfg, 0.0);
     for (auto& g : adj_groups)
         for (size_t t = 0; t < g.tasks.size(); ++t)
-            for (int q = 0; q < 6; ++q) acc[6 * g.tasks[t].cfg + q] += hg[(size_t)(g.block_base + t) * 6 + q];
+            for (int q = 0; q < kGacc; ++q)
+                acc[kGacc * g.tasks[t].cfg + q] += hg[(size_t)(g.block_base + t) * kGacc + q];
     for (int c : adj_plain) {
         const int nb = adjoint_blocks(L->h_dev[c]);
         for (int bk = 0; bk < nb; ++bk)
-            for (int q = 0; q < 6; ++q) acc[6 * c + q] += hg[(size_t)(block_base[c] + bk) * 6 + q];
+            for (int q = 0; q < kGacc; ++q) acc[kGacc * c + q] += hg[(size_t)(block_base[c] + bk) * kGacc + q];
     }
+    // objective: w_E E summed by the reverse sweep, w_M |M_k| from the forward records
+    double obj = 0.0;
+    for (int c = 0; c < L->n_cfg; ++c) obj += acc[kGacc * c + 6];
+    for (int64_t b = 0; b < L->B; ++b)
+        for (int64_t k = 1; k <= n; ++k) obj += wM * std::fabs(hrec[b * R_ + k].x);
+    *objective = obj * inv_norm;
     for (int c = 0; c < L->n_cfg; ++c) {
         const xy_params& p = L->cfg[c].prm;
         const double bb = 1.0 / (1.0 + 0.5 * p.eta * p.dt);
-        const double* ac = &acc[6 * c];
+        const double* ac = &acc[kGacc * c];
         grads[4 * c + 0] = ac[0] * inv_norm;
         grads[4 * c + 1] = ac[1] * inv_norm;
         grads[4 * c + 2] = ac[2] * inv_norm;

@@ -45,7 +45,7 @@ struct CallArgs {
     int record_every;   // 0: no observables
     int fixed_parity;   // 1: always read buffers A and write buffers B
     int err;            // device error flag
-    int pad;
+    int m_only;         // 1: records carry M only (E left 0)
 };
 
 // One thread block of the strip stepper: up to 8 consecutive units of one
@@ -148,7 +148,7 @@ struct AdjArgs {
     int64_t k0;           // first step of the adjoint window
     int64_t k_end;        // k0 + n
     double wE, wM, inv_norm;  // objective weights and 1/(B n)
-    double* gacc;         // [n_blocks][6] per-block FP64 accumulators (J_par, J_perp, h, a-bar, b-bar, c-bar-eta)
+    double* gacc;         // [n_blocks][7] per-block FP64 accumulators (J_par, J_perp, h, a-bar, b-bar, c-bar-eta, w_E E)
 };
 cudaError_t launch_adjoint_phase_a(const DevCfg* d_cfg, const DevCfg& h_cfg, int block_base, AdjArgs a,
                                    cudaStream_t st);
@@ -156,6 +156,8 @@ cudaError_t launch_adjoint_phase_b(const DevCfg* d_cfg, const DevCfg& h_cfg, Adj
 int adjoint_blocks(const DevCfg& h_cfg);
 
 // Fused reverse step on strip tasks: phase B of step kA + 1 and phase A of step kA.
+constexpr int kGacc = 7;  // per-block accumulators of the reverse sweep
+
 struct RevArgs {
     const float* thB;    // theta_{kA+1}
     const float* FbIn;   // F-bar_{kA+1}
@@ -169,10 +171,10 @@ struct RevArgs {
     int64_t kA, k0;
     float wE, wM;
     int doA, doB;
-    double* gacc;        // [blocks][6]
+    double* gacc;        // [blocks][7]
     int block_base;
 };
 cudaError_t launch_adjoint_strip(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, uint64_t seed,
-                                 RevArgs R, cudaStream_t st);
+                                 RevArgs R, bool split, cudaStream_t st);
 
 }  // namespace xy

@@ -293,8 +293,9 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
             if (rec) {
                 const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
                 pm = fmaf(sigma, f.s[s], pm);
-                pe = __fadd_rn(pe, site_energy(cf, so.omega, f.s[s], f.c[s], f.sR[s], f.cR[s], f.sD[s], f.cD[s],
-                                               cosp_of(K.p, f.th[s])));
+                if (!ca.m_only)
+                    pe = __fadd_rn(pe, site_energy(cf, so.omega, f.s[s], f.c[s], f.sR[s], f.cR[s], f.sD[s],
+                                                   f.cD[s], cosp_of(K.p, f.th[s])));
             }
         }
         if (write_state) {
@@ -362,7 +363,7 @@ struct StripCtx {
     float* __restrict__ thD;
     float* __restrict__ omD;
     int Lx, Ly, x, xe, srcL, srcR, lg;
-    bool multi, rec;
+    bool multi, rec, rec_e;
     uint32_t cfgrep;
     int64_t k;
     StepConst K;
@@ -432,8 +433,9 @@ __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const 
             if (REC) {
                 const float sigma = (cf.stag && ((X.x + s + y) & 1)) ? -1.f : 1.f;
                 X.pm = fmaf(sigma, C.s[s], X.pm);
-                X.pe = __fadd_rn(X.pe, site_energy(cf, so.omega, C.s[s], C.c[s], sr, cr, N.s[s], N.c[s],
-                                                   cosp_of(X.K.p, th)));
+                if (X.rec_e)
+                    X.pe = __fadd_rn(X.pe, site_energy(cf, so.omega, C.s[s], C.c[s], sr, cr, N.s[s], N.c[s],
+                                                       cosp_of(X.K.p, th)));
             }
         }
         st4_stream(p_to + X.x, make_float4(to[0], to[1], to[2], to[3]));
@@ -493,6 +495,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     X.srcL = grp * G + (X.lg + G - 1) % G;
     X.srcR = grp * G + (X.lg + 1) % G;
     X.rec = ca.record_every > 0 && (X.k % ca.record_every) == 0;
+    X.rec_e = !ca.m_only;
     X.cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
     X.pm = 0.f;
     X.pe = 0.f;
@@ -684,8 +687,9 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                 if (rec) {
                     const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
                     pm = fmaf(sigma, cur.s[s], pm);
-                    pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
-                                                   cosp_of(K.p, th)));
+                    if (!ca.m_only)
+                        pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
+                                                       cosp_of(K.p, th)));
                 }
             }
             st4(s_th + y * Lx + x, make_float4(to[0], to[1], to[2], to[3]));

@@ -164,9 +164,10 @@ class Lattice:
         L.call("xy_set_kernel_timing", self._h, int(bool(on)))
 
     def kernel_timing(self):
-        """(ms, launches) per kernel class (resident, strip, plain) since timing was switched on."""
-        ms = np.zeros(3, dtype=np.float64)
-        n = np.zeros(3, dtype=np.int64)
+        """(ms, launches) per timing class (resident, strip, plain stepper launches;
+        adjoint forward, recompute and reverse spans) since timing was switched on."""
+        ms = np.zeros(6, dtype=np.float64)
+        n = np.zeros(6, dtype=np.int64)
         L.call("xy_kernel_timing", self._h, ms.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p))
         return ms, n
 
