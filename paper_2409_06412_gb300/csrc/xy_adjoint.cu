@@ -239,225 +239,256 @@ cudaError_t launch_adjoint_phase_b(const DevCfg* d_cfg, const DevCfg& h, AdjArgs
 
 
 // ===========================================================================
-// Fused reverse step on the strip decomposition of the forward stepper.
-//
-// One launch performs phase B of step kB = kA + 1 (the Hessian stencil on
-// F-bar_{kB}, reading theta_{kB}) and phase A of step kA (site-local,
-// reading theta_{kA}, v_{kA}) on the same rows: tb and vb are touched only at
-// their own site, so they are updated in place; F-bar of step kA goes to a
-// second buffer because phase B of the next launch reads it with its
-// neighbours.  Each warp walks its unit's rows with sliding windows of
-// (sin q t, cos q t) of both time levels and of F-bar; x neighbours come by
-// shuffles and the strip's edge columns from global memory, as in the
-// forward stepper.  Either phase can be switched off (segment ends).
+// Reverse step on row bands: phase A and phase B of the SAME step in one
+// launch.  A thread block owns a band of H rows over the full width of one
+// lattice (Lx / 128 warps side by side, each a 128-column strip), or, when
+// Lx <= 128, each group of Lx / 4 lanes owns a band of its own.  Row t:
+// phase A on row t (F-bar, the site-local adjoint, v-bar), then phase B on
+// row t - 1 (the Hessian stencil, which needs F-bar of rows t - 2 .. t).
+// F-bar and (sin q t, cos q t) live in register windows; the strips of a row
+// exchange their edge columns through shared memory, one barrier per row.
+// Phase A also runs on the halo rows y0 - 1 and y0 + H (its F-bar feeds the
+// band's edge rows) without storing anything there, so the adjoint state is
+// read from one buffer pair and written to another.
 // ===========================================================================
 namespace {
 
-struct RevRow {
-    float4 th;
-    float te;
+constexpr int kMaxBandWarps = 16;  // Lx <= 2048
+
+// Asynchronous 16-byte global -> shared copies (one per lane and array), so
+// that the next row's data is in flight while the current row is computed.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct BandSC {
     float s[4], c[4];
 };
 
-__device__ __forceinline__ void rev_sc(float q, RevRow& r)
+__device__ __forceinline__ void band_sc(float q, const float4& t, BandSC& r)
 {
-    sc_q(q, r.th.x, r.s[0], r.c[0]);
-    sc_q(q, r.th.y, r.s[1], r.c[1]);
-    sc_q(q, r.th.z, r.s[2], r.c[2]);
-    sc_q(q, r.th.w, r.s[3], r.c[3]);
-}
-
-__device__ __forceinline__ void rev_load(const float* lat, int64_t row, int x, int xe, RevRow& r)
-{
-    r.th = ld4(lat + row + x);
-    r.te = lat[row + xe];
+    sc_q(q, t.x, r.s[0], r.c[0]);
+    sc_q(q, t.y, r.s[1], r.c[1]);
+    sc_q(q, t.z, r.s[2], r.c[2]);
+    sc_q(q, t.w, r.s[3], r.c[3]);
 }
 
 }  // namespace
 
-template <int MINB, bool DOA, bool DOB>
-__global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* cfgs, const StripTask* tasks, int H,
-                                                                  RevArgs R, PhiloxKeys keys)
+__global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs, const BandTask* tasks, int H,
+                                                              BandArgs R, PhiloxKeys keys)
 {
-    __shared__ double s_red[kGacc][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const StripTask task = tasks[blockIdx.x];
-    const int unit = task.unit0 + warp;
-    const bool active = unit < task.n_units;
+    // per warp, two stages of [theta(t+1), v(t), tb(t), vb(t)] for its 32 lanes
+    extern __shared__ float4 s_stage[];
+    // edge exchange: [slot][warp][side]  side 0 = left edge (site x0), 1 = right edge (site x0 + 127)
+    __shared__ float2 s_sc[3][kMaxBandWarps][2];
+    __shared__ float s_fb[2][kMaxBandWarps][2];
+    __shared__ double s_red[kGacc][kMaxBandWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const BandTask task = tasks[blockIdx.x];
     const DevCfg& cf = cfgs[task.cfg];
     const int Lx = cf.Lx, Ly = cf.Ly;
+    const bool wide = Lx > 128;                        // the block is one band spanning Lx / 128 warps
+    const int G = Lx >= 128 ? 32 : (Lx >> 2);
+    const int groups = 32 / G;
+    const int grp = lane / G, lg = lane - grp * G;
+    const int band_raw = wide ? task.band0 : task.band0 + warp * groups + grp;
+    // lane groups past the last band recompute the last band (so every shuffle
+    // and barrier runs converged) and store nothing
+    const bool active = band_raw < task.n_bands;
+    const int band = active ? band_raw : task.n_bands - 1;
+    const int x = (wide ? warp * 128 : 0) + 4 * lg;
+    const int y0 = band * H;
+    const int srcL = grp * G + (lg + G - 1) % G, srcR = grp * G + (lg + 1) % G;
+    const int wl = (warp + n_warps - 1) % n_warps, wr = (warp + 1) % n_warps;  // neighbour strips (wide)
     const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
-    const float q = cf.q, q2 = __fmul_rn(cf.q, cf.q), hp2 = __fmul_rn(cf.hp, cf.p);
-    const StepConst KA = step_const(cf, noise_amp(cf, R.kA));
-    const float invN = 1.0f / (float)cf.N;
-    const float wE = R.wE, wM = R.wM;
-    const bool observe = R.kA > R.k0, first = R.kA == R.k0;
-    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f, eacc = 0.f;
-    if (active) {
-        const int G = Lx >= 128 ? 32 : (Lx >> 2);
-        const int groups = 32 / G;
-        const int strips = Lx >= 128 ? (Lx >> 7) : 1;
-        const int seg = unit / strips;
-        const int x0 = (unit - seg * strips) * 128;
-        const int grp = lane / G, lg = lane - grp * G;
-        const bool multi = Lx > 128;
-        const int x = x0 + 4 * lg;
-        const int ybeg = seg * H * groups + grp * H;
-        const int xe = multi ? (lg == 0 ? wrapa(x0 - 1, Lx) : wrapa(x0 + 128, Lx)) : x;
-        const int srcL = grp * G + (lg + G - 1) % G;
-        const int srcR = grp * G + (lg + 1) % G;
-        const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
-        const float* thB = R.thB + lat_off;
-        const float* FbI = R.FbIn + lat_off;
-        const float* thA = R.thA + lat_off;
-        const float* vA = R.vA + lat_off;
-        float* tb = R.tb + lat_off;
-        float* vb = R.vb + lat_off;
-        float* FbO = R.FbOut + lat_off;
-        float sgnM = 0.f;
-        if (DOA && observe && R.wM != 0.f) {
-            const double M = R.rec[(int64_t)(cf.b_first + task.rep) * R.rec_stride + (R.kA - R.k0)].x;
-            sgnM = M > 0.0 ? 1.f : (M < 0.0 ? -1.f : 0.f);
-        }
-        RevRow PB, CB, NB, PA, CA, NA;
-        float4 FP, FC, FN;
-        const int yp = wrapa(ybeg - 1, Ly);
-        if (DOB) {
-            rev_load(thB, (int64_t)yp * Lx, x, xe, PB);
-            rev_load(thB, (int64_t)ybeg * Lx, x, xe, CB);
-            rev_sc(q, PB);
-            rev_sc(q, CB);
-            FP = ld4(FbI + (int64_t)yp * Lx + x);
-            FC = ld4(FbI + (int64_t)ybeg * Lx + x);
-        }
-        if (DOA) {
-            rev_load(thA, (int64_t)yp * Lx, x, xe, PA);
-            rev_load(thA, (int64_t)ybeg * Lx, x, xe, CA);
-            rev_sc(KA.q, PA);
-            rev_sc(KA.q, CA);
-        }
-        for (int r = 0; r < H; ++r) {
-            const int y = ybeg + r;
-            const int yn = wrapa(y + 1, Ly);
-            const int64_t row = (int64_t)y * Lx, rown = (int64_t)yn * Lx;
-            float4 tb4 = ld4(tb + row + x);
-            // ---------------- phase B of step kB at row y
-            if (DOB) {
-                rev_load(thB, rown, x, xe, NB);
-                FN = ld4(FbI + rown + x);
-                const float fe = FbI[row + xe];
-                rev_sc(q, NB);
-                float sL = __shfl_sync(kFullA, CB.s[3], srcL), cL = __shfl_sync(kFullA, CB.c[3], srcL);
-                float sR = __shfl_sync(kFullA, CB.s[0], srcR), cR = __shfl_sync(kFullA, CB.c[0], srcR);
-                float fL = __shfl_sync(kFullA, FC.w, srcL), fR = __shfl_sync(kFullA, FC.x, srcR);
-                if (multi) {
-                    float se, ce;
-                    sc_q(q, CB.te, se, ce);
-                    if (lg == 0) { sL = se; cL = ce; fL = fe; }
-                    if (lg == 31) { sR = se; cR = ce; fR = fe; }
-                }
-                float out[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float sl = i == 0 ? sL : CB.s[i - 1], cl = i == 0 ? cL : CB.c[i - 1];
-                    const float sr = i == 3 ? sR : CB.s[i + 1], cr = i == 3 ? cR : CB.c[i + 1];
-                    const float fl = i == 0 ? fL : f4get(FC, i - 1), fr = i == 3 ? fR : f4get(FC, i + 1);
-                    const float fj = f4get(FC, i);
-                    const float kl = fmaf(CB.c[i], cl, CB.s[i] * sl), kr = fmaf(CB.c[i], cr, CB.s[i] * sr);
-                    const float ku = fmaf(CB.c[i], PB.c[i], CB.s[i] * PB.s[i]);
-                    const float kd = fmaf(CB.c[i], NB.c[i], CB.s[i] * NB.s[i]);
-                    const float hx = fmaf(kl, fl - fj, kr * (fr - fj));
-                    const float hy = fmaf(ku, f4get(FP, i) - fj, kd * (f4get(FN, i) - fj));
-                    float acc = q2 * fmaf(cf.Jx, hx, cf.Jy * hy);
-                    acc = fmaf(hp2, __cosf(__fmul_rn(cf.p, f4get(CB.th, i))) * fj, acc);
-                    out[i] = __fadd_rn(f4get(tb4, i), acc);
-                }
-                tb4 = make_float4(out[0], out[1], out[2], out[3]);
-                PB = CB;
-                CB = NB;
-                FP = FC;
-                FC = FN;
-            }
-            // ---------------- phase A of step kA at row y
-            if (DOA) {
-                rev_load(thA, rown, x, xe, NA);
-                const float4 v = ld4(vA + row + x);
-                const float4 vb4 = ld4(vb + row + x);
-                rev_sc(KA.q, NA);
-                float sL = __shfl_sync(kFullA, CA.s[3], srcL), cL = __shfl_sync(kFullA, CA.c[3], srcL);
-                float sR = __shfl_sync(kFullA, CA.s[0], srcR), cR = __shfl_sync(kFullA, CA.c[0], srcR);
-                if (multi) {
-                    float se, ce;
-                    sc_q(KA.q, CA.te, se, ce);
-                    if (lg == 0) { sL = se; cL = ce; }
-                    if (lg == 31) { sR = se; cR = ce; }
-                }
-                const uint32_t quad = (uint32_t)((row + x) >> 2);
-                const float4 nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.kA, 0u), keys), 1.0f);
-                float tbo[4], vbo[4], fbo[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float sl = i == 0 ? sL : CA.s[i - 1], cl = i == 0 ? cL : CA.c[i - 1];
-                    const float sr = i == 3 ? sR : CA.s[i + 1], cr = i == 3 ? cR : CA.c[i + 1];
-                    const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
-                    const float sy = __fadd_rn(PA.s[i], NA.s[i]), cy = __fadd_rn(PA.c[i], NA.c[i]);
-                    const float th = f4get(CA.th, i);
-                    const float sinp = __sinf(__fmul_rn(KA.p, th));
-                    const float F = site_force(KA, CA.s[i], CA.c[i], sx, cx, sy, cy, sinp);
-                    const float cn = __fmul_rn(KA.c, f4get(nz, i));
-                    const float g = fmaf(KA.hdt, F, cn);
-                    const float om = __fmul_rn(__fadd_rn(f4get(v, i), g), KA.inv1pa);
-                    const float vbt = fmaf(KA.dt, f4get(tb4, i), f4get(vb4, i));
-                    float omb = __fmul_rn(KA.oma, vbt);
-                    float gb = vbt;
-                    abar = fmaf(-om, vbt, abar);
-                    float tbi = f4get(tb4, i);
-                    if (observe) {
-                        omb = fmaf(wE * invN, om, omb);
-                        tbi = fmaf(-wE * invN, F, tbi);
-                        const float sigma = (cf.stag && ((x + i + y) & 1)) ? -1.f : 1.f;
-                        tbi = fmaf(wM * invN * sgnM * sigma * KA.q, CA.c[i], tbi);
-                        const float bx = fmaf(CA.c[i], cr, CA.s[i] * sr);
-                        const float by = fmaf(CA.c[i], NA.c[i], CA.s[i] * NA.s[i]);
-                        const float cp = __cosf(__fmul_rn(KA.p, th));
-                        aJx = fmaf(-wE * invN, bx, aJx);
-                        aJy = fmaf(-wE * invN, by, aJy);
-                        ah = fmaf(wE * invN, cp, ah);
-                        // the objective's energy term: w_E E_kA summed over sites (E linear in the sum)
-                        float e = __fmul_rn(0.5f, __fmul_rn(om, om));
-                        e = fmaf(-cf.Jx, bx, e);
-                        e = fmaf(-cf.Jy, by, e);
-                        e = fmaf(cf.h, cp, e);
-                        eacc = fmaf(wE * invN, e, eacc);
-                    }
-                    float vbk = 0.f;
-                    if (!first) {
-                        vbk = __fmul_rn(KA.inv1pa, omb);
-                        gb = fmaf(KA.inv1pa, omb, gb);
-                        bbar = fmaf(__fadd_rn(f4get(v, i), g), omb, bbar);
-                    }
-                    const float fb = __fmul_rn(KA.hdt, gb);
-                    cbar = fmaf(gb, f4get(nz, i), cbar);
-                    aJx = fmaf(fb, -KA.q * fmaf(CA.s[i], cx, -CA.c[i] * sx), aJx);
-                    aJy = fmaf(fb, -KA.q * fmaf(CA.s[i], cy, -CA.c[i] * sy), aJy);
-                    ah = fmaf(fb, KA.p * sinp, ah);
-                    tbo[i] = tbi;
-                    vbo[i] = vbk;
-                    fbo[i] = fb;
-                }
-                st4(tb + row + x, make_float4(tbo[0], tbo[1], tbo[2], tbo[3]));
-                st4(vb + row + x, make_float4(vbo[0], vbo[1], vbo[2], vbo[3]));
-                st4(FbO + row + x, make_float4(fbo[0], fbo[1], fbo[2], fbo[3]));
-                PA = CA;
-                CA = NA;
-            } else {
-                st4(tb + row + x, tb4);
-            }
-        }
+    const float* th = R.theta + lat_off;
+    const float* vv = R.omega + lat_off;
+    const float* tbI = R.tb_in + lat_off;
+    const float* vbI = R.vb_in + lat_off;
+    float* tbO = R.tb_out + lat_off;
+    float* vbO = R.vb_out + lat_off;
+    const StepConst K = step_const(cf, noise_amp(cf, R.k));
+    const float q2 = __fmul_rn(K.q, K.q), hp2 = __fmul_rn(cf.hp, cf.p);
+    const float invN = 1.0f / (float)cf.N, wE = R.wE, wM = R.wM;
+    const bool observe = R.k > R.k0, first = R.k == R.k0;
+    const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
+    float sgnM = 0.f;
+    if (observe && R.wM != 0.f) {
+        const double M = R.rec[(int64_t)(cf.b_first + task.rep) * R.rec_stride + (R.k - R.k0)].x;
+        sgnM = M > 0.0 ? 1.f : (M < 0.0 ? -1.f : 0.f);
     }
-    // per-block FP64 accumulators in a fixed order (only phase A contributes)
-    if (!DOA) return;
-    const double ceta = cf.eta_d > 0.0 ? (double)KA.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
+    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f, eacc = 0.f;
+
+    // window: S0 = row t-2, S1 = t-1, S2 = t, S3 = t+1; F0 = F-bar(t-2), F1 = t-1, F2 = t
+    BandSC S0, S1, S2, S3;
+    float4 F0 = make_float4(0.f, 0.f, 0.f, 0.f), F1 = F0, F2 = F0;
+    float4 th2, tbp1 = F0, cp1 = F0;  // raw theta of row t; tb partial and cos(p theta) of row t-1
+    auto rowp = [&](int y) { return (int64_t)wrapa(y, Ly) * Lx; };
+    auto publish_sc = [&](int slot, const BandSC& S) {
+        if (!wide) return;
+        if (lane == 0) s_sc[slot][warp][0] = make_float2(S.s[0], S.c[0]);
+        if (lane == 31) s_sc[slot][warp][1] = make_float2(S.s[3], S.c[3]);
+    };
+    // x neighbours of the quad's outer sites for one row of (s, c)
+    auto nbr_sc = [&](int slot, const BandSC& S, float& sL, float& cL, float& sR, float& cR) {
+        sL = __shfl_sync(kFullA, S.s[3], srcL);
+        cL = __shfl_sync(kFullA, S.c[3], srcL);
+        sR = __shfl_sync(kFullA, S.s[0], srcR);
+        cR = __shfl_sync(kFullA, S.c[0], srcR);
+        if (wide) {
+            if (lane == 0) { const float2 e = s_sc[slot][wl][1]; sL = e.x; cL = e.y; }
+            if (lane == 31) { const float2 e = s_sc[slot][wr][0]; sR = e.x; cR = e.y; }
+        }
+    };
+    float4* my_stage = s_stage + (size_t)warp * 2 * 4 * 32;
+    auto prefetch = [&](int st, int t) {  // theta of row t + 1 and v, tb, vb of row t into stage st
+        float4* p = my_stage + st * 4 * 32;
+        cp_async16(p + 0 * 32 + lane, th + rowp(t + 1) + x);
+        cp_async16(p + 1 * 32 + lane, vv + rowp(t) + x);
+        cp_async16(p + 2 * 32 + lane, tbI + rowp(t) + x);
+        cp_async16(p + 3 * 32 + lane, vbI + rowp(t) + x);
+        cp_async_commit();
+    };
+    band_sc(K.q, ld4(th + rowp(y0 - 2) + x), S1);
+    th2 = ld4(th + rowp(y0 - 1) + x);
+    band_sc(K.q, th2, S2);
+    publish_sc((y0 - 1 + 3 * Ly) % 3, S2);
+    prefetch(0, y0 - 1);
+    if (wide) __syncthreads(); else __syncwarp();
+    for (int t = y0 - 1; t <= y0 + H; ++t) {
+        const bool own_a = active && t >= y0 && t < y0 + H;  // phase A results stored / accumulated
+        const bool do_b = t - 1 >= y0;                      // phase B on row t-1
+        const int st = (t - y0 + 1) & 1;
+        prefetch(st ^ 1, t + 1);
+        cp_async_wait1();  // this lane's copies of stage st have landed
+        const float4* sp = my_stage + st * 4 * 32;
+        const float4 th3 = sp[0 * 32 + lane];
+        band_sc(K.q, th3, S3);
+        publish_sc((t + 1 + 3 * Ly) % 3, S3);
+        // ---------------- phase A on row t
+        float4 Fn = make_float4(0.f, 0.f, 0.f, 0.f), tbpn = Fn, cpn = Fn;
+        {
+            const int64_t row = rowp(t);
+            const float4 v = sp[1 * 32 + lane];
+            const float4 tb4 = sp[2 * 32 + lane];
+            const float4 vb4 = sp[3 * 32 + lane];
+            float sL, cL, sR, cR;
+            nbr_sc((t + 3 * Ly) % 3, S2, sL, cL, sR, cR);
+            const uint32_t quad = (uint32_t)((row + x) >> 2);
+            const float4 nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.k, 0u), keys), 1.0f);
+            float tbo[4], vbo[4], fbo[4], cpo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float sl = i == 0 ? sL : S2.s[i - 1], cl = i == 0 ? cL : S2.c[i - 1];
+                const float sr = i == 3 ? sR : S2.s[i + 1], cr = i == 3 ? cR : S2.c[i + 1];
+                const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
+                const float sy = __fadd_rn(S1.s[i], S3.s[i]), cy = __fadd_rn(S1.c[i], S3.c[i]);
+                const float tht = f4get(th2, i);
+                const float sinp = __sinf(__fmul_rn(K.p, tht));
+                const float cp = __cosf(__fmul_rn(K.p, tht));
+                const float F = site_force(K, S2.s[i], S2.c[i], sx, cx, sy, cy, sinp);
+                const float cn = __fmul_rn(K.c, f4get(nz, i));
+                const float g = fmaf(K.hdt, F, cn);
+                const float om = __fmul_rn(__fadd_rn(f4get(v, i), g), K.inv1pa);
+                const float vbt = fmaf(K.dt, f4get(tb4, i), f4get(vb4, i));
+                float omb = __fmul_rn(K.oma, vbt);
+                float gb = vbt;
+                float tbi = f4get(tb4, i);
+                const float bx = fmaf(S2.c[i], cr, S2.s[i] * sr);
+                const float by = fmaf(S2.c[i], S3.c[i], S2.s[i] * S3.s[i]);
+                float da = -om * vbt, dJx = 0.f, dJy = 0.f, dh = 0.f, de = 0.f;
+                if (observe) {
+                    omb = fmaf(wE * invN, om, omb);
+                    tbi = fmaf(-wE * invN, F, tbi);
+                    const float sigma = (cf.stag && ((x + i + t) & 1)) ? -1.f : 1.f;
+                    tbi = fmaf(wM * invN * sgnM * sigma * K.q, S2.c[i], tbi);
+                    dJx = -wE * invN * bx;
+                    dJy = -wE * invN * by;
+                    dh = wE * invN * cp;
+                    float e = __fmul_rn(0.5f, __fmul_rn(om, om));
+                    e = fmaf(-cf.Jx, bx, e);
+                    e = fmaf(-cf.Jy, by, e);
+                    e = fmaf(cf.h, cp, e);
+                    de = wE * invN * e;
+                }
+                float vbk = 0.f, db = 0.f;
+                if (!first) {
+                    vbk = __fmul_rn(K.inv1pa, omb);
+                    gb = fmaf(K.inv1pa, omb, gb);
+                    db = __fadd_rn(f4get(v, i), g) * omb;
+                }
+                const float fb = __fmul_rn(K.hdt, gb);
+                dJx = fmaf(fb, -K.q * fmaf(S2.s[i], cx, -S2.c[i] * sx), dJx);
+                dJy = fmaf(fb, -K.q * fmaf(S2.s[i], cy, -S2.c[i] * sy), dJy);
+                dh = fmaf(fb, K.p * sinp, dh);
+                if (own_a) {
+                    aJx += dJx;
+                    aJy += dJy;
+                    ah += dh;
+                    abar += da;
+                    bbar += db;
+                    cbar = fmaf(gb, f4get(nz, i), cbar);
+                    eacc += de;
+                }
+                tbo[i] = tbi;
+                vbo[i] = vbk;
+                fbo[i] = fb;
+                cpo[i] = cp;
+            }
+            if (own_a) st4(vbO + row + x, make_float4(vbo[0], vbo[1], vbo[2], vbo[3]));
+            Fn = make_float4(fbo[0], fbo[1], fbo[2], fbo[3]);
+            tbpn = make_float4(tbo[0], tbo[1], tbo[2], tbo[3]);
+            cpn = make_float4(cpo[0], cpo[1], cpo[2], cpo[3]);
+            if (wide) {
+                if (lane == 0) s_fb[(t + 2 * Ly) & 1][warp][0] = Fn.x;
+                if (lane == 31) s_fb[(t + 2 * Ly) & 1][warp][1] = Fn.w;
+            }
+        }
+        if (wide) __syncthreads(); else __syncwarp();
+        // ---------------- phase B on row t - 1 (needs F-bar of rows t - 2, t - 1, t)
+        if (do_b) {
+            float sL, cL, sR, cR;
+            nbr_sc((t - 1 + 3 * Ly) % 3, S1, sL, cL, sR, cR);
+            float fL = __shfl_sync(kFullA, F1.w, srcL), fR = __shfl_sync(kFullA, F1.x, srcR);
+            if (wide) {
+                if (lane == 0) fL = s_fb[(t - 1 + 2 * Ly) & 1][wl][1];
+                if (lane == 31) fR = s_fb[(t - 1 + 2 * Ly) & 1][wr][0];
+            }
+            float out[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float sl = i == 0 ? sL : S1.s[i - 1], cl = i == 0 ? cL : S1.c[i - 1];
+                const float sr = i == 3 ? sR : S1.s[i + 1], cr = i == 3 ? cR : S1.c[i + 1];
+                const float fl = i == 0 ? fL : f4get(F1, i - 1), fr = i == 3 ? fR : f4get(F1, i + 1);
+                const float fj = f4get(F1, i);
+                const float kl = fmaf(S1.c[i], cl, S1.s[i] * sl), kr = fmaf(S1.c[i], cr, S1.s[i] * sr);
+                const float ku = fmaf(S1.c[i], S0.c[i], S1.s[i] * S0.s[i]);
+                const float kd = fmaf(S1.c[i], S2.c[i], S1.s[i] * S2.s[i]);
+                const float hx = fmaf(kl, fl - fj, kr * (fr - fj));
+                const float hy = fmaf(ku, f4get(F0, i) - fj, kd * (f4get(Fn, i) - fj));
+                float acc = q2 * fmaf(cf.Jx, hx, cf.Jy * hy);
+                acc = fmaf(hp2, f4get(cp1, i) * fj, acc);
+                out[i] = __fadd_rn(f4get(tbp1, i), acc);
+            }
+            if (active) st4(tbO + rowp(t - 1) + x, make_float4(out[0], out[1], out[2], out[3]));
+        }
+        // shift the windows
+        S0 = S1;
+        S1 = S2;
+        S2 = S3;
+        th2 = th3;
+        F0 = F1;
+        F1 = Fn;
+        tbp1 = tbpn;
+        cp1 = cpn;
+    }
+    // per-block FP64 accumulators in a fixed order
+    const double ceta = cf.eta_d > 0.0 ? (double)K.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
     double vals[kGacc] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta, eacc};
 #pragma unroll
     for (int k = 0; k < kGacc; ++k) {
@@ -467,24 +498,22 @@ __global__ void __launch_bounds__(256, MINB) adjoint_strip_kernel(const DevCfg* 
     __syncthreads();
     if (threadIdx.x < kGacc) {
         double acc = 0.0;
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) acc += s_red[threadIdx.x][w2];
+        for (int w2 = 0; w2 < n_warps; ++w2) acc += s_red[threadIdx.x][w2];
         R.gacc[(int64_t)(R.block_base + blockIdx.x) * kGacc + threadIdx.x] += acc;
     }
 }
 
-// R.doA / R.doB select the phases; split = true runs phase B and phase A as
-// two launches (fewer registers each) instead of one fused launch.
-cudaError_t launch_adjoint_strip(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, uint64_t seed,
-                                 RevArgs R, bool split, cudaStream_t st)
+cudaError_t launch_adjoint_band(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, uint64_t seed,
+                                BandArgs R, cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
-    const PhiloxKeys keys = philox_round_keys(seed);
-    if (R.doA && R.doB && !split) {
-        adjoint_strip_kernel<2, true, true><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, keys);
-        return cudaGetLastError();
+    const int threads = Lx > 128 ? (Lx / 128) * 32 : 256;
+    const int smem = (threads / 32) * 2 * 4 * 32 * (int)sizeof(float4);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(adjoint_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
     }
-    if (R.doB) adjoint_strip_kernel<4, false, true><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, keys);
-    if (R.doA) adjoint_strip_kernel<2, true, false><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, R, keys);
+    adjoint_band_kernel<<<(unsigned)n_tasks, threads, smem, st>>>(d_cfg, tasks, H, R, philox_round_keys(seed));
     return cudaGetLastError();
 }
 

@@ -1095,16 +1095,15 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     const int64_t T = L->total_sites;
     const int64_t nseg = (n + K - 1) / K;
     const int64_t R_ = n + 1;
-    // reverse kernels: strip decomposition where the shape allows it (fused
-    // reverse step), per-quad phase kernels otherwise
+    // reverse kernel: row bands where the shape allows it (phases A and B of a
+    // step in one launch), per-quad phase kernels otherwise
     struct AdjGroup {
         int Lx, Ly, H;
         uint64_t seed;
-        std::vector<StripTask> tasks;
-        StripTask* d_tasks = nullptr;
+        std::vector<BandTask> tasks;
+        BandTask* d_tasks = nullptr;
         int block_base = 0;
         int64_t n_lat = 0;
-        bool split = false;  // phase B and phase A as two launches
     };
     std::vector<AdjGroup> adj_groups;
     std::vector<int> adj_plain;
@@ -1116,24 +1115,38 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         cudaGetLastError();
         for (int c = 0; c < L->n_cfg; ++c) {
             const xy_config_desc& d = L->cfg[c].desc;
+            const bool wide_ok = d.Lx > 128 && d.Lx % 128 == 0 && d.Lx <= 2048;
+            const bool narrow_ok = d.Lx <= 128 && 32 % (d.Lx / 4) == 0;
+            if (!wide_ok && !narrow_ok) {
+                adj_plain.push_back(c);
+                continue;
+            }
             int64_t same = 0;
             for (int c2 = 0; c2 < L->n_cfg; ++c2)
                 if (L->cfg[c2].desc.Lx == d.Lx && L->cfg[c2].desc.Ly == d.Ly) same += L->cfg[c2].desc.n_replicas;
-            const int H = choose_strip_H(d.Lx, d.Ly, same, (int64_t)sms * 8);
-            if (H <= 0) {
-                adj_plain.push_back(c);
-                continue;
+            // band height: the largest H <= 64 dividing Ly that still gives 8
+            // warps per SM over the batch (each warp walks its rows serially)
+            const int warps_per_band = wide_ok ? d.Lx / 128 : 1;
+            const int groups = wide_ok ? 1 : 32 / (d.Lx / 4);
+            int H = 0;
+            for (int h : {64, 32, 16, 8, 4, 2, 1}) {
+                if (d.Ly % h != 0) continue;
+                if (H == 0) H = h;
+                const int64_t warps = same * (d.Ly / h) * warps_per_band / groups;
+                H = h;
+                if (warps >= (int64_t)sms * 8) break;
             }
             AdjGroup* g = nullptr;
             for (auto& gg : adj_groups)
                 if (gg.Lx == d.Lx && gg.Ly == d.Ly && gg.H == H && gg.seed == d.seed) g = &gg;
             if (!g) {
-                adj_groups.push_back(AdjGroup{d.Lx, d.Ly, H, d.seed, {}, nullptr, 0});
+                adj_groups.push_back(AdjGroup{d.Lx, d.Ly, H, d.seed, {}, nullptr, 0, 0});
                 g = &adj_groups.back();
             }
-            const int nu = strip_units_per_lattice(d.Lx, d.Ly, H);
+            const int nb = d.Ly / H;
+            const int per_block = wide_ok ? 1 : 8 * groups;
             for (int r = 0; r < d.n_replicas; ++r)
-                for (int u0 = 0; u0 < nu; u0 += 8) g->tasks.push_back(StripTask{c, r, u0, nu});
+                for (int b0 = 0; b0 < nb; b0 += per_block) g->tasks.push_back(BandTask{c, r, b0, nb});
             g->n_lat += d.n_replicas;
         }
         for (auto& g : adj_groups) {
@@ -1145,30 +1158,29 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
             n_blocks += adjoint_blocks(L->h_dev[c]);
         }
     }
-    float *ck = nullptr, *seg = nullptr, *tb = nullptr, *vb = nullptr, *Fb = nullptr;
+    float *ck = nullptr, *seg = nullptr, *adjb = nullptr, *Fb = nullptr;
     double2* arec = nullptr;
     double* gacc = nullptr;
     auto cleanup = [&]() {
         for (auto& g : adj_groups) cudaFree(g.d_tasks);
         cudaFree(ck);
         cudaFree(seg);
-        cudaFree(tb);
-        cudaFree(vb);
+        cudaFree(adjb);
         cudaFree(Fb);
         cudaFree(arec);
         cudaFree(gacc);
     };
     cudaError_t e = cudaMalloc(&ck, sizeof(float) * 2 * T * nseg);
     if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * 2 * T * (K + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&tb, sizeof(float) * T);
-    if (e == cudaSuccess) e = cudaMalloc(&vb, sizeof(float) * T);
-    if (e == cudaSuccess) e = cudaMalloc(&Fb, sizeof(float) * 2 * T);
+    // adjoint state, double-buffered: (tb, vb) of two time levels
+    if (e == cudaSuccess) e = cudaMalloc(&adjb, sizeof(float) * 4 * T);
+    if (e == cudaSuccess && !adj_plain.empty()) e = cudaMalloc(&Fb, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&arec, sizeof(double2) * L->B * R_);
     for (auto& g : adj_groups) {
         if (e != cudaSuccess) break;
-        e = cudaMalloc(&g.d_tasks, sizeof(StripTask) * g.tasks.size());
+        e = cudaMalloc(&g.d_tasks, sizeof(BandTask) * g.tasks.size());
         if (e == cudaSuccess)
-            e = cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(StripTask) * g.tasks.size(), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(BandTask) * g.tasks.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&gacc, sizeof(double) * kGacc * n_blocks);
     if (e != cudaSuccess) {
@@ -1230,139 +1242,63 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         L->h_dev[c].rec_first = k0;
     }
     RCA(upload_cfg(L));
-    CKA(cudaMemsetAsync(tb, 0, state_bytes, L->stream));
-    CKA(cudaMemsetAsync(vb, 0, state_bytes, L->stream));
-    CKA(cudaMemsetAsync(Fb, 0, 2 * state_bytes, L->stream));
+    CKA(cudaMemsetAsync(adjb, 0, 4 * state_bytes, L->stream));
     CKA(cudaMemsetAsync(gacc, 0, sizeof(double) * kGacc * n_blocks, L->stream));
-    int fcur = 0;  // F-bar ping-pong: Fb + fcur * T holds F-bar of the last phase A
-    // one reverse launch: phase B of step kA + 1 (states at slot iB) and phase A
-    // of step kA (slot iA); either may be off
-    auto rev_launch = [&](bool doA, bool doB, int64_t kA, int64_t iA, int64_t iB) -> int {
-        RevArgs R{};
-        R.thB = seg + 2 * T * iB;
-        R.FbIn = Fb + (int64_t)fcur * T;
-        R.thA = seg + 2 * T * iA;
-        R.vA = seg + 2 * T * iA + T;
-        R.tb = tb;
-        R.vb = vb;
-        R.FbOut = Fb + (int64_t)(1 - fcur) * T;
-        R.rec = arec;
-        R.rec_stride = R_;
-        R.kA = kA;
-        R.k0 = k0;
-        R.wE = (float)wE;
-        R.wM = (float)wM;
-        R.doA = doA;
-        R.doB = doB;
-        R.gacc = gacc;
+    int acur = 0;  // adjoint state of step k + 1 in slot acur, of step k written to slot 1 - acur
+    auto tb_of = [&](int slot) { return adjb + (int64_t)slot * 2 * T; };
+    auto vb_of = [&](int slot) { return adjb + (int64_t)slot * 2 * T + T; };
+    // reverse step k from the states at segment slot i
+    auto rev_step = [&](int64_t k, int64_t i) -> int {
+        const float* th = seg + 2 * T * i;
+        const float* om = seg + 2 * T * i + T;
         for (auto& g : adj_groups) {
-            R.block_base = g.block_base;
-            CK(launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, g.split, L->stream));
-            L->launches += (g.split && doA && doB) ? 2 : 1;
-        }
-        for (int c : adj_plain) {
-            if (doB) {
-                AdjArgs a{};
-                a.theta = R.thB;
-                a.tb = tb;
-                a.Fb = Fb + (int64_t)fcur * T;
-                CK(launch_adjoint_phase_b(L->d_cfg, L->h_dev[c], a, L->stream));
-                ++L->launches;
-            }
-            if (doA) {
-                AdjArgs a{};
-                a.theta = R.thA;
-                a.omega = R.vA;
-                a.tb = tb;
-                a.vb = vb;
-                a.Fb = Fb + (int64_t)(1 - fcur) * T;
-                a.rec = arec;
-                a.rec_stride = R_;
-                a.k = kA;
-                a.k0 = k0;
-                a.k_end = k0 + n;
-                a.wE = wE;
-                a.wM = wM;
-                a.inv_norm = inv_norm;
-                a.gacc = gacc;
-                CK(launch_adjoint_phase_a(L->d_cfg, L->h_dev[c], block_base[c], a, L->stream));
-                ++L->launches;
-            }
-        }
-        if (doA) fcur = 1 - fcur;
-        return XY_OK;
-    };
-    // fused or split reverse launches per strip group: timed once on scratch
-    // outputs with the first segment's states (the kernels' cost does not
-    // depend on the data), cached per GPU and shape
-    auto tune_reverse = [&]() -> int {
-        const std::string gpu = gpu_name();
-        float *s_tb = nullptr, *s_vb = nullptr, *s_fb = nullptr;
-        double* s_g = nullptr;
-        bool need = false;
-        for (auto& g : adj_groups) {
-            char key[256];
-            snprintf(key, sizeof key, "%s|adjrev|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
-            int sp = 0, dummy = 0;
-            if (g_tune.get(key, &sp, &dummy)) g.split = sp != 0;
-            else need = true;
-        }
-        if (!need || T < 2) return XY_OK;
-        cudaError_t e2 = cudaMalloc(&s_tb, sizeof(float) * 3 * T);
-        if (e2 == cudaSuccess) e2 = cudaMalloc(&s_g, sizeof(double) * kGacc * n_blocks);
-        if (e2 != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(s_tb);
-            return XY_OK;  // no scratch: keep the fused launch
-        }
-        s_vb = s_tb + T;
-        s_fb = s_tb + 2 * T;
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        for (auto& g : adj_groups) {
-            char key[256];
-            snprintf(key, sizeof key, "%s|adjrev|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
-            int sp = 0, dummy = 0;
-            if (g_tune.get(key, &sp, &dummy)) continue;
-            RevArgs R{};
-            R.thB = seg + 2 * T;
-            R.FbIn = s_fb;
-            R.thA = seg;
-            R.vA = seg + T;
-            R.tb = s_tb;
-            R.vb = s_vb;
-            R.FbOut = s_fb;
+            BandArgs R{};
+            R.theta = th;
+            R.omega = om;
+            R.tb_in = tb_of(acur);
+            R.vb_in = vb_of(acur);
+            R.tb_out = tb_of(1 - acur);
+            R.vb_out = vb_of(1 - acur);
             R.rec = arec;
             R.rec_stride = R_;
-            R.kA = k0;
+            R.k = k;
             R.k0 = k0;
             R.wE = (float)wE;
             R.wM = (float)wM;
-            R.doA = 1;
-            R.doB = 1;
-            R.gacc = s_g;
+            R.gacc = gacc;
             R.block_base = g.block_base;
-            float best[2] = {0.f, 0.f};
-            for (int v = 0; v < 2; ++v) {
-                launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, v == 1, L->stream);
-                cudaEventRecord(e0, L->stream);
-                for (int i = 0; i < 3; ++i)
-                    launch_adjoint_strip(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.seed, R, v == 1, L->stream);
-                cudaEventRecord(e1, L->stream);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&best[v], e0, e1);
-                L->launches += v == 1 ? 8 : 4;
-            }
-            g.split = best[1] < best[0];
-            g_tune.put(key, g.split ? 1 : 0, 0);
+            CK(launch_adjoint_band(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.H, g.seed, R, L->stream));
+            ++L->launches;
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaFree(s_tb);
-        cudaFree(s_g);
-        const cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess) return fail(XY_ECUDA, "reverse tuning: %s", cudaGetErrorString(le));
+        for (int c : adj_plain) {
+            // per-quad kernels update in place: carry this configuration's adjoint
+            // state into the output slot first, then phase A and phase B of step k
+            const DevCfg& d = L->h_dev[c];
+            const size_t off = (size_t)d.offset, cnt = (size_t)d.N * d.n_rep;
+            CK(cudaMemcpyAsync(tb_of(1 - acur) + off, tb_of(acur) + off, sizeof(float) * cnt,
+                               cudaMemcpyDeviceToDevice, L->stream));
+            CK(cudaMemcpyAsync(vb_of(1 - acur) + off, vb_of(acur) + off, sizeof(float) * cnt,
+                               cudaMemcpyDeviceToDevice, L->stream));
+            AdjArgs a{};
+            a.theta = th;
+            a.omega = om;
+            a.tb = tb_of(1 - acur);
+            a.vb = vb_of(1 - acur);
+            a.Fb = Fb;
+            a.rec = arec;
+            a.rec_stride = R_;
+            a.k = k;
+            a.k0 = k0;
+            a.k_end = k0 + n;
+            a.wE = wE;
+            a.wM = wM;
+            a.inv_norm = inv_norm;
+            a.gacc = gacc;
+            CK(launch_adjoint_phase_a(L->d_cfg, d, block_base[c], a, L->stream));
+            CK(launch_adjoint_phase_b(L->d_cfg, d, a, L->stream));
+            L->launches += 2;
+        }
+        acur = 1 - acur;
         return XY_OK;
     };
     for (int64_t s = nseg - 1; s >= 0; --s) {
@@ -1411,14 +1347,9 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
             }
         }
         RCA(spr.close());
-        if (s == nseg - 1) RCA(tune_reverse());
-        // reverse: A(top); B(i) A(i-1) for i = top..1; B(0)
         Span sv{L};
         RCA(sv.open(XY_KCLASS_ADJ_REV));
-        const int64_t top = n_states - 1;
-        RCA(rev_launch(true, false, ks + top, top, top));
-        for (int64_t i = top; i >= 1; --i) RCA(rev_launch(true, true, ks + i - 1, i - 1, i));
-        RCA(rev_launch(false, true, ks - 1, 0, 0));
+        for (int64_t i = n_states - 1; i >= 0; --i) RCA(rev_step(ks + i, i));
         RCA(sv.close());
     }
     std::vector<double2> hrec((size_t)L->B * R_);

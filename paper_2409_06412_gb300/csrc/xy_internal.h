@@ -155,26 +155,29 @@ cudaError_t launch_adjoint_phase_a(const DevCfg* d_cfg, const DevCfg& h_cfg, int
 cudaError_t launch_adjoint_phase_b(const DevCfg* d_cfg, const DevCfg& h_cfg, AdjArgs a, cudaStream_t st);
 int adjoint_blocks(const DevCfg& h_cfg);
 
-// Fused reverse step on strip tasks: phase B of step kA + 1 and phase A of step kA.
 constexpr int kGacc = 7;  // per-block accumulators of the reverse sweep
 
-struct RevArgs {
-    const float* thB;    // theta_{kA+1}
-    const float* FbIn;   // F-bar_{kA+1}
-    const float* thA;    // theta_{kA}
-    const float* vA;     // v_{kA}
-    float* tb;           // adjoint of theta (in place)
-    float* vb;           // adjoint of v (in place)
-    float* FbOut;        // F-bar_{kA}
-    const double2* rec;  // forward observables [B][R]
+// Reverse step on row bands: phases A and B of step k in one launch.
+struct BandTask {
+    int32_t cfg, rep;
+    int32_t band0;    // first band of the block
+    int32_t n_bands;  // bands of the lattice
+};
+struct BandArgs {
+    const float* theta;  // theta_k
+    const float* omega;  // v_k
+    const float* tb_in;  // adjoints of (theta_{k+1}, v_{k+1})
+    const float* vb_in;
+    float* tb_out;       // adjoints of (theta_k, v_k)
+    float* vb_out;
+    const double2* rec;
     int64_t rec_stride;
-    int64_t kA, k0;
+    int64_t k, k0;
     float wE, wM;
-    int doA, doB;
-    double* gacc;        // [blocks][7]
+    double* gacc;        // [blocks][kGacc]
     int block_base;
 };
-cudaError_t launch_adjoint_strip(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, uint64_t seed,
-                                 RevArgs R, bool split, cudaStream_t st);
+cudaError_t launch_adjoint_band(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, uint64_t seed,
+                                BandArgs R, cudaStream_t st);
 
 }  // namespace xy
