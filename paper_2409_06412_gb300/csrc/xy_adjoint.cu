@@ -279,6 +279,9 @@ __device__ __forceinline__ void band_sc(float q, const float4& t, BandSC& r)
 
 }  // namespace
 
+// WIDE: Lx > 128 (a block spans one band of Lx / 128 strips); OBS: k > k0
+// (the step is observed; k = k0 holds omega_{k0} fixed instead).
+template <bool WIDE, bool OBS>
 __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs, const BandTask* tasks, int H,
                                                               BandArgs R, PhiloxKeys keys)
 {
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     const BandTask task = tasks[blockIdx.x];
     const DevCfg& cf = cfgs[task.cfg];
     const int Lx = cf.Lx, Ly = cf.Ly;
-    const bool wide = Lx > 128;                        // the block is one band spanning Lx / 128 warps
+    constexpr bool wide = WIDE;
     const int G = Lx >= 128 ? 32 : (Lx >> 2);
     const int groups = 32 / G;
     const int grp = lane / G, lg = lane - grp * G;
@@ -315,13 +318,18 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     const StepConst K = step_const(cf, noise_amp(cf, R.k));
     const float q2 = __fmul_rn(K.q, K.q), hp2 = __fmul_rn(cf.hp, cf.p);
     const float invN = 1.0f / (float)cf.N, wE = R.wE, wM = R.wM;
-    const bool observe = R.k > R.k0, first = R.k == R.k0;
+    constexpr bool observe = OBS, first = !OBS;
     const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
     float sgnM = 0.f;
     if (observe && R.wM != 0.f) {
         const double M = R.rec[(int64_t)(cf.b_first + task.rep) * R.rec_stride + (R.k - R.k0)].x;
         sgnM = M > 0.0 ? 1.f : (M < 0.0 ? -1.f : 0.f);
     }
+    // configuration constants in registers (the cp.async statements clobber
+    // memory, which would otherwise reload them from the descriptor every row)
+    const float Jx = cf.Jx, Jy = cf.Jy, hF = cf.h;
+    const bool stag = cf.stag != 0;
+    const float wEn = wE * invN, wMs = wM * invN * sgnM * K.q;
     float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f, eacc = 0.f;
 
     // window: S0 = row t-2, S1 = t-1, S2 = t, S3 = t+1; F0 = F-bar(t-2), F1 = t-1, F2 = t
@@ -403,18 +411,18 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
                 const float by = fmaf(S2.c[i], S3.c[i], S2.s[i] * S3.s[i]);
                 float da = -om * vbt, dJx = 0.f, dJy = 0.f, dh = 0.f, de = 0.f;
                 if (observe) {
-                    omb = fmaf(wE * invN, om, omb);
-                    tbi = fmaf(-wE * invN, F, tbi);
-                    const float sigma = (cf.stag && ((x + i + t) & 1)) ? -1.f : 1.f;
-                    tbi = fmaf(wM * invN * sgnM * sigma * K.q, S2.c[i], tbi);
-                    dJx = -wE * invN * bx;
-                    dJy = -wE * invN * by;
-                    dh = wE * invN * cp;
+                    omb = fmaf(wEn, om, omb);
+                    tbi = fmaf(-wEn, F, tbi);
+                    const float sigma = (stag && ((x + i + t) & 1)) ? -wMs : wMs;
+                    tbi = fmaf(sigma, S2.c[i], tbi);
+                    dJx = -wEn * bx;
+                    dJy = -wEn * by;
+                    dh = wEn * cp;
                     float e = __fmul_rn(0.5f, __fmul_rn(om, om));
-                    e = fmaf(-cf.Jx, bx, e);
-                    e = fmaf(-cf.Jy, by, e);
-                    e = fmaf(cf.h, cp, e);
-                    de = wE * invN * e;
+                    e = fmaf(-Jx, bx, e);
+                    e = fmaf(-Jy, by, e);
+                    e = fmaf(hF, cp, e);
+                    de = wEn * e;
                 }
                 float vbk = 0.f, db = 0.f;
                 if (!first) {
@@ -471,7 +479,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
                 const float kd = fmaf(S1.c[i], S2.c[i], S1.s[i] * S2.s[i]);
                 const float hx = fmaf(kl, fl - fj, kr * (fr - fj));
                 const float hy = fmaf(ku, f4get(F0, i) - fj, kd * (f4get(Fn, i) - fj));
-                float acc = q2 * fmaf(cf.Jx, hx, cf.Jy * hy);
+                float acc = q2 * fmaf(Jx, hx, Jy * hy);
                 acc = fmaf(hp2, f4get(cp1, i) * fj, acc);
                 out[i] = __fadd_rn(f4get(tbp1, i), acc);
             }
@@ -507,13 +515,17 @@ cudaError_t launch_adjoint_band(const DevCfg* d_cfg, const BandTask* tasks, int 
                                 BandArgs R, cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
-    const int threads = Lx > 128 ? (Lx / 128) * 32 : 256;
+    const bool wide = Lx > 128;
+    const int threads = wide ? (Lx / 128) * 32 : 256;
     const int smem = (threads / 32) * 2 * 4 * 32 * (int)sizeof(float4);
+    const bool obs = R.k > R.k0;
+    auto kern = wide ? (obs ? adjoint_band_kernel<true, true> : adjoint_band_kernel<true, false>)
+                     : (obs ? adjoint_band_kernel<false, true> : adjoint_band_kernel<false, false>);
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(adjoint_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    adjoint_band_kernel<<<(unsigned)n_tasks, threads, smem, st>>>(d_cfg, tasks, H, R, philox_round_keys(seed));
+    kern<<<(unsigned)n_tasks, threads, smem, st>>>(d_cfg, tasks, H, R, philox_round_keys(seed));
     return cudaGetLastError();
 }
 
