@@ -55,6 +55,13 @@ __device__ __forceinline__ double warp_sum_a(double v)
     return v;
 }
 
+__device__ __forceinline__ float warp_sumf_a(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullA, v, o);
+    return v;
+}
+
 }  // namespace
 
 int adjoint_blocks(const DevCfg& h)
@@ -281,11 +288,16 @@ __device__ __forceinline__ void band_sc(float q, const float4& t, BandSC& r)
 
 // WIDE: Lx > 128 (a block spans one band of Lx / 128 strips); OBS: k > k0
 // (the step is observed; k = k0 holds omega_{k0} fixed instead).
-template <bool WIDE, bool OBS>
+// NZ: regenerate the noise n_k from the counter-based stream.  Without it the
+// step's noise term comes from the stored half-step velocities: in the BBK
+// leapfrog omega_k = (v_k + v_{k+1}) / 2 exactly, g_k = v_{k+1} - (1 - a)
+// omega_k and c_k n_k = g_k - (dt/2) F_k, which costs one more row read and
+// saves the Philox rounds and the Box-Muller transform of every site.
+template <bool WIDE, bool OBS, bool NZ>
 __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs, const BandTask* tasks, int H,
                                                               BandArgs R, PhiloxKeys keys)
 {
-    // per warp, two stages of [theta(t+1), v(t), tb(t), vb(t)] for its 32 lanes
+    // per warp, two stages of [theta(t+1), v(t), tb(t), vb(t), v_{k+1}(t)] for its 32 lanes
     extern __shared__ float4 s_stage[];
     // edge exchange: [slot][warp][side]  side 0 = left edge (site x0), 1 = right edge (site x0 + 127)
     __shared__ float2 s_sc[3][kMaxBandWarps][2];
@@ -353,13 +365,17 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
             if (lane == 31) { const float2 e = s_sc[slot][wr][0]; sR = e.x; cR = e.y; }
         }
     };
-    float4* my_stage = s_stage + (size_t)warp * 2 * 4 * 32;
-    auto prefetch = [&](int st, int t) {  // theta of row t + 1 and v, tb, vb of row t into stage st
-        float4* p = my_stage + st * 4 * 32;
+    constexpr int kStage = (NZ ? 4 : 5) * 32;  // float4 per warp and stage
+    const float* vN = NZ ? nullptr : R.vnext + lat_off;
+    float4* my_stage = s_stage + (size_t)warp * 2 * kStage;
+    auto prefetch = [&](int st, int t) {  // theta of row t + 1 and v, tb, vb (v_{k+1}) of row t into stage st
+        float4* p = my_stage + st * kStage;
+        const int64_t r0 = rowp(t);
         cp_async16(p + 0 * 32 + lane, th + rowp(t + 1) + x);
-        cp_async16(p + 1 * 32 + lane, vv + rowp(t) + x);
-        cp_async16(p + 2 * 32 + lane, tbI + rowp(t) + x);
-        cp_async16(p + 3 * 32 + lane, vbI + rowp(t) + x);
+        cp_async16(p + 1 * 32 + lane, vv + r0 + x);
+        cp_async16(p + 2 * 32 + lane, tbI + r0 + x);
+        cp_async16(p + 3 * 32 + lane, vbI + r0 + x);
+        if (!NZ) cp_async16(p + 4 * 32 + lane, vN + r0 + x);
         cp_async_commit();
     };
     band_sc(K.q, ld4(th + rowp(y0 - 2) + x), S1);
@@ -374,7 +390,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
         const int st = (t - y0 + 1) & 1;
         prefetch(st ^ 1, t + 1);
         cp_async_wait1();  // this lane's copies of stage st have landed
-        const float4* sp = my_stage + st * 4 * 32;
+        const float4* sp = my_stage + st * kStage;
         const float4 th3 = sp[0 * 32 + lane];
         band_sc(K.q, th3, S3);
         publish_sc((t + 1 + 3 * Ly) % 3, S3);
@@ -387,8 +403,13 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
             const float4 vb4 = sp[3 * 32 + lane];
             float sL, cL, sR, cR;
             nbr_sc((t + 3 * Ly) % 3, S2, sL, cL, sR, cR);
-            const uint32_t quad = (uint32_t)((row + x) >> 2);
-            const float4 nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.k, 0u), keys), 1.0f);
+            float4 nz, v1;
+            if (NZ) {
+                const uint32_t quad = (uint32_t)((row + x) >> 2);
+                nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.k, 0u), keys), K.c);
+            } else {
+                v1 = sp[4 * 32 + lane];
+            }
             float tbo[4], vbo[4], fbo[4], cpo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -400,9 +421,16 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
                 const float sinp = __sinf(__fmul_rn(K.p, tht));
                 const float cp = __cosf(__fmul_rn(K.p, tht));
                 const float F = site_force(K, S2.s[i], S2.c[i], sx, cx, sy, cy, sinp);
-                const float cn = __fmul_rn(K.c, f4get(nz, i));
-                const float g = fmaf(K.hdt, F, cn);
-                const float om = __fmul_rn(__fadd_rn(f4get(v, i), g), K.inv1pa);
+                float cn, g, om;  // c_k n_k, g_k, omega_k
+                if (NZ) {
+                    cn = f4get(nz, i);
+                    g = fmaf(K.hdt, F, cn);
+                    om = __fmul_rn(__fadd_rn(f4get(v, i), g), K.inv1pa);
+                } else {
+                    om = 0.5f * (f4get(v, i) + f4get(v1, i));
+                    g = f4get(v1, i) - K.oma * om;
+                    cn = g - K.hdt * F;
+                }
                 const float vbt = fmaf(K.dt, f4get(tb4, i), f4get(vb4, i));
                 float omb = __fmul_rn(K.oma, vbt);
                 float gb = vbt;
@@ -440,7 +468,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
                     ah += dh;
                     abar += da;
                     bbar += db;
-                    cbar = fmaf(gb, f4get(nz, i), cbar);
+                    cbar = fmaf(gb, cn, cbar);
                     eacc += de;
                 }
                 tbo[i] = tbi;
@@ -495,18 +523,21 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
         tbp1 = tbpn;
         cp1 = cpn;
     }
-    // per-block FP64 accumulators in a fixed order
-    const double ceta = cf.eta_d > 0.0 ? (double)K.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
-    double vals[kGacc] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta, eacc};
+    // per-block accumulators: FP32 warp butterflies (a warp covers a few
+    // thousand sites), the warps and the steps combined in FP64 in a fixed order
+    const float vals[kGacc] = {aJx, aJy, ah, abar, bbar, cbar, eacc};
 #pragma unroll
     for (int k = 0; k < kGacc; ++k) {
-        const double w = warp_sum_a(vals[k]);
+        const float w = warp_sumf_a(vals[k]);
         if (lane == 0) s_red[k][warp] = w;
     }
     __syncthreads();
     if (threadIdx.x < kGacc) {
         double acc = 0.0;
         for (int w2 = 0; w2 < n_warps; ++w2) acc += s_red[threadIdx.x][w2];
+        // c-bar (summed against c_k n_k) enters the eta gradient through
+        // d c_k / d eta = c_k / (2 eta)
+        if (threadIdx.x == 5) acc *= cf.eta_d > 0.0 ? 1.0 / (2.0 * cf.eta_d) : 0.0;
         R.gacc[(int64_t)(R.block_base + blockIdx.x) * kGacc + threadIdx.x] += acc;
     }
 }
@@ -517,10 +548,17 @@ cudaError_t launch_adjoint_band(const DevCfg* d_cfg, const BandTask* tasks, int 
     if (n_tasks == 0) return cudaSuccess;
     const bool wide = Lx > 128;
     const int threads = wide ? (Lx / 128) * 32 : 256;
-    const int smem = (threads / 32) * 2 * 4 * 32 * (int)sizeof(float4);
+    const bool nz = R.vnext == nullptr;
+    const int smem = (threads / 32) * 2 * (nz ? 4 : 5) * 32 * (int)sizeof(float4);
     const bool obs = R.k > R.k0;
-    auto kern = wide ? (obs ? adjoint_band_kernel<true, true> : adjoint_band_kernel<true, false>)
-                     : (obs ? adjoint_band_kernel<false, true> : adjoint_band_kernel<false, false>);
+    using Kern = void (*)(const DevCfg*, const BandTask*, int, BandArgs, PhiloxKeys);
+    static const Kern table[2][2][2] = {
+        {{adjoint_band_kernel<false, false, false>, adjoint_band_kernel<false, false, true>},
+         {adjoint_band_kernel<false, true, false>, adjoint_band_kernel<false, true, true>}},
+        {{adjoint_band_kernel<true, false, false>, adjoint_band_kernel<true, false, true>},
+         {adjoint_band_kernel<true, true, false>, adjoint_band_kernel<true, true, true>}},
+    };
+    const Kern kern = table[wide][obs][nz];
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;

@@ -206,10 +206,12 @@ struct xy_lattice {
     bool autotune = true;
     struct Graph {
         int chunk;
+        int rec;
         cudaGraphExec_t exec;
         int64_t kernels;
     };
-    std::vector<Graph> graphs;  // captured chunks, by chunk length
+    std::vector<Graph> graphs;  // captured chunks, by chunk length and recording
+    int cur_rec = 0;            // records of the current window: 0 none, 1 M, 2 M and E
     // kernel timing (direct launches bracketed by events)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
@@ -370,8 +372,8 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     for (int i = 0; i < cnt; ++i) {
         for (auto& g : L->strip_groups) {
             if ((rc = timed_begin(L, st, XY_KCLASS_STRIP, &end))) return rc;
-            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, g.seed, jl0 + i, buf,
-                                 L->d_call, L->pa, st));
+            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, L->cur_rec, g.seed,
+                                 jl0 + i, buf, L->d_call, L->pa, st));
             if ((rc = timed_end(end, st))) return rc;
             ++L->launches;
         }
@@ -394,7 +396,7 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
 int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
     for (auto& g : L->graphs)
-        if (g.chunk == chunk) {
+        if (g.chunk == chunk && g.rec == L->cur_rec) {
             *out = &g;
             return XY_OK;
         }
@@ -414,7 +416,7 @@ int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    L->graphs.push_back({chunk, exec, kernels});
+    L->graphs.push_back({chunk, L->cur_rec, exec, kernels});
     *out = &L->graphs.back();
     return XY_OK;
 }
@@ -472,6 +474,9 @@ int autotune_lattice(xy_lattice* L)
         snprintf(key, sizeof key, "%s|strip|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
         int bh = 0, bv = 0;
         if (!g_tune.get(key, &bh, &bv)) {
+            // per candidate: the best of 5 timings, each over enough launches
+            // to span about half a millisecond (single launches of a small
+            // batch differ by less than their timing noise)
             float best = 1e30f;
             for (int H : {8, 16, 32, 64}) {
                 const int groups = g.Lx >= 128 ? 1 : 32 / (g.Lx / 4);
@@ -479,25 +484,33 @@ int autotune_lattice(xy_lattice* L)
                 if (strip_units_per_lattice(g.Lx, g.Ly, H) > L->pa.max_units) continue;
                 g.H = H;
                 if ((rc = build_strip_tasks(L, g))) break;
-                for (int v : {2, 3, 4}) {
-                    const int nt = (int)g.tasks.size();
-                    CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, g.seed, 0, buf, L->d_call, L->pa,
-                                         L->stream));
-                    CK(cudaEventRecord(e0, L->stream));
-                    for (int i = 0; i < 3; ++i)
-                        CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, g.seed, 0, buf, L->d_call, L->pa,
+                const int nt = (int)g.tasks.size();
+                float t_best[3] = {1e30f, 1e30f, 1e30f};
+                int reps = 3;
+                for (int round = 0; round < 5; ++round)
+                    for (int vi = 0; vi < 3; ++vi) {
+                        const int v = 2 + vi;
+                        CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, g.seed, 0, buf, L->d_call, L->pa,
                                              L->stream));
-                    CK(cudaEventRecord(e1, L->stream));
-                    CK(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, e0, e1));
-                    L->launches += 4;
-                    if (ms < best) {
-                        best = ms;
-                        bh = H;
-                        bv = v;
+                        CK(cudaEventRecord(e0, L->stream));
+                        for (int i = 0; i < reps; ++i)
+                            CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, g.seed, 0, buf, L->d_call,
+                                                 L->pa, L->stream));
+                        CK(cudaEventRecord(e1, L->stream));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        L->launches += 1 + reps;
+                        t_best[vi] = std::min(t_best[vi], ms / reps);
+                        if (round == 0 && vi == 0 && ms < 0.5f)
+                            reps = std::min(64, (int)(0.5f / std::max(ms / reps, 1e-3f)) + 1);
                     }
-                }
+                for (int vi = 0; vi < 3; ++vi)
+                    if (t_best[vi] < best) {
+                        best = t_best[vi];
+                        bh = H;
+                        bv = 2 + vi;
+                    }
             }
             if (rc) break;
             if (bh > 0) g_tune.put(key, bh, bv);
@@ -640,6 +653,7 @@ int advance_core(xy_lattice* L, int64_t n, int record_every, double2* rec_dev, i
     ca.fixed_parity = 0;
     ca.m_only = m_only ? 1 : 0;
     if ((rc = upload_call(L, ca))) return rc;
+    L->cur_rec = record_every > 0 ? (m_only ? 1 : 2) : 0;
     if ((rc = run_window(L, n_max))) return rc;
     if ((rc = fixup_parity(L))) return rc;
     if (do_moments && record_every > 0) {
@@ -1259,6 +1273,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
             R.vb_in = vb_of(acur);
             R.tb_out = tb_of(1 - acur);
             R.vb_out = vb_of(1 - acur);
+            // v_{k+1} is slot i + 1 of the segment for every step but k0 + n
+            R.vnext = k < k0 + n ? seg + 2 * T * (i + 1) + T : nullptr;
             R.rec = arec;
             R.rec_stride = R_;
             R.k = k;
@@ -1336,7 +1352,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                     ++L->launches;
                 }
                 for (auto& g : L->strip_groups) {
-                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, g.seed, i,
+                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, 1, g.seed, i,
                                           buf, L->d_call, L->pa, L->stream));
                     ++L->launches;
                 }

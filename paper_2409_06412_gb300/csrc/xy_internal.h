@@ -108,8 +108,9 @@ cudaError_t launch_omega_full(const DevCfg* d_cfg, const DevCfg& h_cfg, int rep_
                               const float* theta, const float* omega, float* out, cudaStream_t st);
 cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h_cfg, int64_t j_local, Buffers buf,
                               const CallArgs* ca, Partials pa, int write_state, cudaStream_t st);
+// rec: 0 = no records in this launch, 1 = records of M only, 2 = M and E
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
-                              uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
+                              int rec, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
                               cudaStream_t st);
 cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
                                  int threads, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
@@ -170,6 +171,7 @@ struct BandArgs {
     const float* vb_in;
     float* tb_out;       // adjoints of (theta_k, v_k)
     float* vb_out;
+    const float* vnext;  // v_{k+1}, or null: the noise of step k is regenerated
     const double2* rec;
     int64_t rec_stride;
     int64_t k, k0;

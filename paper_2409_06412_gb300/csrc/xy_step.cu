@@ -83,11 +83,23 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// FP32 warp sum in the same order.  A warp's partial covers at most a few
+// thousand sites, each term of magnitude O(1), so FP32 keeps it to ~1e-6
+// relative; the partials of different warps and blocks are combined in FP64.
+// (FP64 issues at a small fraction of the FP32 rate on this GPU, so a double
+// butterfly per warp and per step is not free.)
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
 // Commit one unit's (M, E) partial of lattice b; the unit that arrives last
 // sums all partials of the lattice in a fixed order and writes the record.
 // Must be called by a whole warp (lane 0 holds the partial).
 __device__ void commit_partial(Partials pa, int64_t b, int unit, int n_units, double pm, double pe,
-                               double2* rec_slot, double invN)
+                               double2* rec_slot, int64_t N)
 {
     const int lane = threadIdx.x & 31;
     int last = 0;
@@ -109,7 +121,7 @@ __device__ void commit_partial(Partials pa, int64_t b, int unit, int n_units, do
     sm = warp_sum(sm);
     se = warp_sum(se);
     if (lane == 0) {
-        *rec_slot = make_double2(sm * invN, se * invN);
+        *rec_slot = make_double2(sm / (double)N, se / (double)N);
         pa.count[b] = 0u;
     }
 }
@@ -304,9 +316,9 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
         }
     }
     if (!rec) return;
-    // block partial: per-warp FP64 butterfly, then warp 0 sums the warps in order
+    // block partial: per-warp FP32 butterfly, then warp 0 sums the warps in FP64 in order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double wm = warp_sum((double)pm), we = warp_sum((double)pe);
+    const double wm = warp_sumf(pm), we = warp_sumf(pe);
     if (lane == 0) {
         s_red[0][warp] = wm;
         s_red[1][warp] = we;
@@ -321,7 +333,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
             }
         const int64_t b = cf.b_first + rep;
         const int64_t r = (k - cf.rec_first) / ca.record_every;
-        commit_partial(pa, b, unit, bpl, bm, be, ca.rec_dev + b * ca.rec_stride + r, 1.0 / (double)cf.N);
+        commit_partial(pa, b, unit, bpl, bm, be, ca.rec_dev + b * ca.rec_stride + r, cf.N);
     }
 }
 
@@ -363,17 +375,19 @@ struct StripCtx {
     float* __restrict__ thD;
     float* __restrict__ omD;
     int Lx, Ly, x, xe, srcL, srcR, lg;
-    bool multi, rec, rec_e;
+    bool multi, rec;
     uint32_t cfgrep;
     int64_t k;
     StepConst K;
+    float Jx, Jy, hF;  // energy constants in registers (stores may alias the descriptor)
+    bool stag;
     float pm, pe;
 };
 
 // All rows of the unit, one row per iteration with a sliding window of three
 // rows of (sin q t, cos q t); the raw angles run two rows ahead.  Row
 // pointers advance by Lx per row and wrap at the lattice end.
-template <bool REC>
+template <int REC>
 __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const PhiloxKeys& keys, int ybeg, int H)
 {
     const int64_t Lx = X.Lx;
@@ -430,13 +444,22 @@ __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const 
             const SiteOut so = site_update(X.K, th, f4get(v, s), F, f4get(cn, s));
             to[s] = so.theta;
             vo[s] = so.v;
-            if (REC) {
-                const float sigma = (cf.stag && ((X.x + s + y) & 1)) ? -1.f : 1.f;
-                X.pm = fmaf(sigma, C.s[s], X.pm);
-                if (X.rec_e)
-                    X.pe = __fadd_rn(X.pe, site_energy(cf, so.omega, C.s[s], C.c[s], sr, cr, N.s[s], N.c[s],
-                                                       cosp_of(X.K.p, th)));
+            if (REC == 2) {
+                const float bx = fmaf(C.c[s], cr, __fmul_rn(C.s[s], sr));
+                const float by = fmaf(C.c[s], N.c[s], __fmul_rn(C.s[s], N.s[s]));
+                float e = __fmul_rn(0.5f, __fmul_rn(so.omega, so.omega));
+                e = fmaf(-X.Jx, bx, e);
+                e = fmaf(-X.Jy, by, e);
+                e = fmaf(X.hF, cosp_of(X.K.p, th), e);
+                X.pe = __fadd_rn(X.pe, e);
             }
+        }
+        if (REC) {
+            // order parameter of the row: sites x + 0, x + 2 have the parity of
+            // y (x is a multiple of 4), sites x + 1, x + 3 the other one
+            const float ev = __fadd_rn(C.s[0], C.s[2]), od = __fadd_rn(C.s[1], C.s[3]);
+            const float m = !X.stag ? __fadd_rn(ev, od) : ((y & 1) ? __fadd_rn(od, -ev) : __fadd_rn(ev, -od));
+            X.pm = __fadd_rn(X.pm, m);
         }
         st4_stream(p_to + X.x, make_float4(to[0], to[1], to[2], to[3]));
         st4_stream(p_vo + X.x, make_float4(vo[0], vo[1], vo[2], vo[3]));
@@ -455,16 +478,18 @@ __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const 
 
 }  // namespace
 
-template <int MINB>
+// REC: 0 = the launch records nothing, 1 = it may record M, 2 = M and E.
+// Each kernel carries only the recording code (and registers) it needs.
+template <int MINB, int REC>
 __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfgs, const StripTask* tasks, int H,
                                                                int64_t j_local, Buffers buf, const CallArgs* cap,
                                                                Partials pa, PhiloxKeys keys)
 {
     const CallArgs ca = *cap;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = (int)(threadIdx.x >> 5);
     const StripTask task = tasks[blockIdx.x];  // block-uniform
-    const int unit = task.unit0 + (int)(threadIdx.x >> 5);
-    if (unit >= task.n_units) return;
+    const int unit = task.unit0 + warp;
+    const bool live = unit < task.n_units;     // the lattice's last block may have idle warps
     const DevCfg& cf = cfgs[task.cfg];
     const int64_t j = ca.j_base + j_local;
     if (j >= cf.n_call) return;
@@ -495,18 +520,40 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     X.srcL = grp * G + (X.lg + G - 1) % G;
     X.srcR = grp * G + (X.lg + 1) % G;
     X.rec = ca.record_every > 0 && (X.k % ca.record_every) == 0;
-    X.rec_e = !ca.m_only;
     X.cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
     X.pm = 0.f;
     X.pe = 0.f;
-    if (X.rec) {
-        strip_rows<true>(X, cf, keys, ybeg, H);
-        const double wm = warp_sum((double)X.pm), we = warp_sum((double)X.pe);
-        const int64_t b = cf.b_first + task.rep;
-        const int64_t r = (X.k - cf.rec_first) / ca.record_every;
-        commit_partial(pa, b, unit, task.n_units, wm, we, ca.rec_dev + b * ca.rec_stride + r, 1.0 / (double)cf.N);
-    } else {
-        strip_rows<false>(X, cf, keys, ybeg, H);
+    if (REC > 0 && X.rec) {  // block-uniform
+        X.Jx = cf.Jx;
+        X.Jy = cf.Jy;
+        X.hF = cf.h;
+        X.stag = cf.stag != 0;
+        if (live) strip_rows<REC>(X, cf, keys, ybeg, H);
+        // one partial per block: warp sums, then the block's warps in order
+        __shared__ double2 s_part[8];
+        const double wm = warp_sumf(X.pm), we = warp_sumf(X.pe);
+        if (lane == 0) s_part[warp] = make_double2(wm, we);
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = (int)(blockDim.x >> 5);
+            double bm = 0.0, be = 0.0;
+            for (int w = 0; w < nw; ++w) {
+                bm += s_part[w].x;
+                be += s_part[w].y;
+            }
+            // task, descriptor and call arguments read again here rather than
+            // kept in registers across the row loop (which would spill there)
+            const StripTask t2 = tasks[blockIdx.x];
+            const DevCfg& c2 = cfgs[t2.cfg];
+            const CallArgs a2 = *cap;
+            const int64_t k2 = c2.k_start + a2.j_base + j_local + a2.k_shift;
+            const int64_t b = c2.b_first + t2.rep;
+            const int64_t r = (k2 - c2.rec_first) / a2.record_every;
+            commit_partial(pa, b, t2.unit0 >> 3, (t2.n_units + 7) >> 3, bm, be, a2.rec_dev + b * a2.rec_stride + r,
+                           c2.N);
+        }
+    } else if (live) {
+        strip_rows<0>(X, cf, keys, ybeg, H);
     }
 }
 
@@ -521,17 +568,23 @@ int strip_units_per_lattice(int Lx, int Ly, int H)
 // variant = resident blocks per SM the registers are capped for (2, 3 or 4).
 // Every task of one launch uses the noise key `seed`.
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
-                              uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
+                              int rec, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
                               cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
     const PhiloxKeys keys = philox_round_keys(seed);
-    if (variant >= 4)
-        strip_step_kernel<4><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
-    else if (variant == 3)
-        strip_step_kernel<3><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
-    else
-        strip_step_kernel<2><<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
+    using Kern = void (*)(const DevCfg*, const StripTask*, int, int64_t, Buffers, const CallArgs*, Partials,
+                          PhiloxKeys);
+    // Launches that record run at most 3 blocks per SM: capped at 64
+    // registers the recording code spills inside the row loop.
+    static const Kern table[3][3] = {
+        {strip_step_kernel<2, 0>, strip_step_kernel<2, 1>, strip_step_kernel<2, 2>},
+        {strip_step_kernel<3, 0>, strip_step_kernel<3, 1>, strip_step_kernel<3, 2>},
+        {strip_step_kernel<4, 0>, strip_step_kernel<3, 1>, strip_step_kernel<3, 2>},
+    };
+    const int vi = variant >= 4 ? 2 : (variant == 3 ? 1 : 0);
+    const Kern kern = table[vi][rec < 0 ? 0 : (rec > 2 ? 2 : rec)];
+    kern<<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
     return cudaGetLastError();
 }
 
@@ -698,7 +751,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
             cur = nxt;
         }
         if (rec) {
-            const double wm = warp_sum((double)pm), we = warp_sum((double)pe);
+            const double wm = warp_sumf(pm), we = warp_sumf(pe);
             if (lane == 0) {
                 s_red[warp] = wm;
                 s_red[32 + warp] = we;
