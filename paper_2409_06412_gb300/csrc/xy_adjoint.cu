@@ -542,6 +542,70 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     }
 }
 
+// ===========================================================================
+// Order parameter of every state of a recomputed segment:
+//   M_k = (1/N) sum_i sigma_i sin(q theta_i)   (sigma_i = (-1)^(x+y) when
+// staggered, else 1), the quantity whose sign the |M| term of the objective
+// differentiates.  Block (b, i) reduces lattice b of segment slot i: FP32 over
+// runs of 16 quads per thread, FP64 across runs and threads, in a fixed order.
+// ===========================================================================
+__global__ void __launch_bounds__(256) segment_m_kernel(const DevCfg* cfgs, int n_cfg, const float* seg, int64_t T,
+                                                        double2* rec, int64_t rec_stride, int64_t r0)
+{
+    const int b = blockIdx.x;
+    const int i = blockIdx.y;
+    int c = 0;
+    while (c + 1 < n_cfg && b >= cfgs[c + 1].b_first) ++c;
+    const DevCfg& cf = cfgs[c];
+    const int rep = b - cf.b_first;
+    const int Lx = cf.Lx;
+    const int64_t nq = cf.N / 4;
+    const float q = cf.q;
+    const bool stag = cf.stag != 0;
+    const float* th = seg + 2 * T * (int64_t)i + cf.offset + (int64_t)rep * cf.N;
+    double acc = 0.0;
+    float run = 0.f;
+    int in_run = 0;
+    for (int64_t u = threadIdx.x; u < nq; u += blockDim.x) {
+        const float4 t = ld4(th + 4 * u);
+        const float s0 = __sinf(__fmul_rn(q, t.x)), s1 = __sinf(__fmul_rn(q, t.y));
+        const float s2 = __sinf(__fmul_rn(q, t.z)), s3 = __sinf(__fmul_rn(q, t.w));
+        const float ev = s0 + s2, od = s1 + s3;  // x is a multiple of 4: sites 0, 2 share the parity of y
+        const int y = (int)(4 * u / Lx);
+        run += !stag ? ev + od : ((y & 1) ? od - ev : ev - od);
+        if (++in_run == 16) {
+            acc += run;
+            run = 0.f;
+            in_run = 0;
+        }
+    }
+    acc += run;
+    __shared__ double s_acc[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    acc = warp_sum_a(acc);
+    if (lane == 0) s_acc[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m += s_acc[w];
+        rec[(int64_t)b * rec_stride + r0 + i] = make_double2(m / (double)cf.N, 0.0);
+    }
+}
+
+cudaError_t launch_segment_m(const DevCfg* d_cfg, int n_cfg, int64_t B, const float* seg, int64_t T, int n_states,
+                             double2* rec, int64_t rec_stride, int64_t r0, cudaStream_t st)
+{
+    if (B == 0 || n_states == 0) return cudaSuccess;
+    for (int i0 = 0; i0 < n_states; i0 += 65535) {  // grid.y limit
+        const int n = n_states - i0 < 65535 ? n_states - i0 : 65535;
+        segment_m_kernel<<<dim3((unsigned)B, (unsigned)n), 256, 0, st>>>(d_cfg, n_cfg, seg + 2 * T * (int64_t)i0, T, rec,
+                                                                         rec_stride, r0 + i0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_adjoint_band(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, uint64_t seed,
                                 BandArgs R, cudaStream_t st)
 {

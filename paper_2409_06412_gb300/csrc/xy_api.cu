@@ -138,6 +138,7 @@ struct StripGroup {
     std::vector<StripTask> tasks;
     StripTask* d_tasks = nullptr;
     size_t d_cap = 0;
+    int variant_rec = 0;  // occupancy variant of launches that record (0: derived from variant)
 };
 
 bool is_device_ptr(const void* p)
@@ -372,7 +373,8 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     for (int i = 0; i < cnt; ++i) {
         for (auto& g : L->strip_groups) {
             if ((rc = timed_begin(L, st, XY_KCLASS_STRIP, &end))) return rc;
-            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, L->cur_rec, g.seed,
+            const int var = L->cur_rec && g.variant_rec ? g.variant_rec : g.variant;
+            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, var, L->cur_rec, g.seed,
                                  jl0 + i, buf, L->d_call, L->pa, st));
             if ((rc = timed_end(end, st))) return rc;
             ++L->launches;
@@ -519,6 +521,61 @@ int autotune_lattice(xy_lattice* L)
             g.H = bh;
             g.variant = bv;
             if ((rc = build_strip_tasks(L, g))) break;
+            // launches that record M (every step of the adjoint's recompute)
+            // carry more live registers: their own variant at this H, among
+            // those that do not spill
+            char keyr[256];
+            snprintf(keyr, sizeof keyr, "%s|striprec|%d|%d|%lld|%d", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat, bh);
+            int rv = 0, unused = 0;
+            if (!g_tune.get(keyr, &rv, &unused)) {
+                double2* scratch = nullptr;
+                CK(cudaMalloc(&scratch, sizeof(double2) * (size_t)L->B));
+                CallArgs ca{};
+                ca.fixed_parity = 1;
+                ca.record_every = 1;
+                ca.rec_dev = scratch;
+                ca.rec_stride = 1;
+                ca.m_only = 1;
+                if ((rc = upload_call(L, ca))) {
+                    cudaFree(scratch);
+                    break;
+                }
+                const int nt = (int)g.tasks.size();
+                float t_best[2] = {1e30f, 1e30f};
+                int reps = 3;
+                for (int round = 0; round < 5 && rc == XY_OK; ++round)
+                    for (int vi = 0; vi < 2; ++vi) {
+                        const int v = 2 + vi;
+                        cudaError_t e = launch_strip_step(L->d_cfg, g.d_tasks, nt, bh, v, 1, g.seed, 0, buf,
+                                                          L->d_call, L->pa, L->stream);
+                        if (e == cudaSuccess) e = cudaEventRecord(e0, L->stream);
+                        for (int i = 0; i < reps && e == cudaSuccess; ++i)
+                            e = launch_strip_step(L->d_cfg, g.d_tasks, nt, bh, v, 1, g.seed, 0, buf, L->d_call,
+                                                  L->pa, L->stream);
+                        if (e == cudaSuccess) e = cudaEventRecord(e1, L->stream);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                        if (e != cudaSuccess) {
+                            cudaGetLastError();
+                            rc = fail(XY_ECUDA, "autotune (recording launches): %s", cudaGetErrorString(e));
+                            break;
+                        }
+                        L->launches += 1 + reps;
+                        t_best[vi] = std::min(t_best[vi], ms / reps);
+                        if (round == 0 && vi == 0 && ms < 0.5f)
+                            reps = std::min(64, (int)(0.5f / std::max(ms / reps, 1e-3f)) + 1);
+                    }
+                cudaStreamSynchronize(L->stream);
+                cudaFree(scratch);
+                if (rc) break;
+                rv = t_best[1] < t_best[0] ? 3 : 2;
+                g_tune.put(keyr, rv, 0);
+                CallArgs ca0{};
+                ca0.fixed_parity = 1;
+                if ((rc = upload_call(L, ca0))) break;
+            }
+            g.variant_rec = rv;
         }
     }
     for (auto& g : L->res_groups) {
@@ -1228,25 +1285,6 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         const int64_t ns = std::min<int64_t>(K, n - s * K);
         RCA(advance_core(L, ns, 0, nullptr, 0, false, 0));
     }
-    // observation at k0 + n (first half of the next step, state untouched)
-    for (int c = 0; c < L->n_cfg; ++c) {
-        L->h_dev[c].k_start = k0 + n;
-        L->h_dev[c].n_call = 1;
-        L->h_dev[c].rec_first = k0 + n;
-    }
-    RCA(upload_cfg(L));
-    {
-        CallArgs ca{};
-        ca.rec_stride = R_;
-        ca.rec_dev = arec + n;
-        ca.record_every = 1;
-        ca.m_only = 1;
-        RCA(upload_call(L, ca));
-    }
-    for (int c = 0; c < L->n_cfg; ++c) {
-        CKA(launch_plain_step(L->d_cfg, L->h_dev[c], 0, state_buffers(L), L->d_call, L->pa, 0, L->stream));
-        ++L->launches;
-    }
     RCA(sp.close());
     const double inv_norm = 1.0 / ((double)L->B * (double)n);
     // ---- reverse sweep, segment by segment
@@ -1326,18 +1364,13 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         CKA(cudaMemcpyAsync(seg, ck + 2 * T * s, 2 * state_bytes, cudaMemcpyDeviceToDevice, L->stream));
         {
             // step ks + i runs as local step i (k = k0 + i + (ks - k0)) from slot i
-            // into slot i + 1, and records M_{ks+i} for the signs of |M|
+            // into slot i + 1
             CallArgs ca{};
             ca.k_shift = ks - k0;
             ca.fixed_parity = 1;
-            ca.record_every = 1;
-            ca.rec_dev = arec;
-            ca.rec_stride = R_;
-            ca.m_only = 1;
             RCA(upload_call(L, ca));
         }
-        // Ks steps: every state of the segment is stepped from once, so M of each is
-        // recorded; slot Ks (the next checkpoint, or k0 + n) is written too
+        // Ks steps: slots 1 .. Ks (the next checkpoint, or k0 + n) are written
         for (int64_t i = 0; i < Ks; ++i) {
             Buffers buf{seg + 2 * T * i, seg + 2 * T * i + T, seg + 2 * T * (i + 1), seg + 2 * T * (i + 1) + T};
             if (L->path == XY_PATH_PLAIN) {
@@ -1352,7 +1385,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                     ++L->launches;
                 }
                 for (auto& g : L->strip_groups) {
-                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, 1, g.seed, i,
+                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, 0, g.seed, i,
                                           buf, L->d_call, L->pa, L->stream));
                     ++L->launches;
                 }
@@ -1362,6 +1395,9 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 }
             }
         }
+        // M of the segment's states, for the signs (and values) of |M_k|
+        CKA(launch_segment_m(L->d_cfg, L->n_cfg, L->B, seg, T, (int)n_states, arec, R_, ks - k0, L->stream));
+        ++L->launches;
         RCA(spr.close());
         Span sv{L};
         RCA(sv.open(XY_KCLASS_ADJ_REV));

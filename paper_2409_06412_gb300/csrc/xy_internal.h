@@ -179,6 +179,10 @@ struct BandArgs {
     double* gacc;        // [blocks][kGacc]
     int block_base;
 };
+// M_k of slots [0, n_states) of a segment (slot stride 2 T floats) into
+// rec[b * rec_stride + r0 + slot].x
+cudaError_t launch_segment_m(const DevCfg* d_cfg, int n_cfg, int64_t B, const float* seg, int64_t T, int n_states,
+                             double2* rec, int64_t rec_stride, int64_t r0, cudaStream_t st);
 cudaError_t launch_adjoint_band(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, uint64_t seed,
                                 BandArgs R, cudaStream_t st);
 
