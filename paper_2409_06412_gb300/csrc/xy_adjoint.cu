@@ -340,15 +340,28 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     // configuration constants in registers (the cp.async statements clobber
     // memory, which would otherwise reload them from the descriptor every row)
     const float Jx = cf.Jx, Jy = cf.Jy, hF = cf.h;
+    const float q2Jx = q2 * Jx, q2Jy = q2 * Jy;
     const bool stag = cf.stag != 0;
     const float wEn = wE * invN, wMs = wM * invN * sgnM * K.q;
-    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f, eacc = 0.f;
+    // per-thread sums of the step: F-bar against dF/dJ_par = -q a_x,
+    // dF/dJ_perp = -q a_y, dF/dh = p sin(p t) (the factors -q, p applied at
+    // the end); a-bar, b-bar, c-bar; and the observed site terms omega^2, the
+    // bonds cos q(t - t_{x+1}), cos q(t - t_{y+1}) and cos(p t), from which
+    // the energy and its parameter derivatives are formed at the end
+    float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f;
+    float sw2 = 0.f, sbx = 0.f, sby = 0.f, scp = 0.f;
 
-    // window: S0 = row t-2, S1 = t-1, S2 = t, S3 = t+1; F0 = F-bar(t-2), F1 = t-1, F2 = t
+    // window: S0 = row t-2, S1 = t-1, S2 = t, S3 = t+1; F0 = F-bar(t-2), F1 = t-1
     BandSC S0, S1, S2, S3;
-    float4 F0 = make_float4(0.f, 0.f, 0.f, 0.f), F1 = F0, F2 = F0;
+    float4 F0 = make_float4(0.f, 0.f, 0.f, 0.f), F1 = F0;
     float4 th2, tbp1 = F0, cp1 = F0;  // raw theta of row t; tb partial and cos(p theta) of row t-1
-    auto rowp = [&](int y) { return (int64_t)wrapa(y, Ly) * Lx; };
+    // row offsets of rows t - 1, t, t + 1, t + 2 (advanced by Lx per row, periodic)
+    const int Nl = Lx * Ly;
+    auto rowp = [&](int y) { return wrapa(y, Ly) * Lx; };
+    auto adv = [&](int r) { return r + Lx == Nl ? 0 : r + Lx; };
+    int r_m1 = rowp(y0 - 2), r_0 = rowp(y0 - 1), r_p1 = rowp(y0), r_p2 = rowp(y0 + 1);
+    // slots of the edge exchange: rows t - 1, t, t + 1 modulo 3
+    int sl_m1 = (y0 - 2 + 3 * Ly) % 3, sl_0 = (y0 - 1 + 3 * Ly) % 3, sl_p1 = (y0 + 3 * Ly) % 3;
     auto publish_sc = [&](int slot, const BandSC& S) {
         if (!wide) return;
         if (lane == 0) s_sc[slot][warp][0] = make_float2(S.s[0], S.c[0]);
@@ -368,44 +381,43 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     constexpr int kStage = (NZ ? 4 : 5) * 32;  // float4 per warp and stage
     const float* vN = NZ ? nullptr : R.vnext + lat_off;
     float4* my_stage = s_stage + (size_t)warp * 2 * kStage;
-    auto prefetch = [&](int st, int t) {  // theta of row t + 1 and v, tb, vb (v_{k+1}) of row t into stage st
+    // theta of row offset rt and v, tb, vb (v_{k+1}) of row offset rv into stage st
+    auto prefetch = [&](int st, int rt, int rv) {
         float4* p = my_stage + st * kStage;
-        const int64_t r0 = rowp(t);
-        cp_async16(p + 0 * 32 + lane, th + rowp(t + 1) + x);
-        cp_async16(p + 1 * 32 + lane, vv + r0 + x);
-        cp_async16(p + 2 * 32 + lane, tbI + r0 + x);
-        cp_async16(p + 3 * 32 + lane, vbI + r0 + x);
-        if (!NZ) cp_async16(p + 4 * 32 + lane, vN + r0 + x);
+        cp_async16(p + 0 * 32 + lane, th + rt + x);
+        cp_async16(p + 1 * 32 + lane, vv + rv + x);
+        cp_async16(p + 2 * 32 + lane, tbI + rv + x);
+        cp_async16(p + 3 * 32 + lane, vbI + rv + x);
+        if (!NZ) cp_async16(p + 4 * 32 + lane, vN + rv + x);
         cp_async_commit();
     };
-    band_sc(K.q, ld4(th + rowp(y0 - 2) + x), S1);
-    th2 = ld4(th + rowp(y0 - 1) + x);
+    band_sc(K.q, ld4(th + r_m1 + x), S1);
+    th2 = ld4(th + r_0 + x);
     band_sc(K.q, th2, S2);
-    publish_sc((y0 - 1 + 3 * Ly) % 3, S2);
-    prefetch(0, y0 - 1);
+    publish_sc(sl_0, S2);
+    prefetch(0, r_p1, r_0);
     if (wide) __syncthreads(); else __syncwarp();
     for (int t = y0 - 1; t <= y0 + H; ++t) {
         const bool own_a = active && t >= y0 && t < y0 + H;  // phase A results stored / accumulated
         const bool do_b = t - 1 >= y0;                      // phase B on row t-1
         const int st = (t - y0 + 1) & 1;
-        prefetch(st ^ 1, t + 1);
+        prefetch(st ^ 1, r_p2, r_p1);
         cp_async_wait1();  // this lane's copies of stage st have landed
         const float4* sp = my_stage + st * kStage;
         const float4 th3 = sp[0 * 32 + lane];
         band_sc(K.q, th3, S3);
-        publish_sc((t + 1 + 3 * Ly) % 3, S3);
+        publish_sc(sl_p1, S3);
         // ---------------- phase A on row t
         float4 Fn = make_float4(0.f, 0.f, 0.f, 0.f), tbpn = Fn, cpn = Fn;
         {
-            const int64_t row = rowp(t);
             const float4 v = sp[1 * 32 + lane];
             const float4 tb4 = sp[2 * 32 + lane];
             const float4 vb4 = sp[3 * 32 + lane];
             float sL, cL, sR, cR;
-            nbr_sc((t + 3 * Ly) % 3, S2, sL, cL, sR, cR);
+            nbr_sc(sl_0, S2, sL, cL, sR, cR);
             float4 nz, v1;
             if (NZ) {
-                const uint32_t quad = (uint32_t)((row + x) >> 2);
+                const uint32_t quad = (uint32_t)((r_0 + x) >> 2);
                 nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.k, 0u), keys), K.c);
             } else {
                 v1 = sp[4 * 32 + lane];
@@ -413,87 +425,80 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
             float tbo[4], vbo[4], fbo[4], cpo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
+                const float s_ = S2.s[i], c_ = S2.c[i];
                 const float sl = i == 0 ? sL : S2.s[i - 1], cl = i == 0 ? cL : S2.c[i - 1];
                 const float sr = i == 3 ? sR : S2.s[i + 1], cr = i == 3 ? cR : S2.c[i + 1];
-                const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
-                const float sy = __fadd_rn(S1.s[i], S3.s[i]), cy = __fadd_rn(S1.c[i], S3.c[i]);
+                const float sx = sl + sr, cx = cl + cr;
+                const float sy = S1.s[i] + S3.s[i], cy = S1.c[i] + S3.c[i];
                 const float tht = f4get(th2, i);
-                const float sinp = __sinf(__fmul_rn(K.p, tht));
-                const float cp = __cosf(__fmul_rn(K.p, tht));
-                const float F = site_force(K, S2.s[i], S2.c[i], sx, cx, sy, cy, sinp);
+                const float sinp = __sinf(K.p * tht);
+                const float cp = __cosf(K.p * tht);
+                // F = -q J_par a_x - q J_perp a_y + h p sin(p t)
+                const float ax = fmaf(s_, cx, -c_ * sx), ay = fmaf(s_, cy, -c_ * sy);
+                const float F = fmaf(K.nqJx, ax, fmaf(K.nqJy, ay, K.hp * sinp));
                 float cn, g, om;  // c_k n_k, g_k, omega_k
                 if (NZ) {
                     cn = f4get(nz, i);
                     g = fmaf(K.hdt, F, cn);
-                    om = __fmul_rn(__fadd_rn(f4get(v, i), g), K.inv1pa);
+                    om = (f4get(v, i) + g) * K.inv1pa;
                 } else {
                     om = 0.5f * (f4get(v, i) + f4get(v1, i));
                     g = f4get(v1, i) - K.oma * om;
                     cn = g - K.hdt * F;
                 }
                 const float vbt = fmaf(K.dt, f4get(tb4, i), f4get(vb4, i));
-                float omb = __fmul_rn(K.oma, vbt);
+                float omb = K.oma * vbt;
                 float gb = vbt;
                 float tbi = f4get(tb4, i);
-                const float bx = fmaf(S2.c[i], cr, S2.s[i] * sr);
-                const float by = fmaf(S2.c[i], S3.c[i], S2.s[i] * S3.s[i]);
-                float da = -om * vbt, dJx = 0.f, dJy = 0.f, dh = 0.f, de = 0.f;
                 if (observe) {
                     omb = fmaf(wEn, om, omb);
                     tbi = fmaf(-wEn, F, tbi);
                     const float sigma = (stag && ((x + i + t) & 1)) ? -wMs : wMs;
-                    tbi = fmaf(sigma, S2.c[i], tbi);
-                    dJx = -wEn * bx;
-                    dJy = -wEn * by;
-                    dh = wEn * cp;
-                    float e = __fmul_rn(0.5f, __fmul_rn(om, om));
-                    e = fmaf(-Jx, bx, e);
-                    e = fmaf(-Jy, by, e);
-                    e = fmaf(hF, cp, e);
-                    de = wEn * e;
+                    tbi = fmaf(sigma, c_, tbi);
+                    if (own_a) {
+                        sw2 = fmaf(om, om, sw2);
+                        sbx += fmaf(c_, cr, s_ * sr);
+                        sby += fmaf(c_, S3.c[i], s_ * S3.s[i]);
+                        scp += cp;
+                    }
                 }
-                float vbk = 0.f, db = 0.f;
+                float vbk = 0.f;
                 if (!first) {
-                    vbk = __fmul_rn(K.inv1pa, omb);
-                    gb = fmaf(K.inv1pa, omb, gb);
-                    db = __fadd_rn(f4get(v, i), g) * omb;
+                    vbk = K.inv1pa * omb;
+                    gb += vbk;
+                    if (own_a) bbar = fmaf(f4get(v, i) + g, omb, bbar);
                 }
-                const float fb = __fmul_rn(K.hdt, gb);
-                dJx = fmaf(fb, -K.q * fmaf(S2.s[i], cx, -S2.c[i] * sx), dJx);
-                dJy = fmaf(fb, -K.q * fmaf(S2.s[i], cy, -S2.c[i] * sy), dJy);
-                dh = fmaf(fb, K.p * sinp, dh);
+                const float fb = K.hdt * gb;
                 if (own_a) {
-                    aJx += dJx;
-                    aJy += dJy;
-                    ah += dh;
-                    abar += da;
-                    bbar += db;
+                    aJx = fmaf(fb, ax, aJx);
+                    aJy = fmaf(fb, ay, aJy);
+                    ah = fmaf(fb, sinp, ah);
+                    abar = fmaf(-om, vbt, abar);
                     cbar = fmaf(gb, cn, cbar);
-                    eacc += de;
                 }
                 tbo[i] = tbi;
                 vbo[i] = vbk;
                 fbo[i] = fb;
                 cpo[i] = cp;
             }
-            if (own_a) st4(vbO + row + x, make_float4(vbo[0], vbo[1], vbo[2], vbo[3]));
+            if (own_a) st4(vbO + r_0 + x, make_float4(vbo[0], vbo[1], vbo[2], vbo[3]));
             Fn = make_float4(fbo[0], fbo[1], fbo[2], fbo[3]);
             tbpn = make_float4(tbo[0], tbo[1], tbo[2], tbo[3]);
             cpn = make_float4(cpo[0], cpo[1], cpo[2], cpo[3]);
             if (wide) {
-                if (lane == 0) s_fb[(t + 2 * Ly) & 1][warp][0] = Fn.x;
-                if (lane == 31) s_fb[(t + 2 * Ly) & 1][warp][1] = Fn.w;
+                if (lane == 0) s_fb[t & 1][warp][0] = Fn.x;
+                if (lane == 31) s_fb[t & 1][warp][1] = Fn.w;
             }
         }
         if (wide) __syncthreads(); else __syncwarp();
         // ---------------- phase B on row t - 1 (needs F-bar of rows t - 2, t - 1, t)
         if (do_b) {
             float sL, cL, sR, cR;
-            nbr_sc((t - 1 + 3 * Ly) % 3, S1, sL, cL, sR, cR);
+            nbr_sc(sl_m1, S1, sL, cL, sR, cR);
             float fL = __shfl_sync(kFullA, F1.w, srcL), fR = __shfl_sync(kFullA, F1.x, srcR);
             if (wide) {
-                if (lane == 0) fL = s_fb[(t - 1 + 2 * Ly) & 1][wl][1];
-                if (lane == 31) fR = s_fb[(t - 1 + 2 * Ly) & 1][wr][0];
+                if (lane == 0) fL = s_fb[(t - 1) & 1][wl][1];
+                if (lane == 31) fR = s_fb[(t - 1) & 1][wr][0];
             }
             float out[4];
 #pragma unroll
@@ -507,11 +512,11 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
                 const float kd = fmaf(S1.c[i], S2.c[i], S1.s[i] * S2.s[i]);
                 const float hx = fmaf(kl, fl - fj, kr * (fr - fj));
                 const float hy = fmaf(ku, f4get(F0, i) - fj, kd * (f4get(Fn, i) - fj));
-                float acc = q2 * fmaf(Jx, hx, Jy * hy);
+                float acc = fmaf(q2Jx, hx, q2Jy * hy);
                 acc = fmaf(hp2, f4get(cp1, i) * fj, acc);
-                out[i] = __fadd_rn(f4get(tbp1, i), acc);
+                out[i] = f4get(tbp1, i) + acc;
             }
-            if (active) st4(tbO + rowp(t - 1) + x, make_float4(out[0], out[1], out[2], out[3]));
+            if (active) st4(tbO + r_m1 + x, make_float4(out[0], out[1], out[2], out[3]));
         }
         // shift the windows
         S0 = S1;
@@ -522,10 +527,24 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
         F1 = Fn;
         tbp1 = tbpn;
         cp1 = cpn;
+        r_m1 = r_0;
+        r_0 = r_p1;
+        r_p1 = r_p2;
+        r_p2 = adv(r_p2);
+        const int sl_t = sl_m1;
+        sl_m1 = sl_0;
+        sl_0 = sl_p1;
+        sl_p1 = sl_t;
     }
     // per-block accumulators: FP32 warp butterflies (a warp covers a few
     // thousand sites), the warps and the steps combined in FP64 in a fixed order
-    const float vals[kGacc] = {aJx, aJy, ah, abar, bbar, cbar, eacc};
+    const float vals[kGacc] = {
+        fmaf(-K.q, aJx, -wEn * sbx),                                        // d/d J_par
+        fmaf(-K.q, aJy, -wEn * sby),                                        // d/d J_perp
+        fmaf(K.p, ah, wEn * scp),                                           // d/d h
+        abar, bbar, cbar,
+        wEn * fmaf(0.5f, sw2, fmaf(-Jx, sbx, fmaf(-Jy, sby, hF * scp))),  // w_E E / N
+    };
 #pragma unroll
     for (int k = 0; k < kGacc; ++k) {
         const float w = warp_sumf_a(vals[k]);

@@ -480,10 +480,11 @@ int autotune_lattice(xy_lattice* L)
             // to span about half a millisecond (single launches of a small
             // batch differ by less than their timing noise)
             float best = 1e30f;
-            for (int H : {8, 16, 32, 64}) {
+            for (int H : {4, 8, 16, 32, 64}) {
                 const int groups = g.Lx >= 128 ? 1 : 32 / (g.Lx / 4);
                 if (g.Ly % (H * groups) != 0) continue;
-                if (strip_units_per_lattice(g.Lx, g.Ly, H) > L->pa.max_units) continue;
+                // one record partial per block of 8 units
+                if ((strip_units_per_lattice(g.Lx, g.Ly, H) + 7) / 8 > L->pa.max_units) continue;
                 g.H = H;
                 if ((rc = build_strip_tasks(L, g))) break;
                 const int nt = (int)g.tasks.size();
@@ -1171,6 +1172,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     struct AdjGroup {
         int Lx, Ly, H;
         uint64_t seed;
+        bool wide;
+        std::vector<int> cfgs;
         std::vector<BandTask> tasks;
         BandTask* d_tasks = nullptr;
         int block_base = 0;
@@ -1180,55 +1183,54 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     std::vector<int> adj_plain;
     int n_blocks = 0;
     std::vector<int> block_base(L->n_cfg, 0);
+    int sms = 148;
     {
-        int dev = 0, sms = 148;
+        int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaGetLastError();
-        for (int c = 0; c < L->n_cfg; ++c) {
-            const xy_config_desc& d = L->cfg[c].desc;
-            const bool wide_ok = d.Lx > 128 && d.Lx % 128 == 0 && d.Lx <= 2048;
-            const bool narrow_ok = d.Lx <= 128 && 32 % (d.Lx / 4) == 0;
-            if (!wide_ok && !narrow_ok) {
-                adj_plain.push_back(c);
-                continue;
-            }
-            int64_t same = 0;
-            for (int c2 = 0; c2 < L->n_cfg; ++c2)
-                if (L->cfg[c2].desc.Lx == d.Lx && L->cfg[c2].desc.Ly == d.Ly) same += L->cfg[c2].desc.n_replicas;
-            // band height: the largest H <= 64 dividing Ly that still gives 8
-            // warps per SM over the batch (each warp walks its rows serially)
-            const int warps_per_band = wide_ok ? d.Lx / 128 : 1;
-            const int groups = wide_ok ? 1 : 32 / (d.Lx / 4);
-            int H = 0;
-            for (int h : {64, 32, 16, 8, 4, 2, 1}) {
-                if (d.Ly % h != 0) continue;
-                if (H == 0) H = h;
-                const int64_t warps = same * (d.Ly / h) * warps_per_band / groups;
-                H = h;
-                if (warps >= (int64_t)sms * 8) break;
-            }
-            AdjGroup* g = nullptr;
-            for (auto& gg : adj_groups)
-                if (gg.Lx == d.Lx && gg.Ly == d.Ly && gg.H == H && gg.seed == d.seed) g = &gg;
-            if (!g) {
-                adj_groups.push_back(AdjGroup{d.Lx, d.Ly, H, d.seed, {}, nullptr, 0, 0});
-                g = &adj_groups.back();
-            }
-            const int nb = d.Ly / H;
-            const int per_block = wide_ok ? 1 : 8 * groups;
-            for (int r = 0; r < d.n_replicas; ++r)
-                for (int b0 = 0; b0 < nb; b0 += per_block) g->tasks.push_back(BandTask{c, r, b0, nb});
-            g->n_lat += d.n_replicas;
-        }
-        for (auto& g : adj_groups) {
-            g.block_base = n_blocks;
-            n_blocks += (int)g.tasks.size();
-        }
-        for (int c : adj_plain) {
-            block_base[c] = n_blocks;
-            n_blocks += adjoint_blocks(L->h_dev[c]);
-        }
     }
+    for (int c = 0; c < L->n_cfg; ++c) {
+        const xy_config_desc& d = L->cfg[c].desc;
+        const bool wide_ok = d.Lx > 128 && d.Lx % 128 == 0 && d.Lx <= 2048;
+        const bool narrow_ok = d.Lx <= 128 && 32 % (d.Lx / 4) == 0;
+        if (!wide_ok && !narrow_ok) {
+            adj_plain.push_back(c);
+            continue;
+        }
+        AdjGroup* g = nullptr;
+        for (auto& gg : adj_groups)
+            if (gg.Lx == d.Lx && gg.Ly == d.Ly && gg.seed == d.seed) g = &gg;
+        if (!g) {
+            adj_groups.push_back(AdjGroup{d.Lx, d.Ly, 0, d.seed, wide_ok, {}, {}, nullptr, 0, 0});
+            g = &adj_groups.back();
+        }
+        g->cfgs.push_back(c);
+        g->n_lat += d.n_replicas;
+    }
+    // band tasks of a group for band height H: one block per band (wide), or
+    // 8 warps of Lx/4-lane groups, one band per group (narrow)
+    auto band_tasks = [&](const AdjGroup& g, int H, std::vector<BandTask>& out) {
+        out.clear();
+        const int groups = g.wide ? 1 : 32 / (g.Lx / 4);
+        const int nb = g.Ly / H;
+        const int per_block = g.wide ? 1 : 8 * groups;
+        for (int c : g.cfgs)
+            for (int r = 0; r < L->cfg[c].desc.n_replicas; ++r)
+                for (int b0 = 0; b0 < nb; b0 += per_block) out.push_back(BandTask{c, r, b0, nb});
+    };
+    // default band height: the largest H <= 64 dividing Ly that still gives 8
+    // warps per SM over the batch (each warp walks its rows serially)
+    auto default_H = [&](const AdjGroup& g) {
+        const int warps_per_band = g.wide ? g.Lx / 128 : 1;
+        const int groups = g.wide ? 1 : 32 / (g.Lx / 4);
+        int H = 1;
+        for (int h : {64, 32, 16, 8, 4, 2, 1}) {
+            if (g.Ly % h != 0) continue;
+            H = h;
+            if (g.n_lat * (g.Ly / h) * warps_per_band / groups >= (int64_t)sms * 8) break;
+        }
+        return H;
+    };
     float *ck = nullptr, *seg = nullptr, *adjb = nullptr, *Fb = nullptr;
     double2* arec = nullptr;
     double* gacc = nullptr;
@@ -1247,6 +1249,108 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     if (e == cudaSuccess) e = cudaMalloc(&adjb, sizeof(float) * 4 * T);
     if (e == cudaSuccess && !adj_plain.empty()) e = cudaMalloc(&Fb, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&arec, sizeof(double2) * L->B * R_);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(XY_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
+    }
+    // band height per group: tuned (timed reverse launches on zeroed buffers,
+    // cached per shape and batch) or the default rule
+    {
+        const std::string gpu = gpu_name();
+        bool zeroed = false;
+        for (auto& g : adj_groups) {
+            char key[256];
+            snprintf(key, sizeof key, "%s|adjband|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
+            int bh = 0, unused = 0;
+            const bool big = (int64_t)g.Lx * g.Ly * g.n_lat >= ((int64_t)1 << 21);
+            if (L->autotune && big && !g_tune.get(key, &bh, &unused)) {
+                if (!zeroed) {
+                    e = cudaMemsetAsync(seg, 0, sizeof(float) * 4 * T, L->stream);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(adjb, 0, sizeof(float) * 4 * T, L->stream);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(arec, 0, sizeof(double2) * L->B * R_, L->stream);
+                    zeroed = true;
+                }
+                std::vector<int> cands;
+                for (int h : {4, 8, 16, 32, 64})
+                    if (g.Ly % h == 0) cands.push_back(h);
+                std::vector<BandTask> tk;
+                size_t max_tasks = 0;
+                for (int h : cands) {
+                    band_tasks(g, h, tk);
+                    max_tasks = std::max(max_tasks, tk.size());
+                }
+                BandTask* d_tk = nullptr;
+                double* g_tmp = nullptr;
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (e == cudaSuccess) e = cudaMalloc(&d_tk, sizeof(BandTask) * max_tasks);
+                if (e == cudaSuccess) e = cudaMalloc(&g_tmp, sizeof(double) * kGacc * max_tasks);
+                if (e == cudaSuccess) e = cudaEventCreate(&e0);
+                if (e == cudaSuccess) e = cudaEventCreate(&e1);
+                float best = 1e30f;
+                for (int h : cands) {
+                    if (e != cudaSuccess) break;
+                    band_tasks(g, h, tk);
+                    e = cudaMemcpy(d_tk, tk.data(), sizeof(BandTask) * tk.size(), cudaMemcpyHostToDevice);
+                    BandArgs R{};
+                    R.theta = seg;
+                    R.omega = seg + T;
+                    R.tb_in = adjb;
+                    R.vb_in = adjb + T;
+                    R.tb_out = adjb + 2 * T;
+                    R.vb_out = adjb + 3 * T;
+                    R.vnext = seg + 3 * T;
+                    R.rec = arec;
+                    R.rec_stride = R_;
+                    R.k = k0 + 1;
+                    R.k0 = k0;
+                    R.wE = (float)wE;
+                    R.wM = (float)wM;
+                    R.gacc = g_tmp;
+                    int reps = 2;
+                    float t_best = 1e30f;
+                    for (int round = 0; round < 5 && e == cudaSuccess; ++round) {
+                        e = launch_adjoint_band(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, R, L->stream);
+                        if (e == cudaSuccess) e = cudaEventRecord(e0, L->stream);
+                        for (int i = 0; i < reps && e == cudaSuccess; ++i)
+                            e = launch_adjoint_band(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, R, L->stream);
+                        if (e == cudaSuccess) e = cudaEventRecord(e1, L->stream);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                        L->launches += 1 + reps;
+                        t_best = std::min(t_best, ms / reps);
+                        if (round == 0 && ms < 0.5f) reps = std::min(64, (int)(0.5f / std::max(ms / reps, 1e-3f)) + 1);
+                    }
+                    if (e == cudaSuccess && t_best < best) {
+                        best = t_best;
+                        bh = h;
+                    }
+                }
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
+                cudaStreamSynchronize(L->stream);
+                cudaFree(d_tk);
+                cudaFree(g_tmp);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    cleanup();
+                    return fail(XY_ECUDA, "adjoint band tuning: %s", cudaGetErrorString(e));
+                }
+                if (bh > 0) g_tune.put(key, bh, 0);
+            }
+            g.H = bh > 0 && g.Ly % bh == 0 ? bh : default_H(g);
+            band_tasks(g, g.H, g.tasks);
+        }
+    }
+    for (auto& g : adj_groups) {
+        g.block_base = n_blocks;
+        n_blocks += (int)g.tasks.size();
+    }
+    for (int c : adj_plain) {
+        block_base[c] = n_blocks;
+        n_blocks += adjoint_blocks(L->h_dev[c]);
+    }
     for (auto& g : adj_groups) {
         if (e != cudaSuccess) break;
         e = cudaMalloc(&g.d_tasks, sizeof(BandTask) * g.tasks.size());
