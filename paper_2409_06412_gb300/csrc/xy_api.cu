@@ -55,8 +55,10 @@ struct CfgHost {
 
 struct ResGroup {
     int Lx, Ly, threads;
+    uint64_t seed;  // one noise key per group: the round keys become kernel parameters
     std::vector<ResidentTask> tasks;
     ResidentTask* d_tasks = nullptr;
+    int csize = 1;  // blocks (a thread-block cluster) per lattice
 };
 
 // Autotuner cache: "gpu|kind|Lx|Ly|lattices" -> (a, b), in memory and in a
@@ -82,13 +84,14 @@ struct TuneCache {
         while (fscanf(f, "%511s %d %d", key, &x, &y) == 3) entries.push_back({key, {x, y}});
         fclose(f);
     }
+    // the last entry of a key wins (put appends; a re-tuned choice overrides)
     bool get(const std::string& k, int* x, int* y)
     {
         load();
-        for (auto& e : entries)
-            if (e.first == k) {
-                *x = e.second.first;
-                *y = e.second.second;
+        for (auto it = entries.rbegin(); it != entries.rend(); ++it)
+            if (it->first == k) {
+                *x = it->second.first;
+                *y = it->second.second;
                 return true;
             }
         return false;
@@ -365,7 +368,7 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     int rc;
     for (auto& g : L->res_groups) {
         if ((rc = timed_begin(L, st, XY_KCLASS_RESIDENT, &end))) return rc;
-        CK(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, jl0, cnt, buf,
+        CK(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, g.csize, g.seed, jl0, cnt, buf,
                                 L->d_call, st));
         if ((rc = timed_end(end, st))) return rc;
         ++L->launches;
@@ -475,7 +478,15 @@ int autotune_lattice(xy_lattice* L)
         char key[256];
         snprintf(key, sizeof key, "%s|strip|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
         int bh = 0, bv = 0;
-        if (!g_tune.get(key, &bh, &bv)) {
+        // a cached choice is used only if it satisfies the same constraints
+        // as the candidates below (the cache is a plain text file)
+        auto strip_ok = [&](int H, int v) {
+            const int groups = g.Lx >= 128 ? 1 : 32 / (g.Lx / 4);
+            return H >= 1 && H <= 64 && v >= 2 && v <= 4 && g.Ly % (H * groups) == 0 &&
+                   (strip_units_per_lattice(g.Lx, g.Ly, H) + 7) / 8 <= L->pa.max_units;
+        };
+        if (g_tune.get(key, &bh, &bv) && !strip_ok(bh, bv)) bh = bv = 0;
+        if (bh == 0) {
             // per candidate: the best of 5 timings, each over enough launches
             // to span about half a millisecond (single launches of a small
             // batch differ by less than their timing noise)
@@ -528,7 +539,8 @@ int autotune_lattice(xy_lattice* L)
             char keyr[256];
             snprintf(keyr, sizeof keyr, "%s|striprec|%d|%d|%lld|%d", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat, bh);
             int rv = 0, unused = 0;
-            if (!g_tune.get(keyr, &rv, &unused)) {
+            if (g_tune.get(keyr, &rv, &unused) && (rv < 2 || rv > 4)) rv = 0;
+            if (rv == 0) {
                 double2* scratch = nullptr;
                 CK(cudaMalloc(&scratch, sizeof(double2) * (size_t)L->B));
                 CallArgs ca{};
@@ -579,42 +591,67 @@ int autotune_lattice(xy_lattice* L)
             g.variant_rec = rv;
         }
     }
+    // resident shapes: block size x cluster size (1 = one block per lattice;
+    // more blocks per lattice spread a small batch over more SMs)
     for (auto& g : L->res_groups) {
         if (rc) break;
-        if ((int64_t)g.tasks.size() < 8) continue;
         char key[256];
         snprintf(key, sizeof key, "%s|resident|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.tasks.size());
-        int bt = 0, dummy = 0;
-        if (!g_tune.get(key, &bt, &dummy)) {
+        int bt = 0, bc = 0;
+        const int G = g.Lx / 4;
+        // block size nt and cluster size cs that tile the lattice into whole
+        // bands and fit on the device
+        auto res_ok = [&](int nt, int cs) {
+            if (cs < 1 || cs > 16 || g.Ly % cs != 0 || nt < 32 || nt > 1024 || nt % G != 0) return false;
+            const int Lr = g.Ly / cs;
+            if (nt / G > Lr || Lr % (nt / G) != 0) return false;
+            if (resident_smem_bytes(g.Lx, g.Ly, nt, cs) > 220 * 1024) return false;
+            int fit = 0;
+            return prepare_resident(g.Lx, g.Ly, nt, cs, &fit) == cudaSuccess && fit > 0;
+        };
+        if (g_tune.get(key, &bt, &bc)) {
+            if (bc < 1) bc = 1;  // entries without a cluster size
+            if (!res_ok(bt, bc)) bt = bc = 0;
+        }
+        if (bt == 0) {
             float best = 1e30f;
-            const int G = g.Lx / 4;
-            for (int nt : {1024, 512, 256}) {
-                if (nt % G != 0 || (nt / G) > g.Ly || g.Ly % (nt / G) != 0) continue;
-                if (resident_smem_bytes(g.Lx, g.Ly, nt) > 220 * 1024) continue;
-                CK(prepare_resident(g.Lx, g.Ly, nt));
-                const int n = (int)g.tasks.size();
-                CK(launch_resident_step(L->d_cfg, g.d_tasks, n, g.Lx, g.Ly, nt, 0, 8, buf, L->d_call, L->stream));
-                CK(cudaEventRecord(e0, L->stream));
-                for (int i = 0; i < 3; ++i)
-                    CK(launch_resident_step(L->d_cfg, g.d_tasks, n, g.Lx, g.Ly, nt, 0, 8, buf, L->d_call,
-                                            L->stream));
-                CK(cudaEventRecord(e1, L->stream));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                L->launches += 4;
-                if (ms < best) {
-                    best = ms;
-                    bt = nt;
+            const int n = (int)g.tasks.size();
+            for (int cs : {1, 2, 4, 8, 16}) {
+                for (int nt : {1024, 512, 256, 128, 64}) {
+                    if (!res_ok(nt, cs)) continue;
+                    float t_best = 1e30f;
+                    for (int round = 0; round < 3; ++round) {
+                        CK(launch_resident_step(L->d_cfg, g.d_tasks, n, g.Lx, g.Ly, nt, cs, g.seed, 0, 8, buf, L->d_call,
+                                                L->stream));
+                        CK(cudaEventRecord(e0, L->stream));
+                        for (int i = 0; i < 3; ++i)
+                            CK(launch_resident_step(L->d_cfg, g.d_tasks, n, g.Lx, g.Ly, nt, cs, g.seed, 0, 8, buf,
+                                                    L->d_call, L->stream));
+                        CK(cudaEventRecord(e1, L->stream));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        L->launches += 4;
+                        t_best = std::min(t_best, ms);
+                    }
+                    if (t_best < best) {
+                        best = t_best;
+                        bt = nt;
+                        bc = cs;
+                    }
                 }
             }
-            if (bt > 0) g_tune.put(key, bt, 0);
+            if (bt > 0) g_tune.put(key, bt, bc);
         }
-        if (bt > 0 && bt != g.threads) {
+        if (bc < 1) bc = 1;
+        if (bt > 0 && (bt != g.threads || bc != g.csize)) {
             g.threads = bt;
-            CK(prepare_resident(g.Lx, g.Ly, bt));
+            g.csize = bc;
+            CK(prepare_resident(g.Lx, g.Ly, bt, bc, nullptr));
             for (auto& gr : L->graphs) cudaGraphExecDestroy(gr.exec);
             L->graphs.clear();
+        } else {
+            CK(prepare_resident(g.Lx, g.Ly, g.threads, g.csize, nullptr));
         }
     }
     cudaEventDestroy(e0);
@@ -763,12 +800,12 @@ int classify(xy_lattice* L)
         const int Lx = h.desc.Lx, Ly = h.desc.Ly;
         const int64_t nq = (int64_t)Lx * Ly / 4;
         max_units = std::max<int>(max_units, (int)((nq + 255) / 256));
-        const int rt = resident_threads(Lx, Ly);
+        const int rt = resident_threads(Lx, Ly, 1, 200 * 1024);
         int64_t same = 0;
         for (int c2 = 0; c2 < L->n_cfg; ++c2)
             if (L->cfg[c2].desc.Lx == Lx && L->cfg[c2].desc.Ly == Ly) same += L->cfg[c2].desc.n_replicas;
         const int H = choose_strip_H(Lx, Ly, same, (int64_t)sms * 16);
-        if (rt > 0 && resident_smem_bytes(Lx, Ly, rt) <= 200 * 1024) {
+        if (rt > 0) {
             h.kind = 0;
         } else if (H > 0) {
             h.kind = 1;
@@ -784,12 +821,12 @@ int classify(xy_lattice* L)
         CfgHost& h = L->cfg[c];
         const int Lx = h.desc.Lx, Ly = h.desc.Ly;
         if (h.kind == 0) {
-            const int rt = resident_threads(Lx, Ly);
+            const int rt = resident_threads(Lx, Ly, 1, 200 * 1024);
             ResGroup* g = nullptr;
             for (auto& gg : L->res_groups)
-                if (gg.Lx == Lx && gg.Ly == Ly && gg.threads == rt) g = &gg;
+                if (gg.Lx == Lx && gg.Ly == Ly && gg.threads == rt && gg.seed == h.desc.seed) g = &gg;
             if (!g) {
-                L->res_groups.push_back(ResGroup{Lx, Ly, rt, {}, nullptr});
+                L->res_groups.push_back(ResGroup{Lx, Ly, rt, h.desc.seed, {}, nullptr});
                 g = &L->res_groups.back();
             }
             for (int r = 0; r < h.desc.n_replicas; ++r) g->tasks.push_back(ResidentTask{c, r});
@@ -810,7 +847,7 @@ int classify(xy_lattice* L)
     for (auto& g : L->res_groups) {
         CK(cudaMalloc(&g.d_tasks, sizeof(ResidentTask) * g.tasks.size()));
         CK(cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(ResidentTask) * g.tasks.size(), cudaMemcpyHostToDevice));
-        CK(prepare_resident(g.Lx, g.Ly, g.threads));
+        CK(prepare_resident(g.Lx, g.Ly, g.threads, g.csize, nullptr));
     }
     for (auto& g : L->strip_groups) {
         int rc = build_strip_tasks(L, g);
@@ -1484,7 +1521,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 }
             } else {
                 for (auto& g : L->res_groups) {
-                    CKA(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, i, 1,
+                    CKA(launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, g.csize, g.seed, i, 1,
                                              buf, L->d_call, L->stream));
                     ++L->launches;
                 }

@@ -112,16 +112,17 @@ cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h_cfg, int64_t 
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
                               int rec, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
                               cudaStream_t st);
+// every task of one launch uses the noise key `seed`
 cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
-                                 int threads, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
-                                 cudaStream_t st);
-cudaError_t prepare_resident(int Lx, int Ly, int threads);
+                                 int threads, int csize, uint64_t seed, int64_t j_local, int n_steps, Buffers buf,
+                                 const CallArgs* ca, cudaStream_t st);
+cudaError_t prepare_resident(int Lx, int Ly, int threads, int csize, int* clusters);
 cudaError_t launch_advance(CallArgs* ca, int64_t by, cudaStream_t st);
 cudaError_t launch_add_kshift(CallArgs* ca, int64_t by, cudaStream_t st);
 cudaError_t launch_moments(const DevCfg* d_cfg, int n_cfg, const CallArgs* ca, int64_t t0, double* moments,
                            cudaStream_t st);
-int resident_threads(int Lx, int Ly);
-size_t resident_smem_bytes(int Lx, int Ly, int threads);
+int resident_threads(int Lx, int Ly, int csize, size_t max_smem);
+size_t resident_smem_bytes(int Lx, int Ly, int threads, int csize);
 int strip_units_per_lattice(int Lx, int Ly, int H);
 cudaError_t launch_debug_noise(uint64_t seed, int cfg, int rep, int64_t k, int tag, int64_t n_quads,
                                uint32_t* words, float* gauss, cudaStream_t st);

@@ -12,11 +12,17 @@
 //            (sin q t, cos q t) rows in registers; x neighbours by warp
 //            shuffles, one force and one Philox call per quad per step;
 //            all lattices of all configurations in one launch;
-//   resident one thread block per whole lattice held in shared memory,
-//            stepping many steps per launch (lattices up to ~24k sites).
+//   resident one thread block, or a thread-block cluster of up to 16
+//            blocks sharing rows through distributed shared memory, per
+//            whole lattice held in shared memory, stepping many steps per
+//            launch (Lx <= 128).
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "xy_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace xy {
 
@@ -589,17 +595,6 @@ cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n
 }
 
 
-// ===========================================================================
-// Resident stepper: one thread block holds one whole lattice in shared memory
-// and runs many steps per launch.  Thread t owns the quad column x = 4 (t % G)
-// of band t / G, a band being R consecutive rows; G = Lx / 4 <= 32 lanes span
-// a row, so x neighbours come from warp shuffles of width G.  Each step:
-//   phase 1: every band publishes (sin q t, cos q t) of its first and last
-//            row to shared memory;
-//   phase 2: every band sweeps its rows with a sliding window, taking the
-//            rows above / below the band from phase 1, and updates theta and
-//            v in place (no thread reads another thread's theta).
-// ===========================================================================
 namespace {
 struct SC4 {
     float s[4], c[4];
@@ -628,179 +623,379 @@ __device__ __forceinline__ void sc4_store(float2* p, const SC4& r)
 }
 }  // namespace
 
-int resident_threads(int Lx, int Ly)
+size_t resident_smem_bytes(int Lx, int Ly, int threads, int csize);
+
+// Threads of a resident block when a cluster of `csize` blocks holds the
+// lattice (csize = 1: one block): the largest power of two <= 1024 that is a
+// multiple of G = Lx / 4, gives whole bands of the block's Ly / csize rows
+// and keeps the block's shared memory within max_smem bytes.
+int resident_threads(int Lx, int Ly, int csize, size_t max_smem)
 {
-    if (Lx % 4 != 0 || Lx > 128) return 0;
+    if (Lx % 4 != 0 || Lx > 128 || csize < 1 || Ly % csize != 0) return 0;
     const int G = Lx / 4;
     if (32 % G != 0) return 0;
+    const int Lr = Ly / csize;
     for (int nt = 1024; nt >= 32; nt >>= 1) {
         if (nt % G != 0) continue;
         const int NB = nt / G;
-        if (NB <= Ly && Ly % NB == 0) return nt;
+        if (NB <= Lr && Lr % NB == 0 && resident_smem_bytes(Lx, Ly, nt, csize) <= max_smem) return nt;
     }
     return 0;
 }
 
-size_t resident_smem_bytes(int Lx, int Ly, int threads)
+// Dynamic shared memory of one resident block: theta and v of its rows, the
+// (sin q t, cos q t) exports of its bands' first and last rows for two step
+// parities, and the record partials for two step parities.
+size_t resident_smem_bytes(int Lx, int Ly, int threads, int csize)
 {
     const int G = Lx / 4;
     const int NB = threads / G;
-    return (size_t)Lx * Ly * 8 + (size_t)2 * NB * Lx * 8 + 64 * sizeof(double) + 16;
+    const int Lr = Ly / csize;
+    return (size_t)Lx * Lr * 8 + (size_t)4 * NB * Lx * 8 + 2 * 64 * sizeof(double) + 16;
 }
 
+// ===========================================================================
+// Resident stepper: a thread-block cluster of C blocks (C = 1: one block)
+// holds one whole lattice in shared memory, block r owning rows
+// [r Ly / C, (r + 1) Ly / C), and runs many steps per launch.  Thread t owns
+// the quad column x = 4 (t % G) of band t / G, a band being R consecutive
+// rows; G = Lx / 4 <= 32 lanes span a row, so x neighbours come from warp
+// shuffles of width G.  Each step:
+//   phase 1: every band exports (sin q t, cos q t) of its first and last row
+//            to its block's shared memory (buffers alternate with the step
+//            parity), then the cluster synchronises once;
+//   phase 2: every band sweeps its rows with a sliding window, taking the
+//            rows above / below the band from the neighbouring bands'
+//            exports -- in the block's own shared memory, or in a
+//            neighbouring block's through distributed shared memory -- and
+//            updates theta and v in place (no thread reads another thread's
+//            theta).
+// The parity-alternating exports make one cluster barrier per step enough:
+// an export buffer is rewritten two steps after it was read, and every
+// reader has passed the barrier in between.
+// ===========================================================================
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+
+// Every lattice of one launch uses the noise key whose round keys are `keys`.
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cfgs, const ResidentTask* tasks,
                                                                 int64_t j_local, int n_steps, Buffers buf,
-                                                                const CallArgs* cap)
+                                                                const CallArgs* cap, PhiloxKeys keys)
 {
     extern __shared__ float4 smem4[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
     const CallArgs ca = *cap;
-    const ResidentTask task = tasks[blockIdx.x];
+    const ResidentTask task = tasks[blockIdx.x / C];
     const DevCfg& cf = cfgs[task.cfg];
     const int64_t j0 = ca.j_base + j_local;
     const int64_t j1 = (j0 + n_steps < cf.n_call) ? j0 + n_steps : cf.n_call;
-    if (j0 >= j1) return;
+    if (j0 >= j1) return;  // uniform over the cluster
     const int Lx = cf.Lx, Ly = cf.Ly;
     const int N = Lx * Ly;
+    const int Lr = Ly / C;  // rows of this block
     const int G = Lx >> 2;
     const int NT = blockDim.x;
-    const int NB = NT / G, R = Ly / NB;
+    const int NB = NT / G, R = Lr / NB, NBt = NB * C;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int band = tid / G, lg = tid - band * G;
     const int x = 4 * lg;
     const int gb = (lane / G) * G;
     const int srcL = gb + (lg + G - 1) % G, srcR = gb + (lg + 1) % G;
+    const bool R1 = R == 1;  // a band's first and last rows coincide
 
     float* s_th = reinterpret_cast<float*>(smem4);
-    float* s_om = s_th + N;
-    float2* s_top = reinterpret_cast<float2*>(s_om + N);
-    float2* s_bot = s_top + NB * Lx;
-    double* s_red = reinterpret_cast<double*>(s_bot + NB * Lx);
-    float* s_c = reinterpret_cast<float*>(s_red + 64);
+    float* s_om = s_th + Lr * Lx;
+    float2* s_exp = reinterpret_cast<float2*>(s_om + Lr * Lx);  // [parity][top, bottom][NB][Lx]
+    double* s_red = reinterpret_cast<double*>(s_exp + 4 * NB * Lx);  // [parity][64]
 
     const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
+    const int y_base = rank * Lr;
     {
         const bool odd = !ca.fixed_parity && (j0 & 1) != 0;
-        const float* thS = (odd ? buf.thB : buf.thA) + lat_off;
-        const float* omS = (odd ? buf.omB : buf.omA) + lat_off;
-        for (int i = tid; i < N / 4; i += NT) {
+        const float* thS = (odd ? buf.thB : buf.thA) + lat_off + (int64_t)y_base * Lx;
+        const float* omS = (odd ? buf.omB : buf.omA) + lat_off + (int64_t)y_base * Lx;
+        for (int i = tid; i < Lr * Lx / 4; i += NT) {
             st4(s_th + 4 * i, ld4(thS + 4 * i));
             st4(s_om + 4 * i, ld4(omS + 4 * i));
         }
     }
     const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
-    const int ytop = band * R, ybot = band * R + R - 1;
-    const int band_up = (band + NB - 1) % NB, band_dn = (band + 1) % NB;
+    const int ytop = band * R, ybot = band * R + R - 1;  // rows within the block
+    // neighbouring bands (cluster-wide numbering) and the blocks holding them
+    const int gband = rank * NB + band;
+    const int up = (gband + NBt - 1) % NBt, dn = (gband + 1) % NBt;
+    const int rank_up = up / NB, lb_up = up - rank_up * NB;
+    const int rank_dn = dn / NB, lb_dn = dn - rank_dn * NB;
+    const StepConst K0 = step_const(cf, 0.f);
+    const bool const_T = cf.n_knots <= 1;
+    const float c_const = noise_amp(cf, 0);
+    const bool stag = cf.stag != 0;
+    const int64_t kbase = cf.k_start + ca.k_shift;
+    // noise of the band's single row (R = 1) at step k, computed one step
+    // ahead between the arrival at the cluster barrier and the wait on it
+    const uint32_t quad1 = (uint32_t)(((y_base + ytop) * Lx + x) >> 2);
+    auto noise1 = [&](int64_t k) {
+        return gauss4_scaled(philox4x32_10_rk(noise_counter(quad1, cfgrep, k, 0u), keys),
+                             const_T ? c_const : noise_amp(cf, k));
+    };
+    float4 cn1 = R1 ? noise1(kbase + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();  // the block's rows are in shared memory
 
-    for (int64_t j = j0; j < j1; ++j) {
-        const int64_t k = cf.k_start + j + ca.k_shift;
-        __syncthreads();
-        const StepConst K = step_const(cf, noise_amp(cf, k));
-        const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
-        // phase 1
-        {
-            SC4 a;
-            sc4_from_theta(ld4(s_th + ytop * Lx + x), K.q, a);
-            sc4_store(s_top + band * Lx + x, a);
-            sc4_from_theta(ld4(s_th + ybot * Lx + x), K.q, a);
-            sc4_store(s_bot + band * Lx + x, a);
-        }
-        __syncthreads();
-        // phase 2
-        SC4 prev, cur, nxt;
-        sc4_load(s_bot + band_up * Lx + x, prev);
-        sc4_load(s_top + band * Lx + x, cur);
-        float pm = 0.f, pe = 0.f;
-        for (int r = 0; r < R; ++r) {
-            const int y = ytop + r;
-            if (r == R - 1) sc4_load(s_top + band_dn * Lx + x, nxt);
-            else if (r + 1 == R - 1) sc4_load(s_bot + band * Lx + x, nxt);
-            else sc4_from_theta(ld4(s_th + (y + 1) * Lx + x), K.q, nxt);
-            const float4 th4 = ld4(s_th + y * Lx + x);
-            const float4 v4 = ld4(s_om + y * Lx + x);
+    if (R1) {
+        // one row per band: the thread's quad stays in registers for the
+        // whole launch; shared memory carries only the exported (s, c) rows
+        const int y = ytop;
+        const int gy = y_base + y;
+        float4 th4 = ld4(s_th + y * Lx + x);
+        float4 v4 = ld4(s_om + y * Lx + x);
+        const float2* up_base = cl.map_shared_rank(s_exp + lb_up * Lx + x, rank_up);
+        const float2* dn_base = cl.map_shared_rank(s_exp + lb_dn * Lx + x, rank_dn);
+        for (int64_t j = j0; j < j1; ++j) {
+            const int64_t k = kbase + j;
+            StepConst K = K0;
+            K.c = const_T ? c_const : noise_amp(cf, k);
+            const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
+            const int par = (int)(j & 1);
+            const size_t poff = (size_t)(2 * par) * NB * Lx;
+            SC4 cur, prev, nxt;
+            sc4_from_theta(th4, K.q, cur);
+            sc4_store(s_exp + poff + band * Lx + x, cur);
+            cluster_arrive();
+            float4 cn_next = cn1;
+            if (j + 1 < j1) cn_next = noise1(k + 1);
+            cluster_wait();
+            sc4_load(up_base + poff, prev);
+            sc4_load(dn_base + poff, nxt);
             const float sL = __shfl_sync(kFull, cur.s[3], srcL), cL = __shfl_sync(kFull, cur.c[3], srcL);
             const float sR = __shfl_sync(kFull, cur.s[0], srcR), cR = __shfl_sync(kFull, cur.c[0], srcR);
-            const uint32_t quad = (uint32_t)((y * Lx + x) >> 2);
-            const float4 cn =
-                gauss4_scaled(philox4x32_10(noise_counter(quad, cfgrep, k, 0u), cf.key0, cf.key1), K.c);
             float to[4], vo[4];
+            float pm = 0.f, pe = 0.f;
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 const float sl = s == 0 ? sL : cur.s[s - 1];
-                const float cl = s == 0 ? cL : cur.c[s - 1];
+                const float cl_ = s == 0 ? cL : cur.c[s - 1];
                 const float sr = s == 3 ? sR : cur.s[s + 1];
                 const float cr = s == 3 ? cR : cur.c[s + 1];
-                const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
+                const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl_, cr);
                 const float sy = __fadd_rn(prev.s[s], nxt.s[s]), cy = __fadd_rn(prev.c[s], nxt.c[s]);
                 const float th = f4get(th4, s);
                 const float F = site_force(K, cur.s[s], cur.c[s], sx, cx, sy, cy, sinp_of(K.p, th));
-                const SiteOut so = site_update(K, th, f4get(v4, s), F, f4get(cn, s));
+                const SiteOut so = site_update(K, th, f4get(v4, s), F, f4get(cn1, s));
                 to[s] = so.theta;
                 vo[s] = so.v;
                 if (rec) {
-                    const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
+                    const float sigma = (stag && ((x + s + gy) & 1)) ? -1.f : 1.f;
                     pm = fmaf(sigma, cur.s[s], pm);
                     if (!ca.m_only)
                         pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
                                                        cosp_of(K.p, th)));
                 }
             }
-            st4(s_th + y * Lx + x, make_float4(to[0], to[1], to[2], to[3]));
-            st4(s_om + y * Lx + x, make_float4(vo[0], vo[1], vo[2], vo[3]));
-            prev = cur;
-            cur = nxt;
-        }
-        if (rec) {
-            const double wm = warp_sumf(pm), we = warp_sumf(pe);
-            if (lane == 0) {
-                s_red[warp] = wm;
-                s_red[32 + warp] = we;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double bm = 0.0, be = 0.0;
-                for (int w2 = 0; w2 < NT / 32; ++w2) {
-                    bm += s_red[w2];
-                    be += s_red[32 + w2];
+            th4 = make_float4(to[0], to[1], to[2], to[3]);
+            v4 = make_float4(vo[0], vo[1], vo[2], vo[3]);
+            cn1 = cn_next;
+            if (rec) {
+                double* red = s_red + 64 * par;
+                const double wm = warp_sumf(pm), we = warp_sumf(pe);
+                if (lane == 0) {
+                    red[warp] = wm;
+                    red[32 + warp] = we;
                 }
-                const int64_t b = cf.b_first + task.rep;
-                const int64_t r = (k - cf.rec_first) / ca.record_every;
-                ca.rec_dev[b * ca.rec_stride + r] = make_double2(bm / (double)N, be / (double)N);
+                cl.sync();
+                if (rank == 0 && tid == 0) {
+                    double bm = 0.0, be = 0.0;
+                    for (int rb = 0; rb < C; ++rb) {
+                        const double* rr = cl.map_shared_rank(red, rb);
+                        for (int w2 = 0; w2 < NT / 32; ++w2) {
+                            bm += rr[w2];
+                            be += rr[32 + w2];
+                        }
+                    }
+                    const int64_t b = cf.b_first + task.rep;
+                    const int64_t ri = (k - cf.rec_first) / ca.record_every;
+                    ca.rec_dev[b * ca.rec_stride + ri] = make_double2(bm / (double)N, be / (double)N);
+                }
+            }
+        }
+        st4(s_th + y * Lx + x, th4);
+        st4(s_om + y * Lx + x, v4);
+    } else {
+        for (int64_t j = j0; j < j1; ++j) {
+            const int64_t k = kbase + j;
+            StepConst K = K0;
+            K.c = const_T ? c_const : noise_amp(cf, k);
+            const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
+            const int par = (int)(j & 1);
+            float2* e_top = s_exp + (size_t)(2 * par) * NB * Lx;
+            float2* e_bot = R1 ? e_top : e_top + (size_t)NB * Lx;
+            // phase 1
+            {
+                SC4 a;
+                sc4_from_theta(ld4(s_th + ytop * Lx + x), K.q, a);
+                sc4_store(e_top + band * Lx + x, a);
+                if (!R1) {
+                    sc4_from_theta(ld4(s_th + ybot * Lx + x), K.q, a);
+                    sc4_store(e_bot + band * Lx + x, a);
+                }
+            }
+            cluster_arrive();
+            float4 cn_next = cn1;
+            if (R1 && j + 1 < j1) cn_next = noise1(k + 1);
+            cluster_wait();
+            // phase 2
+            SC4 prev, cur, nxt;
+            sc4_load(cl.map_shared_rank(e_bot + lb_up * Lx + x, rank_up), prev);
+            sc4_load(e_top + band * Lx + x, cur);
+            float pm = 0.f, pe = 0.f;
+            for (int r = 0; r < R; ++r) {
+                const int y = ytop + r;
+                if (r == R - 1) sc4_load(cl.map_shared_rank(e_top + lb_dn * Lx + x, rank_dn), nxt);
+                else if (r + 1 == R - 1) sc4_load(e_bot + band * Lx + x, nxt);
+                else sc4_from_theta(ld4(s_th + (y + 1) * Lx + x), K.q, nxt);
+                const float4 th4 = ld4(s_th + y * Lx + x);
+                const float4 v4 = ld4(s_om + y * Lx + x);
+                const float sL = __shfl_sync(kFull, cur.s[3], srcL), cL = __shfl_sync(kFull, cur.c[3], srcL);
+                const float sR = __shfl_sync(kFull, cur.s[0], srcR), cR = __shfl_sync(kFull, cur.c[0], srcR);
+                float4 cn = cn1;
+                if (!R1) {
+                    const uint32_t quad = (uint32_t)(((y_base + y) * Lx + x) >> 2);
+                    cn = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, k, 0u), keys), K.c);
+                }
+                float to[4], vo[4];
+    #pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const float sl = s == 0 ? sL : cur.s[s - 1];
+                    const float cl_ = s == 0 ? cL : cur.c[s - 1];
+                    const float sr = s == 3 ? sR : cur.s[s + 1];
+                    const float cr = s == 3 ? cR : cur.c[s + 1];
+                    const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl_, cr);
+                    const float sy = __fadd_rn(prev.s[s], nxt.s[s]), cy = __fadd_rn(prev.c[s], nxt.c[s]);
+                    const float th = f4get(th4, s);
+                    const float F = site_force(K, cur.s[s], cur.c[s], sx, cx, sy, cy, sinp_of(K.p, th));
+                    const SiteOut so = site_update(K, th, f4get(v4, s), F, f4get(cn, s));
+                    to[s] = so.theta;
+                    vo[s] = so.v;
+                    if (rec) {
+                        const float sigma = (stag && ((x + s + y_base + y) & 1)) ? -1.f : 1.f;
+                        pm = fmaf(sigma, cur.s[s], pm);
+                        if (!ca.m_only)
+                            pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
+                                                           cosp_of(K.p, th)));
+                    }
+                }
+                st4(s_th + y * Lx + x, make_float4(to[0], to[1], to[2], to[3]));
+                st4(s_om + y * Lx + x, make_float4(vo[0], vo[1], vo[2], vo[3]));
+                prev = cur;
+                cur = nxt;
+            }
+            cn1 = cn_next;
+            if (rec) {
+                // warp partials of every block, summed by block 0 in (block, warp) order
+                double* red = s_red + 64 * par;
+                const double wm = warp_sumf(pm), we = warp_sumf(pe);
+                if (lane == 0) {
+                    red[warp] = wm;
+                    red[32 + warp] = we;
+                }
+                cl.sync();
+                if (rank == 0 && tid == 0) {
+                    double bm = 0.0, be = 0.0;
+                    for (int rb = 0; rb < C; ++rb) {
+                        const double* rr = cl.map_shared_rank(red, rb);
+                        for (int w2 = 0; w2 < NT / 32; ++w2) {
+                            bm += rr[w2];
+                            be += rr[32 + w2];
+                        }
+                    }
+                    const int64_t b = cf.b_first + task.rep;
+                    const int64_t ri = (k - cf.rec_first) / ca.record_every;
+                    ca.rec_dev[b * ca.rec_stride + ri] = make_double2(bm / (double)N, be / (double)N);
+                }
             }
         }
     }
-    __syncthreads();
+    // no block leaves while another may still read its shared memory
+    cl.sync();
     {
         const bool odd = ca.fixed_parity ? true : (j1 & 1) != 0;
-        float* thD = (odd ? buf.thB : buf.thA) + lat_off;
-        float* omD = (odd ? buf.omB : buf.omA) + lat_off;
-        for (int i = tid; i < N / 4; i += NT) {
+        float* thD = (odd ? buf.thB : buf.thA) + lat_off + (int64_t)y_base * Lx;
+        float* omD = (odd ? buf.omB : buf.omA) + lat_off + (int64_t)y_base * Lx;
+        for (int i = tid; i < Lr * Lx / 4; i += NT) {
             st4(thD + 4 * i, ld4(s_th + 4 * i));
             st4(omD + 4 * i, ld4(s_om + 4 * i));
         }
     }
 }
 
+template <int MAXT>
+cudaError_t launch_resident_t(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int threads, int csize,
+                              size_t smem, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
+                              const PhiloxKeys& keys, cudaStream_t st)
+{
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(n_tasks * csize));
+    lc.blockDim = dim3((unsigned)threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, resident_step_kernel<MAXT>, d_cfg, tasks, j_local, n_steps, buf, ca, keys);
+}
+
 cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
-                                 int threads, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
-                                 cudaStream_t st)
+                                 int threads, int csize, uint64_t seed, int64_t j_local, int n_steps, Buffers buf,
+                                 const CallArgs* ca, cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
-    const size_t smem = resident_smem_bytes(Lx, Ly, threads);
-    if (threads > 512)
-        resident_step_kernel<1024><<<n_tasks, threads, smem, st>>>(d_cfg, tasks, j_local, n_steps, buf, ca);
-    else
-        resident_step_kernel<512><<<n_tasks, threads, smem, st>>>(d_cfg, tasks, j_local, n_steps, buf, ca);
+    const size_t smem = resident_smem_bytes(Lx, Ly, threads, csize);
+    const PhiloxKeys keys = philox_round_keys(seed);
+    const cudaError_t e =
+        threads > 512
+            ? launch_resident_t<1024>(d_cfg, tasks, n_tasks, threads, csize, smem, j_local, n_steps, buf, ca, keys, st)
+            : launch_resident_t<512>(d_cfg, tasks, n_tasks, threads, csize, smem, j_local, n_steps, buf, ca, keys, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-// Opt in to the dynamic shared memory of one resident shape (outside any capture).
-cudaError_t prepare_resident(int Lx, int Ly, int threads)
+// Opt in to the dynamic shared memory (and, above 8 blocks, the non-portable
+// cluster size) of one resident shape, outside any capture.  *clusters, when
+// given, receives how many such clusters fit on the device at once (0: the
+// shape cannot run).
+cudaError_t prepare_resident(int Lx, int Ly, int threads, int csize, int* clusters)
 {
-    const int smem = (int)resident_smem_bytes(Lx, Ly, threads);
-    if (threads > 512)
-        return cudaFuncSetAttribute(resident_step_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return cudaFuncSetAttribute(resident_step_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = (int)resident_smem_bytes(Lx, Ly, threads, csize);
+    const void* fn = threads > 512 ? (const void*)resident_step_kernel<1024> : (const void*)resident_step_kernel<512>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && csize > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess || !clusters) return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)csize);
+    lc.blockDim = dim3((unsigned)threads);
+    lc.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    *clusters = 0;
+    e = threads > 512 ? cudaOccupancyMaxActiveClusters(clusters, resident_step_kernel<1024>, &lc)
+                      : cudaOccupancyMaxActiveClusters(clusters, resident_step_kernel<512>, &lc);
+    if (e != cudaSuccess) {  // an unsupported cluster shape is "does not fit", not a failure
+        cudaGetLastError();
+        *clusters = 0;
+        e = cudaSuccess;
+    }
+    return e;
 }
 
 // ===========================================================================
