@@ -211,11 +211,14 @@ struct xy_lattice {
     struct Graph {
         int chunk;
         int rec;
+        uint32_t rec_mask;
         cudaGraphExec_t exec;
         int64_t kernels;
     };
     std::vector<Graph> graphs;  // captured chunks, by chunk length and recording
     int cur_rec = 0;            // records of the current window: 0 none, 1 M, 2 M and E
+    int cur_re = 0;             // its record_every
+    uint32_t cur_mask = ~0u;    // local steps of a chunk at which some strip-stepped lattice records
     // kernel timing (direct launches bracketed by events)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
@@ -376,8 +379,10 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     for (int i = 0; i < cnt; ++i) {
         for (auto& g : L->strip_groups) {
             if ((rc = timed_begin(L, st, XY_KCLASS_STRIP, &end))) return rc;
-            const int var = L->cur_rec && g.variant_rec ? g.variant_rec : g.variant;
-            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, var, L->cur_rec, g.seed,
+            // only the steps that record run the recording kernel
+            const int rec = (L->cur_rec && ((L->cur_mask >> ((jl0 + i) & 31)) & 1u)) ? L->cur_rec : 0;
+            const int var = rec && g.variant_rec ? g.variant_rec : g.variant;
+            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, var, rec, g.seed,
                                  jl0 + i, buf, L->d_call, L->pa, st));
             if ((rc = timed_end(end, st))) return rc;
             ++L->launches;
@@ -401,7 +406,7 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
 int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
     for (auto& g : L->graphs)
-        if (g.chunk == chunk && g.rec == L->cur_rec) {
+        if (g.chunk == chunk && g.rec == L->cur_rec && g.rec_mask == L->cur_mask) {
             *out = &g;
             return XY_OK;
         }
@@ -421,7 +426,7 @@ int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    L->graphs.push_back({chunk, L->cur_rec, exec, kernels});
+    L->graphs.push_back({chunk, L->cur_rec, L->cur_mask, exec, kernels});
     *out = &L->graphs.back();
     return XY_OK;
 }
@@ -680,8 +685,23 @@ int run_window(xy_lattice* L, int64_t n_max)
         return XY_OK;
     }
     // graph replays of 32-step chunks (or one chunk of the whole window when
-    // it is shorter), then direct launches for the remainder
-    const int chunk = (int)std::min<int64_t>(32, n_max);
+    // it is shorter), then direct launches for the remainder.  When the
+    // window records every re <= 32 steps, the chunk is a multiple of re, so
+    // the local steps that record are the same in every chunk and only they
+    // run the recording strip kernel (cur_mask); otherwise every step may.
+    int chunk = (int)std::min<int64_t>(32, n_max);
+    L->cur_mask = ~0u;
+    if (L->cur_rec && L->cur_re > 0 && L->cur_re <= 32) {
+        chunk = (int)std::min<int64_t>((32 / L->cur_re) * L->cur_re, n_max);
+        uint32_t mask = 0;
+        for (const auto& g : L->strip_groups)
+            for (int c : g.cfgs) {
+                const DevCfg& d = L->h_dev[c];
+                for (int jl = 0; jl < chunk; ++jl)
+                    if ((d.k_start + jl) % L->cur_re == 0) mask |= 1u << jl;
+            }
+        L->cur_mask = mask;
+    }
     const int64_t n_full = (L->timing || chunk < 2) ? 0 : n_max / chunk;
     const int rem = (int)(n_max - n_full * chunk);
     if (n_full > 0) {
@@ -749,6 +769,7 @@ int advance_core(xy_lattice* L, int64_t n, int record_every, double2* rec_dev, i
     ca.m_only = m_only ? 1 : 0;
     if ((rc = upload_call(L, ca))) return rc;
     L->cur_rec = record_every > 0 ? (m_only ? 1 : 2) : 0;
+    L->cur_re = record_every;
     if ((rc = run_window(L, n_max))) return rc;
     if ((rc = fixup_parity(L))) return rc;
     if (do_moments && record_every > 0) {
