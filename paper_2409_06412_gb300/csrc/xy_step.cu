@@ -764,11 +764,13 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
             sc4_from_theta(th4, K.q, cur);
             sc4_store(s_exp + poff + band * Lx + x, cur);
             cluster_arrive();
-            float4 cn_next = cn1;
-            if (j + 1 < j1) cn_next = noise1(k + 1);
             cluster_wait();
             sc4_load(up_base + poff, prev);
             sc4_load(dn_base + poff, nxt);
+            // next step's noise: independent of the state, interleaved by the
+            // compiler with this step's update
+            float4 cn_next = cn1;
+            if (j + 1 < j1) cn_next = noise1(k + 1);
             const float sL = __shfl_sync(kFull, cur.s[3], srcL), cL = __shfl_sync(kFull, cur.c[3], srcL);
             const float sR = __shfl_sync(kFull, cur.s[0], srcR), cR = __shfl_sync(kFull, cur.c[0], srcR);
             float to[4], vo[4];
