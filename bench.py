@@ -329,12 +329,20 @@ def run_ours(args):
                              n_total=10 ** 9)], stream=stream)
         c5.step(10)
         snap = c5.save()
+        c5.adjoint(200, checkpoint_every=100, w_E=1.0, w_M=1.0)  # untimed: first-call tuning
+        c5.load(snap)
+        c5.step(2000)  # untimed: graphs of this window length
+        c5.load(snap)
         t_f = cuda_time(lambda: c5.step(2000), stream)
+        c5.load(snap)
+        # the forward pass that evaluates the same objective: M and E every step
+        t_fo = cuda_time(lambda: c5.step(2000, record_every=1), stream)
         c5.load(snap)
         t0 = time.perf_counter()
         obj, grads = c5.adjoint(2000, checkpoint_every=100, w_E=1.0, w_M=1.0)
         t_a = time.perf_counter() - t0
         extra["adjoint"] = {"forward_s": t_f, "adjoint_s": t_a, "adjoint_over_forward": t_a / t_f,
+                            "forward_with_objective_s": t_fo, "adjoint_over_forward_with_objective": t_a / t_fo,
                             "objective": obj, "grads": grads[0].tolist(),
                             "workload": "L=256 x 64 replicas, 2000 steps at T_c, checkpoint every 100"}
         c5.close()
