@@ -75,3 +75,17 @@ def config(Lx, Ly, n_rep, seed=1, init_mode=0, n_total=10**9, knots=None, **para
     p.update(params)
     return dict(Lx=Lx, Ly=Ly, n_rep=n_rep, seed=seed, init_mode=init_mode, params=p,
                 knots=knots if knots is not None else ([0], [T_C]), n_total=n_total)
+
+
+def ar1_field(Lx: int, Ly: int, rho: float, seed: int, axis: int = 1) -> np.ndarray:
+    """float64 angles whose rows (axis=1) or columns (axis=0) are periodic AR(1)
+    sequences with unit variance and lag-one correlation rho: a field with
+    exponentially decaying correlations along one axis (length -1/ln rho)."""
+    rng = np.random.default_rng(seed)
+    n_lines, n = (Ly, Lx) if axis == 1 else (Lx, Ly)
+    # periodic AR(1): circular filter of white noise with the spectrum of the AR(1) process
+    w = rng.standard_normal((n_lines, n))
+    k = np.arange(n)
+    H = np.sqrt(1 - rho ** 2) / (1 - rho * np.exp(-2j * np.pi * k / n))
+    z = np.fft.ifft(np.fft.fft(w, axis=1) * H, axis=1).real
+    return z if axis == 1 else z.T
