@@ -192,6 +192,22 @@ int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, 
 int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w_E, double w_M,
                       double* objective, double* grads);
 
+/* Structure factors of the rotor lattice (Sec. VI, Eq. FT-Corr-delta and
+ * Eq. S-as-lattice-FT), the input of the Lorentzian correlation-length fit of
+ * Eq. Lorentzian-Peak.  With rotors s = (cos(r theta), sin(r theta)) of the
+ * current state (the paper's rotors are r = 1), for lattices
+ * b = b_first .. b_first + b_count - 1 and wavenumbers k = 0 .. K - 1:
+ *   S_par[b - b_first][k]  = 1/(Lx Ly) sum_y sum_kappa |sum_x s^kappa_{x,y} e^{-2 pi i k x / Lx}|^2
+ *   S_perp[b - b_first][k] = 1/(Lx Ly) sum_x sum_kappa |sum_y s^kappa_{x,y} e^{-2 pi i k y / Ly}|^2
+ * which equal the paper's sums over the 2-D transform (Parseval over the
+ * other wavenumber).  x runs along the dimer rows (the J_par direction).
+ * S_par and S_perp: host or device, b_count * K doubles each, row-major.
+ * Requires 1 <= K <= min(Lx, Ly) and Lx, Ly <= 8192 for every lattice of
+ * the range (XY_EINVAL otherwise).  Synchronous when an output is on the
+ * host.  Lattices of different shapes may share one call. */
+int xy_structure_factor(xy_lattice* lat, int b_first, int b_count, int K, double rotor, double* S_par,
+                        double* S_perp);
+
 /* Select the stepping path (XY_PATH_BATCHED default, or XY_PATH_PLAIN). */
 int xy_set_path(xy_lattice* lat, int path);
 

@@ -1210,6 +1210,55 @@ int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, i
     return XY_OK;
 }
 
+int xy_structure_factor(xy_lattice* L, int b_first, int b_count, int K, double rotor, double* S_par,
+                        double* S_perp)
+{
+    if (!L || !S_par || !S_perp) return fail(XY_EINVAL, "NULL argument");
+    if (b_first < 0 || b_count <= 0 || b_first + (int64_t)b_count > L->B)
+        return fail(XY_EINVAL, "lattice range out of bounds");
+    if (K < 1) return fail(XY_EINVAL, "K must be >= 1");
+    if (!std::isfinite(rotor)) return fail(XY_EINVAL, "rotor multiplicity must be finite");
+    std::vector<int64_t> off((size_t)b_count);
+    std::vector<int> lx((size_t)b_count), ly((size_t)b_count);
+    for (int c = 0; c < L->n_cfg; ++c) {
+        const DevCfg& d = L->h_dev[c];
+        const int lo = std::max(b_first, d.b_first), hi = std::min(b_first + b_count, d.b_first + d.n_rep);
+        for (int b = lo; b < hi; ++b) {
+            if (K > std::min(d.Lx, d.Ly)) return fail(XY_EINVAL, "K = %d exceeds min(Lx, Ly) of lattice %d", K, b);
+            if (d.Lx > 8192 || d.Ly > 8192) return fail(XY_EINVAL, "structure factors need Lx, Ly <= 8192");
+            off[(size_t)(b - b_first)] = d.offset + (int64_t)(b - d.b_first) * d.N;
+            lx[(size_t)(b - b_first)] = d.Lx;
+            ly[(size_t)(b - b_first)] = d.Ly;
+        }
+    }
+    const bool dev = is_device_ptr(S_par) && is_device_ptr(S_perp);
+    double *dp = S_par, *dq = S_perp;
+    const size_t bytes = sizeof(double) * (size_t)b_count * K;
+    if (!dev) {
+        cudaError_t e = cudaMalloc(&dp, 2 * bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(XY_ENOMEM, "structure factor output: %s", cudaGetErrorString(e));
+        }
+        dq = dp + (size_t)b_count * K;
+    }
+    int launches = 0;
+    cudaError_t e = launch_structure_factor(L->thA, off.data(), lx.data(), ly.data(), b_count, K, (float)rotor, dp, dq,
+                                            &launches, L->stream);
+    L->launches += launches;
+    if (e == cudaSuccess && !dev) {
+        e = cudaMemcpyAsync(S_par, dp, bytes, cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(S_perp, dq, bytes, cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    }
+    if (!dev) cudaFree(dp);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XY_ECUDA, "structure factor: %s", cudaGetErrorString(e));
+    }
+    return XY_OK;
+}
+
 int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, double* objective, double* grads)
 {
     if (!L || !objective || !grads) return fail(XY_EINVAL, "NULL argument");

@@ -184,6 +184,11 @@ struct BandArgs {
 // rec[b * rec_stride + r0 + slot].x
 cudaError_t launch_segment_m(const DevCfg* d_cfg, int n_cfg, int64_t B, const float* seg, int64_t T, int n_states,
                              double2* rec, int64_t rec_stride, int64_t r0, cudaStream_t st);
+// Structure factors (xy_sf.cu) of n_lat lattices starting at theta +
+// offsets[b], shapes Lx[b] x Ly[b]; S_par, S_perp: device, n_lat * K doubles
+cudaError_t launch_structure_factor(const float* theta, const int64_t* offsets, const int* Lx, const int* Ly,
+                                    int n_lat, int K, float r, double* S_par, double* S_perp, int* n_launches,
+                                    cudaStream_t st);
 cudaError_t launch_adjoint_band(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, uint64_t seed,
                                 BandArgs R, cudaStream_t st);
 

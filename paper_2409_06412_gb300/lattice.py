@@ -142,6 +142,16 @@ class Lattice:
         L.call("xy_label_domains", self._h, b_first, b_count, _ptr(labels), _ptr(hist), hist_cap, _ptr(n_sizes))
         return labels, hist, n_sizes
 
+    def structure_factor(self, b_first: int = 0, b_count: int | None = None, K: int = 16, rotor: float = 1.0):
+        """S_par, S_perp of lattices [b_first, b_first + b_count) for k < K
+        (Sec. VI, Eq. S-as-lattice-FT): two (b_count, K) float64 device tensors."""
+        b_count = self.n_lattices - b_first if b_count is None else b_count
+        S_par = torch.empty((b_count, K), dtype=torch.float64, device=self.device)
+        S_perp = torch.empty((b_count, K), dtype=torch.float64, device=self.device)
+        L.call("xy_structure_factor", self._h, int(b_first), int(b_count), int(K), float(rotor), _ptr(S_par),
+               _ptr(S_perp))
+        return S_par, S_perp
+
     def adjoint(self, n: int, checkpoint_every: int = 100, w_E: float = 1.0, w_M: float = 0.0):
         obj = ctypes.c_double()
         grads = np.zeros((len(self.configs), 4), dtype=np.float64)
