@@ -89,3 +89,16 @@ def ar1_field(Lx: int, Ly: int, rho: float, seed: int, axis: int = 1) -> np.ndar
     H = np.sqrt(1 - rho ** 2) / (1 - rho * np.exp(-2j * np.pi * k / n))
     z = np.fft.ifft(np.fft.fft(w, axis=1) * H, axis=1).real
     return z if axis == 1 else z.T
+
+
+def ar1_series(n: int, phi: float, seed: int, n_series: int = 1) -> np.ndarray:
+    """(n_series, n) stationary AR(1) series x_{t+1} = phi x_t + sqrt(1 - phi^2) w_t
+    with unit variance (float64)."""
+    rng = np.random.default_rng(seed)
+    x = np.empty((n_series, n))
+    x[:, 0] = rng.standard_normal(n_series)
+    w = rng.standard_normal((n_series, n))
+    s = np.sqrt(1 - phi * phi)
+    for t in range(1, n):
+        x[:, t] = phi * x[:, t - 1] + s * w[:, t]
+    return x
