@@ -309,6 +309,15 @@ def run_ours(args):
         tl = time.perf_counter() - t0
         extra["ccl"] = {"value": 64 * 1024 * 1024 / tl, "unit": "labelled sites/s", "lattices": 64, "L": 1024}
 
+        # correlation lengths of the same 64 lattices: structure factors for k < 16 and the Lorentzian fit
+        from paper_2409_06412_gb300 import corrlen
+        lat.structure_factor(b0, 64, 16)
+        t_sf = cuda_time(lambda: lat.structure_factor(b0, 64, 16), stream)
+        s_par, s_perp = lat.structure_factor(b0, 64, 16)
+        xi_par, xi_perp = corrlen.correlation_lengths(s_par, s_perp, 1024, 1024, 1, 8)
+        extra["structure_factor"] = {"value": 64 * 1024 * 1024 / t_sf, "unit": "sites/s", "lattices": 64, "L": 1024,
+                                     "K": 16, "xi_par": xi_par, "xi_perp": xi_perp}
+
         # plain method, 64 x 64 single lattice, 1e4 steps: resident kernel vs plain launches
         c1 = Lattice([Config(Lx=64, Ly=64, n_replicas=1, seed=1, init_mode=0, knots=((0,), (TC,)),
                              n_total=10 ** 9)], stream=stream)

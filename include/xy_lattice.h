@@ -208,6 +208,25 @@ int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w
 int xy_structure_factor(xy_lattice* lat, int b_first, int b_count, int K, double rotor, double* S_par,
                         double* S_perp);
 
+/* Integrated autocorrelation time and error of the mean of recorded series
+ * (App. B: Eq. Autocorrelation-Function, Eq. Autocorrelation-Time,
+ * Eq. Time-Series-Var), the input of the adaptive sampling interval
+ * ds ~ tau_C / 10.  rec: DEVICE records as written by xy_step_n,
+ * [n_series][R] pairs (M, E) of doubles, 16-byte aligned.  For each series b
+ * the values f_s = g(rec[b][skip + s][component]), s < n, with g = identity,
+ * square, fourth power or absolute value for transform 0, 1, 2, 3, give
+ *   out[b] = { f_bar, sigma_f^2 = C(0), tau_C (in records), sigma_mean }
+ * with C(m) = 1/(n - m) sum_s (f_s - f_bar)(f_{s+m} - f_bar),
+ * tau(M) = 1/2 + sum_{m=1}^{M} C(m)/C(0), and sigma_mean^2 = 2 tau_C C(0) / n.
+ * c_window > 0: tau_C = tau(M) at the smallest M >= 1 with M >= c_window tau(M)
+ * (self-consistent window; 6 is customary).  c_window <= 0: M = floor(n/2),
+ * the paper's integration to tau_s / 2 taken literally.
+ * out: host or device, 4 * n_series doubles; synchronous when on the host.
+ * Requires 2 <= n, 0 <= skip, skip + n <= R, component in {0, 1},
+ * transform in {0, 1, 2, 3} (XY_EINVAL otherwise).  cuda_stream may be NULL. */
+int xy_autocorr_time(const double* rec, int64_t n_series, int64_t R, int component, int transform, int64_t skip,
+                     int64_t n, double c_window, double* out, void* cuda_stream);
+
 /* Select the stepping path (XY_PATH_BATCHED default, or XY_PATH_PLAIN). */
 int xy_set_path(xy_lattice* lat, int path);
 

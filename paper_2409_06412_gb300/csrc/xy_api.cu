@@ -1210,6 +1210,41 @@ int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, i
     return XY_OK;
 }
 
+int xy_autocorr_time(const double* rec, int64_t n_series, int64_t R, int component, int transform, int64_t skip,
+                     int64_t n, double c_window, double* out, void* cuda_stream)
+{
+    if (!rec || !out) return fail(XY_EINVAL, "NULL argument");
+    if (n_series < 1 || n_series > INT32_MAX) return fail(XY_EINVAL, "n_series out of range");
+    if (n < 2 || n > INT32_MAX / 2 || skip < 0 || R < skip + n) return fail(XY_EINVAL, "need 2 <= n and skip + n <= R");
+    if (component < 0 || component > 1 || transform < 0 || transform > 3)
+        return fail(XY_EINVAL, "component must be 0 or 1 and transform 0..3");
+    if (!is_device_ptr(rec) || ((uintptr_t)rec & 15) != 0)
+        return fail(XY_EINVAL, "rec must be a 16-byte aligned device buffer");
+    if (!std::isfinite(c_window)) return fail(XY_EINVAL, "c_window must be finite");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const bool dev = is_device_ptr(out);
+    double* d_out = out;
+    if (!dev) {
+        const cudaError_t e = cudaMalloc(&d_out, sizeof(double) * 4 * (size_t)n_series);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(XY_ENOMEM, "autocorrelation output: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = launch_autocorr(reinterpret_cast<const double2*>(rec), n_series, R, component, transform, skip,
+                                    (int)n, c_window, c_window <= 0.0 ? 1 : 0, d_out, st);
+    if (e == cudaSuccess && !dev) {
+        e = cudaMemcpyAsync(out, d_out, sizeof(double) * 4 * (size_t)n_series, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (!dev) cudaFree(d_out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(XY_ECUDA, "autocorrelation time: %s", cudaGetErrorString(e));
+    }
+    return XY_OK;
+}
+
 int xy_structure_factor(xy_lattice* L, int b_first, int b_count, int K, double rotor, double* S_par,
                         double* S_perp)
 {

@@ -184,6 +184,9 @@ struct BandArgs {
 // rec[b * rec_stride + r0 + slot].x
 cudaError_t launch_segment_m(const DevCfg* d_cfg, int n_cfg, int64_t B, const float* seg, int64_t T, int n_states,
                              double2* rec, int64_t rec_stride, int64_t r0, cudaStream_t st);
+// Autocorrelation time of recorded series (xy_tau.cu); out: device, 4 * n_series doubles
+cudaError_t launch_autocorr(const double2* rec, int64_t n_series, int64_t R, int component, int transform,
+                            int64_t skip, int n, double c_win, int half_window, double* out, cudaStream_t st);
 // Structure factors (xy_sf.cu) of n_lat lattices starting at theta +
 // offsets[b], shapes Lx[b] x Ly[b]; S_par, S_perp: device, n_lat * K doubles
 cudaError_t launch_structure_factor(const float* theta, const int64_t* offsets, const int* Lx, const int* Ly,
