@@ -87,10 +87,18 @@ def param_vector(params: dict) -> np.ndarray:
 
 
 def _knots(knots):
+    """Schedule arguments of the C oracle as (n_knots, steps, values): knots
+    ((steps), (T)) for the piecewise-linear schedule, or {"power": (T_c,
+    k_cross, tau_Q, gamma, eps_i, eps_f)} for the nonlinear quench, which the C
+    side takes as n_knots = -1 (see xyo_temperature)."""
+    if isinstance(knots, dict):
+        Ts = np.ascontiguousarray(np.asarray(knots["power"], dtype=np.float64))
+        assert Ts.shape == (6,)
+        return -1, np.zeros(1, dtype=np.int64), Ts
     ks = np.ascontiguousarray(np.asarray(knots[0], dtype=np.int64))
     Ts = np.ascontiguousarray(np.asarray(knots[1], dtype=np.float64))
     assert ks.shape == Ts.shape and ks.ndim == 1 and ks.size >= 1
-    return ks, Ts
+    return ks.size, ks, Ts
 
 
 # ---------------------------------------------------------------- primitives
@@ -122,8 +130,8 @@ def wrap(x) -> np.ndarray:
 
 
 def temperature(k: int, knots) -> float:
-    ks, Ts = _knots(knots)
-    return lib().xyo_temperature(k, ks.size, _ptr(ks), _ptr(Ts))
+    nk, ks, Ts = _knots(knots)
+    return lib().xyo_temperature(k, nk, _ptr(ks), _ptr(Ts))
 
 
 def init_theta(Lx, Ly, cfg, rep, seed, mode) -> np.ndarray:
@@ -152,12 +160,12 @@ def observe(Lx, Ly, params, theta, omega):
 def run_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta, omega, record_every=0):
     """Advance one lattice in place; returns the (n_rec, 2) array of (M_k, E_k)."""
     prm = param_vector(params)
-    ks, Ts = _knots(knots)
+    nk, ks, Ts = _knots(knots)
     assert theta.dtype == np.float64 and omega.dtype == np.float64
     assert theta.flags.c_contiguous and omega.flags.c_contiguous
     nrec_max = (n // record_every + 1) if record_every > 0 else 0
     rec = np.zeros((max(nrec_max, 1), 2), dtype=np.float64)
-    nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), ks.size, _ptr(ks), _ptr(Ts),
+    nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts),
                                  k0, n, _ptr(theta), _ptr(omega), record_every, _ptr(rec))
     return rec[:nrec].copy()
 
@@ -184,14 +192,14 @@ def adjoint_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0
     """Objective sum_{k=k0+1}^{k0+n}(w_E E_k + w_M |M_k|) of one lattice, its
     gradient w.r.t. (J_par, J_perp, h, eta), and the final state."""
     prm = param_vector(params)
-    ks, Ts = _knots(knots)
+    nk, ks, Ts = _knots(knots)
     th0 = np.ascontiguousarray(theta0, dtype=np.float64).ravel()
     om0 = np.ascontiguousarray(omega0, dtype=np.float64).ravel()
     grad = np.zeros(4, dtype=np.float64)
     obj = ctypes.c_double()
     th1 = np.empty_like(th0)
     om1 = np.empty_like(om0)
-    lib().xyo_adjoint_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), ks.size, _ptr(ks), _ptr(Ts), k0, n,
+    lib().xyo_adjoint_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), k0, n,
                               _ptr(th0), _ptr(om0), wE, wM, ctypes.byref(obj), _ptr(grad),
                               _ptr(th1), _ptr(om1))
     return obj.value, grad, th1, om1

@@ -132,11 +132,29 @@ double xyo_wrap(double t)
     return r;
 }
 
+/* Nonlinear quench of order gamma (Sec. VII, the proposed extension
+ * eps(t) = t^gamma / tau_Q^gamma): T(k) = T_c (1 + eps(k)) with
+ * eps(k) = -sign(t) |t / tau_Q|^gamma, t = k - k_cross, held within
+ * [eps_f, eps_i] (eps_i above, eps_f below the critical point).  gamma = 1 is
+ * the linear quench eps(t) = -t / tau_Q of Eq. (Linear-Quench). */
+double xyo_temperature_power(int64_t k, double T_c, double k_cross, double tau_Q, double gamma, double eps_i,
+                             double eps_f)
+{
+    const double t = (double)k - k_cross;
+    double eps = -(t >= 0.0 ? 1.0 : -1.0) * pow(fabs(t) / tau_Q, gamma);
+    if (eps > eps_i) eps = eps_i;
+    if (eps < eps_f) eps = eps_f;
+    return T_c * (1.0 + eps);
+}
+
 /* Piecewise-linear temperature T(k) through the knots (step_i, T_i), constant
- * outside them; a linear ramp is the quench of Eq. (Linear-Quench). */
+ * outside them; a linear ramp is the quench of Eq. (Linear-Quench).  A
+ * negative n_knots selects the nonlinear quench above with
+ * Ts = {T_c, k_cross, tau_Q, gamma, eps_i, eps_f} (ks unused). */
 double xyo_temperature(int64_t k, int n_knots, const int64_t* ks, const double* Ts)
 {
-    if (n_knots <= 0) return 0.0;
+    if (n_knots < 0) return xyo_temperature_power(k, Ts[0], Ts[1], Ts[2], Ts[3], Ts[4], Ts[5]);
+    if (n_knots == 0) return 0.0;
     if (k <= ks[0]) return Ts[0];
     for (int i = 0; i + 1 < n_knots; ++i) {
         if (k <= ks[i + 1]) {

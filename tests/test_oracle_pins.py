@@ -550,3 +550,32 @@ def test_adjoint_forward_equals_stepper():
     rec = oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 41, th, om, 1)
     expect = (0.6 * rec[1:, 1] + 0.4 * np.abs(rec[1:, 0])).sum()
     assert obj == pytest.approx(expect, rel=1e-13)
+
+
+# ---------------------------------------------------------------- nonlinear quench schedule
+# (Sec. VII: eps(t) = t^gamma / tau_Q^gamma; gamma = 1 is Eq. Linear-Quench)
+
+def test_power_quench_gamma_one_is_the_linear_ramp():
+    Tc, kc, tq, ei, ef = 1.969, 500.0, 200.0, 0.5, -1.0
+    power = {"power": (Tc, kc, tq, 1.0, ei, ef)}
+    # the same ramp as knots: eps = +0.5 at k = kc - 0.5 tq, eps = -1 at k = kc + tq
+    lin = ((int(kc - ei * tq), int(kc - ef * tq)), (Tc * (1 + ei), Tc * (1 + ef)))
+    for k in (0, 350, 400, 401, 499, 500, 523, 650, 699, 700, 701, 5000):
+        assert abs(oracle.temperature(k, power) - oracle.temperature(k, lin)) < 1e-12
+
+
+@pytest.mark.parametrize("gamma", [2.0, 3.0])
+def test_power_quench_closed_form(gamma):
+    Tc, kc, tq, ei, ef = 2.0, 1000.0, 300.0, 0.6, -0.9
+    sched = {"power": (Tc, kc, tq, gamma, ei, ef)}
+    for k in (700, 900, 999, 1000, 1001, 1100, 1250):
+        t = k - kc
+        eps = -math.copysign(abs(t / tq) ** gamma, t) if t != 0 else 0.0
+        eps = min(ei, max(ef, eps))
+        assert abs(oracle.temperature(k, sched) - Tc * (1 + eps)) < 1e-12
+    # clamped outside the ramp, continuous and non-increasing throughout
+    ks = np.arange(0, 3000)
+    T = np.array([oracle.temperature(int(k), sched) for k in ks])
+    assert abs(T[0] - Tc * (1 + ei)) < 1e-12 and abs(T[-1] - Tc * (1 + ef)) < 1e-12
+    assert np.all(np.diff(T) <= 1e-15)
+    assert np.max(np.abs(np.diff(T))) < Tc * gamma * 1.5 / tq  # no jumps: |dT/dk| <= Tc gamma max|eps|^(1-1/gamma) / tq
