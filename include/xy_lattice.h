@@ -227,6 +227,18 @@ int xy_structure_factor(xy_lattice* lat, int b_first, int b_count, int K, double
 int xy_autocorr_time(const double* rec, int64_t n_series, int64_t R, int component, int transform, int64_t skip,
                      int64_t n, double c_window, double* out, void* cuda_stream);
 
+/* Nonlinear quench (Sec. VII, the extension eps(t) = t^gamma / tau_Q^gamma of
+ * the linear quench of Eq. Linear-Quench) as the temperature schedule of
+ * configuration cfg, replacing any xy_set_schedule():
+ *   T(k) = T_c (1 + eps(k)),  eps(k) = -sign(t) |t / tau_Q|^gamma,  t = k - k_cross,
+ * held within [eps_f, eps_i]: T = T_c (1 + eps_i) before the ramp and
+ * T_c (1 + eps_f) after it; gamma = 1 is the linear quench.  The device
+ * evaluates T(k) in FP32 once per step and block.  n_steps_total as in
+ * xy_set_schedule.  Requires T_c > 0, tau_Q > 0, gamma > 0 and
+ * -1 <= eps_f <= eps_i (XY_EINVAL otherwise). */
+int xy_set_power_quench(xy_lattice* lat, int cfg, double T_c, int64_t k_cross, double tau_Q, double gamma,
+                        double eps_i, double eps_f, int64_t n_steps_total);
+
 /* Select the stepping path (XY_PATH_BATCHED default, or XY_PATH_PLAIN). */
 int xy_set_path(xy_lattice* lat, int path);
 

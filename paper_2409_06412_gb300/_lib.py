@@ -48,6 +48,7 @@ SIGNATURES = {
     "xy_label_domains_static": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i64, _vp, _vp]),
     "xy_structure_factor": (_i32, [_vp, _i32, _i32, _i32, _d, _vp, _vp]),
     "xy_autocorr_time": (_i32, [_vp, _i64, _i64, _i32, _i32, _i64, _i64, _d, _vp, _vp]),
+    "xy_set_power_quench": (_i32, [_vp, _i32, _d, _i64, _d, _d, _d, _d, _i64]),
     "xy_set_path": (_i32, [_vp, _i32]),
     "xy_autotune": (_i32, [_vp]),
     "xy_set_autotune": (_i32, [_vp, _i32]),

@@ -43,6 +43,8 @@ struct CfgHost {
     xy_params prm{};
     bool has_prm = false;
     bool has_sched = false;
+    int sched_kind = 0;  // 0 knots, 1 nonlinear quench
+    double pw[6] = {};   // T_c, k_cross, tau_Q, gamma, eps_i, eps_f
     int n_knots = 0;
     int64_t knot_step[XY_MAX_KNOTS] = {};
     double knot_T[XY_MAX_KNOTS] = {};
@@ -277,6 +279,19 @@ void fill_schedule_f32(DevCfg& d)
                            ? (float)((d.knot_T[i + 1] - d.knot_T[i]) / (double)(d.knot_step[i + 1] - d.knot_step[i]))
                            : 0.f;
     }
+}
+
+// FP32 parameters of the nonlinear quench for the device (or kind 0)
+void fill_power_f32(DevCfg& d, const CfgHost& h)
+{
+    d.sched_kind = h.sched_kind;
+    if (h.sched_kind != 1) return;
+    d.pw_Tc = (float)h.pw[0];
+    d.pw_kc = (int64_t)h.pw[1];
+    d.pw_inv_tq = (float)(1.0 / h.pw[2]);
+    d.pw_gamma = (float)h.pw[3];
+    d.pw_ei = (float)h.pw[4];
+    d.pw_ef = (float)h.pw[5];
 }
 
 int check_ready(xy_lattice* L)
@@ -1039,9 +1054,36 @@ int xy_set_schedule(xy_lattice* L, int c, const int64_t* ks, const double* Ts, i
         h.knot_step[i] = d.knot_step[i] = i < n_knots ? ks[i] : 0;
         h.knot_T[i] = d.knot_T[i] = i < n_knots ? Ts[i] : 0.0;
     }
+    h.sched_kind = 0;
     h.n_total = n_total;
     d.n_total = n_total;
     fill_schedule_f32(d);
+    fill_power_f32(d, h);
+    h.has_sched = true;
+    return XY_OK;
+}
+
+int xy_set_power_quench(xy_lattice* L, int c, double T_c, int64_t k_cross, double tau_Q, double gamma, double eps_i,
+                        double eps_f, int64_t n_total)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (c < 0 || c >= L->n_cfg) return fail(XY_EINVAL, "configuration %d out of range", c);
+    if (!(T_c > 0.0) || !std::isfinite(T_c)) return fail(XY_EINVAL, "T_c must be finite and > 0");
+    if (!(tau_Q > 0.0) || !std::isfinite(tau_Q)) return fail(XY_EINVAL, "tau_Q must be finite and > 0");
+    if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(XY_EINVAL, "gamma must be finite and > 0");
+    if (!(eps_f >= -1.0) || !(eps_i >= eps_f) || !std::isfinite(eps_i))
+        return fail(XY_EINVAL, "need -1 <= eps_f <= eps_i (finite)");
+    if (n_total < 0) return fail(XY_EINVAL, "n_steps_total must be >= 0");
+    CfgHost& h = L->cfg[c];
+    DevCfg& d = L->h_dev[c];
+    h.sched_kind = 1;
+    const double pw[6] = {T_c, (double)k_cross, tau_Q, gamma, eps_i, eps_f};
+    for (int i = 0; i < 6; ++i) h.pw[i] = pw[i];
+    h.n_knots = 0;
+    d.n_knots = 0;
+    h.n_total = n_total;
+    d.n_total = n_total;
+    fill_power_f32(d, h);
     h.has_sched = true;
     return XY_OK;
 }
@@ -1701,6 +1743,8 @@ struct SnapCfg {
     int64_t has_prm, has_sched, n_knots, n_total, step, primed;
     int64_t knot_step[XY_MAX_KNOTS];
     double knot_T[XY_MAX_KNOTS];
+    int64_t sched_kind;
+    double pw[6];
 };
 }  // namespace
 
@@ -1720,7 +1764,7 @@ int xy_save(xy_lattice* L, void* buf, size_t* size)
     char* p = (char*)buf;
     SnapHeader hd{};
     std::memcpy(hd.magic, "XYLATT1", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.n_cfg = L->n_cfg;
     hd.total = L->total_sites;
     hd.B = L->B;
@@ -1734,6 +1778,8 @@ int xy_save(xy_lattice* L, void* buf, size_t* size)
         s.has_prm = h.has_prm;
         s.has_sched = h.has_sched;
         s.n_knots = h.n_knots;
+        s.sched_kind = h.sched_kind;
+        for (int i = 0; i < 6; ++i) s.pw[i] = h.pw[i];
         s.n_total = h.n_total;
         s.step = h.step;
         s.primed = h.primed;
@@ -1764,7 +1810,7 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
     SnapHeader hd;
     std::memcpy(&hd, p, sizeof hd);
     p += sizeof hd;
-    if (std::memcmp(hd.magic, "XYLATT1", 8) != 0 || hd.version != 1) return fail(XY_EINVAL, "not a snapshot");
+    if (std::memcmp(hd.magic, "XYLATT1", 8) != 0 || hd.version != 2) return fail(XY_EINVAL, "not a snapshot");
     if (hd.n_cfg != L->n_cfg || hd.total != L->total_sites || hd.B != L->B)
         return fail(XY_EINVAL, "snapshot shape does not match this lattice object");
     std::vector<SnapCfg> sc(L->n_cfg);
@@ -1785,6 +1831,8 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
         h.has_prm = s.has_prm != 0;
         h.has_sched = s.has_sched != 0;
         h.n_knots = (int)s.n_knots;
+        h.sched_kind = (int)s.sched_kind;
+        for (int i = 0; i < 6; ++i) h.pw[i] = s.pw[i];
         h.n_total = s.n_total;
         h.step = s.step;
         h.primed = s.primed != 0;
@@ -1797,6 +1845,7 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
             h.knot_T[i] = d.knot_T[i] = s.knot_T[i];
         }
         fill_schedule_f32(d);
+        fill_power_f32(d, h);
     }
     CK(cudaMemcpyAsync(L->d_moments, p, sizeof(double) * 6 * L->n_cfg, cudaMemcpyHostToDevice, L->stream));
     p += sizeof(double) * 6 * L->n_cfg;

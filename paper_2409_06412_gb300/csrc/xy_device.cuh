@@ -127,9 +127,17 @@ struct StepConst {
 
 // Temperature at step k: piecewise linear through the knots, constant outside
 // them, evaluated in FP32 from per-segment slopes (a few instructions per
-// thread block or warp; never FP64 on the stepping path).
+// thread block or warp; never FP64 on the stepping path); or the nonlinear
+// quench of order gamma.
 __device__ __forceinline__ float temperature_at(const DevCfg& cf, int64_t k)
 {
+    if (cf.sched_kind == 1) {  // nonlinear quench (Sec. VII), FP32
+        const float t = (float)(k - cf.pw_kc);
+        float eps = powf(__fmul_rn(fabsf(t), cf.pw_inv_tq), cf.pw_gamma);
+        eps = t >= 0.f ? -eps : eps;
+        eps = fminf(fmaxf(eps, cf.pw_ef), cf.pw_ei);
+        return __fmul_rn(cf.pw_Tc, __fadd_rn(1.0f, eps));
+    }
     if (cf.n_knots <= 1 || k <= cf.knot_step[0]) return cf.knot_Tf[0];
     for (int i = 0; i + 1 < cf.n_knots; ++i)
         if (k <= cf.knot_step[i + 1]) return fmaf(cf.slope_f[i], (float)(k - cf.knot_step[i]), cf.knot_Tf[i]);

@@ -20,7 +20,8 @@ struct DevCfg {
     // FP32 constants of the step
     float Jx, Jy, h, p, q, dt, hdt, oma, inv1pa, nqJx, nqJy, hp;
     double eta_d, dt_d;
-    int32_t n_knots, pad0;
+    int32_t n_knots;
+    int32_t sched_kind;  // 0: knots below; 1: nonlinear quench (pw_* fields)
     int64_t knot_step[XY_MAX_KNOTS];
     double knot_T[XY_MAX_KNOTS];
     // FP32 schedule used on the device: T(k) = knot_Tf[i] + slope_f[i] (k - knot_step[i])
@@ -28,6 +29,10 @@ struct DevCfg {
     float slope_f[XY_MAX_KNOTS];
     float amp_pref;     // (1/2) sqrt(2 eta dt): noise amplitude c_k = amp_pref sqrt(T_k)
     float pad1;
+    // nonlinear quench: T(k) = pw_Tc (1 + eps), eps = -sign(t) (|t| / tau_Q)^gamma, t = k - pw_kc,
+    // held within [pw_ef, pw_ei]
+    int64_t pw_kc;
+    float pw_Tc, pw_inv_tq, pw_gamma, pw_ei, pw_ef, pad2;
     int64_t n_total;
     // per call
     int64_t k_start;    // step at the start of the current call

@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
     const int rank_up = up / NB, lb_up = up - rank_up * NB;
     const int rank_dn = dn / NB, lb_dn = dn - rank_dn * NB;
     const StepConst K0 = step_const(cf, 0.f);
-    const bool const_T = cf.n_knots <= 1;
+    const bool const_T = cf.sched_kind == 0 && cf.n_knots <= 1;
     const float c_const = noise_amp(cf, 0);
     const bool stag = cf.stag != 0;
     const int64_t kbase = cf.k_start + ca.k_shift;

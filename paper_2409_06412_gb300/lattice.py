@@ -16,7 +16,9 @@ PAPER_PARAMS = dict(J_par=10.0, J_perp=0.1, h=1.0, p=2.5, q=2.0, eta=1.0, dt=0.0
 @dataclass
 class Config:
     """One configuration: n_replicas periodic Lx x Ly lattices sharing
-    parameters and a temperature schedule (knots of (step, T))."""
+    parameters and a temperature schedule: knots ((steps), (T)) of a
+    piecewise-linear schedule, or {"power": (T_c, k_cross, tau_Q, gamma,
+    eps_i, eps_f)} for the nonlinear quench of xy_set_power_quench."""
     Lx: int
     Ly: int
     n_replicas: int = 1
@@ -67,7 +69,10 @@ class Lattice:
                 off += c.Lx * c.Ly
         for ci, c in enumerate(self.configs):
             self.set_params(ci, **c.params)
-            self.set_schedule(ci, c.knots[0], c.knots[1], c.n_total)
+            if isinstance(c.knots, dict):
+                self.set_power_quench(ci, *c.knots["power"], n_total=c.n_total)
+            else:
+                self.set_schedule(ci, c.knots[0], c.knots[1], c.n_total)
 
     # ------------------------------------------------------------ setup
     def set_params(self, c: int, **kw):
@@ -84,6 +89,11 @@ class Lattice:
         Ts = np.ascontiguousarray(np.asarray(temps, dtype=np.float64))
         L.call("xy_set_schedule", self._h, c, ks.ctypes.data_as(ctypes.c_void_p),
                Ts.ctypes.data_as(ctypes.c_void_p), int(ks.size), int(n_total))
+
+    def set_power_quench(self, c: int, T_c: float, k_cross: int, tau_Q: float, gamma: float, eps_i: float,
+                         eps_f: float, n_total: int):
+        L.call("xy_set_power_quench", self._h, c, float(T_c), int(k_cross), float(tau_Q), float(gamma),
+               float(eps_i), float(eps_f), int(n_total))
 
     def set_path(self, path: int):
         L.call("xy_set_path", self._h, path)

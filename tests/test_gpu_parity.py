@@ -280,6 +280,32 @@ def test_quench_schedule_parity():
     assert np.abs(g[0, :16, 1] - o_rec[0][0][:, 1]).max() < 1e-4
 
 
+@pytest.mark.parametrize("gamma", [2.0, 3.0])
+def test_nonlinear_quench_parity(gamma):
+    """Nonlinear quench eps = -sign(t) |t / tau_Q|^gamma (Sec. VII) crossing T_c
+    inside a 100-step window, on the batched and the plain path, classified
+    like every trajectory parity test (cusp events, FP32 conditioning)."""
+    sched = {"power": (TC, 45, 40.0, gamma, 0.5, -0.9)}
+    specs = [inputs.config(Lx, Ly, n, seed=5 + i, knots=sched, n_total=400, eta=[0.5, 1.0][i % 2])
+             for i, (Lx, Ly, n) in enumerate([(64, 64, 2), (256, 32, 1), (12, 10, 1)])]
+    thetas = _mixed_thetas(specs, seed=33)
+    for path in (XY_PATH_BATCHED, XY_PATH_PLAIN):
+        lat, o_th, o_om = make_pair(specs, thetas, path=path)
+        res = stepwise_parity(lat, specs, o_th, o_om, 100)
+        assert res["step_now"] == [100] * len(specs)
+        assert not res["unexplained"], (path, res["unexplained"][:10], res["events"][:10], res["ill"][:10])
+        assert res["frac_within_tol"] > 1 - 1e-3
+    # the schedule survives a snapshot
+    lat2, _, _ = make_pair(specs, thetas)
+    lat2.step(60)
+    blob = lat2.save()
+    lat2.step(100)
+    a = lat2.theta.clone()
+    lat2.load(blob)
+    lat2.step(100)
+    assert torch.equal(a, lat2.theta)
+
+
 def test_staggered_order_parameter():
     specs = [inputs.config(64, 64, 2, seed=4, J_par=-10.0, J_perp=-0.1, staggered=1.0)]
     thetas = _mixed_thetas(specs, seed=41)
