@@ -262,15 +262,7 @@ namespace {
 
 constexpr int kMaxBandWarps = 16;  // Lx <= 2048
 
-// Asynchronous 16-byte global -> shared copies (one per lane and array), so
-// that the next row's data is in flight while the current row is computed.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 
 struct BandSC {
     float s[4], c[4];
@@ -402,7 +394,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
         const bool do_b = t - 1 >= y0;                      // phase B on row t-1
         const int st = (t - y0 + 1) & 1;
         prefetch(st ^ 1, r_p2, r_p1);
-        cp_async_wait1();  // this lane's copies of stage st have landed
+        cp_async_wait<1>();  // this lane's copies of stage st have landed
         const float4* sp = my_stage + st * kStage;
         const float4 th3 = sp[0 * 32 + lane];
         band_sc(K.q, th3, S3);

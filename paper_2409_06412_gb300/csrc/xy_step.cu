@@ -393,8 +393,19 @@ struct StripCtx {
 // All rows of the unit, one row per iteration with a sliding window of three
 // rows of (sin q t, cos q t); the raw angles run two rows ahead.  Row
 // pointers advance by Lx per row and wrap at the lattice end.
+// Rows staged by cp.async: slot i of a lane holds theta of row y_i + 2 (with
+// the strip's edge column) and v of row y_i, issued kStages - 1 rows ahead,
+// so that about two rows of every warp are in flight while one is computed.
+constexpr int kStages = 3;
+struct StripStage {
+    float4 th[kStages][32];
+    float4 v[kStages][32];
+    float te[kStages][32];
+};
+
 template <int REC>
-__device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const PhiloxKeys& keys, int ybeg, int H)
+__device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const PhiloxKeys& keys, int ybeg, int H,
+                                           StripStage& stg)
 {
     const int64_t Lx = X.Lx;
     const int64_t Nsites = Lx * X.Ly;
@@ -412,17 +423,35 @@ __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const 
     N.te = X.thS[yn * Lx + X.xe];
     rowbuf_sc(X.K.q, P);
     rowbuf_sc(X.K.q, C);
-    const float* p_nn = X.thS + ynn * Lx;           // row y + 2
-    const float* p_v = X.omS + (int64_t)ybeg * Lx;   // row y
     float* p_to = X.thD + (int64_t)ybeg * Lx;
     float* p_vo = X.omD + (int64_t)ybeg * Lx;
     uint32_t quad = (uint32_t)(((int64_t)ybeg * Lx + X.x) >> 2);
     const uint32_t dquad = (uint32_t)(Lx >> 2);
+    const int ln = (int)(threadIdx.x & 31);
+    const bool edge = X.multi && (X.lg == 0 || X.lg == 31);
+    const float* q_nn = X.thS + ynn * Lx;  // theta row of the next issue (y_i + 2)
+    int s_use = 0;                         // slot of row r; row i sits in slot i % kStages
+    // issue row i (theta of y_i + 2, v of y_i) into its slot; an empty group
+    // past the last row keeps the group count uniform
+    auto issue = [&](int i, int slot) {
+        if (i < H) {
+            cp_async16(&stg.th[slot][ln], q_nn + X.x);
+            cp_async16(&stg.v[slot][ln], X.omS + (int64_t)(ybeg + i) * Lx + X.x);
+            if (edge) cp_async4(&stg.te[slot][ln], q_nn + X.xe);
+            q_nn += Lx;
+            if (q_nn >= X.thS + Nsites) q_nn -= Nsites;
+        }
+        cp_async_commit();
+    };
+    for (int i = 0; i < kStages - 1; ++i) issue(i, i);
     for (int r = 0; r < H; ++r) {
         const int y = ybeg + r;
-        const float4 th_nn = ld4(p_nn + X.x);
-        const float te_nn = p_nn[X.xe];
-        const float4 v = ld4_stream(p_v + X.x);
+        issue(r + kStages - 1, s_use == 0 ? kStages - 1 : s_use - 1);
+        cp_async_wait<kStages - 1>();  // this lane's copies of row y have landed
+        const float4 th_nn = stg.th[s_use][ln];
+        const float te_nn = edge ? stg.te[s_use][ln] : 0.f;
+        const float4 v = stg.v[s_use][ln];
+        s_use = s_use + 1 == kStages ? 0 : s_use + 1;
         rowbuf_sc(X.K.q, N);
         float sL = __shfl_sync(kFull, C.s[3], X.srcL);
         float cL = __shfl_sync(kFull, C.c[3], X.srcL);
@@ -473,12 +502,9 @@ __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const 
         C = N;
         N.th = th_nn;
         N.te = te_nn;
-        p_v += Lx;
         p_to += Lx;
         p_vo += Lx;
         quad += dquad;
-        p_nn += Lx;
-        if (p_nn >= X.thS + Nsites) p_nn -= Nsites;
     }
 }
 
@@ -496,6 +522,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     const StripTask task = tasks[blockIdx.x];  // block-uniform
     const int unit = task.unit0 + warp;
     const bool live = unit < task.n_units;     // the lattice's last block may have idle warps
+    __shared__ StripStage s_stage[8];          // one per warp of the 256-thread block
     const DevCfg& cf = cfgs[task.cfg];
     const int64_t j = ca.j_base + j_local;
     if (j >= cf.n_call) return;
@@ -534,7 +561,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
         X.Jy = cf.Jy;
         X.hF = cf.h;
         X.stag = cf.stag != 0;
-        if (live) strip_rows<REC>(X, cf, keys, ybeg, H);
+        if (live) strip_rows<REC>(X, cf, keys, ybeg, H, s_stage[warp]);
         // one partial per block: warp sums, then the block's warps in order
         __shared__ double2 s_part[8];
         const double wm = warp_sumf(X.pm), we = warp_sumf(X.pe);
@@ -559,7 +586,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
                            c2.N);
         }
     } else if (live) {
-        strip_rows<0>(X, cf, keys, ybeg, H);
+        strip_rows<0>(X, cf, keys, ybeg, H, s_stage[warp]);
     }
 }
 
