@@ -425,6 +425,32 @@ def run_reference(args):
     }), flush=True)
 
 
+def profile_case(name):
+    """Small single-GPU cases for profiler captures (a few hundred MB on the
+    device, a few hundred launches): no JSON line, exit 0 when done."""
+    import torch
+    from paper_2409_06412_gb300 import Config, Lattice
+    if name == "adjoint-small":
+        # the differentiation shape (64 lattices of 256^2) over 200 steps, checkpoint every 100
+        lat = Lattice([Config(Lx=256, Ly=256, n_replicas=64, seed=1, init_mode=1, knots=((0,), (TC,)),
+                              n_total=10 ** 9)])
+        lat.step(10)
+        lat.adjoint(200, checkpoint_every=100, w_E=1.0, w_M=1.0)
+    elif name == "plain64":
+        # the plain-method lattice: 64 x 64, one replica, 300 steps
+        lat = Lattice([Config(Lx=64, Ly=64, n_replicas=1, seed=1, init_mode=0, knots=((0,), (TC,)),
+                              n_total=10 ** 9)])
+        lat.step(100)
+        lat.step(200)
+    elif name == "sf":
+        # structure factors of 64 lattices of 1024^2 for k < 16
+        lat = Lattice([Config(Lx=1024, Ly=1024, n_replicas=64, seed=1, init_mode=0, knots=((0,), (TC,)),
+                              n_total=10 ** 6)])
+        lat.step(2)
+        lat.structure_factor(0, 64, 16)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,7 +458,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["static", "static-L512"], default="static")
+    ap.add_argument("--profile-case", choices=["adjoint-small", "plain64", "sf"], default=None,
+                    help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     set_workload(args.workload)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
