@@ -706,7 +706,9 @@ __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 // Every lattice of one launch uses the noise key whose round keys are `keys`.
-template <int MAXT>
+// ONE_ROW: the launch's bands are one row high (R = 1), the specialisation
+// whose quads stay in registers; the other instantiation serves R > 1.
+template <int MAXT, bool ONE_ROW>
 __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cfgs, const ResidentTask* tasks,
                                                                 int64_t j_local, int n_steps, Buffers buf,
                                                                 const CallArgs* cap, PhiloxKeys keys)
@@ -732,7 +734,8 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
     const int x = 4 * lg;
     const int gb = (lane / G) * G;
     const int srcL = gb + (lg + G - 1) % G, srcR = gb + (lg + 1) % G;
-    const bool R1 = R == 1;  // a band's first and last rows coincide
+    constexpr bool R1 = ONE_ROW;  // a band's first and last rows coincide
+    if ((R == 1) != ONE_ROW) return;  // the host launches the matching instantiation (uniform)
 
     float* s_th = reinterpret_cast<float*>(smem4);
     float* s_om = s_th + Lr * Lx;
@@ -960,25 +963,35 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
     }
 }
 
-template <int MAXT>
-cudaError_t launch_resident_t(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int threads, int csize,
-                              size_t smem, int64_t j_local, int n_steps, Buffers buf, const CallArgs* ca,
-                              const PhiloxKeys& keys, cudaStream_t st)
+namespace {
+using ResidentFn = void (*)(const DevCfg*, const ResidentTask*, int64_t, int, Buffers, const CallArgs*, PhiloxKeys);
+
+// the instantiation for a block size and band height (rows of a band: the
+// block's Ly / csize rows over its threads / (Lx / 4) bands)
+ResidentFn resident_fn(int Lx, int Ly, int threads, int csize)
+{
+    const int R = (Ly / csize) / (threads / (Lx / 4));
+    if (threads > 512) return R == 1 ? resident_step_kernel<1024, true> : resident_step_kernel<1024, false>;
+    return R == 1 ? resident_step_kernel<512, true> : resident_step_kernel<512, false>;
+}
+
+cudaLaunchConfig_t resident_config(int n_tasks, int threads, int csize, size_t smem, cudaStream_t st,
+                                   cudaLaunchAttribute* at)
 {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)(n_tasks * csize));
     lc.blockDim = dim3((unsigned)threads);
     lc.dynamicSmemBytes = smem;
     lc.stream = st;
-    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)csize;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, resident_step_kernel<MAXT>, d_cfg, tasks, j_local, n_steps, buf, ca, keys);
+    return lc;
 }
+}  // namespace
 
 cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
                                  int threads, int csize, uint64_t seed, int64_t j_local, int n_steps, Buffers buf,
@@ -987,10 +1000,10 @@ cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks,
     if (n_tasks == 0) return cudaSuccess;
     const size_t smem = resident_smem_bytes(Lx, Ly, threads, csize);
     const PhiloxKeys keys = philox_round_keys(seed);
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t lc = resident_config(n_tasks, threads, csize, smem, st, at);
     const cudaError_t e =
-        threads > 512
-            ? launch_resident_t<1024>(d_cfg, tasks, n_tasks, threads, csize, smem, j_local, n_steps, buf, ca, keys, st)
-            : launch_resident_t<512>(d_cfg, tasks, n_tasks, threads, csize, smem, j_local, n_steps, buf, ca, keys, st);
+        cudaLaunchKernelEx(&lc, resident_fn(Lx, Ly, threads, csize), d_cfg, tasks, j_local, n_steps, buf, ca, keys);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1002,24 +1015,15 @@ cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks,
 cudaError_t prepare_resident(int Lx, int Ly, int threads, int csize, int* clusters)
 {
     const int smem = (int)resident_smem_bytes(Lx, Ly, threads, csize);
-    const void* fn = threads > 512 ? (const void*)resident_step_kernel<1024> : (const void*)resident_step_kernel<512>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess && csize > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const ResidentFn fn = resident_fn(Lx, Ly, threads, csize);
+    cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && csize > 8)
+        e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess || !clusters) return e;
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)csize);
-    lc.blockDim = dim3((unsigned)threads);
-    lc.dynamicSmemBytes = (size_t)smem;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)csize;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
+    const cudaLaunchConfig_t lc = resident_config(1, threads, csize, (size_t)smem, nullptr, at);
     *clusters = 0;
-    e = threads > 512 ? cudaOccupancyMaxActiveClusters(clusters, resident_step_kernel<1024>, &lc)
-                      : cudaOccupancyMaxActiveClusters(clusters, resident_step_kernel<512>, &lc);
+    e = cudaOccupancyMaxActiveClusters(clusters, (const void*)fn, &lc);
     if (e != cudaSuccess) {  // an unsupported cluster shape is "does not fit", not a failure
         cudaGetLastError();
         *clusters = 0;
