@@ -187,10 +187,32 @@ int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, 
  * d(J_par, J_perp, h, eta) of configuration c.  The full-step state at k0 is
  * held fixed; the wrap has derivative 1; the kink of the field potential at
  * +-pi/2 contributes nothing (derivative almost everywhere).  The state is
- * checkpointed every checkpoint_every steps and each segment recomputed
- * before its reverse sweep.  objective, grads: host. */
+ * checkpointed every checkpoint_every steps; the reverse sweep gets the states
+ * of each segment as xy_set_adjoint_mode() selects.  objective, grads: host. */
 int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w_E, double w_M,
                       double* objective, double* grads);
+
+/* How the reverse sweep of xy_adjoint_step_n() gets the states of a
+ * checkpoint segment (the paper has no adjoint; this is the schedule of the
+ * pathwise derivative of the App. A.1 integrator):
+ *   XY_ADJOINT_RECOMPUTE: recomputed forward from the checkpoint at the
+ *     segment's start and stored (K + 1 states, 8 B per site each); the
+ *     gradient is that of the forward trajectory to rounding of the sums.
+ *   XY_ADJOINT_BACKWARD: integrated backward inside the reverse kernel from
+ *     the checkpoint at the segment's end, theta_k = wrap(theta_{k+1} - dt
+ *     v_{k+1}), omega_k = (v_{k+1} - g_k) / (1 - eta dt / 2), with the noise
+ *     regenerated; no segment storage and no separate recompute pass.  FP32
+ *     inversion recovers the forward states to ~1e-6 rad near equilibrium;
+ *     far from it (random starts) unstable bonds amplify that to ~1e-3 rad
+ *     at a few sites by the segment's start.  Needs the shapes of the band
+ *     kernels (Lx a multiple of 128 up to 2048, or Lx <= 128 with Lx / 4
+ *     dividing 32; Ly >= 2): XY_EINVAL at the adjoint call otherwise.
+ *   XY_ADJOINT_AUTO (default): backward where every shape allows it, else
+ *     recompute. */
+#define XY_ADJOINT_AUTO 0
+#define XY_ADJOINT_RECOMPUTE 1
+#define XY_ADJOINT_BACKWARD 2
+int xy_set_adjoint_mode(xy_lattice* lat, int mode);
 
 /* Structure factors of the rotor lattice (Sec. VI, Eq. FT-Corr-delta and
  * Eq. S-as-lattice-FT), the input of the Lorentzian correlation-length fit of

@@ -13,6 +13,7 @@ from . import build as _build
 XY_OK, XY_EINVAL, XY_ENOMEM, XY_ECUDA, XY_ETIMEOUT, XY_ENAN = 0, -1, -2, -3, -4, -5
 XY_INIT_UNIFORM, XY_INIT_ORDERED, XY_INIT_USER = 0, 1, 2
 XY_PATH_BATCHED, XY_PATH_PLAIN = 0, 1
+XY_ADJOINT_AUTO, XY_ADJOINT_RECOMPUTE, XY_ADJOINT_BACKWARD = 0, 1, 2
 XY_MAX_KNOTS = 16
 XY_STATIC_CCL_MAX_SITES, XY_STATIC_CCL_MAX_LATTICES = 2097152, 65536
 
@@ -45,6 +46,7 @@ SIGNATURES = {
     "xy_omega_full": (_i32, [_vp, _i32, _i32, _vp]),
     "xy_label_domains": (_i32, [_vp, _i32, _i32, _vp, _vp, _i64, _vp]),
     "xy_adjoint_step_n": (_i32, [_vp, _i64, _i32, _d, _d, _vp, _vp]),
+    "xy_set_adjoint_mode": (_i32, [_vp, _i32]),
     "xy_label_domains_static": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i64, _vp, _vp]),
     "xy_structure_factor": (_i32, [_vp, _i32, _i32, _i32, _d, _vp, _vp]),
     "xy_autocorr_time": (_i32, [_vp, _i64, _i64, _i32, _i32, _i64, _i64, _d, _vp, _vp]),

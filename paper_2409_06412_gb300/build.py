@@ -20,10 +20,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libxy_gb300.so")
-SOURCES = ["xy_step.cu", "xy_ccl.cu", "xy_adjoint.cu", "xy_api.cu", "xy_noalloc.cu", "xy_sf.cu", "xy_tau.cu"]
+SOURCES = ["xy_step.cu", "xy_ccl.cu", "xy_adjoint.cu", "xy_adjoint_back.cu", "xy_api.cu", "xy_noalloc.cu", "xy_sf.cu", "xy_tau.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off"]
-FMAD_ON = {"xy_adjoint.cu"}
+FMAD_ON = {"xy_adjoint.cu", "xy_adjoint_back.cu"}
 
 
 def nvcc() -> str:

@@ -205,6 +205,7 @@ struct xy_lattice {
     size_t rec_cap = 0;
     int* d_err = nullptr;
     int path = XY_PATH_BATCHED;
+    int adj_mode = XY_ADJOINT_AUTO;
     std::vector<ResGroup> res_groups;
     std::vector<StripGroup> strip_groups;
     std::vector<int> plain_cfgs;
@@ -1096,6 +1097,15 @@ int xy_set_path(xy_lattice* L, int path)
     return XY_OK;
 }
 
+int xy_set_adjoint_mode(xy_lattice* L, int mode)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (mode != XY_ADJOINT_AUTO && mode != XY_ADJOINT_RECOMPUTE && mode != XY_ADJOINT_BACKWARD)
+        return fail(XY_EINVAL, "unknown adjoint mode %d", mode);
+    L->adj_mode = mode;
+    return XY_OK;
+}
+
 int xy_step_n(xy_lattice* L, int64_t n, int record_every, double* rec, int64_t t0)
 {
     if (!L) return fail(XY_EINVAL, "NULL lattice");
@@ -1375,8 +1385,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     }
     for (int c = 0; c < L->n_cfg; ++c) {
         const xy_config_desc& d = L->cfg[c].desc;
-        const bool wide_ok = d.Lx > 128 && d.Lx % 128 == 0 && d.Lx <= 2048;
-        const bool narrow_ok = d.Lx <= 128 && 32 % (d.Lx / 4) == 0;
+        const bool wide_ok = d.Lx > 128 && d.Lx % 128 == 0 && d.Lx <= 2048 && d.Ly >= 2;
+        const bool narrow_ok = d.Lx <= 128 && 32 % (d.Lx / 4) == 0 && d.Ly >= 2;
         if (!wide_ok && !narrow_ok) {
             adj_plain.push_back(c);
             continue;
@@ -1415,20 +1425,31 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         }
         return H;
     };
-    float *ck = nullptr, *seg = nullptr, *adjb = nullptr, *Fb = nullptr;
+    // states of a segment: integrated backward from the checkpoint at its end
+    // inside the reverse kernel (band shapes only), or recomputed forward
+    // from the checkpoint at its start and stored
+    if (L->adj_mode == XY_ADJOINT_BACKWARD && (!adj_plain.empty() || adj_groups.empty()))
+        return fail(XY_EINVAL, "backward integration needs shapes of the band kernels (Lx a multiple of 128 "
+                               "up to 2048, or Lx <= 128 with Lx / 4 dividing 32; Ly >= 2)");
+    const bool back = L->adj_mode != XY_ADJOINT_RECOMPUTE && adj_plain.empty() && !adj_groups.empty();
+    float *ck = nullptr, *seg = nullptr, *adjb = nullptr, *Fb = nullptr, *sbuf = nullptr;
     double2* arec = nullptr;
-    double* gacc = nullptr;
+    double *gacc = nullptr, *mpart = nullptr;
     auto cleanup = [&]() {
         for (auto& g : adj_groups) cudaFree(g.d_tasks);
         cudaFree(ck);
         cudaFree(seg);
+        cudaFree(sbuf);
         cudaFree(adjb);
         cudaFree(Fb);
         cudaFree(arec);
         cudaFree(gacc);
+        cudaFree(mpart);
     };
     cudaError_t e = cudaMalloc(&ck, sizeof(float) * 2 * T * nseg);
-    if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * 2 * T * (K + 1));
+    // backward: two recovered states (ping-pong); recompute: the K + 1 states of a segment
+    if (e == cudaSuccess && back) e = cudaMalloc(&sbuf, sizeof(float) * 4 * T);
+    if (e == cudaSuccess && !back) e = cudaMalloc(&seg, sizeof(float) * 2 * T * (K + 1));
     // adjoint state, double-buffered: (tb, vb) of two time levels
     if (e == cudaSuccess) e = cudaMalloc(&adjb, sizeof(float) * 4 * T);
     if (e == cudaSuccess && !adj_plain.empty()) e = cudaMalloc(&Fb, sizeof(float) * T);
@@ -1445,12 +1466,13 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         bool zeroed = false;
         for (auto& g : adj_groups) {
             char key[256];
-            snprintf(key, sizeof key, "%s|adjband|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
+            snprintf(key, sizeof key, "%s|%s|%d|%d|%lld", gpu.c_str(), back ? "adjback" : "adjband", g.Lx, g.Ly,
+                     (long long)g.n_lat);
             int bh = 0, unused = 0;
             const bool big = (int64_t)g.Lx * g.Ly * g.n_lat >= ((int64_t)1 << 21);
             if (L->autotune && big && !g_tune.get(key, &bh, &unused)) {
                 if (!zeroed) {
-                    e = cudaMemsetAsync(seg, 0, sizeof(float) * 4 * T, L->stream);
+                    e = cudaMemsetAsync(back ? sbuf : seg, 0, sizeof(float) * 4 * T, L->stream);
                     if (e == cudaSuccess) e = cudaMemsetAsync(adjb, 0, sizeof(float) * 4 * T, L->stream);
                     if (e == cudaSuccess) e = cudaMemsetAsync(arec, 0, sizeof(double2) * L->B * R_, L->stream);
                     zeroed = true;
@@ -1466,16 +1488,36 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 }
                 BandTask* d_tk = nullptr;
                 double* g_tmp = nullptr;
+                double* mp_tmp = nullptr;
+                const int Pt = g.Ly / 4 + 1;  // partials per lattice for any candidate H >= 4
                 cudaEvent_t e0 = nullptr, e1 = nullptr;
                 if (e == cudaSuccess) e = cudaMalloc(&d_tk, sizeof(BandTask) * max_tasks);
                 if (e == cudaSuccess) e = cudaMalloc(&g_tmp, sizeof(double) * kGacc * max_tasks);
-                if (e == cudaSuccess) e = cudaEventCreate(&e0);
-                if (e == cudaSuccess) e = cudaEventCreate(&e1);
-                float best = 1e30f;
-                for (int h : cands) {
-                    if (e != cudaSuccess) break;
-                    band_tasks(g, h, tk);
-                    e = cudaMemcpy(d_tk, tk.data(), sizeof(BandTask) * tk.size(), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess && back) e = cudaMalloc(&mp_tmp, sizeof(double) * 2 * Pt * L->B);
+                if (e == cudaSuccess && back) e = cudaMemsetAsync(mp_tmp, 0, sizeof(double) * 2 * Pt * L->B, L->stream);
+                // one timed reverse launch of candidate band height h on zeroed buffers
+                auto tune_launch = [&](int h) -> cudaError_t {
+                    if (back) {
+                        BackArgs A{};
+                        A.th_in = sbuf;
+                        A.v_in = sbuf + T;
+                        A.th_out = sbuf + 2 * T;
+                        A.v_out = sbuf + 3 * T;
+                        A.tb_in = adjb;
+                        A.vb_in = adjb + T;
+                        A.tb_out = adjb + 2 * T;
+                        A.vb_out = adjb + 3 * T;
+                        A.mpart = mp_tmp;
+                        A.P = Pt;
+                        A.rec = arec;
+                        A.rec_stride = R_;
+                        A.k = n >= 2 ? k0 + 1 : k0;
+                        A.k0 = k0;
+                        A.wE = (float)wE;
+                        A.wM = (float)wM;
+                        A.gacc = g_tmp;
+                        return launch_adjoint_back(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, true, A, L->stream);
+                    }
                     BandArgs R{};
                     R.theta = seg;
                     R.omega = seg + T;
@@ -1491,13 +1533,21 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                     R.wE = (float)wE;
                     R.wM = (float)wM;
                     R.gacc = g_tmp;
+                    return launch_adjoint_band(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, R, L->stream);
+                };
+                if (e == cudaSuccess) e = cudaEventCreate(&e0);
+                if (e == cudaSuccess) e = cudaEventCreate(&e1);
+                float best = 1e30f;
+                for (int h : cands) {
+                    if (e != cudaSuccess) break;
+                    band_tasks(g, h, tk);
+                    e = cudaMemcpy(d_tk, tk.data(), sizeof(BandTask) * tk.size(), cudaMemcpyHostToDevice);
                     int reps = 2;
                     float t_best = 1e30f;
                     for (int round = 0; round < 5 && e == cudaSuccess; ++round) {
-                        e = launch_adjoint_band(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, R, L->stream);
+                        e = tune_launch(h);
                         if (e == cudaSuccess) e = cudaEventRecord(e0, L->stream);
-                        for (int i = 0; i < reps && e == cudaSuccess; ++i)
-                            e = launch_adjoint_band(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, R, L->stream);
+                        for (int i = 0; i < reps && e == cudaSuccess; ++i) e = tune_launch(h);
                         if (e == cudaSuccess) e = cudaEventRecord(e1, L->stream);
                         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                         float ms = 0.f;
@@ -1516,6 +1566,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 cudaStreamSynchronize(L->stream);
                 cudaFree(d_tk);
                 cudaFree(g_tmp);
+                cudaFree(mp_tmp);
                 if (e != cudaSuccess) {
                     cudaGetLastError();
                     cleanup();
@@ -1542,6 +1593,13 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
             e = cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(BandTask) * g.tasks.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&gacc, sizeof(double) * kGacc * n_blocks);
+    // backward integration: per-block partial sums of M, two step slots per lattice
+    int P = 1;
+    for (auto& g : adj_groups) {
+        const int per_block = g.wide ? 1 : 8 * (32 / (g.Lx / 4));
+        P = std::max(P, (g.Ly / g.H + per_block - 1) / per_block);
+    }
+    if (e == cudaSuccess && back) e = cudaMalloc(&mpart, sizeof(double) * 2 * P * L->B);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cleanup();
@@ -1568,8 +1626,10 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     RCA(sp.open(XY_KCLASS_ADJ_FWD));
     // ---- forward with checkpoints; observables at every step
     for (int64_t s = 0; s < nseg; ++s) {
-        CKA(cudaMemcpyAsync(ck + 2 * T * s, L->thA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
-        CKA(cudaMemcpyAsync(ck + 2 * T * s + T, L->omA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
+        if (s > 0 || !back) {  // backward integration starts every segment from its end
+            CKA(cudaMemcpyAsync(ck + 2 * T * s, L->thA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
+            CKA(cudaMemcpyAsync(ck + 2 * T * s + T, L->omA, state_bytes, cudaMemcpyDeviceToDevice, L->stream));
+        }
         const int64_t ns = std::min<int64_t>(K, n - s * K);
         RCA(advance_core(L, ns, 0, nullptr, 0, false, 0));
     }
@@ -1587,6 +1647,55 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     int acur = 0;  // adjoint state of step k + 1 in slot acur, of step k written to slot 1 - acur
     auto tb_of = [&](int slot) { return adjb + (int64_t)slot * 2 * T; };
     auto vb_of = [&](int slot) { return adjb + (int64_t)slot * 2 * T + T; };
+    if (back) {
+        // ---- reverse sweep with the states integrated backward: step k0 + n
+        // from the final state, then every step k from the state of k + 1 (the
+        // checkpoint when k + 1 starts a segment, else the previous launch's output)
+        Span sv{L};
+        RCA(sv.open(XY_KCLASS_ADJ_REV));
+        const float* in_th = L->thA;
+        const float* in_v = L->omA;
+        int sb = 0;
+        for (int64_t k = k0 + n; k >= k0; --k) {
+            const bool bk = k < k0 + n;
+            const int64_t m = k + 1 - k0;
+            if (bk && m < n && m % K == 0) {
+                in_th = ck + 2 * T * (m / K);
+                in_v = in_th + T;
+            }
+            float* out_th = sbuf + 2 * T * sb;
+            for (auto& g : adj_groups) {
+                BackArgs A{};
+                A.th_in = in_th;
+                A.v_in = in_v;
+                A.th_out = bk ? out_th : nullptr;
+                A.v_out = bk ? out_th + T : nullptr;
+                A.tb_in = tb_of(acur);
+                A.vb_in = vb_of(acur);
+                A.tb_out = tb_of(1 - acur);
+                A.vb_out = vb_of(1 - acur);
+                A.mpart = mpart;
+                A.P = P;
+                A.rec = arec;
+                A.rec_stride = R_;
+                A.k = k;
+                A.k0 = k0;
+                A.wE = (float)wE;
+                A.wM = (float)wM;
+                A.gacc = gacc;
+                A.block_base = g.block_base;
+                CKA(launch_adjoint_back(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.H, g.seed, bk, A, L->stream));
+                ++L->launches;
+            }
+            if (bk) {
+                in_th = out_th;
+                in_v = out_th + T;
+                sb ^= 1;
+            }
+            acur = 1 - acur;
+        }
+        RCA(sv.close());
+    }
     // reverse step k from the states at segment slot i
     auto rev_step = [&](int64_t k, int64_t i) -> int {
         const float* th = seg + 2 * T * i;
@@ -1643,7 +1752,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         acur = 1 - acur;
         return XY_OK;
     };
-    for (int64_t s = nseg - 1; s >= 0; --s) {
+    for (int64_t s = back ? -1 : nseg - 1; s >= 0; --s) {
         const int64_t ks = k0 + s * K;
         const int64_t Ks = std::min<int64_t>(K, n - s * K);
         const int64_t n_states = (s == nseg - 1) ? Ks + 1 : Ks;  // the last segment also needs k0 + n

@@ -185,6 +185,28 @@ struct BandArgs {
     double* gacc;        // [blocks][kGacc]
     int block_base;
 };
+// Reverse step on row bands with the state of step k integrated backward
+// from step k + 1 (xy_adjoint_back.cu).
+struct BackArgs {
+    const float* th_in;  // theta_{k+1} (backward launches) or theta_k (the first launch)
+    const float* v_in;   // v_{k+1} or v_k
+    float* th_out;       // theta_k, v_k recovered (backward launches; rows of the own bands)
+    float* v_out;
+    const float* tb_in;  // adjoints of (theta_{k+1}, v_{k+1}), without the |M_{k+1}| term
+    const float* vb_in;
+    float* tb_out;       // adjoints of (theta_k, v_k), without the |M_k| term
+    float* vb_out;
+    double* mpart;       // [B][2][P] per-block sums of sigma sin(q theta): slot k & 1 written
+    int P;               // partial slots per lattice
+    double2* rec;        // [B][rec_stride]: M_{k+1} written to .x of column k + 1 - k0
+    int64_t rec_stride;
+    int64_t k, k0;
+    float wE, wM;
+    double* gacc;        // [blocks][kGacc]
+    int block_base;
+};
+cudaError_t launch_adjoint_back(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, uint64_t seed,
+                                bool back, BackArgs R, cudaStream_t st);
 // M_k of slots [0, n_states) of a segment (slot stride 2 T floats) into
 // rec[b * rec_stride + r0 + slot].x
 cudaError_t launch_segment_m(const DevCfg* d_cfg, int n_cfg, int64_t B, const float* seg, int64_t T, int n_states,

@@ -162,6 +162,11 @@ class Lattice:
                _ptr(S_perp))
         return S_par, S_perp
 
+    def set_adjoint_mode(self, mode: int):
+        """XY_ADJOINT_AUTO, XY_ADJOINT_RECOMPUTE or XY_ADJOINT_BACKWARD: how the
+        reverse sweep gets the states of a checkpoint segment."""
+        L.call("xy_set_adjoint_mode", self._h, int(mode))
+
     def adjoint(self, n: int, checkpoint_every: int = 100, w_E: float = 1.0, w_M: float = 0.0):
         obj = ctypes.c_double()
         grads = np.zeros((len(self.configs), 4), dtype=np.float64)

@@ -17,7 +17,8 @@ import pytest
 import torch
 
 import oracle
-from paper_2409_06412_gb300 import XY_PATH_BATCHED, XY_PATH_PLAIN, XYError, build, debug_noise, debug_philox
+from paper_2409_06412_gb300 import (XY_ADJOINT_AUTO, XY_ADJOINT_BACKWARD, XY_ADJOINT_RECOMPUTE, XY_PATH_BATCHED,
+                                    XY_PATH_PLAIN, XYError, build, debug_noise, debug_philox)
 from paper_2409_06412_gb300.lattice import Config, Lattice
 from tests import inputs
 from tests.gpu_helpers import circ_diff, make_pair, split_state, stepwise_parity, theta_parity
@@ -417,19 +418,29 @@ def _oracle_adjoint(specs, o_th, o_om, n, wE, wM):
     return obj / (B * n), np.array(grads)
 
 
+@pytest.mark.parametrize("mode", ["recompute", "backward"])
 @pytest.mark.parametrize("field", ["smooth_p2", "paper_p2.5_lowT"])
-def test_adjoint_matches_oracle(field):
+def test_adjoint_matches_oracle(field, mode):
     if field == "smooth_p2":
         prm = dict(J_par=2.0, J_perp=0.5, h=1.0, p=2.0, eta=0.8)
         knots = ([0, 100], [1.0, 0.5])
     else:
         prm = dict(h=3.0)
         knots = ([0], [0.05])
-    # fused strip reverse kernel (16 x 8 with sub-warp rows, 128 x 4) and the
-    # per-quad fallback (12 x 10, a width the strip decomposition does not take)
-    specs = [inputs.config(16, 8, 2, seed=3, knots=knots, **prm),
-             inputs.config(128, 4, 1, seed=4, knots=knots, **prm),
-             inputs.config(12, 10, 1, seed=4, knots=knots, **prm)]
+    if mode == "recompute":
+        # band reverse kernel (16 x 8 with sub-warp rows, 128 x 4) and the
+        # per-quad fallback (12 x 10, a width the band decomposition does not
+        # take), each segment recomputed forward
+        specs = [inputs.config(16, 8, 2, seed=3, knots=knots, **prm),
+                 inputs.config(128, 4, 1, seed=4, knots=knots, **prm),
+                 inputs.config(12, 10, 1, seed=4, knots=knots, **prm)]
+    else:
+        # states integrated backward inside the reverse kernel: sub-warp rows,
+        # one full-warp row, and two 128-column strips side by side (one row
+        # per band: every row is a halo row of the neighbouring bands)
+        specs = [inputs.config(16, 8, 2, seed=3, knots=knots, **prm),
+                 inputs.config(128, 4, 1, seed=4, knots=knots, **prm),
+                 inputs.config(256, 6, 1, seed=5, knots=knots, **prm)]
     if field == "smooth_p2":
         thetas = _mixed_thetas(specs, seed=61)
     else:
@@ -437,6 +448,7 @@ def test_adjoint_matches_oracle(field):
                   0.05 * inputs.velocities(s["n_rep"], s["Lx"], s["Ly"], 62 + i) for i, s in enumerate(specs)]
         thetas = [t.astype(np.float32) for t in thetas]
     lat, o_th, o_om = make_pair(specs, thetas)
+    lat.set_adjoint_mode(XY_ADJOINT_RECOMPUTE if mode == "recompute" else XY_ADJOINT_BACKWARD)
     n, K = 100, 30
     obj, grads = lat.adjoint(n, checkpoint_every=K, w_E=0.7, w_M=0.3)
     o_obj, o_grads = _oracle_adjoint(specs, o_th, o_om, n, 0.7, 0.3)
@@ -445,6 +457,45 @@ def test_adjoint_matches_oracle(field):
     assert np.all(np.abs(grads - o_grads) <= 1e-3 * scale), (grads, o_grads)
     _, steps = lat.observe()
     assert list(steps) == [n, n, n]
+
+
+def test_adjoint_modes_agree_on_wide_strips():
+    """Backward integration against the stored recompute on lattices of 128-
+    and 256-column strips at T_c from the ordered state, with n a multiple of
+    the checkpoint interval (the last segment ends at the final state) and
+    not: gradients and objective agree to rounding of the recovered states,
+    and the state after the call is the same forward state."""
+    specs = [inputs.config(384, 32, 2, seed=7, knots=([0], [TC])), inputs.config(256, 16, 3, seed=8, knots=([0], [TC]))]
+    thetas = [np.full((s["n_rep"], s["Lx"] * s["Ly"]), np.float32(2 * PI / 5)) +
+              0.02 * inputs.velocities(s["n_rep"], s["Lx"], s["Ly"], 80 + i) for i, s in enumerate(specs)]
+    thetas = [t.astype(np.float32) for t in thetas]
+    for n, K in ((120, 40), (130, 40)):
+        res = {}
+        for mode in (XY_ADJOINT_RECOMPUTE, XY_ADJOINT_BACKWARD):
+            lat, _, _ = make_pair(specs, thetas)
+            lat.step(20)
+            lat.set_adjoint_mode(mode)
+            obj, grads = lat.adjoint(n, checkpoint_every=K, w_E=1.0, w_M=1.0)
+            res[mode] = (obj, grads, lat.theta.cpu().numpy().copy())
+            lat.close()
+        (o1, g1, t1), (o2, g2, t2) = res[XY_ADJOINT_RECOMPUTE], res[XY_ADJOINT_BACKWARD]
+        assert np.array_equal(t1, t2)
+        assert o2 == pytest.approx(o1, rel=1e-6)
+        scale = np.abs(g1).max(axis=1, keepdims=True)
+        assert np.all(np.abs(g2 - g1) <= 1e-4 * scale), (n, g1, g2)
+
+
+def test_backward_adjoint_rejects_other_shapes():
+    specs = [inputs.config(12, 10, 1, seed=4, knots=([0], [1.0]))]
+    lat, _, _ = make_pair(specs, _mixed_thetas(specs))
+    lat.set_adjoint_mode(XY_ADJOINT_BACKWARD)
+    with pytest.raises(XYError):
+        lat.adjoint(10, checkpoint_every=5)
+    with pytest.raises(XYError):
+        lat.set_adjoint_mode(7)
+    lat.set_adjoint_mode(XY_ADJOINT_AUTO)  # falls back to the recompute for this shape
+    obj, grads = lat.adjoint(10, checkpoint_every=5)
+    assert np.isfinite(obj) and np.all(np.isfinite(grads))
 
 
 def test_adjoint_autograd_function():
