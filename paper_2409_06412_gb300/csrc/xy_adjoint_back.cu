@@ -70,11 +70,11 @@ __device__ __forceinline__ float warp_sumf_b(float v)
 
 // WIDE: Lx > 128 (a block spans one band of Lx / 128 strips); OBS: k > k0;
 // BACK: the state of step k is recovered from that of step k + 1 (every
-// launch but the first, which reads the final state itself).  MAXR: register
-// cap, 144 (7 blocks of 64 threads per SM) up to 448 threads per block, 128
-// for the 512 threads of Lx = 2048.
-template <bool WIDE, bool OBS, bool BACK, int MAXR>
-__global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const BandTask* tasks, int H,
+// launch but the first, which reads the final state itself).  At 128
+// registers an SM partition holds four warps (16 per SM), enough for bands
+// of 16 rows on 64 lattices of 256 x 256 to run in one wave.
+template <bool WIDE, bool OBS, bool BACK>
+__global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs, const BandTask* tasks, int H,
                                                               BackArgs R, PhiloxKeys keys)
 {
     // per warp, two stages of [theta_in(t+1), v_in, tb(t), vb(t)] for its 32 lanes
@@ -146,7 +146,7 @@ __global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const 
     // window: S0 = row t-2, S1 = t-1, S2 = t, S3 = t+1 (of theta_k); F0 = F-bar(t-2), F1 = t-1
     SCb S0, S1, S2, S3;
     float4 F0 = make_float4(0.f, 0.f, 0.f, 0.f), F1 = F0;
-    float4 th2, tbp1 = F0, cp1 = F0;  // theta_k of row t; tb partial and cos(p theta) of row t-1
+    float4 th2, tbp1 = F0;  // theta_k of row t; tb partial of row t-1 (site-local terms of phase B folded in)
     float4 t1c = F0, v1c = F0;        // BACK: theta_{k+1}, v_{k+1} of row t
     const int Nl = Lx * Ly;
     auto rowp = [&](int y) { return wrapb(y, Ly) * Lx; };
@@ -212,7 +212,7 @@ __global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const 
         scb4(K.q, th3, S3);
         publish_sc(sl_p1, S3);
         // ---------------- phase A on row t
-        float4 Fn = make_float4(0.f, 0.f, 0.f, 0.f), tbpn = Fn, cpn = Fn;
+        float4 Fn = make_float4(0.f, 0.f, 0.f, 0.f), tbpn = Fn;
         {
             float4 tb4 = sp[2 * 32 + lane];
             const float4 vb4 = sp[3 * 32 + lane];
@@ -231,7 +231,7 @@ __global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const 
             nbr_sc(sl_0, S2, sL, cL, sR, cR);
             const uint32_t quad = (uint32_t)((r_0 + x) >> 2);
             const float4 nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.k, 0u), keys), K.c);
-            float tbo[4], vbo[4], fbo[4], cpo[4], vko[4];
+            float tbo[4], vbo[4], fbo[4], vko[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float s_ = S2.s[i], c_ = S2.c[i];
@@ -283,10 +283,10 @@ __global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const 
                     abar = fmaf(-om, vbt, abar);
                     cbar = fmaf(gb, cn, cbar);
                 }
-                tbo[i] = tbi;
+                // the field's diagonal Hessian term of phase B, h p^2 cos(p t) F-bar, is site-local
+                tbo[i] = fmaf(hp2 * cp, fb, tbi);
                 vbo[i] = vbk;
                 fbo[i] = fb;
-                cpo[i] = cp;
                 vko[i] = vk;
             }
             if (own_a) {
@@ -298,7 +298,6 @@ __global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const 
             }
             Fn = make_float4(fbo[0], fbo[1], fbo[2], fbo[3]);
             tbpn = make_float4(tbo[0], tbo[1], tbo[2], tbo[3]);
-            cpn = make_float4(cpo[0], cpo[1], cpo[2], cpo[3]);
             if (wide) {
                 if (lane == 0) s_fb[t & 1][warp][0] = Fn.x;
                 if (lane == 31) s_fb[t & 1][warp][1] = Fn.w;
@@ -326,9 +325,7 @@ __global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const 
                 const float kd = fmaf(S1.c[i], S2.c[i], S1.s[i] * S2.s[i]);
                 const float hx = fmaf(kl, fl - fj, kr * (fr - fj));
                 const float hy = fmaf(ku, f4get(F0, i) - fj, kd * (f4get(Fn, i) - fj));
-                float acc = fmaf(q2Jx, hx, q2Jy * hy);
-                acc = fmaf(hp2, f4get(cp1, i) * fj, acc);
-                out[i] = f4get(tbp1, i) + acc;
+                out[i] = f4get(tbp1, i) + fmaf(q2Jx, hx, q2Jy * hy);
             }
             if (active) st4(tbO + r_m1 + x, make_float4(out[0], out[1], out[2], out[3]));
         }
@@ -342,7 +339,6 @@ __global__ void __maxnreg__(MAXR) adjoint_back_kernel(const DevCfg* cfgs, const 
         F0 = F1;
         F1 = Fn;
         tbp1 = tbpn;
-        cp1 = cpn;
         r_m1 = r_0;
         r_0 = r_p1;
         r_p1 = r_p2;
@@ -391,14 +387,13 @@ cudaError_t launch_adjoint_back(const DevCfg* d_cfg, const BandTask* tasks, int 
     const int smem = (threads / 32) * 2 * 4 * 32 * (int)sizeof(float4);
     const bool obs = R.k > R.k0;
     using Kern = void (*)(const DevCfg*, const BandTask*, int, BackArgs, PhiloxKeys);
-#define XY_BACK_TABLE(R)                                                                                      \
-    {{{adjoint_back_kernel<false, false, false, R>, adjoint_back_kernel<false, false, true, R>},                 \
-      {adjoint_back_kernel<false, true, false, R>, adjoint_back_kernel<false, true, true, R>}},                  \
-     {{adjoint_back_kernel<true, false, false, R>, adjoint_back_kernel<true, false, true, R>},                   \
-      {adjoint_back_kernel<true, true, false, R>, adjoint_back_kernel<true, true, true, R>}}}
-    static const Kern table[2][2][2][2] = {XY_BACK_TABLE(144), XY_BACK_TABLE(128)};
-#undef XY_BACK_TABLE
-    const Kern kern = table[threads > 448][wide][obs][back];
+    static const Kern table[2][2][2] = {
+        {{adjoint_back_kernel<false, false, false>, adjoint_back_kernel<false, false, true>},
+         {adjoint_back_kernel<false, true, false>, adjoint_back_kernel<false, true, true>}},
+        {{adjoint_back_kernel<true, false, false>, adjoint_back_kernel<true, false, true>},
+         {adjoint_back_kernel<true, true, false>, adjoint_back_kernel<true, true, true>}},
+    };
+    const Kern kern = table[wide][obs][back];
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
