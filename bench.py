@@ -36,6 +36,7 @@ LS_FULL = (128, 256, 512, 1024)
 LS = LS_FULL
 N_TEMPS, N_REP = 32, 16
 INNER = 10            # BBK steps per bench step
+REF_INNER = 4         # BBK steps per step of the reference arm (the oracle on the host cores)
 N_TOTAL = 10 ** 5     # run length of every configuration
 T0 = N_TOTAL // 5     # moments discard the first fifth
 METRIC = "site-updates/s/GPU and % HBM roofline, batched vs plain; adjoint/forward cost"
@@ -150,35 +151,54 @@ def cuda_time(fn, stream):
     return a.elapsed_time(b) / 1e3
 
 
-def cpu_baseline(budget_s=12.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    one lattice per L (temperature T_c, replica 0), 10-step chunks until the
-    budget is spent; lattices run concurrently on the host cores."""
+def oracle_sample(workers):
+    """A bounded sample of the workload for the FP64 oracle: per host thread,
+    one lattice of each L (the workload's equal lattice counts per L), ordered
+    state at T_c, distinct (configuration, replica) noise ids.  Tasks run
+    largest first on `workers` threads, so every thread gets one lattice of
+    each size and the threads stay evenly loaded."""
     import numpy as np
 
     import oracle
     oracle.build()
+    tasks = []
+    for i, L in reversed(list(enumerate(LS))):
+        for w in range(workers):
+            c, r = 32 * i + w % 32, (w // 32) % N_REP
+            th = oracle.init_theta(L, L, c, r, 1, 1)
+            tasks.append([L, c, r, th, np.zeros_like(th), 0])
+    return tasks
+
+
+def oracle_round(ex, tasks, n):
+    """n BBK steps of every sampled lattice; returns the site-updates done."""
+    import oracle
+
+    def run(t):
+        L, c, r, th, om, k = t
+        oracle.run_lattice(L, L, c, r, 1, {}, ([0], [TC]), k, n, th, om)
+        t[5] += n
+        return L * L * n
+
+    return sum(ex.map(run, tasks))
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload
+    (oracle_sample), 10-step rounds until the budget is spent."""
     from concurrent.futures import ThreadPoolExecutor
-    cores = os.cpu_count() or 1
-    specs = []
-    for i, L in enumerate(LS):
-        th = oracle.init_theta(L, L, 16 * i, 0, 1, 1)
-        specs.append((L, 16 * i, th, np.zeros_like(th)))
-    prm = {}
-    su, t0, k = 0, time.perf_counter(), 0
-
-    def run(sp):
-        L, c, th, om = sp
-        oracle.run_lattice(L, L, c, 0, 1, prm, ([0], [TC]), k, INNER, th, om)
-        return L * L * INNER
-
-    with ThreadPoolExecutor(max_workers=min(cores, len(specs))) as ex:
+    workers = os.cpu_count() or 1
+    tasks = oracle_sample(workers)
+    su, rounds = 0, 0
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        t0 = time.perf_counter()
         while time.perf_counter() - t0 < budget_s:
-            su += sum(ex.map(run, specs))
-            k += INNER
-    dt = time.perf_counter() - t0
-    return {"value": su / dt, "unit": "site-updates/s", "cores": min(cores, len(specs)), "kind": "oracle",
-            "sample": f"one lattice per L in {list(LS)} at T_c, {k} steps each ({su:.3g} site-updates, {dt:.1f} s)"}
+            su += oracle_round(ex, tasks, INNER)
+            rounds += 1
+        dt = time.perf_counter() - t0
+    return {"value": su / dt, "unit": "site-updates/s", "cores": workers, "kind": "oracle",
+            "sample": f"{workers} lattices per L in {list(LS)} at T_c (one of each per host thread), "
+                      f"{rounds * INNER} steps each ({su:.3g} site-updates, {dt:.1f} s)"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -393,44 +413,31 @@ def run_ours(args):
 
 def run_reference(args):
     """The FP64 oracle as it stands on the host cores, on the same metric:
-    each step is 10 BBK steps of a bounded sample of the workload (one lattice
-    per L at T_c)."""
+    each step is REF_INNER BBK steps of a bounded sample of the workload
+    (oracle_sample: per host thread one lattice of each L at T_c)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-
-    import oracle
-    oracle.build()
     from concurrent.futures import ThreadPoolExecutor
-    cores = os.cpu_count() or 1
-    lats = []
-    for i, L in enumerate(LS):
-        th = oracle.init_theta(L, L, 16 * i, 0, 1, 1)
-        lats.append([L, 16 * i, th, np.zeros_like(th), 0])
-
-    def run(sp):
-        L, c, th, om, k = sp
-        oracle.run_lattice(L, L, c, 0, 1, {}, ([0], [TC]), k, INNER, th, om)
-        sp[4] += INNER
-        return L * L * INNER
-
-    su_step = sum(L * L for L in LS) * INNER
-    with ThreadPoolExecutor(max_workers=min(cores, len(lats))) as ex:
+    workers = os.cpu_count() or 1
+    tasks = oracle_sample(workers)
+    with ThreadPoolExecutor(max_workers=workers) as ex:
         for _ in range(args.warmup):
-            list(ex.map(run, lats))
+            oracle_round(ex, tasks, REF_INNER)
+        su = 0
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            list(ex.map(run, lats))
+            su += oracle_round(ex, tasks, REF_INNER)
         dt = time.perf_counter() - t0
-    value = args.steps * su_step / dt
-    sample = f"one lattice per L in {list(LS)} at T_c, {INNER} BBK steps per step"
+    value = su / dt
+    sample = (f"{workers} lattices per L in {list(LS)} at T_c (one of each per host thread), "
+              f"{REF_INNER} BBK steps per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": min(cores, len(lats)), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": workers, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
