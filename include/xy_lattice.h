@@ -319,6 +319,14 @@ const char* xy_last_error(void);
 int xy_debug_noise(uint64_t seed, int cfg, int replica, int64_t k, int tag, int64_t n_quads,
                    uint32_t* words, float* gauss, void* cuda_stream);
 
+/* Diagnostics: bound on the steps of one root search and on the link
+ * retries of one union in the domain labelling (xy_label_domains,
+ * xy_label_domains_static) on the current device; iters <= 0 restores the
+ * default 2^22.  A search or union that reaches the bound stops, and the call
+ * returns XY_ETIMEOUT with incomplete labels (indices stay in range, nothing
+ * faults).  For testing the timeout path; the paper has no counterpart. */
+int xy_debug_set_union_limit(int iters);
+
 /* Diagnostics: raw Philox4x32-10 of n arbitrary counters (device
  * uint32[n][4]) with key (k0, k1) into out (device uint32[n][4]). */
 int xy_debug_philox(const uint32_t* counters, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,

@@ -22,16 +22,29 @@ namespace {
 
 constexpr int kMaxUnionIters = 1 << 22;
 
+}  // namespace
+
+// Upper bound on the steps of one root search and on the link retries of one
+// union in global memory (per device).  xy_debug_set_union_limit() lowers it
+// so that tests can run the timeout path: a loop that reaches the bound sets
+// XY_ETIMEOUT and returns, and since links only ever point at smaller
+// indices the forest stays acyclic and every index stays in range.
+__device__ int g_union_limit = kMaxUnionIters;
+
+namespace {
+
 __device__ __forceinline__ bool spin_of(float t) { return t >= 0.0f; }
 
-__device__ __forceinline__ int find_root_global(const int32_t* L, int x)
+__device__ __forceinline__ int find_root_global(const int32_t* L, int x, int limit, int* err)
 {
     int p = *(volatile const int32_t*)&L[x];
-    int it = 0;
-    while (p != x && it < kMaxUnionIters) {
+    for (int it = 0; p != x; ++it) {
+        if (it >= limit) {
+            atomicExch(err, XY_ETIMEOUT);
+            return x;
+        }
         x = p;
         p = *(volatile const int32_t*)&L[x];
-        ++it;
     }
     return x;
 }
@@ -39,11 +52,11 @@ __device__ __forceinline__ int find_root_global(const int32_t* L, int x)
 // Link the components of a and b (global indices inside one lattice's label
 // array L): the larger root is pointed at the smaller with atomicMin; a failed
 // link (the root changed meanwhile) retries from the value it found.
-__device__ void union_global(int32_t* L, int a, int b, int* err)
+__device__ void union_global(int32_t* L, int a, int b, int limit, int* err)
 {
-    for (int it = 0; it < kMaxUnionIters; ++it) {
-        a = find_root_global(L, a);
-        b = find_root_global(L, b);
+    for (int it = 0; it < limit; ++it) {
+        a = find_root_global(L, a, limit, err);
+        b = find_root_global(L, b, limit, err);
         if (a == b) return;
         if (a < b) {
             const int t = a;
@@ -130,25 +143,26 @@ __global__ void ccl_border_kernel(const float* theta, int Lx, int Ly, int TW, in
     const float* th = theta + (int64_t)lat * N;
     int32_t* L = labels + (int64_t)lat * N;
     const bool sp = spin_of(th[s]);
+    const int limit = g_union_limit;
     if (right_border) {
         const int n = y * Lx + (x + 1 == Lx ? 0 : x + 1);
-        if (spin_of(th[n]) == sp) union_global(L, s, n, err);
+        if (spin_of(th[n]) == sp) union_global(L, s, n, limit, err);
     }
     if (bottom_border) {
         const int n = (y + 1 == Ly ? 0 : y + 1) * Lx + x;
-        if (spin_of(th[n]) == sp) union_global(L, s, n, err);
+        if (spin_of(th[n]) == sp) union_global(L, s, n, limit, err);
     }
 }
 
 // Pass 3: every site points straight at its root; count component sizes.
-__global__ void ccl_flatten_kernel(int64_t N, int n_lat, int32_t* labels, int32_t* sizes)
+__global__ void ccl_flatten_kernel(int64_t N, int n_lat, int32_t* labels, int32_t* sizes, int* err)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N * n_lat) return;
     const int lat = (int)(i / N);
     const int s = (int)(i - (int64_t)lat * N);
     int32_t* L = labels + (int64_t)lat * N;
-    const int r = find_root_global(L, s);
+    const int r = find_root_global(L, s, g_union_limit, err);
     atomicAdd(&sizes[(int64_t)lat * N + r], 1);
     // the final write happens after every find of this pass may have read L[s]
     // as an intermediate node; writing the root keeps the forest valid.
@@ -235,10 +249,23 @@ cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* l
     const int64_t total = N * n_lat;
     const unsigned blocks = (unsigned)((total + 255) / 256);
     ccl_border_kernel<<<blocks, 256, 0, st>>>(theta, Lx, Ly, TW, TH, n_lat, labels, err);
-    ccl_flatten_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch);
+    ccl_flatten_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch, err);
     ccl_size_hist_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch, count_scratch);
     ccl_compact_kernel<<<n_lat, 1024, 0, st>>>(N, count_scratch, hist, hist_cap, n_sizes, err);
     return cudaGetLastError();
 }
 
 }  // namespace xy
+
+// Diagnostics: bound of the union-find loops on the current device
+// (iters <= 0 restores the default 2^22).
+extern "C" int xy_debug_set_union_limit(int iters)
+{
+    const int v = iters > 0 ? iters : xy::kMaxUnionIters;
+    const cudaError_t e = cudaMemcpyToSymbol(xy::g_union_limit, &v, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return xy::report_error(XY_ECUDA, cudaGetErrorString(e));
+    }
+    return XY_OK;
+}

@@ -343,6 +343,64 @@ def test_edge_cases_and_errors():
     assert lat.kernel_launches() > 0
 
 
+# ------------------------------------------------------------------ failure detection
+
+
+def test_union_timeout_is_reported_and_recoverable():
+    """A union-find bound of one step makes the labelling of a percolating
+    pattern run out: the call returns XY_ETIMEOUT (no fault, no hang) and the
+    next call with the default bound is exact again."""
+    from paper_2409_06412_gb300 import _lib
+    spins = inputs.random_spins(512, 512, seed=91, p_up=0.7)
+    th = torch.from_numpy(inputs.spins_to_theta(spins).ravel()).cuda()
+    lat = Lattice([Config(Lx=512, Ly=512, n_replicas=1, init_mode=_lib.XY_INIT_USER)], theta=th,
+                  omega=torch.zeros_like(th))
+    _lib.call("xy_debug_set_union_limit", 1)
+    try:
+        with pytest.raises(XYError) as ei:
+            lat.label_domains(0, 1)
+        assert ei.value.code == _lib.XY_ETIMEOUT
+    finally:
+        _lib.call("xy_debug_set_union_limit", 0)
+    labels, _, _ = lat.label_domains(0, 1)
+    lab_o, _ = oracle.ccl(512, 512, inputs.spins_to_theta(spins).ravel())
+    assert np.array_equal(labels[0].cpu().numpy(), lab_o)
+    lat.close()
+
+
+def test_non_finite_state_is_reported():
+    """A NaN angle in the caller's state spreads to the observables; the FP64
+    moments come back as XY_ENAN from xy_observe."""
+    from paper_2409_06412_gb300 import _lib
+    th = torch.from_numpy(inputs.angles(1, 16, 8, 93).ravel()).cuda()
+    th[37] = float("nan")
+    lat = Lattice([Config(Lx=16, Ly=8, n_replicas=1, init_mode=_lib.XY_INIT_USER)], theta=th,
+                  omega=torch.zeros_like(th))
+    lat.step(10, record_every=5)
+    with pytest.raises(XYError) as ei:
+        lat.observe()
+    assert ei.value.code == _lib.XY_ENAN
+    lat.close()
+
+
+def test_failed_allocation_is_reported_and_recoverable():
+    """An adjoint whose checkpoints cannot be allocated (1e9 steps with a
+    checkpoint every step: 1 TB) returns XY_ENOMEM before launching anything
+    on them; the object stays usable."""
+    from paper_2409_06412_gb300 import _lib
+    specs = [inputs.config(16, 8, 1, seed=3)]
+    lat, _, _ = make_pair(specs, _mixed_thetas(specs))
+    with pytest.raises(XYError) as ei:
+        lat.adjoint(10 ** 9, checkpoint_every=1)
+    assert ei.value.code == _lib.XY_ENOMEM
+    _, steps = lat.observe()
+    assert list(steps) == [0]
+    lat.step(5)
+    obj, grads = lat.adjoint(10, checkpoint_every=5)
+    assert np.isfinite(obj) and np.all(np.isfinite(grads))
+    lat.close()
+
+
 # ------------------------------------------------------------------ domains
 
 
