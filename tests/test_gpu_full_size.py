@@ -140,3 +140,46 @@ def test_kibble_zurek_full_size_sampled():
     _, steps = lat.observe()
     assert list(steps) == [n] * len(cfgs)
     lat.close()
+
+
+def test_differentiation_full_size():
+    """The differentiation workload at full size: 64 lattices of 256 x 256 at
+    T_c from the ordered state (as 64 one-replica configurations, so that the
+    gradients come back per lattice).  A 200-step adjoint (checkpoint every
+    100) against the oracle's FP64 adjoint on two sampled lattices; the full
+    2000-step adjoint with the states integrated backward against the stored
+    recompute (beyond a few hundred steps at T_c the FP32 and FP64
+    trajectories part, so the oracle is compared on the shorter window)."""
+    from paper_2409_06412_gb300 import XY_ADJOINT_BACKWARD, XY_ADJOINT_RECOMPUTE
+    cfgs = [Config(Lx=256, Ly=256, n_replicas=1, seed=1, init_mode=XY_INIT_ORDERED, knots=((0,), (TC,)),
+                   n_total=10 ** 9) for _ in range(64)]
+    lat = Lattice(cfgs)
+    lat.step(10)
+    snap = lat.save()
+    picks = [5, 42]
+    th0 = [lat.lattice_view(lat.theta, c).cpu().numpy().ravel().astype(np.float64) for c in picks]
+    om_full = lat.omega_full().cpu().numpy().reshape(64, -1)
+    om0 = [om_full[c].astype(np.float64) for c in picks]
+    n = 200
+    obj, grads = lat.adjoint(n, checkpoint_every=100, w_E=1.0, w_M=1.0)
+
+    def ref(i):
+        c = picks[i]
+        return oracle.adjoint_lattice(256, 256, c, 0, 1, {}, ([0], [TC]), 10, n, th0[i].copy(), om0[i].copy(), 1.0,
+                                      1.0)
+
+    with ThreadPoolExecutor(max_workers=len(picks)) as ex:
+        res = list(ex.map(ref, range(len(picks))))
+    for i, c in enumerate(picks):
+        o_g = res[i][1] / (64 * n)
+        assert np.all(np.abs(grads[c] - o_g) <= 1e-3 * np.abs(o_g).max()), (c, grads[c], o_g)
+    # 2000 steps, both schedules from the same snapshot
+    out = {}
+    for mode in (XY_ADJOINT_BACKWARD, XY_ADJOINT_RECOMPUTE):
+        lat.load(snap)
+        lat.set_adjoint_mode(mode)
+        out[mode] = lat.adjoint(2000, checkpoint_every=100, w_E=1.0, w_M=1.0)
+    (ob, gb), (orc, grc) = out[XY_ADJOINT_BACKWARD], out[XY_ADJOINT_RECOMPUTE]
+    assert ob == pytest.approx(orc, rel=1e-5)
+    assert np.all(np.abs(gb - grc) <= 1e-3 * np.abs(grc).max(axis=1, keepdims=True))
+    lat.close()
