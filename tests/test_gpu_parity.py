@@ -518,12 +518,13 @@ def test_adjoint_matches_oracle(field, mode):
 
 
 def test_adjoint_modes_agree_on_wide_strips():
-    """Backward integration against the stored recompute on lattices of 128-
-    and 256-column strips at T_c from the ordered state, with n a multiple of
+    """Backward integration against the stored recompute on lattices of 3, 2
+    and 16 strips of 128 columns at T_c from the ordered state, with n a multiple of
     the checkpoint interval (the last segment ends at the final state) and
     not: gradients and objective agree to rounding of the recovered states,
     and the state after the call is the same forward state."""
-    specs = [inputs.config(384, 32, 2, seed=7, knots=([0], [TC])), inputs.config(256, 16, 3, seed=8, knots=([0], [TC]))]
+    specs = [inputs.config(384, 32, 2, seed=7, knots=([0], [TC])), inputs.config(256, 16, 3, seed=8, knots=([0], [TC])),
+             inputs.config(2048, 8, 1, seed=9, knots=([0], [TC]))]  # 16 strips: 512 threads, 64 KB of staging
     thetas = [np.full((s["n_rep"], s["Lx"] * s["Ly"]), np.float32(2 * PI / 5)) +
               0.02 * inputs.velocities(s["n_rep"], s["Lx"], s["Ly"], 80 + i) for i, s in enumerate(specs)]
     thetas = [t.astype(np.float32) for t in thetas]
