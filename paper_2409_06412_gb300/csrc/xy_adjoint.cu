@@ -292,8 +292,11 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     // per warp, two stages of [theta(t+1), v(t), tb(t), vb(t), v_{k+1}(t)] for its 32 lanes
     extern __shared__ float4 s_stage[];
     // edge exchange: [slot][warp][side]  side 0 = left edge (site x0), 1 = right edge (site x0 + 127)
-    __shared__ float2 s_sc[3][kMaxBandWarps][2];
-    __shared__ float s_fb[2][kMaxBandWarps][2];
+    // edge slots of the wide bands, four rows deep: a slot last read in phase B
+    // of row t + 1 is rewritten for row t + 4, in the phase A of a warp that has
+    // passed the barrier of row t + 2, after every warp's phase B of row t + 1
+    __shared__ float2 s_sc[4][kMaxBandWarps][2];
+    __shared__ float s_fb[4][kMaxBandWarps][2];
     __shared__ double s_red[kGacc][kMaxBandWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     const BandTask task = tasks[blockIdx.x];
@@ -353,7 +356,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     auto adv = [&](int r) { return r + Lx == Nl ? 0 : r + Lx; };
     int r_m1 = rowp(y0 - 2), r_0 = rowp(y0 - 1), r_p1 = rowp(y0), r_p2 = rowp(y0 + 1);
     // slots of the edge exchange: rows t - 1, t, t + 1 modulo 3
-    int sl_m1 = (y0 - 2 + 3 * Ly) % 3, sl_0 = (y0 - 1 + 3 * Ly) % 3, sl_p1 = (y0 + 3 * Ly) % 3;
+    // slot of row y: (y - y0 + 8) & 3 (the block's rows share y0 in the wide layout)
+    int sl_m1 = 2, sl_0 = 3, sl_p1 = 0;
     auto publish_sc = [&](int slot, const BandSC& S) {
         if (!wide) return;
         if (lane == 0) s_sc[slot][warp][0] = make_float2(S.s[0], S.c[0]);
@@ -478,8 +482,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
             tbpn = make_float4(tbo[0], tbo[1], tbo[2], tbo[3]);
             cpn = make_float4(cpo[0], cpo[1], cpo[2], cpo[3]);
             if (wide) {
-                if (lane == 0) s_fb[t & 1][warp][0] = Fn.x;
-                if (lane == 31) s_fb[t & 1][warp][1] = Fn.w;
+                if (lane == 0) s_fb[(t - y0 + 8) & 3][warp][0] = Fn.x;
+                if (lane == 31) s_fb[(t - y0 + 8) & 3][warp][1] = Fn.w;
             }
         }
         if (wide) __syncthreads(); else __syncwarp();
@@ -489,8 +493,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
             nbr_sc(sl_m1, S1, sL, cL, sR, cR);
             float fL = __shfl_sync(kFullA, F1.w, srcL), fR = __shfl_sync(kFullA, F1.x, srcR);
             if (wide) {
-                if (lane == 0) fL = s_fb[(t - 1) & 1][wl][1];
-                if (lane == 31) fR = s_fb[(t - 1) & 1][wr][0];
+                if (lane == 0) fL = s_fb[(t - 1 - y0 + 8) & 3][wl][1];
+                if (lane == 31) fR = s_fb[(t - 1 - y0 + 8) & 3][wr][0];
             }
             float out[4];
 #pragma unroll
@@ -523,10 +527,9 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
         r_0 = r_p1;
         r_p1 = r_p2;
         r_p2 = adv(r_p2);
-        const int sl_t = sl_m1;
         sl_m1 = sl_0;
         sl_0 = sl_p1;
-        sl_p1 = sl_t;
+        sl_p1 = (sl_p1 + 1) & 3;
     }
     // per-block accumulators: FP32 warp butterflies (a warp covers a few
     // thousand sites), the warps and the steps combined in FP64 in a fixed order

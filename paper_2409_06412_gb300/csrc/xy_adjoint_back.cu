@@ -79,8 +79,12 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
 {
     // per warp, two stages of [theta_in(t+1), v_in, tb(t), vb(t)] for its 32 lanes
     extern __shared__ float4 s_stage[];
-    __shared__ float2 s_sc[3][kMaxBackWarps][2];
-    __shared__ float s_fb[2][kMaxBackWarps][2];
+    // edge slots of the wide bands, four rows deep: a slot last read in phase B
+    // of row t + 1 is rewritten for row t + 4, in the phase A of a warp that has
+    // passed the barrier of row t + 2, after every warp's phase B of row t + 1
+    __shared__ float2 s_sc[4][kMaxBackWarps][2];
+    __shared__ float s_fb[4][kMaxBackWarps][2];
+    __shared__ float s_bx[4][kMaxBackWarps];  // bond cosine of a strip's last site to the next strip
     __shared__ double s_red[kGacc + 1][kMaxBackWarps];
     __shared__ float s_wm1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
@@ -143,8 +147,12 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     float aJx = 0.f, aJy = 0.f, ah = 0.f, abar = 0.f, bbar = 0.f, cbar = 0.f;
     float sw2 = 0.f, sbx = 0.f, sby = 0.f, scp = 0.f, pm = 0.f;
 
-    // window: S0 = row t-2, S1 = t-1, S2 = t, S3 = t+1 (of theta_k); F0 = F-bar(t-2), F1 = t-1
-    SCb S0, S1, S2, S3;
+    // window: S1 = row t-1, S2 = t, S3 = t+1 (of theta_k); F0 = F-bar(t-2), F1 = t-1;
+    // Bm2, Bm1: bond cosines cos q(theta_y - theta_{y+1}) of rows t-2 and t-1,
+    // formed in phase A and reused by the stencil of phase B
+    SCb S1, S2, S3;
+    float4 Bm2, Bm1;
+    float4 Bx1 = make_float4(0.f, 0.f, 0.f, 0.f);  // cos q(theta_x - theta_{x+1}) of row t-1
     float4 F0 = make_float4(0.f, 0.f, 0.f, 0.f), F1 = F0;
     float4 th2, tbp1 = F0;  // theta_k of row t; tb partial of row t-1 (site-local terms of phase B folded in)
     float4 t1c = F0, v1c = F0;        // BACK: theta_{k+1}, v_{k+1} of row t
@@ -152,7 +160,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     auto rowp = [&](int y) { return wrapb(y, Ly) * Lx; };
     auto adv = [&](int r) { return r + Lx == Nl ? 0 : r + Lx; };
     int r_m1 = rowp(y0 - 2), r_0 = rowp(y0 - 1), r_p1 = rowp(y0), r_p2 = rowp(y0 + 1);
-    int sl_m1 = (y0 - 2 + 3 * Ly) % 3, sl_0 = (y0 - 1 + 3 * Ly) % 3, sl_p1 = (y0 + 3 * Ly) % 3;
+    // slot of row y: (y - y0 + 8) & 3 (the block's rows share y0 in the wide layout)
+    int sl_0 = 3, sl_p1 = 0;
     auto publish_sc = [&](int slot, const SCb& S) {
         if (!wide) return;
         if (lane == 0) s_sc[slot][warp][0] = make_float2(S.s[0], S.c[0]);
@@ -193,6 +202,9 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     }
     scb4(K.q, th2, S2);
     publish_sc(sl_0, S2);
+    Bm1 = make_float4(fmaf(S1.c[0], S2.c[0], S1.s[0] * S2.s[0]), fmaf(S1.c[1], S2.c[1], S1.s[1] * S2.s[1]),
+                      fmaf(S1.c[2], S2.c[2], S1.s[2] * S2.s[2]), fmaf(S1.c[3], S2.c[3], S1.s[3] * S2.s[3]));
+    Bm2 = Bm1;
     __syncthreads();  // s_wm1, and the edge slots of the first rows
     const float wM1 = s_wm1;
     for (int t = y0 - 1; t <= y0 + H; ++t) {
@@ -212,7 +224,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
         scb4(K.q, th3, S3);
         publish_sc(sl_p1, S3);
         // ---------------- phase A on row t
-        float4 Fn = make_float4(0.f, 0.f, 0.f, 0.f), tbpn = Fn;
+        float4 Fn = make_float4(0.f, 0.f, 0.f, 0.f), tbpn = Fn, Bn = Fn, Bxn = Fn;
         {
             float4 tb4 = sp[2 * 32 + lane];
             const float4 vb4 = sp[3 * 32 + lane];
@@ -231,7 +243,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
             nbr_sc(sl_0, S2, sL, cL, sR, cR);
             const uint32_t quad = (uint32_t)((r_0 + x) >> 2);
             const float4 nz = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, R.k, 0u), keys), K.c);
-            float tbo[4], vbo[4], fbo[4], vko[4];
+            float tbo[4], vbo[4], fbo[4], vko[4], byo[4], bxo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float s_ = S2.s[i], c_ = S2.c[i];
@@ -254,6 +266,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
                     vk = f4get(vin, i);
                     om = (vk + g) * K.inv1pa;
                 }
+                byo[i] = fmaf(c_, S3.c[i], s_ * S3.s[i]);  // bond to row t + 1
+                bxo[i] = fmaf(c_, cr, s_ * sr);            // bond to column x + 1
                 const float vbt = fmaf(K.dt, f4get(tb4, i), f4get(vb4, i));
                 float omb = K.oma * vbt;
                 float gb = vbt;
@@ -263,8 +277,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
                     tbi = fmaf(-wEn, F, tbi);
                     if (own_a) {
                         sw2 = fmaf(om, om, sw2);
-                        sbx += fmaf(c_, cr, s_ * sr);
-                        sby += fmaf(c_, S3.c[i], s_ * S3.s[i]);
+                        sbx += bxo[i];
+                        sby += byo[i];
                         scp += cp;
                     }
                 }
@@ -297,32 +311,36 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
                 }
             }
             Fn = make_float4(fbo[0], fbo[1], fbo[2], fbo[3]);
+            Bn = make_float4(byo[0], byo[1], byo[2], byo[3]);
+            Bxn = make_float4(bxo[0], bxo[1], bxo[2], bxo[3]);
             tbpn = make_float4(tbo[0], tbo[1], tbo[2], tbo[3]);
             if (wide) {
-                if (lane == 0) s_fb[t & 1][warp][0] = Fn.x;
-                if (lane == 31) s_fb[t & 1][warp][1] = Fn.w;
+                if (lane == 0) s_fb[(t - y0 + 8) & 3][warp][0] = Fn.x;
+                if (lane == 31) {
+                    s_fb[(t - y0 + 8) & 3][warp][1] = Fn.w;
+                    s_bx[(t - y0 + 8) & 3][warp] = Bxn.w;
+                }
             }
         }
         if (wide) __syncthreads(); else __syncwarp();
         // ---------------- phase B on row t - 1 (needs F-bar of rows t - 2, t - 1, t)
         if (do_b) {
-            float sL, cL, sR, cR;
-            nbr_sc(sl_m1, S1, sL, cL, sR, cR);
             float fL = __shfl_sync(kFullB, F1.w, srcL), fR = __shfl_sync(kFullB, F1.x, srcR);
+            float kl0 = __shfl_sync(kFullB, Bx1.w, srcL);  // bond of the site to its left
             if (wide) {
-                if (lane == 0) fL = s_fb[(t - 1) & 1][wl][1];
-                if (lane == 31) fR = s_fb[(t - 1) & 1][wr][0];
+                if (lane == 0) {
+                    fL = s_fb[(t - 1 - y0 + 8) & 3][wl][1];
+                    kl0 = s_bx[(t - 1 - y0 + 8) & 3][wl];
+                }
+                if (lane == 31) fR = s_fb[(t - 1 - y0 + 8) & 3][wr][0];
             }
             float out[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float sl = i == 0 ? sL : S1.s[i - 1], cl = i == 0 ? cL : S1.c[i - 1];
-                const float sr = i == 3 ? sR : S1.s[i + 1], cr = i == 3 ? cR : S1.c[i + 1];
                 const float fl = i == 0 ? fL : f4get(F1, i - 1), fr = i == 3 ? fR : f4get(F1, i + 1);
                 const float fj = f4get(F1, i);
-                const float kl = fmaf(S1.c[i], cl, S1.s[i] * sl), kr = fmaf(S1.c[i], cr, S1.s[i] * sr);
-                const float ku = fmaf(S1.c[i], S0.c[i], S1.s[i] * S0.s[i]);
-                const float kd = fmaf(S1.c[i], S2.c[i], S1.s[i] * S2.s[i]);
+                const float kl = i == 0 ? kl0 : f4get(Bx1, i - 1), kr = f4get(Bx1, i);
+                const float ku = f4get(Bm2, i), kd = f4get(Bm1, i);
                 const float hx = fmaf(kl, fl - fj, kr * (fr - fj));
                 const float hy = fmaf(ku, f4get(F0, i) - fj, kd * (f4get(Fn, i) - fj));
                 out[i] = f4get(tbp1, i) + fmaf(q2Jx, hx, q2Jy * hy);
@@ -330,7 +348,9 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
             if (active) st4(tbO + r_m1 + x, make_float4(out[0], out[1], out[2], out[3]));
         }
         // shift the windows
-        S0 = S1;
+        Bm2 = Bm1;
+        Bm1 = Bn;
+        Bx1 = Bxn;
         S1 = S2;
         S2 = S3;
         th2 = th3;
@@ -343,10 +363,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
         r_0 = r_p1;
         r_p1 = r_p2;
         r_p2 = adv(r_p2);
-        const int sl_t = sl_m1;
-        sl_m1 = sl_0;
         sl_0 = sl_p1;
-        sl_p1 = sl_t;
+        sl_p1 = (sl_p1 + 1) & 3;
     }
     // per-block accumulators: FP32 warp butterflies, the warps and the steps
     // combined in FP64 in a fixed order; the partial of M_k goes to the ring
