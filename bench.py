@@ -284,16 +284,7 @@ def run_ours(args):
         extra["kernel_ms_per_bbk_step"] = {"resident": round(ms[0] / n_bbk, 4), "strip": round(strip_s * 1e3, 4)}
         extra["resident_su_per_s"] = (res_sites * n_bbk) / (ms[0] / 1e3) if nl[0] else None
 
-    if rank == 0 and args.workload == "static":
-        # plain per-configuration launch path on the same batch
-        lat.set_path(XY_PATH_PLAIN)
-        bench_step()
-        n_plain = 2
-        tp = cuda_time(lambda: [bench_step() for _ in range(n_plain)], stream)
-        lat.set_path(XY_PATH_BATCHED)
-        plain = n_plain * su_step / tp
-        extra["plain"] = {"value": plain, "unit": "site-updates/s", "batched_over_plain": value / world / plain}
-
+    if args.workload == "static":
         # end to end through the public API with host buffers: each step loads
         # its input state from pinned host memory (xy_load), advances INNER BBK
         # steps and returns its records to pinned host memory.  Serial: one
@@ -345,16 +336,32 @@ def run_ours(args):
         e2e_pipelined(2)
         torch.cuda.synchronize()
         n_pipe = max(4, min(args.steps, 10))
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         e2e_pipelined(n_pipe)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        extra["e2e"] = {"value": n_pipe * su_step / te, "unit": "site-updates/s",
+        if world > 1:  # whole job: every rank's steps over the slowest rank's time
+            tt = torch.tensor([te, te_serial], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te, te_serial = float(tt[0]), float(tt[1])
+        extra["e2e"] = {"value": world * n_pipe * su_step / te, "unit": "site-updates/s",
                         "h2d_bytes_per_step": len(blob), "d2h_bytes_per_step": int(rec_host[0].numel() * 8),
                         "mode": "double-buffered: two lattice objects, each step's upload overlaps the other's stepping",
-                        "serial_value": n_e2e * su_step / te_serial}
+                        "serial_value": world * n_e2e * su_step / te_serial}
         lat2.close()
         del lat2, rec_dev
+
+    if rank == 0 and args.workload == "static":
+        # plain per-configuration launch path on the same batch
+        lat.set_path(XY_PATH_PLAIN)
+        bench_step()
+        n_plain = 2
+        tp = cuda_time(lambda: [bench_step() for _ in range(n_plain)], stream)
+        lat.set_path(XY_PATH_BATCHED)
+        plain = n_plain * su_step / tp
+        extra["plain"] = {"value": plain, "unit": "site-updates/s", "batched_over_plain": value / world / plain}
 
         # domain labelling throughput on the 512 L = 1024 lattices (first 64)
         b0 = 3 * N_TEMPS * N_REP
