@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Benchmark of the BBK Langevin stepper on the static-criticality workload.
 
-Workload (one bench "step" = 10 BBK time steps of the whole batch, with one
-observable record per lattice and FP64 moment accumulation):
+Workload (one bench "step" = one sampling interval ds = 100 dt of App. B:
+100 BBK time steps of the whole batch, then one observable record per lattice
+and FP64 moment accumulation):
   L in {128, 256, 512, 1024} periodic lattices, 32 temperatures uniform in
   [0.9, 1.1] T_c, 16 replicas each (2048 lattices, 7.13e8 sites), ordered
   start, J_par = 10, J_perp = 0.1, h = 1, p = 2.5, q = 2, eta = 1, dt = 0.01.
@@ -35,7 +36,8 @@ TC = 1.969
 LS_FULL = (128, 256, 512, 1024)
 LS = LS_FULL
 N_TEMPS, N_REP = 32, 16
-INNER = 10            # BBK steps per bench step
+INNER = 100           # BBK steps per bench step: one sampling interval ds = 100 dt, then one record
+CPU_ROUND = 10        # BBK steps per round of the oracle's bounded sample
 REF_INNER = 4         # BBK steps per step of the reference arm (the oracle on the host cores)
 N_TOTAL = 10 ** 5     # run length of every configuration
 T0 = N_TOTAL // 5     # moments discard the first fifth
@@ -193,12 +195,12 @@ def cpu_baseline(budget_s=12.0):
     with ThreadPoolExecutor(max_workers=workers) as ex:
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < budget_s:
-            su += oracle_round(ex, tasks, INNER)
+            su += oracle_round(ex, tasks, CPU_ROUND)
             rounds += 1
         dt = time.perf_counter() - t0
     return {"value": su / dt, "unit": "site-updates/s", "cores": workers, "kind": "oracle",
             "sample": f"{workers} lattices per L in {list(LS)} at T_c (one of each per host thread), "
-                      f"{rounds * INNER} steps each ({su:.3g} site-updates, {dt:.1f} s)"}
+                      f"{rounds * CPU_ROUND} steps each ({su:.3g} site-updates, {dt:.1f} s)"}
 
 
 # ------------------------------------------------------------------ our arm

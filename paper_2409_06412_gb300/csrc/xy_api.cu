@@ -700,6 +700,51 @@ int run_window(xy_lattice* L, int64_t n_max)
             }
         return XY_OK;
     }
+    // Records further apart than a chunk: the stretches between recording
+    // steps run as non-recording graph chunks, and each step at which some
+    // strip configuration records runs alone with the recording kernel.
+    if (L->cur_rec && L->cur_re > 32) {
+        std::vector<int64_t> rec_steps;
+        for (const auto& g : L->strip_groups)
+            for (int c : g.cfgs) {
+                const DevCfg& d = L->h_dev[c];
+                const int64_t re = L->cur_re;
+                for (int64_t j = ((re - d.k_start % re) % re); j < std::min(n_max, d.n_call); j += re)
+                    rec_steps.push_back(j);
+            }
+        std::sort(rec_steps.begin(), rec_steps.end());
+        rec_steps.erase(std::unique(rec_steps.begin(), rec_steps.end()), rec_steps.end());
+        auto stretch = [&](int64_t cnt) -> int {
+            L->cur_mask = 0u;
+            const int ch = (int)std::min<int64_t>(32, cnt);
+            const int64_t nf = (L->timing || ch < 2) ? 0 : cnt / ch;
+            if (nf > 0) {
+                xy_lattice::Graph* g = nullptr;
+                int rc = get_graph(L, ch, &g);
+                if (rc) return rc;
+                for (int64_t i = 0; i < nf; ++i) {
+                    CK(cudaGraphLaunch(g->exec, L->stream));
+                    L->launches += g->kernels;
+                }
+            }
+            for (int64_t done = nf * ch; done < cnt;) {
+                const int k = (int)std::min<int64_t>(ch, cnt - done);
+                int rc = launch_batched_steps(L, L->stream, 0, k, true);
+                if (rc) return rc;
+                done += k;
+            }
+            return XY_OK;
+        };
+        int64_t pos = 0;
+        for (int64_t r : rec_steps) {
+            int rc = r > pos ? stretch(r - pos) : XY_OK;
+            if (rc) return rc;
+            L->cur_mask = 1u;  // local step 0 of this one-step launch records
+            if ((rc = launch_batched_steps(L, L->stream, 0, 1, true))) return rc;
+            pos = r + 1;
+        }
+        return pos < n_max ? stretch(n_max - pos) : XY_OK;
+    }
     // graph replays of 32-step chunks (or one chunk of the whole window when
     // it is shorter), then direct launches for the remainder.  When the
     // window records every re <= 32 steps, the chunk is a multiple of re, so

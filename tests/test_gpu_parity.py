@@ -208,6 +208,39 @@ def test_records_and_moments_parity():
     assert np.allclose(mom, o_mom, rtol=2e-4, atol=1e-7)
 
 
+def test_records_further_apart_than_a_graph_chunk():
+    """Records every 50 steps (more than a 32-step graph chunk) of a call
+    that starts at step 7: the recording steps run alone with the recording
+    kernel, the stretches between them as non-recording chunks.  Records
+    match the oracle's; the state is bit-identical to a run without records."""
+    specs = _mixed_specs()
+    thetas = _mixed_thetas(specs, seed=17)
+    lat, o_th, o_om = make_pair(specs, thetas)
+    ref, _, _ = make_pair(specs, thetas)
+    lat.step(7)
+    ref.step(7)
+    rec = lat.step(130, record_every=50).cpu().numpy()  # k = 50 and 100
+    ref.step(130)
+    torch.cuda.synchronize()
+    assert torch.equal(lat.theta, ref.theta) and torch.equal(lat.omega, ref.omega)
+    step_now = [0] * len(specs)
+    oracle.run_batch(specs, o_th, o_om, step_now, 7)
+    o_rec, _ = oracle.run_batch(specs, o_th, o_om, step_now, 130, record_every=50)
+    b, loose = 0, 0
+    for c, s in enumerate(specs):
+        for r in range(s["n_rep"]):
+            mine, want = rec[b, :2], o_rec[c][r]
+            assert want.shape == (2, 2)
+            dm = np.abs(mine[:, 0] - want[:, 0])
+            de = np.abs(mine[:, 1] - want[:, 1]) / (1 + np.abs(want[:, 1]))
+            if dm.max() > 2e-5 or de.max() > 2e-5:
+                loose += 1
+                assert dm.max() < 2e-3 and de.max() < 2e-4, (c, r, dm.max(), de.max())
+            assert np.isnan(rec[b, 2]).all()
+            b += 1
+    assert loose <= 2, loose
+
+
 def test_plain_and_batched_are_bit_identical():
     specs = _mixed_specs()
     thetas = _mixed_thetas(specs, seed=9)
