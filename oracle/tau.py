@@ -55,4 +55,7 @@ def tau_int(f: np.ndarray, window: str = "auto", c: float = 6.0) -> float:
 def error_of_mean(f: np.ndarray, window: str = "auto", c: float = 6.0) -> float:
     f = np.asarray(f, dtype=np.float64)
     C0 = autocorrelation(f, 0)[0]
-    return float(np.sqrt(2.0 * tau_int(f, window, c) * C0 / f.size))
+    var = 2.0 * tau_int(f, window, c) * C0 / f.size
+    # the literal half-series window can give tau_C < 0 (App. B's integral of
+    # a finite series' autocovariance); the error of the mean is then undefined
+    return float(np.sqrt(var)) if var >= 0.0 else float("nan")
