@@ -50,13 +50,24 @@ def temps():
     return [TC * (0.9 + 0.2 * i / (N_TEMPS - 1)) for i in range(N_TEMPS)]
 
 
+KZ = False
+
+
 def set_workload(name):
-    """'static' (the full batch) or 'static-L512' (its L = 512 part only: 512
-    lattices, 1.3e8 sites, 1 GB of state, for profiler captures)."""
-    global LS, WORKLOAD
+    """'static' (the full batch), 'static-L512' (its L = 512 part only: 512
+    lattices, 1.3e8 sites, 1 GB of state, for profiler captures) or
+    'kibble-zurek' (the 9216-lattice quench batch, 155 GB on the device; with
+    --warmup 10 the timed steps pass k = 1150, where the tau_Q = 100 ramps end
+    and those lattices retire)."""
+    global LS, WORKLOAD, KZ
     if name == "static-L512":
         LS = (512,)
         WORKLOAD = "static criticality, L = 512 part: 32 T in [0.9,1.1] T_c, 16 replicas, ordered start"
+    elif name == "kibble-zurek":
+        KZ = True
+        WORKLOAD = ("Kibble-Zurek: L = 1024, 16 log-spaced tau_Q in [1e2, 1e5] x eta {0.1, 1, 10} x "
+                    "h {0.5, 1, 2} x 64 replicas (9216 lattices); 1e3 steps at 1.5 T_c, then a linear ramp "
+                    "to 0 over 1.5 tau_Q; uniform random start")
     else:
         LS = LS_FULL
 
@@ -67,8 +78,23 @@ def static_configs(seed):
                    n_total=N_TOTAL) for L in LS for T in temps()]
 
 
-def sites_total():
-    return N_TEMPS * N_REP * sum(L * L for L in LS)
+def kz_configs(seed):
+    import numpy as np
+
+    from paper_2409_06412_gb300 import XY_INIT_UNIFORM, Config
+    out = []
+    for tq in np.round(np.logspace(2, 5, 16)).astype(int):
+        ramp = int(round(1.5 * tq))
+        for eta in (0.1, 1.0, 10.0):
+            for h in (0.5, 1.0, 2.0):
+                out.append(Config(Lx=1024, Ly=1024, n_replicas=64, seed=seed, init_mode=XY_INIT_UNIFORM,
+                                  params=dict(eta=eta, h=h), knots=((0, 1000, 1000 + ramp), (1.5 * TC, 1.5 * TC, 0.0)),
+                                  n_total=1000 + ramp))
+    return out
+
+
+def workload_configs(seed):
+    return kz_configs(seed) if KZ else static_configs(seed)
 
 
 # ------------------------------------------------------------------ clocks
@@ -221,9 +247,18 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    lat = Lattice(static_configs(seed=1 + rank), stream=stream)
-    S = sites_total()
+    cfgs = workload_configs(seed=1 + rank)
+    lat = Lattice(cfgs, stream=stream)
+    S = sum(c.sites for c in cfgs)
     R = INNER // INNER + 1
+
+    def done_su(before, after):
+        """Site-updates between two step-counter readings (lattices that
+        retire mid-window count their own steps only), split by stepper:
+        (lattices with L >= 256: strip; the rest: cluster-resident)."""
+        strip = sum(c.sites * int(a - b) for c, a, b in zip(cfgs, after, before) if c.Lx >= 256)
+        res = sum(c.sites * int(a - b) for c, a, b in zip(cfgs, after, before) if c.Lx < 256)
+        return strip, res
 
     def bench_step():
         lat.step(INNER, record_every=INNER, t0=T0)
@@ -233,6 +268,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    steps0 = lat.observe()[1]
     clocks = ClockSampler(local)
     l0 = lat.kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -253,38 +289,40 @@ def run_ours(args):
         t = torch.tensor([elapsed], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
-    su_step = S * INNER
-    value = world * args.steps * su_step / elapsed
     mom, steps = lat.observe()
+    su_timed = sum(done_su(steps0, steps))
+    su_step = su_timed / args.steps
+    value = world * su_timed / elapsed
 
     extra = {}
     if rank == 0:
         # dominant kernel, timed live with events on its stream (the strip
         # stepper carries every lattice with L >= 256)
+        s_before = lat.observe()[1]
         lat.set_kernel_timing(True)
         for _ in range(3):
             bench_step()
         ms, nl = lat.kernel_timing()
         lat.set_kernel_timing(False)
-        strip_sites = N_TEMPS * N_REP * sum(L * L for L in LS if L >= 256)
-        res_sites = N_TEMPS * N_REP * sum(L * L for L in LS if L < 256)
+        su_strip, su_res = done_su(s_before, lat.observe()[1])
         hbm, peak_kind = peaks()
         # the strip stepper runs one launch per lattice shape per BBK step:
-        # bytes and time summed over its launches give bytes per launch over
-        # the average launch duration
+        # the site-updates it did (from the step counters) and its summed
+        # launch time give bytes per launch over the average launch duration
         n_bbk = 3 * INNER
         strip_s = ms[1] / 1e3 / n_bbk                      # strip time per BBK step
-        n_shapes = max(1, round(nl[1] / n_bbk))
-        achieved = BYTES_PER_SU * strip_sites / strip_s / 1e9
+        n_launch = max(1, int(nl[1]))
+        achieved = BYTES_PER_SU * su_strip / (ms[1] / 1e3) / 1e9
         traffic = ncu_traffic("strip_step_kernel")
         extra["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(achieved / hbm, 4), "peak_kind": f"{peak_kind} copy bandwidth",
                              "kernel": "strip_step_kernel",
-                             "traffic": (round(traffic * strip_sites / n_shapes) if traffic else None),
-                             "algorithmic_bytes_per_launch": int(BYTES_PER_SU * strip_sites / n_shapes),
-                             "launch_ms": round(strip_s * 1e3 / n_shapes, 4), "launches_per_bbk_step": n_shapes}
+                             "traffic": (round(traffic * su_strip / n_launch) if traffic else None),
+                             "algorithmic_bytes_per_launch": int(BYTES_PER_SU * su_strip / n_launch),
+                             "launch_ms": round(ms[1] / n_launch, 4),
+                             "launches_per_bbk_step": max(1, round(nl[1] / n_bbk))}
         extra["kernel_ms_per_bbk_step"] = {"resident": round(ms[0] / n_bbk, 4), "strip": round(strip_s * 1e3, 4)}
-        extra["resident_su_per_s"] = (res_sites * n_bbk) / (ms[0] / 1e3) if nl[0] else None
+        extra["resident_su_per_s"] = su_res / (ms[0] / 1e3) if nl[0] else None
 
     if args.workload == "static":
         # end to end through the public API with host buffers: each step loads
@@ -354,6 +392,18 @@ def run_ours(args):
                         "serial_value": world * n_e2e * su_step / te_serial}
         lat2.close()
         del lat2, rec_dev
+
+    if rank == 0 and KZ:
+        # domain labels of the frozen state of the tau_Q = 100 ramps (the
+        # first 64 lattices, retired at k = 1150 when the window passes it)
+        lat.label_domains(0, 8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, n_sizes = lat.label_domains(0, 64)
+        torch.cuda.synchronize()
+        tl = time.perf_counter() - t0
+        extra["ccl"] = {"value": 64 * 1024 * 1024 / tl, "unit": "labelled sites/s", "lattices": 64, "L": 1024,
+                        "step": int(lat.observe()[1][0]), "distinct_domain_sizes_max": int(n_sizes.max())}
 
     if rank == 0 and args.workload == "static":
         # plain per-configuration launch path on the same batch
@@ -442,7 +492,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattices": len(static_configs(1)) * N_REP, "sites": S,
+            "config": {"workload": WORKLOAD, "lattices": sum(c.n_replicas for c in cfgs), "sites": S,
                        "bbk_steps_per_step": INNER, "record_every": INNER, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (state of every step >> 129 MB), no flush"},
             "gpu_launches": int(launches), "clocks": clk,
@@ -521,7 +571,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["static", "static-L512"], default="static")
+    ap.add_argument("--workload", choices=["static", "static-L512", "kibble-zurek"], default="static")
     ap.add_argument("--profile-case", choices=["adjoint-small", "plain64", "sf"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
