@@ -51,18 +51,26 @@ def temps():
 
 
 KZ = False
+DYNZ = False
+REC_EVERY = INNER     # record interval of the timed steps
 
 
 def set_workload(name):
     """'static' (the full batch), 'static-L512' (its L = 512 part only: 512
     lattices, 1.3e8 sites, 1 GB of state, for profiler captures) or
+    'dynamic-z' (L up to 2048 x 256 replicas, a record every 10 steps) or
     'kibble-zurek' (the 9216-lattice quench batch, 155 GB on the device; with
     --warmup 10 the timed steps pass k = 1150, where the tau_Q = 100 ramps end
     and those lattices retire)."""
-    global LS, WORKLOAD, KZ
+    global LS, WORKLOAD, KZ, DYNZ, REC_EVERY
     if name == "static-L512":
         LS = (512,)
         WORKLOAD = "static criticality, L = 512 part: 32 T in [0.9,1.1] T_c, 16 replicas, ordered start"
+    elif name == "dynamic-z":
+        DYNZ = True
+        REC_EVERY = 10
+        WORKLOAD = ("dynamic exponent z: L in {256, 512, 1024, 2048} x 256 replicas, ordered start at T_c, "
+                    "M and E recorded every 10 steps")
     elif name == "kibble-zurek":
         KZ = True
         WORKLOAD = ("Kibble-Zurek: L = 1024, 16 log-spaced tau_Q in [1e2, 1e5] x eta {0.1, 1, 10} x "
@@ -93,8 +101,16 @@ def kz_configs(seed):
     return out
 
 
+def dynz_configs(seed):
+    from paper_2409_06412_gb300 import XY_INIT_ORDERED, Config
+    return [Config(Lx=L, Ly=L, n_replicas=256, seed=seed, init_mode=XY_INIT_ORDERED, knots=((0,), (TC,)),
+                   n_total=N_TOTAL) for L in (256, 512, 1024, 2048)]
+
+
 def workload_configs(seed):
-    return kz_configs(seed) if KZ else static_configs(seed)
+    if KZ:
+        return kz_configs(seed)
+    return dynz_configs(seed) if DYNZ else static_configs(seed)
 
 
 # ------------------------------------------------------------------ clocks
@@ -250,7 +266,7 @@ def run_ours(args):
     cfgs = workload_configs(seed=1 + rank)
     lat = Lattice(cfgs, stream=stream)
     S = sum(c.sites for c in cfgs)
-    R = INNER // INNER + 1
+    R = INNER // REC_EVERY + 1
 
     def done_su(before, after):
         """Site-updates between two step-counter readings (lattices that
@@ -261,7 +277,7 @@ def run_ours(args):
         return strip, res
 
     def bench_step():
-        lat.step(INNER, record_every=INNER, t0=T0)
+        lat.step(INNER, record_every=REC_EVERY, t0=T0)
 
     for _ in range(args.warmup):
         bench_step()
@@ -493,7 +509,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattices": sum(c.n_replicas for c in cfgs), "sites": S,
-                       "bbk_steps_per_step": INNER, "record_every": INNER, "parallelism": f"replicas x{world}",
+                       "bbk_steps_per_step": INNER, "record_every": REC_EVERY, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (state of every step >> 129 MB), no flush"},
             "gpu_launches": int(launches), "clocks": clk,
             "binder_U_range": [float(U.min()), float(U.max())] if U.size else None,
@@ -571,7 +587,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["static", "static-L512", "kibble-zurek"], default="static")
+    ap.add_argument("--workload", choices=["static", "static-L512", "dynamic-z", "kibble-zurek"], default="static")
     ap.add_argument("--profile-case", choices=["adjoint-small", "plain64", "sf"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
