@@ -577,6 +577,24 @@ def test_adjoint_modes_agree_on_wide_strips():
         assert np.all(np.abs(g2 - g1) <= 1e-4 * scale), (n, g1, g2)
 
 
+@pytest.mark.parametrize("n,K", [(1, 1), (1, 100), (5, 1), (7, 100), (9, 3)])
+def test_adjoint_schedules_agree_on_short_windows(n, K):
+    """Degenerate windows: one step, a checkpoint every step, a checkpoint
+    interval longer than the window, n a multiple of K."""
+    specs = [inputs.config(256, 8, 2, seed=21, knots=([0], [TC])), inputs.config(32, 16, 3, seed=22, knots=([0], [TC]))]
+    thetas = _mixed_thetas(specs, seed=23)
+    res = {}
+    for mode in (XY_ADJOINT_RECOMPUTE, XY_ADJOINT_BACKWARD):
+        lat, _, _ = make_pair(specs, thetas)
+        lat.set_adjoint_mode(mode)
+        res[mode] = lat.adjoint(n, checkpoint_every=K, w_E=0.6, w_M=0.4) + (lat.theta.cpu().numpy().copy(),)
+        lat.close()
+    (o1, g1, t1), (o2, g2, t2) = res[XY_ADJOINT_RECOMPUTE], res[XY_ADJOINT_BACKWARD]
+    assert np.array_equal(t1, t2)
+    assert o2 == pytest.approx(o1, rel=1e-6)
+    assert np.all(np.abs(g2 - g1) <= 1e-4 * np.abs(g1).max(axis=1, keepdims=True)), (g1, g2)
+
+
 def test_backward_adjoint_rejects_other_shapes():
     specs = [inputs.config(12, 10, 1, seed=4, knots=([0], [1.0]))]
     lat, _, _ = make_pair(specs, _mixed_thetas(specs))
