@@ -620,7 +620,7 @@ def test_adjoint_autograd_function():
     obj = bbk_objective(lat, J, Jp, h, eta, n=40, checkpoint_every=10, w_E=1.0, w_M=0.0)
     obj.backward()
     o_obj, o_grads = _oracle_adjoint(specs, o_th, o_om, 40, 1.0, 0.0)
-    assert float(obj) == pytest.approx(o_obj, rel=1e-5)
+    assert float(obj.detach()) == pytest.approx(o_obj, rel=1e-5)
     got = np.array([J.grad.item(), Jp.grad.item(), h.grad.item(), eta.grad.item()])
     assert np.all(np.abs(got - o_grads[0]) <= 1e-3 * np.abs(o_grads[0]).max())
 
