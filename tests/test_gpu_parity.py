@@ -162,6 +162,24 @@ def test_mixed_batch_parity_100_steps(path):
                 assert np.abs(om[c][r] - o_om[c][r]).max() < 2e-3, (c, r)
 
 
+@pytest.mark.parametrize("path", [XY_PATH_BATCHED, XY_PATH_PLAIN])
+def test_ordered_start_parity_100_steps(path):
+    """From the ordered state the benchmark workloads start in (theta =
+    2 pi / 5 at T_c), 100 steps on the resident, strip and plain kernels:
+    every site within 1e-4 rad of the oracle except sites next to a cusp
+    event, which T_c reaches within 100 steps; such sites are listed."""
+    shapes = [(64, 64, 2), (256, 64, 2), (32, 256, 1), (12, 10, 2)]
+    specs = [inputs.config(Lx, Ly, n, seed=31 + i, knots=([0], [TC])) for i, (Lx, Ly, n) in enumerate(shapes)]
+    thetas = [np.full((s["n_rep"], s["Lx"] * s["Ly"]), np.float32(2 * PI / 5)) for s in specs]
+    lat, o_th, o_om = make_pair(specs, thetas, path=path)
+    res = stepwise_parity(lat, specs, o_th, o_om, 100)
+    report = (f"worst {res['worst_all']:.3g}; within 1e-4: {res['frac_within_tol']:.6f} of {res['n_sites']}; "
+              f"cusp events {len(res['events'])}; cusp-explained {len(res['cusp'])}; ill-conditioned {len(res['ill'])}")
+    print(report)
+    assert not res["unexplained"], (res["unexplained"][:10], report)
+    assert res["frac_within_tol"] > 1 - 1e-3, report
+
+
 def test_plain_method_workload_parity():
     """64 x 64, one replica, seed 1, theta uniform from the library's own
     initialisation (noise stream tag 1), T_c, 100 steps."""
