@@ -528,10 +528,15 @@ def _oracle_adjoint(specs, o_th, o_om, n, wE, wM):
 
 
 @pytest.mark.parametrize("mode", ["recompute", "backward"])
-@pytest.mark.parametrize("field", ["smooth_p2", "paper_p2.5_lowT"])
+@pytest.mark.parametrize("field", ["smooth_p2", "paper_p2.5_lowT", "staggered_af"])
 def test_adjoint_matches_oracle(field, mode):
     if field == "smooth_p2":
         prm = dict(J_par=2.0, J_perp=0.5, h=1.0, p=2.0, eta=0.8)
+        knots = ([0, 100], [1.0, 0.5])
+    elif field == "staggered_af":
+        # the antiferromagnetic reading: negative couplings, |M| of the
+        # staggered order parameter sigma = (-1)^(x+y)
+        prm = dict(J_par=-2.0, J_perp=-0.5, h=1.0, p=2.0, eta=0.8, staggered=1.0)
         knots = ([0, 100], [1.0, 0.5])
     else:
         prm = dict(h=3.0)
@@ -550,7 +555,7 @@ def test_adjoint_matches_oracle(field, mode):
         specs = [inputs.config(16, 8, 2, seed=3, knots=knots, **prm),
                  inputs.config(128, 4, 1, seed=4, knots=knots, **prm),
                  inputs.config(256, 6, 1, seed=5, knots=knots, **prm)]
-    if field == "smooth_p2":
+    if field in ("smooth_p2", "staggered_af"):
         thetas = _mixed_thetas(specs, seed=61)
     else:
         thetas = [np.full((s["n_rep"], s["Lx"] * s["Ly"]), np.float32(2 * PI / 5)) +
@@ -561,7 +566,10 @@ def test_adjoint_matches_oracle(field, mode):
     n, K = 100, 30
     obj, grads = lat.adjoint(n, checkpoint_every=K, w_E=0.7, w_M=0.3)
     o_obj, o_grads = _oracle_adjoint(specs, o_th, o_om, n, 0.7, 0.3)
-    assert obj == pytest.approx(o_obj, rel=1e-5)
+    # the objective averages per-site terms of size |J| ~ 2 in FP32 partial
+    # sums; where they nearly cancel (antiferromagnetic couplings) the bound is
+    # that rounding, 1e-6 of the terms, not a fraction of the small sum
+    assert obj == pytest.approx(o_obj, rel=1e-5, abs=2e-6)
     scale = np.abs(o_grads).max(axis=1, keepdims=True)
     assert np.all(np.abs(grads - o_grads) <= 1e-3 * scale), (grads, o_grads)
     _, steps = lat.observe()
