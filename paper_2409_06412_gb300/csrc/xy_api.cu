@@ -194,6 +194,12 @@ struct xy_lattice {
     float *thA = nullptr, *omA = nullptr, *thB = nullptr, *omB = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // branches of a captured chunk: one per stepper group (created at the
+    // first capture that has more than one group)
+    static constexpr int kBranches = 8;
+    cudaStream_t aux[kBranches] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kBranches] = {};
     CallArgs* d_call = nullptr;
     static constexpr int kRing = 64;
     CallArgs* h_call = nullptr;  // pinned staging ring of kRing slots
@@ -417,8 +423,51 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     return XY_OK;
 }
 
+// The launches of one stepper group for local steps [jl0, jl0 + cnt): branch
+// b < resident groups is resident group b, then the strip groups, then all
+// plain configurations together.  Lattices of different groups never read
+// each other, so the branches of a chunk need no order among themselves.
+int n_branches(const xy_lattice* L)
+{
+    return (int)(L->res_groups.size() + L->strip_groups.size()) + (L->plain_cfgs.empty() ? 0 : 1);
+}
+
+cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, int b, int64_t jl0, int cnt)
+{
+    const Buffers buf = state_buffers(L);
+    cudaError_t e = cudaSuccess;
+    const int nr = (int)L->res_groups.size(), ns = (int)L->strip_groups.size();
+    if (b < nr) {
+        auto& g = L->res_groups[b];
+        e = launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, g.csize, g.seed,
+                                 jl0, cnt, buf, L->d_call, st);
+        ++L->launches;
+        return e;
+    }
+    for (int i = 0; i < cnt && e == cudaSuccess; ++i) {
+        if (b < nr + ns) {
+            auto& g = L->strip_groups[b - nr];
+            const int rec = (L->cur_rec && ((L->cur_mask >> ((jl0 + i) & 31)) & 1u)) ? L->cur_rec : 0;
+            const int var = rec && g.variant_rec ? g.variant_rec : g.variant;
+            e = launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, var, rec, g.seed, jl0 + i, buf,
+                                  L->d_call, L->pa, st);
+            ++L->launches;
+        } else {
+            for (int c : L->plain_cfgs) {
+                if (e != cudaSuccess) break;
+                e = launch_plain_step(L->d_cfg, L->h_dev[c], jl0 + i, buf, L->d_call, L->pa, 1, st);
+                ++L->launches;
+            }
+        }
+    }
+    return e;
+}
+
 // Capture `chunk` batched steps (kernels + chunk counter) into a graph, or
-// reuse the one captured before for that length.
+// reuse the one captured before for that length.  With several stepper
+// groups the chunk forks into one branch per group and joins before the
+// chunk counter advances, so the groups' kernels overlap (the small shapes
+// fill the large shape's last wave) instead of taking turns every step.
 int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
     for (auto& g : L->graphs)
@@ -426,9 +475,36 @@ int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
             *out = &g;
             return XY_OK;
         }
+    const int nb = n_branches(L);
+    const bool fork = nb >= 2 && nb <= xy_lattice::kBranches + 1;
+    if (fork && !L->fork_ev) {
+        cudaError_t e0 = cudaEventCreateWithFlags(&L->fork_ev, cudaEventDisableTiming);
+        for (int i = 0; i < xy_lattice::kBranches && e0 == cudaSuccess; ++i) {
+            e0 = cudaStreamCreateWithFlags(&L->aux[i], cudaStreamNonBlocking);
+            if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&L->join_ev[i], cudaEventDisableTiming);
+        }
+        if (e0 != cudaSuccess) return fail(XY_ECUDA, "branch streams: %s", cudaGetErrorString(e0));
+    }
     const int64_t before = L->launches;
     CK(cudaStreamBeginCapture(L->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = launch_batched_steps(L, L->cap_stream, 0, chunk, true);
+    int rc = XY_OK;
+    if (fork) {
+        cudaError_t e1 = cudaEventRecord(L->fork_ev, L->cap_stream);
+        for (int b = 1; b < nb && e1 == cudaSuccess; ++b) e1 = cudaStreamWaitEvent(L->aux[b - 1], L->fork_ev, 0);
+        for (int b = 0; b < nb && e1 == cudaSuccess; ++b)
+            e1 = launch_branch(L, b == 0 ? L->cap_stream : L->aux[b - 1], b, 0, chunk);
+        for (int b = 1; b < nb && e1 == cudaSuccess; ++b) {
+            e1 = cudaEventRecord(L->join_ev[b - 1], L->aux[b - 1]);
+            if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(L->cap_stream, L->join_ev[b - 1], 0);
+        }
+        if (e1 == cudaSuccess) {
+            e1 = launch_advance(L->d_call, chunk, L->cap_stream);
+            ++L->launches;
+        }
+        if (e1 != cudaSuccess) rc = fail(XY_ECUDA, "graph capture of the branches: %s", cudaGetErrorString(e1));
+    } else {
+        rc = launch_batched_steps(L, L->cap_stream, 0, chunk, true);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(L->cap_stream, &g);
     const int64_t kernels = L->launches - before;
@@ -961,6 +1037,11 @@ void free_lattice(xy_lattice* L)
     cudaFree(L->rec_buf);
     cudaFree(L->d_err);
     if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
+    for (int i = 0; i < xy_lattice::kBranches; ++i) {
+        if (L->aux[i]) cudaStreamDestroy(L->aux[i]);
+        if (L->join_ev[i]) cudaEventDestroy(L->join_ev[i]);
+    }
+    if (L->fork_ev) cudaEventDestroy(L->fork_ev);
     delete L;
 }
 
