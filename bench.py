@@ -572,6 +572,13 @@ def profile_case(name):
                               n_total=10 ** 9)])
         lat.step(100)
         lat.step(200)
+    elif name == "ccl":
+        # domain labels of 64 lattices of 1024^2 after 200 steps from a random start
+        lat = Lattice([Config(Lx=1024, Ly=1024, n_replicas=64, seed=1, init_mode=0, knots=((0,), (TC,)),
+                              n_total=10 ** 6)])
+        lat.step(200)
+        lat.label_domains(0, 64)
+        lat.label_domains(0, 64)
     elif name == "sf":
         # structure factors of 64 lattices of 1024^2 for k < 16
         lat = Lattice([Config(Lx=1024, Ly=1024, n_replicas=64, seed=1, init_mode=0, knots=((0,), (TC,)),
@@ -588,7 +595,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["static", "static-L512", "dynamic-z", "kibble-zurek"], default="static")
-    ap.add_argument("--profile-case", choices=["adjoint-small", "plain64", "sf"], default=None,
+    ap.add_argument("--profile-case", choices=["adjoint-small", "plain64", "sf", "ccl"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

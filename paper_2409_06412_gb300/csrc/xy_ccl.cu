@@ -116,10 +116,29 @@ __global__ void ccl_local_kernel(const float* theta, int Lx, int Ly, int TW, int
     const int64_t N = (int64_t)Lx * Ly;
     const float* th = theta + (int64_t)lat * N;
     const bool sp = spin_of(th[(int64_t)gy * Lx + gx]);
-    s_lab[lid] = lid;
-    __syncthreads();
-    if (lx + 1 < TW && spin_of(th[(int64_t)gy * Lx + gx + 1]) == sp) union_shared(s_lab, lid, lid + 1);
-    if (ly + 1 < TH && spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp) union_shared(s_lab, lid, lid + TW);
+    if (TW == 32) {
+        // a warp is one tile row: every site points at the first site of its
+        // run of equal spins (the run's smallest index), found with one
+        // ballot, and only vertical contacts need unions, one per pair of
+        // runs touching side by side
+        constexpr unsigned kAll = 0xFFFFFFFFu;
+        const bool spL = __shfl_up_sync(kAll, sp, 1);
+        const bool horiz = lx > 0 && sp == spL;  // same run as the left site
+        const unsigned starts = __ballot_sync(kAll, !horiz);
+        const unsigned upto = lx == 31 ? starts : (starts & ((2u << lx) - 1u));
+        s_lab[lid] = ly * 32 + (31 - __clz(upto));
+        __syncthreads();
+        if (ly + 1 < TH) {  // uniform in the warp
+            const bool vert = spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp;
+            const bool vertL = __shfl_up_sync(kAll, vert, 1);
+            if (vert && !(horiz && vertL)) union_shared(s_lab, lid, lid + 32);
+        }
+    } else {
+        s_lab[lid] = lid;
+        __syncthreads();
+        if (lx + 1 < TW && spin_of(th[(int64_t)gy * Lx + gx + 1]) == sp) union_shared(s_lab, lid, lid + 1);
+        if (ly + 1 < TH && spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp) union_shared(s_lab, lid, lid + TW);
+    }
     __syncthreads();
     const int root = find_root_shared(s_lab, lid);
     const int rly = root / TW, rlx = root - rly * TW;
@@ -163,7 +182,11 @@ __global__ void ccl_flatten_kernel(int64_t N, int n_lat, int32_t* labels, int32_
     const int s = (int)(i - (int64_t)lat * N);
     int32_t* L = labels + (int64_t)lat * N;
     const int r = find_root_global(L, s, g_union_limit, err);
-    atomicAdd(&sizes[(int64_t)lat * N + r], 1);
+    // lanes that found the same root of the same lattice add their count
+    // once (a large domain would otherwise serialise on one address)
+    const unsigned long long key = ((unsigned long long)(unsigned)lat << 32) | (unsigned)r;
+    const unsigned grp = __match_any_sync(__activemask(), key);
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&sizes[(int64_t)lat * N + r], __popc(grp));
     // the final write happens after every find of this pass may have read L[s]
     // as an intermediate node; writing the root keeps the forest valid.
     L[s] = r;
@@ -183,44 +206,64 @@ __global__ void ccl_size_hist_kernel(int64_t N, int n_lat, const int32_t* labels
 }
 
 // Pass 5: ordered compaction of the nonzero counts into (size, count) pairs,
-// one block per lattice, ascending size.
-__global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, const int32_t* counts, int64_t* hist,
-                                                           int64_t hist_cap, int64_t* n_sizes, int* err)
+// one block per lattice, ascending size.  Warp w owns a contiguous slice of
+// the sizes 1..N and reads it 32 consecutive entries at a time, so the order
+// of the slices is the order of the sizes: each warp counts its nonzero
+// entries, one block-wide prefix over the warps places them, and a second
+// pass writes them with ballot ranks.
+__global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, const int32_t* __restrict__ counts,
+                                                           int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err)
 {
-    __shared__ int s_warp[32];
-    __shared__ int64_t s_base;
+    __shared__ int64_t s_warp[32];
     const int lat = blockIdx.x;
     const int32_t* cnt = counts + (int64_t)lat * (N + 1);
     int64_t* out = hist ? hist + (int64_t)lat * hist_cap * 2 : nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) s_base = 0;
-    __syncthreads();
-    for (int64_t c0 = 1; c0 <= N; c0 += blockDim.x) {
-        const int64_t sz = c0 + threadIdx.x;
-        const int v = sz <= N ? cnt[sz] : 0;
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, v != 0);
-        const int before = __popc(m & ((1u << lane) - 1u));
-        if (lane == 0) s_warp[warp] = __popc(m);
-        __syncthreads();
-        int woff = 0, total = 0;
-        for (int w = 0; w < nw; ++w) {
-            if (w < warp) woff += s_warp[w];
-            total += s_warp[w];
+    const int64_t per = ((N + nw - 1) / nw + 31) / 32 * 32;  // whole rounds of 32 per warp
+    const int64_t lo = 1 + (int64_t)warp * per;
+    const int64_t hi = lo + per < N + 1 ? lo + per : N + 1;
+    int64_t mine = 0;  // nonzero entries of this warp's slice (same in every lane)
+    constexpr int kU = 8;  // rounds of 32 loaded before their ballots: eight loads in flight
+    for (int64_t z0 = lo; z0 < hi; z0 += 32 * kU) {
+        int v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t z = z0 + 32 * u + lane;
+            v[u] = z < hi ? cnt[z] : 0;
         }
-        const int64_t pos = s_base + woff + before;
-        if (v != 0 && out) {
-            if (pos < hist_cap) {
-                out[2 * pos] = sz;
-                out[2 * pos + 1] = v;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) mine += __popc(__ballot_sync(0xFFFFFFFFu, v[u] != 0));
+    }
+    if (lane == 0) s_warp[warp] = mine;
+    __syncthreads();
+    int64_t pos = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < warp) pos += s_warp[w];
+        total += s_warp[w];
+    }
+    if (out && mine > 0) {
+        for (int64_t z0 = lo; z0 < hi; z0 += 32 * kU) {
+            int v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t z = z0 + 32 * u + lane;
+                v[u] = z < hi ? cnt[z] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, v[u] != 0);
+                const int64_t at = pos + __popc(m & ((1u << lane) - 1u));
+                if (v[u] != 0 && at < hist_cap) {
+                    out[2 * at] = z0 + 32 * u + lane;
+                    out[2 * at + 1] = v[u];
+                }
+                pos += __popc(m);
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_base += total;
-        __syncthreads();
     }
     if (threadIdx.x == 0) {
-        if (n_sizes) n_sizes[lat] = s_base;
-        if (out && s_base > hist_cap) atomicExch(err, XY_EINVAL);
+        if (n_sizes) n_sizes[lat] = total;
+        if (out && total > hist_cap) atomicExch(err, XY_EINVAL);
     }
 }
 
