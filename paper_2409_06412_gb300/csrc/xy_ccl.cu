@@ -146,31 +146,30 @@ __global__ void ccl_local_kernel(const float* theta, int Lx, int Ly, int TW, int
 }
 
 // Pass 2: merge across the right and bottom border of every tile (periodic).
+// One thread per border site: the TH sites of a tile's right column (each
+// linked to its right neighbour) and the TW sites of its bottom row (each
+// linked to the site below); the corner does both.
 __global__ void ccl_border_kernel(const float* theta, int Lx, int Ly, int TW, int TH, int n_lat, int32_t* labels,
                                   int* err)
 {
     const int64_t N = (int64_t)Lx * Ly;
-    const int64_t per_lat = N;
+    const int tiles_x = Lx / TW, tiles = tiles_x * (Ly / TH), per_tile = TH + TW;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= per_lat * n_lat) return;
-    const int lat = (int)(i / per_lat);
-    const int s = (int)(i - (int64_t)lat * per_lat);
-    const int y = s / Lx, x = s - y * Lx;
-    const bool right_border = (x % TW) == TW - 1;
-    const bool bottom_border = (y % TH) == TH - 1;
-    if (!right_border && !bottom_border) return;
+    if (i >= (int64_t)n_lat * tiles * per_tile) return;
+    const int lat = (int)(i / ((int64_t)tiles * per_tile));
+    const int rem = (int)(i - (int64_t)lat * tiles * per_tile);
+    const int tile = rem / per_tile, k = rem - tile * per_tile;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const bool right = k < TH;
+    const int y = right ? ty * TH + k : ty * TH + TH - 1;
+    const int x = right ? tx * TW + TW - 1 : tx * TW + (k - TH);
+    const int s = y * Lx + x;
     const float* th = theta + (int64_t)lat * N;
     int32_t* L = labels + (int64_t)lat * N;
     const bool sp = spin_of(th[s]);
     const int limit = g_union_limit;
-    if (right_border) {
-        const int n = y * Lx + (x + 1 == Lx ? 0 : x + 1);
-        if (spin_of(th[n]) == sp) union_global(L, s, n, limit, err);
-    }
-    if (bottom_border) {
-        const int n = (y + 1 == Ly ? 0 : y + 1) * Lx + x;
-        if (spin_of(th[n]) == sp) union_global(L, s, n, limit, err);
-    }
+    const int n = right ? y * Lx + (x + 1 == Lx ? 0 : x + 1) : (y + 1 == Ly ? 0 : y + 1) * Lx + x;
+    if (spin_of(th[n]) == sp) union_global(L, s, n, limit, err);
 }
 
 // Pass 3: every site points straight at its root; count component sizes.
@@ -291,7 +290,8 @@ cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* l
                                                                                         labels);
     const int64_t total = N * n_lat;
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    ccl_border_kernel<<<blocks, 256, 0, st>>>(theta, Lx, Ly, TW, TH, n_lat, labels, err);
+    const int64_t border = (int64_t)n_lat * tiles * (TW + TH);
+    ccl_border_kernel<<<(unsigned)((border + 255) / 256), 256, 0, st>>>(theta, Lx, Ly, TW, TH, n_lat, labels, err);
     ccl_flatten_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch, err);
     ccl_size_hist_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch, count_scratch);
     ccl_compact_kernel<<<n_lat, 1024, 0, st>>>(N, count_scratch, hist, hist_cap, n_sizes, err);
