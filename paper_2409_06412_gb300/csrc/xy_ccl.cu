@@ -191,17 +191,25 @@ __global__ void ccl_flatten_kernel(int64_t N, int n_lat, int32_t* labels, int32_
     L[s] = r;
 }
 
-// Pass 4: histogram of component sizes: count[size] over roots.
+// Pass 4: histogram of component sizes: count[size] over roots.  One thread
+// per quad of sites (Lx is a multiple of 4); the label buffer may be the
+// caller's and only 4-byte aligned, so the quad is read as four words.
 __global__ void ccl_size_hist_kernel(int64_t N, int n_lat, const int32_t* labels, const int32_t* sizes,
                                      int32_t* counts)
 {
+    const int64_t nq = N / 4;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N * n_lat) return;
-    const int lat = (int)(i / N);
-    const int s = (int)(i - (int64_t)lat * N);
-    if (labels[(int64_t)lat * N + s] != s) return;
-    const int sz = sizes[(int64_t)lat * N + s];
-    atomicAdd(&counts[(int64_t)lat * (N + 1) + sz], 1);
+    if (i >= nq * n_lat) return;
+    const int lat = (int)(i / nq);
+    const int s0 = (int)(4 * (i - (int64_t)lat * nq));
+    const int32_t* lp = labels + (int64_t)lat * N + s0;
+    const int l4[4] = {lp[0], lp[1], lp[2], lp[3]};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (l4[k] != s0 + k) continue;
+        const int sz = sizes[(int64_t)lat * N + s0 + k];
+        atomicAdd(&counts[(int64_t)lat * (N + 1) + sz], 1);
+    }
 }
 
 // Pass 5: ordered compaction of the nonzero counts into (size, count) pairs,
@@ -293,7 +301,8 @@ cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* l
     const int64_t border = (int64_t)n_lat * tiles * (TW + TH);
     ccl_border_kernel<<<(unsigned)((border + 255) / 256), 256, 0, st>>>(theta, Lx, Ly, TW, TH, n_lat, labels, err);
     ccl_flatten_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch, err);
-    ccl_size_hist_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch, count_scratch);
+    ccl_size_hist_kernel<<<(unsigned)((total / 4 + 255) / 256), 256, 0, st>>>(N, n_lat, labels, size_scratch,
+                                                                              count_scratch);
     ccl_compact_kernel<<<n_lat, 1024, 0, st>>>(N, count_scratch, hist, hist_cap, n_sizes, err);
     return cudaGetLastError();
 }
