@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(256) sf_rows_kernel(const float* theta, const 
 #pragma unroll
         for (int q = 0; q < kKC; ++q) idx[q] = idx0[q];
         const float* row = th + (int64_t)y * Lx;
-        for (int x = lane; x < Lx; x += 32) {
+        // one site of this lane: its rotor against the kKC twiddles, in x order
+        auto site = [&](float t) {
             float sn, cs;
-            sincosf(r * row[x], &sn, &cs);
+            sincosf(r * t, &sn, &cs);
 #pragma unroll
             for (int q = 0; q < kKC; ++q) {
                 const float2 w = W[idx[q]];
@@ -94,7 +95,16 @@ __global__ void __launch_bounds__(256) sf_rows_kernel(const float* theta, const 
                 idx[q] += step[q];
                 if (idx[q] >= Lx) idx[q] -= Lx;
             }
+        };
+        int x = lane;
+        for (; x + 96 < Lx; x += 128) {  // four loads in flight, then the four sites in order
+            float t4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t4[u] = row[x + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) site(t4[u]);
         }
+        for (; x < Lx; x += 32) site(row[x]);
         // reduce-scatter butterfly: afterwards lane i holds the warp total of v[i]
 #pragma unroll
         for (int o = 16, n = 32; o >= 1; o >>= 1, n >>= 1) {
@@ -149,9 +159,10 @@ __global__ void __launch_bounds__(256) sf_cols_kernel(const float* theta, const 
 #pragma unroll
     for (int i = 0; i < 4 * kKC; ++i) v[i] = 0.f;
     const float* col = theta + lt.offset + (live ? x : 0);
-    for (int y = 0; y < Ly; ++y) {
+    // one site of this column: its rotor against the kKC twiddles, in y order
+    auto site = [&](float t) {
         float sn = 0.f, cs = 0.f;
-        if (live) sincosf(r * col[(int64_t)y * Lx], &sn, &cs);
+        if (live) sincosf(r * t, &sn, &cs);
 #pragma unroll
         for (int q = 0; q < kKC; ++q) {
             const float2 w = W[idx[q]];
@@ -162,7 +173,18 @@ __global__ void __launch_bounds__(256) sf_cols_kernel(const float* theta, const 
             idx[q] += step[q];
             if (idx[q] >= Ly) idx[q] -= Ly;
         }
+    };
+    int y = 0;
+    for (; y + 3 < Ly; y += 4) {  // four loads in flight, then the four sites in order
+        float t4[4] = {0.f, 0.f, 0.f, 0.f};
+        if (live) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t4[u] = col[(int64_t)(y + u) * Lx];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) site(t4[u]);
     }
+    for (; y < Ly; ++y) site(live ? col[(int64_t)y * Lx] : 0.f);
     // |a_k(x)|^2 per thread, summed over the block's columns in a fixed order
     __shared__ double s_acc[kKC][256 / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
