@@ -423,33 +423,155 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     return XY_OK;
 }
 
-// The launches of one stepper group for local steps [jl0, jl0 + cnt): branch
-// b < resident groups is resident group b, then the strip groups, then all
-// plain configurations together.  Lattices of different groups never read
-// each other, so the branches of a chunk need no order among themselves.
-int n_branches(const xy_lattice* L)
+// Concurrent slices of a set of kernel groups.  Lattices never read each
+// other within a step, so a group's blocks may be cut into slices at lattice
+// boundaries and each slice launched on its own stream, keeping only its own
+// step order: when one slice's launch drains, the next slice's blocks fill
+// the SMs it leaves idle, instead of every step waiting for the slowest SM.
+// Each group with m lattices gets min(kMaxSlices, m) slices, fewer (largest
+// counts first) while the total, with `fixed` unsplit branches, exceeds
+// `budget`; cuts fall at the task nearest an even share of the group's tasks
+// that starts a lattice.
+constexpr int kMaxSlices = 4;
+
+template <class Task>
+std::vector<int> lattice_starts(const std::vector<Task>& tk)
 {
-    return (int)(L->res_groups.size() + L->strip_groups.size()) + (L->plain_cfgs.empty() ? 0 : 1);
+    std::vector<int> st;
+    for (int i = 0; i < (int)tk.size(); ++i)
+        if (i == 0 || tk[i].cfg != tk[i - 1].cfg || tk[i].rep != tk[i - 1].rep) st.push_back(i);
+    return st;
 }
 
-cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, int b, int64_t jl0, int cnt)
+// Slices per group: the counts depend only on the groups' lattice counts
+// (n_lat), so they are known before a group's tasks are built.
+template <class Group>
+std::vector<int> slice_parts(const std::vector<Group>& groups, int fixed, int budget)
+{
+    const size_t G = groups.size();
+    std::vector<int> parts(G);
+    int total = fixed;
+    for (size_t g = 0; g < G; ++g) {
+        parts[g] = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSlices, groups[g].n_lat));
+        total += parts[g];
+    }
+    while (total > budget) {
+        size_t big = G;
+        for (size_t g = 0; g < G; ++g)
+            if (parts[g] > 1 && (big == G || parts[g] > parts[big])) big = g;
+        if (big == G) break;
+        --parts[big];
+        --total;
+    }
+    return parts;
+}
+
+// The first task of each of `parts` slices of tk, followed by tk's size.
+template <class Task>
+std::vector<int> cut_tasks(const std::vector<Task>& tk, int parts)
+{
+    const int nt = (int)tk.size();
+    const std::vector<int> starts = lattice_starts(tk);
+    std::vector<int> cuts{0};
+    for (int p = 1; p < parts; ++p) {
+        const int64_t want = (int64_t)nt * p / parts;
+        int best = -1;
+        for (int s : starts)
+            if (s > cuts.back() && (best < 0 || std::llabs(s - want) < std::llabs(best - want))) best = s;
+        if (best > 0 && best < nt) cuts.push_back(best);
+    }
+    cuts.push_back(nt);
+    return cuts;
+}
+
+// cuts[g]: the first task of each slice of group g followed by the group's task count
+template <class Group>
+std::vector<std::vector<int>> slice_groups(const std::vector<Group>& groups, int fixed, int budget)
+{
+    const std::vector<int> parts = slice_parts(groups, fixed, budget);
+    std::vector<std::vector<int>> cuts(groups.size());
+    for (size_t g = 0; g < groups.size(); ++g) cuts[g] = cut_tasks(groups[g].tasks, parts[g]);
+    return cuts;
+}
+
+// The branch streams and their fork/join events, created on first use.
+cudaError_t ensure_branch_streams(xy_lattice* L)
+{
+    if (L->fork_ev) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&L->fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < xy_lattice::kBranches && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&L->aux[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->join_ev[i], cudaEventDisableTiming);
+    }
+    return e;
+}
+
+// fn(stream, task0, n_tasks) `reps` times for each slice of `cuts`, slice q
+// on stream q (the object's stream, then its branch streams), forked from
+// and joined back to the object's stream: the way a captured chunk runs a
+// sliced group, so that the autotuner times its candidates that way too.
+template <class F>
+cudaError_t launch_sliced(xy_lattice* L, const std::vector<int>& cuts, int reps, F&& fn)
+{
+    const int ns = std::min((int)cuts.size() - 1, xy_lattice::kBranches + 1);
+    cudaError_t e = cudaSuccess;
+    if (ns <= 1) {
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = fn(L->stream, 0, cuts.back());
+        return e;
+    }
+    if ((int)cuts.size() - 1 > ns) return cudaErrorInvalidValue;
+    e = ensure_branch_streams(L);
+    if (e == cudaSuccess) e = cudaEventRecord(L->fork_ev, L->stream);
+    for (int q = 1; q < ns && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(L->aux[q - 1], L->fork_ev, 0);
+    for (int q = 0; q < ns && e == cudaSuccess; ++q)
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = fn(q == 0 ? L->stream : L->aux[q - 1], cuts[q], cuts[q + 1] - cuts[q]);
+    for (int q = 1; q < ns && e == cudaSuccess; ++q) {
+        e = cudaEventRecord(L->join_ev[q - 1], L->aux[q - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(L->stream, L->join_ev[q - 1], 0);
+    }
+    return e;
+}
+
+// Branches of a captured chunk: each resident group, each slice of a strip
+// group, and all plain configurations together.  Branches share no lattice,
+// so a chunk's branches need no order among themselves.
+struct Branch {
+    int kind;  // 0 resident group, 1 strip group slice, 2 plain configurations
+    int group;
+    int task0, n_tasks;
+};
+
+std::vector<Branch> chunk_branches(const xy_lattice* L)
+{
+    std::vector<Branch> out;
+    for (int r = 0; r < (int)L->res_groups.size(); ++r) out.push_back({0, r, 0, 0});
+    const int fixed = (int)L->res_groups.size() + (L->plain_cfgs.empty() ? 0 : 1);
+    const auto cuts = slice_groups(L->strip_groups, fixed, xy_lattice::kBranches + 1);
+    for (int s = 0; s < (int)L->strip_groups.size(); ++s)
+        for (size_t p = 0; p + 1 < cuts[s].size(); ++p)
+            out.push_back({1, s, cuts[s][p], cuts[s][p + 1] - cuts[s][p]});
+    if (!L->plain_cfgs.empty()) out.push_back({2, 0, 0, 0});
+    return out;
+}
+
+cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, const Branch& br, int64_t jl0, int cnt)
 {
     const Buffers buf = state_buffers(L);
     cudaError_t e = cudaSuccess;
-    const int nr = (int)L->res_groups.size(), ns = (int)L->strip_groups.size();
-    if (b < nr) {
-        auto& g = L->res_groups[b];
+    if (br.kind == 0) {
+        auto& g = L->res_groups[br.group];
         e = launch_resident_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.Ly, g.threads, g.csize, g.seed,
                                  jl0, cnt, buf, L->d_call, st);
         ++L->launches;
         return e;
     }
     for (int i = 0; i < cnt && e == cudaSuccess; ++i) {
-        if (b < nr + ns) {
-            auto& g = L->strip_groups[b - nr];
+        if (br.kind == 1) {
+            auto& g = L->strip_groups[br.group];
             const int rec = (L->cur_rec && ((L->cur_mask >> ((jl0 + i) & 31)) & 1u)) ? L->cur_rec : 0;
             const int var = rec && g.variant_rec ? g.variant_rec : g.variant;
-            e = launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, var, rec, g.seed, jl0 + i, buf,
+            e = launch_strip_step(L->d_cfg, g.d_tasks + br.task0, br.n_tasks, g.H, var, rec, g.seed, jl0 + i, buf,
                                   L->d_call, L->pa, st);
             ++L->launches;
         } else {
@@ -464,10 +586,10 @@ cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, int b, int64_t jl0, in
 }
 
 // Capture `chunk` batched steps (kernels + chunk counter) into a graph, or
-// reuse the one captured before for that length.  With several stepper
-// groups the chunk forks into one branch per group and joins before the
-// chunk counter advances, so the groups' kernels overlap (the small shapes
-// fill the large shape's last wave) instead of taking turns every step.
+// reuse the one captured before for that length.  The chunk forks into its
+// branches (chunk_branches) and joins before the chunk counter advances, so
+// their kernels overlap (one branch's launches fill the SMs another's leave
+// idle as its launch drains) instead of taking turns every step.
 int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
     for (auto& g : L->graphs)
@@ -475,14 +597,11 @@ int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
             *out = &g;
             return XY_OK;
         }
-    const int nb = n_branches(L);
+    const std::vector<Branch> brs = chunk_branches(L);
+    const int nb = (int)brs.size();
     const bool fork = nb >= 2 && nb <= xy_lattice::kBranches + 1;
-    if (fork && !L->fork_ev) {
-        cudaError_t e0 = cudaEventCreateWithFlags(&L->fork_ev, cudaEventDisableTiming);
-        for (int i = 0; i < xy_lattice::kBranches && e0 == cudaSuccess; ++i) {
-            e0 = cudaStreamCreateWithFlags(&L->aux[i], cudaStreamNonBlocking);
-            if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&L->join_ev[i], cudaEventDisableTiming);
-        }
+    if (fork) {
+        const cudaError_t e0 = ensure_branch_streams(L);
         if (e0 != cudaSuccess) return fail(XY_ECUDA, "branch streams: %s", cudaGetErrorString(e0));
     }
     const int64_t before = L->launches;
@@ -492,7 +611,7 @@ int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
         cudaError_t e1 = cudaEventRecord(L->fork_ev, L->cap_stream);
         for (int b = 1; b < nb && e1 == cudaSuccess; ++b) e1 = cudaStreamWaitEvent(L->aux[b - 1], L->fork_ev, 0);
         for (int b = 0; b < nb && e1 == cudaSuccess; ++b)
-            e1 = launch_branch(L, b == 0 ? L->cap_stream : L->aux[b - 1], b, 0, chunk);
+            e1 = launch_branch(L, b == 0 ? L->cap_stream : L->aux[b - 1], brs[b], 0, chunk);
         for (int b = 1; b < nb && e1 == cudaSuccess; ++b) {
             e1 = cudaEventRecord(L->join_ev[b - 1], L->aux[b - 1]);
             if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(L->cap_stream, L->join_ev[b - 1], 0);
@@ -569,11 +688,16 @@ int autotune_lattice(xy_lattice* L)
     CK(cudaEventCreate(&e1));
     int rc = time_window(L, 8);
     const Buffers buf = state_buffers(L);
+    // candidates run sliced the way the captured chunks run them
+    const std::vector<int> parts =
+        slice_parts(L->strip_groups, (int)L->res_groups.size() + (L->plain_cfgs.empty() ? 0 : 1),
+                    xy_lattice::kBranches + 1);
     for (auto& g : L->strip_groups) {
         if (rc) break;
         if ((int64_t)g.Lx * g.Ly * g.n_lat < ((int64_t)1 << 21)) continue;  // too small to matter
+        const int n_parts = parts[&g - L->strip_groups.data()];
         char key[256];
-        snprintf(key, sizeof key, "%s|strip|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
+        snprintf(key, sizeof key, "%s|strip-sliced|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
         int bh = 0, bv = 0;
         // a cached choice is used only if it satisfies the same constraints
         // as the candidates below (the cache is a plain text file)
@@ -595,23 +719,24 @@ int autotune_lattice(xy_lattice* L)
                 if ((strip_units_per_lattice(g.Lx, g.Ly, H) + 7) / 8 > L->pa.max_units) continue;
                 g.H = H;
                 if ((rc = build_strip_tasks(L, g))) break;
-                const int nt = (int)g.tasks.size();
+                const std::vector<int> cuts = cut_tasks(g.tasks, n_parts);
                 float t_best[3] = {1e30f, 1e30f, 1e30f};
                 int reps = 3;
                 for (int round = 0; round < 5; ++round)
                     for (int vi = 0; vi < 3; ++vi) {
                         const int v = 2 + vi;
-                        CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, g.seed, 0, buf, L->d_call, L->pa,
-                                             L->stream));
+                        auto run = [&](cudaStream_t st, int t0, int cnt) {
+                            return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, H, v, 0, g.seed, 0, buf,
+                                                     L->d_call, L->pa, st);
+                        };
+                        CK(launch_sliced(L, cuts, 1, run));
                         CK(cudaEventRecord(e0, L->stream));
-                        for (int i = 0; i < reps; ++i)
-                            CK(launch_strip_step(L->d_cfg, g.d_tasks, nt, H, v, 0, g.seed, 0, buf, L->d_call,
-                                                 L->pa, L->stream));
+                        CK(launch_sliced(L, cuts, reps, run));
                         CK(cudaEventRecord(e1, L->stream));
                         CK(cudaEventSynchronize(e1));
                         float ms = 0.f;
                         CK(cudaEventElapsedTime(&ms, e0, e1));
-                        L->launches += 1 + reps;
+                        L->launches += (int64_t)(1 + reps) * ((int)cuts.size() - 1);
                         t_best[vi] = std::min(t_best[vi], ms / reps);
                         if (round == 0 && vi == 0 && ms < 0.5f)
                             reps = std::min(64, (int)(0.5f / std::max(ms / reps, 1e-3f)) + 1);
@@ -634,7 +759,8 @@ int autotune_lattice(xy_lattice* L)
             // carry more live registers: their own variant at this H, among
             // those that do not spill
             char keyr[256];
-            snprintf(keyr, sizeof keyr, "%s|striprec|%d|%d|%lld|%d", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat, bh);
+            snprintf(keyr, sizeof keyr, "%s|striprec-sliced|%d|%d|%lld|%d", gpu.c_str(), g.Lx, g.Ly,
+                     (long long)g.n_lat, bh);
             int rv = 0, unused = 0;
             if (g_tune.get(keyr, &rv, &unused) && (rv < 2 || rv > 4)) rv = 0;
             if (rv == 0) {
@@ -650,18 +776,19 @@ int autotune_lattice(xy_lattice* L)
                     cudaFree(scratch);
                     break;
                 }
-                const int nt = (int)g.tasks.size();
+                const std::vector<int> cuts = cut_tasks(g.tasks, n_parts);
                 float t_best[2] = {1e30f, 1e30f};
                 int reps = 3;
                 for (int round = 0; round < 5 && rc == XY_OK; ++round)
                     for (int vi = 0; vi < 2; ++vi) {
                         const int v = 2 + vi;
-                        cudaError_t e = launch_strip_step(L->d_cfg, g.d_tasks, nt, bh, v, 1, g.seed, 0, buf,
-                                                          L->d_call, L->pa, L->stream);
+                        auto run = [&](cudaStream_t st, int t0, int cnt) {
+                            return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, bh, v, 1, g.seed, 0, buf,
+                                                     L->d_call, L->pa, st);
+                        };
+                        cudaError_t e = launch_sliced(L, cuts, 1, run);
                         if (e == cudaSuccess) e = cudaEventRecord(e0, L->stream);
-                        for (int i = 0; i < reps && e == cudaSuccess; ++i)
-                            e = launch_strip_step(L->d_cfg, g.d_tasks, nt, bh, v, 1, g.seed, 0, buf, L->d_call,
-                                                  L->pa, L->stream);
+                        if (e == cudaSuccess) e = launch_sliced(L, cuts, reps, run);
                         if (e == cudaSuccess) e = cudaEventRecord(e1, L->stream);
                         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                         float ms = 0.f;
@@ -671,7 +798,7 @@ int autotune_lattice(xy_lattice* L)
                             rc = fail(XY_ECUDA, "autotune (recording launches): %s", cudaGetErrorString(e));
                             break;
                         }
-                        L->launches += 1 + reps;
+                        L->launches += (int64_t)(1 + reps) * ((int)cuts.size() - 1);
                         t_best[vi] = std::min(t_best[vi], ms / reps);
                         if (round == 0 && vi == 0 && ms < 0.5f)
                             reps = std::min(64, (int)(0.5f / std::max(ms / reps, 1e-3f)) + 1);
@@ -1590,10 +1717,11 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     {
         const std::string gpu = gpu_name();
         bool zeroed = false;
+        const std::vector<int> back_parts = slice_parts(adj_groups, 0, xy_lattice::kBranches + 1);
         for (auto& g : adj_groups) {
             char key[256];
-            snprintf(key, sizeof key, "%s|%s|%d|%d|%lld", gpu.c_str(), back ? "adjback" : "adjband", g.Lx, g.Ly,
-                     (long long)g.n_lat);
+            snprintf(key, sizeof key, "%s|%s|%d|%d|%lld", gpu.c_str(), back ? "adjback-sliced" : "adjband", g.Lx,
+                     g.Ly, (long long)g.n_lat);
             int bh = 0, unused = 0;
             const bool big = (int64_t)g.Lx * g.Ly * g.n_lat >= ((int64_t)1 << 21);
             if (L->autotune && big && !g_tune.get(key, &bh, &unused)) {
@@ -1622,7 +1750,11 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 if (e == cudaSuccess && back) e = cudaMalloc(&mp_tmp, sizeof(double) * 2 * Pt * L->B);
                 if (e == cudaSuccess && back) e = cudaMemsetAsync(mp_tmp, 0, sizeof(double) * 2 * Pt * L->B, L->stream);
                 // one timed reverse launch of candidate band height h on zeroed buffers
-                auto tune_launch = [&](int h) -> cudaError_t {
+                // the backward schedule's candidates run sliced the way the
+                // reverse sweep runs them
+                const int n_parts = back ? back_parts[&g - adj_groups.data()] : 1;
+                std::vector<int> cuts;
+                auto tune_launch = [&](int h, int reps) -> cudaError_t {
                     if (back) {
                         BackArgs A{};
                         A.th_in = sbuf;
@@ -1642,7 +1774,10 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                         A.wE = (float)wE;
                         A.wM = (float)wM;
                         A.gacc = g_tmp;
-                        return launch_adjoint_back(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, true, A, L->stream);
+                        return launch_sliced(L, cuts, reps, [&](cudaStream_t st, int t0, int cnt) {
+                            A.block_base = t0;
+                            return launch_adjoint_back(L->d_cfg, d_tk + t0, cnt, g.Lx, h, g.seed, true, A, st);
+                        });
                     }
                     BandArgs R{};
                     R.theta = seg;
@@ -1659,7 +1794,10 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                     R.wE = (float)wE;
                     R.wM = (float)wM;
                     R.gacc = g_tmp;
-                    return launch_adjoint_band(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, R, L->stream);
+                    cudaError_t er = cudaSuccess;
+                    for (int i = 0; i < reps && er == cudaSuccess; ++i)
+                        er = launch_adjoint_band(L->d_cfg, d_tk, (int)tk.size(), g.Lx, h, g.seed, R, L->stream);
+                    return er;
                 };
                 if (e == cudaSuccess) e = cudaEventCreate(&e0);
                 if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -1667,18 +1805,19 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 for (int h : cands) {
                     if (e != cudaSuccess) break;
                     band_tasks(g, h, tk);
+                    cuts = cut_tasks(tk, n_parts);
                     e = cudaMemcpy(d_tk, tk.data(), sizeof(BandTask) * tk.size(), cudaMemcpyHostToDevice);
                     int reps = 2;
                     float t_best = 1e30f;
                     for (int round = 0; round < 5 && e == cudaSuccess; ++round) {
-                        e = tune_launch(h);
+                        e = tune_launch(h, 1);
                         if (e == cudaSuccess) e = cudaEventRecord(e0, L->stream);
-                        for (int i = 0; i < reps && e == cudaSuccess; ++i) e = tune_launch(h);
+                        if (e == cudaSuccess) e = tune_launch(h, reps);
                         if (e == cudaSuccess) e = cudaEventRecord(e1, L->stream);
                         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                         float ms = 0.f;
                         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                        L->launches += 1 + reps;
+                        L->launches += (int64_t)(1 + reps) * (back ? (int)cuts.size() - 1 : 1);
                         t_best = std::min(t_best, ms / reps);
                         if (round == 0 && ms < 0.5f) reps = std::min(64, (int)(0.5f / std::max(ms / reps, 1e-3f)) + 1);
                     }
@@ -1782,6 +1921,21 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         const float* in_th = L->thA;
         const float* in_v = L->omA;
         int sb = 0;
+        // Each group's lattices run as slices on their own streams
+        // (slice_groups); slice q of the whole sweep goes on stream q.
+        const auto cuts = slice_groups(adj_groups, 0, xy_lattice::kBranches + 1);
+        int n_slices = 0;
+        for (const auto& c : cuts) n_slices += (int)c.size() - 1;
+        const int n_aux = std::min(n_slices, xy_lattice::kBranches + 1) - 1;
+        if (n_aux > 0) {
+            const cudaError_t e0 = ensure_branch_streams(L);
+            if (e0 != cudaSuccess) {
+                cleanup();
+                return fail(XY_ECUDA, "reverse streams: %s", cudaGetErrorString(e0));
+            }
+        }
+        if (n_aux > 0) CKA(cudaEventRecord(L->fork_ev, L->stream));
+        for (int i = 0; i < n_aux; ++i) CKA(cudaStreamWaitEvent(L->aux[i], L->fork_ev, 0));
         for (int64_t k = k0 + n; k >= k0; --k) {
             const bool bk = k < k0 + n;
             const int64_t m = k + 1 - k0;
@@ -1790,6 +1944,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 in_v = in_th + T;
             }
             float* out_th = sbuf + 2 * T * sb;
+            int q = 0;  // slice of the sweep
             for (auto& g : adj_groups) {
                 BackArgs A{};
                 A.th_in = in_th;
@@ -1809,9 +1964,13 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 A.wE = (float)wE;
                 A.wM = (float)wM;
                 A.gacc = gacc;
-                A.block_base = g.block_base;
-                CKA(launch_adjoint_back(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.Lx, g.H, g.seed, bk, A, L->stream));
-                ++L->launches;
+                const auto& c = cuts[&g - adj_groups.data()];
+                for (size_t p = 0; p + 1 < c.size(); ++p, ++q) {
+                    A.block_base = g.block_base + c[p];
+                    CKA(launch_adjoint_back(L->d_cfg, g.d_tasks + c[p], c[p + 1] - c[p], g.Lx, g.H, g.seed, bk, A,
+                                            q == 0 ? L->stream : L->aux[(q - 1) % n_aux]));
+                    ++L->launches;
+                }
             }
             if (bk) {
                 in_th = out_th;
@@ -1819,6 +1978,10 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 sb ^= 1;
             }
             acur = 1 - acur;
+        }
+        for (int i = 0; i < n_aux; ++i) {
+            CKA(cudaEventRecord(L->join_ev[i], L->aux[i]));
+            CKA(cudaStreamWaitEvent(L->stream, L->join_ev[i], 0));
         }
         RCA(sv.close());
     }
