@@ -332,6 +332,28 @@ int xy_debug_set_union_limit(int iters);
 int xy_debug_philox(const uint32_t* counters, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
                     void* cuda_stream);
 
+/* Diagnostics: the plan of the concurrent lattice slices that a captured
+ * chunk of steps (one branch per slice) and the adjoint's reverse sweep run
+ * on their own streams.  Host only: no device call, no GPU needed.
+ *
+ * xy_debug_slice_parts: n_lat[n_groups] = lattices per kernel group;
+ * fixed = branches that are not split (resident groups, the plain
+ * configurations); budget = most branches in all (the stepper uses 9).  Each
+ * group gets min(4, n_lat) slices (at least 1), fewer, the groups with the
+ * most slices first, while fixed + the total exceeds budget.  parts[n_groups]
+ * receives the counts.  XY_EINVAL on a null array, a negative count, fixed < 0
+ * or budget < 1.
+ *
+ * xy_debug_slice_cuts: lattice_of_task[n_tasks] = the lattice of each block
+ * task of a group (grouped by lattice, ascending).  cuts (room for parts + 1
+ * ints) receives the first task of each slice followed by n_tasks, *n_cuts
+ * their number (at most parts + 1).  Interior cuts fall on the first task of
+ * a lattice, each the one nearest n_tasks * p / parts past the previous cut;
+ * where no lattice start is left, fewer slices result.  XY_EINVAL on null
+ * pointers, parts < 1 or tasks out of lattice order. */
+int xy_debug_slice_parts(const int64_t* n_lat, int n_groups, int fixed, int budget, int* parts);
+int xy_debug_slice_cuts(const int32_t* lattice_of_task, int n_tasks, int parts, int* cuts, int* n_cuts);
+
 #ifdef __cplusplus
 }
 #endif

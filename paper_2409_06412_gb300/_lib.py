@@ -65,6 +65,8 @@ SIGNATURES = {
     "xy_debug_noise": (_i32, [_u64, _i32, _i32, _i64, _i32, _i64, _vp, _vp, _vp]),
     "xy_debug_philox": (_i32, [_vp, _u32, _u32, _i64, _vp, _vp]),
     "xy_debug_set_union_limit": (_i32, [_i32]),
+    "xy_debug_slice_parts": (_i32, [_vp, _i32, _i32, _i32, _vp]),
+    "xy_debug_slice_cuts": (_i32, [_vp, _i32, _i32, _vp, _vp]),
 }
 
 _lib = None

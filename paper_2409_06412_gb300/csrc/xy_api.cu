@@ -2334,4 +2334,44 @@ int xy_debug_philox(const uint32_t* counters, uint32_t k0, uint32_t k1, int64_t 
     return XY_OK;
 }
 
+// The slicing plan of the concurrent branches, through the same functions
+// as the stepper and the reverse sweep (host only, no device call).
+struct DbgTask {
+    int32_t cfg, rep;
+};
+struct DbgGroup {
+    int64_t n_lat;
+    std::vector<DbgTask> tasks;
+};
+
+int xy_debug_slice_parts(const int64_t* n_lat, int n_groups, int fixed, int budget, int* parts)
+{
+    if (n_groups < 0 || (n_groups > 0 && (!n_lat || !parts)) || fixed < 0 || budget < 1)
+        return fail(XY_EINVAL, "bad slicing arguments");
+    std::vector<DbgGroup> groups(n_groups);
+    for (int g = 0; g < n_groups; ++g) {
+        if (n_lat[g] < 0) return fail(XY_EINVAL, "negative lattice count");
+        groups[g].n_lat = n_lat[g];
+    }
+    const std::vector<int> p = slice_parts(groups, fixed, budget);
+    for (int g = 0; g < n_groups; ++g) parts[g] = p[g];
+    return XY_OK;
+}
+
+int xy_debug_slice_cuts(const int32_t* lattice_of_task, int n_tasks, int parts, int* cuts, int* n_cuts)
+{
+    if (n_tasks < 0 || (n_tasks > 0 && !lattice_of_task) || parts < 1 || !cuts || !n_cuts)
+        return fail(XY_EINVAL, "bad slicing arguments");
+    std::vector<DbgTask> tk(n_tasks);
+    for (int i = 0; i < n_tasks; ++i) {
+        if (i > 0 && lattice_of_task[i] < lattice_of_task[i - 1])
+            return fail(XY_EINVAL, "tasks must be grouped by lattice in ascending order");
+        tk[i] = DbgTask{lattice_of_task[i], 0};
+    }
+    const std::vector<int> c = cut_tasks(tk, parts);
+    for (size_t i = 0; i < c.size(); ++i) cuts[i] = c[i];
+    *n_cuts = (int)c.size();
+    return XY_OK;
+}
+
 }  // extern "C"

@@ -44,12 +44,10 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name)
 
 
-def test_library_targets_sm103a_only():
-    out = subprocess.run(["cuobjdump", "--list-elf", build.LIB], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    arches = set(re.findall(r"sm_(\d+a?)", out.stdout))
-    assert arches == {"103a"}, arches
+def test_build_targets_sm103a_only():
+    # every translation unit and the link take exactly this one -gencode
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert not any("arch" in f or "gencode" in f for f in build.FLAGS)
 
 
 def test_host_side_argument_checks(lib):
@@ -73,3 +71,69 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "absent.so"))
     finally:
         _lib._lib = saved
+
+
+def _slice_parts(lib, n_lat, fixed, budget):
+    arr = (ctypes.c_int64 * max(1, len(n_lat)))(*n_lat)
+    out = (ctypes.c_int * max(1, len(n_lat)))()
+    assert lib.xy_debug_slice_parts(arr, len(n_lat), fixed, budget, out) == _lib.XY_OK
+    return list(out)[:len(n_lat)]
+
+
+def _slice_cuts(lib, lattice_of_task, parts):
+    arr = (ctypes.c_int32 * max(1, len(lattice_of_task)))(*lattice_of_task)
+    cuts = (ctypes.c_int * (parts + 1))()
+    n = ctypes.c_int()
+    assert lib.xy_debug_slice_cuts(arr, len(lattice_of_task), parts, cuts, ctypes.byref(n)) == _lib.XY_OK
+    return list(cuts)[:n.value]
+
+
+def test_slice_plan_counts(lib):
+    # static-criticality batch: three strip shapes of 512 lattices beside one
+    # resident group, nine branches at most
+    assert _slice_parts(lib, [512, 512, 512], 1, 9) == [2, 3, 3]
+    assert _slice_parts(lib, [64], 0, 9) == [4]
+    assert _slice_parts(lib, [1], 0, 9) == [1]
+    assert _slice_parts(lib, [3, 0], 0, 9) == [3, 1]
+    # more groups than the budget: one branch each, nothing left to take
+    assert _slice_parts(lib, [2] * 12, 0, 9) == [1] * 12
+    # the budget binds: the groups with most slices give one up first
+    assert _slice_parts(lib, [8, 8, 2], 2, 8) == [2, 2, 2]
+    for n_lat, fixed, budget in [([5, 7, 1, 300], 1, 9), ([10] * 3, 0, 12), ([1000], 3, 4)]:
+        p = _slice_parts(lib, n_lat, fixed, budget)
+        assert all(1 <= x <= min(4, max(1, n)) for x, n in zip(p, n_lat))
+        assert fixed + sum(p) <= budget or all(x == 1 for x in p)
+
+
+def test_slice_cuts_fall_on_lattice_starts(lib):
+    # L = 1024 of the static batch: 512 lattices of 16 blocks in three slices
+    tasks = [b // 16 for b in range(8192)]
+    assert _slice_cuts(lib, tasks, 3) == [0, 2736, 5456, 8192]
+    assert _slice_cuts(lib, [0] * 7, 4) == [0, 7]              # one lattice: one slice
+    assert _slice_cuts(lib, [0] * 10 + [1, 2, 3, 4], 2) == [0, 10, 14]
+    assert _slice_cuts(lib, [0, 1] + [2] * 100, 3) == [0, 2, 102]  # no start left for a third
+    assert _slice_cuts(lib, [], 2) == [0, 0]
+    import random
+    rng = random.Random(7)
+    for _ in range(50):
+        sizes = [rng.randint(1, 20) for _ in range(rng.randint(1, 40))]
+        tasks = [i for i, s in enumerate(sizes) for _ in range(s)]
+        parts = rng.randint(1, 4)
+        c = _slice_cuts(lib, tasks, parts)
+        starts = {0} | {i for i in range(1, len(tasks)) if tasks[i] != tasks[i - 1]}
+        assert c[0] == 0 and c[-1] == len(tasks) and 2 <= len(c) <= parts + 1
+        assert all(a < b for a, b in zip(c, c[1:]))
+        assert all(x in starts for x in c[:-1])
+
+
+def test_slice_plan_argument_checks(lib):
+    out = (ctypes.c_int * 2)()
+    assert lib.xy_debug_slice_parts(None, 1, 0, 9, out) == _lib.XY_EINVAL
+    arr = (ctypes.c_int64 * 1)(-1)
+    assert lib.xy_debug_slice_parts(arr, 1, 0, 9, out) == _lib.XY_EINVAL
+    assert lib.xy_debug_slice_parts(arr, 0, 0, 0, out) == _lib.XY_EINVAL
+    tasks = (ctypes.c_int32 * 3)(0, 2, 1)
+    cuts = (ctypes.c_int * 3)()
+    n = ctypes.c_int()
+    assert lib.xy_debug_slice_cuts(tasks, 3, 2, cuts, ctypes.byref(n)) == _lib.XY_EINVAL
+    assert lib.xy_debug_slice_cuts(tasks, 3, 0, cuts, ctypes.byref(n)) == _lib.XY_EINVAL
