@@ -29,6 +29,10 @@
  *  - Calls are asynchronous on the stream given at creation unless stated
  *    otherwise.  Output pointers marked "host or device" are classified with
  *    cudaPointerGetAttributes; a host pointer makes the call synchronous.
+ *    Internally a call may fork work from that stream onto the object's own
+ *    streams (concurrent lattice slices); it joins them back before anything
+ *    later on the creation stream runs, so stream order is as if all of it ran
+ *    there.
  *  - Thread safety: one lattice object must not be used from two threads at
  *    once.  Distinct objects are independent.
  */
