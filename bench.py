@@ -566,6 +566,14 @@ def profile_case(name):
                               n_total=10 ** 9)])
         lat.step(10)
         lat.adjoint(200, checkpoint_every=100, w_E=1.0, w_M=1.0)
+    elif name == "adjoint-short":
+        # the differentiation shape over 20 steps, checkpoint every 10: the
+        # same per-step launches as above in a launch list short enough to
+        # capture whole
+        lat = Lattice([Config(Lx=256, Ly=256, n_replicas=64, seed=1, init_mode=1, knots=((0,), (TC,)),
+                              n_total=10 ** 9)])
+        lat.step(10)
+        lat.adjoint(20, checkpoint_every=10, w_E=1.0, w_M=1.0)
     elif name == "plain64":
         # the plain-method lattice: 64 x 64, one replica, 300 steps
         lat = Lattice([Config(Lx=64, Ly=64, n_replicas=1, seed=1, init_mode=0, knots=((0,), (TC,)),
@@ -595,7 +603,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["static", "static-L512", "dynamic-z", "kibble-zurek"], default="static")
-    ap.add_argument("--profile-case", choices=["adjoint-small", "plain64", "sf", "ccl"], default=None,
+    ap.add_argument("--profile-case", choices=["adjoint-small", "adjoint-short", "plain64", "sf", "ccl"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:
