@@ -139,22 +139,31 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        text = open(self.f.name).read()
         os.unlink(self.f.name)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [x.strip() for x in r]
-            try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
-            except (ValueError, IndexError):
-                continue
-            for i, nm in enumerate(names):
-                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_samples(text)
+
+
+def parse_clock_samples(text):
+    """Summary of `nvidia-smi --query-gpu=<CLOCK_Q> --format=csv,noheader,nounits`
+    rows: median and maximum SM clock and the throttle reasons seen Active in
+    any sample (malformed rows are skipped)."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in text.strip().splitlines():
+        if not line.strip():
+            continue
+        r = [x.strip() for x in line.split(",")]
+        try:
+            sm.append(float(r[1]))
+            mx.append(float(r[2]))
+        except (ValueError, IndexError):
+            continue
+        for i, nm in enumerate(names):
+            if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ------------------------------------------------------------------ helpers

@@ -61,3 +61,36 @@ def test_reference_arm_prints_its_json_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "site-updates/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+
+
+def test_clock_samples_summary(bench):
+    rows = "\n".join([
+        "0, 2070, 2070, 812.4, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1395.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",  # skipped
+        "",
+    ])
+    c = bench.parse_clock_samples(rows)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.parse_clock_samples("0, 1500, 2070, 900, 0x28, Not Active, Active, Active, Not Active")
+    assert hot["reasons"] == ["hw_thermal_slowdown", "sw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    assert bench.parse_clock_samples("") == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_ncu_traffic_only_for_the_profiled_source(bench, tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2409_06412_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "xy_step.cu").write_text("kernel v1\n")
+    (csrc / "xy_device.cuh").write_text("header\n")
+    import hashlib
+    digest = hashlib.sha256(b"kernel v1\nheader\n").hexdigest()[:16]
+    (tmp_path / "profiles" / "ncu_traffic.txt").write_text(
+        f"kernel=strip_step_kernel source={digest} dram_bytes_per_site=15.94 workload=x\n"
+        "kernel=strip_step_kernel source=0000000000000000 dram_bytes_per_site=99.0 workload=y\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("strip_step_kernel") == 15.94
+    assert bench.ncu_traffic("other_kernel") is None
+    (csrc / "xy_step.cu").write_text("kernel v2\n")  # changed since the capture
+    assert bench.ncu_traffic("strip_step_kernel") is None
