@@ -106,8 +106,10 @@ typedef struct {
 int xy_lattice_create(const xy_config_desc* cfg, int n_cfg, float* theta, float* omega,
                       void* cuda_stream, xy_lattice** out);
 
-/* Set the parameters of configuration cfg (must precede the first step).
- * Requires dt > 0, eta >= 0. */
+/* Set the parameters of configuration cfg (must precede the first step): the
+ * couplings and field of the Hamiltonian of Sec. III.A, Eq. (XY-Hamilton-
+ * Field), the damping of the Langevin equations of Sec. III.D and the time
+ * step of the BBK integrator of App. A.1.  Requires dt > 0, eta >= 0. */
 int xy_set_params(xy_lattice* lat, int cfg, const xy_params* params);
 
 /* Temperature schedule of configuration cfg: T(k) piecewise linear through
@@ -140,11 +142,14 @@ int xy_observe(xy_lattice* lat, double* moments, int64_t* step_now);
 int xy_reset_moments(xy_lattice* lat);
 
 /* Full-step angular velocity omega_k of lattices [b_first, b_first+b_count)
- * into out (device, b_count*Lx*Ly floats, same layout as the state). */
+ * into out (device, b_count*Lx*Ly floats, same layout as the state): the
+ * omega(t) of the three-stage BBK scheme of App. A.1 (Eq. BBK-2), which the
+ * stored half-step velocity v_k and the noise of step k determine. */
 int xy_omega_full(xy_lattice* lat, int b_first, int b_count, float* out);
 
-/* Frozen-domain labelling (connected components of the Ising projection
- * spin = (theta >= 0), 4-neighbour adjacency, periodic) of lattices
+/* Frozen-domain labelling: the domains of equal buckling left by a quench
+ * (abstract; Sec. IV.C, Fig. 6), as connected components of the Ising
+ * projection spin = (theta >= 0), 4-neighbour adjacency, periodic, of lattices
  * [b_first, b_first+b_count), which must all have the same Lx, Ly.
  * labels (nullable; host or device): int32[b_count][Ly*Lx], label = smallest
  * site index of the component.  hist (nullable; host or device):
@@ -183,8 +188,11 @@ int xy_label_domains(xy_lattice* lat, int b_first, int b_count, int32_t* labels,
 int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, int32_t* labels, int64_t* hist,
                             int64_t hist_cap, int64_t* n_sizes, void* cuda_stream);
 
-/* Pathwise adjoint (synchronous).  Runs n BBK steps from the current state
- * (which advances by n) with the noise held fixed and returns
+/* Pathwise adjoint (synchronous) of the BBK trajectory of App. A.1 (the
+ * paper has no adjoint; the objective's E_k and M_k are those of xy_step_n,
+ * Eq. (XY-Hamilton-Kinetic) and Eq. (lattice-average)).  Runs n BBK steps
+ * from the current state (which advances by n) with the noise held fixed and
+ * returns
  *   objective = (1 / (B n)) sum_b sum_{k=k0+1}^{k0+n} [w_E E_k + w_M |M_k|]
  * (B = number of lattices, k0 = current step; every configuration must be at
  * the same step with n steps left) and grads[c][0..3] = d objective /
