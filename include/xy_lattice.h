@@ -107,9 +107,10 @@ int xy_lattice_create(const xy_config_desc* cfg, int n_cfg, float* theta, float*
                       void* cuda_stream, xy_lattice** out);
 
 /* Set the parameters of configuration cfg (must precede the first step): the
- * couplings and field of the Hamiltonian of Sec. III.A, Eq. (XY-Hamilton-
- * Field), the damping of the Langevin equations of Sec. III.D and the time
- * step of the BBK integrator of App. A.1.  Requires dt > 0, eta >= 0. */
+ * couplings and field of the Hamiltonian of Sec. III.A,
+ * Eq. (XY-Hamilton-Field), the damping of the Langevin equations of
+ * Sec. III.D and the time step of the BBK integrator of App. A.1.
+ * Requires dt > 0, eta >= 0. */
 int xy_set_params(xy_lattice* lat, int cfg, const xy_params* params);
 
 /* Temperature schedule of configuration cfg: T(k) piecewise linear through
