@@ -80,7 +80,11 @@ __device__ __forceinline__ int find_root_shared(const int* L, int x)
     return x;
 }
 
-__device__ void union_shared(int* L, int a, int b)
+// Link in shared memory, with a bound on the retries: every failed atomicMin
+// means another thread lowered the same label, so the loop ends long before
+// the bound in practice; reaching it sets XY_ETIMEOUT like the global loops
+// (the tile's forest stays valid, links only point at smaller indices).
+__device__ void union_shared(int* L, int a, int b, int* err)
 {
     for (int it = 0; it < 4096 * 4; ++it) {
         a = find_root_shared(L, a);
@@ -95,6 +99,7 @@ __device__ void union_shared(int* L, int a, int b)
         if (old == a) return;
         a = old;
     }
+    atomicExch(err, XY_ETIMEOUT);
 }
 
 }  // namespace
@@ -102,7 +107,8 @@ __device__ void union_shared(int* L, int a, int b)
 // Pass 1: one block per TW x TH tile, one thread per site; union-find on
 // tile-local indices (row-major in the tile, hence ordered like global
 // indices), result written as the global index of the local root.
-__global__ void ccl_local_kernel(const float* theta, int Lx, int Ly, int TW, int TH, int32_t* labels)
+__global__ void ccl_local_kernel(const float* theta, int Lx, int Ly, int TW, int TH, int32_t* labels,
+                                 int* err)
 {
     extern __shared__ int s_lab[];
     const int tiles_x = Lx / TW, tiles_y = Ly / TH;
@@ -131,13 +137,13 @@ __global__ void ccl_local_kernel(const float* theta, int Lx, int Ly, int TW, int
         if (ly + 1 < TH) {  // uniform in the warp
             const bool vert = spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp;
             const bool vertL = __shfl_up_sync(kAll, vert, 1);
-            if (vert && !(horiz && vertL)) union_shared(s_lab, lid, lid + 32);
+            if (vert && !(horiz && vertL)) union_shared(s_lab, lid, lid + 32, err);
         }
     } else {
         s_lab[lid] = lid;
         __syncthreads();
-        if (lx + 1 < TW && spin_of(th[(int64_t)gy * Lx + gx + 1]) == sp) union_shared(s_lab, lid, lid + 1);
-        if (ly + 1 < TH && spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp) union_shared(s_lab, lid, lid + TW);
+        if (lx + 1 < TW && spin_of(th[(int64_t)gy * Lx + gx + 1]) == sp) union_shared(s_lab, lid, lid + 1, err);
+        if (ly + 1 < TH && spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp) union_shared(s_lab, lid, lid + TW, err);
     }
     __syncthreads();
     const int root = find_root_shared(s_lab, lid);
@@ -295,7 +301,7 @@ cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* l
     if ((e = cudaMemsetAsync(count_scratch, 0, sizeof(int32_t) * (N + 1) * n_lat, st)) != cudaSuccess) return e;
     const int tiles = (Lx / TW) * (Ly / TH);
     ccl_local_kernel<<<(unsigned)(tiles * n_lat), TW * TH, TW * TH * sizeof(int), st>>>(theta, Lx, Ly, TW, TH,
-                                                                                        labels);
+                                                                                        labels, err);
     const int64_t total = N * n_lat;
     const unsigned blocks = (unsigned)((total + 255) / 256);
     const int64_t border = (int64_t)n_lat * tiles * (TW + TH);

@@ -31,6 +31,18 @@ int32_t* g_scratch_addr[kMaxDevices] = {};
 
 int fail_static(int code, const char* msg) { return xy::report_error(code, msg); }
 
+// True for memory the current device's kernels can address (device or
+// managed); host and foreign pointers would become illegal accesses on the GPU.
+bool on_device(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a stand-in, so the address is looked up once per
 // device with that device current.
@@ -65,6 +77,8 @@ extern "C" int xy_label_domains_static(const float* theta, int Lx, int Ly, int n
         return fail_static(XY_EINVAL, "xy_label_domains_static: need Lx a positive multiple of 4, Ly >= 1, "
                                       "n_lattices >= 1");
     if (hist && hist_cap <= 0) return fail_static(XY_EINVAL, "xy_label_domains_static: hist_cap must be > 0");
+    if (!on_device(theta) || !on_device(labels) || (hist && !on_device(hist)) || (n_sizes && !on_device(n_sizes)))
+        return fail_static(XY_EINVAL, "xy_label_domains_static: theta, labels, hist and n_sizes must be device memory");
     const int64_t N = (int64_t)Lx * Ly;
     if (n_lattices > XY_STATIC_CCL_MAX_LATTICES || N * n_lattices > XY_STATIC_CCL_MAX_SITES)
         return fail_static(XY_EINVAL, "xy_label_domains_static: more than XY_STATIC_CCL_MAX_SITES sites or "
@@ -76,6 +90,15 @@ extern "C" int xy_label_domains_static(const float* theta, int Lx, int Ly, int n
     int32_t* counts = base + kSizeWords;
     int* err = reinterpret_cast<int*>(base + kSizeWords + kCountWords);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // the call reads its error flag back and synchronises the stream, which a
+    // capturing stream does not allow (and the attempt would end the capture)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_static(XY_EINVAL, "xy_label_domains_static: the stream cannot be queried");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail_static(XY_EINVAL, "xy_label_domains_static: the stream is capturing; the call synchronises it");
     // the array keeps the previous call's contents: clear what must start at zero
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (e == cudaSuccess && hist) e = cudaMemsetAsync(hist, 0, sizeof(int64_t) * 2 * hist_cap * n_lattices, st);

@@ -75,6 +75,39 @@ def test_static_labelling_matches_allocating_entry_point_twice():
             assert torch.equal(r, g)
 
 
+def test_static_labelling_at_the_size_limit():
+    """Exactly XY_STATIC_CCL_MAX_SITES sites in several lattices (8 of 512 x
+    512): the far end of the working array (the last lattices' size counts
+    and the error word after them) is in use, and the result is still
+    bit-identical to the allocating entry point's, on two calls in a row."""
+    n, L = 8, 512
+    assert n * L * L == _lib.XY_STATIC_CCL_MAX_SITES
+    th = np.concatenate([_batch("random", L, L, n // 2, 30), _batch("sparse", L, L, n // 2, 40)])
+    lat, _, _ = make_pair([inputs.config(L, L, n)], [th])
+    ref = _reference(lat, 0, n, 1 << 14)
+    for _ in range(2):
+        got = _static(lat.theta, L, L, n, 1 << 14)
+        torch.cuda.synchronize()
+        for r, g in zip(ref, got):
+            assert torch.equal(r, g)
+
+
+def test_static_labelling_rejects_host_pointers():
+    lib = _lib.load()
+    theta_h = np.zeros(64, dtype=np.float32)
+    labels_d = torch.zeros(64, dtype=torch.int32, device="cuda")
+    theta_d = torch.zeros(64, dtype=torch.float32, device="cuda")
+    labels_h = np.zeros(64, dtype=np.int32)
+    for th, lab in ((theta_h.ctypes.data, labels_d.data_ptr()), (theta_d.data_ptr(), labels_h.ctypes.data)):
+        rc = lib.xy_label_domains_static(ctypes.c_void_p(th), 8, 8, 1, ctypes.c_void_p(lab), None, 0, None, None)
+        assert rc == _lib.XY_EINVAL
+        assert b"device memory" in lib.xy_last_error()
+    hist_h = np.zeros((1, 4, 2), dtype=np.int64)
+    rc = lib.xy_label_domains_static(ctypes.c_void_p(theta_d.data_ptr()), 8, 8, 1, ctypes.c_void_p(labels_d.data_ptr()),
+                                     ctypes.c_void_p(hist_h.ctypes.data), 4, None, None)
+    assert rc == _lib.XY_EINVAL
+
+
 def test_static_labelling_rejects_oversize_calls():
     lib = _lib.load()
     theta = torch.zeros(16, dtype=torch.float32, device="cuda")
