@@ -450,14 +450,21 @@ def run_ours(args):
         tl = time.perf_counter() - t0
         extra["ccl"] = {"value": 64 * 1024 * 1024 / tl, "unit": "labelled sites/s", "lattices": 64, "L": 1024}
 
-        # correlation lengths of the same 64 lattices: structure factors for k < 16 and the Lorentzian fit
+        # correlation lengths of the same 64 lattices: structure factors for k < 16 (timed), then over
+        # the half zone for the fit, whose window follows each direction's length (xi_perp is below a
+        # site here: J_perp = J_par / 100)
         from paper_2409_06412_gb300 import corrlen
         lat.structure_factor(b0, 64, 16)
         t_sf = cuda_time(lambda: lat.structure_factor(b0, 64, 16), stream)
-        s_par, s_perp = lat.structure_factor(b0, 64, 16)
-        xi_par, xi_perp = corrlen.correlation_lengths(s_par, s_perp, 1024, 1024, 1, 8)
+        K_fit = 512
+        t_sf_fit = cuda_time(lambda: lat.structure_factor(b0, 64, K_fit), stream)
+        s_par, s_perp = lat.structure_factor(b0, 64, K_fit)
+        _, xi_par, w_par = corrlen.fit_lorentzian(s_par.cpu().numpy().mean(axis=0), 1024, return_window=True)
+        _, xi_perp, w_perp = corrlen.fit_lorentzian(s_perp.cpu().numpy().mean(axis=0), 1024, return_window=True)
         extra["structure_factor"] = {"value": 64 * 1024 * 1024 / t_sf, "unit": "sites/s", "lattices": 64, "L": 1024,
-                                     "K": 16, "xi_par": xi_par, "xi_perp": xi_perp}
+                                     "K": 16, "xi_par": xi_par, "xi_perp": xi_perp, "K_fit": K_fit,
+                                     "fit_windows": [list(w_par), list(w_perp)], "fit_form": "lattice",
+                                     "s_half_zone": t_sf_fit}
 
         # plain method, 64 x 64 single lattice, 1e4 steps: resident kernel vs plain launches
         c1 = Lattice([Config(Lx=64, Ly=64, n_replicas=1, seed=1, init_mode=0, knots=((0,), (TC,)),

@@ -17,7 +17,11 @@ s[j, i] with j the perpendicular index (N_perp rows) and i the parallel index
   Eq. Lorentzian-Peak:   S_delta(k) ~ 2 xi / (1 + 4 pi^2 xi^2 k^2), k the
                          wavenumber in cycles per site (index / N_delta);
                          fitted here as a / (1 + (2 pi xi k / N_delta)^2)
-                         over a window of small k, k = 0 dropped below T_c.
+                         over a window of small k, k = 0 dropped below T_c
+                         ("continuum"), or with (2 pi k / N)^2 replaced by
+                         the lattice Laplacian's 4 sin^2(pi k / N)
+                         ("lattice"), the exact transform of exponentially
+                         decaying correlations on a periodic chain.
 
 Every step is the plain definition; numpy's FFT serves as the 2-D transform.
 """
@@ -83,15 +87,30 @@ def ft_of_correlation(C: np.ndarray) -> np.ndarray:
     return np.array([np.sum(C * np.cos(2 * np.pi * k * r / N)) for k in range(N)])
 
 
-def lorentzian(k: np.ndarray, a: float, xi: float, N: int) -> np.ndarray:
-    return a / (1.0 + (2.0 * np.pi * xi * np.asarray(k, dtype=np.float64) / N) ** 2)
+def lorentzian(k: np.ndarray, a: float, xi: float, N: int, form: str = "continuum") -> np.ndarray:
+    k = np.asarray(k, dtype=np.float64)
+    if form == "continuum":
+        q2 = (2.0 * np.pi * k / N) ** 2
+    elif form == "lattice":
+        q2 = 4.0 * np.sin(np.pi * k / N) ** 2
+    else:
+        raise ValueError(form)
+    return a / (1.0 + xi * xi * q2)
 
 
-def fit_lorentzian(S: np.ndarray, N: int, k_lo: int, k_hi: int, xi0: float = 2.0):
-    """Least-squares fit of S[k_lo..k_hi] to a / (1 + (2 pi xi k / N)^2); returns (a, xi)."""
+def exponential_chain_spectrum(rho: float, N: int) -> np.ndarray:
+    """S(k), k = 0..N-1, of unit-variance correlations C(r) = rho^|r| on an
+    infinite chain sampled at N-periodic wavenumbers: the geometric series
+    sum_r rho^|r| e^{-2 pi i k r / N} = (1 - rho^2) / (1 - 2 rho cos(2 pi k / N) + rho^2)."""
+    q = 2.0 * np.pi * np.arange(N) / N
+    return (1.0 - rho * rho) / (1.0 - 2.0 * rho * np.cos(q) + rho * rho)
+
+
+def fit_lorentzian(S: np.ndarray, N: int, k_lo: int, k_hi: int, xi0: float = 2.0, form: str = "continuum"):
+    """Least-squares fit of S[k_lo..k_hi] to the Lorentzian of ``form``; returns (a, xi)."""
     k = np.arange(k_lo, k_hi + 1, dtype=np.float64)
     y = np.asarray(S, dtype=np.float64)[k_lo:k_hi + 1]
-    a0 = float(y[0] * (1.0 + (2 * np.pi * xi0 * k[0] / N) ** 2))
-    res = least_squares(lambda p: lorentzian(k, p[0], p[1], N) - y, x0=[a0, xi0],
+    a0 = float(y[0] / lorentzian(k[:1], 1.0, xi0, N, form)[0])
+    res = least_squares(lambda p: lorentzian(k, p[0], p[1], N, form) - y, x0=[a0, xi0],
                         bounds=([0.0, 1e-6], [np.inf, 1e6]), xtol=1e-14, ftol=1e-14, gtol=1e-14)
     return float(res.x[0]), float(res.x[1])

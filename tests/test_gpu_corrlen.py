@@ -89,10 +89,29 @@ def test_correlation_length_of_correlated_rows():
     o_par, o_perp = ocl.structure_factor(th.astype(np.float64))
     check(S_par, o_par[:, :16], 512)
     xi_par, xi_perp = corrlen.correlation_lengths(S_par, S_perp, 512, 128, 1, 12)
-    _, xi_o = ocl.fit_lorentzian(o_par.mean(axis=0), 512, 1, 12)
+    _, xi_o = ocl.fit_lorentzian(o_par.mean(axis=0), 512, 1, 12, form="lattice")
     assert abs(xi_par / xi_o - 1) < 1e-3
     assert abs(xi_par / (np.sqrt(rho) / (1 - rho)) - 1) < 0.10
-    assert xi_perp < 1.0
+    assert np.isnan(xi_perp) or xi_perp < 1.0  # uncorrelated columns: no decay, or a length below a site
+
+
+def test_correlation_length_below_one_site():
+    """Periodic AR(1) columns with rho = 0.3 (xi_perp = sqrt(rho)/(1 - rho) =
+    0.78): S_perp over the whole half zone from the GPU, the window chosen
+    from the data; the fit agrees with the oracle's fit of the oracle's
+    S_perp on the same window and finds the generating length."""
+    rho, eps, L = 0.3, 0.05, 256
+    th = np.stack([eps * ar1_field(L, L, rho, seed=200 + b, axis=0) for b in range(8)]).astype(np.float32)
+    lat = lattice_from([(L, L, th)])
+    K = L // 2
+    S_par, S_perp = lat.structure_factor(0, 8, K, 1.0)
+    o_par, o_perp = ocl.structure_factor(th.astype(np.float64))
+    check(S_perp, o_perp[:, :K], L)
+    _, xi, (lo, hi) = corrlen.fit_lorentzian(S_perp.cpu().numpy().mean(axis=0), L, return_window=True)
+    _, xi_o = ocl.fit_lorentzian(o_perp.mean(axis=0)[:K], L, lo, hi, form="lattice")
+    assert abs(xi / xi_o - 1) < 1e-3, (xi, xi_o, lo, hi)
+    assert abs(xi / (np.sqrt(rho) / (1 - rho)) - 1) < 0.10, xi
+    assert np.isnan(corrlen.correlation_lengths(S_par, S_perp, L, L)[0])  # rows uncorrelated: no length
 
 
 def test_full_size_lattice_after_dynamics():

@@ -90,3 +90,32 @@ def test_fit_recovers_exponential_correlation_length():
     assert abs(xi / (math.sqrt(rho) / (1 - rho)) - 1) < 0.10
     # no correlation across the rows: flat S_perp away from k = 0
     assert abs(S_perp.mean(axis=0)[1:].mean() / eps ** 2 - 1) < 0.05
+
+
+@pytest.mark.parametrize("rho,N", [(0.2, 64), (0.5, 128), (0.9, 256)])
+def test_exponential_chain_spectrum_is_the_transform_of_rho_to_the_r(rho, N):
+    # brute force: the N-periodic correlation sum_m rho^|r + m N| (images out
+    # to where rho^|r| underflows), transformed by the FFT
+    r = np.arange(N)
+    C = np.zeros(N)
+    for m in range(-60, 61):
+        C += rho ** np.abs(r + m * N)
+    S_fft = np.fft.fft(C).real
+    np.testing.assert_allclose(corrlen.exponential_chain_spectrum(rho, N), S_fft, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("rho,N", [(0.2, 64), (0.5, 128), (0.9, 256), (0.3, 1024)])
+def test_lattice_lorentzian_recovers_the_exponential_length(rho, N):
+    """On a periodic chain with C(r) = rho^|r| the lattice form of the
+    Lorentzian is exact over the whole zone: xi = sqrt(rho) / (1 - rho)
+    (C(r) = exp(-r / l), l = -1 / ln rho; xi -> l for l >> 1) and
+    a = (1 + rho) / (1 - rho), from any window."""
+    S = corrlen.exponential_chain_spectrum(rho, N)
+    xi = math.sqrt(rho) / (1 - rho)
+    for lo, hi in ((1, N // 2), (1, 5), (N // 8, N // 4)):
+        a_f, xi_f = corrlen.fit_lorentzian(S, N, lo, hi, form="lattice")
+        assert abs(xi_f / xi - 1) < 1e-8 and abs(a_f / ((1 + rho) / (1 - rho)) - 1) < 1e-8
+    # the continuum form of Eq. Lorentzian-Peak agrees near k = 0 when xi >> 1
+    if xi > 5:
+        _, xi_c = corrlen.fit_lorentzian(S, N, 1, 3, form="continuum")
+        assert abs(xi_c / xi - 1) < 1e-3
