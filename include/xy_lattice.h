@@ -182,8 +182,11 @@ int xy_label_domains(xy_lattice* lat, int b_first, int b_count, int32_t* labels,
  * contents (each call clears what must start at zero), so calls whose work
  * overlaps on the GPU (other streams, other threads) race: issue them one
  * after another.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  No call allocates memory (no cudaMalloc or cudaFree). */
+ * address (cudaGetSymbolAddress).  Every call reads its error flag back and
+ * synchronises cuda_stream, so no call may be issued on a capturing stream:
+ * such a call returns XY_EINVAL without touching the stream.  theta, labels
+ * and the non-null hist and n_sizes must be device (or managed) memory, else
+ * XY_EINVAL.  No call allocates memory (no cudaMalloc or cudaFree). */
 #define XY_STATIC_CCL_MAX_SITES 2097152
 #define XY_STATIC_CCL_MAX_LATTICES 65536
 int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, int32_t* labels, int64_t* hist,
@@ -220,8 +223,12 @@ int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w
  *     at a few sites by the segment's start.  Needs the shapes of the band
  *     kernels (Lx a multiple of 128 up to 2048, or Lx <= 128 with Lx / 4
  *     dividing 32; Ly >= 2): XY_EINVAL at the adjoint call otherwise.
- *   XY_ADJOINT_AUTO (default): backward where every shape allows it, else
- *     recompute. */
+ *     Undoing the damping amplifies the rounding of the recovered states by
+ *     about exp(eta dt K) over a segment of K steps: measured against the
+ *     recompute at T_c with K = 100, the eta gradient agrees to 1e-5
+ *     relative at eta dt K = 5 and only to 2e-3 at eta dt K = 10.
+ *   XY_ADJOINT_AUTO (default): backward where every shape allows it and
+ *     eta dt min(K, n) <= 5 for every configuration, else recompute. */
 #define XY_ADJOINT_AUTO 0
 #define XY_ADJOINT_RECOMPUTE 1
 #define XY_ADJOINT_BACKWARD 2
@@ -339,6 +346,14 @@ int xy_debug_noise(uint64_t seed, int cfg, int replica, int64_t k, int tag, int6
  * returns XY_ETIMEOUT with incomplete labels (indices stay in range, nothing
  * faults).  For testing the timeout path; the paper has no counterpart. */
 int xy_debug_set_union_limit(int iters);
+
+/* Diagnostics: the Box-Muller map of the steppers (App. A.1 noise) applied to
+ * given Philox words: words (device uint32[n_quads][4], 16-byte aligned) ->
+ * out (device float[4*n_quads], 16-byte aligned) = c*g0..c*g3 exactly as a
+ * stepping kernel forms the scaled noise of the quad's four sites from its
+ * Philox output.  Lets tests sweep every uniform the generator can produce.
+ * Asynchronous on cuda_stream. */
+int xy_debug_gauss4(const uint32_t* words, int64_t n_quads, float c, float* out, void* cuda_stream);
 
 /* Diagnostics: raw Philox4x32-10 of n arbitrary counters (device
  * uint32[n][4]) with key (k0, k1) into out (device uint32[n][4]). */

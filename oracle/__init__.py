@@ -74,6 +74,8 @@ def _declare(L):
     L.xyo_ccl.restype = i64
     L.xyo_adjoint_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i64, i64, vp, vp,
                                       d, d, P(d), vp, vp, vp]
+    L.xyo_theta_sensitivity.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i64, i64, vp, vp,
+                                        i32, vp, vp, vp, vp, vp, vp, vp, vp]
 
 
 def _ptr(a: np.ndarray):
@@ -203,6 +205,40 @@ def adjoint_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0
                               _ptr(th0), _ptr(om0), wE, wM, ctypes.byref(obj), _ptr(grad),
                               _ptr(th1), _ptr(om1))
     return obj.value, grad, th1, om1
+
+
+def theta_sensitivity(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, targets, wt=None, wv=None,
+                      trajectory=False, fields=False):
+    """First-order sensitivity of the final angles theta_t(k0 + n), t in
+    ``targets``, to perturbations along the FP64 trajectory from the full-step
+    state (theta0, omega0) (see xyo_theta_sensitivity): an (n_targets, 2)
+    array of [sum |l| w, sqrt(sum l^2 w^2)] over the angles (weights wt, shape
+    (n, N): steps 1..n) and the half-step velocities (weights wv, shape
+    (n, N): steps 0..n-1); weights default to 1.  With ``trajectory``, also
+    the (n + 1, N) arrays theta_j, omega_j; with ``fields``, also the (n, N)
+    fields lt, lv of the first target."""
+    prm = param_vector(params)
+    nk, ks, Ts = _knots(knots)
+    th0 = np.ascontiguousarray(theta0, dtype=np.float64).ravel()
+    om0 = np.ascontiguousarray(omega0, dtype=np.float64).ravel()
+    tg = np.ascontiguousarray(np.asarray(targets, dtype=np.int64).ravel())
+    N = Lx * Ly
+    out = np.zeros((tg.size, 2), dtype=np.float64)
+    w_t = None if wt is None else np.ascontiguousarray(wt, dtype=np.float64).reshape(n, N)
+    w_v = None if wv is None else np.ascontiguousarray(wv, dtype=np.float64).reshape(n, N)
+    tth = np.zeros((n + 1, N)) if trajectory else None
+    tom = np.zeros((n + 1, N)) if trajectory else None
+    lt = np.zeros((n, N)) if fields else None
+    lv = np.zeros((n, N)) if fields else None
+    p = lambda a: None if a is None else _ptr(a)
+    lib().xyo_theta_sensitivity(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), k0, n, _ptr(th0), _ptr(om0),
+                                int(tg.size), _ptr(tg), p(w_t), p(w_v), _ptr(out), p(tth), p(tom), p(lt), p(lv))
+    res = (out,)
+    if trajectory:
+        res += (tth, tom)
+    if fields:
+        res += (lt, lv)
+    return res if len(res) > 1 else out
 
 
 # ---------------------------------------------------------------- batches

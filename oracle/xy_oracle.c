@@ -574,6 +574,117 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
 }
 
 /* ------------------------------------------------------------------------- */
+/* First-order sensitivity of one final angle to perturbations along the path */
+/* ------------------------------------------------------------------------- */
+
+/* Forward n BBK steps of one lattice from the full-step state (theta0, omega0)
+ * at step k0 (the three stages of App. A.1, as in xyo_run_lattice), then, for
+ * each target site t, one reverse sweep of the linearised step (the same
+ * Jacobian as xyo_adjoint_lattice, with the final angle theta_t(k0 + n) as the
+ * objective and the parameters fixed).  It yields
+ *   lt_s(j) = d theta_t(k0+n) / d theta_s(k0+j),  j = 1..n  (a perturbation of
+ *             the angle after the drift of step j-1, including its effect on
+ *             the force F_j and everything after it),
+ *   lv_s(j) = d theta_t(k0+n) / d wh_s(j),        j = 0..n-1 (a perturbation of
+ *             the half-step velocity of Eq. (BBK-1) of step j, before its
+ *             drift).
+ * With per-site weights wt[j-1][s] (j = 1..n) on the angles and wv[j][s]
+ * (j = 0..n-1) on the half-step velocities (nullable: all 1),
+ *   out[2 t]     = sum_j sum_s |lt_s(j)| wt[j-1][s] + sum_j sum_s |lv_s(j)| wv[j][s]
+ *   out[2 t + 1] = sqrt(sum_j sum_s lt_s(j)^2 wt[j-1][s]^2 + sum_j sum_s lv_s(j)^2 wv[j][s]^2)
+ * so that local perturbations bounded by the weights move theta_t(k0+n) by at
+ * most out[2 t] to first order, and independent ones spread it by a root mean
+ * square at most out[2 t + 1] / sqrt(3) when each is uniform within its bound.
+ * The wrap has derivative 1 (its kink is ignored, as in the adjoint).
+ * traj_theta, traj_omega (nullable): [n + 1][N] receive the trajectory theta_j,
+ * omega_j; lt_out, lv_out (nullable, used on tiny lattices by the tests): the
+ * fields of the first target, [n][N] each, lt_out[j - 1] and lv_out[j]. */
+void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, const double* prm,
+                           int n_knots, const int64_t* knot_step, const double* knot_T,
+                           int64_t k0, int64_t n, const double* theta0, const double* omega0,
+                           int n_targets, const int64_t* targets, const double* wt, const double* wv,
+                           double* out, double* traj_theta, double* traj_omega,
+                           double* lt_out, double* lv_out)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    double eta = prm[P_ETA], dt = prm[P_DT];
+    double a = 0.5 * eta * dt, b = 1.0 / (1.0 + a);
+    double* th = (double*)malloc(sizeof(double) * N * (n + 1));
+    double* om = (double*)malloc(sizeof(double) * N * (n + 1));
+    double* F = (double*)malloc(sizeof(double) * N);
+    double* F1 = (double*)malloc(sizeof(double) * N);
+    double* z0 = (double*)malloc(sizeof(double) * N);
+    double* z1 = (double*)malloc(sizeof(double) * N);
+    double* wh = (double*)malloc(sizeof(double) * N);
+
+    memcpy(th, theta0, sizeof(double) * N);
+    memcpy(om, omega0, sizeof(double) * N);
+    xyo_force(Lx, Ly, prm, th, F);
+    gauss_field(seed, cfg, rep, N, k0, z0);
+    for (int64_t j = 0; j < n; ++j) {
+        double *t0 = th + N * j, *w0 = om + N * j, *t1 = th + N * (j + 1), *w1 = om + N * (j + 1);
+        double amp0 = half_kick_amp(eta, xyo_temperature(k0 + j, n_knots, knot_step, knot_T), dt);
+        double amp1 = half_kick_amp(eta, xyo_temperature(k0 + j + 1, n_knots, knot_step, knot_T), dt);
+        gauss_field(seed, cfg, rep, N, k0 + j + 1, z1);
+        for (int64_t i = 0; i < N; ++i) wh[i] = (1.0 - a) * w0[i] + 0.5 * dt * F[i] + amp0 * z0[i];
+        for (int64_t i = 0; i < N; ++i) t1[i] = xyo_wrap(t0[i] + wh[i] * dt);
+        xyo_force(Lx, Ly, prm, t1, F1);
+        for (int64_t i = 0; i < N; ++i) w1[i] = (wh[i] + 0.5 * dt * F1[i] + amp1 * z1[i]) / (1.0 + a);
+        double* tmp = F; F = F1; F1 = tmp;
+        tmp = z0; z0 = z1; z1 = tmp;
+    }
+    if (traj_theta) memcpy(traj_theta, th, sizeof(double) * N * (n + 1));
+    if (traj_omega) memcpy(traj_omega, om, sizeof(double) * N * (n + 1));
+
+    double* tb = (double*)malloc(sizeof(double) * N);
+    double* wb = (double*)malloc(sizeof(double) * N);
+    double* Fb = (double*)malloc(sizeof(double) * N);
+    double* hb = (double*)malloc(sizeof(double) * N);
+    for (int t = 0; t < n_targets; ++t) {
+        double s1 = 0.0, s2 = 0.0;
+        memset(tb, 0, sizeof(double) * N);
+        memset(wb, 0, sizeof(double) * N);
+        memset(Fb, 0, sizeof(double) * N);
+        tb[targets[t]] = 1.0;
+        for (int64_t j = n - 1; j >= 0; --j) {
+            double* t1 = th + N * (j + 1);
+            /* omega_{j+1} = b (wh_j + dt/2 F_{j+1} + amp n): its adjoint wb passes
+             * to wh_j and to F_{j+1} */
+            for (int64_t i = 0; i < N; ++i) {
+                hb[i] = wb[i] * b;
+                Fb[i] += wb[i] * b * 0.5 * dt;
+            }
+            /* F_{j+1} = F(theta_{j+1}): tb is now the whole adjoint of theta_{j+1} */
+            force_jacobian_T(Lx, Ly, prm, t1, Fb, tb);
+            for (int64_t i = 0; i < N; ++i) {
+                double w = wt ? wt[N * j + i] : 1.0;
+                s1 += fabs(tb[i]) * w;
+                s2 += tb[i] * tb[i] * w * w;
+            }
+            if (t == 0 && lt_out) memcpy(lt_out + N * j, tb, sizeof(double) * N);
+            /* theta_{j+1} = wrap(theta_j + dt wh_j): hb is now the whole adjoint of wh_j */
+            for (int64_t i = 0; i < N; ++i) hb[i] += tb[i] * dt;
+            for (int64_t i = 0; i < N; ++i) {
+                double w = wv ? wv[N * j + i] : 1.0;
+                s1 += fabs(hb[i]) * w;
+                s2 += hb[i] * hb[i] * w * w;
+            }
+            if (t == 0 && lv_out) memcpy(lv_out + N * j, hb, sizeof(double) * N);
+            /* wh_j = (1 - a) omega_j + dt/2 F_j + amp n_j; tb carries on as the
+             * adjoint of theta_j (the drift has derivative 1) */
+            for (int64_t i = 0; i < N; ++i) {
+                Fb[i] = hb[i] * 0.5 * dt;   /* F_j enters wh_j with dt/2 */
+                wb[i] = hb[i] * (1.0 - a);  /* omega_j enters wh_j with 1 - a */
+            }
+        }
+        out[2 * t] = s1;
+        out[2 * t + 1] = sqrt(s2);
+    }
+    free(th); free(om); free(F); free(F1); free(z0); free(z1); free(wh);
+    free(tb); free(wb); free(Fb); free(hb);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Batch helpers for the tests (loops over the functions above)               */
 /* ------------------------------------------------------------------------- */
 

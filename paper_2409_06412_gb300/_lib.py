@@ -64,6 +64,7 @@ SIGNATURES = {
     "xy_last_error": (_c.c_char_p, []),
     "xy_debug_noise": (_i32, [_u64, _i32, _i32, _i64, _i32, _i64, _vp, _vp, _vp]),
     "xy_debug_philox": (_i32, [_vp, _u32, _u32, _i64, _vp, _vp]),
+    "xy_debug_gauss4": (_i32, [_vp, _i64, ctypes.c_float, _vp, _vp]),
     "xy_debug_set_union_limit": (_i32, [_i32]),
     "xy_debug_slice_parts": (_i32, [_vp, _i32, _i32, _i32, _vp]),
     "xy_debug_slice_cuts": (_i32, [_vp, _i32, _i32, _vp, _vp]),

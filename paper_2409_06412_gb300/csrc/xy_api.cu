@@ -276,6 +276,10 @@ void fill_params(DevCfg& d, const xy_params& p)
     d.dt_d = p.dt;
     d.stag = p.staggered_M ? 1 : 0;
     d.amp_pref = (float)(0.5 * std::sqrt(2.0 * p.eta * p.dt));
+    // a lower bound of a site's potential energy: sums of E_k run over the
+    // site energies minus it, which at and below T_c are ~10x smaller than
+    // the energies themselves, and so are their FP32 roundings
+    d.e_ref = (float)(-(std::fabs(p.J_par) + std::fabs(p.J_perp) + std::fabs(p.h)));
 }
 
 void fill_schedule_f32(DevCfg& d)
@@ -433,6 +437,10 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
 // `budget`; cuts fall at the task nearest an even share of the group's tasks
 // that starts a lattice.
 constexpr int kMaxSlices = 4;
+
+// Largest eta dt K (segment of K steps) at which XY_ADJOINT_AUTO integrates a
+// segment's states backward (see xy_adjoint_step_n).
+constexpr double kAutoBackMaxDamping = 5.0;
 
 template <class Task>
 std::vector<int> lattice_starts(const std::vector<Task>& tk)
@@ -1684,7 +1692,17 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     if (L->adj_mode == XY_ADJOINT_BACKWARD && (!adj_plain.empty() || adj_groups.empty()))
         return fail(XY_EINVAL, "backward integration needs shapes of the band kernels (Lx a multiple of 128 "
                                "up to 2048, or Lx <= 128 with Lx / 4 dividing 32; Ly >= 2)");
-    const bool back = L->adj_mode != XY_ADJOINT_RECOMPUTE && adj_plain.empty() && !adj_groups.empty();
+    // Undoing the damping of App. A.1 multiplies the rounding of the recovered
+    // states by (1 + eta dt / 2) / (1 - eta dt / 2) per step, about
+    // exp(eta dt K) over a segment of K steps.  Measured against the stored
+    // recompute (64 x 64 and 256 x 64 at T_c, K = 100): the eta gradient
+    // agrees to 1e-5 relative at eta dt K = 5 and only to 2e-3 at 10, so the
+    // automatic choice integrates backward only up to eta dt K = 5.
+    double damp = 0.0;
+    for (int c = 0; c < L->n_cfg; ++c)
+        damp = std::max(damp, L->h_dev[c].eta_d * L->h_dev[c].dt_d * (double)std::min<int64_t>(K, n));
+    const bool back = L->adj_mode != XY_ADJOINT_RECOMPUTE && adj_plain.empty() && !adj_groups.empty() &&
+                      (L->adj_mode == XY_ADJOINT_BACKWARD || damp <= kAutoBackMaxDamping);
     float *ck = nullptr, *seg = nullptr, *adjb = nullptr, *Fb = nullptr, *sbuf = nullptr;
     double2* arec = nullptr;
     double *gacc = nullptr, *mpart = nullptr;
@@ -2324,6 +2342,14 @@ int xy_debug_noise(uint64_t seed, int cfg, int replica, int64_t k, int tag, int6
     if (n_quads < 0 || cfg < 0 || cfg > 65535 || replica < 0 || replica > 65535 || tag < 0 || tag > 255)
         return fail(XY_EINVAL, "bad noise coordinates");
     CK(launch_debug_noise(seed, cfg, replica, k, tag, n_quads, words, gauss, (cudaStream_t)stream));
+    return XY_OK;
+}
+
+int xy_debug_gauss4(const uint32_t* words, int64_t n_quads, float c, float* out, void* stream)
+{
+    if (n_quads < 0 || (n_quads > 0 && (!words || !out))) return fail(XY_EINVAL, "bad arguments");
+    if ((((uintptr_t)words | (uintptr_t)out) & 15) != 0) return fail(XY_EINVAL, "words and out must be 16-byte aligned");
+    CK(launch_debug_gauss4(words, n_quads, c, out, (cudaStream_t)stream));
     return XY_OK;
 }
 

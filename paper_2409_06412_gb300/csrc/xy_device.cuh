@@ -211,19 +211,27 @@ __device__ __forceinline__ SiteOut site_update(const StepConst& K, float theta, 
     return o;
 }
 
-// Energy of one site with its forward bonds (x+1, y+1), per Eq. (XY-Hamilton-Kinetic):
-//   omega^2 / 2 - J_par cos q(t - t_{x+1}) - J_perp cos q(t - t_{y+1}) + h cos(p t)
-// with cos q(a - b) = c_a c_b + s_a s_b.
+// Energy of one site with its forward bonds (x+1, y+1), per Eq. (XY-Hamilton-Kinetic),
+// relative to the reference e_ref = -(|J_par| + |J_perp| + |h|) <= the potential part:
+//   omega^2 / 2 - J_par cos q(t - t_{x+1}) - J_perp cos q(t - t_{y+1}) + h cos(p t) - e_ref
+// with cos q(a - b) = c_a c_b + s_a s_b, bx, by those bond cosines.  The
+// potential terms are added to the small h cos(p t) - e_ref first, so every
+// rounding is relative to the (small) result; the caller adds N e_ref back in FP64.
+__device__ __forceinline__ float site_energy_rel(float omega, float bx, float by, float cosp, float Jx, float Jy,
+                                                 float h, float e_ref)
+{
+    float e = fmaf(h, cosp, -e_ref);
+    e = fmaf(-Jx, bx, e);
+    e = fmaf(-Jy, by, e);
+    return fmaf(__fmul_rn(0.5f, omega), omega, e);
+}
+
 __device__ __forceinline__ float site_energy(const DevCfg& cf, float omega, float s, float c, float sR,
                                              float cR, float sD, float cD, float cosp)
 {
     const float bx = fmaf(c, cR, __fmul_rn(s, sR));
     const float by = fmaf(c, cD, __fmul_rn(s, sD));
-    float e = __fmul_rn(0.5f, __fmul_rn(omega, omega));
-    e = fmaf(-cf.Jx, bx, e);
-    e = fmaf(-cf.Jy, by, e);
-    e = fmaf(cf.h, cosp, e);
-    return e;
+    return site_energy_rel(omega, bx, by, cosp, cf.Jx, cf.Jy, cf.h, cf.e_ref);
 }
 
 // Asynchronous global -> shared copies (cp.async), issued by one lane for its

@@ -28,7 +28,7 @@ struct DevCfg {
     float knot_Tf[XY_MAX_KNOTS];
     float slope_f[XY_MAX_KNOTS];
     float amp_pref;     // (1/2) sqrt(2 eta dt): noise amplitude c_k = amp_pref sqrt(T_k)
-    float pad1;
+    float e_ref;        // -(|J_par| + |J_perp| + |h|): site energies are summed relative to it
     // nonlinear quench: T(k) = pw_Tc (1 + eps), eps = -sign(t) (|t| / tau_Q)^gamma, t = k - pw_kc,
     // held within [pw_ef, pw_ei]
     int64_t pw_kc;
@@ -131,6 +131,7 @@ size_t resident_smem_bytes(int Lx, int Ly, int threads, int csize);
 int strip_units_per_lattice(int Lx, int Ly, int H);
 cudaError_t launch_debug_noise(uint64_t seed, int cfg, int rep, int64_t k, int tag, int64_t n_quads,
                                uint32_t* words, float* gauss, cudaStream_t st);
+cudaError_t launch_debug_gauss4(const uint32_t* words, int64_t n_quads, float c, float* out, cudaStream_t st);
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out,
                                 cudaStream_t st);
 

@@ -105,7 +105,7 @@ __device__ __forceinline__ float warp_sumf(float v)
 // sums all partials of the lattice in a fixed order and writes the record.
 // Must be called by a whole warp (lane 0 holds the partial).
 __device__ void commit_partial(Partials pa, int64_t b, int unit, int n_units, double pm, double pe,
-                               double2* rec_slot, int64_t N)
+                               double2* rec_slot, int64_t N, double e_ref)
 {
     const int lane = threadIdx.x & 31;
     int last = 0;
@@ -127,7 +127,7 @@ __device__ void commit_partial(Partials pa, int64_t b, int unit, int n_units, do
     sm = warp_sum(sm);
     se = warp_sum(se);
     if (lane == 0) {
-        *rec_slot = make_double2(sm / (double)N, se / (double)N);
+        *rec_slot = make_double2(sm / (double)N, se / (double)N + e_ref);
         pa.count[b] = 0u;
     }
 }
@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
             }
         const int64_t b = cf.b_first + rep;
         const int64_t r = (k - cf.rec_first) / ca.record_every;
-        commit_partial(pa, b, unit, bpl, bm, be, ca.rec_dev + b * ca.rec_stride + r, cf.N);
+        commit_partial(pa, b, unit, bpl, bm, be, ca.rec_dev + b * ca.rec_stride + r, cf.N,
+                       ca.m_only ? 0.0 : (double)cf.e_ref);
     }
 }
 
@@ -385,7 +386,7 @@ struct StripCtx {
     uint32_t cfgrep;
     int64_t k;
     StepConst K;
-    float Jx, Jy, hF;  // energy constants in registers (stores may alias the descriptor)
+    float Jx, Jy, hF, eref;  // energy constants in registers (stores may alias the descriptor)
     bool stag;
     float pm, pe;
 };
@@ -483,11 +484,8 @@ __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const 
             if (REC == 2) {
                 const float bx = fmaf(C.c[s], cr, __fmul_rn(C.s[s], sr));
                 const float by = fmaf(C.c[s], N.c[s], __fmul_rn(C.s[s], N.s[s]));
-                float e = __fmul_rn(0.5f, __fmul_rn(so.omega, so.omega));
-                e = fmaf(-X.Jx, bx, e);
-                e = fmaf(-X.Jy, by, e);
-                e = fmaf(X.hF, cosp_of(X.K.p, th), e);
-                X.pe = __fadd_rn(X.pe, e);
+                X.pe = __fadd_rn(X.pe, site_energy_rel(so.omega, bx, by, cosp_of(X.K.p, th), X.Jx, X.Jy, X.hF,
+                                                       X.eref));
             }
         }
         if (REC) {
@@ -561,6 +559,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
         X.Jx = cf.Jx;
         X.Jy = cf.Jy;
         X.hF = cf.h;
+        X.eref = cf.e_ref;
         X.stag = cf.stag != 0;
         if (live) strip_rows<REC>(X, cf, keys, ybeg, H, s_stage[warp]);
         // one partial per block: warp sums, then the block's warps in order
@@ -584,7 +583,8 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
             const int64_t b = c2.b_first + t2.rep;
             const int64_t r = (k2 - c2.rec_first) / a2.record_every;
             commit_partial(pa, b, t2.unit0 >> 3, (t2.n_units + 7) >> 3, bm, be, a2.rec_dev + b * a2.rec_stride + r,
-                           c2.N);
+                           c2.N,
+                           REC == 2 ? (double)c2.e_ref : 0.0);
         }
     } else if (live) {
         strip_rows<0>(X, cf, keys, ybeg, H, s_stage[warp]);
@@ -849,7 +849,8 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                     }
                     const int64_t b = cf.b_first + task.rep;
                     const int64_t ri = (k - cf.rec_first) / ca.record_every;
-                    ca.rec_dev[b * ca.rec_stride + ri] = make_double2(bm / (double)N, be / (double)N);
+                    ca.rec_dev[b * ca.rec_stride + ri] =
+                        make_double2(bm / (double)N, ca.m_only ? 0.0 : be / (double)N + (double)cf.e_ref);
                 }
             }
         }
@@ -945,7 +946,8 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                     }
                     const int64_t b = cf.b_first + task.rep;
                     const int64_t ri = (k - cf.rec_first) / ca.record_every;
-                    ca.rec_dev[b * ca.rec_stride + ri] = make_double2(bm / (double)N, be / (double)N);
+                    ca.rec_dev[b * ca.rec_stride + ri] =
+                        make_double2(bm / (double)N, ca.m_only ? 0.0 : be / (double)N + (double)cf.e_ref);
                 }
             }
         }
@@ -1115,6 +1117,20 @@ cudaError_t launch_debug_noise(uint64_t seed, int cfg, int rep, int64_t k, int t
     if (n_quads <= 0) return cudaSuccess;
     debug_noise_kernel<<<(unsigned)((n_quads + 255) / 256), 256, 0, st>>>(seed, cfg, rep, k, tag, n_quads, words,
                                                                           gauss);
+    return cudaGetLastError();
+}
+
+__global__ void debug_gauss4_kernel(const uint32_t* words, int64_t n_quads, float c, float* out)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_quads) return;
+    st4(out + 4 * q, gauss4_scaled(*reinterpret_cast<const uint4*>(words + 4 * q), c));
+}
+
+cudaError_t launch_debug_gauss4(const uint32_t* words, int64_t n_quads, float c, float* out, cudaStream_t st)
+{
+    if (n_quads <= 0) return cudaSuccess;
+    debug_gauss4_kernel<<<(unsigned)((n_quads + 255) / 256), 256, 0, st>>>(words, n_quads, c, out);
     return cudaGetLastError();
 }
 

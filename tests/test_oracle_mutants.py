@@ -24,6 +24,7 @@ equip = lambda P: P.test_equipartition_halves_with_fresh_draws_reading()
 msd = lambda P: P.test_benchmark_harmonic_msd(0.05, 1.0)
 adj_E = lambda P: P.test_adjoint_matches_finite_differences_smooth_field(1.0, 0.0)
 adj_M = lambda P: P.test_adjoint_matches_finite_differences_smooth_field(0.0, 1.0)
+sens = lambda P: P.test_theta_sensitivity_matches_finite_differences()
 
 # name: (text in the oracle, planted replacement, pins of which one must fail)
 MUTANTS = {
@@ -72,6 +73,9 @@ MUTANTS = {
                          "grad[3] = 0.5 * dt * (abar - b * bbar) + geta_amp;", [adj_E]),
     "adjoint_forward_bond_x": ("tb[ix] -= wE * Jx * q * sin(q * dx) / N;",
                                "tb[ix] += wE * Jx * q * sin(q * dx) / N;", [adj_E]),
+    "sensitivity_drops_drift": ("hb[i] += tb[i] * dt;", "hb[i] += tb[i] * 0.0;", [sens]),
+    "sensitivity_damping_reverse": ("wb[i] = hb[i] * (1.0 - a);", "wb[i] = hb[i] * (1.0 + a);", [sens]),
+    "sensitivity_second_kick_force": ("Fb[i] += wb[i] * b * 0.5 * dt;", "Fb[i] = wb[i] * b * 0.5 * dt;", [sens]),
 }
 
 
@@ -110,5 +114,5 @@ def test_unmutated_copy_passes_the_same_pins(tmp_path, monkeypatch):
     """Control: the copy mechanism itself changes nothing."""
     m = _mutant_oracle(tmp_path, "control", "double xyo_uniform(uint32_t x)", "double xyo_uniform(uint32_t x)")
     monkeypatch.setattr(pins, "oracle", m)
-    for check in {force, init, equip, adj_E, adj_M}:
+    for check in {force, init, equip, adj_E, adj_M, sens}:
         check(pins)

@@ -579,3 +579,119 @@ def test_power_quench_closed_form(gamma):
     assert abs(T[0] - Tc * (1 + ei)) < 1e-12 and abs(T[-1] - Tc * (1 + ef)) < 1e-12
     assert np.all(np.diff(T) <= 1e-15)
     assert np.max(np.abs(np.diff(T))) < Tc * gamma * 1.5 / tq  # no jumps: |dT/dk| <= Tc gamma max|eps|^(1-1/gamma) / tq
+
+
+# ---------------------------------------------------------------- path sensitivity (test infrastructure)
+
+
+def _state_after(Lx, Ly, prm, knots, th0, om0, k0, j):
+    th, om = th0.copy(), om0.copy()
+    oracle.run_lattice(Lx, Ly, 0, 0, 5, prm, knots, k0, j, th, om)
+    return th, om
+
+
+def test_theta_sensitivity_matches_finite_differences():
+    """lt_s(j) = d theta_t(n) / d theta_s(j) and lv_s(j) = d theta_t(n) /
+    d wh_s(j) against central differences of the oracle's own trajectory:
+    the angle perturbed after step j - 1 (the second half-kick of that step
+    then sees the perturbed force), the half-step velocity of step j
+    perturbed through omega_j (wh_j = (1 - a) omega_j + ...)."""
+    Lx, Ly, n, k0 = 6, 4, 12, 3
+    prm = dict(J_par=2.0, J_perp=0.7, h=1.0, p=2.0, eta=0.8, dt=0.02)
+    knots = ([0], [0.2])
+    rng = np.random.default_rng(5)
+    th0 = rng.uniform(-0.5, 0.5, Lx * Ly)
+    om0 = 0.3 * rng.standard_normal(Lx * Ly)
+    target = 9
+    _, lt, lv = oracle.theta_sensitivity(Lx, Ly, 0, 0, 5, prm, knots, k0, n, th0, om0, [target], fields=True)
+    a = 0.5 * prm["eta"] * prm["dt"]
+    eps = 1e-6
+    for j, s in ((1, target), (4, target + 1), (7, 2), (n, target), (n, 3)):
+        th_j, om_j = _state_after(Lx, Ly, prm, knots, th0, om0, k0, j)
+        out = []
+        for sgn in (1.0, -1.0):
+            th_p, om_p = th_j.copy(), om_j.copy()
+            th_p[s] += sgn * eps
+            # omega_j was formed with F(theta_j): redo that half-kick's force term
+            dF = oracle.force(Lx, Ly, prm, th_p) - oracle.force(Lx, Ly, prm, th_j)
+            om_p += 0.5 * prm["dt"] * dF / (1 + a)
+            th_e, om_e = _state_after(Lx, Ly, prm, knots, th_p, om_p, k0 + j, n - j)
+            out.append(th_e[target])
+        fd = (out[0] - out[1]) / (2 * eps)
+        assert abs(fd - lt[j - 1, s]) <= 1e-6 * abs(fd) + 1e-9, (j, s, fd, lt[j - 1, s])
+    for j, s in ((0, target), (3, target - 1), (6, 15), (n - 1, target)):
+        th_j, om_j = _state_after(Lx, Ly, prm, knots, th0, om0, k0, j)
+        out = []
+        for sgn in (1.0, -1.0):
+            om_p = om_j.copy()
+            om_p[s] += sgn * eps / (1 - a)
+            th_e, _ = _state_after(Lx, Ly, prm, knots, th_j.copy(), om_p, k0 + j, n - j)
+            out.append(th_e[target])
+        fd = (out[0] - out[1]) / (2 * eps)
+        assert abs(fd - lv[j, s]) <= 1e-6 * abs(fd) + 1e-9, (j, s, fd, lv[j, s])
+
+
+def test_theta_sensitivity_sums_and_free_rotor_closed_form():
+    """J = h = 0 and T = 0: free damped rotors, theta_n = theta_j + dt sum_{m>=j} wh_m
+    with wh_{m+1} = r wh_m, r = (1 - a) / (1 + a).  So lt_s(j) = delta_st and
+    lv_t(j) = dt (1 - r^(n - j)) / (1 - r); the weighted sums follow in closed form."""
+    Lx, Ly, n = 8, 2, 20
+    prm = dict(J_par=0.0, J_perp=0.0, h=0.0, eta=1.5, dt=0.05)
+    th0 = np.linspace(-1.0, 1.0, Lx * Ly)
+    om0 = np.full(Lx * Ly, 0.1)
+    t = 5
+    a = 0.5 * 1.5 * 0.05
+    r = (1 - a) / (1 + a)
+    want_lv = np.array([0.05 * (1 - r ** (n - j)) / (1 - r) for j in range(n)])
+    out, tth, tom, lt, lv = oracle.theta_sensitivity(Lx, Ly, 0, 0, 1, prm, ([0], [0.0]), 0, n, th0, om0, [t, 2],
+                                                     trajectory=True, fields=True)
+    np.testing.assert_allclose(lv[:, t], want_lv, rtol=1e-12)
+    assert np.abs(np.delete(lv, t, axis=1)).max() == 0.0
+    assert np.all(lt[:, t] == 1.0) and np.abs(np.delete(lt, t, axis=1)).max() == 0.0
+    np.testing.assert_allclose(out[0], [n + want_lv.sum(), math.sqrt(n + (want_lv ** 2).sum())], rtol=1e-12)
+    assert abs(out[1][0] - out[0][0]) < 1e-12  # another rotor, the same sums
+    # the trajectory of a free rotor: omega_j = omega_0 r^j, theta_j = theta_0 + dt (1 - a) omega_0 (1 - r^j) / (1 - r)
+    j = np.arange(n + 1)
+    np.testing.assert_allclose(tom[:, t], 0.1 * r ** j, rtol=1e-12)
+    np.testing.assert_allclose(tth[:, t], th0[t] + 0.05 * 0.1 * (1 - a) * (1 - r ** j) / (1 - r), rtol=1e-12)
+    # weights: sum |l| w over the fields
+    rng = np.random.default_rng(2)
+    wt, wv = rng.random((n, Lx * Ly)), rng.random((n, Lx * Ly))
+    out_w = oracle.theta_sensitivity(Lx, Ly, 0, 0, 1, prm, ([0], [0.0]), 0, n, th0, om0, [t], wt=wt, wv=wv)
+    np.testing.assert_allclose(out_w[0], [wt[:, t].sum() + (want_lv * wv[:, t]).sum(),
+                                          math.sqrt((wt[:, t] ** 2).sum() + ((want_lv * wv[:, t]) ** 2).sum())],
+                               rtol=1e-12)
+
+
+def test_first_order_bound_holds_for_binary32_state_rounding():
+    """The propagation behind the parity tests' first-order bound, on the CPU:
+    a run that rounds its state to binary32 after every step makes local
+    errors of at most U |theta_j| in the angles and U |omega_j| in the
+    full-step velocities (hence (1 - a) U |omega_j| in the next half-step
+    velocity); after 100 steps from a random start at T_c every site must lie
+    within sum |lambda| w of the exact run, and the sum must not be vacuous
+    (within a factor 1000 of the largest deviation)."""
+    Lx, Ly, n = 16, 12, 100
+    prm = dict(inputs.PAPER)
+    knots = ([0], [inputs.T_C])
+    th0 = inputs.angles(1, Lx, Ly, seed=12)[0].astype(np.float64)
+    om0 = np.zeros(Lx * Ly)
+    U = 2.0 ** -24
+    a = 0.5 * prm["eta"] * prm["dt"]
+    ex_t, ex_w = th0.copy(), om0.copy()
+    oracle.run_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, n, ex_t, ex_w)
+    r_t, r_w = th0.copy(), om0.copy()
+    for k in range(n):
+        oracle.run_lattice(Lx, Ly, 0, 0, 3, prm, knots, k, 1, r_t, r_w)
+        r_t[:] = r_t.astype(np.float32)
+        r_w[:] = r_w.astype(np.float32)
+    d = np.abs(r_t - ex_t) % math.pi
+    d = np.minimum(d, math.pi - d)
+    _, tth, tom = oracle.theta_sensitivity(Lx, Ly, 0, 0, 3, prm, knots, 0, n, th0, om0, [], trajectory=True)
+    wt = U * np.abs(tth[1:])
+    wv = (1 - a) * U * np.abs(tom[:n])
+    wv[0] = 0.0  # the start is exact
+    sites = np.arange(Lx * Ly)
+    bound = oracle.theta_sensitivity(Lx, Ly, 0, 0, 3, prm, knots, 0, n, th0, om0, sites, wt=wt, wv=wv)[:, 0]
+    assert np.all(d <= bound), (d / bound).max()
+    assert d.max() > 1e-3 * bound.max()
