@@ -82,3 +82,37 @@ def test_cluster_resident_matches_plain(tmp_path, Lx, Ly, n_rep, threads, csize,
     # records: the same site terms, summed in a different order
     assert res["rec_same_slots"] and res["rec_count"] == n_rep * 15, res
     assert res["rec_max_diff"] < 1e-5, res
+
+
+SHARED = textwrap.dedent(r"""
+    import sys
+    import torch
+    sys.path.insert(0, sys.argv[1])
+    from paper_2409_06412_gb300 import Config, Lattice, XY_PATH_PLAIN
+    big = Lattice([Config(Lx=128, Ly=128, n_replicas=1, seed=3, init_mode=0, n_total=10**6)])
+    big.step(40)
+    ref = Lattice([Config(Lx=128, Ly=128, n_replicas=1, seed=3, init_mode=0, n_total=10**6)])
+    ref.set_path(XY_PATH_PLAIN)
+    ref.step(40)
+    # a second object whose shape runs on the same kernel instance with less shared memory
+    small = Lattice([Config(Lx=64, Ly=64, n_replicas=1, seed=4, init_mode=0, n_total=10**6)])
+    small.step(40)
+    big.step(40)   # must still launch with its own (larger) shared memory
+    ref.step(40)
+    torch.cuda.synchronize()
+    print("RESULT", int(torch.equal(big.theta, ref.theta) and torch.equal(big.omega, ref.omega)))
+""")
+
+
+@pytest.mark.gpu
+def test_resident_shapes_sharing_a_kernel_keep_their_shared_memory(tmp_path):
+    """Two objects whose resident shapes use the same kernel instance (512
+    threads, several rows per band) with different shared memory: preparing
+    the smaller one after the larger must not take the larger one's shared
+    memory away (the opt-in is an attribute of the kernel, not of a shape)."""
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{gpu_key_name()}|resident|128|128|1 512 1\n{gpu_key_name()}|resident|64|64|1 512 1\n")
+    env = dict(os.environ, XY_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", SHARED, ROOT], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert [l for l in r.stdout.splitlines() if l.startswith("RESULT ")][-1] == "RESULT 1"
