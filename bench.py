@@ -603,6 +603,15 @@ def profile_case(name):
         lat.step(200)
         lat.label_domains(0, 64)
         lat.label_domains(0, 64)
+    elif name in ("strip1024", "band2-1024"):
+        # 128 lattices of 1024^2 (1.07 GB of state in both halves of the double
+        # buffer), 32 steps with one or two steps per launch (32-row bands for
+        # two); four concurrent slices of 32 lattices, each launch several waves
+        lat = Lattice([Config(Lx=1024, Ly=1024, n_replicas=128, seed=1, init_mode=1, knots=((0,), (TC,)),
+                              n_total=10 ** 6)])
+        lat.set_autotune(False)
+        lat.set_temporal_blocking(2 if name == "band2-1024" else 1)
+        lat.step(32)
     elif name == "sf":
         # structure factors of 64 lattices of 1024^2 for k < 16
         lat = Lattice([Config(Lx=1024, Ly=1024, n_replicas=64, seed=1, init_mode=0, knots=((0,), (TC,)),
@@ -619,7 +628,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["static", "static-L512", "dynamic-z", "kibble-zurek"], default="static")
-    ap.add_argument("--profile-case", choices=["adjoint-small", "adjoint-short", "plain64", "sf", "ccl"], default=None,
+    ap.add_argument("--profile-case", choices=["adjoint-small", "adjoint-short", "plain64", "sf", "ccl", "strip1024",
+                                               "band2-1024"], default=None,
                     help="run one small case for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

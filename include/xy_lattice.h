@@ -208,6 +208,25 @@ int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, 
 int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w_E, double w_M,
                       double* objective, double* grads);
 
+/* Temporal blocking of the batched stepper (the paper steps one time step
+ * per pass; this is a property of the library).  Lattices with
+ * 256 <= Lx <= 1024 (Lx a multiple of 128, Ly a multiple of 8) can advance two
+ * BBK steps per launch: a thread block sweeps a band of H rows across the
+ * lattice width, carrying the intermediate step in registers, so the state
+ * crosses HBM once per two steps (8 bytes per site-update instead of 16); the
+ * two bands' boundary rows of the intermediate step are computed twice.
+ * States are bit-identical either way.  Two-step launches run only over
+ * stretches of steps that record nothing, in batches of a multiple of four
+ * steps, and only for shapes whose configurations all run the whole call.
+ *   kt = 0 (default): the autotuner times one and two steps per launch (and
+ *          the band height H in {8, 16, 32, 64}) per lattice shape and keeps
+ *          two only if at least 5 % faster per step;
+ *   kt = 1: one step per launch everywhere;
+ *   kt = 2: two steps per launch wherever the shape allows (the tuner's
+ *          fastest band height, else the largest of 32, 16, 8 dividing Ly).
+ * XY_EINVAL for any other value. */
+int xy_set_temporal_blocking(xy_lattice* lat, int kt);
+
 /* How the reverse sweep of xy_adjoint_step_n() gets the states of a
  * checkpoint segment (the paper has no adjoint; this is the schedule of the
  * pathwise derivative of the App. A.1 integrator):
@@ -314,7 +333,8 @@ int64_t xy_kernel_launches(xy_lattice* lat);
 #define XY_KCLASS_ADJ_FWD 3   /* adjoint: forward pass with checkpoints and records (one span per call) */
 #define XY_KCLASS_ADJ_RECOMP 4 /* adjoint: recompute of the checkpoint segments (one span per call) */
 #define XY_KCLASS_ADJ_REV 5   /* adjoint: reverse sweep kernels (one span per call) */
-#define XY_KCLASS_COUNT 6
+#define XY_KCLASS_STRIP2 6    /* two-step band launches (temporal blocking; each launch is two steps) */
+#define XY_KCLASS_COUNT 7
 
 /* Kernel timing.  on != 0: the batched path launches its kernels directly
  * (no graph replay) and brackets every stepper launch with CUDA events on the

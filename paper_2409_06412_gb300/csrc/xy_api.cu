@@ -144,7 +144,19 @@ struct StripGroup {
     StripTask* d_tasks = nullptr;
     size_t d_cap = 0;
     int variant_rec = 0;  // occupancy variant of launches that record (0: derived from variant)
+    // two steps per launch (temporal blocking): band height chosen by the
+    // autotuner, 0 when one step per pass is faster or the shape does not fit
+    int b2_H = 0;
+    int b2_auto = 0;  // the tuner's choice (0: one step per pass)
+    int b2_var = 2;   // occupancy variant of the two-step kernel (2 or 3 blocks per SM)
+    int b2_best = 0;  // the fastest band height it timed, chosen or not
+    std::vector<BandTask> b2_tasks;
+    BandTask* d_b2_tasks = nullptr;
+    size_t d_b2_cap = 0;
 };
+
+// Shapes the two-step band kernel takes: one warp per 128 columns, 2..8 warps.
+bool b2_shape(int Lx, int Ly) { return Lx >= 256 && Lx <= 1024 && Lx % 128 == 0 && Ly >= 8 && Ly % 8 == 0; }
 
 bool is_device_ptr(const void* p)
 {
@@ -221,6 +233,7 @@ struct xy_lattice {
         int chunk;
         int rec;
         uint32_t rec_mask;
+        uint32_t kt2;
         cudaGraphExec_t exec;
         int64_t kernels;
     };
@@ -228,6 +241,8 @@ struct xy_lattice {
     int cur_rec = 0;            // records of the current window: 0 none, 1 M, 2 M and E
     int cur_re = 0;             // its record_every
     uint32_t cur_mask = ~0u;    // local steps of a chunk at which some strip-stepped lattice records
+    uint32_t cur_kt2 = 0u;      // strip groups that take two steps per launch in this window
+    int kt_mode = 0;            // xy_set_temporal_blocking: 0 tuner, 1 one step, 2 two steps per launch
     // kernel timing (direct launches bracketed by events)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
@@ -389,6 +404,19 @@ struct Span {
     int close() { return timed_end(end, L->stream); }
 };
 
+// Whether strip group g takes the local steps [jl0, jl0 + cnt) two per launch:
+// the window allows it (cur_kt2: every configuration of the group runs the
+// whole window), none of the steps records, and the batch holds an even number
+// of pairs, so that after it the state is where single steps would leave it.
+bool kt2_batch(const xy_lattice* L, int g, int64_t jl0, int cnt)
+{
+    if (!((L->cur_kt2 >> g) & 1u) || cnt % 4 != 0 || L->strip_groups[g].b2_H == 0) return false;
+    if (L->cur_rec)
+        for (int i = 0; i < cnt; ++i)
+            if ((L->cur_mask >> ((jl0 + i) & 31)) & 1u) return false;
+    return true;
+}
+
 // Launch the batched kernels for local steps [jl0, jl0 + cnt) of the current window.
 int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, bool advance)
 {
@@ -404,6 +432,15 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
     }
     for (int i = 0; i < cnt; ++i) {
         for (auto& g : L->strip_groups) {
+            if (kt2_batch(L, (int)(&g - L->strip_groups.data()), jl0, cnt)) {
+                if (i & 1) continue;  // the launch at step i took step i + 1 too
+                if ((rc = timed_begin(L, st, XY_KCLASS_STRIP2, &end))) return rc;
+                CK(launch_band2_step(L->d_cfg, g.d_b2_tasks, (int)g.b2_tasks.size(), g.Lx, g.b2_H, g.b2_var, g.seed,
+                                     jl0 + i, buf, L->d_call, st));
+                if ((rc = timed_end(end, st))) return rc;
+                ++L->launches;
+                continue;
+            }
             if ((rc = timed_begin(L, st, XY_KCLASS_STRIP, &end))) return rc;
             // only the steps that record run the recording kernel
             const int rec = (L->cur_rec && ((L->cur_mask >> ((jl0 + i) & 31)) & 1u)) ? L->cur_rec : 0;
@@ -548,7 +585,18 @@ struct Branch {
     int kind;  // 0 resident group, 1 strip group slice, 2 plain configurations
     int group;
     int task0, n_tasks;
+    int b2_task0 = 0, b2_n_tasks = 0;  // the same lattices' tasks of the two-step kernel
 };
+
+// Index of the first two-step task of the lattice that strip task t starts
+// (both task lists run lattice by lattice, every lattice of a group alike).
+int b2_index_of(const StripGroup& g, int t)
+{
+    if (g.b2_H == 0 || g.tasks.empty()) return 0;
+    if (t >= (int)g.tasks.size()) return (int)g.b2_tasks.size();
+    const int per_strip = (int)(g.tasks.size() / g.n_lat);
+    return (t / per_strip) * (g.Ly / g.b2_H);
+}
 
 std::vector<Branch> chunk_branches(const xy_lattice* L)
 {
@@ -556,9 +604,15 @@ std::vector<Branch> chunk_branches(const xy_lattice* L)
     for (int r = 0; r < (int)L->res_groups.size(); ++r) out.push_back({0, r, 0, 0});
     const int fixed = (int)L->res_groups.size() + (L->plain_cfgs.empty() ? 0 : 1);
     const auto cuts = slice_groups(L->strip_groups, fixed, xy_lattice::kBranches + 1);
-    for (int s = 0; s < (int)L->strip_groups.size(); ++s)
-        for (size_t p = 0; p + 1 < cuts[s].size(); ++p)
-            out.push_back({1, s, cuts[s][p], cuts[s][p + 1] - cuts[s][p]});
+    for (int s = 0; s < (int)L->strip_groups.size(); ++s) {
+        const StripGroup& g = L->strip_groups[s];
+        for (size_t p = 0; p + 1 < cuts[s].size(); ++p) {
+            Branch b{1, s, cuts[s][p], cuts[s][p + 1] - cuts[s][p]};
+            b.b2_task0 = b2_index_of(g, cuts[s][p]);
+            b.b2_n_tasks = b2_index_of(g, cuts[s][p + 1]) - b.b2_task0;
+            out.push_back(b);
+        }
+    }
     if (!L->plain_cfgs.empty()) out.push_back({2, 0, 0, 0});
     return out;
 }
@@ -574,8 +628,15 @@ cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, const Branch& br, int6
         ++L->launches;
         return e;
     }
+    const bool two = br.kind == 1 && kt2_batch(L, br.group, jl0, cnt);
     for (int i = 0; i < cnt && e == cudaSuccess; ++i) {
-        if (br.kind == 1) {
+        if (two) {
+            if (i & 1) continue;
+            auto& g = L->strip_groups[br.group];
+            e = launch_band2_step(L->d_cfg, g.d_b2_tasks + br.b2_task0, br.b2_n_tasks, g.Lx, g.b2_H, g.b2_var, g.seed,
+                                  jl0 + i, buf, L->d_call, st);
+            ++L->launches;
+        } else if (br.kind == 1) {
             auto& g = L->strip_groups[br.group];
             const int rec = (L->cur_rec && ((L->cur_mask >> ((jl0 + i) & 31)) & 1u)) ? L->cur_rec : 0;
             const int var = rec && g.variant_rec ? g.variant_rec : g.variant;
@@ -601,7 +662,7 @@ cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, const Branch& br, int6
 int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
     for (auto& g : L->graphs)
-        if (g.chunk == chunk && g.rec == L->cur_rec && g.rec_mask == L->cur_mask) {
+        if (g.chunk == chunk && g.rec == L->cur_rec && g.rec_mask == L->cur_mask && g.kt2 == L->cur_kt2) {
             *out = &g;
             return XY_OK;
         }
@@ -645,13 +706,14 @@ int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    L->graphs.push_back({chunk, L->cur_rec, L->cur_mask, exec, kernels});
+    L->graphs.push_back({chunk, L->cur_rec, L->cur_mask, L->cur_kt2, exec, kernels});
     *out = &L->graphs.back();
     return XY_OK;
 }
 
 
 int build_strip_tasks(xy_lattice* L, StripGroup& g);
+int build_b2_tasks(xy_lattice* L, StripGroup& g, int H);
 
 // ---- autotuner: per strip shape, time strip heights x occupancy variants;
 // per resident shape, time the block sizes.  Candidates run one step from
@@ -685,11 +747,38 @@ std::string gpu_name()
     return s;
 }
 
+// Band height of the two-step kernel per strip group under the current mode:
+// the tuner's choice, none, or (forced) the tuner's fastest height, else the
+// largest of 32, 16, 8 dividing Ly.
+int apply_kt_mode(xy_lattice* L)
+{
+    for (auto& g : L->strip_groups) {
+        int h = 0;
+        if (L->kt_mode == 0) h = g.b2_auto;
+        if (L->kt_mode == 2 && b2_shape(g.Lx, g.Ly)) {
+            h = g.b2_best;
+            for (int c : {32, 16, 8})
+                if (h == 0 && g.Ly % c == 0) h = c;
+        }
+        if (h == g.b2_H) continue;
+        g.b2_H = 0;
+        if (h > 0) {
+            int rc = build_b2_tasks(L, g, h);
+            if (rc) return rc;
+            g.b2_H = h;
+        } else {
+            for (auto& gr : L->graphs) cudaGraphExecDestroy(gr.exec);
+            L->graphs.clear();
+        }
+    }
+    return XY_OK;
+}
+
 int autotune_lattice(xy_lattice* L)
 {
     if (L->tuned) return XY_OK;
     L->tuned = true;
-    if (!L->autotune) return XY_OK;
+    if (!L->autotune) return apply_kt_mode(L);
     const std::string gpu = gpu_name();
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -822,7 +911,76 @@ int autotune_lattice(xy_lattice* L)
             }
             g.variant_rec = rv;
         }
+        // temporal blocking: two steps per launch on bands of H2 rows, timed
+        // against one step per pass as chosen above, sliced alike; kept only
+        // when at least 5 % faster per step
+        if (rc == XY_OK && bh > 0 && b2_shape(g.Lx, g.Ly)) {
+            char key2[256];
+            snprintf(key2, sizeof key2, "%s|band2-sliced|%d|%d|%lld", gpu.c_str(), g.Lx, g.Ly, (long long)g.n_lat);
+            int h2 = -1, unused = 0;
+            if (g_tune.get(key2, &h2, &unused) && !(h2 == 0 || (h2 >= 8 && h2 <= 64 && g.Ly % h2 == 0))) h2 = -1;
+            if (h2 < 0) {
+                const std::vector<int> cuts1 = cut_tasks(g.tasks, n_parts);
+                auto time_it = [&](const std::vector<int>& cuts, auto&& run, float& out) -> int {
+                    int reps = 3;
+                    out = 1e30f;
+                    for (int round = 0; round < 5; ++round) {
+                        CK(launch_sliced(L, cuts, 1, run));
+                        CK(cudaEventRecord(e0, L->stream));
+                        CK(launch_sliced(L, cuts, reps, run));
+                        CK(cudaEventRecord(e1, L->stream));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        L->launches += (int64_t)(1 + reps) * ((int)cuts.size() - 1);
+                        out = std::min(out, ms / reps);
+                        if (round == 0 && ms < 0.5f) reps = std::min(64, (int)(0.5f / std::max(ms / reps, 1e-3f)) + 1);
+                    }
+                    return XY_OK;
+                };
+                float t1 = 1e30f;
+                rc = time_it(cuts1, [&](cudaStream_t st, int t0, int cnt) {
+                    return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, g.H, g.variant, 0, g.seed, 0, buf,
+                                             L->d_call, L->pa, st);
+                }, t1);
+                float best2 = 1e30f;
+                int bestH = 0, bestV = 2;
+                for (int H2 : {8, 16, 32, 64}) {
+                    if (rc || g.Ly % H2 != 0) continue;
+                    if ((rc = build_b2_tasks(L, g, H2))) break;
+                    g.b2_H = H2;
+                    std::vector<int> cuts2;
+                    for (int c1 : cuts1) cuts2.push_back(b2_index_of(g, c1));
+                    for (int v2 : {2, 3}) {
+                        float t2 = 1e30f;
+                        rc = time_it(cuts2, [&](cudaStream_t st, int t0, int cnt) {
+                            return launch_band2_step(L->d_cfg, g.d_b2_tasks + t0, cnt, g.Lx, H2, v2, g.seed, 0, buf,
+                                                     L->d_call, st);
+                        }, t2);
+                        if (rc) break;
+                        if (t2 / 2 < best2) {
+                            best2 = t2 / 2;
+                            bestH = H2;
+                            bestV = v2;
+                        }
+                    }
+                }
+                g.b2_H = 0;
+                if (rc) break;
+                // a margin: isolated sliced timings overstate the two-step
+                // kernel's gain inside a mixed batch (512^2 lattices of the
+                // static-criticality batch: 2 % faster alone, 0.4 % slower in the batch)
+                h2 = best2 < 0.95f * t1 ? bestH : 0;
+                unused = bestH * 8 + bestV;  // height and variant of the fastest two-step candidate
+                g_tune.put(key2, h2, unused);
+            }
+            g.b2_auto = h2;
+            const int hb = unused / 8, vb = unused % 8;
+            g.b2_best = (hb >= 8 && hb <= 64 && g.Ly % hb == 0) ? hb : 0;
+            g.b2_var = (vb == 3) ? 3 : 2;
+        }
     }
+    if (rc == XY_OK) rc = apply_kt_mode(L);
     // resident shapes: block size x cluster size (1 = one block per lattice;
     // more blocks per lattice spread a small batch over more SMs)
     for (auto& g : L->res_groups) {
@@ -898,6 +1056,16 @@ int autotune_lattice(xy_lattice* L)
 int run_window(xy_lattice* L, int64_t n_max)
 {
     if (n_max <= 0) return XY_OK;
+    // two steps per launch for the strip groups the tuner gave a band height,
+    // when every configuration of the group runs the whole window (a pair
+    // never straddles the last step of one of them)
+    L->cur_kt2 = 0u;
+    for (int gi = 0; gi < (int)L->strip_groups.size() && gi < 32; ++gi) {
+        const StripGroup& g = L->strip_groups[gi];
+        bool all = g.b2_H > 0;
+        for (int c : g.cfgs) all = all && L->h_dev[c].n_call == n_max;
+        if (all) L->cur_kt2 |= 1u << gi;
+    }
     if (L->path == XY_PATH_PLAIN) {
         for (int64_t j = 0; j < n_max; ++j)
             for (int c = 0; c < L->n_cfg; ++c) {
@@ -1072,6 +1240,28 @@ int build_strip_tasks(xy_lattice* L, StripGroup& g)
     return XY_OK;
 }
 
+// Tasks of the two-step band kernel: one block per band of H rows of every
+// lattice of the group, lattice by lattice like the strip tasks.
+int build_b2_tasks(xy_lattice* L, StripGroup& g, int H)
+{
+    g.b2_tasks.clear();
+    const int nb = g.Ly / H;
+    for (int c : g.cfgs)
+        for (int r = 0; r < L->cfg[c].desc.n_replicas; ++r)
+            for (int b = 0; b < nb; ++b) g.b2_tasks.push_back(BandTask{c, r, b, nb});
+    if (g.b2_tasks.size() > g.d_b2_cap) {
+        cudaFree(g.d_b2_tasks);
+        g.d_b2_tasks = nullptr;
+        g.d_b2_cap = 0;
+        CK(cudaMalloc(&g.d_b2_tasks, sizeof(BandTask) * g.b2_tasks.size()));
+        g.d_b2_cap = g.b2_tasks.size();
+    }
+    CK(cudaMemcpy(g.d_b2_tasks, g.b2_tasks.data(), sizeof(BandTask) * g.b2_tasks.size(), cudaMemcpyHostToDevice));
+    for (auto& gr : L->graphs) cudaGraphExecDestroy(gr.exec);
+    L->graphs.clear();
+    return XY_OK;
+}
+
 // smallest strip height the autotuner may pick for a shape
 int min_strip_H(int Lx, int Ly)
 {
@@ -1158,7 +1348,10 @@ void free_lattice(xy_lattice* L)
         cudaEventDestroy(pr.second);
     }
     for (auto& g : L->res_groups) cudaFree(g.d_tasks);
-    for (auto& g : L->strip_groups) cudaFree(g.d_tasks);
+    for (auto& g : L->strip_groups) {
+        cudaFree(g.d_tasks);
+        cudaFree(g.d_b2_tasks);
+    }
     cudaFree(L->thB);
     cudaFree(L->omB);
     cudaFree(L->d_cfg);
@@ -1356,6 +1549,14 @@ int xy_set_path(xy_lattice* L, int path)
     if (path != XY_PATH_BATCHED && path != XY_PATH_PLAIN) return fail(XY_EINVAL, "unknown path %d", path);
     L->path = path;
     return XY_OK;
+}
+
+int xy_set_temporal_blocking(xy_lattice* L, int kt)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (kt < 0 || kt > 2) return fail(XY_EINVAL, "temporal blocking must be 0 (tuner), 1 or 2 steps per launch");
+    L->kt_mode = kt;
+    return L->tuned ? apply_kt_mode(L) : XY_OK;
 }
 
 int xy_set_adjoint_mode(xy_lattice* L, int mode)

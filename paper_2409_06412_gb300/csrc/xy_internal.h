@@ -117,6 +117,12 @@ cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h_cfg, int64_t 
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
                               int rec, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
                               cudaStream_t st);
+// two steps per launch (k -> k + 2) on bands of H rows across the lattice
+// width (256 <= Lx <= 1024); the launch at j_local takes steps j and j + 1 of
+// the call; a batch of launches must hold an even number of such pairs
+struct BandTask;
+cudaError_t launch_band2_step(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, int variant,
+                              uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, cudaStream_t st);
 // every task of one launch uses the noise key `seed`
 cudaError_t launch_resident_step(const DevCfg* d_cfg, const ResidentTask* tasks, int n_tasks, int Lx, int Ly,
                                  int threads, int csize, uint64_t seed, int64_t j_local, int n_steps, Buffers buf,

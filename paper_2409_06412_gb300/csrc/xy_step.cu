@@ -623,6 +623,201 @@ cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n
 }
 
 
+// ===========================================================================
+// Two steps per pass (temporal blocking over K_t = 2 steps)
+// ===========================================================================
+// A block owns a band of H rows across the whole lattice width (Lx / 128
+// warps side by side, 256 <= Lx <= 1024) and sweeps it once for two steps:
+// iteration i loads row y = y0 - 2 + i of theta_k (and v_k of row y - 1),
+// advances row a = y - 1 to step k + 1 (level 1, rows y0 - 1 .. y0 + H) and
+// row b = y - 2 to step k + 2 (level 2, rows y0 .. y0 + H - 1), which is the
+// only row written back: 8 bytes per site-update instead of 16.  The two
+// extra level-1 rows are recomputed by the neighbouring bands too (2 / H
+// more level-1 work).  Columns next to a warp's strip come from the
+// neighbouring warp through shared memory (one barrier per row, the lattice's
+// periodic wrap inside the block); the per-site arithmetic is that of every
+// other stepper, so states are bit-identical to two single steps.
+namespace {
+
+constexpr int kB2Stages = 4;
+struct B2Stage {
+    float4 th[kB2Stages][32];  // theta_k of the row loaded by an iteration
+    float4 v[kB2Stages][32];   // v_k of the row above it
+};
+struct R0 {  // a level-0 row: theta_k and its (sin q t, cos q t)
+    float4 th;
+    float s[4], c[4];
+};
+struct R1 {  // a level-1 row: theta_{k+1}, v_{k+1} and (sin q t, cos q t)
+    float4 th, v;
+    float s[4], c[4];
+};
+
+__device__ __forceinline__ void sc_row(float q, const float4& t, float* s, float* c)
+{
+    sc_of(q, t.x, s[0], c[0]);
+    sc_of(q, t.y, s[1], c[1]);
+    sc_of(q, t.z, s[2], c[2]);
+    sc_of(q, t.w, s[3], c[3]);
+}
+
+// One row of one level: the update of the center row C from its rows above
+// (P) and below (N); sL.. are the x neighbours of the row's first and last
+// site of this lane (shuffles, or the neighbouring warp's edge for lanes 0, 31).
+__device__ __forceinline__ void b2_update(const StepConst& K, const float* Ps, const float* Pc, const float4& th,
+                                          const float* Cs, const float* Cc, const float* Ns, const float* Nc,
+                                          const float4& v, float sL, float cL, float sR, float cR, const float4& cn,
+                                          float4& th_out, float4& v_out)
+{
+    float to[4], vo[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float sl = s == 0 ? sL : Cs[s - 1];
+        const float cl = s == 0 ? cL : Cc[s - 1];
+        const float sr = s == 3 ? sR : Cs[s + 1];
+        const float cr = s == 3 ? cR : Cc[s + 1];
+        const float sx = __fadd_rn(sl, sr), cx = __fadd_rn(cl, cr);
+        const float sy = __fadd_rn(Ps[s], Ns[s]), cy = __fadd_rn(Pc[s], Nc[s]);
+        const float t = f4get(th, s);
+        const float F = site_force(K, Cs[s], Cc[s], sx, cx, sy, cy, sinp_of(K.p, t));
+        const SiteOut so = site_update(K, t, f4get(v, s), F, f4get(cn, s));
+        to[s] = so.theta;
+        vo[s] = so.v;
+    }
+    th_out = make_float4(to[0], to[1], to[2], to[3]);
+    v_out = make_float4(vo[0], vo[1], vo[2], vo[3]);
+}
+
+}  // namespace
+
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) band2_step_kernel(const DevCfg* cfgs, const BandTask* tasks, int H,
+                                                               int64_t j_local, Buffers buf, const CallArgs* cap,
+                                                               PhiloxKeys keys)
+{
+    extern __shared__ B2Stage s_b2stage[];  // one per warp
+    __shared__ float2 s_edge[2][2][8][2];  // [slot][level][warp][first, last site]: (sin q t, cos q t)
+    const CallArgs ca = *cap;
+    const int lane = threadIdx.x & 31, warp = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5);
+    const BandTask task = tasks[blockIdx.x];
+    const DevCfg& cf = cfgs[task.cfg];
+    const int64_t j = ca.j_base + j_local;
+    if (j >= cf.n_call) return;
+    if (j + 1 >= cf.n_call) {  // the host never pairs a last single step; say so if it ever did
+        if (threadIdx.x == 0) atomicExch(&((CallArgs*)cap)->err, XY_EINVAL);
+        return;
+    }
+    const int64_t k = cf.k_start + j + ca.k_shift;
+    const StepConst K1 = step_const(cf, noise_amp(cf, k));
+    const float c2 = noise_amp(cf, k + 1);
+    const int Lx = cf.Lx, Ly = cf.Ly;
+    const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
+    // a batch of steps holds an even number of pairs: pair p = j_local / 2 of it
+    // reads the buffer the single-step convention gives for step j, flipped when
+    // p is odd, and writes the other
+    const bool rd_b = ca.fixed_parity ? false : (((j & 1) != 0) != (((j_local >> 1) & 1) != 0));
+    const float* thS = (rd_b ? buf.thB : buf.thA) + lat_off;
+    const float* omS = (rd_b ? buf.omB : buf.omA) + lat_off;
+    float* thD = (rd_b ? buf.thA : buf.thB) + lat_off;
+    float* omD = (rd_b ? buf.omA : buf.omB) + lat_off;
+    const int x = warp * 128 + 4 * lane;
+    const int y0 = task.band0 * H;
+    const int wl = warp == 0 ? nw - 1 : warp - 1, wr = warp + 1 == nw ? 0 : warp + 1;
+    const int srcL = (lane + 31) & 31, srcR = (lane + 1) & 31;
+    const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
+    B2Stage& stg = s_b2stage[warp];
+    const int n_it = H + 4;
+    // prefetch: iteration ii loads theta_k of row y0 - 2 + ii and (ii >= 2) v_k of row y0 - 3 + ii
+    auto issue = [&](int ii) {
+        if (ii < n_it) {
+            const int sl = ii % kB2Stages;
+            cp_async16(&stg.th[sl][lane], thS + (int64_t)wrapi(y0 - 2 + ii, Ly) * Lx + x);
+            if (ii >= 2) cp_async16(&stg.v[sl][lane], omS + (int64_t)wrapi(y0 - 3 + ii, Ly) * Lx + x);
+        }
+        cp_async_commit();
+    };
+    for (int ii = 0; ii < kB2Stages - 1; ++ii) issue(ii);
+    // neighbours in x of a row of this lane: shuffles inside the warp, the
+    // neighbouring warps' edge sites (published the iteration before) for lanes 0 and 31
+    auto x_nbrs = [&](const float* Cs, const float* Cc, int slot, int lev, float& sL, float& cL, float& sR, float& cR) {
+        sL = __shfl_sync(kFull, Cs[3], srcL);
+        cL = __shfl_sync(kFull, Cc[3], srcL);
+        sR = __shfl_sync(kFull, Cs[0], srcR);
+        cR = __shfl_sync(kFull, Cc[0], srcR);
+        // every lane reads the two edge words (a broadcast) and lanes 0 and 31
+        // select them: no divergent branch in the row loop
+        const float2 el = s_edge[slot][lev][wl][1], er = s_edge[slot][lev][wr][0];
+        sL = lane == 0 ? el.x : sL;
+        cL = lane == 0 ? el.y : cL;
+        sR = lane == 31 ? er.x : sR;
+        cR = lane == 31 ? er.y : cR;
+    };
+    auto publish = [&](const float* Cs, const float* Cc, int slot, int lev) {
+        if (lane == 0) s_edge[slot][lev][warp][0] = make_float2(Cs[0], Cc[0]);
+        if (lane == 31) s_edge[slot][lev][warp][1] = make_float2(Cs[3], Cc[3]);
+    };
+    R0 a0, b0, c0;
+    R1 a1, b1, c1;
+    // iteration i: P0, C0, N0 = level-0 rows y - 2, y - 1, y; P1, C1, N1 =
+    // level-1 rows b - 1, b, a (N1 computed here)
+    auto body = [&](int i, R0& P0, R0& C0, R0& N0, R1& P1, R1& C1, R1& N1) {
+        issue(i + kB2Stages - 1);
+        cp_async_wait<kB2Stages - 1>();  // this lane's copies of iteration i have landed
+        const int sl = i % kB2Stages;
+        const int slot = i & 1, prev = slot ^ 1;
+        N0.th = stg.th[sl][lane];
+        sc_row(K1.q, N0.th, N0.s, N0.c);
+        publish(N0.s, N0.c, slot, 0);
+        if (i >= 2) {  // level 1 on row a = y - 1
+            const int a = wrapi(y0 - 3 + i, Ly);
+            const float4 va = stg.v[sl][lane];
+            float sL, cL, sR, cR;
+            x_nbrs(C0.s, C0.c, prev, 0, sL, cL, sR, cR);
+            const uint32_t quad = (uint32_t)(((int64_t)a * Lx + x) >> 2);
+            const float4 cn = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, k, 0u), keys), K1.c);
+            b2_update(K1, P0.s, P0.c, C0.th, C0.s, C0.c, N0.s, N0.c, va, sL, cL, sR, cR, cn, N1.th, N1.v);
+            sc_row(K1.q, N1.th, N1.s, N1.c);
+            publish(N1.s, N1.c, slot, 1);
+        }
+        if (i >= 4) {  // level 2 on row b = y - 2
+            const int b = wrapi(y0 - 4 + i, Ly);
+            float sL, cL, sR, cR;
+            x_nbrs(C1.s, C1.c, prev, 1, sL, cL, sR, cR);
+            const uint32_t quad = (uint32_t)(((int64_t)b * Lx + x) >> 2);
+            StepConst K2 = K1;
+            K2.c = c2;
+            const float4 cn = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, k + 1, 0u), keys), c2);
+            float4 to, vo;
+            b2_update(K2, P1.s, P1.c, C1.th, C1.s, C1.c, N1.s, N1.c, C1.v, sL, cL, sR, cR, cn, to, vo);
+            st4_stream(thD + (int64_t)b * Lx + x, to);
+            st4_stream(omD + (int64_t)b * Lx + x, vo);
+        }
+        __syncthreads();  // edges of this iteration visible; the slot read here free for the next
+    };
+    for (int i = 0; i < n_it; i += 3) {
+        body(i, a0, b0, c0, a1, b1, c1);
+        if (i + 1 < n_it) body(i + 1, b0, c0, a0, b1, c1, a1);
+        if (i + 2 < n_it) body(i + 2, c0, a0, b0, c1, a1, b1);
+    }
+    cp_async_wait<0>();
+}
+
+// Bands of the two-step kernel: H (dividing Ly) is the tuner's to choose;
+// threads = Lx / 4, one warp per 128 columns.
+cudaError_t launch_band2_step(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, int variant,
+                              uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, cudaStream_t st)
+{
+    if (n_tasks == 0) return cudaSuccess;
+    if (Lx < 256 || Lx > 1024 || Lx % 128 != 0) return cudaErrorInvalidValue;
+    // variant = resident 256-thread blocks per SM the registers are capped for:
+    // 2 (no spills) or 3 (a few spilled words, more warps to hide latency)
+    using Kern = void (*)(const DevCfg*, const BandTask*, int, int64_t, Buffers, const CallArgs*, PhiloxKeys);
+    const Kern kern = variant >= 3 ? band2_step_kernel<3> : band2_step_kernel<2>;
+    const size_t smem = sizeof(B2Stage) * (size_t)(Lx / 128);
+    kern<<<(unsigned)n_tasks, Lx / 4, smem, st>>>(d_cfg, tasks, H, j_local, buf, ca, philox_round_keys(seed));
+    return cudaGetLastError();
+}
+
 namespace {
 struct SC4 {
     float s[4], c[4];
@@ -1018,7 +1213,14 @@ cudaError_t prepare_resident(int Lx, int Ly, int threads, int csize, int* cluste
 {
     const int smem = (int)resident_smem_bytes(Lx, Ly, threads, csize);
     const ResidentFn fn = resident_fn(Lx, Ly, threads, csize);
-    cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // Several shapes (of one object or of several, and the tuner's
+    // candidates) share a kernel instance, and the attribute belongs to the
+    // instance: only ever raise it, so that no shape prepared earlier, or a
+    // graph captured with it, loses the shared memory it launches with.
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)fn);
+    if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < smem)
+        e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess && csize > 8)
         e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess || !clusters) return e;

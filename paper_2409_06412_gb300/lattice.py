@@ -162,6 +162,11 @@ class Lattice:
                _ptr(S_perp))
         return S_par, S_perp
 
+    def set_temporal_blocking(self, kt: int):
+        """0: the autotuner chooses one or two steps per launch per lattice
+        shape; 1: one step per launch; 2: two steps wherever the shape allows."""
+        L.call("xy_set_temporal_blocking", self._h, int(kt))
+
     def set_adjoint_mode(self, mode: int):
         """XY_ADJOINT_AUTO, XY_ADJOINT_RECOMPUTE or XY_ADJOINT_BACKWARD: how the
         reverse sweep gets the states of a checkpoint segment."""
@@ -190,9 +195,10 @@ class Lattice:
 
     def kernel_timing(self):
         """(ms, launches) per timing class (resident, strip, plain stepper launches;
-        adjoint forward, recompute and reverse spans) since timing was switched on."""
-        ms = np.zeros(6, dtype=np.float64)
-        n = np.zeros(6, dtype=np.int64)
+        adjoint forward, recompute and reverse spans; two-step band launches)
+        since timing was switched on."""
+        ms = np.zeros(7, dtype=np.float64)
+        n = np.zeros(7, dtype=np.int64)
         L.call("xy_kernel_timing", self._h, ms.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p))
         return ms, n
 
