@@ -208,6 +208,21 @@ int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, 
 int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w_E, double w_M,
                       double* objective, double* grads);
 
+/* Field schedule of configuration cfg: the orthogonal quench, in which the
+ * symmetry-breaking field changes in time beside (or instead of) the
+ * temperature, crossing the phase boundary T_c(h) of App. D (Fig. 10) at an
+ * angle (Sec. VII names such quenches as an extension).  The field of step k
+ * is h_k = h s(k), with h from xy_set_params and s piecewise linear through
+ * the knots (step_knots[i], scale_knots[i]) (steps strictly increasing,
+ * scales finite) and constant outside them, evaluated in FP32 like T(k).
+ * h_k replaces h in the force of time point k (both half-kicks that touch k)
+ * and in E_k of Eq. (XY-Hamilton-Kinetic).  The adjoint's d/dh is the
+ * derivative with respect to h at a fixed profile s.  n_knots = 0 removes
+ * the schedule (s = 1: the same bits as a configuration that never had one).
+ * Carried by xy_save/xy_load.  XY_EINVAL for bad knots. */
+int xy_set_field_schedule(xy_lattice* lat, int cfg, const int64_t* step_knots, const double* scale_knots,
+                          int n_knots);
+
 /* Temporal blocking of the batched stepper (the paper steps one time step
  * per pass; this is a property of the library).  Lattices with
  * 256 <= Lx <= 1024 (Lx a multiple of 128, Ly a multiple of 8) can advance two

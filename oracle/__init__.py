@@ -67,14 +67,16 @@ def _declare(L):
     L.xyo_init_theta.argtypes = [i32, i32, i32, i32, u64, i32, vp]
     L.xyo_force.argtypes = [i32, i32, vp, vp, vp]
     L.xyo_observe.argtypes = [i32, i32, vp, vp, vp, P(d), P(d)]
-    L.xyo_run_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i64, i64, vp, vp, i32, vp]
+    L.xyo_field_scale.argtypes = [i64, i32, vp, vp]
+    L.xyo_field_scale.restype = d
+    L.xyo_run_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64, vp, vp, i32, vp]
     L.xyo_run_lattice.restype = i64
     L.xyo_harmonic_msd.argtypes = [i64, i64, d, d, d, d, u64, vp]
     L.xyo_ccl.argtypes = [i32, i32, vp, vp]
     L.xyo_ccl.restype = i64
-    L.xyo_adjoint_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i64, i64, vp, vp,
+    L.xyo_adjoint_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64, vp, vp,
                                       d, d, P(d), vp, vp, vp]
-    L.xyo_theta_sensitivity.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i64, i64, vp, vp,
+    L.xyo_theta_sensitivity.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64, vp, vp,
                                         i32, vp, vp, vp, vp, vp, vp, vp, vp]
 
 
@@ -101,6 +103,17 @@ def _knots(knots):
     Ts = np.ascontiguousarray(np.asarray(knots[1], dtype=np.float64))
     assert ks.shape == Ts.shape and ks.ndim == 1 and ks.size >= 1
     return ks.size, ks, Ts
+
+
+def _field(field):
+    """Field schedule arguments of the C oracle as (n, steps, scales): field
+    ((steps), (scales)) of h_k = h s(k), or None for s = 1."""
+    if field is None:
+        return 0, np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.float64)
+    ks = np.ascontiguousarray(np.asarray(field[0], dtype=np.int64))
+    ss = np.ascontiguousarray(np.asarray(field[1], dtype=np.float64))
+    assert ks.shape == ss.shape and ks.ndim == 1
+    return ks.size, ks, ss
 
 
 # ---------------------------------------------------------------- primitives
@@ -136,6 +149,11 @@ def temperature(k: int, knots) -> float:
     return lib().xyo_temperature(k, nk, _ptr(ks), _ptr(Ts))
 
 
+def field_scale(k: int, field) -> float:
+    nf, fks, fss = _field(field)
+    return lib().xyo_field_scale(k, nf, _ptr(fks), _ptr(fss))
+
+
 def init_theta(Lx, Ly, cfg, rep, seed, mode) -> np.ndarray:
     th = np.zeros(Lx * Ly, dtype=np.float64)
     lib().xyo_init_theta(Lx, Ly, cfg, rep, seed, mode, _ptr(th))
@@ -159,15 +177,16 @@ def observe(Lx, Ly, params, theta, omega):
     return M.value, E.value
 
 
-def run_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta, omega, record_every=0):
+def run_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta, omega, record_every=0, field=None):
     """Advance one lattice in place; returns the (n_rec, 2) array of (M_k, E_k)."""
     prm = param_vector(params)
     nk, ks, Ts = _knots(knots)
+    nf, fks, fss = _field(field)
     assert theta.dtype == np.float64 and omega.dtype == np.float64
     assert theta.flags.c_contiguous and omega.flags.c_contiguous
     nrec_max = (n // record_every + 1) if record_every > 0 else 0
     rec = np.zeros((max(nrec_max, 1), 2), dtype=np.float64)
-    nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts),
+    nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks), _ptr(fss),
                                  k0, n, _ptr(theta), _ptr(omega), record_every, _ptr(rec))
     return rec[:nrec].copy()
 
@@ -190,25 +209,26 @@ def ccl(Lx, Ly, theta32) -> tuple[np.ndarray, np.ndarray]:
     return lab, hist
 
 
-def adjoint_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, wE, wM):
+def adjoint_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, wE, wM, field=None):
     """Objective sum_{k=k0+1}^{k0+n}(w_E E_k + w_M |M_k|) of one lattice, its
     gradient w.r.t. (J_par, J_perp, h, eta), and the final state."""
     prm = param_vector(params)
     nk, ks, Ts = _knots(knots)
+    nf, fks, fss = _field(field)
     th0 = np.ascontiguousarray(theta0, dtype=np.float64).ravel()
     om0 = np.ascontiguousarray(omega0, dtype=np.float64).ravel()
     grad = np.zeros(4, dtype=np.float64)
     obj = ctypes.c_double()
     th1 = np.empty_like(th0)
     om1 = np.empty_like(om0)
-    lib().xyo_adjoint_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), k0, n,
+    lib().xyo_adjoint_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks), _ptr(fss), k0, n,
                               _ptr(th0), _ptr(om0), wE, wM, ctypes.byref(obj), _ptr(grad),
                               _ptr(th1), _ptr(om1))
     return obj.value, grad, th1, om1
 
 
 def theta_sensitivity(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, targets, wt=None, wv=None,
-                      trajectory=False, fields=False):
+                      trajectory=False, fields=False, field=None):
     """First-order sensitivity of the final angles theta_t(k0 + n), t in
     ``targets``, to perturbations along the FP64 trajectory from the full-step
     state (theta0, omega0) (see xyo_theta_sensitivity): an (n_targets, 2)
@@ -219,6 +239,7 @@ def theta_sensitivity(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omeg
     fields lt, lv of the first target."""
     prm = param_vector(params)
     nk, ks, Ts = _knots(knots)
+    nf, fks, fss = _field(field)
     th0 = np.ascontiguousarray(theta0, dtype=np.float64).ravel()
     om0 = np.ascontiguousarray(omega0, dtype=np.float64).ravel()
     tg = np.ascontiguousarray(np.asarray(targets, dtype=np.int64).ravel())
@@ -231,7 +252,8 @@ def theta_sensitivity(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omeg
     lt = np.zeros((n, N)) if fields else None
     lv = np.zeros((n, N)) if fields else None
     p = lambda a: None if a is None else _ptr(a)
-    lib().xyo_theta_sensitivity(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), k0, n, _ptr(th0), _ptr(om0),
+    lib().xyo_theta_sensitivity(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks), _ptr(fss),
+                                k0, n, _ptr(th0), _ptr(om0),
                                 int(tg.size), _ptr(tg), p(w_t), p(w_v), _ptr(out), p(tth), p(tom), p(lt), p(lv))
     res = (out,)
     if trajectory:
@@ -250,7 +272,8 @@ def _workers():
 def run_batch(configs, thetas, omegas, step_now, n, record_every=0, t0=0, threads=None):
     """Advance a batch of lattices described like the library's configurations.
 
-    configs: list of dicts with keys Lx, Ly, n_rep, seed, params, knots, n_total.
+    configs: list of dicts with keys Lx, Ly, n_rep, seed, params, knots, n_total
+    (and optionally field: ((steps), (scales)) of h_k = h s(k)).
     thetas/omegas: per config, float64 arrays (n_rep, Ly*Lx) updated in place
     (omega is the full-step angular velocity).  step_now: per config step
     counters (list, updated).  Returns (rec, moments) with rec[c] of shape
@@ -270,7 +293,7 @@ def run_batch(configs, thetas, omegas, step_now, n, record_every=0, t0=0, thread
         c, r, k0, ne = job
         cf = configs[c]
         return run_lattice(cf["Lx"], cf["Ly"], c, r, cf["seed"], cf["params"], cf["knots"], k0, ne,
-                           thetas[c][r], omegas[c][r], record_every)
+                           thetas[c][r], omegas[c][r], record_every, cf.get("field"))
 
     with ThreadPoolExecutor(max_workers=threads or _workers()) as ex:
         results = list(ex.map(work, jobs))

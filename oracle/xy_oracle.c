@@ -18,6 +18,7 @@
  *   order parameter      Sec. IV.A, Eq. (lattice-average), s_i = sin(q theta_i)
  *   benchmark 1 (MSD)    App. A.2, Eq. (MSD-HO)
  *   quench schedule      Sec. II.B, Eq. (Linear-Quench)
+ *   field schedule       h_k = h s(k), the orthogonal quench named in Sec. VII
  *
  * Readings where the paper is silent (noise keying, sharing of one Gaussian per
  * time point between the two half-kicks, periodic boundaries, domain labels,
@@ -166,6 +167,29 @@ double xyo_temperature(int64_t k, int n_knots, const int64_t* ks, const double* 
 }
 
 /* Noise amplitude of one half-kick: (1/2) sqrt(2 eta k_B T) sqrt(dt), App. A.1. */
+/* Field schedule of the orthogonal quench (Sec. VII names quenches that cross
+ * the phase boundary T_c(h) of App. D at an angle): h_k = h s(k), with s
+ * piecewise linear through (ks[i], ss[i]) and constant outside them; n = 0
+ * means s = 1. */
+double xyo_field_scale(int64_t k, int n, const int64_t* ks, const double* ss)
+{
+    if (n <= 0) return 1.0;
+    if (k <= ks[0]) return ss[0];
+    for (int i = 0; i + 1 < n; ++i)
+        if (k <= ks[i + 1]) {
+            double f = (double)(k - ks[i]) / (double)(ks[i + 1] - ks[i]);
+            return ss[i] + (ss[i + 1] - ss[i]) * f;
+        }
+    return ss[n - 1];
+}
+
+/* The parameter vector of time point k: h replaced by h s(k). */
+static void params_at(const double* prm, int64_t k, int nf, const int64_t* fks, const double* fss, double* out)
+{
+    memcpy(out, prm, sizeof(double) * P_COUNT);
+    out[P_H] = prm[P_H] * xyo_field_scale(k, nf, fks, fss);
+}
+
 static double half_kick_amp(double eta, double T, double dt)
 {
     return 0.5 * sqrt(2.0 * eta * T) * sqrt(dt);
@@ -286,6 +310,7 @@ static void lattice_force_cb(const void* ctx, const double* x, double* F)
  * Returns the number of records written. */
 int64_t xyo_run_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const double* prm,
                         int n_knots, const int64_t* knot_step, const double* knot_T,
+                        int nf, const int64_t* fks, const double* fss,
                         int64_t k0, int64_t n, double* theta, double* omega,
                         int record_every, double* rec)
 {
@@ -295,20 +320,25 @@ int64_t xyo_run_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const d
     double* nz0 = (double*)malloc(sizeof(double) * N);
     double* nz1 = (double*)malloc(sizeof(double) * N);
     double* wh = (double*)malloc(sizeof(double) * N);
-    lattice_ctx ctx = { Lx, Ly, prm };
+    double prm_k[P_COUNT], prm_next[P_COUNT];  /* the field of time points k and k + 1 */
+    lattice_ctx ctx = { Lx, Ly, prm_next };
     int64_t nrec = 0;
 
-    xyo_force(Lx, Ly, prm, theta, F);
+    params_at(prm, k0, nf, fks, fss, prm_k);
+    xyo_force(Lx, Ly, prm_k, theta, F);
     gauss_field(seed, cfg, rep, N, k0, nz0);
     for (int64_t j = 0; j < n; ++j) {
         int64_t k = k0 + j;
+        params_at(prm, k, nf, fks, fss, prm_k);
         if (record_every > 0 && k % record_every == 0) {
-            xyo_observe(Lx, Ly, prm, theta, omega, &rec[2 * nrec], &rec[2 * nrec + 1]);
+            xyo_observe(Lx, Ly, prm_k, theta, omega, &rec[2 * nrec], &rec[2 * nrec + 1]);
             ++nrec;
         }
         gauss_field(seed, cfg, rep, N, k + 1, nz1);
         double amp0 = half_kick_amp(eta, xyo_temperature(k, n_knots, knot_step, knot_T), dt);
         double amp1 = half_kick_amp(eta, xyo_temperature(k + 1, n_knots, knot_step, knot_T), dt);
+        /* the force at the new position belongs to time point k + 1 */
+        params_at(prm, k + 1, nf, fks, fss, prm_next);
         bbk_step(N, theta, omega, F, nz0, nz1, amp0, amp1, eta, dt, 1, lattice_force_cb, &ctx, wh);
         double* t = nz0; nz0 = nz1; nz1 = t;
     }
@@ -478,6 +508,7 @@ static void observation_grad(int Lx, int Ly, const double* prm, const double* th
  * theta_out/omega_out (nullable) receive the final state. */
 void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const double* prm,
                          int n_knots, const int64_t* knot_step, const double* knot_T,
+                         int nf, const int64_t* fks, const double* fss,
                          int64_t k0, int64_t n, const double* theta0, const double* omega0,
                          double wE, double wM, double* obj_out, double* grad,
                          double* theta_out, double* omega_out)
@@ -493,9 +524,12 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
     double* wh = (double*)malloc(sizeof(double) * N * (n > 0 ? n : 1));
     double* amp = (double*)malloc(sizeof(double) * (n + 1));
 
+    /* the parameters of every time point k0 .. k0 + n (the field h s(k)) */
+    double* prmj = (double*)malloc(sizeof(double) * P_COUNT * (n + 1));
+    for (int64_t j = 0; j <= n; ++j) params_at(prm, k0 + j, nf, fks, fss, prmj + P_COUNT * j);
     memcpy(th, theta0, sizeof(double) * N);
     memcpy(om, omega0, sizeof(double) * N);
-    xyo_force(Lx, Ly, prm, th, F);
+    xyo_force(Lx, Ly, prmj, th, F);
     for (int64_t j = 0; j <= n; ++j) {
         gauss_field(seed, cfg, rep, N, k0 + j, nz + N * j);
         amp[j] = half_kick_amp(eta, xyo_temperature(k0 + j, n_knots, knot_step, knot_T), dt);
@@ -507,10 +541,10 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
         double* h = wh + N * j;
         for (int64_t i = 0; i < N; ++i) h[i] = (1.0 - a) * w0[i] + 0.5 * dt * F0[i] + amp[j] * z0[i];
         for (int64_t i = 0; i < N; ++i) t1[i] = xyo_wrap(t0[i] + h[i] * dt);
-        xyo_force(Lx, Ly, prm, t1, F1);
+        xyo_force(Lx, Ly, prmj + P_COUNT * (j + 1), t1, F1);
         for (int64_t i = 0; i < N; ++i) w1[i] = (h[i] + 0.5 * dt * F1[i] + amp[j + 1] * z1[i]) / (1.0 + a);
         double M, E;
-        xyo_observe(Lx, Ly, prm, t1, w1, &M, &E);
+        xyo_observe(Lx, Ly, prmj + P_COUNT * (j + 1), t1, w1, &M, &E);
         obj += wE * E + wM * fabs(M);
     }
 
@@ -524,9 +558,11 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
         double *t0 = th + N * j, *w0 = om + N * j, *z0 = nz + N * j;
         double *t1 = th + N * (j + 1), *w1 = om + N * (j + 1), *z1 = nz + N * (j + 1);
         double gp[3] = { 0.0, 0.0, 0.0 };
+        const double* p1 = prmj + P_COUNT * (j + 1);  /* parameters of time point j + 1 */
+        double s1 = xyo_field_scale(k0 + j + 1, nf, fks, fss);  /* d h_{j+1} / d h */
         /* observation at j+1 */
-        observation_grad(Lx, Ly, prm, t1, w1, wE, wM, tb, wb, gp);
-        gJx += gp[0]; gJy += gp[1]; gh += gp[2];
+        observation_grad(Lx, Ly, p1, t1, w1, wE, wM, tb, wb, gp);
+        gJx += gp[0]; gJy += gp[1]; gh += gp[2] * s1;
         /* omega_{j+1} = b (wh_j + dt/2 F_{j+1} + amp_{j+1} n_{j+1}) */
         double ampb = 0.0;
         for (int64_t i = 0; i < N; ++i) {
@@ -537,11 +573,11 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
         }
         geta_amp += ampb * (eta > 0.0 ? amp[j + 1] / (2.0 * eta) : 0.0);
         /* F_{j+1} = F(theta_{j+1}) */
-        force_jacobian_T(Lx, Ly, prm, t1, Fb, tb);
+        force_jacobian_T(Lx, Ly, p1, t1, Fb, tb);
         for (int64_t i = 0; i < N; ++i) {
             double d[3];
-            force_param_derivs(Lx, Ly, prm, t1, i, d);
-            gJx += Fb[i] * d[0]; gJy += Fb[i] * d[1]; gh += Fb[i] * d[2];
+            force_param_derivs(Lx, Ly, p1, t1, i, d);
+            gJx += Fb[i] * d[0]; gJy += Fb[i] * d[1]; gh += Fb[i] * d[2] * s1;
         }
         /* theta_{j+1} = wrap(theta_j + dt wh_j) */
         for (int64_t i = 0; i < N; ++i) hb[i] += dt * tb[i];
@@ -557,10 +593,11 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
         (void)t0;
     }
     /* F_{k0} = F(theta_{k0}; params): theta_{k0} is fixed, the parameters are not */
+    double s0 = xyo_field_scale(k0, nf, fks, fss);
     for (int64_t i = 0; i < N; ++i) {
         double d[3];
-        force_param_derivs(Lx, Ly, prm, th, i, d);
-        gJx += Fb[i] * d[0]; gJy += Fb[i] * d[1]; gh += Fb[i] * d[2];
+        force_param_derivs(Lx, Ly, prmj, th, i, d);
+        gJx += Fb[i] * d[0]; gJy += Fb[i] * d[1]; gh += Fb[i] * d[2] * s0;
     }
     grad[0] = gJx;
     grad[1] = gJy;
@@ -569,7 +606,7 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
     *obj_out = obj;
     if (theta_out) memcpy(theta_out, th + N * n, sizeof(double) * N);
     if (omega_out) memcpy(omega_out, om + N * n, sizeof(double) * N);
-    free(th); free(om); free(F); free(nz); free(wh); free(amp);
+    free(th); free(om); free(F); free(nz); free(wh); free(amp); free(prmj);
     free(tb); free(wb); free(Fb); free(hb);
 }
 
@@ -601,6 +638,7 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
  * fields of the first target, [n][N] each, lt_out[j - 1] and lv_out[j]. */
 void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, const double* prm,
                            int n_knots, const int64_t* knot_step, const double* knot_T,
+                           int nf, const int64_t* fks, const double* fss,
                            int64_t k0, int64_t n, const double* theta0, const double* omega0,
                            int n_targets, const int64_t* targets, const double* wt, const double* wv,
                            double* out, double* traj_theta, double* traj_omega,
@@ -617,9 +655,11 @@ void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, cons
     double* z1 = (double*)malloc(sizeof(double) * N);
     double* wh = (double*)malloc(sizeof(double) * N);
 
+    double* prmj = (double*)malloc(sizeof(double) * P_COUNT * (n + 1));
+    for (int64_t j = 0; j <= n; ++j) params_at(prm, k0 + j, nf, fks, fss, prmj + P_COUNT * j);
     memcpy(th, theta0, sizeof(double) * N);
     memcpy(om, omega0, sizeof(double) * N);
-    xyo_force(Lx, Ly, prm, th, F);
+    xyo_force(Lx, Ly, prmj, th, F);
     gauss_field(seed, cfg, rep, N, k0, z0);
     for (int64_t j = 0; j < n; ++j) {
         double *t0 = th + N * j, *w0 = om + N * j, *t1 = th + N * (j + 1), *w1 = om + N * (j + 1);
@@ -628,7 +668,7 @@ void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, cons
         gauss_field(seed, cfg, rep, N, k0 + j + 1, z1);
         for (int64_t i = 0; i < N; ++i) wh[i] = (1.0 - a) * w0[i] + 0.5 * dt * F[i] + amp0 * z0[i];
         for (int64_t i = 0; i < N; ++i) t1[i] = xyo_wrap(t0[i] + wh[i] * dt);
-        xyo_force(Lx, Ly, prm, t1, F1);
+        xyo_force(Lx, Ly, prmj + P_COUNT * (j + 1), t1, F1);
         for (int64_t i = 0; i < N; ++i) w1[i] = (wh[i] + 0.5 * dt * F1[i] + amp1 * z1[i]) / (1.0 + a);
         double* tmp = F; F = F1; F1 = tmp;
         tmp = z0; z0 = z1; z1 = tmp;
@@ -655,7 +695,7 @@ void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, cons
                 Fb[i] += wb[i] * b * 0.5 * dt;
             }
             /* F_{j+1} = F(theta_{j+1}): tb is now the whole adjoint of theta_{j+1} */
-            force_jacobian_T(Lx, Ly, prm, t1, Fb, tb);
+            force_jacobian_T(Lx, Ly, prmj + P_COUNT * (j + 1), t1, Fb, tb);
             for (int64_t i = 0; i < N; ++i) {
                 double w = wt ? wt[N * j + i] : 1.0;
                 s1 += fabs(tb[i]) * w;
@@ -680,7 +720,7 @@ void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, cons
         out[2 * t] = s1;
         out[2 * t + 1] = sqrt(s2);
     }
-    free(th); free(om); free(F); free(F1); free(z0); free(z1); free(wh);
+    free(th); free(om); free(F); free(F1); free(z0); free(z1); free(wh); free(prmj);
     free(tb); free(wb); free(Fb); free(hb);
 }
 

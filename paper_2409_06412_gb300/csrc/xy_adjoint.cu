@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
     const int64_t k = A.k;
     if (threadIdx.x == 0) s_c = noise_amp(cf, k);
     __syncthreads();
-    const StepConst K = step_const(cf, s_c);
+    const StepConst K = step_const_k(cf, k, s_c);
+    const float hk = field_h(cf, k);
     const int64_t nq_lat = cf.N / 4;
     const int bpl = (int)((nq_lat + blockDim.x - 1) / blockDim.x);
     const int rep = blockIdx.x / bpl;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
                 float e = __fmul_rn(0.5f, __fmul_rn(om, om));
                 e = fmaf(-cf.Jx, bx, e);
                 e = fmaf(-cf.Jy, by, e);
-                e = fmaf(cf.h, cp, e);
+                e = fmaf(hk, cp, e);
                 eacc = fmaf(wE * invN, e, eacc);
             }
             float vbk = 0.f;
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
     }
     // block sums in FP64, fixed order; per-block accumulators across steps
     const double ceta = cf.eta_d > 0.0 ? (double)K.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
-    double vals[kGacc] = {aJx, aJy, ah, abar, bbar, (double)cbar * ceta, eacc};
+    // with a field schedule the field of step k is h s(k): d/dh of its terms carries s(k)
+    double vals[kGacc] = {aJx, aJy, (double)ah * field_scale(cf, k), abar, bbar, (double)cbar * ceta, eacc};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < kGacc; ++q) {
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_b_kernel(const DevCfg* cfgs
         const float hx = fmaf(kL, fL - fj, kR * (fR - fj));
         const float hy = fmaf(kU, f.tu[i] - fj, kD * (f.td[i] - fj));
         float acc = q2 * fmaf(cf.Jx, hx, cf.Jy * hy);
-        acc = fmaf(cf.hp * cf.p, __cosf(__fmul_rn(cf.p, t.t[i])) * fj, acc);
+        acc = fmaf(field_hp(cf, A.k) * cf.p, __cosf(__fmul_rn(cf.p, t.t[i])) * fj, acc);
         out[i] = __fadd_rn(f4get(tb4, i), acc);
     }
     st4(A.tb + lat_off + 4 * quad, make_float4(out[0], out[1], out[2], out[3]));
@@ -322,8 +324,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     const float* vbI = R.vb_in + lat_off;
     float* tbO = R.tb_out + lat_off;
     float* vbO = R.vb_out + lat_off;
-    const StepConst K = step_const(cf, noise_amp(cf, R.k));
-    const float q2 = __fmul_rn(K.q, K.q), hp2 = __fmul_rn(cf.hp, cf.p);
+    const StepConst K = step_const_k(cf, R.k, noise_amp(cf, R.k));
+    const float q2 = __fmul_rn(K.q, K.q), hp2 = __fmul_rn(K.hp, cf.p);
     const float invN = 1.0f / (float)cf.N, wE = R.wE, wM = R.wM;
     constexpr bool observe = OBS, first = !OBS;
     const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     }
     // configuration constants in registers (the cp.async statements clobber
     // memory, which would otherwise reload them from the descriptor every row)
-    const float Jx = cf.Jx, Jy = cf.Jy, hF = cf.h;
+    const float Jx = cf.Jx, Jy = cf.Jy, hF = field_h(cf, R.k);
     const float q2Jx = q2 * Jx, q2Jy = q2 * Jy;
     const bool stag = cf.stag != 0;
     const float wEn = wE * invN, wMs = wM * invN * sgnM * K.q;
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     const float vals[kGacc] = {
         fmaf(-K.q, aJx, -wEn * sbx),                                        // d/d J_par
         fmaf(-K.q, aJy, -wEn * sby),                                        // d/d J_perp
-        fmaf(K.p, ah, wEn * scp),                                           // d/d h
+        fmaf(K.p, ah, wEn * scp) * field_scale(cf, R.k),                    // d/d h (h_k = h s(k))
         abar, bbar, cbar,
         wEn * fmaf(0.5f, sw2, fmaf(-Jx, sbx, fmaf(-Jy, sby, hF * scp))),  // w_E E / N
     };

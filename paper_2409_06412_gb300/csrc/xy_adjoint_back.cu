@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     const float* vbI = R.vb_in + lat_off;
     float* tbO = R.tb_out + lat_off;
     float* vbO = R.vb_out + lat_off;
-    const StepConst K = step_const(cf, noise_amp(cf, R.k));
-    const float q2 = K.q * K.q, hp2 = cf.hp * cf.p;
+    const StepConst K = step_const_k(cf, R.k, noise_amp(cf, R.k));
+    const float q2 = K.q * K.q, hp2 = K.hp * cf.p;
     const float invN = 1.0f / (float)cf.N, wE = R.wE;
     constexpr bool observe = OBS, first = !OBS;
     const uint32_t cfgrep = ((uint32_t)cf.noise_cfg << 16) | (uint32_t)(cf.rep0 + task.rep);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     }
     // configuration constants in registers (the cp.async statements clobber
     // memory, which would otherwise reload them from the descriptor every row)
-    const float Jx = cf.Jx, Jy = cf.Jy, hF = cf.h;
+    const float Jx = cf.Jx, Jy = cf.Jy, hF = field_h(cf, R.k);
     const float q2Jx = q2 * Jx, q2Jy = q2 * Jy;
     const bool stag = cf.stag != 0;
     const float wEn = wE * invN;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     const float vals[kGacc + 1] = {
         fmaf(-K.q, aJx, -wEn * sbx),                                        // d/d J_par
         fmaf(-K.q, aJy, -wEn * sby),                                        // d/d J_perp
-        fmaf(K.p, ah, wEn * scp),                                           // d/d h
+        fmaf(K.p, ah, wEn * scp) * field_scale(cf, R.k),                    // d/d h (h_k = h s(k))
         abar, bbar, cbar,
         wEn * fmaf(0.5f, sw2, fmaf(-Jx, sbx, fmaf(-Jy, sby, hF * scp))),  // w_E E / N
         pm,                                                                 // sum of sigma sin(q theta_k)

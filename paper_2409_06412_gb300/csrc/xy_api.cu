@@ -51,6 +51,9 @@ struct CfgHost {
     int64_t n_total = 0;
     int64_t step = 0;
     bool primed = false;
+    int f_n_knots = 0;  // field schedule s(k): h_k = h s(k)
+    int64_t f_knot_step[XY_MAX_KNOTS] = {};
+    double f_knot_s[XY_MAX_KNOTS] = {};
     int kind = 2;   // 0 resident, 1 strip, 2 plain (inside the batched path)
     int H = 0;      // strip rows per row group
 };
@@ -295,6 +298,25 @@ void fill_params(DevCfg& d, const xy_params& p)
     // site energies minus it, which at and below T_c are ~10x smaller than
     // the energies themselves, and so are their FP32 roundings
     d.e_ref = (float)(-(std::fabs(p.J_par) + std::fabs(p.J_perp) + std::fabs(p.h)));
+}
+
+// FP32 field schedule of the device record and the energy reference: the
+// potential part of a site's energy is >= -(|J_par| + |J_perp| + |h| max|s|).
+void fill_field_f32(DevCfg& d, const CfgHost& h)
+{
+    d.f_n_knots = h.f_n_knots;
+    double smax = h.f_n_knots == 0 ? 1.0 : 0.0;
+    for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+        const bool on = i < h.f_n_knots;
+        d.f_knot_step[i] = on ? h.f_knot_step[i] : 0;
+        d.f_knot_s[i] = on ? (float)h.f_knot_s[i] : 0.f;
+        d.f_slope[i] = (i + 1 < h.f_n_knots)
+                           ? (float)((h.f_knot_s[i + 1] - h.f_knot_s[i]) / (double)(h.f_knot_step[i + 1] - h.f_knot_step[i]))
+                           : 0.f;
+        if (on) smax = std::max(smax, std::fabs(h.f_knot_s[i]));
+    }
+    if (h.has_prm)
+        d.e_ref = (float)(-(std::fabs(h.prm.J_par) + std::fabs(h.prm.J_perp) + std::fabs(h.prm.h) * smax));
 }
 
 void fill_schedule_f32(DevCfg& d)
@@ -1488,6 +1510,27 @@ int xy_set_params(xy_lattice* L, int c, const xy_params* p)
     L->cfg[c].prm = *p;
     L->cfg[c].has_prm = true;
     fill_params(L->h_dev[c], *p);
+    fill_field_f32(L->h_dev[c], L->cfg[c]);
+    return XY_OK;
+}
+
+int xy_set_field_schedule(xy_lattice* L, int c, const int64_t* ks, const double* ss, int n_knots)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (c < 0 || c >= L->n_cfg) return fail(XY_EINVAL, "configuration %d out of range", c);
+    if (n_knots < 0 || n_knots > XY_MAX_KNOTS) return fail(XY_EINVAL, "0..%d knots", XY_MAX_KNOTS);
+    if (n_knots > 0 && (!ks || !ss)) return fail(XY_EINVAL, "NULL knots");
+    for (int i = 0; i < n_knots; ++i) {
+        if (!std::isfinite(ss[i])) return fail(XY_EINVAL, "field scales must be finite");
+        if (i > 0 && ks[i] <= ks[i - 1]) return fail(XY_EINVAL, "knot steps must increase strictly");
+    }
+    CfgHost& h = L->cfg[c];
+    h.f_n_knots = n_knots;
+    for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+        h.f_knot_step[i] = i < n_knots ? ks[i] : 0;
+        h.f_knot_s[i] = i < n_knots ? ss[i] : 0.0;
+    }
+    fill_field_f32(L->h_dev[c], h);
     return XY_OK;
 }
 
@@ -2362,6 +2405,9 @@ struct SnapCfg {
     double knot_T[XY_MAX_KNOTS];
     int64_t sched_kind;
     double pw[6];
+    int64_t f_n_knots;
+    int64_t f_knot_step[XY_MAX_KNOTS];
+    double f_knot_s[XY_MAX_KNOTS];
 };
 }  // namespace
 
@@ -2381,7 +2427,7 @@ int xy_save(xy_lattice* L, void* buf, size_t* size)
     char* p = (char*)buf;
     SnapHeader hd{};
     std::memcpy(hd.magic, "XYLATT1", 8);
-    hd.version = 2;
+    hd.version = 3;
     hd.n_cfg = L->n_cfg;
     hd.total = L->total_sites;
     hd.B = L->B;
@@ -2403,7 +2449,10 @@ int xy_save(xy_lattice* L, void* buf, size_t* size)
         for (int i = 0; i < XY_MAX_KNOTS; ++i) {
             s.knot_step[i] = h.knot_step[i];
             s.knot_T[i] = h.knot_T[i];
+            s.f_knot_step[i] = h.f_knot_step[i];
+            s.f_knot_s[i] = h.f_knot_s[i];
         }
+        s.f_n_knots = h.f_n_knots;
         std::memcpy(p, &s, sizeof s);
         p += sizeof s;
     }
@@ -2427,7 +2476,7 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
     SnapHeader hd;
     std::memcpy(&hd, p, sizeof hd);
     p += sizeof hd;
-    if (std::memcmp(hd.magic, "XYLATT1", 8) != 0 || hd.version != 2) return fail(XY_EINVAL, "not a snapshot");
+    if (std::memcmp(hd.magic, "XYLATT1", 8) != 0 || hd.version != 3) return fail(XY_EINVAL, "not a snapshot");
     if (hd.n_cfg != L->n_cfg || hd.total != L->total_sites || hd.B != L->B)
         return fail(XY_EINVAL, "snapshot shape does not match this lattice object");
     std::vector<SnapCfg> sc(L->n_cfg);
@@ -2463,6 +2512,12 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
         }
         fill_schedule_f32(d);
         fill_power_f32(d, h);
+        h.f_n_knots = (int)s.f_n_knots;
+        for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+            h.f_knot_step[i] = s.f_knot_step[i];
+            h.f_knot_s[i] = s.f_knot_s[i];
+        }
+        fill_field_f32(d, h);
     }
     CK(cudaMemcpyAsync(L->d_moments, p, sizeof(double) * 6 * L->n_cfg, cudaMemcpyHostToDevice, L->stream));
     p += sizeof(double) * 6 * L->n_cfg;

@@ -162,6 +162,26 @@ __device__ __forceinline__ float noise_amp(const DevCfg& cf, int64_t k)
     return __fmul_rn(cf.amp_pref, __fsqrt_rn(T > 0.f ? T : 0.f));
 }
 
+// Field schedule s(k) of the orthogonal quench: h_k = h s(k) (1 without one).
+__device__ __forceinline__ float field_scale(const DevCfg& cf, int64_t k)
+{
+    if (cf.f_n_knots <= 1 || k <= cf.f_knot_step[0]) return cf.f_n_knots == 0 ? 1.0f : cf.f_knot_s[0];
+    for (int i = 0; i + 1 < cf.f_n_knots; ++i)
+        if (k <= cf.f_knot_step[i + 1]) return fmaf(cf.f_slope[i], (float)(k - cf.f_knot_step[i]), cf.f_knot_s[i]);
+    return cf.f_knot_s[cf.f_n_knots - 1];
+}
+
+// h p and h at step k: the configuration's constants themselves without a
+// schedule (the same bits as before schedules existed), else scaled by s(k)
+__device__ __forceinline__ float field_hp(const DevCfg& cf, int64_t k)
+{
+    return cf.f_n_knots == 0 ? cf.hp : __fmul_rn(cf.hp, field_scale(cf, k));
+}
+__device__ __forceinline__ float field_h(const DevCfg& cf, int64_t k)
+{
+    return cf.f_n_knots == 0 ? cf.h : __fmul_rn(cf.h, field_scale(cf, k));
+}
+
 __device__ __forceinline__ StepConst step_const(const DevCfg& cf, float c)
 {
     StepConst s;
@@ -175,6 +195,14 @@ __device__ __forceinline__ StepConst step_const(const DevCfg& cf, float c)
     s.hp = cf.hp;
     s.q = cf.q;
     s.p = cf.p;
+    return s;
+}
+
+// The constants of step k: noise amplitude c_k and the field's h_k p.
+__device__ __forceinline__ StepConst step_const_k(const DevCfg& cf, int64_t k, float c)
+{
+    StepConst s = step_const(cf, c);
+    s.hp = field_hp(cf, k);
     return s;
 }
 
@@ -226,12 +254,13 @@ __device__ __forceinline__ float site_energy_rel(float omega, float bx, float by
     return fmaf(__fmul_rn(0.5f, omega), omega, e);
 }
 
-__device__ __forceinline__ float site_energy(const DevCfg& cf, float omega, float s, float c, float sR,
+// hk: the field at the recorded step (field_h)
+__device__ __forceinline__ float site_energy(const DevCfg& cf, float hk, float omega, float s, float c, float sR,
                                              float cR, float sD, float cD, float cosp)
 {
     const float bx = fmaf(c, cR, __fmul_rn(s, sR));
     const float by = fmaf(c, cD, __fmul_rn(s, sD));
-    return site_energy_rel(omega, bx, by, cosp, cf.Jx, cf.Jy, cf.h, cf.e_ref);
+    return site_energy_rel(omega, bx, by, cosp, cf.Jx, cf.Jy, hk, cf.e_ref);
 }
 
 // Asynchronous global -> shared copies (cp.async), issued by one lane for its

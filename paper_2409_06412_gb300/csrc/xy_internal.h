@@ -34,6 +34,14 @@ struct DevCfg {
     int64_t pw_kc;
     float pw_Tc, pw_inv_tq, pw_gamma, pw_ei, pw_ef, pad2;
     int64_t n_total;
+    // field schedule (the orthogonal quench): h_k = h s(k), s piecewise linear
+    // through (f_knot_step[i], f_knot_s[i]) and constant outside them, in FP32
+    // from per-segment slopes like T(k); f_n_knots = 0: s = 1 (no schedule)
+    int32_t f_n_knots;
+    float f_pad;
+    int64_t f_knot_step[XY_MAX_KNOTS];
+    float f_knot_s[XY_MAX_KNOTS];
+    float f_slope[XY_MAX_KNOTS];
     // per call
     int64_t k_start;    // step at the start of the current call
     int64_t n_call;     // steps this configuration takes in the current call

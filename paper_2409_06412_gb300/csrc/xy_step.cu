@@ -190,7 +190,7 @@ __global__ void prime_kernel(const DevCfg* cfgs, int c, float* theta, float* ome
     __shared__ float s_c;
     if (threadIdx.x == 0) s_c = noise_amp(cf, cf.k_start);
     __syncthreads();
-    const StepConst K = step_const(cf, s_c);
+    const StepConst K = step_const_k(cf, cf.k_start, s_c);
     const int64_t nq_lat = cf.N / 4;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nq_lat * cf.n_rep) return;
@@ -230,7 +230,7 @@ __global__ void omega_full_kernel(const DevCfg* cfgs, int c, int rep_first, int 
     __shared__ float s_c;
     if (threadIdx.x == 0) s_c = noise_amp(cf, cf.k_start);
     __syncthreads();
-    const StepConst K = step_const(cf, s_c);
+    const StepConst K = step_const_k(cf, cf.k_start, s_c);
     const int64_t nq_lat = cf.N / 4;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nq_lat * rep_count) return;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
     const int64_t k = cf.k_start + j + ca.k_shift;
     if (threadIdx.x == 0) s_c = noise_amp(cf, k);
     __syncthreads();
-    const StepConst K = step_const(cf, s_c);
+    const StepConst K = step_const_k(cf, k, s_c);
     const int64_t nq_lat = cf.N / 4;
     const int bpl = (int)((nq_lat + blockDim.x - 1) / blockDim.x);
     const int rep = blockIdx.x / bpl;
@@ -312,8 +312,8 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
                 const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
                 pm = fmaf(sigma, f.s[s], pm);
                 if (!ca.m_only)
-                    pe = __fadd_rn(pe, site_energy(cf, so.omega, f.s[s], f.c[s], f.sR[s], f.cR[s], f.sD[s],
-                                                   f.cD[s], cosp_of(K.p, f.th[s])));
+                    pe = __fadd_rn(pe, site_energy(cf, field_h(cf, k), so.omega, f.s[s], f.c[s], f.sR[s], f.cR[s],
+                                                   f.sD[s], f.cD[s], cosp_of(K.p, f.th[s])));
             }
         }
         if (write_state) {
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     if (j >= cf.n_call) return;
     StripCtx X;
     X.k = cf.k_start + j + ca.k_shift;
-    X.K = step_const(cf, noise_amp(cf, X.k));
+    X.K = step_const_k(cf, X.k, noise_amp(cf, X.k));
     X.Lx = cf.Lx;
     X.Ly = cf.Ly;
     const bool odd = !ca.fixed_parity && (j & 1) != 0;
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     if (REC > 0 && X.rec) {  // block-uniform
         X.Jx = cf.Jx;
         X.Jy = cf.Jy;
-        X.hF = cf.h;
+        X.hF = field_h(cf, X.k);
         X.eref = cf.e_ref;
         X.stag = cf.stag != 0;
         if (live) strip_rows<REC>(X, cf, keys, ybeg, H, s_stage[warp]);
@@ -708,8 +708,9 @@ __global__ void __launch_bounds__(256, MINB) band2_step_kernel(const DevCfg* cfg
         return;
     }
     const int64_t k = cf.k_start + j + ca.k_shift;
-    const StepConst K1 = step_const(cf, noise_amp(cf, k));
+    const StepConst K1 = step_const_k(cf, k, noise_amp(cf, k));
     const float c2 = noise_amp(cf, k + 1);
+    const float hp2 = field_hp(cf, k + 1);
     const int Lx = cf.Lx, Ly = cf.Ly;
     const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
     // a batch of steps holds an even number of pairs: pair p = j_local / 2 of it
@@ -786,6 +787,7 @@ __global__ void __launch_bounds__(256, MINB) band2_step_kernel(const DevCfg* cfg
             const uint32_t quad = (uint32_t)(((int64_t)b * Lx + x) >> 2);
             StepConst K2 = K1;
             K2.c = c2;
+            K2.hp = hp2;
             const float4 cn = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, k + 1, 0u), keys), c2);
             float4 to, vo;
             b2_update(K2, P1.s, P1.c, C1.th, C1.s, C1.c, N1.s, N1.c, C1.v, sL, cL, sR, cR, cn, to, vo);
@@ -983,6 +985,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
             const int64_t k = kbase + j;
             StepConst K = K0;
             K.c = const_T ? c_const : noise_amp(cf, k);
+            K.hp = field_hp(cf, k);
             const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
             const int par = (int)(j & 1);
             const size_t poff = (size_t)(2 * par) * NB * Lx;
@@ -1018,8 +1021,8 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                     const float sigma = (stag && ((x + s + gy) & 1)) ? -1.f : 1.f;
                     pm = fmaf(sigma, cur.s[s], pm);
                     if (!ca.m_only)
-                        pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
-                                                       cosp_of(K.p, th)));
+                        pe = __fadd_rn(pe, site_energy(cf, field_h(cf, k), so.omega, cur.s[s], cur.c[s], sr, cr,
+                                                       nxt.s[s], nxt.c[s], cosp_of(K.p, th)));
                 }
             }
             th4 = make_float4(to[0], to[1], to[2], to[3]);
@@ -1056,6 +1059,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
             const int64_t k = kbase + j;
             StepConst K = K0;
             K.c = const_T ? c_const : noise_amp(cf, k);
+            K.hp = field_hp(cf, k);
             const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
             const int par = (int)(j & 1);
             float2* e_top = s_exp + (size_t)(2 * par) * NB * Lx;
@@ -1111,8 +1115,8 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                         const float sigma = (stag && ((x + s + y_base + y) & 1)) ? -1.f : 1.f;
                         pm = fmaf(sigma, cur.s[s], pm);
                         if (!ca.m_only)
-                            pe = __fadd_rn(pe, site_energy(cf, so.omega, cur.s[s], cur.c[s], sr, cr, nxt.s[s], nxt.c[s],
-                                                           cosp_of(K.p, th)));
+                            pe = __fadd_rn(pe, site_energy(cf, field_h(cf, k), so.omega, cur.s[s], cur.c[s], sr, cr,
+                                                           nxt.s[s], nxt.c[s], cosp_of(K.p, th)));
                     }
                 }
                 st4(s_th + y * Lx + x, make_float4(to[0], to[1], to[2], to[3]));

@@ -29,6 +29,7 @@ class Config:
     n_total: int = 10**12
     cfg_id: int = -1      # configuration id in the noise counter (-1: position in the list)
     replica0: int = 0     # replica id of replica 0 in the noise counter
+    field: tuple | None = None  # ((steps), (scales)): field schedule h_k = h s(k) (xy_set_field_schedule)
 
     @property
     def sites(self) -> int:
@@ -73,6 +74,8 @@ class Lattice:
                 self.set_power_quench(ci, *c.knots["power"], n_total=c.n_total)
             else:
                 self.set_schedule(ci, c.knots[0], c.knots[1], c.n_total)
+            if c.field is not None:
+                self.set_field_schedule(ci, c.field[0], c.field[1])
 
     # ------------------------------------------------------------ setup
     def set_params(self, c: int, **kw):
@@ -94,6 +97,14 @@ class Lattice:
                          eps_f: float, n_total: int):
         L.call("xy_set_power_quench", self._h, c, float(T_c), int(k_cross), float(tau_Q), float(gamma),
                float(eps_i), float(eps_f), int(n_total))
+
+    def set_field_schedule(self, c: int, steps, scales):
+        """Field of step k = h s(k), s piecewise linear through (steps, scales);
+        empty lists remove the schedule."""
+        ks = np.ascontiguousarray(np.asarray(steps, dtype=np.int64))
+        ss = np.ascontiguousarray(np.asarray(scales, dtype=np.float64))
+        L.call("xy_set_field_schedule", self._h, c, ks.ctypes.data_as(ctypes.c_void_p),
+               ss.ctypes.data_as(ctypes.c_void_p), int(ks.size))
 
     def set_path(self, path: int):
         L.call("xy_set_path", self._h, path)

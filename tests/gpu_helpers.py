@@ -17,7 +17,7 @@ def gpu_config(spec: dict) -> Config:
     p = dict(spec["params"])
     return Config(Lx=spec["Lx"], Ly=spec["Ly"], n_replicas=spec["n_rep"], seed=spec["seed"],
                   init_mode=spec.get("init_mode", XY_INIT_USER), params=p, knots=spec["knots"],
-                  n_total=spec["n_total"])
+                  n_total=spec["n_total"], field=spec.get("field"))
 
 
 def make_pair(specs, thetas, omegas=None, path=None):
@@ -106,10 +106,10 @@ def box_muller_error(r: np.ndarray) -> np.ndarray:
     return ER1 / r + (ERR + ETRIG + 2 * U32) * r
 
 
-def _force_error(prm: dict) -> tuple[float, float]:
+def _force_error(prm: dict, smax: float = 1.0) -> tuple[float, float]:
     U = U32
     qJx, qJy = abs(prm["q"] * prm["J_par"]), abs(prm["q"] * prm["J_perp"])
-    hp = abs(prm["h"] * prm["p"])
+    hp = abs(prm["h"] * prm["p"]) * smax  # the largest field of a schedule h s(k)
     F_max = 2 * qJx + 2 * qJy + hp
     d_bond = 8 * ESC + 8 * U
     dF = (qJx * (1 + U) * d_bond + 2 * qJx * U + qJy * (1 + U) * d_bond + 2 * qJy * U
@@ -124,7 +124,11 @@ def local_error_weights(spec: dict, cfg: int, rep: int, k0: int, n: int, theta: 
     U = U32
     N = theta.shape[1]
     hdt, dt = 0.5 * prm["dt"], prm["dt"]
-    dF, F_max = _force_error(prm)
+    field = spec.get("field")
+    smax = max([1.0] if field is None else [abs(x) for x in field[1]])
+    dF, F_max = _force_error(prm, smax)
+    if field is not None:
+        dF += abs(prm["h"] * prm["p"]) * smax * 2 * U  # h p s(k): the scale and the product rounded
     amps = np.array([0.5 * math.sqrt(2.0 * prm["eta"] * max(oracle.temperature(k0 + j, spec["knots"]), 0.0) * dt)
                      for j in range(n + 1)])
     g_max = hdt * F_max + amps.max() * R_MAX
@@ -150,10 +154,10 @@ def first_order_bound(spec: dict, cfg: int, rep: int, k0: int, n: int, theta0, o
     uniform within their bounds."""
     Lx, Ly = spec["Lx"], spec["Ly"]
     _, tth, tom = oracle.theta_sensitivity(Lx, Ly, cfg, rep, spec["seed"], spec["params"], spec["knots"], k0, n,
-                                           theta0, omega0, [], trajectory=True)
+                                           theta0, omega0, [], trajectory=True, field=spec.get("field"))
     wt, wv = local_error_weights(spec, cfg, rep, k0, n, tth, tom)
     out = oracle.theta_sensitivity(Lx, Ly, cfg, rep, spec["seed"], spec["params"], spec["knots"], k0, n, theta0,
-                                   omega0, sites, wt=wt, wv=wv)
+                                   omega0, sites, wt=wt, wv=wv, field=spec.get("field"))
     return out[:, 0], out[:, 1] / math.sqrt(3.0)
 
 

@@ -103,6 +103,17 @@ def test_uneven_lengths_keep_one_step_per_launch():
     assert launches[STRIP2] > 0
 
 
+def test_two_steps_with_a_field_schedule():
+    """The two-step kernel takes each step's own field (h_k and h_{k+1} of a
+    ramp): the same bits as one step per launch."""
+    specs = [dict(s, field=([0, 60], [0.4, 2.2])) for s in _specs()]
+    two, ref = _pair(specs, seed=9)
+    for n in (64, 36):
+        two.step(n)
+        ref.step(n)
+    assert _same(two, ref)
+
+
 def test_temporal_blocking_rejects_bad_modes():
     from paper_2409_06412_gb300 import XYError
     two, _ = _pair(_specs())

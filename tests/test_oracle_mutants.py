@@ -25,6 +25,8 @@ msd = lambda P: P.test_benchmark_harmonic_msd(0.05, 1.0)
 adj_E = lambda P: P.test_adjoint_matches_finite_differences_smooth_field(1.0, 0.0)
 adj_M = lambda P: P.test_adjoint_matches_finite_differences_smooth_field(0.0, 1.0)
 sens = lambda P: P.test_theta_sensitivity_matches_finite_differences()
+fwd_field = lambda P: P.test_adjoint_forward_equals_stepper(([5, 30], [0.4, 2.5]))
+adj_field = lambda P: P.test_adjoint_with_field_schedule_matches_finite_differences()
 
 # name: (text in the oracle, planted replacement, pins of which one must fail)
 MUTANTS = {
@@ -76,6 +78,11 @@ MUTANTS = {
     "sensitivity_drops_drift": ("hb[i] += tb[i] * dt;", "hb[i] += tb[i] * 0.0;", [sens]),
     "sensitivity_damping_reverse": ("wb[i] = hb[i] * (1.0 - a);", "wb[i] = hb[i] * (1.0 + a);", [sens]),
     "sensitivity_second_kick_force": ("Fb[i] += wb[i] * b * 0.5 * dt;", "Fb[i] = wb[i] * b * 0.5 * dt;", [sens]),
+    "field_force_of_the_wrong_time_point": ("params_at(prm, k + 1, nf, fks, fss, prm_next);",
+                                            "params_at(prm, k, nf, fks, fss, prm_next);", [fwd_field]),
+    "field_adjoint_drops_the_profile": ("gh += gp[2] * s1;", "gh += gp[2];", [adj_field]),
+    "field_interpolation_reversed": ("return ss[i] + (ss[i + 1] - ss[i]) * f;", "return ss[i + 1] + (ss[i] - ss[i + 1]) * f;",
+                                     [lambda P: P.test_field_schedule_is_linear_interpolation()]),
 }
 
 

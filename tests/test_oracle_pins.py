@@ -492,7 +492,7 @@ def test_ccl_zero_angle_counts_as_up():
 # ----------------------------------------------------------------- adjoint
 
 
-def _fd_grad(Lx, Ly, prm, knots, n, th0, om0, wE, wM, rel=1e-5):
+def _fd_grad(Lx, Ly, prm, knots, n, th0, om0, wE, wM, rel=1e-5, field=None):
     names = ("J_par", "J_perp", "h", "eta")
     g = []
     for nm in names:
@@ -502,7 +502,7 @@ def _fd_grad(Lx, Ly, prm, knots, n, th0, om0, wE, wM, rel=1e-5):
         for s in (+1, -1):
             p2 = dict(prm)
             p2[nm] = base + s * eps
-            obj, _, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, p2, knots, 0, n, th0, om0, wE, wM)
+            obj, _, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, p2, knots, 0, n, th0, om0, wE, wM, field=field)
             vals.append(obj)
         g.append((vals[0] - vals[1]) / (2 * eps))
     return np.array(g)
@@ -535,19 +535,22 @@ def test_adjoint_matches_finite_differences_paper_field_low_T():
     assert np.allclose(grad, fd, rtol=1e-6, atol=1e-8 * max(1.0, np.abs(fd).max())), (grad, fd)
 
 
-def test_adjoint_forward_equals_stepper():
-    """The adjoint's forward trajectory and objective are the stepper's."""
+@pytest.mark.parametrize("field", [None, ([5, 30], [0.4, 2.5])])
+def test_adjoint_forward_equals_stepper(field):
+    """The adjoint's forward trajectory and objective are the stepper's (two
+    loops written apart; with a field schedule each must give every time
+    point its own field)."""
     Lx, Ly = 8, 8
     th0 = inputs.angles(1, Lx, Ly, 1)[0].astype(np.float64)
     om0 = np.zeros(Lx * Ly)
     knots = ([0], [inputs.T_C])
-    obj, grad, th1, om1 = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th0, om0, 0.6, 0.4)
+    obj, grad, th1, om1 = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th0, om0, 0.6, 0.4, field=field)
     th, om = th0.copy(), om0.copy()
-    oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th, om)
+    oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th, om, field=field)
     assert np.array_equal(th, th1) and np.array_equal(om, om1)
     # objective = sum over k = 1..n of the stepper's records
     th, om = th0.copy(), om0.copy()
-    rec = oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 41, th, om, 1)
+    rec = oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 41, th, om, 1, field=field)
     expect = (0.6 * rec[1:, 1] + 0.4 * np.abs(rec[1:, 0])).sum()
     assert obj == pytest.approx(expect, rel=1e-13)
 
@@ -695,3 +698,83 @@ def test_first_order_bound_holds_for_binary32_state_rounding():
     bound = oracle.theta_sensitivity(Lx, Ly, 0, 0, 3, prm, knots, 0, n, th0, om0, sites, wt=wt, wv=wv)[:, 0]
     assert np.all(d <= bound), (d / bound).max()
     assert d.max() > 1e-3 * bound.max()
+
+
+
+# ---------------------------------------------------------------- field schedule (orthogonal quench)
+
+
+def test_field_schedule_is_linear_interpolation():
+    """s(k) through the knots and constant outside them: numpy's interpolation
+    of the same knots, at the knots, between them and beyond both ends."""
+    field = ([10, 40, 41, 200], [0.5, 2.0, -1.0, 3.25])
+    ks = np.arange(-5, 260)
+    got = np.array([oracle.field_scale(int(k), field) for k in ks])
+    want = np.interp(ks.astype(np.float64), np.array(field[0], dtype=np.float64), np.array(field[1]))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+    assert oracle.field_scale(123, None) == 1.0
+
+
+def test_field_schedule_scales_the_field_exactly():
+    """A schedule of ones changes nothing, and a constant scale 2 with h = 1
+    is the run with h = 2 (h s(k) enters the force and the energy exactly)."""
+    Lx, Ly, n = 8, 6, 60
+    prm = dict(inputs.PAPER)
+    knots = ([0], [inputs.T_C])
+    th0 = inputs.angles(1, Lx, Ly, 4)[0].astype(np.float64)
+    runs = []
+    for p_, field in ((prm, None), (prm, ([0, 30], [1.0, 1.0])), (dict(prm, h=0.5), ([0], [2.0])),
+                      (dict(prm, h=1.0), None)):
+        th, om = th0.copy(), np.zeros(Lx * Ly)
+        rec = oracle.run_lattice(Lx, Ly, 0, 0, 7, p_, knots, 0, n, th, om, record_every=5, field=field)
+        runs.append((th, om, rec))
+    for a, b in ((0, 1), (2, 3)):
+        assert all(np.array_equal(x, y) for x, y in zip(runs[a], runs[b]))
+
+
+def test_single_angle_boltzmann_at_the_held_field():
+    """J = 0: a ramp of the field from 0.25 h to 2 h over 400 steps, then held:
+    the angles follow exp(-2 h cos(p theta) / T) of the field now applied."""
+    T, h = 1.0, 1.0
+    prm = dict(J_par=0.0, J_perp=0.0, h=h)
+    field = ([0, 400], [0.25, 2.0])
+    Lx, Ly = 32, 32
+    th = oracle.init_theta(Lx, Ly, 0, 0, 9, 0)
+    om = np.zeros(Lx * Ly)
+    oracle.run_lattice(Lx, Ly, 0, 0, 9, prm, ([0], [T]), 0, 900, th, om, field=field)
+    samples, k = [], 900
+    while k < 900 + 8000:
+        oracle.run_lattice(Lx, Ly, 0, 0, 9, prm, ([0], [T]), k, 40, th, om, field=field)
+        k += 40
+        samples.append(th.copy())
+    x = np.array(samples).ravel()
+    edges = np.linspace(-PI / 2, PI / 2, 41)
+    hist, _ = np.histogram(x, bins=edges)
+    dens = lambda t: math.exp(-2.0 * h * math.cos(2.5 * t) / T)
+    Z = integrate.quad(dens, -PI / 2, PI / 2)[0]
+    expect = np.array([integrate.quad(dens, a, b)[0] / Z for a, b in zip(edges[:-1], edges[1:])]) * x.size
+    z = (hist - expect) / np.sqrt(4 * expect)
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    # and not the distribution of the starting field 0.25 h
+    dens0 = lambda t: math.exp(-0.25 * h * math.cos(2.5 * t) / T)
+    Z0 = integrate.quad(dens0, -PI / 2, PI / 2)[0]
+    exp0 = np.array([integrate.quad(dens0, a, b)[0] / Z0 for a, b in zip(edges[:-1], edges[1:])]) * x.size
+    assert np.abs((hist - exp0) / np.sqrt(4 * exp0)).max() > 10.0
+
+
+def test_adjoint_with_field_schedule_matches_finite_differences():
+    """p = 2 (smooth) with a field ramp and a temperature ramp: d/dh at the
+    fixed profile s(k) and the other three components against central
+    differences."""
+    Lx, Ly = 6, 4
+    prm = dict(inputs.PAPER, J_par=2.0, J_perp=0.5, h=1.2, p=2.0, eta=0.8)
+    th0 = inputs.angles(1, Lx, Ly, 18)[0].astype(np.float64)
+    om0 = 0.3 * inputs.velocities(1, Lx, Ly, 18)[0].astype(np.float64)
+    knots = ([0, 150], [1.0, 0.5])
+    field = ([20, 120], [0.3, 1.7])
+    obj, grad, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, 150, th0, om0, 0.6, 0.4, field=field)
+    fd = _fd_grad(Lx, Ly, prm, knots, 150, th0, om0, 0.6, 0.4, field=field)
+    assert np.allclose(grad, fd, rtol=1e-6, atol=1e-7 * max(1.0, np.abs(fd).max())), (grad, fd)
+    # the schedule matters: without it d/dh differs
+    _, g1, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, 150, th0, om0, 0.6, 0.4)
+    assert abs(g1[2] - grad[2]) > 1e-3 * abs(grad[2])
