@@ -71,6 +71,9 @@ def _declare(L):
     L.xyo_field_scale.restype = d
     L.xyo_run_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64, vp, vp, i32, vp]
     L.xyo_run_lattice.restype = i64
+    L.xyo_run_strip.argtypes = [i32, i32, i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64,
+                                vp, vp, vp, i32, i32, i32, vp]
+    L.xyo_run_strip.restype = i64
     L.xyo_harmonic_msd.argtypes = [i64, i64, d, d, d, d, u64, vp]
     L.xyo_ccl.argtypes = [i32, i32, vp, vp]
     L.xyo_ccl.restype = i64
@@ -188,6 +191,29 @@ def run_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta, omega, reco
     rec = np.zeros((max(nrec_max, 1), 2), dtype=np.float64)
     nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks), _ptr(fss),
                                  k0, n, _ptr(theta), _ptr(omega), record_every, _ptr(rec))
+    return rec[:nrec].copy()
+
+
+def run_strip(Lx, Ly, y0, cfg, rep, seed, params, knots, k0, n, theta, omega, F, rows=None, record_every=0,
+              field=None):
+    """Advance one row strip of an Lx x Ly lattice in place (see
+    xyo_run_strip): theta, omega, F are (R, Lx) float64 buffers whose local
+    row i is global row (y0 + i) mod Ly, F holding F(theta) on entry.  Rows
+    that lose a neighbour become NaN, one per step at either end.  With
+    ``record_every``, returns the (n_rec, 2) raw sums over the local rows
+    ``rows`` = (r0, r1) of sigma sin(q theta) and of the site energy."""
+    prm = param_vector(params)
+    nk, ks, Ts = _knots(knots)
+    nf, fks, fss = _field(field)
+    for a in (theta, omega, F):
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == theta.shape
+    R = theta.shape[0]
+    assert theta.size == R * Lx
+    r0, r1 = (0, 0) if rows is None else rows
+    nrec_max = (n // record_every + 1) if record_every > 0 else 0
+    rec = np.zeros((max(nrec_max, 1), 2), dtype=np.float64)
+    nrec = lib().xyo_run_strip(Lx, Ly, y0, R, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks),
+                               _ptr(fss), k0, n, _ptr(theta), _ptr(omega), _ptr(F), r0, r1, record_every, _ptr(rec))
     return rec[:nrec].copy()
 
 

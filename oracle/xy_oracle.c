@@ -347,6 +347,107 @@ int64_t xyo_run_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const d
 }
 
 /* ------------------------------------------------------------------------- */
+/* One row strip of a lattice (the lattice split over workers along y)        */
+/* ------------------------------------------------------------------------- */
+
+/* Force on local row i of a strip buffer of R rows.  x is periodic; the rows
+ * above and below are the buffer's own rows i - 1 and i + 1, so rows 0 and
+ * R - 1, which lack one of them, get NaN.  The sum is taken in the order of
+ * xyo_force. */
+static void strip_force(int Lx, int R, const double* prm, const double* th, double* F)
+{
+    double jpar = prm[P_JPAR], jperp = prm[P_JPERP], hk = prm[P_H], p = prm[P_P], q = prm[P_Q];
+    for (int i = 0; i < R; ++i)
+        for (int x = 0; x < Lx; ++x) {
+            int64_t s = (int64_t)i * Lx + x;
+            if (i == 0 || i == R - 1) { F[s] = NAN; continue; }
+            const double* row = th + (int64_t)i * Lx;
+            double t = row[x];
+            double right = row[(x + 1) % Lx], left = row[(x + Lx - 1) % Lx];
+            double below = th[s + Lx], above = th[s - Lx];
+            double fx = sin(q * (t - right)) + sin(q * (t - left));
+            double fy = sin(q * (t - below)) + sin(q * (t - above));
+            F[s] = -q * jpar * fx - q * jperp * fy + hk * p * sin(p * t);
+        }
+}
+
+/* Advance one strip of an Lx x Ly lattice by n BBK steps.  Local row i of the
+ * buffers theta, omega, F (R rows of Lx) holds global row (y0 + i) mod Ly.
+ * Every site takes the noise of its global index and the arithmetic of
+ * xyo_run_lattice, so a site whose dependencies lie inside the buffer gets the
+ * bits of the whole-lattice run.  The state between steps is
+ * (theta_k, omega_k, F_k = F(theta_k)), the three arrays xyo_run_lattice
+ * carries from one step to the next; F must hold F_{k0} on entry.  Each step
+ * loses one row at either end (NaN, see strip_force): started from a buffer
+ * exact everywhere, after n steps omega and F are exact on local rows
+ * [n, R - n) and theta on [n - 1, R - n + 1).  With record_every > 0 the raw
+ * sums over local rows [r0, r1) of sigma_i sin(q t_i) and of the site energy
+ * (bonds to the forward neighbours x + 1 and y + 1, as xyo_observe counts
+ * them) are appended to rec as pairs at every step k with
+ * k % record_every == 0, before the step.  Returns the number of records. */
+int64_t xyo_run_strip(int Lx, int Ly, int y0, int R, int cfg, int rep, uint64_t seed, const double* prm,
+                      int n_knots, const int64_t* knot_step, const double* knot_T,
+                      int nf, const int64_t* fks, const double* fss,
+                      int64_t k0, int64_t n, double* theta, double* omega, double* F,
+                      int r0, int r1, int record_every, double* rec)
+{
+    int64_t M = (int64_t)R * Lx;
+    double eta = prm[P_ETA], dt = prm[P_DT];
+    double* nz0 = (double*)malloc(sizeof(double) * M);
+    double* nz1 = (double*)malloc(sizeof(double) * M);
+    double* wh = (double*)malloc(sizeof(double) * M);
+    double prm_k[P_COUNT];
+    int64_t nrec = 0;
+
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t k = k0 + j;
+        params_at(prm, k, nf, fks, fss, prm_k);
+        if (record_every > 0 && k % record_every == 0) {
+            int stag = prm_k[P_STAG] != 0.0;
+            double sm = 0.0, se = 0.0;
+            for (int i = r0; i < r1; ++i) {
+                int gy = (int)(((int64_t)y0 + i) % Ly);
+                for (int x = 0; x < Lx; ++x) {
+                    int64_t s = (int64_t)i * Lx + x;
+                    double sigma = (stag && ((x + gy) & 1)) ? -1.0 : 1.0;
+                    double t = theta[s];
+                    sm += sigma * sin(prm_k[P_Q] * t);
+                    se += 0.5 * omega[s] * omega[s]
+                        - prm_k[P_JPAR] * cos(prm_k[P_Q] * (t - theta[(int64_t)i * Lx + (x + 1) % Lx]))
+                        - prm_k[P_JPERP] * cos(prm_k[P_Q] * (t - theta[s + Lx]))
+                        + prm_k[P_H] * cos(prm_k[P_P] * t);
+                }
+            }
+            rec[2 * nrec] = sm;
+            rec[2 * nrec + 1] = se;
+            ++nrec;
+        }
+        /* n(t) and n(t + dt) of the global sites held here */
+        for (int i = 0; i < R; ++i) {
+            int64_t g0 = (((int64_t)y0 + i) % Ly) * Lx;
+            for (int x = 0; x < Lx; ++x) {
+                nz0[(int64_t)i * Lx + x] = xyo_gauss_site(seed, cfg, rep, (uint64_t)(g0 + x), k, 0);
+                nz1[(int64_t)i * Lx + x] = xyo_gauss_site(seed, cfg, rep, (uint64_t)(g0 + x), k + 1, 0);
+            }
+        }
+        double amp0 = half_kick_amp(eta, xyo_temperature(k, n_knots, knot_step, knot_T), dt);
+        double amp1 = half_kick_amp(eta, xyo_temperature(k + 1, n_knots, knot_step, knot_T), dt);
+        /* Eq. (BBK-1), the drift with the wrap, the force of time point k + 1,
+         * Eq. (BBK-2) */
+        for (int64_t s = 0; s < M; ++s)
+            wh[s] = (1.0 - 0.5 * eta * dt) * omega[s] + 0.5 * dt * F[s] + amp0 * nz0[s];
+        for (int64_t s = 0; s < M; ++s)
+            theta[s] = xyo_wrap(theta[s] + wh[s] * dt);
+        params_at(prm, k + 1, nf, fks, fss, prm_k);
+        strip_force(Lx, R, prm_k, theta, F);
+        for (int64_t s = 0; s < M; ++s)
+            omega[s] = (wh[s] + 0.5 * dt * F[s] + amp1 * nz1[s]) / (1.0 + 0.5 * eta * dt);
+    }
+    free(nz0); free(nz1); free(wh);
+    return nrec;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Benchmark 1 of App. A.2: thermal harmonic oscillators, V = w2 x^2 / 2      */
 /* ------------------------------------------------------------------------- */
 

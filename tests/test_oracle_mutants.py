@@ -28,6 +28,17 @@ sens = lambda P: P.test_theta_sensitivity_matches_finite_differences()
 fwd_field = lambda P: P.test_adjoint_forward_equals_stepper(([5, 30], [0.4, 2.5]))
 adj_field = lambda P: P.test_adjoint_with_field_schedule_matches_finite_differences()
 
+
+def strip(P):
+    """The split run against the whole lattice, both through P's oracle."""
+    from tests import test_strips
+    saved = test_strips.oracle
+    test_strips.oracle = P.oracle
+    try:
+        test_strips.test_split_run_equals_the_whole_lattice_bit_for_bit(8, 22, 3, 3, 10)
+    finally:
+        test_strips.oracle = saved
+
 # name: (text in the oracle, planted replacement, pins of which one must fail)
 MUTANTS = {
     "force_sign_J_par": ("F[i] = -q * Jx * fx - q * Jy * fy", "F[i] = q * Jx * fx - q * Jy * fy", [force]),
@@ -83,6 +94,10 @@ MUTANTS = {
     "field_adjoint_drops_the_profile": ("gh += gp[2] * s1;", "gh += gp[2];", [adj_field]),
     "field_interpolation_reversed": ("return ss[i] + (ss[i + 1] - ss[i]) * f;", "return ss[i + 1] + (ss[i] - ss[i + 1]) * f;",
                                      [lambda P: P.test_field_schedule_is_linear_interpolation()]),
+    "strip_noise_of_the_local_row": ("int64_t g0 = (((int64_t)y0 + i) % Ly) * Lx;", "int64_t g0 = (int64_t)i * Lx;",
+                                     [strip]),
+    "strip_force_drops_the_row_above": ("double fy = sin(q * (t - below)) + sin(q * (t - above));",
+                                        "double fy = sin(q * (t - below)) + sin(q * (t - below));", [strip]),
 }
 
 
