@@ -252,6 +252,11 @@ struct xy_lattice {
     std::vector<int> ev_class;
     size_t ev_used = 0;
     int64_t launches = 0;
+    // working memory of the domain labelling, kept between calls (grown on
+    // demand); its leading ccl_clean bytes are known to be zero
+    void* ccl_buf = nullptr;
+    int64_t ccl_bytes = 0;
+    int64_t ccl_clean = 0;
 };
 
 namespace {
@@ -1385,6 +1390,7 @@ void free_lattice(xy_lattice* L)
     cudaFree(L->pa.count);
     cudaFree(L->d_moments);
     cudaFree(L->rec_buf);
+    cudaFree(L->ccl_buf);
     cudaFree(L->d_err);
     if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
     for (int i = 0; i < xy_lattice::kBranches; ++i) {
@@ -1707,60 +1713,76 @@ int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, i
     const bool dev_lab = labels && is_device_ptr(labels);
     const bool dev_hist = hist && is_device_ptr(hist);
     const bool dev_ns = n_sizes && is_device_ptr(n_sizes);
-    // lattices per chunk: 12 bytes per site of scratch, capped at 512 MB
-    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(b_count, ((int64_t)512 << 20) / (12 * N + 8)));
-    int32_t *lab = nullptr, *sz = nullptr, *cnt = nullptr;
-    int64_t *hs = nullptr, *ns = nullptr;
-    auto cleanup = [&]() {
-        if (!dev_lab) cudaFree(lab);
-        cudaFree(sz);
-        cudaFree(cnt);
-        if (!dev_hist) cudaFree(hs);
-        cudaFree(ns);
-    };
-    cudaError_t e = cudaSuccess;
-    if (!dev_lab) e = cudaMalloc(&lab, sizeof(int32_t) * N * per);
-    if (e == cudaSuccess) e = cudaMalloc(&sz, sizeof(int32_t) * N * per);
-    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(int32_t) * (N + 1) * per);
-    if (e == cudaSuccess && hist && !dev_hist) e = cudaMalloc(&hs, sizeof(int64_t) * 2 * hist_cap * per);
-    if (e == cudaSuccess) e = cudaMalloc(&ns, sizeof(int64_t) * per);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        cleanup();
-        return fail(XY_ENOMEM, "labelling scratch: %s", cudaGetErrorString(e));
+    const bool want = hist || n_sizes;
+    // lattices per chunk: all of them unless the working memory would pass
+    // 4 GB or the chunk 2^31 - 1 sites; outputs that live on the host are
+    // staged behind the working memory
+    const int64_t stage1 = (dev_lab ? 0 : 4 * N) + (hist && !dev_hist ? 16 * hist_cap : 0) + (want ? 8 : 0);
+    const int64_t per_lat = ccl_scratch_bytes(Lx, Ly, 1, nullptr) + stage1;
+    int64_t per = std::min<int64_t>(b_count, std::max<int64_t>(1, ((int64_t)4 << 30) / per_lat));
+    per = std::min<int64_t>(per, std::max<int64_t>(1, INT32_MAX / N));
+    while (per > 1 && ccl_scratch_bytes(Lx, Ly, (int)per, nullptr) + stage1 * per + 1024 > ((int64_t)4 << 30)) --per;
+    int64_t zeroed = 0;
+    const int64_t work = ccl_scratch_bytes(Lx, Ly, (int)per, &zeroed);
+    const int64_t need = work + stage1 * per + 1024;
+    if (need > L->ccl_bytes) {
+        cudaFree(L->ccl_buf);
+        L->ccl_buf = nullptr;
+        L->ccl_bytes = 0;
+        if (cudaMalloc(&L->ccl_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            L->ccl_buf = nullptr;
+            return fail(XY_ENOMEM, "labelling working memory of %lld bytes", (long long)need);
+        }
+        L->ccl_bytes = need;
+        L->ccl_clean = 0;
     }
+    // the passes leave zero what they set; a larger layout than the last one,
+    // or a failed call, needs the clearing done here
+    if (zeroed > L->ccl_clean) CK(cudaMemsetAsync(L->ccl_buf, 0, zeroed, L->stream));
+    L->ccl_clean = 0;  // until this call has ended well
+    char* stage = static_cast<char*>(L->ccl_buf) + (work + 255) / 256 * 256;
+    int32_t* lab = dev_lab ? nullptr : reinterpret_cast<int32_t*>(stage);
+    int64_t* hs = reinterpret_cast<int64_t*>(stage + (dev_lab ? 0 : (4 * N * per + 255) / 256 * 256));
+    int64_t* ns = hs + (hist && !dev_hist ? 2 * hist_cap * per : 0);
+    const CclScratch scratch = ccl_scratch_carve(L->ccl_buf, Lx, Ly, (int)per);
     int rc = XY_OK;
+    cudaError_t e = cudaSuccess;
     CK(cudaMemsetAsync(L->d_err, 0, sizeof(int), L->stream));
     for (int64_t b0 = 0; b0 < b_count && rc == XY_OK; b0 += per) {
         const int nl = (int)std::min<int64_t>(per, b_count - b0);
         int32_t* lab_out = dev_lab ? labels + b0 * N : lab;
         int64_t* h_out = hist ? (dev_hist ? hist + b0 * hist_cap * 2 : hs) : nullptr;
+        int64_t* ns_out = n_sizes ? (dev_ns ? n_sizes + b0 : ns) : nullptr;
         if (h_out) e = cudaMemsetAsync(h_out, 0, sizeof(int64_t) * 2 * hist_cap * nl, L->stream);
         if (e == cudaSuccess)
-            e = launch_ccl(L->thA + site0 + b0 * N, Lx, Ly, nl, lab_out, sz, cnt, h_out, hist ? hist_cap : 0, ns,
-                           L->d_err, L->stream);
+            e = launch_ccl(L->thA + site0 + b0 * N, Lx, Ly, nl, lab_out, scratch, h_out,
+                           hist ? hist_cap : 0, ns_out, L->d_err, L->stream);
         if (e != cudaSuccess) {
             rc = fail(XY_ECUDA, "labelling: %s", cudaGetErrorString(e));
             break;
         }
-        L->launches += 5;
+        L->launches += want ? 5 : 3;
         if (labels && !dev_lab)
             e = cudaMemcpyAsync(labels + b0 * N, lab, sizeof(int32_t) * N * nl, cudaMemcpyDeviceToHost, L->stream);
         if (e == cudaSuccess && hist && !dev_hist)
             e = cudaMemcpyAsync(hist + b0 * hist_cap * 2, hs, sizeof(int64_t) * 2 * hist_cap * nl,
                                 cudaMemcpyDeviceToHost, L->stream);
-        if (e == cudaSuccess && n_sizes)
-            e = cudaMemcpyAsync(n_sizes + b0, ns, sizeof(int64_t) * nl,
-                                dev_ns ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, L->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+        if (e == cudaSuccess && n_sizes && !dev_ns)
+            e = cudaMemcpyAsync(n_sizes + b0, ns, sizeof(int64_t) * nl, cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess && b0 + per < b_count) e = cudaStreamSynchronize(L->stream);
         if (e != cudaSuccess) rc = fail(XY_ECUDA, "labelling: %s", cudaGetErrorString(e));
     }
     int err = 0;
     if (rc == XY_OK) {
-        if (cudaMemcpy(&err, L->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) err = XY_ECUDA;
-        cudaMemset(L->d_err, 0, sizeof(int));
+        if (cudaMemcpyAsync(&err, L->d_err, sizeof(int), cudaMemcpyDeviceToHost, L->stream) != cudaSuccess ||
+            cudaStreamSynchronize(L->stream) != cudaSuccess) {
+            cudaGetLastError();
+            err = XY_ECUDA;
+        }
+        cudaMemsetAsync(L->d_err, 0, sizeof(int), L->stream);
     }
-    cleanup();
+    if (!rc && !err) L->ccl_clean = zeroed;  // else some entries were left set
     if (rc) return rc;
     if (err == XY_EINVAL) return fail(XY_EINVAL, "a lattice has more distinct domain sizes than hist_cap");
     if (err) return fail(err, "labelling: a bounded union loop ran out of iterations");

@@ -7,11 +7,27 @@
 // Each site gets the smallest site index of its component, which makes the
 // labels unique and comparable bit for bit.
 //
-// Union-find in three passes (block-local union-find in shared memory, then
-// a global merge across tile borders and a flattening pass; unions always
-// link the larger root under the smaller, so every root is its component's
-// minimum), followed by a per-component size count and an ordered compaction
-// of the size histogram into (size, count) pairs.
+// Passes (unions always link the larger root under the smaller, so every
+// root is its component's minimum):
+//   tile    one warp per 32 x 32 tile: the rows' spins as 32-bit masks, runs
+//           of equal spin, union-find over the runs in shared memory; every
+//           site gets its tile root, and each piece its tile-local size.
+//           A piece that does not reach the tile's edge is a whole domain and
+//           goes into the size histogram at once; one that does goes on a
+//           short list (batch index, local size) for the merge.
+//   border  one warp per tile edge: one union in global memory per pair of
+//           runs that touch across the edge.
+//   sizes   the listed pieces add their local sizes at their global roots
+//           (and point their tile roots at them).
+//   flatten one warp per tile: every site points straight at its root; the
+//           domain roots among the edge pieces enter the histogram.
+//   compact the histogram's nonzero entries become (size, count) pairs in
+//           ascending order: sizes below 64 are scanned directly, larger ones
+//           through a bitmap with one bit per size.
+// The component sizes, the histogram counts and the bitmap are zero between
+// calls: the passes clear every entry they set, so no pass reads or clears
+// memory in proportion to the lattice beyond the labels themselves.
+#include <algorithm>
 #include <cstdint>
 
 #include "xy_internal.h"
@@ -21,6 +37,10 @@ namespace xy {
 namespace {
 
 constexpr int kMaxUnionIters = 1 << 22;
+constexpr unsigned kAll = 0xFFFFFFFFu;
+constexpr int kTileWarps = 4;      // tiles (warps) per block of the tile pass
+constexpr int kSmallSizes = 64;    // sizes counted in shared memory before the global histogram
+constexpr int kEdgeFlag = 1 << 16;  // added to a piece's size count for each of its runs on the tile edge
 
 }  // namespace
 
@@ -35,7 +55,17 @@ namespace {
 
 __device__ __forceinline__ bool spin_of(float t) { return t >= 0.0f; }
 
-__device__ __forceinline__ int find_root_global(const int32_t* L, int x, int limit, int* err)
+// Bit x set where a run of equal bits starts in the row mask m (bit 0 always),
+// over the tile's columns vm.
+__device__ __forceinline__ unsigned run_starts(unsigned m, unsigned vm) { return ((m ^ (m << 1)) | 1u) & vm; }
+
+// Column of the start of the run that holds column x.
+__device__ __forceinline__ int run_of(unsigned starts, int x) { return 31 - __clz(starts & ((2u << x) - 1u)); }
+
+// Root of x in the forest L (global memory), halving the path on the way:
+// each visited node is pointed at its grandparent, an ancestor, so concurrent
+// searches and links stay valid.
+__device__ __forceinline__ int find_root_global(int32_t* L, int x, int limit, int* err)
 {
     int p = *(volatile const int32_t*)&L[x];
     for (int it = 0; p != x; ++it) {
@@ -43,10 +73,19 @@ __device__ __forceinline__ int find_root_global(const int32_t* L, int x, int lim
             atomicExch(err, XY_ETIMEOUT);
             return x;
         }
-        x = p;
+        const int g = *(volatile const int32_t*)&L[p];
+        if (g == p) return p;
+        L[x] = g;
+        x = g;
         p = *(volatile const int32_t*)&L[x];
     }
     return x;
+}
+
+// The same search, out of line: the rare long walks of the flattening pass.
+__device__ __noinline__ int find_root_far(int32_t* L, int x, int limit, int* err)
+{
+    return find_root_global(L, x, limit, err);
 }
 
 // Link the components of a and b (global indices inside one lattice's label
@@ -70,209 +109,492 @@ __device__ void union_global(int32_t* L, int a, int b, int limit, int* err)
     atomicExch(err, XY_ETIMEOUT);
 }
 
-__device__ __forceinline__ int find_root_shared(const int* L, int x)
+// Tile-local site i = y * 32 + x lives at shared-memory word i + y (rows
+// padded to 33 words): lanes that each own a row and touch the same column
+// then hit 32 different banks.  Indices keep the site order; only the
+// address is padded.
+__device__ __forceinline__ int ph(int i) { return i + (i >> 5); }
+
+// Root of x in a tile's forest (padded layout), halving the path.
+__device__ __forceinline__ int find_root_tile(int* L, int x)
 {
-    int p = L[x];
+    int p = L[ph(x)];
     while (p != x) {
-        x = p;
-        p = L[x];
+        const int g = L[ph(p)];
+        if (g == p) return p;
+        L[ph(x)] = g;
+        x = g;
+        p = L[ph(x)];
     }
     return x;
 }
 
-// Link in shared memory, with a bound on the retries: every failed atomicMin
-// means another thread lowered the same label, so the loop ends long before
-// the bound in practice; reaching it sets XY_ETIMEOUT like the global loops
-// (the tile's forest stays valid, links only point at smaller indices).
-__device__ void union_shared(int* L, int a, int b, int* err)
+// The same search without writes: while lanes point their own run starts at
+// their roots, a halving step elsewhere could replace such a pointer with an
+// older ancestor.
+__device__ __forceinline__ int find_root_tile_ro(const int* L, int x)
+{
+    int p = L[ph(x)];
+    while (p != x) {
+        x = p;
+        p = L[ph(x)];
+    }
+    return x;
+}
+
+// Link in a tile's forest (padded layout), with a bound on the retries:
+// every failed atomicMin means another lane lowered the same entry, so the
+// loop ends long before the bound in practice; reaching it sets XY_ETIMEOUT
+// like the global loops (the forest stays valid, links only point at
+// smaller indices).
+__device__ void union_tile(int* L, int a, int b, int* err)
 {
     for (int it = 0; it < 4096 * 4; ++it) {
-        a = find_root_shared(L, a);
-        b = find_root_shared(L, b);
+        a = find_root_tile(L, a);
+        b = find_root_tile(L, b);
         if (a == b) return;
         if (a < b) {
             const int t = a;
             a = b;
             b = t;
         }
-        const int old = atomicMin(&L[a], b);
+        const int old = atomicMin(&L[ph(a)], b);
         if (old == a) return;
         a = old;
     }
     atomicExch(err, XY_ETIMEOUT);
 }
 
+// how_many more domains of size sz in lattice lat's histogram.  Small sizes
+// are hot (every tile has some): their counts are spread over s.copies
+// copies per lattice, picked by tile, and the compaction adds the copies.  A
+// larger size is marked in the bitmap by the first add that finds its count
+// at zero, so no lane reads a shared word.
+__device__ __forceinline__ void count_size(const CclScratch& s, int64_t N, int lat, int sz, int how_many, int tile)
+{
+    if (sz < kSmallSizes) {
+        atomicAdd(s.small + ((int64_t)lat * s.copies + tile % s.copies) * kSmallSizes + sz, how_many);
+    } else if (atomicAdd(s.counts + (int64_t)lat * (N + 1) + sz, how_many) == 0) {
+        atomicOr(s.bits + (int64_t)lat * s.words + (sz >> 5), 1u << (sz & 31));
+    }
+}
+
+// Shared memory of one tile: the forest over run starts (tile-local index
+// y * 32 + x at word ph(i); other entries unused), and the counts of small
+// sizes.  Once the forest is final, a root's own entry holds
+// -1 - (size + kEdgeFlag * edge runs) of its piece: every other run start
+// then points straight at its root, so the entry is free.
+struct TileSmem {
+    int P[32 * 33];
+    int H[kSmallSizes];
+};
+
 }  // namespace
 
-// Pass 1: one block per TW x TH tile, one thread per site; union-find on
-// tile-local indices (row-major in the tile, hence ordered like global
-// indices), result written as the global index of the local root.
-__global__ void ccl_local_kernel(const float* theta, int Lx, int Ly, int TW, int TH, int32_t* labels,
-                                 int* err)
+// Pass 1: one warp per tile of up to 32 x 32 sites (the last tile of a row or
+// column of tiles may be narrower).  Tile-local indices y * 32 + x order like
+// global indices, so a tile root is its piece's smallest site.
+__global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const float* __restrict__ theta, int Lx, int Ly,
+                                                                     int n_lat, int32_t* __restrict__ labels,
+                                                                     int want_sizes, CclScratch s, int* err)
 {
-    extern __shared__ int s_lab[];
-    const int tiles_x = Lx / TW, tiles_y = Ly / TH;
-    const int tiles = tiles_x * tiles_y;
-    const int lat = blockIdx.x / tiles;
-    const int tile = blockIdx.x - lat * tiles;
+    __shared__ TileSmem sm[kTileWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int tiles_x = (Lx + 31) >> 5, tiles_y = (Ly + 31) >> 5;
+    const int tiles = tiles_x * tiles_y;  // the batch has fewer than 2^31 sites
+    const int t = blockIdx.x * kTileWarps + wib;
+    if (t >= tiles * n_lat) return;  // a whole warp
+    const int lat = t / tiles;
+    const int tile = t - lat * tiles;
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const int lid = threadIdx.x;
-    const int ly = lid / TW, lx = lid - ly * TW;
-    const int gx = tx * TW + lx, gy = ty * TH + ly;
+    const int gx0 = tx * 32, gy0 = ty * 32;
+    const int tw = min(32, Lx - gx0), thh = min(32, Ly - gy0);
+    const unsigned vm = tw == 32 ? kAll : ((1u << tw) - 1u);
     const int64_t N = (int64_t)Lx * Ly;
-    const float* th = theta + (int64_t)lat * N;
-    const bool sp = spin_of(th[(int64_t)gy * Lx + gx]);
-    if (TW == 32) {
-        // a warp is one tile row: every site points at the first site of its
-        // run of equal spins (the run's smallest index), found with one
-        // ballot, and only vertical contacts need unions, one per pair of
-        // runs touching side by side
-        constexpr unsigned kAll = 0xFFFFFFFFu;
-        const bool spL = __shfl_up_sync(kAll, sp, 1);
-        const bool horiz = lx > 0 && sp == spL;  // same run as the left site
-        const unsigned starts = __ballot_sync(kAll, !horiz);
-        const unsigned upto = lx == 31 ? starts : (starts & ((2u << lx) - 1u));
-        s_lab[lid] = ly * 32 + (31 - __clz(upto));
-        __syncthreads();
-        if (ly + 1 < TH) {  // uniform in the warp
-            const bool vert = spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp;
-            const bool vertL = __shfl_up_sync(kAll, vert, 1);
-            if (vert && !(horiz && vertL)) union_shared(s_lab, lid, lid + 32, err);
-        }
-    } else {
-        s_lab[lid] = lid;
-        __syncthreads();
-        if (lx + 1 < TW && spin_of(th[(int64_t)gy * Lx + gx + 1]) == sp) union_shared(s_lab, lid, lid + 1, err);
-        if (ly + 1 < TH && spin_of(th[(int64_t)(gy + 1) * Lx + gx]) == sp) union_shared(s_lab, lid, lid + TW, err);
-    }
-    __syncthreads();
-    const int root = find_root_shared(s_lab, lid);
-    const int rly = root / TW, rlx = root - rly * TW;
-    labels[(int64_t)lat * N + (int64_t)gy * Lx + gx] = (int32_t)((ty * TH + rly) * Lx + tx * TW + rlx);
-}
+    const float* th = theta + (int64_t)lat * N + gy0 * Lx + gx0;
+    int32_t* lab = labels + (int64_t)lat * N + gy0 * Lx + gx0;
+    int* P = sm[wib].P;
+    int* H = sm[wib].H;
 
-// Pass 2: merge across the right and bottom border of every tile (periodic).
-// One thread per border site: the TH sites of a tile's right column (each
-// linked to its right neighbour) and the TW sites of its bottom row (each
-// linked to the site below); the corner does both.
-__global__ void ccl_border_kernel(const float* theta, int Lx, int Ly, int TW, int TH, int n_lat, int32_t* labels,
-                                  int* err)
-{
-    const int64_t N = (int64_t)Lx * Ly;
-    const int tiles_x = Lx / TW, tiles = tiles_x * (Ly / TH), per_tile = TH + TW;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n_lat * tiles * per_tile) return;
-    const int lat = (int)(i / ((int64_t)tiles * per_tile));
-    const int rem = (int)(i - (int64_t)lat * tiles * per_tile);
-    const int tile = rem / per_tile, k = rem - tile * per_tile;
-    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const bool right = k < TH;
-    const int y = right ? ty * TH + k : ty * TH + TH - 1;
-    const int x = right ? tx * TW + TW - 1 : tx * TW + (k - TH);
-    const int s = y * Lx + x;
-    const float* th = theta + (int64_t)lat * N;
-    int32_t* L = labels + (int64_t)lat * N;
-    const bool sp = spin_of(th[s]);
-    const int limit = g_union_limit;
-    const int n = right ? y * Lx + (x + 1 == Lx ? 0 : x + 1) : (y + 1 == Ly ? 0 : y + 1) * Lx + x;
-    if (spin_of(th[n]) == sp) union_global(L, s, n, limit, err);
-}
-
-// Pass 3: every site points straight at its root; count component sizes.
-__global__ void ccl_flatten_kernel(int64_t N, int n_lat, int32_t* labels, int32_t* sizes, int* err)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N * n_lat) return;
-    const int lat = (int)(i / N);
-    const int s = (int)(i - (int64_t)lat * N);
-    int32_t* L = labels + (int64_t)lat * N;
-    const int r = find_root_global(L, s, g_union_limit, err);
-    // lanes that found the same root of the same lattice add their count
-    // once (a large domain would otherwise serialise on one address)
-    const unsigned long long key = ((unsigned long long)(unsigned)lat << 32) | (unsigned)r;
-    const unsigned grp = __match_any_sync(__activemask(), key);
-    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&sizes[(int64_t)lat * N + r], __popc(grp));
-    // the final write happens after every find of this pass may have read L[s]
-    // as an intermediate node; writing the root keeps the forest valid.
-    L[s] = r;
-}
-
-// Pass 4: histogram of component sizes: count[size] over roots.  One thread
-// per quad of sites (Lx is a multiple of 4); the label buffer may be the
-// caller's and only 4-byte aligned, so the quad is read as four words.
-__global__ void ccl_size_hist_kernel(int64_t N, int n_lat, const int32_t* labels, const int32_t* sizes,
-                                     int32_t* counts)
-{
-    const int64_t nq = N / 4;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nq * n_lat) return;
-    const int lat = (int)(i / nq);
-    const int s0 = (int)(4 * (i - (int64_t)lat * nq));
-    const int32_t* lp = labels + (int64_t)lat * N + s0;
-    const int l4[4] = {lp[0], lp[1], lp[2], lp[3]};
+    // the rows' spins as masks (lane y keeps row y); all 32 loads in flight
+    float v[32];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (l4[k] != s0 + k) continue;
-        const int sz = sizes[(int64_t)lat * N + s0 + k];
-        atomicAdd(&counts[(int64_t)lat * (N + 1) + sz], 1);
+    for (int y = 0; y < 32; ++y) v[y] = (y < thh && lane < tw) ? th[y * Lx + lane] : 0.0f;
+    unsigned row = 0;
+#pragma unroll
+    for (int y = 0; y < 32; ++y) {
+        const unsigned m = __ballot_sync(kAll, spin_of(v[y])) & vm;
+        if (lane == y) row = m;
+    }
+    const unsigned st = run_starts(row, vm);  // lane y: the run starts of row y
+
+    // every run start is a root
+    for (unsigned b = st; b; b &= b - 1) {
+        const int i = lane * 32 + __ffs(b) - 1;
+        P[ph(i)] = i;
+    }
+    H[lane] = 0;
+    H[lane + 32] = 0;
+    __syncwarp();
+
+    // vertical contacts between rows y and y + 1 (lane y): one union per pair
+    // of runs, at the first column where they touch
+    {
+        const unsigned below = __shfl_down_sync(kAll, row, 1);
+        const unsigned sb = __shfl_down_sync(kAll, st, 1);
+        if (lane + 1 < thh) {
+            const unsigned c = ~(row ^ below) & vm;
+            unsigned u = c & ~((c << 1) & c & ~st & ~sb);
+            while (u) {
+                const int x = __ffs(u) - 1;
+                u &= u - 1;
+                union_tile(P, lane * 32 + run_of(st, x), (lane + 1) * 32 + run_of(sb, x), err);
+            }
+        }
+    }
+    __syncwarp();
+
+    // every run start points straight at its root: each lane writes only its
+    // own run starts, and only roots; the searches write nothing
+    unsigned roots = 0;  // lane y: the tile roots of row y
+    if (lane < thh) {
+        for (unsigned b = st; b; b &= b - 1) {
+            const int i = lane * 32 + __ffs(b) - 1;
+            const int r = find_root_tile_ro(P, i);
+            if (r != i)
+                P[ph(i)] = r;
+            else
+                roots |= 1u << (i & 31);
+        }
+    }
+    __syncwarp();
+    if (want_sizes) {
+        // a root's entry becomes its piece's count: -1 - (size + kEdgeFlag * edge runs)
+        for (unsigned b = roots; b; b &= b - 1) P[ph(lane * 32 + __ffs(b) - 1)] = -1;
+        __syncwarp();
+        if (lane < thh) {
+            for (unsigned b = st; b; b &= b - 1) {
+                const int x = __ffs(b) - 1;
+                const int i = lane * 32 + x;
+                const int q = P[ph(i)];
+                const int r = q < 0 ? i : q;
+                const unsigned later = b & (b - 1);
+                const int end = later ? __ffs(later) - 1 : tw;
+                const bool edge = lane == 0 || lane == thh - 1 || x == 0 || end == tw;
+                atomicSub(&P[ph(r)], (end - x) + (edge ? kEdgeFlag : 0));
+            }
+        }
+        __syncwarp();
+    }
+
+    // labels, a row at a time (coalesced): each site's root through its run start
+#pragma unroll 4
+    for (int y = 0; y < thh; ++y) {
+        const unsigned sy = __shfl_sync(kAll, st, y);
+        if (lane < tw) {
+            const int i = y * 32 + run_of(sy, lane);
+            const int q = P[y * 33 + (i & 31)];
+            const int r = q < 0 ? i : q;
+            lab[y * Lx + lane] = (gy0 + (r >> 5)) * Lx + gx0 + (r & 31);
+        }
+    }
+    if (!want_sizes) return;
+
+    // the pieces: whole domains into the histogram, edge pieces onto the list
+    int n_edge = 0;
+    for (unsigned b = roots; b; b &= b - 1) n_edge += -1 - P[lane * 33 + __ffs(b) - 1] >= kEdgeFlag;
+    int before = n_edge;  // inclusive prefix over the lanes
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(kAll, before, d);
+        if (lane >= d) before += o;
+    }
+    const int total = __shfl_sync(kAll, before, 31);
+    int base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(s.list_n, total);
+    base = __shfl_sync(kAll, base, 31) + before - n_edge;
+    unsigned emask = 0;  // lane y: the roots of row y whose piece reaches the tile's edge
+    for (unsigned b = roots; b; b &= b - 1) {
+        const int x = __ffs(b) - 1;
+        const int c = -1 - P[lane * 33 + x];
+        const int sz = c & (kEdgeFlag - 1);
+        if (c >= kEdgeFlag) {
+            emask |= 1u << x;
+            if (base < s.list_cap)
+                s.list[base] = make_int2((int)((int64_t)lat * N + (gy0 + lane) * Lx + gx0 + x), sz);
+            else
+                atomicExch(err, XY_EINVAL);
+            ++base;
+        } else if (sz < kSmallSizes) {
+            atomicAdd(&H[sz], 1);
+        } else {
+            count_size(s, N, lat, sz, 1, tile);
+        }
+    }
+    if (lane < thh) s.eroot[((int64_t)lat * Ly + gy0 + lane) * tiles_x + tx] = emask;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int sz = lane + 32 * k;
+        if (H[sz] > 0) count_size(s, N, lat, sz, H[sz], tile);
+    }
+}
+
+// Pass 2: merge across the right and bottom edge of every tile (periodic).
+// One warp per (tile, edge), lane k at the k-th site along the edge, linked
+// to its neighbour across.  Where the previous lane also touches and its site
+// continues the run along the edge (then so does the neighbour's, which has
+// the same spin), the pair of pieces is already linked: one union per pair of
+// touching runs.
+__global__ void __launch_bounds__(256) ccl_border_kernel(const float* __restrict__ theta, int Lx, int Ly, int n_lat,
+                                                         int32_t* labels, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    const int tiles_x = (Lx + 31) >> 5, tiles_y = (Ly + 31) >> 5;
+    const int tiles = tiles_x * tiles_y;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= tiles * 2 * n_lat) return;  // a whole warp
+    const int lat = w / (2 * tiles);
+    const int rem = w - lat * 2 * tiles;
+    const int tile = rem >> 1, side = rem & 1;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int gx0 = tx * 32, gy0 = ty * 32;
+    const int tw = min(32, Lx - gx0), thh = min(32, Ly - gy0);
+    const int64_t N = (int64_t)Lx * Ly;
+    const float* th = theta + (int64_t)lat * N;
+    int32_t* L = labels + (int64_t)lat * N;
+    int a = 0, b = 0;
+    bool act;
+    if (side == 0) {  // right edge: column gx0 + tw - 1 against the next column
+        act = lane < thh;
+        const int y = gy0 + lane, x = gx0 + tw - 1;
+        a = y * Lx + x;
+        b = y * Lx + (x + 1 == Lx ? 0 : x + 1);
+    } else {  // bottom edge: row gy0 + thh - 1 against the next row
+        act = lane < tw;
+        const int y = gy0 + thh - 1, x = gx0 + lane;
+        a = y * Lx + x;
+        b = (y + 1 == Ly ? 0 : y + 1) * Lx + x;
+    }
+    const bool sa = act && spin_of(th[act ? a : 0]);
+    const bool sb = act && spin_of(th[act ? b : 0]);
+    const bool touch = act && sa == sb;
+    const unsigned tm = __ballot_sync(kAll, touch);
+    const bool prev_sa = __shfl_up_sync(kAll, sa, 1);
+    const bool linked = lane > 0 && ((tm >> (lane - 1)) & 1u) && prev_sa == sa;
+    if (touch && !linked) union_global(L, a, b, g_union_limit, err);
+}
+
+// Pass 3: each listed piece adds its tile-local size at its domain's root and
+// points its tile root there.  A block takes 256 consecutive entries, which
+// come from a few tiles; a domain spanning many tiles (at T_c one percolates
+// through the lattice) would get an atomic from nearly every entry, all on
+// one address, so the pieces of the block's first entry's domain are summed
+// in shared memory and added once.
+__global__ void __launch_bounds__(256) ccl_list_size_kernel(int64_t N, int32_t* labels, CclScratch s, int* err)
+{
+    __shared__ int64_t s_key;
+    __shared__ int s_sum;
+    const int64_t n = min(*s.list_n, (int)s.list_cap);
+    const int limit = g_union_limit;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int64_t key = -1;
+        int sz = 0;
+        if (i < n) {
+            const int2 e = s.list[i];
+            const int64_t lat = e.x / N;
+            const int g = (int)(e.x - lat * N);
+            int32_t* L = labels + lat * N;
+            const int r = find_root_global(L, g, limit, err);
+            if (r != g) L[g] = r;  // the piece's sites then reach the root in one step
+            key = lat * N + r;
+            sz = e.y;
+        }
+        if (threadIdx.x == 0) {
+            s_key = key;
+            s_sum = 0;
+        }
+        __syncthreads();
+        const int64_t k0 = s_key;
+        if (key >= 0) {
+            if (key == k0)
+                atomicAdd(&s_sum, sz);
+            else
+                atomicAdd(&s.gsize[key], sz);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_sum > 0) atomicAdd(&s.gsize[k0], s_sum);
+        __syncthreads();
+    }
+}
+
+// Pass 4: every site points straight at its root; one warp per tile, lane =
+// column.  The tile's rows are read 16 at a time (16 loads in flight per lane),
+// then their parents, then the sizes of the roots: three rounds of latency per
+// 16 rows instead of two per row.  A site whose tile root is still a root (a
+// piece no merge linked) is final and is not written; the tile roots of merged
+// pieces already point at their roots (pass 3), so searches end at once.
+// Writing a root into a node that another search may be passing keeps the
+// forest valid.  A site that is the root of its domain and of an edge piece
+// (marked by the tile pass) enters the histogram with the domain's size from
+// pass 3, which it clears.
+__global__ void __launch_bounds__(256, 3) ccl_flatten_kernel(int Lx, int Ly, int n_lat, int32_t* labels, int want_sizes,
+                                                          CclScratch s, int* err)
+{
+    __shared__ int H[8][kSmallSizes];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int tiles_x = (Lx + 31) >> 5, tiles_y = (Ly + 31) >> 5;
+    const int tiles = tiles_x * tiles_y;
+    const int t = blockIdx.x * 8 + wib;
+    if (t >= tiles * n_lat) return;  // a whole warp
+    const int lat = t / tiles;
+    const int tile = t - lat * tiles;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int gx0 = tx * 32, gy0 = ty * 32;
+    const int tw = min(32, Lx - gx0), thh = min(32, Ly - gy0);
+    const int64_t N = (int64_t)Lx * Ly;
+    int32_t* L = labels + (int64_t)lat * N;
+    const int limit = g_union_limit;
+    unsigned em = 0;
+    if (want_sizes && lane < thh) em = s.eroot[((int64_t)lat * Ly + gy0 + lane) * tiles_x + tx];
+    H[wib][lane] = 0;
+    H[wib][lane + 32] = 0;
+    __syncwarp();
+    const bool col = lane < tw;
+    for (int y0 = 0; y0 < thh; y0 += 16) {  // two halves of 16 rows
+        const int site0 = (gy0 + y0) * Lx + gx0 + lane;
+        const int nr = min(16, thh - y0);
+        int l[16], p[16], q[16];
+#pragma unroll
+        for (int y = 0; y < 16; ++y) l[y] = (col && y < nr) ? L[site0 + y * Lx] : 0;
+#pragma unroll
+        for (int y = 0; y < 16; ++y) p[y] = (col && y < nr) ? L[l[y]] : 0;
+        // bit y: row y0 + y holds the root of a domain that an edge piece starts
+        unsigned counted = 0, moved = 0;
+#pragma unroll
+        for (int y = 0; y < 16; ++y) {
+            const unsigned e = __shfl_sync(kAll, em, y0 + y);
+            if (col && y < nr) {
+                if (p[y] != l[y])
+                    moved |= 1u << y;
+                else if (l[y] == site0 + y * Lx && ((e >> lane) & 1u))
+                    counted |= 1u << y;
+            }
+        }
+        // third round: the size of a counted root, or the parent's parent of a moved site
+#pragma unroll
+        for (int y = 0; y < 16; ++y)
+            q[y] = ((counted >> y) & 1u) ? s.gsize[(int64_t)lat * N + site0 + y * Lx]
+                                          : (((moved >> y) & 1u) ? L[p[y]] : 0);
+#pragma unroll
+        for (int y = 0; y < 16; ++y) {
+            if ((moved >> y) & 1u) {
+                L[site0 + y * Lx] = q[y] == p[y] ? p[y] : find_root_far(L, q[y], limit, err);
+            } else if ((counted >> y) & 1u) {
+                s.gsize[(int64_t)lat * N + site0 + y * Lx] = 0;
+                if (q[y] < kSmallSizes)
+                    atomicAdd(&H[wib][q[y]], 1);
+                else
+                    count_size(s, N, lat, q[y], 1, tile);
+            }
+        }
+    }
+    if (!want_sizes) return;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int z = lane + 32 * k;
+        if (H[wib][z] > 0) count_size(s, N, lat, z, H[wib][z], tile);
     }
 }
 
 // Pass 5: ordered compaction of the nonzero counts into (size, count) pairs,
-// one block per lattice, ascending size.  Warp w owns a contiguous slice of
-// the sizes 1..N and reads it 32 consecutive entries at a time, so the order
-// of the slices is the order of the sizes: each warp counts its nonzero
-// entries, one block-wide prefix over the warps places them, and a second
-// pass writes them with ballot ranks.
-__global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, const int32_t* __restrict__ counts,
-                                                           int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err)
+// one block per lattice, ascending size.  Sizes 1..63 are summed over their
+// copies;
+// larger ones through the bitmap, one bit per size, whose words are split into
+// contiguous ranges, one per warp, so the order of the warps is the order of
+// the sizes.  Each warp counts its set bits, one block-wide prefix places
+// them, and a second walk writes them and clears what it read.
+__global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, CclScratch s, int64_t* hist, int64_t hist_cap,
+                                                           int64_t* n_sizes, int* err)
 {
     __shared__ int64_t s_warp[32];
+    __shared__ int s_small[kSmallSizes];
     const int lat = blockIdx.x;
-    const int32_t* cnt = counts + (int64_t)lat * (N + 1);
+    int32_t* cnt = s.counts + (int64_t)lat * (N + 1);
+    uint32_t* bw = s.bits + (int64_t)lat * s.words;
     int64_t* out = hist ? hist + (int64_t)lat * hist_cap * 2 : nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t per = ((N + nw - 1) / nw + 31) / 32 * 32;  // whole rounds of 32 per warp
-    const int64_t lo = 1 + (int64_t)warp * per;
-    const int64_t hi = lo + per < N + 1 ? lo + per : N + 1;
-    int64_t mine = 0;  // nonzero entries of this warp's slice (same in every lane)
-    constexpr int kU = 8;  // rounds of 32 loaded before their ballots: eight loads in flight
-    for (int64_t z0 = lo; z0 < hi; z0 += 32 * kU) {
-        int v[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t z = z0 + 32 * u + lane;
-            v[u] = z < hi ? cnt[z] : 0;
+    const int n_small = (int)(N < kSmallSizes - 1 ? N : kSmallSizes - 1);  // sizes 1..n_small
+    if (threadIdx.x < kSmallSizes) {
+        const int z = threadIdx.x;
+        int v = 0;
+        if (z >= 1 && z <= n_small) {
+            int32_t* c = s.small + (int64_t)lat * s.copies * kSmallSizes + z;
+            for (int k = 0; k < s.copies; ++k, c += kSmallSizes) {
+                const int a = *c;
+                if (a) {
+                    v += a;
+                    *c = 0;
+                }
+            }
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) mine += __popc(__ballot_sync(0xFFFFFFFFu, v[u] != 0));
+        s_small[z] = v;
     }
+    // words holding sizes >= 64
+    const int64_t w0 = kSmallSizes / 32;
+    const int64_t per = (s.words - w0 + nw - 1) / nw;
+    const int64_t lo = w0 + (int64_t)warp * per;
+    const int64_t hi = lo + per < s.words ? lo + per : s.words;
+    int64_t mine = 0;
+    for (int64_t w = lo + lane; w < hi; w += 32) mine += __popc(bw[w]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(kAll, mine, d);
     if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
-    int64_t pos = 0, total = 0;
+    int64_t small_total = 0;
+    for (int z = 1; z < kSmallSizes; ++z) small_total += s_small[z] != 0;
+    int64_t pos = small_total, total = small_total;
     for (int w = 0; w < nw; ++w) {
         if (w < warp) pos += s_warp[w];
         total += s_warp[w];
     }
-    if (out && mine > 0) {
-        for (int64_t z0 = lo; z0 < hi; z0 += 32 * kU) {
-            int v[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t z = z0 + 32 * u + lane;
-                v[u] = z < hi ? cnt[z] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, v[u] != 0);
-                const int64_t at = pos + __popc(m & ((1u << lane) - 1u));
-                if (v[u] != 0 && at < hist_cap) {
-                    out[2 * at] = z0 + 32 * u + lane;
-                    out[2 * at + 1] = v[u];
+    if (out && threadIdx.x == 0) {
+        int64_t at = 0;
+        for (int z = 1; z < kSmallSizes; ++z)
+            if (s_small[z] != 0) {
+                if (at < hist_cap) {
+                    out[2 * at] = z;
+                    out[2 * at + 1] = s_small[z];
                 }
-                pos += __popc(m);
+                ++at;
             }
+    }
+    for (int64_t wb = lo; wb < hi; wb += 32) {
+        const int64_t w = wb + lane;
+        const uint32_t word = w < hi ? bw[w] : 0u;
+        // lanes in word order: each lane's first position after the lanes before it
+        int before = __popc(word);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(kAll, before, d);
+            if (lane >= d) before += o;
         }
+        const int all = __shfl_sync(kAll, before, 31);
+        int64_t at = pos + before - __popc(word);
+        for (uint32_t b = word; b; b &= b - 1) {
+            const int64_t z = (w << 5) + __ffs(b) - 1;
+            const int v = cnt[z];
+            if (out && at < hist_cap) {
+                out[2 * at] = z;
+                out[2 * at + 1] = v;
+            }
+            cnt[z] = 0;
+            ++at;
+        }
+        if (word) bw[w] = 0;
+        pos += all;
     }
     if (threadIdx.x == 0) {
         if (n_sizes) n_sizes[lat] = total;
@@ -280,36 +602,86 @@ __global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, const int3
     }
 }
 
-static int gcd_int(int a, int b)
+namespace {
+
+constexpr int64_t kAlign = 256;
+
+int64_t round_up(int64_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+
+// Edge sites of one tile: a bound on the pieces of the tile that reach its edge.
+int64_t edge_sites(int tw, int th) { return (tw <= 2 || th <= 2) ? (int64_t)tw * th : 2 * (int64_t)(tw + th) - 4; }
+
+int64_t list_capacity(int Lx, int Ly, int n_lat)
 {
-    while (b) {
-        const int t = a % b;
-        a = b;
-        b = t;
-    }
-    return a;
+    const int fx = Lx / 32, fy = Ly / 32, rx = Lx % 32, ry = Ly % 32;
+    int64_t per = (int64_t)fx * fy * edge_sites(32, 32);
+    if (rx) per += (int64_t)fy * edge_sites(rx, 32);
+    if (ry) per += (int64_t)fx * edge_sites(32, ry);
+    if (rx && ry) per += edge_sites(rx, ry);
+    return per * n_lat;
 }
 
-cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* labels, int32_t* size_scratch,
-                       int32_t* count_scratch, int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err,
-                       cudaStream_t st)
+}  // namespace
+
+// Copies of the small-size counts per lattice: one per 32 tiles, at most 32.
+int small_copies(int Lx, int Ly)
+{
+    const int64_t tiles = (int64_t)((Lx + 31) / 32) * ((Ly + 31) / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(32, tiles / 32));
+}
+
+int64_t ccl_scratch_bytes(int Lx, int Ly, int n_lat, int64_t* zeroed_bytes)
 {
     const int64_t N = (int64_t)Lx * Ly;
-    int TW = gcd_int(Lx, 32), TH = gcd_int(Ly, 32);
+    const int64_t words = (N + 1 + 31) / 32;
+    const int64_t z = round_up(4 * N * n_lat) + round_up(4 * (N + 1) * n_lat) + round_up(4 * words * n_lat) +
+                      round_up((int64_t)4 * kSmallSizes * small_copies(Lx, Ly) * n_lat);
+    if (zeroed_bytes) *zeroed_bytes = z;
+    const int64_t eroot = 4 * (int64_t)((Lx + 31) / 32) * Ly * n_lat;
+    return z + round_up(8 * list_capacity(Lx, Ly, n_lat)) + round_up(eroot) + kAlign;
+}
+
+CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat)
+{
+    const int64_t N = (int64_t)Lx * Ly;
+    CclScratch s{};
+    s.words = (N + 1 + 31) / 32;
+    s.list_cap = list_capacity(Lx, Ly, n_lat);
+    char* p = static_cast<char*>(base);
+    s.gsize = reinterpret_cast<int32_t*>(p);
+    p += round_up(4 * N * n_lat);
+    s.counts = reinterpret_cast<int32_t*>(p);
+    p += round_up(4 * (N + 1) * n_lat);
+    s.bits = reinterpret_cast<uint32_t*>(p);
+    p += round_up(4 * s.words * n_lat);
+    s.copies = small_copies(Lx, Ly);
+    s.small = reinterpret_cast<int32_t*>(p);
+    p += round_up((int64_t)4 * kSmallSizes * s.copies * n_lat);
+    s.list = reinterpret_cast<int2*>(p);
+    p += round_up(8 * s.list_cap);
+    s.eroot = reinterpret_cast<uint32_t*>(p);
+    p += round_up(4 * (int64_t)((Lx + 31) / 32) * Ly * n_lat);
+    s.list_n = reinterpret_cast<int*>(p);
+    return s;
+}
+
+cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* labels, const CclScratch& s,
+                       int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err, cudaStream_t st)
+{
+    const int64_t N = (int64_t)Lx * Ly;
+    const int want = (hist || n_sizes) ? 1 : 0;
+    const int64_t tiles = (int64_t)((Lx + 31) / 32) * ((Ly + 31) / 32) * n_lat;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(size_scratch, 0, sizeof(int32_t) * N * n_lat, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(count_scratch, 0, sizeof(int32_t) * (N + 1) * n_lat, st)) != cudaSuccess) return e;
-    const int tiles = (Lx / TW) * (Ly / TH);
-    ccl_local_kernel<<<(unsigned)(tiles * n_lat), TW * TH, TW * TH * sizeof(int), st>>>(theta, Lx, Ly, TW, TH,
-                                                                                        labels, err);
-    const int64_t total = N * n_lat;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
-    const int64_t border = (int64_t)n_lat * tiles * (TW + TH);
-    ccl_border_kernel<<<(unsigned)((border + 255) / 256), 256, 0, st>>>(theta, Lx, Ly, TW, TH, n_lat, labels, err);
-    ccl_flatten_kernel<<<blocks, 256, 0, st>>>(N, n_lat, labels, size_scratch, err);
-    ccl_size_hist_kernel<<<(unsigned)((total / 4 + 255) / 256), 256, 0, st>>>(N, n_lat, labels, size_scratch,
-                                                                              count_scratch);
-    ccl_compact_kernel<<<n_lat, 1024, 0, st>>>(N, count_scratch, hist, hist_cap, n_sizes, err);
+    if (want && (e = cudaMemsetAsync(s.list_n, 0, sizeof(int), st)) != cudaSuccess) return e;
+    ccl_tile_kernel<<<(unsigned)((tiles + kTileWarps - 1) / kTileWarps), 32 * kTileWarps, 0, st>>>(
+        theta, Lx, Ly, n_lat, labels, want, s, err);
+    ccl_border_kernel<<<(unsigned)((2 * tiles + 7) / 8), 256, 0, st>>>(theta, Lx, Ly, n_lat, labels, err);
+    if (want) {
+        const unsigned g = (unsigned)std::min<int64_t>((s.list_cap + 255) / 256, 152 * 8);
+        ccl_list_size_kernel<<<g, 256, 0, st>>>(N, labels, s, err);
+    }
+    ccl_flatten_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(Lx, Ly, n_lat, labels, want, s, err);
+    if (want) ccl_compact_kernel<<<n_lat, 1024, 0, st>>>(N, s, hist, hist_cap, n_sizes, err);
     return cudaGetLastError();
 }
 

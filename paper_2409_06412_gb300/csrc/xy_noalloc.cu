@@ -1,7 +1,8 @@
 // xy_noalloc.cu -- domain labelling for callers that must not allocate.
 //
-// xy_label_domains() takes its working memory (component sizes and the size
-// histogram, 8 bytes per site) from cudaMalloc on every call.  Some callers
+// xy_label_domains() takes its working memory (component sizes, the size
+// histogram, the pieces to merge) from cudaMalloc, kept by the lattice
+// object between calls.  Some callers
 // cannot allow that: services that hand every byte of device memory to their
 // own pool and forbid libraries from allocating behind its back, loops where
 // an allocation and the device-wide synchronisation of cudaFree are not
@@ -17,11 +18,21 @@
 
 namespace {
 
-// Working memory of one call: component sizes (one int32 per site), the size
-// histogram (one int32 per possible size, per lattice) and an error flag.
-constexpr int64_t kSizeWords = XY_STATIC_CCL_MAX_SITES;
-constexpr int64_t kCountWords = XY_STATIC_CCL_MAX_SITES + XY_STATIC_CCL_MAX_LATTICES;
-constexpr int64_t kScratchWords = kSizeWords + kCountWords + 64;
+// Working memory of one call (component sizes, the size histogram and its
+// bitmap, the list of tile pieces to merge; laid out by ccl_scratch_carve)
+// and an error flag.  Bound for at most XY_STATIC_CCL_MAX_SITES sites in at
+// most XY_STATIC_CCL_MAX_LATTICES lattices: 4 bytes per site of sizes, 4 per
+// site and lattice of counts, 4 per 32 sizes and 8 per lattice of bitmap, at
+// most 8 per site of list (a tile has no more pieces on its edge than sites),
+// a word per row of each column of tiles (at most Lx / 32 + 1 per row, and
+// at most a quarter as many rows as sites), 256 bytes per copy of the small
+// size counts (one copy per 32 tiles of at least 32 sites, at least one per
+// lattice), and the alignment of each part.
+constexpr int64_t kSites = XY_STATIC_CCL_MAX_SITES;
+constexpr int64_t kLats = XY_STATIC_CCL_MAX_LATTICES;
+constexpr int64_t kScratchBytes = 4 * kSites + 4 * (kSites + kLats) + 4 * (kSites / 32 + 2 * kLats) + 8 * kSites +
+                                  4 * (kSites / 32 + kSites / 4) + 256 * (kSites / 1024 + kLats) + 9 * 256;
+constexpr int64_t kScratchWords = kScratchBytes / 4 + 64;
 
 static __device__ __align__(256) int32_t g_ccl_scratch[kScratchWords];
 
@@ -86,9 +97,11 @@ extern "C" int xy_label_domains_static(const float* theta, int Lx, int Ly, int n
     int32_t* base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;
-    int32_t* sizes = base;
-    int32_t* counts = base + kSizeWords;
-    int* err = reinterpret_cast<int*>(base + kSizeWords + kCountWords);
+    int64_t zeroed = 0;
+    if (xy::ccl_scratch_bytes(Lx, Ly, n_lattices, &zeroed) > kScratchBytes)
+        return fail_static(XY_EINVAL, "xy_label_domains_static: working memory exceeds the static array");
+    const xy::CclScratch scratch = xy::ccl_scratch_carve(base, Lx, Ly, n_lattices);
+    int* err = reinterpret_cast<int*>(base + kScratchBytes / 4);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // the call reads its error flag back and synchronises the stream, which a
     // capturing stream does not allow (and the attempt would end the capture)
@@ -101,10 +114,10 @@ extern "C" int xy_label_domains_static(const float* theta, int Lx, int Ly, int n
         return fail_static(XY_EINVAL, "xy_label_domains_static: the stream is capturing; the call synchronises it");
     // the array keeps the previous call's contents: clear what must start at zero
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, zeroed, st);
     if (e == cudaSuccess && hist) e = cudaMemsetAsync(hist, 0, sizeof(int64_t) * 2 * hist_cap * n_lattices, st);
     if (e == cudaSuccess)
-        e = xy::launch_ccl(theta, Lx, Ly, n_lattices, labels, sizes, counts, hist, hist ? hist_cap : 0, n_sizes, err,
-                           st);
+        e = xy::launch_ccl(theta, Lx, Ly, n_lattices, labels, scratch, hist, hist ? hist_cap : 0, n_sizes, err, st);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
