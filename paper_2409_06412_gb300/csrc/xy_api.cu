@@ -1762,7 +1762,7 @@ int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, i
             rc = fail(XY_ECUDA, "labelling: %s", cudaGetErrorString(e));
             break;
         }
-        L->launches += want ? 5 : 3;
+        L->launches += 5;
         if (labels && !dev_lab)
             e = cudaMemcpyAsync(labels + b0 * N, lab, sizeof(int32_t) * N * nl, cudaMemcpyDeviceToHost, L->stream);
         if (e == cudaSuccess && hist && !dev_hist)

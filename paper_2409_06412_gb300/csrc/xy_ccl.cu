@@ -17,16 +17,16 @@
 //           short list (batch index, local size) for the merge.
 //   border  one warp per tile edge: one union in global memory per pair of
 //           runs that touch across the edge.
-//   sizes   the listed pieces add their local sizes at their global roots
-//           (and point their tile roots at them).
-//   flatten one warp per tile: every site points straight at its root; the
-//           domain roots among the edge pieces enter the histogram.
+//   sizes   the listed pieces add their local sizes at their domain's root's
+//           entry of the list (and point their tile roots at the root); the
+//           roots' entries then enter the histogram.
+//   flatten one warp per tile: every site points straight at its root.
 //   compact the histogram's nonzero entries become (size, count) pairs in
 //           ascending order: sizes below 64 are scanned directly, larger ones
 //           through a bitmap with one bit per size.
-// The component sizes, the histogram counts and the bitmap are zero between
-// calls: the passes clear every entry they set, so no pass reads or clears
-// memory in proportion to the lattice beyond the labels themselves.
+// The histogram counts and the bitmap are zero between calls: the passes
+// clear every entry they set, so no pass reads or clears memory in
+// proportion to the lattice beyond the labels themselves.
 #include <algorithm>
 #include <cstdint>
 
@@ -82,10 +82,21 @@ __device__ __forceinline__ int find_root_global(int32_t* L, int x, int limit, in
     return x;
 }
 
-// The same search, out of line: the rare long walks of the flattening pass.
-__device__ __noinline__ int find_root_far(int32_t* L, int x, int limit, int* err)
+// The same search without writes (used while the owners of nodes point them
+// at their roots: a halving step could replace such a pointer with an older
+// ancestor).
+__device__ __forceinline__ int find_root_global_ro(const int32_t* L, int x, int limit, int* err)
 {
-    return find_root_global(L, x, limit, err);
+    int p = *(volatile const int32_t*)&L[x];
+    for (int it = 0; p != x; ++it) {
+        if (it >= limit) {
+            atomicExch(err, XY_ETIMEOUT);
+            return x;
+        }
+        x = p;
+        p = *(volatile const int32_t*)&L[x];
+    }
+    return x;
 }
 
 // Link the components of a and b (global indices inside one lattice's label
@@ -313,17 +324,19 @@ __global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const floa
     int base = 0;
     if (lane == 31 && total > 0) base = atomicAdd(s.list_n, total);
     base = __shfl_sync(kAll, base, 31) + before - n_edge;
-    unsigned emask = 0;  // lane y: the roots of row y whose piece reaches the tile's edge
     for (unsigned b = roots; b; b &= b - 1) {
         const int x = __ffs(b) - 1;
         const int c = -1 - P[lane * 33 + x];
         const int sz = c & (kEdgeFlag - 1);
         if (c >= kEdgeFlag) {
-            emask |= 1u << x;
-            if (base < s.list_cap)
-                s.list[base] = make_int2((int)((int64_t)lat * N + (gy0 + lane) * Lx + gx0 + x), sz);
-            else
+            if (base < s.list_cap) {
+                const int g = (gy0 + lane) * Lx + gx0 + x;
+                s.list[base] = make_int2((int)((int64_t)lat * N + g), sz);
+                s.aux[base] = make_int2(-1, 0);
+                s.entry[(int64_t)lat * N + g] = base;
+            } else {
                 atomicExch(err, XY_EINVAL);
+            }
             ++base;
         } else if (sz < kSmallSizes) {
             atomicAdd(&H[sz], 1);
@@ -331,7 +344,6 @@ __global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const floa
             count_size(s, N, lat, sz, 1, tile);
         }
     }
-    if (lane < thh) s.eroot[((int64_t)lat * Ly + gy0 + lane) * tiles_x + tx] = emask;
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -341,74 +353,120 @@ __global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const floa
 }
 
 // Pass 2: merge across the right and bottom edge of every tile (periodic).
-// One warp per (tile, edge), lane k at the k-th site along the edge, linked
-// to its neighbour across.  Where the previous lane also touches and its site
-// continues the run along the edge (then so does the neighbour's, which has
-// the same spin), the pair of pieces is already linked: one union per pair of
-// touching runs.
+// One warp per tile; lane k takes the k-th site of the right edge (linked to
+// its right neighbour) and of the bottom edge (linked to the site below).
+// Where the previous lane also touches and its site continues the run along
+// the edge (then so does the neighbour's, which has the same spin), the pair
+// of pieces is already linked: one union per pair of touching runs.  The
+// loads go in three rounds for both edges at once (spins, the sites' tile
+// roots, their parents); two roots are then linked straight away, anything
+// else goes through the general union.
 __global__ void __launch_bounds__(256) ccl_border_kernel(const float* __restrict__ theta, int Lx, int Ly, int n_lat,
                                                          int32_t* labels, int* err)
 {
     const int lane = threadIdx.x & 31;
     const int tiles_x = (Lx + 31) >> 5, tiles_y = (Ly + 31) >> 5;
     const int tiles = tiles_x * tiles_y;
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= tiles * 2 * n_lat) return;  // a whole warp
-    const int lat = w / (2 * tiles);
-    const int rem = w - lat * 2 * tiles;
-    const int tile = rem >> 1, side = rem & 1;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= tiles * n_lat) return;  // a whole warp
+    const int lat = t / tiles;
+    const int tile = t - lat * tiles;
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const int gx0 = tx * 32, gy0 = ty * 32;
     const int tw = min(32, Lx - gx0), thh = min(32, Ly - gy0);
     const int64_t N = (int64_t)Lx * Ly;
     const float* th = theta + (int64_t)lat * N;
     int32_t* L = labels + (int64_t)lat * N;
-    int a = 0, b = 0;
-    bool act;
-    if (side == 0) {  // right edge: column gx0 + tw - 1 against the next column
-        act = lane < thh;
+    const int limit = g_union_limit;
+    // edge 0: right (column gx0 + tw - 1 against the next column); edge 1: bottom
+    int a[2], b[2];
+    bool act[2];
+    {
         const int y = gy0 + lane, x = gx0 + tw - 1;
-        a = y * Lx + x;
-        b = y * Lx + (x + 1 == Lx ? 0 : x + 1);
-    } else {  // bottom edge: row gy0 + thh - 1 against the next row
-        act = lane < tw;
-        const int y = gy0 + thh - 1, x = gx0 + lane;
-        a = y * Lx + x;
-        b = (y + 1 == Ly ? 0 : y + 1) * Lx + x;
+        act[0] = lane < thh;
+        a[0] = act[0] ? y * Lx + x : 0;
+        b[0] = act[0] ? y * Lx + (x + 1 == Lx ? 0 : x + 1) : 0;
     }
-    const bool sa = act && spin_of(th[act ? a : 0]);
-    const bool sb = act && spin_of(th[act ? b : 0]);
-    const bool touch = act && sa == sb;
-    const unsigned tm = __ballot_sync(kAll, touch);
-    const bool prev_sa = __shfl_up_sync(kAll, sa, 1);
-    const bool linked = lane > 0 && ((tm >> (lane - 1)) & 1u) && prev_sa == sa;
-    if (touch && !linked) union_global(L, a, b, g_union_limit, err);
+    {
+        const int y = gy0 + thh - 1, x = gx0 + lane;
+        act[1] = lane < tw;
+        a[1] = act[1] ? y * Lx + x : 0;
+        b[1] = act[1] ? (y + 1 == Ly ? 0 : y + 1) * Lx + x : 0;
+    }
+    float fa[2], fb[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        fa[e] = act[e] ? th[a[e]] : 0.0f;
+        fb[e] = act[e] ? th[b[e]] : 0.0f;
+    }
+    bool need[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const bool sa = act[e] && spin_of(fa[e]);
+        const bool touch = act[e] && sa == spin_of(fb[e]);
+        const unsigned tm = __ballot_sync(kAll, touch);
+        const bool prev_sa = __shfl_up_sync(kAll, sa, 1);
+        need[e] = touch && !(lane > 0 && ((tm >> (lane - 1)) & 1u) && prev_sa == sa);
+    }
+    int la[2], lb[2], ra[2], rb[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        la[e] = need[e] ? L[a[e]] : 0;
+        lb[e] = need[e] ? L[b[e]] : 0;
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        ra[e] = need[e] ? L[la[e]] : 0;
+        rb[e] = need[e] ? L[lb[e]] : 0;
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        if (!need[e]) continue;
+        if (ra[e] == la[e] && rb[e] == lb[e]) {  // two roots
+            if (la[e] == lb[e]) continue;
+            const int hi = max(la[e], lb[e]), lo = min(la[e], lb[e]);
+            const int old = atomicMin(&L[hi], lo);
+            if (old != hi) union_global(L, old, lo, limit, err);  // hi was linked meanwhile
+        } else {
+            union_global(L, la[e], lb[e], limit, err);
+        }
+    }
 }
 
-// Pass 3: each listed piece adds its tile-local size at its domain's root and
-// points its tile root there.  A block takes 256 consecutive entries, which
-// come from a few tiles; a domain spanning many tiles (at T_c one percolates
-// through the lattice) would get an atomic from nearly every entry, all on
-// one address, so the pieces of the block's first entry's domain are summed
-// in shared memory and added once.
+// Pass 3: each listed piece finds its domain's root, points its tile root
+// there, and adds its tile-local size to the root's own entry of the list
+// (the root is the tile root of a listed piece: a domain that spans tiles
+// reaches the edge of each of its tiles; the tile pass recorded each listed
+// tile root's entry).  Searches write nothing here, so afterwards every tile
+// root of a merged piece points straight at its domain's root.  A block
+// takes 256 consecutive entries from a few tiles; a domain spanning many
+// tiles would get an atomic from nearly every entry, all on one address, so
+// the pieces of the block's first entry's domain are summed in shared
+// memory and added once.
 __global__ void __launch_bounds__(256) ccl_list_size_kernel(int64_t N, int32_t* labels, CclScratch s, int* err)
 {
-    __shared__ int64_t s_key;
+    __shared__ int s_key;
     __shared__ int s_sum;
-    const int64_t n = min(*s.list_n, (int)s.list_cap);
+    const int n = min(*s.list_n, (int)s.list_cap);
     const int limit = g_union_limit;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        int64_t key = -1;
-        int sz = 0;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        int key = -1, sz = 0;
         if (i < n) {
             const int2 e = s.list[i];
-            const int64_t lat = e.x / N;
+            const int lat = (int)(e.x / N);
             const int g = (int)(e.x - lat * N);
-            int32_t* L = labels + lat * N;
-            const int r = find_root_global(L, g, limit, err);
-            if (r != g) L[g] = r;  // the piece's sites then reach the root in one step
-            key = lat * N + r;
+            int32_t* L = labels + (int64_t)lat * N;
+            const int r = find_root_global_ro(L, g, limit, err);
+            if (r != g) L[g] = r;  // every merged tile root now points at its domain's root
+            key = r == g ? i : s.entry[(int64_t)lat * N + r];
+            // the root's entry, checked (a search cut short by the bound ends
+            // at a node that may not be listed)
+            if (key < 0 || key >= n || s.list[key].x != (int)((int64_t)lat * N + r)) {
+                atomicExch(err, XY_ETIMEOUT);
+                key = -1;
+            }
+            s.aux[i].x = key;
             sz = e.y;
         }
         if (threadIdx.x == 0) {
@@ -416,33 +474,62 @@ __global__ void __launch_bounds__(256) ccl_list_size_kernel(int64_t N, int32_t* 
             s_sum = 0;
         }
         __syncthreads();
-        const int64_t k0 = s_key;
+        const int k0 = s_key;
         if (key >= 0) {
             if (key == k0)
                 atomicAdd(&s_sum, sz);
             else
-                atomicAdd(&s.gsize[key], sz);
+                atomicAdd(&s.aux[key].y, sz);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && s_sum > 0) atomicAdd(&s.gsize[k0], s_sum);
+        if (threadIdx.x == 0 && s_sum > 0) atomicAdd(&s.aux[k0].y, s_sum);
+        __syncthreads();
+    }
+}
+
+// Pass 3b: the listed pieces whose tile root is their domain's root enter the
+// histogram with the domain's size.  A block takes 256 consecutive entries,
+// from a few tiles of one lattice: small sizes of that lattice are counted
+// in shared memory and added with one atomic per size.
+__global__ void __launch_bounds__(256) ccl_list_hist_kernel(int64_t N, CclScratch s, int* err)
+{
+    __shared__ int bins[kSmallSizes];
+    __shared__ int blat;
+    const int n = min(*s.list_n, (int)s.list_cap);
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        if (threadIdx.x < kSmallSizes) bins[threadIdx.x] = 0;
+        if (threadIdx.x == 0) blat = (int)(s.list[base].x / N);
+        __syncthreads();
+        const int i = base + threadIdx.x;
+        if (i < n) {
+            const int2 a = s.aux[i];
+            if (a.x == i && (a.y < 1 || a.y > N)) {
+                atomicExch(err, XY_ETIMEOUT);  // only after a search was cut short
+            } else if (a.x == i) {
+                const int l = (int)(s.list[i].x / N);
+                if (l == blat && a.y < kSmallSizes)
+                    atomicAdd(&bins[a.y], 1);
+                else
+                    count_size(s, N, l, a.y, 1, blockIdx.x);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < kSmallSizes && bins[threadIdx.x] > 0)
+            count_size(s, N, blat, threadIdx.x, bins[threadIdx.x], blockIdx.x);
         __syncthreads();
     }
 }
 
 // Pass 4: every site points straight at its root; one warp per tile, lane =
-// column.  The tile's rows are read 16 at a time (16 loads in flight per lane),
-// then their parents, then the sizes of the roots: three rounds of latency per
-// 16 rows instead of two per row.  A site whose tile root is still a root (a
-// piece no merge linked) is final and is not written; the tile roots of merged
-// pieces already point at their roots (pass 3), so searches end at once.
-// Writing a root into a node that another search may be passing keeps the
-// forest valid.  A site that is the root of its domain and of an edge piece
-// (marked by the tile pass) enters the histogram with the domain's size from
-// pass 3, which it clears.
-__global__ void __launch_bounds__(256, 3) ccl_flatten_kernel(int Lx, int Ly, int n_lat, int32_t* labels, int want_sizes,
-                                                          CclScratch s, int* err)
+// column.  A site's label is its tile root, a site of the same tile (the
+// tile root's own entry is the exception: after a merge it points outside),
+// and after pass 3 the tile root's own entry is the domain's root (or
+// itself): so the warp reads the tile's labels once (16 rows at a time per
+// lane), keeps them in shared memory, and looks every tile root up there.  A
+// site whose tile root is still a root is final and is not written.
+__global__ void __launch_bounds__(256, 4) ccl_flatten_kernel(int Lx, int Ly, int n_lat, float inv_lx, int32_t* labels)
 {
-    __shared__ int H[8][kSmallSizes];
+    __shared__ int T[8][32 * 33];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int tiles_x = (Lx + 31) >> 5, tiles_y = (Ly + 31) >> 5;
     const int tiles = tiles_x * tiles_y;
@@ -453,59 +540,36 @@ __global__ void __launch_bounds__(256, 3) ccl_flatten_kernel(int Lx, int Ly, int
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const int gx0 = tx * 32, gy0 = ty * 32;
     const int tw = min(32, Lx - gx0), thh = min(32, Ly - gy0);
-    const int64_t N = (int64_t)Lx * Ly;
-    int32_t* L = labels + (int64_t)lat * N;
-    const int limit = g_union_limit;
-    unsigned em = 0;
-    if (want_sizes && lane < thh) em = s.eroot[((int64_t)lat * Ly + gy0 + lane) * tiles_x + tx];
-    H[wib][lane] = 0;
-    H[wib][lane + 32] = 0;
-    __syncwarp();
-    const bool col = lane < tw;
-    for (int y0 = 0; y0 < thh; y0 += 16) {  // two halves of 16 rows
-        const int site0 = (gy0 + y0) * Lx + gx0 + lane;
-        const int nr = min(16, thh - y0);
-        int l[16], p[16], q[16];
+    const bool in = lane < tw;
+    int32_t* L = labels + (int64_t)lat * Lx * Ly;
+    const int base = gy0 * Lx + gx0;
+    int* Tw = T[wib];
 #pragma unroll
-        for (int y = 0; y < 16; ++y) l[y] = (col && y < nr) ? L[site0 + y * Lx] : 0;
+    for (int h = 0; h < 32; h += 16) {
+        int l[16];
 #pragma unroll
-        for (int y = 0; y < 16; ++y) p[y] = (col && y < nr) ? L[l[y]] : 0;
-        // bit y: row y0 + y holds the root of a domain that an edge piece starts
-        unsigned counted = 0, moved = 0;
+        for (int y = 0; y < 16; ++y) l[y] = (in && h + y < thh) ? L[base + (h + y) * Lx + lane] : 0;
 #pragma unroll
-        for (int y = 0; y < 16; ++y) {
-            const unsigned e = __shfl_sync(kAll, em, y0 + y);
-            if (col && y < nr) {
-                if (p[y] != l[y])
-                    moved |= 1u << y;
-                else if (l[y] == site0 + y * Lx && ((e >> lane) & 1u))
-                    counted |= 1u << y;
-            }
-        }
-        // third round: the size of a counted root, or the parent's parent of a moved site
-#pragma unroll
-        for (int y = 0; y < 16; ++y)
-            q[y] = ((counted >> y) & 1u) ? s.gsize[(int64_t)lat * N + site0 + y * Lx]
-                                          : (((moved >> y) & 1u) ? L[p[y]] : 0);
-#pragma unroll
-        for (int y = 0; y < 16; ++y) {
-            if ((moved >> y) & 1u) {
-                L[site0 + y * Lx] = q[y] == p[y] ? p[y] : find_root_far(L, q[y], limit, err);
-            } else if ((counted >> y) & 1u) {
-                s.gsize[(int64_t)lat * N + site0 + y * Lx] = 0;
-                if (q[y] < kSmallSizes)
-                    atomicAdd(&H[wib][q[y]], 1);
-                else
-                    count_size(s, N, lat, q[y], 1, tile);
-            }
-        }
+        for (int y = 0; y < 16; ++y) Tw[(h + y) * 33 + lane] = l[y];
     }
-    if (!want_sizes) return;
     __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int z = lane + 32 * k;
-        if (H[wib][z] > 0) count_size(s, N, lat, z, H[wib][z], tile);
+    if (!in) return;
+#pragma unroll 4
+    for (int y = 0; y < thh; ++y) {
+        const int li = Tw[y * 33 + lane];
+        const int d = li - base;  // a site of the tile at row ry, column rx: d = ry * Lx + rx
+        int ry = (int)((float)d * inv_lx);
+        if (ry * Lx > d)
+            --ry;
+        else if ((ry + 1) * Lx <= d)
+            ++ry;
+        const int rx = d - ry * Lx;
+        // a label outside the tile belongs to a tile root whose entry points
+        // at its domain's root already: final
+        if (ry >= 0 && ry < thh && rx >= 0 && rx < tw) {
+            const int p = Tw[ry * 33 + rx];
+            if (p != li) L[base + y * Lx + lane] = p;
+        }
     }
 }
 
@@ -634,11 +698,11 @@ int64_t ccl_scratch_bytes(int Lx, int Ly, int n_lat, int64_t* zeroed_bytes)
 {
     const int64_t N = (int64_t)Lx * Ly;
     const int64_t words = (N + 1 + 31) / 32;
-    const int64_t z = round_up(4 * N * n_lat) + round_up(4 * (N + 1) * n_lat) + round_up(4 * words * n_lat) +
+    const int64_t z = round_up(4 * (N + 1) * n_lat) + round_up(4 * words * n_lat) +
                       round_up((int64_t)4 * kSmallSizes * small_copies(Lx, Ly) * n_lat);
     if (zeroed_bytes) *zeroed_bytes = z;
-    const int64_t eroot = 4 * (int64_t)((Lx + 31) / 32) * Ly * n_lat;
-    return z + round_up(8 * list_capacity(Lx, Ly, n_lat)) + round_up(eroot) + kAlign;
+    const int64_t cap = list_capacity(Lx, Ly, n_lat);
+    return z + round_up(4 * N * n_lat) + 2 * round_up(8 * cap) + kAlign;
 }
 
 CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat)
@@ -648,8 +712,6 @@ CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat)
     s.words = (N + 1 + 31) / 32;
     s.list_cap = list_capacity(Lx, Ly, n_lat);
     char* p = static_cast<char*>(base);
-    s.gsize = reinterpret_cast<int32_t*>(p);
-    p += round_up(4 * N * n_lat);
     s.counts = reinterpret_cast<int32_t*>(p);
     p += round_up(4 * (N + 1) * n_lat);
     s.bits = reinterpret_cast<uint32_t*>(p);
@@ -657,10 +719,12 @@ CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat)
     s.copies = small_copies(Lx, Ly);
     s.small = reinterpret_cast<int32_t*>(p);
     p += round_up((int64_t)4 * kSmallSizes * s.copies * n_lat);
+    s.entry = reinterpret_cast<int32_t*>(p);
+    p += round_up(4 * N * n_lat);
     s.list = reinterpret_cast<int2*>(p);
     p += round_up(8 * s.list_cap);
-    s.eroot = reinterpret_cast<uint32_t*>(p);
-    p += round_up(4 * (int64_t)((Lx + 31) / 32) * Ly * n_lat);
+    s.aux = reinterpret_cast<int2*>(p);
+    p += round_up(8 * s.list_cap);
     s.list_n = reinterpret_cast<int*>(p);
     return s;
 }
@@ -668,20 +732,21 @@ CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat)
 cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* labels, const CclScratch& s,
                        int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err, cudaStream_t st)
 {
+    // every pass runs whether or not sizes are asked for: the size pass also
+    // points every merged tile root at its domain's root, which the flattening
+    // relies on, and the compaction clears the counts for the next call
     const int64_t N = (int64_t)Lx * Ly;
-    const int want = (hist || n_sizes) ? 1 : 0;
     const int64_t tiles = (int64_t)((Lx + 31) / 32) * ((Ly + 31) / 32) * n_lat;
     cudaError_t e;
-    if (want && (e = cudaMemsetAsync(s.list_n, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(s.list_n, 0, sizeof(int), st)) != cudaSuccess) return e;
     ccl_tile_kernel<<<(unsigned)((tiles + kTileWarps - 1) / kTileWarps), 32 * kTileWarps, 0, st>>>(
-        theta, Lx, Ly, n_lat, labels, want, s, err);
-    ccl_border_kernel<<<(unsigned)((2 * tiles + 7) / 8), 256, 0, st>>>(theta, Lx, Ly, n_lat, labels, err);
-    if (want) {
-        const unsigned g = (unsigned)std::min<int64_t>((s.list_cap + 255) / 256, 152 * 8);
-        ccl_list_size_kernel<<<g, 256, 0, st>>>(N, labels, s, err);
-    }
-    ccl_flatten_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(Lx, Ly, n_lat, labels, want, s, err);
-    if (want) ccl_compact_kernel<<<n_lat, 1024, 0, st>>>(N, s, hist, hist_cap, n_sizes, err);
+        theta, Lx, Ly, n_lat, labels, 1, s, err);
+    ccl_border_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(theta, Lx, Ly, n_lat, labels, err);
+    const unsigned g = (unsigned)std::min<int64_t>((s.list_cap + 255) / 256, 152 * 8);
+    ccl_list_size_kernel<<<g, 256, 0, st>>>(N, labels, s, err);
+    ccl_list_hist_kernel<<<g, 256, 0, st>>>(N, s, err);
+    ccl_flatten_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(Lx, Ly, n_lat, 1.0f / (float)Lx, labels);
+    ccl_compact_kernel<<<n_lat, 1024, 0, st>>>(N, s, hist, hist_cap, n_sizes, err);
     return cudaGetLastError();
 }
 

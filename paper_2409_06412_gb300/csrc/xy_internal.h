@@ -153,19 +153,21 @@ cudaError_t launch_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, i
 int report_error(int code, const char* msg);
 
 // ---- domains (xy_ccl.cu)
-// Working memory of a labelling call.  gsize (int32 per site), counts
-// (int32 per possible size, N + 1 per lattice) and bits (one mark per group of
-// 32 sizes) must be zero when a call starts and are zero again when it ends
-// without error; list holds up to list_cap (batch index, size) pieces,
-// list_n their number, and eroot marks the sites that are roots of pieces
-// reaching their tile's edge.
+// Working memory of a labelling call.  counts (int32 per possible size, N + 1
+// per lattice), bits (one mark per size) and small (counts of sizes below
+// 64, in `copies` copies per lattice) must be zero when a call starts and are
+// zero again when it ends without error.  list holds up to list_cap pieces
+// that reach their tile's edge (batch index of the tile root, local size),
+// list_n their number, aux per piece (list index of its domain's root, the
+// domain's size at the root's entry), and entry maps a listed tile root's
+// site to its list index.
 struct CclScratch {
-    int32_t* gsize;
     int32_t* counts;
     uint32_t* bits;
-    int32_t* small;   // counts of sizes below 64, in `copies` copies per lattice (zero between calls)
+    int32_t* small;
+    int32_t* entry;
     int2* list;
-    uint32_t* eroot;  // per lattice, row and tile column: the roots of edge pieces
+    int2* aux;
     int* list_n;
     int64_t list_cap;
     int64_t words;  // bitmap words per lattice
@@ -177,8 +179,9 @@ struct CclScratch {
 int64_t ccl_scratch_bytes(int Lx, int Ly, int n_lat, int64_t* zeroed_bytes);
 // The parts of a block of ccl_scratch_bytes() bytes (256-byte aligned).
 CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat);
-// Labels (device, n_lat * Lx * Ly), and the size histogram when hist or
-// n_sizes is non-null.  The batch must have fewer than 2^31 sites.
+// Labels (device, n_lat * Lx * Ly), and the size histogram into hist and
+// n_sizes where they are non-null.  The batch must have fewer than 2^31
+// sites.
 cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* labels, const CclScratch& s,
                        int64_t* hist, int64_t hist_cap, int64_t* n_sizes, int* err, cudaStream_t st);
 

@@ -18,20 +18,19 @@
 
 namespace {
 
-// Working memory of one call (component sizes, the size histogram and its
-// bitmap, the list of tile pieces to merge; laid out by ccl_scratch_carve)
-// and an error flag.  Bound for at most XY_STATIC_CCL_MAX_SITES sites in at
-// most XY_STATIC_CCL_MAX_LATTICES lattices: 4 bytes per site of sizes, 4 per
-// site and lattice of counts, 4 per 32 sizes and 8 per lattice of bitmap, at
-// most 8 per site of list (a tile has no more pieces on its edge than sites),
-// a word per row of each column of tiles (at most Lx / 32 + 1 per row, and
-// at most a quarter as many rows as sites), 256 bytes per copy of the small
-// size counts (one copy per 32 tiles of at least 32 sites, at least one per
-// lattice), and the alignment of each part.
+// Working memory of one call (the size histogram and its bitmap, the pieces
+// to merge and their list index by site; laid out by ccl_scratch_carve) and
+// an error flag.  Bound for at most XY_STATIC_CCL_MAX_SITES sites in at most
+// XY_STATIC_CCL_MAX_LATTICES lattices: 4 bytes per site and lattice of
+// counts, 4 per 32 sizes and 8 per lattice of bitmap, 256 bytes per copy of
+// the small size counts (one copy per 32 tiles of at least 32 sites, at least
+// one per lattice), 4 per site of list index, at most 16 per site of list (a
+// tile has no more pieces on its edge than sites), and the alignment of each
+// part.
 constexpr int64_t kSites = XY_STATIC_CCL_MAX_SITES;
 constexpr int64_t kLats = XY_STATIC_CCL_MAX_LATTICES;
-constexpr int64_t kScratchBytes = 4 * kSites + 4 * (kSites + kLats) + 4 * (kSites / 32 + 2 * kLats) + 8 * kSites +
-                                  4 * (kSites / 32 + kSites / 4) + 256 * (kSites / 1024 + kLats) + 9 * 256;
+constexpr int64_t kScratchBytes = 4 * (kSites + kLats) + 4 * (kSites / 32 + 2 * kLats) +
+                                  256 * (kSites / 1024 + kLats) + 4 * kSites + 16 * kSites + 8 * 256;
 constexpr int64_t kScratchWords = kScratchBytes / 4 + 64;
 
 static __device__ __align__(256) int32_t g_ccl_scratch[kScratchWords];
