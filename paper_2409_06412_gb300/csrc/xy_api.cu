@@ -1754,9 +1754,7 @@ int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, i
         int32_t* lab_out = dev_lab ? labels + b0 * N : lab;
         int64_t* h_out = hist ? (dev_hist ? hist + b0 * hist_cap * 2 : hs) : nullptr;
         int64_t* ns_out = n_sizes ? (dev_ns ? n_sizes + b0 : ns) : nullptr;
-        if (h_out) e = cudaMemsetAsync(h_out, 0, sizeof(int64_t) * 2 * hist_cap * nl, L->stream);
-        if (e == cudaSuccess)
-            e = launch_ccl(L->thA + site0 + b0 * N, Lx, Ly, nl, lab_out, scratch, h_out,
+        e = launch_ccl(L->thA + site0 + b0 * N, Lx, Ly, nl, lab_out, scratch, h_out,
                            hist ? hist_cap : 0, ns_out, L->d_err, L->stream);
         if (e != cudaSuccess) {
             rc = fail(XY_ECUDA, "labelling: %s", cudaGetErrorString(e));

@@ -15,8 +15,9 @@
 //           A piece that does not reach the tile's edge is a whole domain and
 //           goes into the size histogram at once; one that does goes on a
 //           short list (batch index, local size) for the merge.
-//   border  one warp per tile edge: one union in global memory per pair of
-//           runs that touch across the edge.
+//   border  one warp per tile, from the spins and tile roots of the edge sites
+//           that the tile pass kept: one union in global memory per pair of
+//           runs that touch across the tile's right and bottom edges.
 //   sizes   the listed pieces add their local sizes at their domain's root's
 //           entry of the list (and point their tile roots at the root); the
 //           roots' entries then enter the histogram.
@@ -205,7 +206,7 @@ struct TileSmem {
 // Pass 1: one warp per tile of up to 32 x 32 sites (the last tile of a row or
 // column of tiles may be narrower).  Tile-local indices y * 32 + x order like
 // global indices, so a tile root is its piece's smallest site.
-__global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const float* __restrict__ theta, int Lx, int Ly,
+__global__ void __launch_bounds__(32 * kTileWarps, 12) ccl_tile_kernel(const float* __restrict__ theta, int Lx, int Ly,
                                                                      int n_lat, int32_t* __restrict__ labels,
                                                                      int want_sizes, CclScratch s, int* err)
 {
@@ -227,15 +228,18 @@ __global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const floa
     int* P = sm[wib].P;
     int* H = sm[wib].H;
 
-    // the rows' spins as masks (lane y keeps row y); all 32 loads in flight
-    float v[32];
-#pragma unroll
-    for (int y = 0; y < 32; ++y) v[y] = (y < thh && lane < tw) ? th[y * Lx + lane] : 0.0f;
+    // the rows' spins as masks (lane y keeps row y); 16 loads in flight per lane
     unsigned row = 0;
 #pragma unroll
-    for (int y = 0; y < 32; ++y) {
-        const unsigned m = __ballot_sync(kAll, spin_of(v[y])) & vm;
-        if (lane == y) row = m;
+    for (int h = 0; h < 32; h += 16) {
+        float v[16];
+#pragma unroll
+        for (int y = 0; y < 16; ++y) v[y] = (h + y < thh && lane < tw) ? th[(h + y) * Lx + lane] : 0.0f;
+#pragma unroll
+        for (int y = 0; y < 16; ++y) {
+            const unsigned m = __ballot_sync(kAll, spin_of(v[y])) & vm;
+            if (lane == h + y) row = m;
+        }
     }
     const unsigned st = run_starts(row, vm);  // lane y: the run starts of row y
 
@@ -298,7 +302,9 @@ __global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const floa
         __syncwarp();
     }
 
-    // labels, a row at a time (coalesced): each site's root through its run start
+    // labels, a row at a time (coalesced): each site's root through its run
+    // start; the tile roots and spins of the edge sites go to the border pass
+    uint16_t* er = s.edge_root + (int64_t)t * 128;  // top row, bottom row, left column, right column
 #pragma unroll 4
     for (int y = 0; y < thh; ++y) {
         const unsigned sy = __shfl_sync(kAll, st, y);
@@ -307,7 +313,17 @@ __global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const floa
             const int q = P[y * 33 + (i & 31)];
             const int r = q < 0 ? i : q;
             lab[y * Lx + lane] = (gy0 + (r >> 5)) * Lx + gx0 + (r & 31);
+            if (y == 0) er[lane] = (uint16_t)r;
+            if (y == thh - 1) er[32 + lane] = (uint16_t)r;
+            if (lane == 0) er[64 + y] = (uint16_t)r;
+            if (lane == tw - 1) er[96 + y] = (uint16_t)r;
         }
+    }
+    {
+        const unsigned left = __ballot_sync(kAll, lane < thh && (row & 1u));
+        const unsigned right = __ballot_sync(kAll, lane < thh && ((row >> (tw - 1)) & 1u));
+        const unsigned top = __shfl_sync(kAll, row, 0), bottom = __shfl_sync(kAll, row, thh - 1);
+        if (lane == 0) s.edge_spin[t] = make_uint4(top, bottom, left, right);
     }
     if (!want_sizes) return;
 
@@ -353,16 +369,17 @@ __global__ void __launch_bounds__(32 * kTileWarps, 9) ccl_tile_kernel(const floa
 }
 
 // Pass 2: merge across the right and bottom edge of every tile (periodic).
-// One warp per tile; lane k takes the k-th site of the right edge (linked to
-// its right neighbour) and of the bottom edge (linked to the site below).
-// Where the previous lane also touches and its site continues the run along
-// the edge (then so does the neighbour's, which has the same spin), the pair
-// of pieces is already linked: one union per pair of touching runs.  The
-// loads go in three rounds for both edges at once (spins, the sites' tile
-// roots, their parents); two roots are then linked straight away, anything
-// else goes through the general union.
-__global__ void __launch_bounds__(256) ccl_border_kernel(const float* __restrict__ theta, int Lx, int Ly, int n_lat,
-                                                         int32_t* labels, int* err)
+// One warp per tile; lane k takes the k-th site of the right edge (against
+// the first column of the next tile) and of the bottom edge (against the top
+// row of the tile below).  The spins and tile roots of edge sites come from
+// the tile pass (no angle or label is read along the edges).  Where the
+// previous lane also touches and its site continues the run along the edge
+// (then so does the neighbour's, which has the same spin), the pair of
+// pieces is already linked: one union per pair of touching runs.  The roots'
+// entries are read at once for both edges; two roots are then linked
+// straight away, anything else goes through the general union.
+__global__ void __launch_bounds__(256) ccl_border_kernel(int Lx, int Ly, int n_lat, int32_t* labels, CclScratch s,
+                                                         int* err)
 {
     const int lane = threadIdx.x & 31;
     const int tiles_x = (Lx + 31) >> 5, tiles_y = (Ly + 31) >> 5;
@@ -374,61 +391,52 @@ __global__ void __launch_bounds__(256) ccl_border_kernel(const float* __restrict
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const int gx0 = tx * 32, gy0 = ty * 32;
     const int tw = min(32, Lx - gx0), thh = min(32, Ly - gy0);
-    const int64_t N = (int64_t)Lx * Ly;
-    const float* th = theta + (int64_t)lat * N;
-    int32_t* L = labels + (int64_t)lat * N;
+    const int txr = tx + 1 == tiles_x ? 0 : tx + 1, tyb = ty + 1 == tiles_y ? 0 : ty + 1;
+    const int t0 = lat * tiles;
+    const int tr = t0 + ty * tiles_x + txr, tb = t0 + tyb * tiles_x + tx;  // the tiles to the right and below
+    int32_t* L = labels + (int64_t)lat * Lx * Ly;
     const int limit = g_union_limit;
-    // edge 0: right (column gx0 + tw - 1 against the next column); edge 1: bottom
+    const uint4 me = s.edge_spin[t];
+    const unsigned sp_right = me.w, sp_bottom = me.y;
+    const unsigned sp_nleft = s.edge_spin[tr].z, sp_ntop = s.edge_spin[tb].x;
+    const uint16_t* er = s.edge_root + (int64_t)t * 128;
+    // edge 0: right (rows k < thh); edge 1: bottom (columns k < tw)
     int a[2], b[2];
-    bool act[2];
-    {
-        const int y = gy0 + lane, x = gx0 + tw - 1;
-        act[0] = lane < thh;
-        a[0] = act[0] ? y * Lx + x : 0;
-        b[0] = act[0] ? y * Lx + (x + 1 == Lx ? 0 : x + 1) : 0;
-    }
-    {
-        const int y = gy0 + thh - 1, x = gx0 + lane;
-        act[1] = lane < tw;
-        a[1] = act[1] ? y * Lx + x : 0;
-        b[1] = act[1] ? (y + 1 == Ly ? 0 : y + 1) * Lx + x : 0;
-    }
-    float fa[2], fb[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        fa[e] = act[e] ? th[a[e]] : 0.0f;
-        fb[e] = act[e] ? th[b[e]] : 0.0f;
-    }
     bool need[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const bool sa = act[e] && spin_of(fa[e]);
-        const bool touch = act[e] && sa == spin_of(fb[e]);
+        const bool act = lane < (e == 0 ? thh : tw);
+        const unsigned ms = e == 0 ? sp_right : sp_bottom, mn = e == 0 ? sp_nleft : sp_ntop;
+        const bool sa = act && ((ms >> lane) & 1u);
+        const bool touch = act && sa == (((mn >> lane) & 1u) != 0);
         const unsigned tm = __ballot_sync(kAll, touch);
         const bool prev_sa = __shfl_up_sync(kAll, sa, 1);
         need[e] = touch && !(lane > 0 && ((tm >> (lane - 1)) & 1u) && prev_sa == sa);
+        a[e] = b[e] = 0;
+        if (need[e]) {
+            const int ra = er[(e == 0 ? 96 : 32) + lane];
+            const int rb = s.edge_root[(int64_t)(e == 0 ? tr : tb) * 128 + (e == 0 ? 64 : 0) + lane];
+            const int gxn = e == 0 ? txr * 32 : gx0, gyn = e == 0 ? gy0 : tyb * 32;
+            a[e] = (gy0 + (ra >> 5)) * Lx + gx0 + (ra & 31);
+            b[e] = (gyn + (rb >> 5)) * Lx + gxn + (rb & 31);
+        }
     }
-    int la[2], lb[2], ra[2], rb[2];
+    int pa[2], pb[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        la[e] = need[e] ? L[a[e]] : 0;
-        lb[e] = need[e] ? L[b[e]] : 0;
-    }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        ra[e] = need[e] ? L[la[e]] : 0;
-        rb[e] = need[e] ? L[lb[e]] : 0;
+        pa[e] = need[e] ? L[a[e]] : 0;
+        pb[e] = need[e] ? L[b[e]] : 0;
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         if (!need[e]) continue;
-        if (ra[e] == la[e] && rb[e] == lb[e]) {  // two roots
-            if (la[e] == lb[e]) continue;
-            const int hi = max(la[e], lb[e]), lo = min(la[e], lb[e]);
+        if (pa[e] == a[e] && pb[e] == b[e]) {  // two roots
+            if (a[e] == b[e]) continue;
+            const int hi = max(a[e], b[e]), lo = min(a[e], b[e]);
             const int old = atomicMin(&L[hi], lo);
             if (old != hi) union_global(L, old, lo, limit, err);  // hi was linked meanwhile
         } else {
-            union_global(L, la[e], lb[e], limit, err);
+            union_global(L, a[e], b[e], limit, err);
         }
     }
 }
@@ -574,22 +582,22 @@ __global__ void __launch_bounds__(256, 4) ccl_flatten_kernel(int Lx, int Ly, int
 }
 
 // Pass 5: ordered compaction of the nonzero counts into (size, count) pairs,
-// one block per lattice, ascending size.  Sizes 1..63 are summed over their
-// copies;
-// larger ones through the bitmap, one bit per size, whose words are split into
-// contiguous ranges, one per warp, so the order of the warps is the order of
-// the sizes.  Each warp counts its set bits, one block-wide prefix places
-// them, and a second walk writes them and clears what it read.
+// one block per lattice, ascending size; the rest of the lattice's hist_cap
+// pairs is zeroed.  Sizes 1..63 are summed over their copies; larger ones
+// are found through the bitmap, one bit per size, a word per thread per
+// round in order: each round's set bits are placed by one block-wide prefix,
+// and each thread writes its word's pairs and clears what it read.
 __global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, CclScratch s, int64_t* hist, int64_t hist_cap,
                                                            int64_t* n_sizes, int* err)
 {
-    __shared__ int64_t s_warp[32];
+    __shared__ int s_warp[32];
     __shared__ int s_small[kSmallSizes];
+    __shared__ int64_t s_pos;
     const int lat = blockIdx.x;
     int32_t* cnt = s.counts + (int64_t)lat * (N + 1);
     uint32_t* bw = s.bits + (int64_t)lat * s.words;
     int64_t* out = hist ? hist + (int64_t)lat * hist_cap * 2 : nullptr;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_small = (int)(N < kSmallSizes - 1 ? N : kSmallSizes - 1);  // sizes 1..n_small
     if (threadIdx.x < kSmallSizes) {
         const int z = threadIdx.x;
@@ -606,60 +614,73 @@ __global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, CclScratch
         }
         s_small[z] = v;
     }
-    // words holding sizes >= 64
-    const int64_t w0 = kSmallSizes / 32;
-    const int64_t per = (s.words - w0 + nw - 1) / nw;
-    const int64_t lo = w0 + (int64_t)warp * per;
-    const int64_t hi = lo + per < s.words ? lo + per : s.words;
-    int64_t mine = 0;
-    for (int64_t w = lo + lane; w < hi; w += 32) mine += __popc(bw[w]);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(kAll, mine, d);
-    if (lane == 0) s_warp[warp] = mine;
     __syncthreads();
-    int64_t small_total = 0;
-    for (int z = 1; z < kSmallSizes; ++z) small_total += s_small[z] != 0;
-    int64_t pos = small_total, total = small_total;
-    for (int w = 0; w < nw; ++w) {
-        if (w < warp) pos += s_warp[w];
-        total += s_warp[w];
-    }
-    if (out && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         int64_t at = 0;
         for (int z = 1; z < kSmallSizes; ++z)
             if (s_small[z] != 0) {
-                if (at < hist_cap) {
+                if (out && at < hist_cap) {
                     out[2 * at] = z;
                     out[2 * at + 1] = s_small[z];
                 }
                 ++at;
             }
+        s_pos = at;
     }
-    for (int64_t wb = lo; wb < hi; wb += 32) {
-        const int64_t w = wb + lane;
-        const uint32_t word = w < hi ? bw[w] : 0u;
-        // lanes in word order: each lane's first position after the lanes before it
-        int before = __popc(word);
+    __syncthreads();
+    // words holding sizes >= 64: round k of a chunk gives thread j the word
+    // k * blockDim + j, so the order within a round is the order of the
+    // threads; all 32 rounds' words are read at once
+    const int64_t w0 = kSmallSizes / 32;
+    const int nt = blockDim.x;
+    for (int64_t wc = w0; wc < s.words; wc += 32 * (int64_t)nt) {
+        uint32_t wd[32];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int o = __shfl_up_sync(kAll, before, d);
-            if (lane >= d) before += o;
+        for (int k = 0; k < 32; ++k) {
+            const int64_t w = wc + (int64_t)k * nt + threadIdx.x;
+            wd[k] = w < s.words ? bw[w] : 0u;
         }
-        const int all = __shfl_sync(kAll, before, 31);
-        int64_t at = pos + before - __popc(word);
-        for (uint32_t b = word; b; b &= b - 1) {
-            const int64_t z = (w << 5) + __ffs(b) - 1;
-            const int v = cnt[z];
-            if (out && at < hist_cap) {
-                out[2 * at] = z;
-                out[2 * at + 1] = v;
+#pragma unroll 1
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t word = wd[k];
+            if (!__syncthreads_or(word != 0u)) continue;  // uniform
+            const int c = __popc(word);
+            int before = c;  // inclusive prefix over the warp
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(kAll, before, d);
+                if (lane >= d) before += o;
             }
-            cnt[z] = 0;
-            ++at;
+            if (lane == 31) s_warp[warp] = before;
+            __syncthreads();
+            int64_t at = s_pos + before - c;
+            int round = 0;
+            for (int w = 0; w < (nt >> 5); ++w) {
+                if (w < warp) at += s_warp[w];
+                round += s_warp[w];
+            }
+            const int64_t w = wc + (int64_t)k * nt + threadIdx.x;
+            for (uint32_t b = word; b; b &= b - 1) {
+                const int64_t z = (w << 5) + __ffs(b) - 1;
+                if (out && at < hist_cap) {
+                    out[2 * at] = z;
+                    out[2 * at + 1] = cnt[z];
+                }
+                cnt[z] = 0;
+                ++at;
+            }
+            if (word) bw[w] = 0;
+            __syncthreads();  // every thread has read s_pos and s_warp
+            if (threadIdx.x == 0) s_pos += round;
+            __syncthreads();
         }
-        if (word) bw[w] = 0;
-        pos += all;
     }
+    const int64_t total = s_pos;
+    if (out)
+        for (int64_t i = total + threadIdx.x; i < hist_cap; i += blockDim.x) {
+            out[2 * i] = 0;
+            out[2 * i + 1] = 0;
+        }
     if (threadIdx.x == 0) {
         if (n_sizes) n_sizes[lat] = total;
         if (out && total > hist_cap) atomicExch(err, XY_EINVAL);
@@ -702,7 +723,8 @@ int64_t ccl_scratch_bytes(int Lx, int Ly, int n_lat, int64_t* zeroed_bytes)
                       round_up((int64_t)4 * kSmallSizes * small_copies(Lx, Ly) * n_lat);
     if (zeroed_bytes) *zeroed_bytes = z;
     const int64_t cap = list_capacity(Lx, Ly, n_lat);
-    return z + round_up(4 * N * n_lat) + 2 * round_up(8 * cap) + kAlign;
+    const int64_t tiles = (int64_t)((Lx + 31) / 32) * ((Ly + 31) / 32) * n_lat;
+    return z + round_up(4 * N * n_lat) + 2 * round_up(8 * cap) + round_up(256 * tiles) + round_up(16 * tiles) + kAlign;
 }
 
 CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat)
@@ -725,6 +747,11 @@ CclScratch ccl_scratch_carve(void* base, int Lx, int Ly, int n_lat)
     p += round_up(8 * s.list_cap);
     s.aux = reinterpret_cast<int2*>(p);
     p += round_up(8 * s.list_cap);
+    const int64_t tiles = (int64_t)((Lx + 31) / 32) * ((Ly + 31) / 32) * n_lat;
+    s.edge_root = reinterpret_cast<uint16_t*>(p);
+    p += round_up(256 * tiles);
+    s.edge_spin = reinterpret_cast<uint4*>(p);
+    p += round_up(16 * tiles);
     s.list_n = reinterpret_cast<int*>(p);
     return s;
 }
@@ -741,7 +768,7 @@ cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* l
     if ((e = cudaMemsetAsync(s.list_n, 0, sizeof(int), st)) != cudaSuccess) return e;
     ccl_tile_kernel<<<(unsigned)((tiles + kTileWarps - 1) / kTileWarps), 32 * kTileWarps, 0, st>>>(
         theta, Lx, Ly, n_lat, labels, 1, s, err);
-    ccl_border_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(theta, Lx, Ly, n_lat, labels, err);
+    ccl_border_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(Lx, Ly, n_lat, labels, s, err);
     const unsigned g = (unsigned)std::min<int64_t>((s.list_cap + 255) / 256, 152 * 8);
     ccl_list_size_kernel<<<g, 256, 0, st>>>(N, labels, s, err);
     ccl_list_hist_kernel<<<g, 256, 0, st>>>(N, s, err);

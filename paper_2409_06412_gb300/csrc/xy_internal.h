@@ -168,6 +168,8 @@ struct CclScratch {
     int32_t* entry;
     int2* list;
     int2* aux;
+    uint16_t* edge_root;  // per tile: tile roots of the top row, bottom row, left and right columns (32 each)
+    uint4* edge_spin;     // per tile: spin masks of the same (top, bottom, left, right)
     int* list_n;
     int64_t list_cap;
     int64_t words;  // bitmap words per lattice

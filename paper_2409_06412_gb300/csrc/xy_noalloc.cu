@@ -25,12 +25,15 @@ namespace {
 // counts, 4 per 32 sizes and 8 per lattice of bitmap, 256 bytes per copy of
 // the small size counts (one copy per 32 tiles of at least 32 sites, at least
 // one per lattice), 4 per site of list index, at most 16 per site of list (a
-// tile has no more pieces on its edge than sites), and the alignment of each
-// part.
+// tile has no more pieces on its edge than sites), 272 per tile of edge data
+// (ceil(Lx/32) ceil(Ly/32) <= N/1024 + Lx/32 + Ly/32 + 1 <= N/24 + 1 tiles per
+// lattice, as Lx >= 4), and the alignment of each part.  The call checks its
+// own layout against this size.
 constexpr int64_t kSites = XY_STATIC_CCL_MAX_SITES;
 constexpr int64_t kLats = XY_STATIC_CCL_MAX_LATTICES;
 constexpr int64_t kScratchBytes = 4 * (kSites + kLats) + 4 * (kSites / 32 + 2 * kLats) +
-                                  256 * (kSites / 1024 + kLats) + 4 * kSites + 16 * kSites + 8 * 256;
+                                  256 * (kSites / 1024 + kLats) + 4 * kSites + 16 * kSites +
+                                  272 * (kSites / 24 + kLats) + 10 * 256;
 constexpr int64_t kScratchWords = kScratchBytes / 4 + 64;
 
 static __device__ __align__(256) int32_t g_ccl_scratch[kScratchWords];
@@ -114,7 +117,6 @@ extern "C" int xy_label_domains_static(const float* theta, int Lx, int Ly, int n
     // the array keeps the previous call's contents: clear what must start at zero
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, zeroed, st);
-    if (e == cudaSuccess && hist) e = cudaMemsetAsync(hist, 0, sizeof(int64_t) * 2 * hist_cap * n_lattices, st);
     if (e == cudaSuccess)
         e = xy::launch_ccl(theta, Lx, Ly, n_lattices, labels, scratch, hist, hist ? hist_cap : 0, n_sizes, err, st);
     int herr = 0;

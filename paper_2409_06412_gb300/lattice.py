@@ -158,8 +158,8 @@ class Lattice:
         c = self.configs[self.b_cfg[b_first]]
         N = c.Lx * c.Ly
         labels = torch.empty((b_count, N), dtype=torch.int32, device=self.device)
-        hist = torch.zeros((b_count, hist_cap, 2), dtype=torch.int64, device=self.device)
-        n_sizes = torch.zeros(b_count, dtype=torch.int64, device=self.device)
+        hist = torch.empty((b_count, hist_cap, 2), dtype=torch.int64, device=self.device)
+        n_sizes = torch.empty(b_count, dtype=torch.int64, device=self.device)
         L.call("xy_label_domains", self._h, b_first, b_count, _ptr(labels), _ptr(hist), hist_cap, _ptr(n_sizes))
         return labels, hist, n_sizes
 
