@@ -192,6 +192,23 @@ def ncu_traffic(kernel):
     return None
 
 
+def time_labels(lat, b0, n, calls=5):
+    """Seconds per domain-labelling call of lattices [b0, b0 + n) (the
+    library call through its Python binding, outputs on the device), median
+    of `calls` after two warm-up calls that also size the working memory."""
+    import torch
+    for _ in range(2):
+        lat.label_domains(b0, n)
+    ts = []
+    for _ in range(calls):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, n_sizes = lat.label_domains(b0, n)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return sorted(ts)[len(ts) // 2], n_sizes
+
+
 def cuda_time(fn, stream):
     import torch
     a = torch.cuda.Event(enable_timing=True)
@@ -432,14 +449,10 @@ def run_ours(args):
     if rank == 0 and KZ:
         # domain labels of the frozen state of the tau_Q = 100 ramps (the
         # first 64 lattices, retired at k = 1150 when the window passes it)
-        lat.label_domains(0, 8)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, _, n_sizes = lat.label_domains(0, 64)
-        torch.cuda.synchronize()
-        tl = time.perf_counter() - t0
+        tl, n_sizes = time_labels(lat, 0, 64)
         extra["ccl"] = {"value": 64 * 1024 * 1024 / tl, "unit": "labelled sites/s", "lattices": 64, "L": 1024,
-                        "step": int(lat.observe()[1][0]), "distinct_domain_sizes_max": int(n_sizes.max())}
+                        "step": int(lat.observe()[1][0]), "distinct_domain_sizes_max": int(n_sizes.max()),
+                        "timing": "median of 5 calls after 2 warm-up calls, host clock around the synchronised call"}
 
     if rank == 0 and args.workload == "static":
         # plain per-configuration launch path on the same batch
@@ -453,13 +466,10 @@ def run_ours(args):
 
         # domain labelling throughput on the 512 L = 1024 lattices (first 64)
         b0 = 3 * N_TEMPS * N_REP
-        lat.label_domains(b0, 8)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        lat.label_domains(b0, 64)
-        torch.cuda.synchronize()
-        tl = time.perf_counter() - t0
-        extra["ccl"] = {"value": 64 * 1024 * 1024 / tl, "unit": "labelled sites/s", "lattices": 64, "L": 1024}
+        tl, n_sizes = time_labels(lat, b0, 64)
+        extra["ccl"] = {"value": 64 * 1024 * 1024 / tl, "unit": "labelled sites/s", "lattices": 64, "L": 1024,
+                        "distinct_domain_sizes_max": int(n_sizes.max()),
+                        "timing": "median of 5 calls after 2 warm-up calls, host clock around the synchronised call"}
 
         # correlation lengths of the same 64 lattices: structure factors for k < 16 (timed), then over
         # the half zone for the fit, whose window follows each direction's length (xi_perp is below a
