@@ -157,7 +157,10 @@ int xy_omega_full(xy_lattice* lat, int b_first, int b_count, float* out);
  * int64[b_count][hist_cap][2] of (size, count) pairs in ascending size,
  * zero-padded; n_sizes (nullable; host or device): int64[b_count] number of
  * distinct sizes.  Returns XY_EINVAL (after writing labels) if a lattice has
- * more than hist_cap distinct sizes. */
+ * more than hist_cap distinct sizes.  The working memory (about 8.5 bytes per
+ * site of the call, 4 more when labels go to host memory) is allocated on the
+ * first call that needs more than the lattice object holds and kept until
+ * xy_lattice_destroy; XY_ENOMEM if it cannot be allocated.  Synchronous. */
 int xy_label_domains(xy_lattice* lat, int b_first, int b_count, int32_t* labels, int64_t* hist,
                      int64_t hist_cap, int64_t* n_sizes);
 
@@ -173,10 +176,10 @@ int xy_label_domains(xy_lattice* lat, int b_first, int b_count, int32_t* labels,
  *   labels: device int32[n_lattices][Ly*Lx]; hist (nullable): device
  *   int64[n_lattices][hist_cap][2]; n_sizes (nullable): device
  *   int64[n_lattices]; cuda_stream: the stream the work runs on.
- * Working memory is one fixed array inside the library image,
- * 4 * (2 * XY_STATIC_CCL_MAX_SITES + XY_STATIC_CCL_MAX_LATTICES + 64) bytes
- * (about 16.3 MB) that every GPU which loads the library holds until the
- * process exits.  A call with more than XY_STATIC_CCL_MAX_SITES sites or
+ * Working memory is one fixed array inside the library image, sized for the
+ * worst lattice shape within the limits below (about 105 MB: narrow lattices
+ * cut into many small tiles), that every GPU which loads the library holds
+ * until the process exits.  A call with more than XY_STATIC_CCL_MAX_SITES sites or
  * XY_STATIC_CCL_MAX_LATTICES lattices returns XY_EINVAL without launching
  * anything.  Every call shares that array and it keeps the previous call's
  * contents (each call clears what must start at zero), so calls whose work
