@@ -20,6 +20,8 @@
 
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "xy_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -960,6 +962,13 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
     const StepConst K0 = step_const(cf, 0.f);
     const bool const_T = cf.sched_kind == 0 && cf.n_knots <= 1;
     const float c_const = noise_amp(cf, 0);
+    // without a field schedule h and h p are the configuration's own for every
+    // step: read once here, not from the descriptor after every cluster barrier
+    const bool const_h = cf.f_n_knots == 0;
+    const float h0 = cf.h;
+    // (each step loop below is compiled twice, with and without the schedule's
+    // code, and the block takes one of them: without a schedule the loop
+    // carries none of the knot search's registers)
     const bool stag = cf.stag != 0;
     const int64_t kbase = cf.k_start + ca.k_shift;
     // noise of the band's single row (R = 1) at step k, computed one step
@@ -981,11 +990,13 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
         float4 v4 = ld4(s_om + y * Lx + x);
         const float2* up_base = cl.map_shared_rank(s_exp + lb_up * Lx + x, rank_up);
         const float2* dn_base = cl.map_shared_rank(s_exp + lb_dn * Lx + x, rank_dn);
+        auto steps = [&](auto fs) {
+        constexpr bool FS = decltype(fs)::value;
         for (int64_t j = j0; j < j1; ++j) {
             const int64_t k = kbase + j;
             StepConst K = K0;
             K.c = const_T ? c_const : noise_amp(cf, k);
-            K.hp = field_hp(cf, k);
+            K.hp = FS ? field_hp(cf, k) : K0.hp;
             const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
             const int par = (int)(j & 1);
             const size_t poff = (size_t)(2 * par) * NB * Lx;
@@ -1021,7 +1032,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                     const float sigma = (stag && ((x + s + gy) & 1)) ? -1.f : 1.f;
                     pm = fmaf(sigma, cur.s[s], pm);
                     if (!ca.m_only)
-                        pe = __fadd_rn(pe, site_energy(cf, field_h(cf, k), so.omega, cur.s[s], cur.c[s], sr, cr,
+                        pe = __fadd_rn(pe, site_energy(cf, FS ? field_h(cf, k) : h0, so.omega, cur.s[s], cur.c[s], sr, cr,
                                                        nxt.s[s], nxt.c[s], cosp_of(K.p, th)));
                 }
             }
@@ -1052,14 +1063,18 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                 }
             }
         }
+        };
+        if (const_h) steps(std::false_type{}); else steps(std::true_type{});
         st4(s_th + y * Lx + x, th4);
         st4(s_om + y * Lx + x, v4);
     } else {
+        auto steps = [&](auto fs) {
+        constexpr bool FS = decltype(fs)::value;
         for (int64_t j = j0; j < j1; ++j) {
             const int64_t k = kbase + j;
             StepConst K = K0;
             K.c = const_T ? c_const : noise_amp(cf, k);
-            K.hp = field_hp(cf, k);
+            K.hp = FS ? field_hp(cf, k) : K0.hp;
             const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
             const int par = (int)(j & 1);
             float2* e_top = s_exp + (size_t)(2 * par) * NB * Lx;
@@ -1115,7 +1130,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                         const float sigma = (stag && ((x + s + y_base + y) & 1)) ? -1.f : 1.f;
                         pm = fmaf(sigma, cur.s[s], pm);
                         if (!ca.m_only)
-                            pe = __fadd_rn(pe, site_energy(cf, field_h(cf, k), so.omega, cur.s[s], cur.c[s], sr, cr,
+                            pe = __fadd_rn(pe, site_energy(cf, FS ? field_h(cf, k) : h0, so.omega, cur.s[s], cur.c[s], sr, cr,
                                                            nxt.s[s], nxt.c[s], cosp_of(K.p, th)));
                     }
                 }
@@ -1150,6 +1165,8 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                 }
             }
         }
+        };
+        if (const_h) steps(std::false_type{}); else steps(std::true_type{});
     }
     // no block leaves while another may still read its shared memory
     cl.sync();
