@@ -1783,6 +1783,7 @@ int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, i
     if (!rc && !err) L->ccl_clean = zeroed;  // else some entries were left set
     if (rc) return rc;
     if (err == XY_EINVAL) return fail(XY_EINVAL, "a lattice has more distinct domain sizes than hist_cap");
+    if (err == XY_ENOMEM) return fail(XY_ENOMEM, "labelling: the list of pieces on tile edges overflowed");
     if (err) return fail(err, "labelling: a bounded union loop ran out of iterations");
     return XY_OK;
 }

@@ -23,10 +23,11 @@
 //           roots' entries then enter the histogram.
 //   flatten one warp per tile: every site points straight at its root.
 //   compact the histogram's nonzero entries become (size, count) pairs in
-//           ascending order: sizes below 64 are scanned directly, larger ones
-//           through a bitmap with one bit per size.
-// The histogram counts and the bitmap are zero between calls: the passes
-// clear every entry they set, so no pass reads or clears memory in
+//           ascending order: sizes below 64 are summed over the copies their
+//           counts are spread over, larger ones are found through a bitmap
+//           with one bit per size.
+// The histogram counts, their copies and the bitmap are zero between calls:
+// the passes clear every entry they set, so no pass reads or clears memory in
 // proportion to the lattice beyond the labels themselves.
 #include <algorithm>
 #include <cstdint>
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(32 * kTileWarps, 12) ccl_tile_kernel(const flo
                 s.aux[base] = make_int2(-1, 0);
                 s.entry[(int64_t)lat * N + g] = base;
             } else {
-                atomicExch(err, XY_EINVAL);
+                atomicExch(err, XY_ENOMEM);  // not reached: the capacity bounds the pieces on tile edges
             }
             ++base;
         } else if (sz < kSmallSizes) {

@@ -127,6 +127,8 @@ extern "C" int xy_label_domains_static(const float* theta, int Lx, int Ly, int n
         return fail_static(XY_ECUDA, cudaGetErrorString(e));
     }
     if (herr == XY_EINVAL) return fail_static(XY_EINVAL, "xy_label_domains_static: more distinct sizes than hist_cap");
+    if (herr == XY_ENOMEM)
+        return fail_static(XY_ENOMEM, "xy_label_domains_static: the list of pieces on tile edges overflowed");
     if (herr) return fail_static(herr, "xy_label_domains_static: a bounded union loop ran out of iterations");
     return XY_OK;
 }
