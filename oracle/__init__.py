@@ -69,17 +69,17 @@ def _declare(L):
     L.xyo_observe.argtypes = [i32, i32, vp, vp, vp, P(d), P(d)]
     L.xyo_field_scale.argtypes = [i64, i32, vp, vp]
     L.xyo_field_scale.restype = d
-    L.xyo_run_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64, vp, vp, i32, vp]
+    L.xyo_run_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, vp, i64, i64, vp, vp, i32, vp]
     L.xyo_run_lattice.restype = i64
-    L.xyo_run_strip.argtypes = [i32, i32, i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64,
+    L.xyo_run_strip.argtypes = [i32, i32, i32, i32, i32, i32, u64, vp, i32, vp, vp, vp, i64, i64,
                                 vp, vp, vp, i32, i32, i32, vp]
     L.xyo_run_strip.restype = i64
     L.xyo_harmonic_msd.argtypes = [i64, i64, d, d, d, d, u64, vp]
     L.xyo_ccl.argtypes = [i32, i32, vp, vp]
     L.xyo_ccl.restype = i64
-    L.xyo_adjoint_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64, vp, vp,
+    L.xyo_adjoint_lattice.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, vp, i64, i64, vp, vp,
                                       d, d, P(d), vp, vp, vp]
-    L.xyo_theta_sensitivity.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, i32, vp, vp, i64, i64, vp, vp,
+    L.xyo_theta_sensitivity.argtypes = [i32, i32, i32, i32, u64, vp, i32, vp, vp, vp, i64, i64, vp, vp,
                                         i32, vp, vp, vp, vp, vp, vp, vp, vp]
 
 
@@ -109,14 +109,39 @@ def _knots(knots):
 
 
 def _field(field):
-    """Field schedule arguments of the C oracle as (n, steps, scales): field
-    ((steps), (scales)) of h_k = h s(k), or None for s = 1."""
+    """A profile of the C oracle as (n, steps, scales): ((steps), (scales)),
+    or None for a constant 1."""
     if field is None:
         return 0, np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.float64)
     ks = np.ascontiguousarray(np.asarray(field[0], dtype=np.int64))
     ss = np.ascontiguousarray(np.asarray(field[1], dtype=np.float64))
     assert ks.shape == ss.shape and ks.ndim == 1
     return ks.size, ks, ss
+
+
+class _Sched(ctypes.Structure):
+    """xyo_sched: the field profile s(k) of h and the coupling profiles a(k),
+    b(k) of J_par and J_perp (one knot grid for both)."""
+    _fields_ = [("nf", ctypes.c_int), ("fks", ctypes.c_void_p), ("fss", ctypes.c_void_p),
+                ("nc", ctypes.c_int), ("cks", ctypes.c_void_p), ("cpar", ctypes.c_void_p),
+                ("cperp", ctypes.c_void_p)]
+
+
+def _sched(field=None, couplings=None):
+    """(struct, arrays it points into): field ((steps), (scales)) of h;
+    couplings ((steps), (scales of J_par), (scales of J_perp))."""
+    nf, fks, fss = _field(field)
+    if couplings is None:
+        nc, cks, ca, cb = 0, np.zeros(1, np.int64), np.zeros(1), np.zeros(1)
+    else:
+        cks = np.ascontiguousarray(np.asarray(couplings[0], dtype=np.int64))
+        ca = np.ascontiguousarray(np.asarray(couplings[1], dtype=np.float64))
+        cb = np.ascontiguousarray(np.asarray(couplings[2], dtype=np.float64))
+        assert cks.shape == ca.shape == cb.shape and cks.ndim == 1
+        nc = cks.size
+    keep = (fks, fss, cks, ca, cb)
+    st = _Sched(nf, fks.ctypes.data, fss.ctypes.data, nc, cks.ctypes.data, ca.ctypes.data, cb.ctypes.data)
+    return st, keep
 
 
 # ---------------------------------------------------------------- primitives
@@ -180,22 +205,23 @@ def observe(Lx, Ly, params, theta, omega):
     return M.value, E.value
 
 
-def run_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta, omega, record_every=0, field=None):
+def run_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta, omega, record_every=0, field=None,
+                couplings=None):
     """Advance one lattice in place; returns the (n_rec, 2) array of (M_k, E_k)."""
     prm = param_vector(params)
     nk, ks, Ts = _knots(knots)
-    nf, fks, fss = _field(field)
+    sc, _keep = _sched(field, couplings)
     assert theta.dtype == np.float64 and omega.dtype == np.float64
     assert theta.flags.c_contiguous and omega.flags.c_contiguous
     nrec_max = (n // record_every + 1) if record_every > 0 else 0
     rec = np.zeros((max(nrec_max, 1), 2), dtype=np.float64)
-    nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks), _ptr(fss),
+    nrec = lib().xyo_run_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), ctypes.byref(sc),
                                  k0, n, _ptr(theta), _ptr(omega), record_every, _ptr(rec))
     return rec[:nrec].copy()
 
 
 def run_strip(Lx, Ly, y0, cfg, rep, seed, params, knots, k0, n, theta, omega, F, rows=None, record_every=0,
-              field=None):
+              field=None, couplings=None):
     """Advance one row strip of an Lx x Ly lattice in place (see
     xyo_run_strip): theta, omega, F are (R, Lx) float64 buffers whose local
     row i is global row (y0 + i) mod Ly, F holding F(theta) on entry.  Rows
@@ -204,7 +230,7 @@ def run_strip(Lx, Ly, y0, cfg, rep, seed, params, knots, k0, n, theta, omega, F,
     ``rows`` = (r0, r1) of sigma sin(q theta) and of the site energy."""
     prm = param_vector(params)
     nk, ks, Ts = _knots(knots)
-    nf, fks, fss = _field(field)
+    sc, _keep = _sched(field, couplings)
     for a in (theta, omega, F):
         assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == theta.shape
     R = theta.shape[0]
@@ -212,8 +238,8 @@ def run_strip(Lx, Ly, y0, cfg, rep, seed, params, knots, k0, n, theta, omega, F,
     r0, r1 = (0, 0) if rows is None else rows
     nrec_max = (n // record_every + 1) if record_every > 0 else 0
     rec = np.zeros((max(nrec_max, 1), 2), dtype=np.float64)
-    nrec = lib().xyo_run_strip(Lx, Ly, y0, R, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks),
-                               _ptr(fss), k0, n, _ptr(theta), _ptr(omega), _ptr(F), r0, r1, record_every, _ptr(rec))
+    nrec = lib().xyo_run_strip(Lx, Ly, y0, R, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), ctypes.byref(sc),
+                               k0, n, _ptr(theta), _ptr(omega), _ptr(F), r0, r1, record_every, _ptr(rec))
     return rec[:nrec].copy()
 
 
@@ -235,26 +261,27 @@ def ccl(Lx, Ly, theta32) -> tuple[np.ndarray, np.ndarray]:
     return lab, hist
 
 
-def adjoint_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, wE, wM, field=None):
+def adjoint_lattice(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, wE, wM, field=None,
+                    couplings=None):
     """Objective sum_{k=k0+1}^{k0+n}(w_E E_k + w_M |M_k|) of one lattice, its
     gradient w.r.t. (J_par, J_perp, h, eta), and the final state."""
     prm = param_vector(params)
     nk, ks, Ts = _knots(knots)
-    nf, fks, fss = _field(field)
+    sc, _keep = _sched(field, couplings)
     th0 = np.ascontiguousarray(theta0, dtype=np.float64).ravel()
     om0 = np.ascontiguousarray(omega0, dtype=np.float64).ravel()
     grad = np.zeros(4, dtype=np.float64)
     obj = ctypes.c_double()
     th1 = np.empty_like(th0)
     om1 = np.empty_like(om0)
-    lib().xyo_adjoint_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks), _ptr(fss), k0, n,
+    lib().xyo_adjoint_lattice(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), ctypes.byref(sc), k0, n,
                               _ptr(th0), _ptr(om0), wE, wM, ctypes.byref(obj), _ptr(grad),
                               _ptr(th1), _ptr(om1))
     return obj.value, grad, th1, om1
 
 
 def theta_sensitivity(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omega0, targets, wt=None, wv=None,
-                      trajectory=False, fields=False, field=None):
+                      trajectory=False, fields=False, field=None, couplings=None):
     """First-order sensitivity of the final angles theta_t(k0 + n), t in
     ``targets``, to perturbations along the FP64 trajectory from the full-step
     state (theta0, omega0) (see xyo_theta_sensitivity): an (n_targets, 2)
@@ -265,7 +292,7 @@ def theta_sensitivity(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omeg
     fields lt, lv of the first target."""
     prm = param_vector(params)
     nk, ks, Ts = _knots(knots)
-    nf, fks, fss = _field(field)
+    sc, _keep = _sched(field, couplings)
     th0 = np.ascontiguousarray(theta0, dtype=np.float64).ravel()
     om0 = np.ascontiguousarray(omega0, dtype=np.float64).ravel()
     tg = np.ascontiguousarray(np.asarray(targets, dtype=np.int64).ravel())
@@ -278,7 +305,7 @@ def theta_sensitivity(Lx, Ly, cfg, rep, seed, params, knots, k0, n, theta0, omeg
     lt = np.zeros((n, N)) if fields else None
     lv = np.zeros((n, N)) if fields else None
     p = lambda a: None if a is None else _ptr(a)
-    lib().xyo_theta_sensitivity(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), nf, _ptr(fks), _ptr(fss),
+    lib().xyo_theta_sensitivity(Lx, Ly, cfg, rep, seed, _ptr(prm), nk, _ptr(ks), _ptr(Ts), ctypes.byref(sc),
                                 k0, n, _ptr(th0), _ptr(om0),
                                 int(tg.size), _ptr(tg), p(w_t), p(w_v), _ptr(out), p(tth), p(tom), p(lt), p(lv))
     res = (out,)
@@ -299,7 +326,8 @@ def run_batch(configs, thetas, omegas, step_now, n, record_every=0, t0=0, thread
     """Advance a batch of lattices described like the library's configurations.
 
     configs: list of dicts with keys Lx, Ly, n_rep, seed, params, knots, n_total
-    (and optionally field: ((steps), (scales)) of h_k = h s(k)).
+    (and optionally field: ((steps), (scales)) of h_k = h s(k); couplings:
+    ((steps), (scales of J_par), (scales of J_perp))).
     thetas/omegas: per config, float64 arrays (n_rep, Ly*Lx) updated in place
     (omega is the full-step angular velocity).  step_now: per config step
     counters (list, updated).  Returns (rec, moments) with rec[c] of shape
@@ -319,7 +347,7 @@ def run_batch(configs, thetas, omegas, step_now, n, record_every=0, t0=0, thread
         c, r, k0, ne = job
         cf = configs[c]
         return run_lattice(cf["Lx"], cf["Ly"], c, r, cf["seed"], cf["params"], cf["knots"], k0, ne,
-                           thetas[c][r], omegas[c][r], record_every, cf.get("field"))
+                           thetas[c][r], omegas[c][r], record_every, cf.get("field"), cf.get("couplings"))
 
     with ThreadPoolExecutor(max_workers=threads or _workers()) as ex:
         results = list(ex.map(work, jobs))

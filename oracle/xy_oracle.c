@@ -166,11 +166,11 @@ double xyo_temperature(int64_t k, int n_knots, const int64_t* ks, const double* 
     return Ts[n_knots - 1];
 }
 
-/* Noise amplitude of one half-kick: (1/2) sqrt(2 eta k_B T) sqrt(dt), App. A.1. */
-/* Field schedule of the orthogonal quench (Sec. VII names quenches that cross
- * the phase boundary T_c(h) of App. D at an angle): h_k = h s(k), with s
- * piecewise linear through (ks[i], ss[i]) and constant outside them; n = 0
- * means s = 1. */
+/* A parameter profile: the field schedule of the orthogonal quench (Sec. VII
+ * names quenches that cross the phase boundary T_c(h) of App. D at an
+ * angle), h_k = h s(k), and the coupling profiles of the anisotropic quench.
+ * Piecewise linear through (ks[i], ss[i]) and constant outside them; n = 0
+ * means 1. */
 double xyo_field_scale(int64_t k, int n, const int64_t* ks, const double* ss)
 {
     if (n <= 0) return 1.0;
@@ -183,11 +183,30 @@ double xyo_field_scale(int64_t k, int n, const int64_t* ks, const double* ss)
     return ss[n - 1];
 }
 
-/* The parameter vector of time point k: h replaced by h s(k). */
-static void params_at(const double* prm, int64_t k, int nf, const int64_t* fks, const double* fss, double* out)
+/* Schedules of the parameters beside T(k): the field profile s(k) of the
+ * orthogonal quench, and the anisotropic quench's profiles a(k), b(k) of the
+ * two directional couplings, J_par(k) = J_par a(k), J_perp(k) = J_perp b(k)
+ * (the quench moves the two coupling directions of App. D's coupling space
+ * at different rates).  Each is piecewise linear through its knots and
+ * constant outside them (xyo_field_scale); n = 0 means 1. */
+typedef struct {
+    int nf;
+    const int64_t* fks;
+    const double* fss;
+    int nc;
+    const int64_t* cks;
+    const double* cpar;
+    const double* cperp;
+} xyo_sched;
+
+/* The parameter vector of time point k: h, J_par and J_perp scaled by their
+ * profiles. */
+static void params_at(const double* prm, int64_t k, const xyo_sched* sc, double* out)
 {
     memcpy(out, prm, sizeof(double) * P_COUNT);
-    out[P_H] = prm[P_H] * xyo_field_scale(k, nf, fks, fss);
+    out[P_H] = prm[P_H] * xyo_field_scale(k, sc->nf, sc->fks, sc->fss);
+    out[P_JPAR] = prm[P_JPAR] * xyo_field_scale(k, sc->nc, sc->cks, sc->cpar);
+    out[P_JPERP] = prm[P_JPERP] * xyo_field_scale(k, sc->nc, sc->cks, sc->cperp);
 }
 
 static double half_kick_amp(double eta, double T, double dt)
@@ -310,7 +329,7 @@ static void lattice_force_cb(const void* ctx, const double* x, double* F)
  * Returns the number of records written. */
 int64_t xyo_run_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const double* prm,
                         int n_knots, const int64_t* knot_step, const double* knot_T,
-                        int nf, const int64_t* fks, const double* fss,
+                        const xyo_sched* sc,
                         int64_t k0, int64_t n, double* theta, double* omega,
                         int record_every, double* rec)
 {
@@ -324,12 +343,12 @@ int64_t xyo_run_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const d
     lattice_ctx ctx = { Lx, Ly, prm_next };
     int64_t nrec = 0;
 
-    params_at(prm, k0, nf, fks, fss, prm_k);
+    params_at(prm, k0, sc, prm_k);
     xyo_force(Lx, Ly, prm_k, theta, F);
     gauss_field(seed, cfg, rep, N, k0, nz0);
     for (int64_t j = 0; j < n; ++j) {
         int64_t k = k0 + j;
-        params_at(prm, k, nf, fks, fss, prm_k);
+        params_at(prm, k, sc, prm_k);
         if (record_every > 0 && k % record_every == 0) {
             xyo_observe(Lx, Ly, prm_k, theta, omega, &rec[2 * nrec], &rec[2 * nrec + 1]);
             ++nrec;
@@ -338,7 +357,7 @@ int64_t xyo_run_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const d
         double amp0 = half_kick_amp(eta, xyo_temperature(k, n_knots, knot_step, knot_T), dt);
         double amp1 = half_kick_amp(eta, xyo_temperature(k + 1, n_knots, knot_step, knot_T), dt);
         /* the force at the new position belongs to time point k + 1 */
-        params_at(prm, k + 1, nf, fks, fss, prm_next);
+        params_at(prm, k + 1, sc, prm_next);
         bbk_step(N, theta, omega, F, nz0, nz1, amp0, amp1, eta, dt, 1, lattice_force_cb, &ctx, wh);
         double* t = nz0; nz0 = nz1; nz1 = t;
     }
@@ -387,7 +406,7 @@ static void strip_force(int Lx, int R, const double* prm, const double* th, doub
  * k % record_every == 0, before the step.  Returns the number of records. */
 int64_t xyo_run_strip(int Lx, int Ly, int y0, int R, int cfg, int rep, uint64_t seed, const double* prm,
                       int n_knots, const int64_t* knot_step, const double* knot_T,
-                      int nf, const int64_t* fks, const double* fss,
+                      const xyo_sched* sc,
                       int64_t k0, int64_t n, double* theta, double* omega, double* F,
                       int r0, int r1, int record_every, double* rec)
 {
@@ -401,7 +420,7 @@ int64_t xyo_run_strip(int Lx, int Ly, int y0, int R, int cfg, int rep, uint64_t 
 
     for (int64_t j = 0; j < n; ++j) {
         int64_t k = k0 + j;
-        params_at(prm, k, nf, fks, fss, prm_k);
+        params_at(prm, k, sc, prm_k);
         if (record_every > 0 && k % record_every == 0) {
             int stag = prm_k[P_STAG] != 0.0;
             double sm = 0.0, se = 0.0;
@@ -438,7 +457,7 @@ int64_t xyo_run_strip(int Lx, int Ly, int y0, int R, int cfg, int rep, uint64_t 
             wh[s] = (1.0 - 0.5 * eta * dt) * omega[s] + 0.5 * dt * F[s] + amp0 * nz0[s];
         for (int64_t s = 0; s < M; ++s)
             theta[s] = xyo_wrap(theta[s] + wh[s] * dt);
-        params_at(prm, k + 1, nf, fks, fss, prm_k);
+        params_at(prm, k + 1, sc, prm_k);
         strip_force(Lx, R, prm_k, theta, F);
         for (int64_t s = 0; s < M; ++s)
             omega[s] = (wh[s] + 0.5 * dt * F[s] + amp1 * nz1[s]) / (1.0 + 0.5 * eta * dt);
@@ -609,7 +628,7 @@ static void observation_grad(int Lx, int Ly, const double* prm, const double* th
  * theta_out/omega_out (nullable) receive the final state. */
 void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const double* prm,
                          int n_knots, const int64_t* knot_step, const double* knot_T,
-                         int nf, const int64_t* fks, const double* fss,
+                         const xyo_sched* sc,
                          int64_t k0, int64_t n, const double* theta0, const double* omega0,
                          double wE, double wM, double* obj_out, double* grad,
                          double* theta_out, double* omega_out)
@@ -627,7 +646,7 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
 
     /* the parameters of every time point k0 .. k0 + n (the field h s(k)) */
     double* prmj = (double*)malloc(sizeof(double) * P_COUNT * (n + 1));
-    for (int64_t j = 0; j <= n; ++j) params_at(prm, k0 + j, nf, fks, fss, prmj + P_COUNT * j);
+    for (int64_t j = 0; j <= n; ++j) params_at(prm, k0 + j, sc, prmj + P_COUNT * j);
     memcpy(th, theta0, sizeof(double) * N);
     memcpy(om, omega0, sizeof(double) * N);
     xyo_force(Lx, Ly, prmj, th, F);
@@ -660,10 +679,13 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
         double *t1 = th + N * (j + 1), *w1 = om + N * (j + 1), *z1 = nz + N * (j + 1);
         double gp[3] = { 0.0, 0.0, 0.0 };
         const double* p1 = prmj + P_COUNT * (j + 1);  /* parameters of time point j + 1 */
-        double s1 = xyo_field_scale(k0 + j + 1, nf, fks, fss);  /* d h_{j+1} / d h */
+        /* d h_{j+1} / d h, d J_par(j+1) / d J_par, d J_perp(j+1) / d J_perp */
+        double s1 = xyo_field_scale(k0 + j + 1, sc->nf, sc->fks, sc->fss);
+        double a1 = xyo_field_scale(k0 + j + 1, sc->nc, sc->cks, sc->cpar);
+        double b1 = xyo_field_scale(k0 + j + 1, sc->nc, sc->cks, sc->cperp);
         /* observation at j+1 */
         observation_grad(Lx, Ly, p1, t1, w1, wE, wM, tb, wb, gp);
-        gJx += gp[0]; gJy += gp[1]; gh += gp[2] * s1;
+        gJx += gp[0] * a1; gJy += gp[1] * b1; gh += gp[2] * s1;
         /* omega_{j+1} = b (wh_j + dt/2 F_{j+1} + amp_{j+1} n_{j+1}) */
         double ampb = 0.0;
         for (int64_t i = 0; i < N; ++i) {
@@ -678,7 +700,7 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
         for (int64_t i = 0; i < N; ++i) {
             double d[3];
             force_param_derivs(Lx, Ly, p1, t1, i, d);
-            gJx += Fb[i] * d[0]; gJy += Fb[i] * d[1]; gh += Fb[i] * d[2] * s1;
+            gJx += Fb[i] * d[0] * a1; gJy += Fb[i] * d[1] * b1; gh += Fb[i] * d[2] * s1;
         }
         /* theta_{j+1} = wrap(theta_j + dt wh_j) */
         for (int64_t i = 0; i < N; ++i) hb[i] += dt * tb[i];
@@ -694,11 +716,13 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
         (void)t0;
     }
     /* F_{k0} = F(theta_{k0}; params): theta_{k0} is fixed, the parameters are not */
-    double s0 = xyo_field_scale(k0, nf, fks, fss);
+    double s0 = xyo_field_scale(k0, sc->nf, sc->fks, sc->fss);
+    double a0 = xyo_field_scale(k0, sc->nc, sc->cks, sc->cpar);
+    double b0 = xyo_field_scale(k0, sc->nc, sc->cks, sc->cperp);
     for (int64_t i = 0; i < N; ++i) {
         double d[3];
         force_param_derivs(Lx, Ly, prmj, th, i, d);
-        gJx += Fb[i] * d[0]; gJy += Fb[i] * d[1]; gh += Fb[i] * d[2] * s0;
+        gJx += Fb[i] * d[0] * a0; gJy += Fb[i] * d[1] * b0; gh += Fb[i] * d[2] * s0;
     }
     grad[0] = gJx;
     grad[1] = gJy;
@@ -739,7 +763,7 @@ void xyo_adjoint_lattice(int Lx, int Ly, int cfg, int rep, uint64_t seed, const 
  * fields of the first target, [n][N] each, lt_out[j - 1] and lv_out[j]. */
 void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, const double* prm,
                            int n_knots, const int64_t* knot_step, const double* knot_T,
-                           int nf, const int64_t* fks, const double* fss,
+                           const xyo_sched* sc,
                            int64_t k0, int64_t n, const double* theta0, const double* omega0,
                            int n_targets, const int64_t* targets, const double* wt, const double* wv,
                            double* out, double* traj_theta, double* traj_omega,
@@ -757,7 +781,7 @@ void xyo_theta_sensitivity(int Lx, int Ly, int cfg, int rep, uint64_t seed, cons
     double* wh = (double*)malloc(sizeof(double) * N);
 
     double* prmj = (double*)malloc(sizeof(double) * P_COUNT * (n + 1));
-    for (int64_t j = 0; j <= n; ++j) params_at(prm, k0 + j, nf, fks, fss, prmj + P_COUNT * j);
+    for (int64_t j = 0; j <= n; ++j) params_at(prm, k0 + j, sc, prmj + P_COUNT * j);
     memcpy(th, theta0, sizeof(double) * N);
     memcpy(om, omega0, sizeof(double) * N);
     xyo_force(Lx, Ly, prmj, th, F);

@@ -27,6 +27,8 @@ adj_M = lambda P: P.test_adjoint_matches_finite_differences_smooth_field(0.0, 1.
 sens = lambda P: P.test_theta_sensitivity_matches_finite_differences()
 fwd_field = lambda P: P.test_adjoint_forward_equals_stepper(([5, 30], [0.4, 2.5]))
 adj_field = lambda P: P.test_adjoint_with_field_schedule_matches_finite_differences()
+cpl_exact = lambda P: P.test_coupling_schedule_scales_the_couplings_exactly()
+adj_cpl = lambda P: P.test_adjoint_with_coupling_schedule_matches_finite_differences()
 
 
 def strip(P):
@@ -89,11 +91,15 @@ MUTANTS = {
     "sensitivity_drops_drift": ("hb[i] += tb[i] * dt;", "hb[i] += tb[i] * 0.0;", [sens]),
     "sensitivity_damping_reverse": ("wb[i] = hb[i] * (1.0 - a);", "wb[i] = hb[i] * (1.0 + a);", [sens]),
     "sensitivity_second_kick_force": ("Fb[i] += wb[i] * b * 0.5 * dt;", "Fb[i] = wb[i] * b * 0.5 * dt;", [sens]),
-    "field_force_of_the_wrong_time_point": ("params_at(prm, k + 1, nf, fks, fss, prm_next);",
-                                            "params_at(prm, k, nf, fks, fss, prm_next);", [fwd_field]),
+    "field_force_of_the_wrong_time_point": ("params_at(prm, k + 1, sc, prm_next);",
+                                            "params_at(prm, k, sc, prm_next);", [fwd_field]),
     "field_adjoint_drops_the_profile": ("gh += gp[2] * s1;", "gh += gp[2];", [adj_field]),
     "field_interpolation_reversed": ("return ss[i] + (ss[i + 1] - ss[i]) * f;", "return ss[i + 1] + (ss[i] - ss[i + 1]) * f;",
                                      [lambda P: P.test_field_schedule_is_linear_interpolation()]),
+    "coupling_profiles_swapped": ("out[P_JPERP] = prm[P_JPERP] * xyo_field_scale(k, sc->nc, sc->cks, sc->cperp);",
+                                  "out[P_JPERP] = prm[P_JPERP] * xyo_field_scale(k, sc->nc, sc->cks, sc->cpar);",
+                                  [cpl_exact]),
+    "coupling_adjoint_drops_the_profile": ("gJx += gp[0] * a1;", "gJx += gp[0];", [adj_cpl]),
     "strip_noise_of_the_local_row": ("int64_t g0 = (((int64_t)y0 + i) % Ly) * Lx;", "int64_t g0 = (int64_t)i * Lx;",
                                      [strip]),
     "strip_force_drops_the_row_above": ("double fy = sin(q * (t - below)) + sin(q * (t - above));",

@@ -492,7 +492,7 @@ def test_ccl_zero_angle_counts_as_up():
 # ----------------------------------------------------------------- adjoint
 
 
-def _fd_grad(Lx, Ly, prm, knots, n, th0, om0, wE, wM, rel=1e-5, field=None):
+def _fd_grad(Lx, Ly, prm, knots, n, th0, om0, wE, wM, rel=1e-5, field=None, couplings=None):
     names = ("J_par", "J_perp", "h", "eta")
     g = []
     for nm in names:
@@ -502,7 +502,8 @@ def _fd_grad(Lx, Ly, prm, knots, n, th0, om0, wE, wM, rel=1e-5, field=None):
         for s in (+1, -1):
             p2 = dict(prm)
             p2[nm] = base + s * eps
-            obj, _, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, p2, knots, 0, n, th0, om0, wE, wM, field=field)
+            obj, _, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, p2, knots, 0, n, th0, om0, wE, wM, field=field,
+                                                  couplings=couplings)
             vals.append(obj)
         g.append((vals[0] - vals[1]) / (2 * eps))
     return np.array(g)
@@ -778,3 +779,65 @@ def test_adjoint_with_field_schedule_matches_finite_differences():
     # the schedule matters: without it d/dh differs
     _, g1, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, 150, th0, om0, 0.6, 0.4)
     assert abs(g1[2] - grad[2]) > 1e-3 * abs(grad[2])
+
+
+# ---------------------------------------------------------------- anisotropic quench: coupling profiles
+# (Sec. VII, Sec. VIII: the two directional couplings quenched at different
+# rates, J_par(k) = J_par a(k), J_perp(k) = J_perp b(k))
+
+def test_coupling_schedule_scales_the_couplings_exactly():
+    """Profiles of ones change nothing; constant scales a = 2, b = 1/2 are the
+    run with J_par doubled and J_perp halved (both enter the force and the
+    energy exactly), and swapping the two profiles is a different run."""
+    Lx, Ly, n = 8, 6, 60
+    prm = dict(inputs.PAPER)
+    knots = ([0], [inputs.T_C])
+    th0 = inputs.angles(1, Lx, Ly, 4)[0].astype(np.float64)
+    runs = []
+    for p_, cpl in ((prm, None), (prm, ([0, 30], [1.0, 1.0], [1.0, 1.0])),
+                    (prm, ([0], [2.0], [0.5])), (dict(prm, J_par=2 * prm["J_par"], J_perp=0.5 * prm["J_perp"]), None),
+                    (prm, ([0], [0.5], [2.0]))):
+        th, om = th0.copy(), np.zeros(Lx * Ly)
+        rec = oracle.run_lattice(Lx, Ly, 0, 0, 7, p_, knots, 0, n, th, om, record_every=5, couplings=cpl)
+        runs.append((th, om, rec))
+    for a, b in ((0, 1), (2, 3)):
+        assert all(np.array_equal(x, y) for x, y in zip(runs[a], runs[b]))
+    assert not np.array_equal(runs[2][0], runs[4][0])
+
+
+def test_coupling_ramp_gives_every_time_point_its_couplings():
+    """The adjoint's forward loop and the stepper give every time point its
+    own couplings: the same trajectory and objective under a ramp of both."""
+    Lx, Ly = 8, 8
+    th0 = inputs.angles(1, Lx, Ly, 1)[0].astype(np.float64)
+    om0 = np.zeros(Lx * Ly)
+    knots = ([0], [inputs.T_C])
+    cpl = ([5, 30], [1.0, 0.3], [0.2, 3.0])
+    obj, _, th1, om1 = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th0, om0, 0.6, 0.4, couplings=cpl)
+    th, om = th0.copy(), om0.copy()
+    rec = oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 41, th, om, 1, couplings=cpl)
+    th, om = th0.copy(), om0.copy()
+    oracle.run_lattice(Lx, Ly, 0, 0, 3, {}, knots, 0, 40, th, om, couplings=cpl)
+    assert np.array_equal(th, th1) and np.array_equal(om, om1)
+    expect = (0.6 * rec[1:, 1] + 0.4 * np.abs(rec[1:, 0])).sum()
+    assert obj == pytest.approx(expect, rel=1e-13)
+
+
+def test_adjoint_with_coupling_schedule_matches_finite_differences():
+    """p = 2 (smooth), both couplings ramped at different rates together with
+    a temperature ramp and a field ramp: d/dJ_par and d/dJ_perp at the fixed
+    profiles, and the other two components, against central differences."""
+    Lx, Ly = 6, 4
+    prm = dict(inputs.PAPER, J_par=2.0, J_perp=0.5, h=1.2, p=2.0, eta=0.8)
+    th0 = inputs.angles(1, Lx, Ly, 28)[0].astype(np.float64)
+    om0 = 0.3 * inputs.velocities(1, Lx, Ly, 28)[0].astype(np.float64)
+    knots = ([0, 150], [1.0, 0.5])
+    field = ([20, 120], [0.3, 1.7])
+    cpl = ([10, 90, 140], [1.5, 0.6, 1.0], [0.4, 2.2, 1.3])
+    obj, grad, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, 150, th0, om0, 0.6, 0.4, field=field,
+                                             couplings=cpl)
+    fd = _fd_grad(Lx, Ly, prm, knots, 150, th0, om0, 0.6, 0.4, field=field, couplings=cpl)
+    assert np.allclose(grad, fd, rtol=1e-6, atol=1e-7 * max(1.0, np.abs(fd).max())), (grad, fd)
+    # the profiles matter: without them d/dJ differ
+    _, g1, _, _ = oracle.adjoint_lattice(Lx, Ly, 0, 0, 3, prm, knots, 0, 150, th0, om0, 0.6, 0.4, field=field)
+    assert abs(g1[0] - grad[0]) > 1e-3 * abs(grad[0]) and abs(g1[1] - grad[1]) > 1e-3 * abs(grad[1])
