@@ -214,7 +214,7 @@ int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w
 /* Field schedule of configuration cfg: the orthogonal quench, in which the
  * symmetry-breaking field changes in time beside (or instead of) the
  * temperature, crossing the phase boundary T_c(h) of App. D (Fig. 10) at an
- * angle (Sec. VII names such quenches as an extension).  The field of step k
+ * angle (Sec. V proposes such quenches; Sec. IV.C the quench angle).  The field of step k
  * is h_k = h s(k), with h from xy_set_params and s piecewise linear through
  * the knots (step_knots[i], scale_knots[i]) (steps strictly increasing,
  * scales finite) and constant outside them, evaluated in FP32 like T(k).
@@ -225,6 +225,22 @@ int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w
  * Carried by xy_save/xy_load.  XY_EINVAL for bad knots. */
 int xy_set_field_schedule(xy_lattice* lat, int cfg, const int64_t* step_knots, const double* scale_knots,
                           int n_knots);
+
+/* Coupling profiles of configuration cfg: the anisotropic quench, in which
+ * the two directional couplings move at different rates (Sec. V names
+ * anisotropic quenches as an extension; in the coupling space of App. D the
+ * path then leaves the temperature ray).  The couplings of step k are
+ * J_par(k) = J_par a(k) and J_perp(k) = J_perp b(k), with J_par, J_perp from
+ * xy_set_params and a, b piecewise linear through the knots
+ * (step_knots[i], par_scales[i], perp_scales[i]) (steps strictly increasing,
+ * scales finite) and constant outside them, evaluated in FP32 like T(k).
+ * They replace J_par, J_perp in the force of time point k and in E_k of
+ * Eq. (XY-Hamilton-Kinetic).  The adjoint's d/dJ_par and d/dJ_perp are the
+ * derivatives at fixed profiles.  n_knots = 0 removes the schedule (the same
+ * bits as a configuration that never had one).  Carried by xy_save/xy_load.
+ * XY_EINVAL for bad knots. */
+int xy_set_coupling_schedule(xy_lattice* lat, int cfg, const int64_t* step_knots, const double* par_scales,
+                             const double* perp_scales, int n_knots);
 
 /* Temporal blocking of the batched stepper (the paper steps one time step
  * per pass; this is a property of the library).  Lattices with
@@ -271,7 +287,7 @@ int xy_set_temporal_blocking(xy_lattice* lat, int kt);
 #define XY_ADJOINT_BACKWARD 2
 int xy_set_adjoint_mode(xy_lattice* lat, int mode);
 
-/* Structure factors of the rotor lattice (Sec. VI, Eq. FT-Corr-delta and
+/* Structure factors of the rotor lattice (App. C, Eq. FT-Corr-delta and
  * Eq. S-as-lattice-FT), the input of the Lorentzian correlation-length fit of
  * Eq. Lorentzian-Peak.  With rotors s = (cos(r theta), sin(r theta)) of the
  * current state (the paper's rotors are r = 1), for lattices
@@ -306,7 +322,7 @@ int xy_structure_factor(xy_lattice* lat, int b_first, int b_count, int K, double
 int xy_autocorr_time(const double* rec, int64_t n_series, int64_t R, int component, int transform, int64_t skip,
                      int64_t n, double c_window, double* out, void* cuda_stream);
 
-/* Nonlinear quench (Sec. VII, the extension eps(t) = t^gamma / tau_Q^gamma of
+/* Nonlinear quench (Sec. V, the extension eps(t) = t^gamma / tau_Q^gamma of
  * the linear quench of Eq. Linear-Quench) as the temperature schedule of
  * configuration cfg, replacing any xy_set_schedule():
  *   T(k) = T_c (1 + eps(k)),  eps(k) = -sign(t) |t / tau_Q|^gamma,  t = k - k_cross,

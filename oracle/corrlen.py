@@ -1,4 +1,4 @@
-"""FP64 oracle of the correlation-length pipeline (arXiv 2409.06412, Sec. VI,
+"""FP64 oracle of the correlation-length pipeline (arXiv 2409.06412, App. C,
 "Correlation Length Extraction").
 
 TEST INFRASTRUCTURE, like the rest of ``oracle/``: only ``tests/``,

@@ -18,7 +18,7 @@
  *   order parameter      Sec. IV.A, Eq. (lattice-average), s_i = sin(q theta_i)
  *   benchmark 1 (MSD)    App. A.2, Eq. (MSD-HO)
  *   quench schedule      Sec. II.B, Eq. (Linear-Quench)
- *   field schedule       h_k = h s(k), the orthogonal quench named in Sec. VII
+ *   field schedule       h_k = h s(k), the orthogonal quench named in Sec. V
  *
  * Readings where the paper is silent (noise keying, sharing of one Gaussian per
  * time point between the two half-kicks, periodic boundaries, domain labels,
@@ -133,7 +133,7 @@ double xyo_wrap(double t)
     return r;
 }
 
-/* Nonlinear quench of order gamma (Sec. VII, the proposed extension
+/* Nonlinear quench of order gamma (Sec. V, the proposed extension
  * eps(t) = t^gamma / tau_Q^gamma): T(k) = T_c (1 + eps(k)) with
  * eps(k) = -sign(t) |t / tau_Q|^gamma, t = k - k_cross, held within
  * [eps_f, eps_i] (eps_i above, eps_f below the critical point).  gamma = 1 is
@@ -166,9 +166,9 @@ double xyo_temperature(int64_t k, int n_knots, const int64_t* ks, const double* 
     return Ts[n_knots - 1];
 }
 
-/* A parameter profile: the field schedule of the orthogonal quench (Sec. VII
- * names quenches that cross the phase boundary T_c(h) of App. D at an
- * angle), h_k = h s(k), and the coupling profiles of the anisotropic quench.
+/* A parameter profile: the field schedule of the orthogonal quench (Sec. V
+ * proposes quenches orthogonal to the phase boundary T_c(h) of App. D; Sec.
+ * IV.C the quench angle), h_k = h s(k), and the coupling profiles of the anisotropic quench.
  * Piecewise linear through (ks[i], ss[i]) and constant outside them; n = 0
  * means 1. */
 double xyo_field_scale(int64_t k, int n, const int64_t* ks, const double* ss)

@@ -47,6 +47,7 @@ SIGNATURES = {
     "xy_label_domains": (_i32, [_vp, _i32, _i32, _vp, _vp, _i64, _vp]),
     "xy_adjoint_step_n": (_i32, [_vp, _i64, _i32, _d, _d, _vp, _vp]),
     "xy_set_field_schedule": (_i32, [_vp, _i32, _vp, _vp, _i32]),
+    "xy_set_coupling_schedule": (_i32, [_vp, _i32, _vp, _vp, _vp, _i32]),
     "xy_set_temporal_blocking": (_i32, [_vp, _i32]),
     "xy_set_adjoint_mode": (_i32, [_vp, _i32]),
     "xy_label_domains_static": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _i64, _vp, _vp]),

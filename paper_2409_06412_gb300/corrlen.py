@@ -1,4 +1,4 @@
-"""Correlation length from the structure factor (arXiv 2409.06412, Sec. VI).
+"""Correlation length from the structure factor (arXiv 2409.06412, App. C).
 
 Near k = 0 the structure factor of exponentially decaying correlations is a
 Lorentzian (Eq. Lorentzian-Peak), S(k) = a / (1 + (2 pi xi k / N)^2) with k the

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
     __syncthreads();
     const StepConst K = step_const_k(cf, k, s_c);
     const float hk = field_h(cf, k);
+    const float2 Jk = couplings_at(cf, k), abk = coupling_scales(cf, k);
     const int64_t nq_lat = cf.N / 4;
     const int bpl = (int)((nq_lat + blockDim.x - 1) / blockDim.x);
     const int rep = blockIdx.x / bpl;
@@ -146,8 +147,8 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
                 aJy = fmaf(-wE * invN, by, aJy);
                 ah = fmaf(wE * invN, cp, ah);
                 float e = __fmul_rn(0.5f, __fmul_rn(om, om));
-                e = fmaf(-cf.Jx, bx, e);
-                e = fmaf(-cf.Jy, by, e);
+                e = fmaf(-Jk.x, bx, e);
+                e = fmaf(-Jk.y, by, e);
                 e = fmaf(hk, cp, e);
                 eacc = fmaf(wE * invN, e, eacc);
             }
@@ -173,8 +174,10 @@ __global__ void __launch_bounds__(256) adjoint_phase_a_kernel(const DevCfg* cfgs
     }
     // block sums in FP64, fixed order; per-block accumulators across steps
     const double ceta = cf.eta_d > 0.0 ? (double)K.c / (2.0 * cf.eta_d) : 0.0;  // d c_k / d eta = c_k / (2 eta)
-    // with a field schedule the field of step k is h s(k): d/dh of its terms carries s(k)
-    double vals[kGacc] = {aJx, aJy, (double)ah * field_scale(cf, k), abar, bbar, (double)cbar * ceta, eacc};
+    // with schedules the field of step k is h s(k) and the couplings J a(k),
+    // J b(k): d/dh and d/dJ of their terms carry s(k), a(k), b(k)
+    double vals[kGacc] = {(double)aJx * abk.x, (double)aJy * abk.y, (double)ah * field_scale(cf, k), abar, bbar,
+                          (double)cbar * ceta, eacc};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < kGacc; ++q) {
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_b_kernel(const DevCfg* cfgs
     const int Lx = cf.Lx, Ly = cf.Ly;
     const int y = (int)(4 * quad / Lx), x = (int)(4 * quad - (int64_t)y * Lx);
     const float q = cf.q, q2 = __fmul_rn(cf.q, cf.q);
+    const float2 Jk = couplings_at(cf, A.k);
     Nbr4 t, f;
     load_nbr(A.theta + lat_off, Lx, Ly, x, y, t);
     load_nbr(A.Fb + lat_off, Lx, Ly, x, y, f);
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(256) adjoint_phase_b_kernel(const DevCfg* cfgs
         const float kU = fmaf(co[i], cu[i], s[i] * su[i]), kD = fmaf(co[i], cd[i], s[i] * sd[i]);
         const float hx = fmaf(kL, fL - fj, kR * (fR - fj));
         const float hy = fmaf(kU, f.tu[i] - fj, kD * (f.td[i] - fj));
-        float acc = q2 * fmaf(cf.Jx, hx, cf.Jy * hy);
+        float acc = q2 * fmaf(Jk.x, hx, Jk.y * hy);
         acc = fmaf(field_hp(cf, A.k) * cf.p, __cosf(__fmul_rn(cf.p, t.t[i])) * fj, acc);
         out[i] = __fadd_rn(f4get(tb4, i), acc);
     }
@@ -336,7 +340,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     }
     // configuration constants in registers (the cp.async statements clobber
     // memory, which would otherwise reload them from the descriptor every row)
-    const float Jx = cf.Jx, Jy = cf.Jy, hF = field_h(cf, R.k);
+    const float2 Jk = couplings_at(cf, R.k), abk = coupling_scales(cf, R.k);
+    const float Jx = Jk.x, Jy = Jk.y, hF = field_h(cf, R.k);
     const float q2Jx = q2 * Jx, q2Jy = q2 * Jy;
     const bool stag = cf.stag != 0;
     const float wEn = wE * invN, wMs = wM * invN * sgnM * K.q;
@@ -536,8 +541,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_band_kernel(const DevCfg* cfgs
     // per-block accumulators: FP32 warp butterflies (a warp covers a few
     // thousand sites), the warps and the steps combined in FP64 in a fixed order
     const float vals[kGacc] = {
-        fmaf(-K.q, aJx, -wEn * sbx),                                        // d/d J_par
-        fmaf(-K.q, aJy, -wEn * sby),                                        // d/d J_perp
+        fmaf(-K.q, aJx, -wEn * sbx) * abk.x,                                // d/d J_par (J_par(k) = J_par a(k))
+        fmaf(-K.q, aJy, -wEn * sby) * abk.y,                                // d/d J_perp (J_perp b(k))
         fmaf(K.p, ah, wEn * scp) * field_scale(cf, R.k),                    // d/d h (h_k = h s(k))
         abar, bbar, cbar,
         wEn * fmaf(0.5f, sw2, fmaf(-Jx, sbx, fmaf(-Jy, sby, hF * scp))),  // w_E E / N

@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     }
     // configuration constants in registers (the cp.async statements clobber
     // memory, which would otherwise reload them from the descriptor every row)
-    const float Jx = cf.Jx, Jy = cf.Jy, hF = field_h(cf, R.k);
+    const float2 Jk = couplings_at(cf, R.k), abk = coupling_scales(cf, R.k);
+    const float Jx = Jk.x, Jy = Jk.y, hF = field_h(cf, R.k);
     const float q2Jx = q2 * Jx, q2Jy = q2 * Jy;
     const bool stag = cf.stag != 0;
     const float wEn = wE * invN;
@@ -369,8 +370,8 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     // per-block accumulators: FP32 warp butterflies, the warps and the steps
     // combined in FP64 in a fixed order; the partial of M_k goes to the ring
     const float vals[kGacc + 1] = {
-        fmaf(-K.q, aJx, -wEn * sbx),                                        // d/d J_par
-        fmaf(-K.q, aJy, -wEn * sby),                                        // d/d J_perp
+        fmaf(-K.q, aJx, -wEn * sbx) * abk.x,                                // d/d J_par (J_par(k) = J_par a(k))
+        fmaf(-K.q, aJy, -wEn * sby) * abk.y,                                // d/d J_perp (J_perp b(k))
         fmaf(K.p, ah, wEn * scp) * field_scale(cf, R.k),                    // d/d h (h_k = h s(k))
         abar, bbar, cbar,
         wEn * fmaf(0.5f, sw2, fmaf(-Jx, sbx, fmaf(-Jy, sby, hF * scp))),  // w_E E / N

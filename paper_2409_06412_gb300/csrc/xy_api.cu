@@ -54,6 +54,10 @@ struct CfgHost {
     int f_n_knots = 0;  // field schedule s(k): h_k = h s(k)
     int64_t f_knot_step[XY_MAX_KNOTS] = {};
     double f_knot_s[XY_MAX_KNOTS] = {};
+    int c_n_knots = 0;  // coupling profiles a(k), b(k): J_par a(k), J_perp b(k)
+    int64_t c_knot_step[XY_MAX_KNOTS] = {};
+    double c_knot_a[XY_MAX_KNOTS] = {};
+    double c_knot_b[XY_MAX_KNOTS] = {};
     int kind = 2;   // 0 resident, 1 strip, 2 plain (inside the batched path)
     int H = 0;      // strip rows per row group
 };
@@ -305,12 +309,28 @@ void fill_params(DevCfg& d, const xy_params& p)
     d.e_ref = (float)(-(std::fabs(p.J_par) + std::fabs(p.J_perp) + std::fabs(p.h)));
 }
 
-// FP32 field schedule of the device record and the energy reference: the
-// potential part of a site's energy is >= -(|J_par| + |J_perp| + |h| max|s|).
+// Largest |scale| of a profile (1 without one).
+double profile_max(int n, const double* v)
+{
+    double m = n == 0 ? 1.0 : 0.0;
+    for (int i = 0; i < n; ++i) m = std::max(m, std::fabs(v[i]));
+    return m;
+}
+
+// The energy reference: the potential part of a site's energy is
+// >= -(|J_par| max|a| + |J_perp| max|b| + |h| max|s|) at every step.
+void fill_e_ref(DevCfg& d, const CfgHost& h)
+{
+    if (!h.has_prm) return;
+    d.e_ref = (float)(-(std::fabs(h.prm.J_par) * profile_max(h.c_n_knots, h.c_knot_a) +
+                        std::fabs(h.prm.J_perp) * profile_max(h.c_n_knots, h.c_knot_b) +
+                        std::fabs(h.prm.h) * profile_max(h.f_n_knots, h.f_knot_s)));
+}
+
+// FP32 field schedule of the device record, and the energy reference.
 void fill_field_f32(DevCfg& d, const CfgHost& h)
 {
     d.f_n_knots = h.f_n_knots;
-    double smax = h.f_n_knots == 0 ? 1.0 : 0.0;
     for (int i = 0; i < XY_MAX_KNOTS; ++i) {
         const bool on = i < h.f_n_knots;
         d.f_knot_step[i] = on ? h.f_knot_step[i] : 0;
@@ -318,10 +338,25 @@ void fill_field_f32(DevCfg& d, const CfgHost& h)
         d.f_slope[i] = (i + 1 < h.f_n_knots)
                            ? (float)((h.f_knot_s[i + 1] - h.f_knot_s[i]) / (double)(h.f_knot_step[i + 1] - h.f_knot_step[i]))
                            : 0.f;
-        if (on) smax = std::max(smax, std::fabs(h.f_knot_s[i]));
     }
-    if (h.has_prm)
-        d.e_ref = (float)(-(std::fabs(h.prm.J_par) + std::fabs(h.prm.J_perp) + std::fabs(h.prm.h) * smax));
+    fill_e_ref(d, h);
+}
+
+// FP32 coupling profiles of the device record, and the energy reference.
+void fill_coupling_f32(DevCfg& d, const CfgHost& h)
+{
+    d.c_n_knots = h.c_n_knots;
+    for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+        const bool on = i < h.c_n_knots;
+        const bool seg = i + 1 < h.c_n_knots;
+        const double dk = seg ? (double)(h.c_knot_step[i + 1] - h.c_knot_step[i]) : 1.0;
+        d.c_knot_step[i] = on ? h.c_knot_step[i] : 0;
+        d.c_knot_a[i] = on ? (float)h.c_knot_a[i] : 0.f;
+        d.c_knot_b[i] = on ? (float)h.c_knot_b[i] : 0.f;
+        d.c_slope_a[i] = seg ? (float)((h.c_knot_a[i + 1] - h.c_knot_a[i]) / dk) : 0.f;
+        d.c_slope_b[i] = seg ? (float)((h.c_knot_b[i + 1] - h.c_knot_b[i]) / dk) : 0.f;
+    }
+    fill_e_ref(d, h);
 }
 
 void fill_schedule_f32(DevCfg& d)
@@ -1516,7 +1551,7 @@ int xy_set_params(xy_lattice* L, int c, const xy_params* p)
     L->cfg[c].prm = *p;
     L->cfg[c].has_prm = true;
     fill_params(L->h_dev[c], *p);
-    fill_field_f32(L->h_dev[c], L->cfg[c]);
+    fill_e_ref(L->h_dev[c], L->cfg[c]);
     return XY_OK;
 }
 
@@ -1537,6 +1572,28 @@ int xy_set_field_schedule(xy_lattice* L, int c, const int64_t* ks, const double*
         h.f_knot_s[i] = i < n_knots ? ss[i] : 0.0;
     }
     fill_field_f32(L->h_dev[c], h);
+    return XY_OK;
+}
+
+int xy_set_coupling_schedule(xy_lattice* L, int c, const int64_t* ks, const double* as, const double* bs,
+                             int n_knots)
+{
+    if (!L) return fail(XY_EINVAL, "NULL lattice");
+    if (c < 0 || c >= L->n_cfg) return fail(XY_EINVAL, "configuration %d out of range", c);
+    if (n_knots < 0 || n_knots > XY_MAX_KNOTS) return fail(XY_EINVAL, "0..%d knots", XY_MAX_KNOTS);
+    if (n_knots > 0 && (!ks || !as || !bs)) return fail(XY_EINVAL, "NULL knots");
+    for (int i = 0; i < n_knots; ++i) {
+        if (!std::isfinite(as[i]) || !std::isfinite(bs[i])) return fail(XY_EINVAL, "coupling scales must be finite");
+        if (i > 0 && ks[i] <= ks[i - 1]) return fail(XY_EINVAL, "knot steps must increase strictly");
+    }
+    CfgHost& h = L->cfg[c];
+    h.c_n_knots = n_knots;
+    for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+        h.c_knot_step[i] = i < n_knots ? ks[i] : 0;
+        h.c_knot_a[i] = i < n_knots ? as[i] : 0.0;
+        h.c_knot_b[i] = i < n_knots ? bs[i] : 0.0;
+    }
+    fill_coupling_f32(L->h_dev[c], h);
     return XY_OK;
 }
 
@@ -2429,6 +2486,10 @@ struct SnapCfg {
     int64_t f_n_knots;
     int64_t f_knot_step[XY_MAX_KNOTS];
     double f_knot_s[XY_MAX_KNOTS];
+    int64_t c_n_knots;
+    int64_t c_knot_step[XY_MAX_KNOTS];
+    double c_knot_a[XY_MAX_KNOTS];
+    double c_knot_b[XY_MAX_KNOTS];
 };
 }  // namespace
 
@@ -2448,7 +2509,7 @@ int xy_save(xy_lattice* L, void* buf, size_t* size)
     char* p = (char*)buf;
     SnapHeader hd{};
     std::memcpy(hd.magic, "XYLATT1", 8);
-    hd.version = 3;
+    hd.version = 4;
     hd.n_cfg = L->n_cfg;
     hd.total = L->total_sites;
     hd.B = L->B;
@@ -2474,6 +2535,12 @@ int xy_save(xy_lattice* L, void* buf, size_t* size)
             s.f_knot_s[i] = h.f_knot_s[i];
         }
         s.f_n_knots = h.f_n_knots;
+        for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+            s.c_knot_step[i] = h.c_knot_step[i];
+            s.c_knot_a[i] = h.c_knot_a[i];
+            s.c_knot_b[i] = h.c_knot_b[i];
+        }
+        s.c_n_knots = h.c_n_knots;
         std::memcpy(p, &s, sizeof s);
         p += sizeof s;
     }
@@ -2497,7 +2564,7 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
     SnapHeader hd;
     std::memcpy(&hd, p, sizeof hd);
     p += sizeof hd;
-    if (std::memcmp(hd.magic, "XYLATT1", 8) != 0 || hd.version != 3) return fail(XY_EINVAL, "not a snapshot");
+    if (std::memcmp(hd.magic, "XYLATT1", 8) != 0 || hd.version != 4) return fail(XY_EINVAL, "not a snapshot");
     if (hd.n_cfg != L->n_cfg || hd.total != L->total_sites || hd.B != L->B)
         return fail(XY_EINVAL, "snapshot shape does not match this lattice object");
     std::vector<SnapCfg> sc(L->n_cfg);
@@ -2538,7 +2605,14 @@ int xy_load(xy_lattice* L, const void* buf, size_t size)
             h.f_knot_step[i] = s.f_knot_step[i];
             h.f_knot_s[i] = s.f_knot_s[i];
         }
+        h.c_n_knots = (int)s.c_n_knots;
+        for (int i = 0; i < XY_MAX_KNOTS; ++i) {
+            h.c_knot_step[i] = s.c_knot_step[i];
+            h.c_knot_a[i] = s.c_knot_a[i];
+            h.c_knot_b[i] = s.c_knot_b[i];
+        }
         fill_field_f32(d, h);
+        fill_coupling_f32(d, h);
     }
     CK(cudaMemcpyAsync(L->d_moments, p, sizeof(double) * 6 * L->n_cfg, cudaMemcpyHostToDevice, L->stream));
     p += sizeof(double) * 6 * L->n_cfg;

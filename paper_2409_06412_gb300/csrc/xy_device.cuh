@@ -142,7 +142,7 @@ struct StepConst {
 // quench of order gamma.
 __device__ __forceinline__ float temperature_at(const DevCfg& cf, int64_t k)
 {
-    if (cf.sched_kind == 1) {  // nonlinear quench (Sec. VII), FP32
+    if (cf.sched_kind == 1) {  // nonlinear quench (Sec. V), FP32
         const float t = (float)(k - cf.pw_kc);
         float eps = powf(__fmul_rn(fabsf(t), cf.pw_inv_tq), cf.pw_gamma);
         eps = t >= 0.f ? -eps : eps;
@@ -198,11 +198,42 @@ __device__ __forceinline__ StepConst step_const(const DevCfg& cf, float c)
     return s;
 }
 
-// The constants of step k: noise amplitude c_k and the field's h_k p.
+// Coupling profiles of the anisotropic quench: J_par(k) = J_par a(k),
+// J_perp(k) = J_perp b(k), piecewise linear through one knot grid and
+// constant outside it, in FP32 like T(k); (1, 1) without a schedule.
+__device__ __forceinline__ float2 coupling_scales(const DevCfg& cf, int64_t k)
+{
+    const int n = cf.c_n_knots;
+    if (n <= 1 || k <= cf.c_knot_step[0])
+        return n == 0 ? make_float2(1.f, 1.f) : make_float2(cf.c_knot_a[0], cf.c_knot_b[0]);
+    for (int i = 0; i + 1 < n; ++i)
+        if (k <= cf.c_knot_step[i + 1]) {
+            const float dk = (float)(k - cf.c_knot_step[i]);
+            return make_float2(fmaf(cf.c_slope_a[i], dk, cf.c_knot_a[i]), fmaf(cf.c_slope_b[i], dk, cf.c_knot_b[i]));
+        }
+    return make_float2(cf.c_knot_a[n - 1], cf.c_knot_b[n - 1]);
+}
+
+// J_par(k), J_perp(k): the configuration's own without a schedule (the same
+// bits as before schedules existed), else scaled by the profiles
+__device__ __forceinline__ float2 couplings_at(const DevCfg& cf, int64_t k)
+{
+    if (cf.c_n_knots == 0) return make_float2(cf.Jx, cf.Jy);
+    const float2 ab = coupling_scales(cf, k);
+    return make_float2(__fmul_rn(cf.Jx, ab.x), __fmul_rn(cf.Jy, ab.y));
+}
+
+// The constants of step k: noise amplitude c_k, the field's h_k p, and the
+// couplings' -q J_par(k), -q J_perp(k).
 __device__ __forceinline__ StepConst step_const_k(const DevCfg& cf, int64_t k, float c)
 {
     StepConst s = step_const(cf, c);
     s.hp = field_hp(cf, k);
+    if (cf.c_n_knots != 0) {
+        const float2 ab = coupling_scales(cf, k);
+        s.nqJx = __fmul_rn(cf.nqJx, ab.x);
+        s.nqJy = __fmul_rn(cf.nqJy, ab.y);
+    }
     return s;
 }
 
@@ -240,7 +271,7 @@ __device__ __forceinline__ SiteOut site_update(const StepConst& K, float theta, 
 }
 
 // Energy of one site with its forward bonds (x+1, y+1), per Eq. (XY-Hamilton-Kinetic),
-// relative to the reference e_ref = -(|J_par| + |J_perp| + |h|) <= the potential part:
+// relative to the reference e_ref <= the potential part at every step:
 //   omega^2 / 2 - J_par cos q(t - t_{x+1}) - J_perp cos q(t - t_{y+1}) + h cos(p t) - e_ref
 // with cos q(a - b) = c_a c_b + s_a s_b, bx, by those bond cosines.  The
 // potential terms are added to the small h cos(p t) - e_ref first, so every
@@ -254,13 +285,13 @@ __device__ __forceinline__ float site_energy_rel(float omega, float bx, float by
     return fmaf(__fmul_rn(0.5f, omega), omega, e);
 }
 
-// hk: the field at the recorded step (field_h)
-__device__ __forceinline__ float site_energy(const DevCfg& cf, float hk, float omega, float s, float c, float sR,
-                                             float cR, float sD, float cD, float cosp)
+// Jk: the couplings (couplings_at) and hk the field (field_h) of the recorded step
+__device__ __forceinline__ float site_energy(const DevCfg& cf, float2 Jk, float hk, float omega, float s, float c,
+                                             float sR, float cR, float sD, float cD, float cosp)
 {
     const float bx = fmaf(c, cR, __fmul_rn(s, sR));
     const float by = fmaf(c, cD, __fmul_rn(s, sD));
-    return site_energy_rel(omega, bx, by, cosp, cf.Jx, cf.Jy, hk, cf.e_ref);
+    return site_energy_rel(omega, bx, by, cosp, Jk.x, Jk.y, hk, cf.e_ref);
 }
 
 // Asynchronous global -> shared copies (cp.async), issued by one lane for its

@@ -42,6 +42,16 @@ struct DevCfg {
     int64_t f_knot_step[XY_MAX_KNOTS];
     float f_knot_s[XY_MAX_KNOTS];
     float f_slope[XY_MAX_KNOTS];
+    // coupling profiles (the anisotropic quench): J_par(k) = J_par a(k),
+    // J_perp(k) = J_perp b(k), piecewise linear through one knot grid, in FP32
+    // from per-segment slopes; c_n_knots = 0: a = b = 1 (no schedule)
+    int32_t c_n_knots;
+    float c_pad;
+    int64_t c_knot_step[XY_MAX_KNOTS];
+    float c_knot_a[XY_MAX_KNOTS];
+    float c_knot_b[XY_MAX_KNOTS];
+    float c_slope_a[XY_MAX_KNOTS];
+    float c_slope_b[XY_MAX_KNOTS];
     // per call
     int64_t k_start;    // step at the start of the current call
     int64_t n_call;     // steps this configuration takes in the current call

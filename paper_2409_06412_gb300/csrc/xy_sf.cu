@@ -1,5 +1,5 @@
 // xy_sf.cu -- structure factors S_par(k), S_perp(k) of the rotor lattice for
-// the correlation-length extraction of arXiv 2409.06412, Sec. VI.
+// the correlation-length extraction of arXiv 2409.06412, App. C.
 //
 // With rotors s = (cos(r theta), sin(r theta)) (the paper's definition is
 // r = 1) on an N_par x N_perp lattice (x along the dimer rows, y across),

@@ -314,7 +314,8 @@ __global__ void __launch_bounds__(256) plain_step_kernel(const DevCfg* cfgs, int
                 const float sigma = (cf.stag && ((x + s + y) & 1)) ? -1.f : 1.f;
                 pm = fmaf(sigma, f.s[s], pm);
                 if (!ca.m_only)
-                    pe = __fadd_rn(pe, site_energy(cf, field_h(cf, k), so.omega, f.s[s], f.c[s], f.sR[s], f.cR[s],
+                    pe = __fadd_rn(pe, site_energy(cf, couplings_at(cf, k), field_h(cf, k), so.omega, f.s[s], f.c[s],
+                                                   f.sR[s], f.cR[s],
                                                    f.sD[s], f.cD[s], cosp_of(K.p, f.th[s])));
             }
         }
@@ -558,8 +559,9 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     X.pm = 0.f;
     X.pe = 0.f;
     if (REC > 0 && X.rec) {  // block-uniform
-        X.Jx = cf.Jx;
-        X.Jy = cf.Jy;
+        const float2 Jk = couplings_at(cf, X.k);
+        X.Jx = Jk.x;
+        X.Jy = Jk.y;
         X.hF = field_h(cf, X.k);
         X.eref = cf.e_ref;
         X.stag = cf.stag != 0;
@@ -712,7 +714,7 @@ __global__ void __launch_bounds__(256, MINB) band2_step_kernel(const DevCfg* cfg
     const int64_t k = cf.k_start + j + ca.k_shift;
     const StepConst K1 = step_const_k(cf, k, noise_amp(cf, k));
     const float c2 = noise_amp(cf, k + 1);
-    const float hp2 = field_hp(cf, k + 1);
+    const StepConst K2c = step_const_k(cf, k + 1, c2);  // the field and couplings of step k + 1
     const int Lx = cf.Lx, Ly = cf.Ly;
     const int64_t lat_off = cf.offset + (int64_t)task.rep * cf.N;
     // a batch of steps holds an even number of pairs: pair p = j_local / 2 of it
@@ -787,9 +789,7 @@ __global__ void __launch_bounds__(256, MINB) band2_step_kernel(const DevCfg* cfg
             float sL, cL, sR, cR;
             x_nbrs(C1.s, C1.c, prev, 1, sL, cL, sR, cR);
             const uint32_t quad = (uint32_t)(((int64_t)b * Lx + x) >> 2);
-            StepConst K2 = K1;
-            K2.c = c2;
-            K2.hp = hp2;
+            const StepConst K2 = K2c;
             const float4 cn = gauss4_scaled(philox4x32_10_rk(noise_counter(quad, cfgrep, k + 1, 0u), keys), c2);
             float4 to, vo;
             b2_update(K2, P1.s, P1.c, C1.th, C1.s, C1.c, N1.s, N1.c, C1.v, sL, cL, sR, cR, cn, to, vo);
@@ -962,13 +962,15 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
     const StepConst K0 = step_const(cf, 0.f);
     const bool const_T = cf.sched_kind == 0 && cf.n_knots <= 1;
     const float c_const = noise_amp(cf, 0);
-    // without a field schedule h and h p are the configuration's own for every
-    // step: read once here, not from the descriptor after every cluster barrier
-    const bool const_h = cf.f_n_knots == 0;
+    // without a field or coupling schedule h, h p and the couplings are the
+    // configuration's own for every step: read once here, not from the
+    // descriptor after every cluster barrier
+    const bool const_h = cf.f_n_knots == 0 && cf.c_n_knots == 0;
     const float h0 = cf.h;
-    // (each step loop below is compiled twice, with and without the schedule's
+    const float2 J0 = make_float2(cf.Jx, cf.Jy);
+    // (each step loop below is compiled twice, with and without the schedules'
     // code, and the block takes one of them: without a schedule the loop
-    // carries none of the knot search's registers)
+    // carries none of the knot searches' registers)
     const bool stag = cf.stag != 0;
     const int64_t kbase = cf.k_start + ca.k_shift;
     // noise of the band's single row (R = 1) at step k, computed one step
@@ -996,7 +998,12 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
             const int64_t k = kbase + j;
             StepConst K = K0;
             K.c = const_T ? c_const : noise_amp(cf, k);
-            K.hp = FS ? field_hp(cf, k) : K0.hp;
+            if constexpr (FS) {
+                const StepConst Kk = step_const_k(cf, k, K.c);
+                K.hp = Kk.hp;
+                K.nqJx = Kk.nqJx;
+                K.nqJy = Kk.nqJy;
+            }
             const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
             const int par = (int)(j & 1);
             const size_t poff = (size_t)(2 * par) * NB * Lx;
@@ -1032,7 +1039,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                     const float sigma = (stag && ((x + s + gy) & 1)) ? -1.f : 1.f;
                     pm = fmaf(sigma, cur.s[s], pm);
                     if (!ca.m_only)
-                        pe = __fadd_rn(pe, site_energy(cf, FS ? field_h(cf, k) : h0, so.omega, cur.s[s], cur.c[s], sr, cr,
+                        pe = __fadd_rn(pe, site_energy(cf, FS ? couplings_at(cf, k) : J0, FS ? field_h(cf, k) : h0, so.omega, cur.s[s], cur.c[s], sr, cr,
                                                        nxt.s[s], nxt.c[s], cosp_of(K.p, th)));
                 }
             }
@@ -1074,7 +1081,12 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
             const int64_t k = kbase + j;
             StepConst K = K0;
             K.c = const_T ? c_const : noise_amp(cf, k);
-            K.hp = FS ? field_hp(cf, k) : K0.hp;
+            if constexpr (FS) {
+                const StepConst Kk = step_const_k(cf, k, K.c);
+                K.hp = Kk.hp;
+                K.nqJx = Kk.nqJx;
+                K.nqJy = Kk.nqJy;
+            }
             const bool rec = ca.record_every > 0 && (k % ca.record_every) == 0;
             const int par = (int)(j & 1);
             float2* e_top = s_exp + (size_t)(2 * par) * NB * Lx;
@@ -1130,7 +1142,7 @@ __global__ void __launch_bounds__(MAXT, 1) resident_step_kernel(const DevCfg* cf
                         const float sigma = (stag && ((x + s + y_base + y) & 1)) ? -1.f : 1.f;
                         pm = fmaf(sigma, cur.s[s], pm);
                         if (!ca.m_only)
-                            pe = __fadd_rn(pe, site_energy(cf, FS ? field_h(cf, k) : h0, so.omega, cur.s[s], cur.c[s], sr, cr,
+                            pe = __fadd_rn(pe, site_energy(cf, FS ? couplings_at(cf, k) : J0, FS ? field_h(cf, k) : h0, so.omega, cur.s[s], cur.c[s], sr, cr,
                                                            nxt.s[s], nxt.c[s], cosp_of(K.p, th)));
                     }
                 }

@@ -30,6 +30,9 @@ class Config:
     cfg_id: int = -1      # configuration id in the noise counter (-1: position in the list)
     replica0: int = 0     # replica id of replica 0 in the noise counter
     field: tuple | None = None  # ((steps), (scales)): field schedule h_k = h s(k) (xy_set_field_schedule)
+    # ((steps), (scales of J_par), (scales of J_perp)): coupling profiles of the
+    # anisotropic quench, J_par a(k) and J_perp b(k) (xy_set_coupling_schedule)
+    couplings: tuple | None = None
 
     @property
     def sites(self) -> int:
@@ -76,6 +79,8 @@ class Lattice:
                 self.set_schedule(ci, c.knots[0], c.knots[1], c.n_total)
             if c.field is not None:
                 self.set_field_schedule(ci, c.field[0], c.field[1])
+            if c.couplings is not None:
+                self.set_coupling_schedule(ci, *c.couplings)
 
     # ------------------------------------------------------------ setup
     def set_params(self, c: int, **kw):
@@ -105,6 +110,17 @@ class Lattice:
         ss = np.ascontiguousarray(np.asarray(scales, dtype=np.float64))
         L.call("xy_set_field_schedule", self._h, c, ks.ctypes.data_as(ctypes.c_void_p),
                ss.ctypes.data_as(ctypes.c_void_p), int(ks.size))
+
+    def set_coupling_schedule(self, c: int, steps, par_scales, perp_scales):
+        """Coupling profiles of the anisotropic quench: J_par(k) = J_par a(k),
+        J_perp(k) = J_perp b(k), piecewise linear through the knots (empty:
+        remove)."""
+        ks = np.ascontiguousarray(np.asarray(steps, dtype=np.int64))
+        a = np.ascontiguousarray(np.asarray(par_scales, dtype=np.float64))
+        b = np.ascontiguousarray(np.asarray(perp_scales, dtype=np.float64))
+        assert ks.shape == a.shape == b.shape and ks.ndim == 1
+        L.call("xy_set_coupling_schedule", self._h, c, ks.ctypes.data_as(ctypes.c_void_p),
+               a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p), int(ks.size))
 
     def set_path(self, path: int):
         L.call("xy_set_path", self._h, path)
@@ -165,7 +181,7 @@ class Lattice:
 
     def structure_factor(self, b_first: int = 0, b_count: int | None = None, K: int = 16, rotor: float = 1.0):
         """S_par, S_perp of lattices [b_first, b_first + b_count) for k < K
-        (Sec. VI, Eq. S-as-lattice-FT): two (b_count, K) float64 device tensors."""
+        (App. C, Eq. S-as-lattice-FT): two (b_count, K) float64 device tensors."""
         b_count = self.n_lattices - b_first if b_count is None else b_count
         S_par = torch.empty((b_count, K), dtype=torch.float64, device=self.device)
         S_perp = torch.empty((b_count, K), dtype=torch.float64, device=self.device)

@@ -17,7 +17,8 @@ def gpu_config(spec: dict) -> Config:
     p = dict(spec["params"])
     return Config(Lx=spec["Lx"], Ly=spec["Ly"], n_replicas=spec["n_rep"], seed=spec["seed"],
                   init_mode=spec.get("init_mode", XY_INIT_USER), params=p, knots=spec["knots"],
-                  n_total=spec["n_total"], field=spec.get("field"))
+                  n_total=spec["n_total"], field=spec.get("field"),
+                  couplings=spec.get("couplings"))
 
 
 def make_pair(specs, thetas, omegas=None, path=None):
@@ -106,9 +107,10 @@ def box_muller_error(r: np.ndarray) -> np.ndarray:
     return ER1 / r + (ERR + ETRIG + 2 * U32) * r
 
 
-def _force_error(prm: dict, smax: float = 1.0) -> tuple[float, float]:
+def _force_error(prm: dict, smax: float = 1.0, amax: float = 1.0, bmax: float = 1.0) -> tuple[float, float]:
     U = U32
-    qJx, qJy = abs(prm["q"] * prm["J_par"]), abs(prm["q"] * prm["J_perp"])
+    # the largest couplings of profiles J_par a(k), J_perp b(k)
+    qJx, qJy = abs(prm["q"] * prm["J_par"]) * amax, abs(prm["q"] * prm["J_perp"]) * bmax
     hp = abs(prm["h"] * prm["p"]) * smax  # the largest field of a schedule h s(k)
     F_max = 2 * qJx + 2 * qJy + hp
     d_bond = 8 * ESC + 8 * U
@@ -126,9 +128,14 @@ def local_error_weights(spec: dict, cfg: int, rep: int, k0: int, n: int, theta: 
     hdt, dt = 0.5 * prm["dt"], prm["dt"]
     field = spec.get("field")
     smax = max([1.0] if field is None else [abs(x) for x in field[1]])
-    dF, F_max = _force_error(prm, smax)
+    cpl = spec.get("couplings")
+    amax = max([1.0] if cpl is None else [abs(x) for x in cpl[1]])
+    bmax = max([1.0] if cpl is None else [abs(x) for x in cpl[2]])
+    dF, F_max = _force_error(prm, smax, amax, bmax)
     if field is not None:
         dF += abs(prm["h"] * prm["p"]) * smax * 2 * U  # h p s(k): the scale and the product rounded
+    if cpl is not None:  # -q J a(k), -q J b(k): the scales and the products rounded, times |bond sums| <= 2
+        dF += 2 * 2 * U * (abs(prm["q"] * prm["J_par"]) * amax + abs(prm["q"] * prm["J_perp"]) * bmax)
     amps = np.array([0.5 * math.sqrt(2.0 * prm["eta"] * max(oracle.temperature(k0 + j, spec["knots"]), 0.0) * dt)
                      for j in range(n + 1)])
     g_max = hdt * F_max + amps.max() * R_MAX
@@ -154,10 +161,12 @@ def first_order_bound(spec: dict, cfg: int, rep: int, k0: int, n: int, theta0, o
     uniform within their bounds."""
     Lx, Ly = spec["Lx"], spec["Ly"]
     _, tth, tom = oracle.theta_sensitivity(Lx, Ly, cfg, rep, spec["seed"], spec["params"], spec["knots"], k0, n,
-                                           theta0, omega0, [], trajectory=True, field=spec.get("field"))
+                                           theta0, omega0, [], trajectory=True, field=spec.get("field"),
+                                           couplings=spec.get("couplings"))
     wt, wv = local_error_weights(spec, cfg, rep, k0, n, tth, tom)
     out = oracle.theta_sensitivity(Lx, Ly, cfg, rep, spec["seed"], spec["params"], spec["knots"], k0, n, theta0,
-                                   omega0, sites, wt=wt, wv=wv, field=spec.get("field"))
+                                   omega0, sites, wt=wt, wv=wv, field=spec.get("field"),
+                                   couplings=spec.get("couplings"))
     return out[:, 0], out[:, 1] / math.sqrt(3.0)
 
 

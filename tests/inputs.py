@@ -70,13 +70,15 @@ def spiral(L: int) -> np.ndarray:
     return g
 
 
-def config(Lx, Ly, n_rep, seed=1, init_mode=0, n_total=10**9, knots=None, field=None, **params):
+def config(Lx, Ly, n_rep, seed=1, init_mode=0, n_total=10**9, knots=None, field=None, couplings=None, **params):
     p = dict(PAPER)
     p.update(params)
     d = dict(Lx=Lx, Ly=Ly, n_rep=n_rep, seed=seed, init_mode=init_mode, params=p,
              knots=knots if knots is not None else ([0], [T_C]), n_total=n_total)
     if field is not None:
         d["field"] = field
+    if couplings is not None:
+        d["couplings"] = couplings
     return d
 
 

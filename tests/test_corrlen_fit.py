@@ -1,7 +1,7 @@
 """Host side of the correlation-length pipeline: the library's Lorentzian fit
 (paper_2409_06412_gb300.corrlen) recovers exact Lorentzians and agrees with
 the oracle's independent least-squares fit on structure factors the oracle
-computed (Sec. VI, Eq. Lorentzian-Peak)."""
+computed (App. C, Eq. Lorentzian-Peak)."""
 import math
 
 import numpy as np

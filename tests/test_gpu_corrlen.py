@@ -1,5 +1,5 @@
 """GPU structure factors (xy_structure_factor) against the oracle's literal
-2-D transform (Sec. VI, Eq. S-as-lattice-FT), element by element."""
+2-D transform (App. C, Eq. S-as-lattice-FT), element by element."""
 import numpy as np
 import pytest
 import torch

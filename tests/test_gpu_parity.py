@@ -335,7 +335,7 @@ def test_quench_schedule_parity():
 
 @pytest.mark.parametrize("gamma", [2.0, 3.0])
 def test_nonlinear_quench_parity(gamma):
-    """Nonlinear quench eps = -sign(t) |t / tau_Q|^gamma (Sec. VII) crossing T_c
+    """Nonlinear quench eps = -sign(t) |t / tau_Q|^gamma (Sec. V) crossing T_c
     inside a 100-step window, on the batched and the plain path, classified
     like every trajectory parity test (cusp events, FP32 conditioning)."""
     sched = {"power": (TC, 45, 40.0, gamma, 0.5, -0.9)}
@@ -430,6 +430,92 @@ def test_adjoint_with_field_schedule_matches_oracle(mode):
         shapes = [(16, 8, 2), (128, 4, 1), (256, 6, 1)]
     specs = [inputs.config(Lx, Ly, n, seed=3 + i, knots=knots, field=field, **prm) for i, (Lx, Ly, n) in enumerate(shapes)]
     thetas = _mixed_thetas(specs, seed=81)
+    lat, o_th, o_om = make_pair(specs, thetas)
+    lat.set_adjoint_mode(XY_ADJOINT_RECOMPUTE if mode == "recompute" else XY_ADJOINT_BACKWARD)
+    obj, grads = lat.adjoint(100, checkpoint_every=30, w_E=0.7, w_M=0.3)
+    o_obj, o_grads = _oracle_adjoint(specs, o_th, o_om, 100, 0.7, 0.3)
+    assert obj == pytest.approx(o_obj, rel=1e-5, abs=2e-6)
+    assert_grads_close(grads, o_grads, 1e-3)
+
+
+# an anisotropic quench: J_par ramps down by half while J_perp triples
+COUPLINGS = ([15, 85], [1.0, 0.5], [0.6, 3.0])
+
+
+@pytest.mark.parametrize("path", [XY_PATH_BATCHED, XY_PATH_PLAIN])
+def test_coupling_schedule_parity(path):
+    """Coupling profiles J_par a(k), J_perp b(k) (anisotropic quench) with a
+    temperature ramp and a field ramp at the same time, on the resident,
+    strip and plain kernels: 100 steps one at a time against the oracle,
+    classified like every trajectory test; then records of (M, E), which
+    carry the couplings of step k in E_k."""
+    knots = ([0, 100], [1.3 * TC, 0.6 * TC])
+    shapes = [(64, 64, 2), (256, 32, 1), (12, 10, 1)]
+    specs = [inputs.config(Lx, Ly, n, seed=91 + i, knots=knots, field=FIELD, couplings=COUPLINGS)
+             for i, (Lx, Ly, n) in enumerate(shapes)]
+    thetas = _mixed_thetas(specs, seed=93)
+    lat, o_th, o_om = make_pair(specs, thetas, path=path)
+    res = stepwise_parity(lat, specs, o_th, o_om, 100)
+    print(path, parity_report(res))
+    assert res["step_now"] == [100] * len(specs)
+    assert not res["unexplained"], (res["unexplained"][:10], res["events"][:10])
+    assert res["frac_within_tol"] > 1 - 1e-3
+    lat2, o_th2, o_om2 = make_pair(specs, thetas, path=path)
+    rec = lat2.step(60, record_every=6).cpu().numpy()
+    o_rec, _ = oracle.run_batch(specs, o_th2, o_om2, [0, 0, 0], 60, record_every=6)
+    b = 0
+    for c, s_ in enumerate(specs):
+        for r in range(s_["n_rep"]):
+            dm = np.abs(rec[b, :10, 0] - o_rec[c][r][:, 0]).max()
+            de = (np.abs(rec[b, :10, 1] - o_rec[c][r][:, 1]) / (1 + np.abs(o_rec[c][r][:, 1]))).max()
+            assert dm < 2e-5 and de < 2e-5, (c, r, dm, de)
+            b += 1
+
+
+def test_coupling_schedule_removed_and_snapshot():
+    """Removing the profiles restores the bits of a run that never had them;
+    they survive a snapshot; bad knots are refused."""
+    specs = [inputs.config(256, 32, 1, seed=95), inputs.config(64, 64, 1, seed=96)]
+    thetas = _mixed_thetas(specs, seed=97)
+    a, _, _ = make_pair(specs, thetas)
+    b, _, _ = make_pair([dict(s, couplings=COUPLINGS) for s in specs], thetas)
+    b.set_coupling_schedule(0, [], [], [])
+    b.set_coupling_schedule(1, [], [], [])
+    a.step(50)
+    b.step(50)
+    torch.cuda.synchronize()
+    assert torch.equal(a.theta, b.theta) and torch.equal(a.omega, b.omega)
+    c, _, _ = make_pair([dict(s, couplings=COUPLINGS) for s in specs], thetas)
+    c.step(30)
+    blob = c.save()
+    c.step(60)
+    t1 = c.theta.clone()
+    c.load(blob)
+    c.step(60)
+    torch.cuda.synchronize()
+    assert torch.equal(t1, c.theta)
+    with pytest.raises(XYError):
+        c.set_coupling_schedule(0, [5, 5], [1.0, 2.0], [1.0, 1.0])
+    with pytest.raises(XYError):
+        c.set_coupling_schedule(0, [5], [float("nan")], [1.0])
+
+
+@pytest.mark.parametrize("mode", ["recompute", "backward"])
+def test_adjoint_with_coupling_schedule_matches_oracle(mode):
+    """d/d(J_par, J_perp, h, eta) with both couplings ramped at different rates
+    and a field ramp (d/dJ and d/dh at the fixed profiles) against the
+    oracle's FP64 adjoint, every component within 1e-3."""
+    prm = dict(J_par=2.0, J_perp=0.5, h=1.0, p=2.0, eta=0.8)
+    knots = ([0, 100], [1.0, 0.5])
+    field = ([5, 70], [0.3, 1.8])
+    cpl = ([10, 60, 95], [1.4, 0.6, 1.0], [0.5, 2.0, 1.2])
+    if mode == "recompute":
+        shapes = [(16, 8, 2), (128, 4, 1), (12, 10, 1)]
+    else:
+        shapes = [(16, 8, 2), (128, 4, 1), (256, 6, 1)]
+    specs = [inputs.config(Lx, Ly, n, seed=13 + i, knots=knots, field=field, couplings=cpl, **prm)
+             for i, (Lx, Ly, n) in enumerate(shapes)]
+    thetas = _mixed_thetas(specs, seed=83)
     lat, o_th, o_om = make_pair(specs, thetas)
     lat.set_adjoint_mode(XY_ADJOINT_RECOMPUTE if mode == "recompute" else XY_ADJOINT_BACKWARD)
     obj, grads = lat.adjoint(100, checkpoint_every=30, w_E=0.7, w_M=0.3)
@@ -600,7 +686,8 @@ def _oracle_adjoint(specs, o_th, o_om, n, wE, wM):
         g = np.zeros(4)
         for r in range(s["n_rep"]):
             ob, gr, _, _ = oracle.adjoint_lattice(s["Lx"], s["Ly"], c, r, s["seed"], s["params"], s["knots"], 0, n,
-                                                  o_th[c][r], o_om[c][r], wE, wM, field=s.get("field"))
+                                                  o_th[c][r], o_om[c][r], wE, wM, field=s.get("field"),
+                                                  couplings=s.get("couplings"))
             obj += ob
             g += gr
         grads.append(g / (B * n))

@@ -114,6 +114,17 @@ def test_two_steps_with_a_field_schedule():
     assert _same(two, ref)
 
 
+def test_two_steps_with_coupling_profiles():
+    """The two-step kernel takes each step's own couplings (J_par a(k),
+    J_perp b(k) of an anisotropic ramp): the same bits as one step per launch."""
+    specs = [dict(s, couplings=([0, 60], [1.0, 0.4], [0.5, 2.5])) for s in _specs()]
+    two, ref = _pair(specs, seed=10)
+    for n in (64, 36):
+        two.step(n)
+        ref.step(n)
+    assert _same(two, ref)
+
+
 def test_temporal_blocking_rejects_bad_modes():
     from paper_2409_06412_gb300 import XYError
     two, _ = _pair(_specs())

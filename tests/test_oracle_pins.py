@@ -557,7 +557,7 @@ def test_adjoint_forward_equals_stepper(field):
 
 
 # ---------------------------------------------------------------- nonlinear quench schedule
-# (Sec. VII: eps(t) = t^gamma / tau_Q^gamma; gamma = 1 is Eq. Linear-Quench)
+# (Sec. V: eps(t) = t^gamma / tau_Q^gamma; gamma = 1 is Eq. Linear-Quench)
 
 def test_power_quench_gamma_one_is_the_linear_ramp():
     Tc, kc, tq, ei, ef = 1.969, 500.0, 200.0, 0.5, -1.0
@@ -782,7 +782,7 @@ def test_adjoint_with_field_schedule_matches_finite_differences():
 
 
 # ---------------------------------------------------------------- anisotropic quench: coupling profiles
-# (Sec. VII, Sec. VIII: the two directional couplings quenched at different
+# (Sec. V: the two directional couplings quenched at different
 # rates, J_par(k) = J_par a(k), J_perp(k) = J_perp b(k))
 
 def test_coupling_schedule_scales_the_couplings_exactly():
