@@ -368,12 +368,15 @@ int64_t xy_kernel_launches(xy_lattice* lat);
 #define XY_KCLASS_ADJ_RECOMP 4 /* adjoint: recompute of the checkpoint segments (one span per call) */
 #define XY_KCLASS_ADJ_REV 5   /* adjoint: reverse sweep kernels (one span per call) */
 #define XY_KCLASS_STRIP2 6    /* two-step band launches (temporal blocking; each launch is two steps) */
-#define XY_KCLASS_COUNT 7
+#define XY_KCLASS_LABELS 7    /* domain labelling: the passes of one chunk of xy_label_domains (one span each) */
+#define XY_KCLASS_COUNT 8
 
 /* Kernel timing.  on != 0: the batched path launches its kernels directly
  * (no graph replay) and brackets every stepper launch with CUDA events on the
- * object's stream, and the adjoint brackets its three phases (the spans
- * include the kernels of every class inside them); nothing is skipped.  on == 0 (default): graphs, no events.
+ * object's stream, the adjoint brackets its three phases (the spans include
+ * the kernels of every class inside them) and xy_label_domains the passes of
+ * each chunk (from the first pass to the last, host copies excluded); nothing
+ * is skipped.  on == 0 (default): graphs, no events.
  * Switching clears the accumulated times. */
 int xy_set_kernel_timing(xy_lattice* lat, int on);
 

@@ -16,6 +16,9 @@ XY_PATH_BATCHED, XY_PATH_PLAIN = 0, 1
 XY_ADJOINT_AUTO, XY_ADJOINT_RECOMPUTE, XY_ADJOINT_BACKWARD = 0, 1, 2
 XY_MAX_KNOTS = 16
 XY_STATIC_CCL_MAX_SITES, XY_STATIC_CCL_MAX_LATTICES = 2097152, 65536
+(XY_KCLASS_RESIDENT, XY_KCLASS_STRIP, XY_KCLASS_PLAIN, XY_KCLASS_ADJ_FWD, XY_KCLASS_ADJ_RECOMP, XY_KCLASS_ADJ_REV,
+ XY_KCLASS_STRIP2, XY_KCLASS_LABELS) = range(8)
+XY_KCLASS_COUNT = 8
 
 ERROR_NAMES = {XY_EINVAL: "XY_EINVAL", XY_ENOMEM: "XY_ENOMEM", XY_ECUDA: "XY_ECUDA",
                XY_ETIMEOUT: "XY_ETIMEOUT", XY_ENAN: "XY_ENAN"}

@@ -1811,13 +1811,16 @@ int xy_label_domains(xy_lattice* L, int b_first, int b_count, int32_t* labels, i
         int32_t* lab_out = dev_lab ? labels + b0 * N : lab;
         int64_t* h_out = hist ? (dev_hist ? hist + b0 * hist_cap * 2 : hs) : nullptr;
         int64_t* ns_out = n_sizes ? (dev_ns ? n_sizes + b0 : ns) : nullptr;
-        e = launch_ccl(L->thA + site0 + b0 * N, Lx, Ly, nl, lab_out, scratch, h_out,
-                           hist ? hist_cap : 0, ns_out, L->d_err, L->stream);
+        cudaEvent_t span_end = nullptr;
+        if ((rc = timed_begin(L, L->stream, XY_KCLASS_LABELS, &span_end))) break;
+        e = launch_ccl(L->thA + site0 + b0 * N, Lx, Ly, nl, lab_out, scratch, h_out, hist ? hist_cap : 0, ns_out,
+                       L->d_err, L->stream);
+        if (e == cudaSuccess && span_end) e = cudaEventRecord(span_end, L->stream);
         if (e != cudaSuccess) {
             rc = fail(XY_ECUDA, "labelling: %s", cudaGetErrorString(e));
             break;
         }
-        L->launches += 5;
+        L->launches += 6;
         if (labels && !dev_lab)
             e = cudaMemcpyAsync(labels + b0 * N, lab, sizeof(int32_t) * N * nl, cudaMemcpyDeviceToHost, L->stream);
         if (e == cudaSuccess && hist && !dev_hist)

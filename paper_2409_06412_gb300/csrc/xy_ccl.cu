@@ -600,12 +600,17 @@ __global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, CclScratch
     int64_t* out = hist ? hist + (int64_t)lat * hist_cap * 2 : nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_small = (int)(N < kSmallSizes - 1 ? N : kSmallSizes - 1);  // sizes 1..n_small
-    if (threadIdx.x < kSmallSizes) {
-        const int z = threadIdx.x;
+    if (threadIdx.x < kSmallSizes) s_small[threadIdx.x] = 0;
+    __syncthreads();
+    {
+        // thread j adds copies j / 64, j / 64 + 16, ... of size j % 64: every
+        // copy is read by one thread, at most two loads deep
+        const int z = threadIdx.x & (kSmallSizes - 1);
+        const int nk = (int)blockDim.x / kSmallSizes;
         int v = 0;
         if (z >= 1 && z <= n_small) {
-            int32_t* c = s.small + (int64_t)lat * s.copies * kSmallSizes + z;
-            for (int k = 0; k < s.copies; ++k, c += kSmallSizes) {
+            for (int k = (int)threadIdx.x / kSmallSizes; k < s.copies; k += nk) {
+                int32_t* c = s.small + ((int64_t)lat * s.copies + k) * kSmallSizes + z;
                 const int a = *c;
                 if (a) {
                     v += a;
@@ -613,7 +618,7 @@ __global__ void __launch_bounds__(1024) ccl_compact_kernel(int64_t N, CclScratch
                 }
             }
         }
-        s_small[z] = v;
+        if (v) atomicAdd(&s_small[z], v);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -222,10 +222,10 @@ class Lattice:
 
     def kernel_timing(self):
         """(ms, launches) per timing class (resident, strip, plain stepper launches;
-        adjoint forward, recompute and reverse spans; two-step band launches)
-        since timing was switched on."""
-        ms = np.zeros(7, dtype=np.float64)
-        n = np.zeros(7, dtype=np.int64)
+        adjoint forward, recompute and reverse spans; two-step band launches;
+        domain labelling spans) since timing was switched on."""
+        ms = np.zeros(L.XY_KCLASS_COUNT, dtype=np.float64)
+        n = np.zeros(L.XY_KCLASS_COUNT, dtype=np.int64)
         L.call("xy_kernel_timing", self._h, ms.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p))
         return ms, n
 

@@ -35,6 +35,17 @@ def test_header_and_binding_agree():
     assert declared == set(_lib.SIGNATURES), declared ^ set(_lib.SIGNATURES)
 
 
+def test_binding_constants_match_the_header():
+    """Every integer #define XY_... of the header that the binding also
+    defines has the same value there."""
+    src = open(os.path.join(ROOT, "include", "xy_lattice.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(XY_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src)}
+    shared = {k for k in defs if hasattr(_lib, k)}
+    assert {"XY_KCLASS_LABELS", "XY_KCLASS_COUNT", "XY_INIT_ORDERED", "XY_ETIMEOUT"} <= shared
+    for k in shared:
+        assert getattr(_lib, k) == defs[k], k
+
+
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (xy_[a-z_0-9]+)", out))

@@ -674,6 +674,15 @@ def test_domain_labels_after_quench_and_host_outputs():
     if ns_h.max() > 8:
         assert rc == _lib.XY_EINVAL  # more distinct sizes than hist_cap
     assert np.array_equal(hist_h[:, :8], hist[:, :8].cpu().numpy())
+    # with kernel timing on, each call records one span of its passes and the
+    # labels do not change
+    lat.set_kernel_timing(True)
+    for _ in range(2):
+        lab_t, _, _ = lat.label_domains(hist_cap=4096)
+    ms, n = lat.kernel_timing()
+    lat.set_kernel_timing(False)
+    assert n[_lib.XY_KCLASS_LABELS] == 2 and ms[_lib.XY_KCLASS_LABELS] > 0
+    assert np.array_equal(lab_t.cpu().numpy(), labels.cpu().numpy())
 
 
 # ------------------------------------------------------------------ adjoint
