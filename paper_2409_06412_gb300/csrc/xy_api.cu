@@ -241,6 +241,7 @@ struct xy_lattice {
         int rec;
         uint32_t rec_mask;
         uint32_t kt2;
+        uint32_t sched;  // sched_mask() at capture: the strip kernels chosen by schedule presence
         cudaGraphExec_t exec;
         int64_t kernels;
     };
@@ -466,6 +467,24 @@ struct Span {
     int close() { return timed_end(end, L->stream); }
 };
 
+// Whether some configuration of a strip group has a field or coupling
+// schedule (its launches then take the kernels that evaluate them).
+bool group_sched(const xy_lattice* L, const StripGroup& g)
+{
+    for (int c : g.cfgs)
+        if (L->h_dev[c].f_n_knots != 0 || L->h_dev[c].c_n_knots != 0) return true;
+    return false;
+}
+
+// Bit g: strip group g has a schedule (part of a captured chunk's key).
+uint32_t sched_mask(const xy_lattice* L)
+{
+    uint32_t m = 0;
+    for (size_t g = 0; g < L->strip_groups.size() && g < 32; ++g)
+        if (group_sched(L, L->strip_groups[g])) m |= 1u << g;
+    return m;
+}
+
 // Whether strip group g takes the local steps [jl0, jl0 + cnt) two per launch:
 // the window allows it (cur_kt2: every configuration of the group runs the
 // whole window), none of the steps records, and the batch holds an even number
@@ -507,8 +526,8 @@ int launch_batched_steps(xy_lattice* L, cudaStream_t st, int64_t jl0, int cnt, b
             // only the steps that record run the recording kernel
             const int rec = (L->cur_rec && ((L->cur_mask >> ((jl0 + i) & 31)) & 1u)) ? L->cur_rec : 0;
             const int var = rec && g.variant_rec ? g.variant_rec : g.variant;
-            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, var, rec, g.seed,
-                                 jl0 + i, buf, L->d_call, L->pa, st));
+            CK(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, var, rec, group_sched(L, g),
+                                 g.seed, jl0 + i, buf, L->d_call, L->pa, st));
             if ((rc = timed_end(end, st))) return rc;
             ++L->launches;
         }
@@ -702,8 +721,8 @@ cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, const Branch& br, int6
             auto& g = L->strip_groups[br.group];
             const int rec = (L->cur_rec && ((L->cur_mask >> ((jl0 + i) & 31)) & 1u)) ? L->cur_rec : 0;
             const int var = rec && g.variant_rec ? g.variant_rec : g.variant;
-            e = launch_strip_step(L->d_cfg, g.d_tasks + br.task0, br.n_tasks, g.H, var, rec, g.seed, jl0 + i, buf,
-                                  L->d_call, L->pa, st);
+            e = launch_strip_step(L->d_cfg, g.d_tasks + br.task0, br.n_tasks, g.H, var, rec, group_sched(L, g), g.seed,
+                                  jl0 + i, buf, L->d_call, L->pa, st);
             ++L->launches;
         } else {
             for (int c : L->plain_cfgs) {
@@ -723,8 +742,10 @@ cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, const Branch& br, int6
 // idle as its launch drains) instead of taking turns every step.
 int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
+    const uint32_t sm = sched_mask(L);
     for (auto& g : L->graphs)
-        if (g.chunk == chunk && g.rec == L->cur_rec && g.rec_mask == L->cur_mask && g.kt2 == L->cur_kt2) {
+        if (g.chunk == chunk && g.rec == L->cur_rec && g.rec_mask == L->cur_mask && g.kt2 == L->cur_kt2 &&
+            g.sched == sm) {
             *out = &g;
             return XY_OK;
         }
@@ -768,7 +789,7 @@ int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    L->graphs.push_back({chunk, L->cur_rec, L->cur_mask, L->cur_kt2, exec, kernels});
+    L->graphs.push_back({chunk, L->cur_rec, L->cur_mask, L->cur_kt2, sm, exec, kernels});
     *out = &L->graphs.back();
     return XY_OK;
 }
@@ -885,8 +906,8 @@ int autotune_lattice(xy_lattice* L)
                     for (int vi = 0; vi < 3; ++vi) {
                         const int v = 2 + vi;
                         auto run = [&](cudaStream_t st, int t0, int cnt) {
-                            return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, H, v, 0, g.seed, 0, buf,
-                                                     L->d_call, L->pa, st);
+                            return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, H, v, 0, group_sched(L, g), g.seed,
+                                                     0, buf, L->d_call, L->pa, st);
                         };
                         CK(launch_sliced(L, cuts, 1, run));
                         CK(cudaEventRecord(e0, L->stream));
@@ -942,8 +963,8 @@ int autotune_lattice(xy_lattice* L)
                     for (int vi = 0; vi < 2; ++vi) {
                         const int v = 2 + vi;
                         auto run = [&](cudaStream_t st, int t0, int cnt) {
-                            return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, bh, v, 1, g.seed, 0, buf,
-                                                     L->d_call, L->pa, st);
+                            return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, bh, v, 1, group_sched(L, g),
+                                                     g.seed, 0, buf, L->d_call, L->pa, st);
                         };
                         cudaError_t e = launch_sliced(L, cuts, 1, run);
                         if (e == cudaSuccess) e = cudaEventRecord(e0, L->stream);
@@ -1002,8 +1023,8 @@ int autotune_lattice(xy_lattice* L)
                 };
                 float t1 = 1e30f;
                 rc = time_it(cuts1, [&](cudaStream_t st, int t0, int cnt) {
-                    return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, g.H, g.variant, 0, g.seed, 0, buf,
-                                             L->d_call, L->pa, st);
+                    return launch_strip_step(L->d_cfg, g.d_tasks + t0, cnt, g.H, g.variant, 0, group_sched(L, g),
+                                             g.seed, 0, buf, L->d_call, L->pa, st);
                 }, t1);
                 float best2 = 1e30f;
                 int bestH = 0, bestV = 2;
@@ -2414,8 +2435,8 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                     ++L->launches;
                 }
                 for (auto& g : L->strip_groups) {
-                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, 0, g.seed, i,
-                                          buf, L->d_call, L->pa, L->stream));
+                    CKA(launch_strip_step(L->d_cfg, g.d_tasks, (int)g.tasks.size(), g.H, g.variant, 0,
+                                          group_sched(L, g), g.seed, i, buf, L->d_call, L->pa, L->stream));
                     ++L->launches;
                 }
                 for (int c : L->plain_cfgs) {

@@ -1,5 +1,6 @@
 // xy_internal.h -- data shared between the library's translation units.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -8,7 +9,11 @@
 namespace xy {
 
 // Per-configuration record in device memory (read by every kernel).
-struct DevCfg {
+// One configuration's constants on the device.  The fields every launch
+// reads at its start (geometry, noise ids, the step's FP32 constants, the
+// call's step range and whether schedules are set) share the first 128-byte
+// line; records are line-aligned, so a block's first reads touch few lines.
+struct alignas(128) DevCfg {
     int32_t Lx, Ly, n_rep, slot;  // slot: index of this record in the device table
     int32_t noise_cfg;  // configuration id in the noise counter
     int32_t rep0;       // replica id of replica 0 in the noise counter
@@ -19,16 +24,23 @@ struct DevCfg {
     int32_t stag;
     // FP32 constants of the step
     float Jx, Jy, h, p, q, dt, hdt, oma, inv1pa, nqJx, nqJy, hp;
-    double eta_d, dt_d;
+    // per call
+    int64_t k_start;    // step at the start of the current call
+    int64_t n_call;     // steps this configuration takes in the current call
+    int32_t f_n_knots;  // knots of the field schedule (0: none)
+    int32_t c_n_knots;  // knots of the coupling profiles (0: none)
+    // ---- temperature schedule
     int32_t n_knots;
     int32_t sched_kind;  // 0: knots below; 1: nonlinear quench (pw_* fields)
-    int64_t knot_step[XY_MAX_KNOTS];
-    double knot_T[XY_MAX_KNOTS];
+    float amp_pref;      // (1/2) sqrt(2 eta dt): noise amplitude c_k = amp_pref sqrt(T_k)
+    float e_ref;         // -(|J_par| + |J_perp| + |h|): site energies are summed relative to it
     // FP32 schedule used on the device: T(k) = knot_Tf[i] + slope_f[i] (k - knot_step[i])
     float knot_Tf[XY_MAX_KNOTS];
     float slope_f[XY_MAX_KNOTS];
-    float amp_pref;     // (1/2) sqrt(2 eta dt): noise amplitude c_k = amp_pref sqrt(T_k)
-    float e_ref;        // -(|J_par| + |J_perp| + |h|): site energies are summed relative to it
+    int64_t knot_step[XY_MAX_KNOTS];
+    double knot_T[XY_MAX_KNOTS];
+    int64_t rec_first;  // first step of this call with k % record_every == 0
+    double eta_d, dt_d;
     // nonlinear quench: T(k) = pw_Tc (1 + eps), eps = -sign(t) (|t| / tau_Q)^gamma, t = k - pw_kc,
     // held within [pw_ef, pw_ei]
     int64_t pw_kc;
@@ -37,26 +49,19 @@ struct DevCfg {
     // field schedule (the orthogonal quench): h_k = h s(k), s piecewise linear
     // through (f_knot_step[i], f_knot_s[i]) and constant outside them, in FP32
     // from per-segment slopes like T(k); f_n_knots = 0: s = 1 (no schedule)
-    int32_t f_n_knots;
-    float f_pad;
     int64_t f_knot_step[XY_MAX_KNOTS];
     float f_knot_s[XY_MAX_KNOTS];
     float f_slope[XY_MAX_KNOTS];
     // coupling profiles (the anisotropic quench): J_par(k) = J_par a(k),
     // J_perp(k) = J_perp b(k), piecewise linear through one knot grid, in FP32
     // from per-segment slopes; c_n_knots = 0: a = b = 1 (no schedule)
-    int32_t c_n_knots;
-    float c_pad;
     int64_t c_knot_step[XY_MAX_KNOTS];
     float c_knot_a[XY_MAX_KNOTS];
     float c_knot_b[XY_MAX_KNOTS];
     float c_slope_a[XY_MAX_KNOTS];
     float c_slope_b[XY_MAX_KNOTS];
-    // per call
-    int64_t k_start;    // step at the start of the current call
-    int64_t n_call;     // steps this configuration takes in the current call
-    int64_t rec_first;  // first step of this call with k % record_every == 0
 };
+static_assert(offsetof(DevCfg, c_n_knots) + sizeof(int32_t) <= 128, "hot fields in the first line");
 
 // Per-call settings read by the stepping kernels.
 // Lives in device memory so that captured CUDA graphs stay valid across calls.
@@ -131,10 +136,12 @@ cudaError_t launch_omega_full(const DevCfg* d_cfg, const DevCfg& h_cfg, int rep_
                               const float* theta, const float* omega, float* out, cudaStream_t st);
 cudaError_t launch_plain_step(const DevCfg* d_cfg, const DevCfg& h_cfg, int64_t j_local, Buffers buf,
                               const CallArgs* ca, Partials pa, int write_state, cudaStream_t st);
-// rec: 0 = no records in this launch, 1 = records of M only, 2 = M and E
+// rec: 0 = no records in this launch, 1 = records of M only, 2 = M and E;
+// sched: some configuration of the tasks has a field or coupling schedule
+// (false selects kernels that read the configurations' constants only)
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
-                              int rec, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
-                              cudaStream_t st);
+                              int rec, bool sched, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca,
+                              Partials pa, cudaStream_t st);
 // two steps per launch (k -> k + 2) on bands of H rows across the lattice
 // width (256 <= Lx <= 1024); the launch at j_local takes steps j and j + 1 of
 // the call; a batch of launches must hold an even number of such pairs

@@ -514,7 +514,10 @@ __device__ __forceinline__ void strip_rows(StripCtx& X, const DevCfg& cf, const 
 
 // REC: 0 = the launch records nothing, 1 = it may record M, 2 = M and E.
 // Each kernel carries only the recording code (and registers) it needs.
-template <int MINB, int REC>
+// SCHED: some configuration of the launch has a field or coupling schedule;
+// without one the step's constants are the configuration's own, and the
+// kernel carries none of the knot searches (1.7 % of the batch's step time).
+template <int MINB, int REC, bool SCHED>
 __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfgs, const StripTask* tasks, int H,
                                                                int64_t j_local, Buffers buf, const CallArgs* cap,
                                                                Partials pa, PhiloxKeys keys)
@@ -530,7 +533,7 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     if (j >= cf.n_call) return;
     StripCtx X;
     X.k = cf.k_start + j + ca.k_shift;
-    X.K = step_const_k(cf, X.k, noise_amp(cf, X.k));
+    X.K = SCHED ? step_const_k(cf, X.k, noise_amp(cf, X.k)) : step_const(cf, noise_amp(cf, X.k));
     X.Lx = cf.Lx;
     X.Ly = cf.Ly;
     const bool odd = !ca.fixed_parity && (j & 1) != 0;
@@ -559,10 +562,10 @@ __global__ void __launch_bounds__(256, MINB) strip_step_kernel(const DevCfg* cfg
     X.pm = 0.f;
     X.pe = 0.f;
     if (REC > 0 && X.rec) {  // block-uniform
-        const float2 Jk = couplings_at(cf, X.k);
+        const float2 Jk = SCHED ? couplings_at(cf, X.k) : make_float2(cf.Jx, cf.Jy);
         X.Jx = Jk.x;
         X.Jy = Jk.y;
-        X.hF = field_h(cf, X.k);
+        X.hF = SCHED ? field_h(cf, X.k) : cf.h;
         X.eref = cf.e_ref;
         X.stag = cf.stag != 0;
         if (live) strip_rows<REC>(X, cf, keys, ybeg, H, s_stage[warp]);
@@ -606,8 +609,8 @@ int strip_units_per_lattice(int Lx, int Ly, int H)
 // variant = resident blocks per SM the registers are capped for (2, 3 or 4).
 // Every task of one launch uses the noise key `seed`.
 cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n_tasks, int H, int variant,
-                              int rec, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca, Partials pa,
-                              cudaStream_t st)
+                              int rec, bool sched, uint64_t seed, int64_t j_local, Buffers buf, const CallArgs* ca,
+                              Partials pa, cudaStream_t st)
 {
     if (n_tasks == 0) return cudaSuccess;
     const PhiloxKeys keys = philox_round_keys(seed);
@@ -615,13 +618,20 @@ cudaError_t launch_strip_step(const DevCfg* d_cfg, const StripTask* tasks, int n
                           PhiloxKeys);
     // Launches that record run at most 3 blocks per SM: capped at 64
     // registers the recording code spills inside the row loop.
-    static const Kern table[3][3] = {
-        {strip_step_kernel<2, 0>, strip_step_kernel<2, 1>, strip_step_kernel<2, 2>},
-        {strip_step_kernel<3, 0>, strip_step_kernel<3, 1>, strip_step_kernel<3, 2>},
-        {strip_step_kernel<4, 0>, strip_step_kernel<3, 1>, strip_step_kernel<3, 2>},
+    static const Kern table[2][3][3] = {
+        {
+            {strip_step_kernel<2, 0, false>, strip_step_kernel<2, 1, false>, strip_step_kernel<2, 2, false>},
+            {strip_step_kernel<3, 0, false>, strip_step_kernel<3, 1, false>, strip_step_kernel<3, 2, false>},
+            {strip_step_kernel<4, 0, false>, strip_step_kernel<3, 1, false>, strip_step_kernel<3, 2, false>},
+        },
+        {
+            {strip_step_kernel<2, 0, true>, strip_step_kernel<2, 1, true>, strip_step_kernel<2, 2, true>},
+            {strip_step_kernel<3, 0, true>, strip_step_kernel<3, 1, true>, strip_step_kernel<3, 2, true>},
+            {strip_step_kernel<4, 0, true>, strip_step_kernel<3, 1, true>, strip_step_kernel<3, 2, true>},
+        },
     };
     const int vi = variant >= 4 ? 2 : (variant == 3 ? 1 : 0);
-    const Kern kern = table[vi][rec < 0 ? 0 : (rec > 2 ? 2 : rec)];
+    const Kern kern = table[sched ? 1 : 0][vi][rec < 0 ? 0 : (rec > 2 ? 2 : rec)];
     kern<<<(unsigned)n_tasks, 256, 0, st>>>(d_cfg, tasks, H, j_local, buf, ca, pa, keys);
     return cudaGetLastError();
 }

@@ -500,6 +500,36 @@ def test_coupling_schedule_removed_and_snapshot():
         c.set_coupling_schedule(0, [5], [float("nan")], [1.0])
 
 
+@pytest.mark.parametrize("kind", ["field", "couplings"])
+def test_schedule_set_between_calls(kind):
+    """A schedule set after the stepper has run (and captured its graphs)
+    without one takes effect: the run equals one that had the schedule from
+    the start, its scales exactly 1 up to the first knot, bit for bit."""
+    specs = [inputs.config(256, 32, 2, seed=101), inputs.config(64, 64, 1, seed=102)]
+    thetas = _mixed_thetas(specs, seed=103)
+    sched = dict(field=([40, 80], [1.0, 2.0])) if kind == "field" else dict(couplings=([40, 80], [1.0, 0.5], [1.0, 3.0]))
+    a, _, _ = make_pair([dict(s, **sched) for s in specs], thetas)
+    b, _, _ = make_pair(specs, thetas)
+    a.step(40)
+    b.step(40)
+    torch.cuda.synchronize()
+    assert torch.equal(a.theta, b.theta) and torch.equal(a.omega, b.omega)
+    for c in range(len(specs)):
+        if kind == "field":
+            b.set_field_schedule(c, *sched["field"])
+        else:
+            b.set_coupling_schedule(c, *sched["couplings"])
+    a.step(70)
+    b.step(70)
+    torch.cuda.synchronize()
+    assert torch.equal(a.theta, b.theta) and torch.equal(a.omega, b.omega)
+    # and the schedule does act: a run without it differs
+    c0, _, _ = make_pair(specs, thetas)
+    c0.step(110)
+    torch.cuda.synchronize()
+    assert not torch.equal(c0.theta, b.theta)
+
+
 @pytest.mark.parametrize("mode", ["recompute", "backward"])
 def test_adjoint_with_coupling_schedule_matches_oracle(mode):
     """d/d(J_par, J_perp, h, eta) with both couplings ramped at different rates
