@@ -207,7 +207,12 @@ int xy_label_domains_static(const float* theta, int Lx, int Ly, int n_lattices, 
  * held fixed; the wrap has derivative 1; the kink of the field potential at
  * +-pi/2 contributes nothing (derivative almost everywhere).  The state is
  * checkpointed every checkpoint_every steps; the reverse sweep gets the states
- * of each segment as xy_set_adjoint_mode() selects.  objective, grads: host. */
+ * of each segment as xy_set_adjoint_mode() selects.  objective, grads: host.
+ * The working memory (the checkpoints, 8 bytes per site per segment, plus
+ * 32 bytes per site of segment and adjoint states; the stored recompute
+ * 8 bytes per site per step of a segment instead) is allocated by the first
+ * call that needs more than the lattice object holds and kept until
+ * xy_lattice_destroy; XY_ENOMEM if it cannot be allocated. */
 int xy_adjoint_step_n(xy_lattice* lat, int64_t n, int checkpoint_every, double w_E, double w_M,
                       double* objective, double* grads);
 

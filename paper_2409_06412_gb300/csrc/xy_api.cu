@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "xy_internal.h"
@@ -262,6 +263,15 @@ struct xy_lattice {
     void* ccl_buf = nullptr;
     int64_t ccl_bytes = 0;
     int64_t ccl_clean = 0;
+    // working memory of the adjoint, kept between calls (each slot grown on
+    // demand, all freed with the object): checkpoints, segment states,
+    // adjoint states, records, gradient partials, partials of M, band tasks
+    struct DevSlot {
+        void* p = nullptr;
+        size_t cap = 0;
+    };
+    enum { kAdjCk, kAdjSbuf, kAdjSeg, kAdjB, kAdjFb, kAdjRec, kAdjGacc, kAdjMpart, kAdjTasks, kAdjSlots };
+    DevSlot adj_slot[kAdjSlots];
 };
 
 namespace {
@@ -1447,6 +1457,7 @@ void free_lattice(xy_lattice* L)
     cudaFree(L->d_moments);
     cudaFree(L->rec_buf);
     cudaFree(L->ccl_buf);
+    for (auto& sl : L->adj_slot) cudaFree(sl.p);
     cudaFree(L->d_err);
     if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
     for (int i = 0; i < xy_lattice::kBranches; ++i) {
@@ -1953,6 +1964,27 @@ int xy_structure_factor(xy_lattice* L, int b_first, int b_count, int K, double r
     return XY_OK;
 }
 
+// At least `bytes` of slot i of the adjoint's working memory (reallocated
+// only when it must grow; cudaFree waits for the device, so no launch still
+// uses the old block).
+cudaError_t adj_reserve(xy_lattice* L, int i, size_t bytes, void** out)
+{
+    xy_lattice::DevSlot& sl = L->adj_slot[i];
+    if (bytes > sl.cap) {
+        cudaFree(sl.p);
+        sl.p = nullptr;
+        sl.cap = 0;
+        const cudaError_t e = cudaMalloc(&sl.p, bytes);
+        if (e != cudaSuccess) {
+            sl.p = nullptr;
+            return e;
+        }
+        sl.cap = bytes;
+    }
+    *out = sl.p;
+    return cudaSuccess;
+}
+
 int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, double* objective, double* grads)
 {
     if (!L || !objective || !grads) return fail(XY_EINVAL, "NULL argument");
@@ -2052,28 +2084,23 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     float *ck = nullptr, *seg = nullptr, *adjb = nullptr, *Fb = nullptr, *sbuf = nullptr;
     double2* arec = nullptr;
     double *gacc = nullptr, *mpart = nullptr;
-    auto cleanup = [&]() {
-        for (auto& g : adj_groups) cudaFree(g.d_tasks);
-        cudaFree(ck);
-        cudaFree(seg);
-        cudaFree(sbuf);
-        cudaFree(adjb);
-        cudaFree(Fb);
-        cudaFree(arec);
-        cudaFree(gacc);
-        cudaFree(mpart);
+    // the buffers are slots of the object's working memory, kept for the next call
+    auto reserve = [&](int i, size_t bytes, auto** out) {
+        void* p = nullptr;
+        const cudaError_t e1 = adj_reserve(L, i, bytes, &p);
+        *out = static_cast<std::remove_reference_t<decltype(**out)>*>(p);
+        return e1;
     };
-    cudaError_t e = cudaMalloc(&ck, sizeof(float) * 2 * T * nseg);
+    cudaError_t e = reserve(xy_lattice::kAdjCk, sizeof(float) * 2 * T * nseg, &ck);
     // backward: two recovered states (ping-pong); recompute: the K + 1 states of a segment
-    if (e == cudaSuccess && back) e = cudaMalloc(&sbuf, sizeof(float) * 4 * T);
-    if (e == cudaSuccess && !back) e = cudaMalloc(&seg, sizeof(float) * 2 * T * (K + 1));
+    if (e == cudaSuccess && back) e = reserve(xy_lattice::kAdjSbuf, sizeof(float) * 4 * T, &sbuf);
+    if (e == cudaSuccess && !back) e = reserve(xy_lattice::kAdjSeg, sizeof(float) * 2 * T * (K + 1), &seg);
     // adjoint state, double-buffered: (tb, vb) of two time levels
-    if (e == cudaSuccess) e = cudaMalloc(&adjb, sizeof(float) * 4 * T);
-    if (e == cudaSuccess && !adj_plain.empty()) e = cudaMalloc(&Fb, sizeof(float) * T);
-    if (e == cudaSuccess) e = cudaMalloc(&arec, sizeof(double2) * L->B * R_);
+    if (e == cudaSuccess) e = reserve(xy_lattice::kAdjB, sizeof(float) * 4 * T, &adjb);
+    if (e == cudaSuccess && !adj_plain.empty()) e = reserve(xy_lattice::kAdjFb, sizeof(float) * T, &Fb);
+    if (e == cudaSuccess) e = reserve(xy_lattice::kAdjRec, sizeof(double2) * L->B * R_, &arec);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cleanup();
         return fail(XY_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
     }
     // band height per group: tuned (timed reverse launches on zeroed buffers,
@@ -2198,7 +2225,6 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 cudaFree(mp_tmp);
                 if (e != cudaSuccess) {
                     cudaGetLastError();
-                    cleanup();
                     return fail(XY_ECUDA, "adjoint band tuning: %s", cudaGetErrorString(e));
                 }
                 if (bh > 0) g_tune.put(key, bh, 0);
@@ -2215,40 +2241,39 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         block_base[c] = n_blocks;
         n_blocks += adjoint_blocks(L->h_dev[c]);
     }
-    for (auto& g : adj_groups) {
-        if (e != cudaSuccess) break;
-        e = cudaMalloc(&g.d_tasks, sizeof(BandTask) * g.tasks.size());
-        if (e == cudaSuccess)
+    {
+        size_t n_tasks = 0;
+        for (auto& g : adj_groups) n_tasks += g.tasks.size();
+        BandTask* tasks = nullptr;
+        if (e == cudaSuccess && n_tasks > 0) e = reserve(xy_lattice::kAdjTasks, sizeof(BandTask) * n_tasks, &tasks);
+        for (auto& g : adj_groups) {
+            if (e != cudaSuccess) break;
+            g.d_tasks = tasks;
             e = cudaMemcpy(g.d_tasks, g.tasks.data(), sizeof(BandTask) * g.tasks.size(), cudaMemcpyHostToDevice);
+            tasks += g.tasks.size();
+        }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&gacc, sizeof(double) * kGacc * n_blocks);
+    if (e == cudaSuccess) e = reserve(xy_lattice::kAdjGacc, sizeof(double) * kGacc * n_blocks, &gacc);
     // backward integration: per-block partial sums of M, two step slots per lattice
     int P = 1;
     for (auto& g : adj_groups) {
         const int per_block = g.wide ? 1 : 8 * (32 / (g.Lx / 4));
         P = std::max(P, (g.Ly / g.H + per_block - 1) / per_block);
     }
-    if (e == cudaSuccess && back) e = cudaMalloc(&mpart, sizeof(double) * 2 * P * L->B);
+    if (e == cudaSuccess && back) e = reserve(xy_lattice::kAdjMpart, sizeof(double) * 2 * P * L->B, &mpart);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cleanup();
         return fail(XY_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
     }
 #define CKA(call)                                                                                  \
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess) {                                                                   \
-            cleanup();                                                                             \
-            return fail(XY_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));                        \
-        }                                                                                          \
+        if (e_ != cudaSuccess) return fail(XY_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
     } while (0)
 #define RCA(expr)                                                                                  \
     do {                                                                                           \
         int r_ = (expr);                                                                           \
-        if (r_) {                                                                                  \
-            cleanup();                                                                             \
-            return r_;                                                                             \
-        }                                                                                          \
+        if (r_) return r_;                                                                         \
     } while (0)
     const size_t state_bytes = sizeof(float) * T;
     Span sp{L};
@@ -2293,10 +2318,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
         const int n_aux = std::min(n_slices, xy_lattice::kBranches + 1) - 1;
         if (n_aux > 0) {
             const cudaError_t e0 = ensure_branch_streams(L);
-            if (e0 != cudaSuccess) {
-                cleanup();
-                return fail(XY_ECUDA, "reverse streams: %s", cudaGetErrorString(e0));
-            }
+            if (e0 != cudaSuccess) return fail(XY_ECUDA, "reverse streams: %s", cudaGetErrorString(e0));
         }
         if (n_aux > 0) CKA(cudaEventRecord(L->fork_ev, L->stream));
         for (int i = 0; i < n_aux; ++i) CKA(cudaStreamWaitEvent(L->aux[i], L->fork_ev, 0));
@@ -2487,7 +2509,6 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
     // restore the idle window
     set_window_idle(L);
     RCA(upload_cfg(L));
-    cleanup();
 #undef CKA
 #undef RCA
     return XY_OK;
