@@ -70,10 +70,12 @@ __device__ __forceinline__ float warp_sumf_b(float v)
 
 // WIDE: Lx > 128 (a block spans one band of Lx / 128 strips); OBS: k > k0;
 // BACK: the state of step k is recovered from that of step k + 1 (every
-// launch but the first, which reads the final state itself).  At 128
+// launch but the first, which reads the final state itself); SCHED: some
+// configuration of the launch has a field or coupling schedule (without one
+// the step's constants are the configuration's own and no knot is searched).  At 128
 // registers an SM partition holds four warps (16 per SM), enough for bands
 // of 16 rows on 64 lattices of 256 x 256 to run in one wave.
-template <bool WIDE, bool OBS, bool BACK>
+template <bool WIDE, bool OBS, bool BACK, bool SCHED>
 __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs, const BandTask* tasks, int H,
                                                               BackArgs R, PhiloxKeys keys)
 {
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     const float* vbI = R.vb_in + lat_off;
     float* tbO = R.tb_out + lat_off;
     float* vbO = R.vb_out + lat_off;
-    const StepConst K = step_const_k(cf, R.k, noise_amp(cf, R.k));
+    const StepConst K = SCHED ? step_const_k(cf, R.k, noise_amp(cf, R.k)) : step_const(cf, noise_amp(cf, R.k));
     const float q2 = K.q * K.q, hp2 = K.hp * cf.p;
     const float invN = 1.0f / (float)cf.N, wE = R.wE;
     constexpr bool observe = OBS, first = !OBS;
@@ -139,8 +141,9 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     }
     // configuration constants in registers (the cp.async statements clobber
     // memory, which would otherwise reload them from the descriptor every row)
-    const float2 Jk = couplings_at(cf, R.k), abk = coupling_scales(cf, R.k);
-    const float Jx = Jk.x, Jy = Jk.y, hF = field_h(cf, R.k);
+    const float2 Jk = SCHED ? couplings_at(cf, R.k) : make_float2(cf.Jx, cf.Jy);
+    const float2 abk = SCHED ? coupling_scales(cf, R.k) : make_float2(1.f, 1.f);
+    const float Jx = Jk.x, Jy = Jk.y, hF = SCHED ? field_h(cf, R.k) : cf.h;
     const float q2Jx = q2 * Jx, q2Jy = q2 * Jy;
     const bool stag = cf.stag != 0;
     const float wEn = wE * invN;
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(512, 1) adjoint_back_kernel(const DevCfg* cfgs
     const float vals[kGacc + 1] = {
         fmaf(-K.q, aJx, -wEn * sbx) * abk.x,                                // d/d J_par (J_par(k) = J_par a(k))
         fmaf(-K.q, aJy, -wEn * sby) * abk.y,                                // d/d J_perp (J_perp b(k))
-        fmaf(K.p, ah, wEn * scp) * field_scale(cf, R.k),                    // d/d h (h_k = h s(k))
+        fmaf(K.p, ah, wEn * scp) * (SCHED ? field_scale(cf, R.k) : 1.f),    // d/d h (h_k = h s(k))
         abar, bbar, cbar,
         wEn * fmaf(0.5f, sw2, fmaf(-Jx, sbx, fmaf(-Jy, sby, hF * scp))),  // w_E E / N
         pm,                                                                 // sum of sigma sin(q theta_k)
@@ -406,13 +409,17 @@ cudaError_t launch_adjoint_back(const DevCfg* d_cfg, const BandTask* tasks, int 
     const int smem = (threads / 32) * 2 * 4 * 32 * (int)sizeof(float4);
     const bool obs = R.k > R.k0;
     using Kern = void (*)(const DevCfg*, const BandTask*, int, BackArgs, PhiloxKeys);
-    static const Kern table[2][2][2] = {
-        {{adjoint_back_kernel<false, false, false>, adjoint_back_kernel<false, false, true>},
-         {adjoint_back_kernel<false, true, false>, adjoint_back_kernel<false, true, true>}},
-        {{adjoint_back_kernel<true, false, false>, adjoint_back_kernel<true, false, true>},
-         {adjoint_back_kernel<true, true, false>, adjoint_back_kernel<true, true, true>}},
+    static const Kern table[2][2][2][2] = {
+        {{{adjoint_back_kernel<false, false, false, false>, adjoint_back_kernel<false, false, true, false>},
+          {adjoint_back_kernel<false, true, false, false>, adjoint_back_kernel<false, true, true, false>}},
+         {{adjoint_back_kernel<true, false, false, false>, adjoint_back_kernel<true, false, true, false>},
+          {adjoint_back_kernel<true, true, false, false>, adjoint_back_kernel<true, true, true, false>}}},
+        {{{adjoint_back_kernel<false, false, false, true>, adjoint_back_kernel<false, false, true, true>},
+          {adjoint_back_kernel<false, true, false, true>, adjoint_back_kernel<false, true, true, true>}},
+         {{adjoint_back_kernel<true, false, false, true>, adjoint_back_kernel<true, false, true, true>},
+          {adjoint_back_kernel<true, true, false, true>, adjoint_back_kernel<true, true, true, true>}}},
     };
-    const Kern kern = table[wide][obs][back];
+    const Kern kern = table[R.sched != 0][wide][obs][back];
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;

@@ -477,14 +477,15 @@ struct Span {
     int close() { return timed_end(end, L->stream); }
 };
 
-// Whether some configuration of a strip group has a field or coupling
-// schedule (its launches then take the kernels that evaluate them).
-bool group_sched(const xy_lattice* L, const StripGroup& g)
+// Whether some configuration in cfgs has a field or coupling schedule (the
+// launches over them then take the kernels that evaluate them).
+bool any_sched(const xy_lattice* L, const std::vector<int>& cfgs)
 {
-    for (int c : g.cfgs)
+    for (int c : cfgs)
         if (L->h_dev[c].f_n_knots != 0 || L->h_dev[c].c_n_knots != 0) return true;
     return false;
 }
+bool group_sched(const xy_lattice* L, const StripGroup& g) { return any_sched(L, g.cfgs); }
 
 // Bit g: strip group g has a schedule (part of a captured chunk's key).
 uint32_t sched_mask(const xy_lattice* L)
@@ -2148,6 +2149,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
                 auto tune_launch = [&](int h, int reps) -> cudaError_t {
                     if (back) {
                         BackArgs A{};
+                        A.sched = any_sched(L, g.cfgs);
                         A.th_in = sbuf;
                         A.v_in = sbuf + T;
                         A.th_out = sbuf + 2 * T;
@@ -2333,6 +2335,7 @@ int xy_adjoint_step_n(xy_lattice* L, int64_t n, int K, double wE, double wM, dou
             int q = 0;  // slice of the sweep
             for (auto& g : adj_groups) {
                 BackArgs A{};
+                A.sched = any_sched(L, g.cfgs);
                 A.th_in = in_th;
                 A.v_in = in_v;
                 A.th_out = bk ? out_th : nullptr;

@@ -209,7 +209,7 @@ struct TileSmem {
 // global indices, so a tile root is its piece's smallest site.
 __global__ void __launch_bounds__(32 * kTileWarps, 12) ccl_tile_kernel(const float* __restrict__ theta, int Lx, int Ly,
                                                                      int n_lat, int32_t* __restrict__ labels,
-                                                                     int want_sizes, CclScratch s, int* err)
+                                                                     CclScratch s, int* err)
 {
     __shared__ TileSmem sm[kTileWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -284,24 +284,22 @@ __global__ void __launch_bounds__(32 * kTileWarps, 12) ccl_tile_kernel(const flo
         }
     }
     __syncwarp();
-    if (want_sizes) {
-        // a root's entry becomes its piece's count: -1 - (size + kEdgeFlag * edge runs)
-        for (unsigned b = roots; b; b &= b - 1) P[ph(lane * 32 + __ffs(b) - 1)] = -1;
-        __syncwarp();
-        if (lane < thh) {
-            for (unsigned b = st; b; b &= b - 1) {
-                const int x = __ffs(b) - 1;
-                const int i = lane * 32 + x;
-                const int q = P[ph(i)];
-                const int r = q < 0 ? i : q;
-                const unsigned later = b & (b - 1);
-                const int end = later ? __ffs(later) - 1 : tw;
-                const bool edge = lane == 0 || lane == thh - 1 || x == 0 || end == tw;
-                atomicSub(&P[ph(r)], (end - x) + (edge ? kEdgeFlag : 0));
-            }
+    // a root's entry becomes its piece's count: -1 - (size + kEdgeFlag * edge runs)
+    for (unsigned b = roots; b; b &= b - 1) P[ph(lane * 32 + __ffs(b) - 1)] = -1;
+    __syncwarp();
+    if (lane < thh) {
+        for (unsigned b = st; b; b &= b - 1) {
+            const int x = __ffs(b) - 1;
+            const int i = lane * 32 + x;
+            const int q = P[ph(i)];
+            const int r = q < 0 ? i : q;
+            const unsigned later = b & (b - 1);
+            const int end = later ? __ffs(later) - 1 : tw;
+            const bool edge = lane == 0 || lane == thh - 1 || x == 0 || end == tw;
+            atomicSub(&P[ph(r)], (end - x) + (edge ? kEdgeFlag : 0));
         }
-        __syncwarp();
     }
+    __syncwarp();
 
     // labels, a row at a time (coalesced): each site's root through its run
     // start; the tile roots and spins of the edge sites go to the border pass
@@ -326,7 +324,6 @@ __global__ void __launch_bounds__(32 * kTileWarps, 12) ccl_tile_kernel(const flo
         const unsigned top = __shfl_sync(kAll, row, 0), bottom = __shfl_sync(kAll, row, thh - 1);
         if (lane == 0) s.edge_spin[t] = make_uint4(top, bottom, left, right);
     }
-    if (!want_sizes) return;
 
     // the pieces: whole domains into the histogram, edge pieces onto the list
     int n_edge = 0;
@@ -773,7 +770,7 @@ cudaError_t launch_ccl(const float* theta, int Lx, int Ly, int n_lat, int32_t* l
     cudaError_t e;
     if ((e = cudaMemsetAsync(s.list_n, 0, sizeof(int), st)) != cudaSuccess) return e;
     ccl_tile_kernel<<<(unsigned)((tiles + kTileWarps - 1) / kTileWarps), 32 * kTileWarps, 0, st>>>(
-        theta, Lx, Ly, n_lat, labels, 1, s, err);
+        theta, Lx, Ly, n_lat, labels, s, err);
     ccl_border_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(Lx, Ly, n_lat, labels, s, err);
     const unsigned g = (unsigned)std::min<int64_t>((s.list_cap + 255) / 256, 152 * 8);
     ccl_list_size_kernel<<<g, 256, 0, st>>>(N, labels, s, err);

@@ -266,6 +266,7 @@ struct BackArgs {
     float wE, wM;
     double* gacc;        // [blocks][kGacc]
     int block_base;
+    int sched;           // some configuration of the tasks has a field or coupling schedule
 };
 cudaError_t launch_adjoint_back(const DevCfg* d_cfg, const BandTask* tasks, int n_tasks, int Lx, int H, uint64_t seed,
                                 bool back, BackArgs R, cudaStream_t st);
