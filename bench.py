@@ -417,6 +417,18 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         te_serial = time.perf_counter() - t0
+        # where a serial step's time goes: the upload (xy_load, synchronous)
+        # and the stepping with the records' read-back, each host-timed
+        t_load, t_adv = [], []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            load(lat)
+            tb = time.perf_counter()
+            lat.step(INNER, record_every=INNER, t0=T0, rec=rec_host[0])
+            torch.cuda.synchronize()
+            t_load.append(tb - ta)
+            t_adv.append(time.perf_counter() - tb)
 
         s2 = torch.cuda.Stream()
         lat2 = Lattice(static_configs(seed=1 + rank), stream=s2)
@@ -450,7 +462,8 @@ def run_ours(args):
         extra["e2e"] = {"value": world * n_pipe * su_step / te, "unit": "site-updates/s",
                         "h2d_bytes_per_step": len(blob), "d2h_bytes_per_step": int(rec_host[0].numel() * 8),
                         "mode": "double-buffered: two lattice objects, each step's upload overlaps the other's stepping",
-                        "serial_value": world * n_e2e * su_step / te_serial}
+                        "serial_value": world * n_e2e * su_step / te_serial,
+                        "serial_upload_ms": round(min(t_load) * 1e3, 2), "serial_step_ms": round(min(t_adv) * 1e3, 2)}
         lat2.close()
         del lat2, rec_dev
 
