@@ -242,7 +242,7 @@ struct xy_lattice {
         int rec;
         uint32_t rec_mask;
         uint32_t kt2;
-        uint32_t sched;  // sched_mask() at capture: the strip kernels chosen by schedule presence
+        std::vector<uint8_t> sched;  // sched_flags() at capture: the strip kernels chosen by schedule presence
         cudaGraphExec_t exec;
         int64_t kernels;
     };
@@ -487,13 +487,12 @@ bool any_sched(const xy_lattice* L, const std::vector<int>& cfgs)
 }
 bool group_sched(const xy_lattice* L, const StripGroup& g) { return any_sched(L, g.cfgs); }
 
-// Bit g: strip group g has a schedule (part of a captured chunk's key).
-uint32_t sched_mask(const xy_lattice* L)
+// Entry g: strip group g has a schedule (part of a captured chunk's key).
+std::vector<uint8_t> sched_flags(const xy_lattice* L)
 {
-    uint32_t m = 0;
-    for (size_t g = 0; g < L->strip_groups.size() && g < 32; ++g)
-        if (group_sched(L, L->strip_groups[g])) m |= 1u << g;
-    return m;
+    std::vector<uint8_t> f(L->strip_groups.size());
+    for (size_t g = 0; g < f.size(); ++g) f[g] = group_sched(L, L->strip_groups[g]) ? 1 : 0;
+    return f;
 }
 
 // Whether strip group g takes the local steps [jl0, jl0 + cnt) two per launch:
@@ -502,7 +501,8 @@ uint32_t sched_mask(const xy_lattice* L)
 // of pairs, so that after it the state is where single steps would leave it.
 bool kt2_batch(const xy_lattice* L, int g, int64_t jl0, int cnt)
 {
-    if (!((L->cur_kt2 >> g) & 1u) || cnt % 4 != 0 || L->strip_groups[g].b2_H == 0) return false;
+    // (groups past the 32 bits of cur_kt2 always take one step per launch)
+    if (g >= 32 || !((L->cur_kt2 >> g) & 1u) || cnt % 4 != 0 || L->strip_groups[g].b2_H == 0) return false;
     if (L->cur_rec)
         for (int i = 0; i < cnt; ++i)
             if ((L->cur_mask >> ((jl0 + i) & 31)) & 1u) return false;
@@ -753,7 +753,7 @@ cudaError_t launch_branch(xy_lattice* L, cudaStream_t st, const Branch& br, int6
 // idle as its launch drains) instead of taking turns every step.
 int get_graph(xy_lattice* L, int chunk, xy_lattice::Graph** out)
 {
-    const uint32_t sm = sched_mask(L);
+    const std::vector<uint8_t> sm = sched_flags(L);
     for (auto& g : L->graphs)
         if (g.chunk == chunk && g.rec == L->cur_rec && g.rec_mask == L->cur_mask && g.kt2 == L->cur_kt2 &&
             g.sched == sm) {
