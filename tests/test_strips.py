@@ -18,6 +18,7 @@ from tests import inputs
 PARAMS = dict(oracle.PAPER_PARAMS, dt=0.05)
 KNOTS = ([0, 6], [3.0, 1.0])    # a quench inside the run
 FIELD = ([2, 9], [0.5, 1.5])    # and a field ramp
+COUPLINGS = ([3, 8], [1.0, 0.4], [1.0, 2.5])  # and coupling profiles (1 at the start)
 SEED = 5
 
 
@@ -28,9 +29,10 @@ def _whole_start(Lx, Ly, seed=SEED):
     return th, om
 
 
-def _whole_run(Lx, Ly, n, every):
+def _whole_run(Lx, Ly, n, every, couplings=None):
     th, om = _whole_start(Lx, Ly)
-    rec = oracle.run_lattice(Lx, Ly, 0, 0, SEED, PARAMS, KNOTS, 0, n, th, om, record_every=every, field=FIELD)
+    rec = oracle.run_lattice(Lx, Ly, 0, 0, SEED, PARAMS, KNOTS, 0, n, th, om, record_every=every, field=FIELD,
+                             couplings=couplings)
     return th.reshape(Ly, Lx), om.reshape(Ly, Lx), rec
 
 
@@ -40,10 +42,10 @@ def _buffers(s: st.Strip):
     return [s.fill(a.reshape(s.Ly, s.Lx)) for a in (th, om, F)]
 
 
-def _step_strip(s: st.Strip, bufs, k0, n, every):
+def _step_strip(s: st.Strip, bufs, k0, n, every, couplings=None):
     th, om, F = bufs
     return oracle.run_strip(s.Lx, s.Ly, s.buffer_y0, 0, 0, SEED, PARAMS, KNOTS, k0, n, th, om, F,
-                            rows=(s.halo, s.halo + s.rows), record_every=every, field=FIELD)
+                            rows=(s.halo, s.halo + s.rows), record_every=every, field=FIELD, couplings=couplings)
 
 
 # ---------------------------------------------------------------------------
@@ -104,11 +106,12 @@ def test_plan_rejects_what_it_cannot_feed():
 # split runs against the whole lattice (one process, all ranks' buffers)
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("couplings", [None, COUPLINGS], ids=["field", "field+couplings"])
 @pytest.mark.parametrize("Lx,Ly,world,k_t,n", [(10, 12, 2, 2, 9), (8, 22, 3, 3, 10), (6, 20, 4, 1, 7),
                                                (7, 9, 1, 2, 5), (12, 16, 2, 4, 11)])
-def test_split_run_equals_the_whole_lattice_bit_for_bit(Lx, Ly, world, k_t, n):
+def test_split_run_equals_the_whole_lattice_bit_for_bit(Lx, Ly, world, k_t, n, couplings):
     every = 2
-    th_w, om_w, rec_w = _whole_run(Lx, Ly, n, every)
+    th_w, om_w, rec_w = _whole_run(Lx, Ly, n, every, couplings)
     plan = st.plan_strips(Lx, Ly, world, k_t)
     copies = st.halo_copies(plan)
     bufs = [_buffers(s) for s in plan]
@@ -116,7 +119,7 @@ def test_split_run_equals_the_whole_lattice_bit_for_bit(Lx, Ly, world, k_t, n):
     k = 0
     for w in st.window_lengths(n, k_t):
         for s, b in zip(plan, bufs):
-            recs[s.rank].append(_step_strip(s, b, k, w, every))
+            recs[s.rank].append(_step_strip(s, b, k, w, every, couplings))
         k += w
         st.apply_copies(bufs, copies)
     th = np.empty((Ly, Lx))
