@@ -37,7 +37,7 @@ def strip(P):
     saved = test_strips.oracle
     test_strips.oracle = P.oracle
     try:
-        test_strips.test_split_run_equals_the_whole_lattice_bit_for_bit(8, 22, 3, 3, 10)
+        test_strips.test_split_run_equals_the_whole_lattice_bit_for_bit(8, 22, 3, 3, 10, test_strips.COUPLINGS)
     finally:
         test_strips.oracle = saved
 
